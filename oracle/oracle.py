@@ -1,0 +1,404 @@
+"""Plain CPU oracle for the sector-restricted bosonic-mode solver of
+Eberhardt, Zamora, Kopp & Abel (arXiv:2111.00050).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module.  It shares no code with
+the CUDA library in ``paper_2111_00050_gb300``; the heavy loops live in
+``qb_oracle.c`` (plain C, built by :func:`build`), the rest is plain numpy.
+
+Conventions (the readings of the paper this oracle follows):
+
+* H = sum_p w_p n_p + sum over ordered (p,q,r,s) with p+q = r+s (mod M) of
+  L_{pq;rs} a_p^dag a_q^dag a_r a_s, i.e. Eq. (Ham) with L_{pq;rs} equal to
+  Lambda^{rs}_{pq}/2 (upper indices annihilate, lower indices create).
+* Mode labels are i - (M-1)/2 for odd M (i for even M); momentum is conserved
+  modulo M and a sector is the pair (N, P = sum label*n mod M) (Sec. III B).
+* Expectations are <psi|O|psi>/<psi|psi>; n_tot = <N> = Tr M (Sec. II C-D).
+* RK4 is the classic four-stage scheme, applied sector by sector (Sec. III B:
+  sectors evolve independently).
+
+Parity pins for every function live in ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile qb_oracle.c into a shared library with the host C compiler."""
+    src = os.path.join(_HERE, "qb_oracle.c")
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", src, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        i64, i32, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+        lib.orc_sector_basis.restype = i64
+        lib.orc_sector_basis.argtypes = [i32, i32, i32, vp, i64]
+        lib.orc_find.restype = i64
+        lib.orc_find.argtypes = [i32, vp, i64, vp]
+        lib.orc_check_coupling.restype = i32
+        lib.orc_check_coupling.argtypes = [i32, vp]
+        lib.orc_apply_h.restype = i32
+        lib.orc_apply_h.argtypes = [i32, i64, vp, vp, vp, vp, vp, i32]
+        lib.orc_rk4.restype = i32
+        lib.orc_rk4.argtypes = [i32, i64, vp, vp, vp, vp, ctypes.c_double, i64]
+        lib.orc_moments.restype = None
+        lib.orc_moments.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp]
+        lib.orc_apply_mode_op.restype = None
+        lib.orc_apply_mode_op.argtypes = [i32, i32, vp, vp, vp, vp, vp, i32, i32, vp]
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def label(M: int, i: int) -> int:
+    """Momentum label of mode index i."""
+    return i - (M - 1) // 2 if M % 2 else i
+
+
+def labels(M: int) -> np.ndarray:
+    return np.array([label(M, i) for i in range(M)], dtype=np.int64)
+
+
+def sector_of(occ) -> tuple[int, int]:
+    """(N, P) of an occupation vector (Sec. III B)."""
+    occ = np.asarray(occ, dtype=np.int64)
+    M = occ.size
+    return int(occ.sum()), int(np.dot(labels(M), occ) % M)
+
+
+def sector_basis(M: int, N: int, P: int) -> np.ndarray:
+    """All occupation vectors of sector (N, P), lexicographic, shape [D, M]."""
+    lib = _L()
+    D = lib.orc_sector_basis(M, N, P, None, 0)
+    out = np.zeros((max(D, 0), M), dtype=np.int32)
+    if D > 0:
+        lib.orc_sector_basis(M, N, P, _p(out), D)
+    return out
+
+
+def sector_dim(M: int, N: int, P: int) -> int:
+    return int(_L().orc_sector_basis(M, N, P, None, 0))
+
+
+def check_coupling(M: int, L: np.ndarray) -> bool:
+    Lc = np.ascontiguousarray(L, dtype=np.complex128).reshape(-1)
+    return _L().orc_check_coupling(M, _p(Lc)) == 0
+
+
+class Space:
+    """A list of sectors with their concatenated lexicographic bases."""
+
+    def __init__(self, M: int, sectors):
+        self.M = M
+        self.sectors = [(int(N), int(P) % M) for N, P in sectors]
+        bases = [sector_basis(M, N, P) for N, P in self.sectors]
+        self.dims = np.array([b.shape[0] for b in bases], dtype=np.int64)
+        self.off = np.zeros(len(bases) + 1, dtype=np.int64)
+        self.off[1:] = np.cumsum(self.dims)
+        self.basis = np.ascontiguousarray(np.concatenate(bases, axis=0) if bases else np.zeros((0, M), np.int32))
+        self.secN = np.array([s[0] for s in self.sectors], dtype=np.int32)
+        self.secP = np.array([s[1] for s in self.sectors], dtype=np.int32)
+
+    @property
+    def total(self) -> int:
+        return int(self.off[-1])
+
+    def index_of(self, occ) -> int:
+        """Global index of an occupation vector, or -1."""
+        occ = np.ascontiguousarray(occ, dtype=np.int32)
+        N, P = sector_of(occ)
+        for s, (sN, sP) in enumerate(self.sectors):
+            if (sN, sP) == (N, P):
+                b = self.basis[self.off[s]:self.off[s + 1]]
+                k = _L().orc_find(self.M, _p(np.ascontiguousarray(b)), b.shape[0], _p(occ))
+                return -1 if k < 0 else int(self.off[s] + k)
+        return -1
+
+    def sector_slice(self, s: int) -> slice:
+        return slice(int(self.off[s]), int(self.off[s + 1]))
+
+
+def all_sectors(M: int, n_min: int, n_max: int):
+    return [(N, P) for N in range(n_min, n_max + 1) for P in range(M) if sector_dim(M, N, P) > 0]
+
+
+# --------------------------------------------------------------------------- H
+
+def apply_h(space: Space, w, L, psi: np.ndarray, dagger: bool = False) -> np.ndarray:
+    """H psi (or H^dag psi) sector by sector, Eq. (Ham) applied literally."""
+    M = space.M
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    Lc = np.ascontiguousarray(L, dtype=np.complex128).reshape(-1)
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    out = np.zeros_like(psi)
+    lib = _L()
+    for s in range(len(space.sectors)):
+        sl = space.sector_slice(s)
+        b = np.ascontiguousarray(space.basis[sl])
+        x = np.ascontiguousarray(psi[sl])
+        y = np.zeros_like(x)
+        rc = lib.orc_apply_h(M, b.shape[0], _p(b), _p(w), _p(Lc), _p(x), _p(y), int(dagger))
+        if rc != 0:
+            raise ValueError("coupling maps a ket outside its sector")
+        out[sl] = y
+    return out
+
+
+def rk4(space: Space, w, L, psi: np.ndarray, dt: float, steps: int) -> np.ndarray:
+    """`steps` classic RK4 steps of d psi/dt = -i H psi (Eq. Schr), per sector."""
+    M = space.M
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    Lc = np.ascontiguousarray(L, dtype=np.complex128).reshape(-1)
+    out = np.array(psi, dtype=np.complex128, copy=True)
+    lib = _L()
+    for s in range(len(space.sectors)):
+        sl = space.sector_slice(s)
+        b = np.ascontiguousarray(space.basis[sl])
+        x = np.ascontiguousarray(out[sl])
+        rc = lib.orc_rk4(M, b.shape[0], _p(b), _p(w), _p(Lc), _p(x), float(dt), int(steps))
+        if rc != 0:
+            raise ValueError("coupling maps a ket outside its sector")
+        out[sl] = x
+    return out
+
+
+def h_dense(space: Space, s: int, w, L) -> np.ndarray:
+    """Dense matrix of H restricted to sector s, column j = H e_j."""
+    sl = space.sector_slice(s)
+    D = sl.stop - sl.start
+    sub = Space(space.M, [space.sectors[s]])
+    Hm = np.zeros((D, D), dtype=np.complex128)
+    for j in range(D):
+        e = np.zeros(D, dtype=np.complex128)
+        e[j] = 1.0
+        Hm[:, j] = apply_h(sub, w, L, e)
+    return Hm
+
+
+# --------------------------------------------------------------- initial states
+
+def _fact(n: np.ndarray) -> np.ndarray:
+    return np.array([float(math.factorial(int(k))) for k in n.reshape(-1)]).reshape(n.shape)
+
+
+def number_state(space: Space, occ) -> np.ndarray:
+    """The single Fock ket |{n}> (Eq. numEigenstate)."""
+    psi = np.zeros(space.total, dtype=np.complex128)
+    k = space.index_of(occ)
+    if k < 0:
+        raise ValueError("occupation vector is not in the space")
+    psi[k] = 1.0
+    return psi
+
+
+def coherent_amplitudes(space: Space, z) -> np.ndarray:
+    """<n|z>_C = prod_i exp(-|z_i|^2/2) z_i^{n_i} / sqrt(n_i!) (Eq. coherentStates),
+    unnormalised over the held (truncated) space."""
+    z = np.asarray(z, dtype=np.complex128)
+    n = space.basis.astype(np.int64)
+    amp = np.ones(space.total, dtype=np.complex128)
+    for i in range(space.M):
+        amp *= np.exp(-abs(z[i]) ** 2 / 2) * np.power(z[i], n[:, i]) / np.sqrt(_fact(n[:, i]))
+    return amp
+
+
+def coherent_state(space: Space, z):
+    """Coherent state truncated to the held sectors and renormalised to 1.
+    Returns (psi, kept_norm) with kept_norm = sum |<n|z>|^2 before renormalising."""
+    amp = coherent_amplitudes(space, z)
+    kept = float(np.vdot(amp, amp).real)
+    return amp / math.sqrt(kept), kept
+
+
+def field_number_state(space: Space, z, n_tot: int) -> np.ndarray:
+    """Field number state (Eq. fieldNumState) with the amplitudes z/sqrt(sum|z|^2)
+    so that the multinomial weights sum to one: on kets with sum n = n_tot,
+    sqrt(n_tot!) prod_i zeta_i^{n_i}/sqrt(n_i!), zero elsewhere."""
+    z = np.asarray(z, dtype=np.complex128)
+    zeta = z / math.sqrt(float(np.sum(np.abs(z) ** 2)))
+    n = space.basis.astype(np.int64)
+    amp = np.full(space.total, math.sqrt(float(math.factorial(n_tot))), dtype=np.complex128)
+    for i in range(space.M):
+        amp *= np.power(zeta[i], n[:, i]) / np.sqrt(_fact(n[:, i]))
+    amp[n.sum(axis=1) != n_tot] = 0.0
+    return amp
+
+
+# ------------------------------------------------------------------ observables
+
+def moments(space: Space, psi: np.ndarray) -> dict:
+    """Raw moments <psi|O|psi> by acting with each operator on every ket."""
+    M = space.M
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    out = np.zeros(2 + 2 * M + 4 * M * M, dtype=np.float64)
+    _L().orc_moments(M, len(space.sectors), _p(space.secN), _p(space.secP), _p(space.off), _p(space.basis),
+                     _p(psi), _p(out))
+    c = out[2:].view(np.complex128)
+    return {
+        "norm": out[0],
+        "N": out[1],
+        "a": c[:M].copy(),
+        "Mij": c[M:M + M * M].reshape(M, M).copy(),
+        "aa": c[M + M * M:].reshape(M, M).copy(),
+    }
+
+
+def apply_mode_op(space: Space, psi: np.ndarray, kind: str, i: int) -> np.ndarray:
+    """a_i psi, a_i^dag psi or n_i psi on the held space."""
+    k = {"a": 0, "adag": 1, "n": 2}[kind]
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    out = np.zeros_like(psi)
+    _L().orc_apply_mode_op(space.M, len(space.sectors), _p(space.secN), _p(space.secP), _p(space.off),
+                           _p(space.basis), _p(psi), k, int(i), _p(out))
+    return out
+
+
+def vminus(dOdO: float, varO: complex) -> float:
+    """Minimum quadrature variance V_- = 1 + 2<dO^dag dO> - 2|Var O| (Eq. generalVminus)."""
+    return 1.0 + 2.0 * dOdO - 2.0 * abs(varO)
+
+
+def observables(space: Space, psi: np.ndarray, w=None, L=None) -> dict:
+    """Normalised observables of Sec. II C-E:
+    <a_i>, M_ij = <a_i^dag a_j>, <a_i a_j>, n_tot = Tr M, Q (Eq. Qparam),
+    principal eigenvalue/eigenvector of M (Eq. POcriterion), V_- for every mode
+    operator a_i and for a^p = sum_k xi_k a_k (Eq. a_op), and <H> if w, L given."""
+    m = moments(space, psi)
+    nrm = m["norm"]
+    a = m["a"] / nrm
+    Mij = m["Mij"] / nrm
+    aa = m["aa"] / nrm
+    n_tot = float(np.trace(Mij).real)
+    Q = float(sum(Mij[j, j].real - abs(a[j]) ** 2 for j in range(space.M)) / n_tot)
+    evals, evecs = np.linalg.eigh(Mij)
+    lam = float(evals[-1])
+    xi = evecs[:, -1]
+    Vm = [vminus(Mij[i, i].real - abs(a[i]) ** 2, aa[i, i] - a[i] ** 2) for i in range(space.M)]
+    dOdO = sum(np.conj(xi[k]) * xi[l] * (Mij[k, l] - np.conj(a[k]) * a[l]) for k in range(space.M)
+               for l in range(space.M))
+    varO = sum(xi[k] * xi[l] * (aa[k, l] - a[k] * a[l]) for k in range(space.M) for l in range(space.M))
+    out = {
+        "norm": nrm,
+        "N": m["N"] / nrm,
+        "a": a,
+        "Mij": Mij,
+        "aa": aa,
+        "n_tot": n_tot,
+        "Q": Q,
+        "lam_p": lam,
+        "eigvals": evals,
+        "xi": xi,
+        "gap": float(evals[-1] - evals[-2]) if space.M > 1 else float("inf"),
+        "Vminus_modes": np.array(Vm),
+        "Vminus_p": vminus(float(dOdO.real), varO),
+        "PO": 1.0 - lam / n_tot,
+    }
+    if w is not None and L is not None:
+        Hpsi = apply_h(space, w, L, psi)
+        out["H"] = float(np.vdot(psi, Hpsi).real / nrm)
+    return out
+
+
+# -------------------------------------------------------------------- mean field
+
+def mf_rhs(w, L, a):
+    """d a_k/dt = -i (w_k a_k + sum_{q,r,s} (L_{kq;rs} + L_{qk;rs}) a_q^* a_r a_s),
+    Eq. (classicalFieldEqns) with Lambda^{rs}_{kq} = 2 L^sym."""
+    L = np.asarray(L, dtype=np.complex128)
+    G = L + L.transpose(1, 0, 2, 3)
+    return -1j * (np.asarray(w) * a + np.einsum("kqrs,q,r,s->k", G, np.conj(a), a, a))
+
+
+def meanfield(w, L, a0, dt: float, steps: int, every: int = 1) -> np.ndarray:
+    """Classic RK4 of the mean-field equations; returns a[t_k] for k*every steps
+    (row 0 is the initial condition)."""
+    a = np.array(a0, dtype=np.complex128)
+    out = [a.copy()]
+    for st in range(1, steps + 1):
+        k1 = mf_rhs(w, L, a)
+        k2 = mf_rhs(w, L, a + 0.5 * dt * k1)
+        k3 = mf_rhs(w, L, a + 0.5 * dt * k2)
+        k4 = mf_rhs(w, L, a + dt * k3)
+        a = a + dt / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+        if st % every == 0:
+            out.append(a.copy())
+    return np.array(out)
+
+
+# --------------------------------------------------------------------- breaktime
+
+CROSSED, AT_START, NOT_CROSSED = 0, 1, 2
+
+
+def breaktime(values, dt_obs: float, thr: float):
+    """First sample with value >= thr, linearly interpolated with the previous
+    sample (Sec. IV C-D define the thresholds; the crossing rule is a reading).
+    Returns (t_br, flag)."""
+    v = np.asarray(values, dtype=np.float64)
+    for k in range(v.size):
+        if v[k] >= thr:
+            if k == 0:
+                return 0.0, AT_START
+            f = (thr - v[k - 1]) / (v[k] - v[k - 1])
+            return (k - 1 + f) * dt_obs, CROSSED
+    return float("nan"), NOT_CROSSED
+
+
+# ---------------------------------------------------------------------- adjoint
+
+def rk4_step_adjoint(space: Space, w, L, psi_n: np.ndarray, lam_next: np.ndarray, dt: float, dH_list):
+    """Exact discrete adjoint of one classic RK4 step psi' = Phi(psi).
+
+    Given the stored state psi_n and the cotangent lam_next = dloss/dpsi'^*, returns
+    (lam_n, [g_theta]) where lam_n = (dPhi/dpsi)^dag lam_next and
+    g_theta = 2 Re <lam_next, dPhi/dtheta> for each callable dH(v) = (dH/dtheta) v.
+    """
+    A = lambda v: -1j * dt * apply_h(space, w, L, v)
+    Ad = lambda v: 1j * dt * apply_h(space, w, L, v, dagger=True)
+    u1 = psi_n
+    k1 = A(u1)
+    u2 = psi_n + 0.5 * k1
+    k2 = A(u2)
+    u3 = psi_n + 0.5 * k2
+    k3 = A(u3)
+    u4 = psi_n + k3
+    # psi' = psi + (k1 + 2 k2 + 2 k3 + k4)/6, k_i = A u_i
+    g4 = lam_next / 6
+    ub4 = Ad(g4)
+    g3 = lam_next / 3 + ub4
+    ub3 = Ad(g3)
+    g2 = lam_next / 3 + 0.5 * ub3
+    ub2 = Ad(g2)
+    g1 = lam_next / 6 + 0.5 * ub2
+    ub1 = Ad(g1)
+    lam_n = lam_next + ub1 + ub2 + ub3 + ub4
+    grads = []
+    for dH in dH_list:
+        dA = lambda v: -1j * dt * dH(v)
+        g = 0.0
+        for gk, uk in ((g1, u1), (g2, u2), (g3, u3), (g4, u4)):
+            g += 2.0 * np.vdot(gk, dA(uk)).real
+        grads.append(g)
+    return lam_n, grads

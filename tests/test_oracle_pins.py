@@ -1,0 +1,466 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these tests touch the CUDA library.  Each pin is chosen so that a
+plausible mistake in the oracle (a dropped term, a wrong sign or index, a
+transposed operand, a factor of two in the coupling) fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.sparse as sp
+
+import oracle as orc
+import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- helpers
+
+def gen_function_dims(M, N):
+    """Sector sizes from the generating function prod_i 1/(1 - t x^{label_i}) taken
+    modulo x^M - 1: coefficient array c[n, k] = #kets with n particles, momentum k."""
+    lab = wl.mode_labels(M) % M
+    c = np.zeros((N + 1, M), dtype=object)
+    c[0, 0] = 1
+    for i in range(M):
+        new = np.zeros_like(c)
+        for n in range(N + 1):
+            for k in range(M):
+                if c[n, k] == 0:
+                    continue
+                for v in range(0, N - n + 1):
+                    new[n + v, (k + v * lab[i]) % M] += c[n, k]
+        c = new
+    return c[N]
+
+
+def fock_ops(M, cutoff):
+    """Annihilation operators on the truncated tensor-product space (sparse)."""
+    d = cutoff + 1
+    a1 = sp.diags([np.sqrt(np.arange(1, d))], [1], shape=(d, d), format="csr")
+    eye = sp.identity(d, format="csr")
+    ops = []
+    for i in range(M):
+        op = None
+        for k in range(M):
+            f = a1 if k == i else eye
+            op = f if op is None else sp.kron(op, f, format="csr")
+        ops.append(op)
+    return ops
+
+
+def fock_hamiltonian(M, cutoff, w, L):
+    a = fock_ops(M, cutoff)
+    ad = [x.conj().T.tocsr() for x in a]
+    H = sum(w[p] * (ad[p] @ a[p]) for p in range(M))
+    for p in range(M):
+        for q in range(M):
+            for r in range(M):
+                for s in range(M):
+                    if L[p, q, r, s] != 0:
+                        H = H + L[p, q, r, s] * (ad[p] @ ad[q] @ a[r] @ a[s])
+    return H.tocsr()
+
+
+def full_index(occ, cutoff):
+    d = cutoff + 1
+    idx = 0
+    for n in occ:
+        idx = idx * d + int(n)
+    return idx
+
+
+def random_hermitian_coupling(M, rng, scale=0.1):
+    """Random complex coupling with the operator symmetries and Hermiticity,
+    supported on momentum-conserving tuples only."""
+    L = (rng.standard_normal((M,) * 4) + 1j * rng.standard_normal((M,) * 4)) * scale
+    L = L * wl._conserving(M)
+    L = 0.5 * (L + np.conj(L.transpose(3, 2, 1, 0)))  # L_{pq;rs} = conj(L_{sr;qp}) term by term
+    return L
+
+
+def R4(z):
+    return 1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24
+
+
+# ------------------------------------------------------------- sector sizes
+
+def test_sector_dims_match_generating_function():
+    for M, N in [(1, 5), (3, 6), (5, 6), (5, 9), (7, 8), (4, 5), (6, 4)]:
+        c = gen_function_dims(M, N)
+        tot = 0
+        for P in range(M):
+            d = orc.sector_dim(M, N, P)
+            assert d == c[P], (M, N, P)
+            tot += d
+        assert tot == math.comb(N + M - 1, M - 1)  # stars and bars
+
+
+def test_sector_dims_golden():
+    """Stored sizes (written by tests/golden/make_sector_dims.py from the oracle),
+    re-derived here from the generating function; includes the M=11, N=20, P=0
+    sector of about 2.7M kets."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "sector_dims.txt")) if l.strip() and l[0] != "#"]
+    for M, N, P, D in ((int(a), int(b), int(c), int(d)) for a, b, c, d in rows):
+        assert gen_function_dims(M, N)[P % M] == D
+
+
+def test_sector_dim_scaling_appendix():
+    """App. A counts D ~ C(n, M-2) for exact momentum conservation.  Under the
+    modulo-M reading the momentum constraint only splits the C(N+M-1, M-1)
+    compositions into M nearly equal residue classes, so D ~ N^{M-1}/(M (M-1)!)."""
+    for M, N in [(5, 40), (7, 30)]:
+        comp = math.comb(N + M - 1, M - 1)
+        for P in range(M):
+            assert abs(orc.sector_dim(M, N, P) * M / comp - 1) < 0.01
+
+
+def test_basis_is_sorted_and_in_sector():
+    b = orc.sector_basis(5, 6, 0)
+    assert b.shape == (42, 5)
+    keys = [tuple(r) for r in b]
+    assert keys == sorted(keys) and len(set(keys)) == len(keys)
+    for r in b:
+        assert orc.sector_of(r) == (6, 0)
+
+
+# ---------------------------------------------------- Hamiltonian vs Fock space
+
+@pytest.mark.parametrize("case", ["random", "contact", "long_range", "paper"])
+def test_sector_hamiltonian_matches_tensor_product_construction(case):
+    rng = np.random.default_rng(1)
+    if case == "random":
+        M, N = 3, 4
+        w = rng.standard_normal(M)
+        L = random_hermitian_coupling(M, rng)
+    elif case == "contact":
+        M, N = 5, 3
+        w = wl.dispersion_quadratic(M)
+        L = wl.contact_coupling(M, -0.3)
+    elif case == "long_range":
+        M, N = 5, 3
+        w = wl.dispersion_abs(M)
+        L = wl.long_range_coupling(M, 0.7)
+    else:
+        M, N = 4, 3
+        w = rng.standard_normal(M)
+        L = wl.paper_coupling(M, -0.2, 0.05)
+    Hf = fock_hamiltonian(M, N, w, L)
+    for P in range(M):
+        sp_ = orc.Space(M, [(N, P)])
+        if sp_.total == 0:
+            continue
+        Hs = orc.h_dense(sp_, 0, w, L)
+        idx = [full_index(o, N) for o in sp_.basis]
+        ref = Hf[idx][:, idx].toarray()
+        np.testing.assert_allclose(Hs, ref, atol=1e-13, rtol=0)
+        # the sector is closed under H: no amplitude leaks to other kets
+        col_mass = np.asarray(abs(Hf[:, idx]).sum(axis=0)).ravel()
+        np.testing.assert_allclose(col_mass, np.abs(ref).sum(axis=0), atol=1e-12)
+
+
+def test_dagger_is_adjoint():
+    rng = np.random.default_rng(2)
+    M = 5
+    L = random_hermitian_coupling(M, rng)
+    L[0, 1, 2, 4] += 0.3  # break Hermiticity deliberately: dagger must still be the adjoint
+    L = L * wl._conserving(M)
+    w = rng.standard_normal(M)
+    sp_ = orc.Space(M, [(4, 1)])
+    x = rng.standard_normal(sp_.total) + 1j * rng.standard_normal(sp_.total)
+    y = rng.standard_normal(sp_.total) + 1j * rng.standard_normal(sp_.total)
+    lhs = np.vdot(y, orc.apply_h(sp_, w, L, x))
+    rhs = np.vdot(orc.apply_h(sp_, w, L, y, dagger=True), x)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_non_conserving_coupling_rejected():
+    M = 5
+    L = np.zeros((M,) * 4, dtype=np.complex128)
+    L[0, 0, 0, 1] = 1.0
+    assert not orc.check_coupling(M, L)
+    assert orc.check_coupling(M, wl.contact_coupling(M, 0.1))
+
+
+# ------------------------------------------------------------- integrator
+
+def test_rk4_discrete_exact_on_diagonal_hamiltonian():
+    """For diagonal H every amplitude is multiplied by R(-i E dt) per step."""
+    M = 3
+    w = np.array([0.7, -1.3, 2.1])
+    L = np.zeros((M,) * 4, dtype=np.complex128)
+    sp_ = orc.Space(M, orc.all_sectors(M, 0, 6))
+    rng = np.random.default_rng(3)
+    psi0 = rng.standard_normal(sp_.total) + 1j * rng.standard_normal(sp_.total)
+    E = sp_.basis @ w
+    dt, k = 1e-2, 300
+    ref = psi0 * R4(-1j * E * dt) ** k
+    got = orc.rk4(sp_, w, L, psi0, dt, k)
+    assert np.linalg.norm(got - ref) < 1e-12 * np.linalg.norm(ref)
+
+
+def test_rk4_equals_matrix_polynomial_on_interacting_sector():
+    M, N = 5, 4
+    w = wl.dispersion_quadratic(M)
+    L = wl.contact_coupling(M, -0.4)
+    sp_ = orc.Space(M, [(N, 1)])
+    Hs = orc.h_dense(sp_, 0, w, L)
+    lam, V = np.linalg.eigh(Hs)
+    rng = np.random.default_rng(4)
+    psi0 = rng.standard_normal(sp_.total) + 1j * rng.standard_normal(sp_.total)
+    dt, k = 2e-3, 400
+    ref = V @ (R4(-1j * lam * dt) ** k * (V.conj().T @ psi0))
+    got = orc.rk4(sp_, w, L, psi0, dt, k)
+    assert np.linalg.norm(got - ref) < 1e-12 * np.linalg.norm(ref)
+
+
+def test_norm_decay_and_energy_under_rk4():
+    """|R(iy)|^2 = 1 - y^6/72 + y^8/576 per eigencomponent: norm decays only at O(dt^6)."""
+    y = 0.3
+    assert abs(abs(R4(-1j * y)) ** 2 - (1 - y ** 6 / 72 + y ** 8 / 576)) < 1e-15
+    M, N = 5, 6
+    w = wl.dispersion_quadratic(M)
+    L = wl.contact_coupling(M, -0.1)
+    sp_ = orc.Space(M, [(N, 0)])
+    psi0 = orc.number_state(sp_, [0, 2, 2, 2, 0])
+    psi = orc.rk4(sp_, w, L, psi0, 1e-3, 2000)
+    assert abs(np.vdot(psi, psi).real - 1) < 1e-12
+    e0 = orc.observables(sp_, psi0, w, L)["H"]
+    e1 = orc.observables(sp_, psi, w, L)["H"]
+    assert abs(e1 - e0) < 1e-10 * abs(e0)
+
+
+# ------------------------------------------------- single-mode Kerr closed forms
+
+def kerr_exact(space, w, L, psi0, t):
+    """Exact propagation exp(-iHt) psi0 for the diagonal single-mode H."""
+    E = np.array([orc.h_dense(space, s, w, L).diagonal() for s in range(len(space.sectors))], dtype=object)
+    E = np.concatenate([np.asarray(e, dtype=np.complex128) for e in E]).real
+    return np.exp(-1j * E * t) * psi0
+
+
+@pytest.mark.parametrize("a0", [1.3 * np.exp(0.4j), 0.9 - 1.1j])
+def test_single_mode_kerr_closed_forms(a0):
+    """<a(t)> = a0 e^{-iwt} exp(|a0|^2 (e^{-2iLt} - 1)), <a^2(t)> = a0^2 e^{-i(2w+2L)t}
+    exp(|a0|^2 (e^{-4iLt} - 1)), Q(t) = 1 - exp(2|a0|^2 (cos 2Lt - 1)),
+    for H = w n + L a^dag a^dag a a and a coherent start."""
+    w, Lk = 0.7, 0.13
+    L = np.full((1, 1, 1, 1), Lk, dtype=np.complex128)
+    space = orc.Space(1, [(N, 0) for N in range(0, 45)])
+    psi0, kept = orc.coherent_state(space, [a0])
+    assert abs(kept - 1) < 1e-15
+    n0 = abs(a0) ** 2
+    for t in [0.0, 0.5, 2.0, 7.3]:
+        psi = kerr_exact(space, [w], L, psi0, t)
+        ob = orc.observables(space, psi)
+        a_ref = a0 * np.exp(-1j * w * t) * np.exp(n0 * (np.exp(-2j * Lk * t) - 1))
+        aa_ref = a0 ** 2 * np.exp(-1j * (2 * w + 2 * Lk) * t) * np.exp(n0 * (np.exp(-4j * Lk * t) - 1))
+        Q_ref = 1 - np.exp(2 * n0 * (np.cos(2 * Lk * t) - 1))
+        assert abs(ob["a"][0] - a_ref) < 1e-12
+        assert abs(ob["aa"][0, 0] - aa_ref) < 1e-12
+        assert abs(ob["Q"] - Q_ref) < 1e-12
+        assert abs(ob["n_tot"] - n0) < 1e-12
+        V_ref = 1 + 2 * (n0 - abs(a_ref) ** 2) - 2 * abs(aa_ref - a_ref ** 2)
+        assert abs(ob["Vminus_modes"][0] - V_ref) < 1e-11
+        assert abs(ob["Vminus_p"] - V_ref) < 1e-11
+
+
+def test_single_mode_kerr_rk4_converges_to_closed_form():
+    """The oracle's RK4 approaches the closed form at the O(dt^4) rate."""
+    w, Lk, a0 = 0.5, 0.1, 1.1 + 0.3j
+    L = np.full((1, 1, 1, 1), Lk, dtype=np.complex128)
+    space = orc.Space(1, [(N, 0) for N in range(0, 40)])
+    psi0, _ = orc.coherent_state(space, [a0])
+    t = 1.0
+    a_ref = a0 * np.exp(-1j * w * t) * np.exp(abs(a0) ** 2 * (np.exp(-2j * Lk * t) - 1))
+    errs = []
+    for dt in (1e-2, 5e-3):
+        psi = orc.rk4(space, [w], L, psi0, dt, int(round(t / dt)))
+        errs.append(abs(orc.observables(space, psi)["a"][0] - a_ref))
+    assert errs[0] < 1e-6
+    assert 10 < errs[0] / errs[1] < 22  # ~2^4
+
+
+def test_vminus_bajer_approximation_and_squeezing_onset():
+    """Eq. (VminusBajer) approximates the exact single-mode V_-(tau), tau = n_tot|chi|t,
+    with chi = L for L = Lambda/2 (a factor-two slip in the coupling fails this);
+    V_- = 0.8 is reached near tau = 0.05 (Sec. II E: t_sqz ~ 0.05/(n_tot|chi|), the
+    linear estimate 1 - 4 tau; the curvature of Eq. (VminusBajer) moves it to ~0.056)."""
+    n_tot, Lk = 25.0, -0.004
+    L = np.full((1, 1, 1, 1), Lk, dtype=np.complex128)
+    space = orc.Space(1, [(N, 0) for N in range(0, 100)])
+    psi0, _ = orc.coherent_state(space, [math.sqrt(n_tot)])
+    chi = abs(Lk)
+    worst = 0.0
+    taus = np.linspace(0.0, 0.3, 31)
+    vs = []
+    for tau in taus:
+        t = tau / (n_tot * chi)
+        ob = orc.observables(space, kerr_exact(space, [0.0], L, psi0, t))
+        s = math.sqrt(1 + 4 * tau ** 2)
+        v_b = 1 - 4 * tau * s + 8 * tau ** 2 + 8 * tau ** 3 * (5 + 12 * tau ** 2) / (n_tot * s) - 16 * tau ** 4 / n_tot
+        worst = max(worst, abs(ob["Vminus_p"] - v_b))
+        vs.append(ob["Vminus_p"])
+    assert worst < 1e-3
+    tau_sqz = np.interp(0.8, vs[::-1], taus[::-1])
+    assert abs(tau_sqz - 0.05) < 0.01
+
+
+# ------------------------------------------------------------- initial states
+
+def test_coherent_layer_weights_are_poisson():
+    M = 3
+    z = np.array([0.8 + 0.2j, -0.5j, 1.1])
+    space = orc.Space(M, orc.all_sectors(M, 0, 30))
+    amp = orc.coherent_amplitudes(space, z)
+    lam = float(np.sum(np.abs(z) ** 2))
+    Ns = space.basis.sum(axis=1)
+    for N in range(12):
+        wN = float(np.sum(np.abs(amp[Ns == N]) ** 2))
+        assert abs(wN - math.exp(-lam) * lam ** N / math.factorial(N)) < 1e-14
+
+
+def test_coherent_t0_observables():
+    M = 5
+    z = np.array([0, 1.2j, 0.9, -0.7 + 0.4j, 0])
+    space = orc.Space(M, orc.all_sectors(M, 0, 25))
+    psi, kept = orc.coherent_state(space, z)
+    ob = orc.observables(space, psi)
+    n_tot = float(np.sum(np.abs(z) ** 2))
+    assert abs(kept - 1) < 1e-12
+    np.testing.assert_allclose(ob["a"], z, atol=1e-12)
+    assert abs(ob["Q"]) < 1e-12
+    assert abs(ob["lam_p"] - n_tot) < 1e-11
+    assert abs(ob["Vminus_p"] - 1) < 1e-11
+    np.testing.assert_allclose(ob["Vminus_modes"], 1.0, atol=1e-11)
+    # principal eigenvector is z^*/|z| up to a phase (Sec. II D)
+    ov = abs(np.vdot(np.conj(z) / math.sqrt(n_tot), ob["xi"]))
+    assert abs(ov - 1) < 1e-12
+
+
+def test_field_number_state_t0():
+    M = 5
+    n = np.array([0, 3, 2, 1, 0])
+    z = np.sqrt(n) * np.exp(1j * np.array([0, 0.3, 1.9, -2.2, 0]))
+    n_tot = int(n.sum())
+    space = orc.Space(M, [(n_tot, P) for P in range(M)])
+    psi = orc.field_number_state(space, z, n_tot)
+    assert abs(np.vdot(psi, psi).real - 1) < 1e-13  # multinomial theorem
+    ob = orc.observables(space, psi)
+    np.testing.assert_allclose(ob["a"], 0, atol=1e-14)
+    assert abs(ob["Q"] - 1) < 1e-13
+    assert abs(ob["lam_p"] - n_tot) < 1e-12
+    np.testing.assert_allclose(ob["Mij"], np.outer(np.conj(z), z), atol=1e-12)
+
+
+def test_number_state_t0():
+    M = 5
+    occ = [0, 2, 2, 2, 0]
+    space = orc.Space(M, [(6, 0)])
+    ob = orc.observables(space, orc.number_state(space, occ))
+    np.testing.assert_allclose(ob["Mij"], np.diag(occ), atol=1e-15)
+    assert abs(ob["lam_p"] - 2) < 1e-14 and ob["gap"] < 1e-12
+    assert abs(ob["Q"] - 1) < 1e-15
+
+
+def test_moments_match_fock_space_operators():
+    """<a_i>, <a_i^dag a_j>, <a_i a_j> against the tensor-product construction."""
+    M, cutoff = 3, 5
+    rng = np.random.default_rng(5)
+    space = orc.Space(M, orc.all_sectors(M, 0, cutoff))
+    psi = rng.standard_normal(space.total) + 1j * rng.standard_normal(space.total)
+    full = np.zeros((cutoff + 1) ** M, dtype=np.complex128)
+    for k, o in enumerate(space.basis):
+        full[full_index(o, cutoff)] = psi[k]
+    a = fock_ops(M, cutoff)
+    # only kets with N <= cutoff are held: truncate operators the same way
+    keep = np.zeros_like(full, dtype=bool)
+    keep[[full_index(o, cutoff) for o in space.basis]] = True
+    proj = lambda v: np.where(keep, v, 0)
+    m = orc.moments(space, psi)
+    for i in range(M):
+        assert abs(m["a"][i] - np.vdot(full, proj(a[i] @ full))) < 1e-11
+        for j in range(M):
+            assert abs(m["Mij"][i, j] - np.vdot(full, proj(a[i].conj().T @ (a[j] @ full)))) < 1e-11
+            assert abs(m["aa"][i, j] - np.vdot(full, proj(a[i] @ (a[j] @ full)))) < 1e-11
+
+
+# ---------------------------------------------------------------- mean field
+
+def test_meanfield_free_and_single_mode():
+    M = 5
+    w = wl.dispersion_quadratic(M)
+    z = np.array([0.3, 1j, 0.5 - 0.5j, 2.0, 0.1j])
+    L0 = np.zeros((M,) * 4, dtype=np.complex128)
+    traj = orc.meanfield(w, L0, z, 1e-3, 3000, every=1000)
+    for k, t in enumerate([0, 1, 2, 3]):
+        np.testing.assert_allclose(traj[k], z * np.exp(-1j * w * t), atol=1e-10)
+    Lk, a0 = 0.2, 1.3 + 0.2j
+    L1 = np.full((1, 1, 1, 1), Lk, dtype=np.complex128)
+    traj = orc.meanfield([0.4], L1, [a0], 1e-3, 2000, every=2000)
+    ref = a0 * np.exp(-1j * (0.4 + 2 * Lk * abs(a0) ** 2) * 2.0)
+    assert abs(traj[-1][0] - ref) < 1e-10
+
+
+def test_quantum_free_coherent_follows_classical_field():
+    """At L = 0 the coherent state stays coherent: <a_p(t)> = z_p e^{-i w_p t}."""
+    M = 3
+    w = np.array([0.5, 0.0, 0.5])
+    L0 = np.zeros((M,) * 4, dtype=np.complex128)
+    z = np.array([0.6, 0.8j, -0.4])
+    space = orc.Space(M, orc.all_sectors(M, 0, 22))
+    psi0, _ = orc.coherent_state(space, z)
+    psi = orc.rk4(space, w, L0, psi0, 1e-3, 1000)
+    ob = orc.observables(space, psi)
+    np.testing.assert_allclose(ob["a"], z * np.exp(-1j * w * 1.0), atol=1e-10)
+    assert abs(ob["Q"]) < 1e-10
+
+
+# ------------------------------------------------------------------ breaktime
+
+def test_breaktime_rule():
+    t, f = orc.breaktime([0.0, 0.05, 0.08, 0.12, 0.3], 0.5, 0.1)
+    assert f == orc.CROSSED and abs(t - (1.0 + 0.5 * 0.5)) < 1e-15
+    assert orc.breaktime([0.2, 0.3], 1.0, 0.1) == (0.0, orc.AT_START)
+    t, f = orc.breaktime([0.0, 0.01], 1.0, 0.1)
+    assert f == orc.NOT_CROSSED and math.isnan(t)
+
+
+# ------------------------------------------------------------------- adjoint
+
+def test_rk4_step_adjoint_matches_finite_differences():
+    """The oracle's discrete adjoint of one RK4 step against central differences."""
+    M, N = 3, 3
+    rng = np.random.default_rng(6)
+    w = rng.standard_normal(M)
+    L0 = wl.contact_coupling(M, 1.0)
+    C = -0.3
+    space = orc.Space(M, [(N, P) for P in range(M)])
+    psi = rng.standard_normal(space.total) + 1j * rng.standard_normal(space.total)
+    c = rng.standard_normal(space.total) + 1j * rng.standard_normal(space.total)
+    dt = 0.05
+
+    def loss(Cv, wv, ps):
+        out = orc.rk4(space, wv, Cv * L0, ps, dt, 1)
+        return float(np.vdot(c, out).real)
+
+    lam_next = c / 2  # d Re<c, psi'> / d psi'^* = c/2
+    nop = lambda v: orc.apply_h(space, np.zeros(M), L0, v)
+    dws = [lambda v, i=i: orc.apply_mode_op(space, v, "n", i) for i in range(M)]
+    lam0, g = orc.rk4_step_adjoint(space, w, C * L0, psi, lam_next, dt, [nop] + dws)
+    h = 1e-6
+    fd_C = (loss(C + h, w, psi) - loss(C - h, w, psi)) / (2 * h)
+    assert abs(g[0] - fd_C) < 1e-7 * max(1, abs(fd_C))
+    for i in range(M):
+        e = np.zeros(M)
+        e[i] = h
+        fd = (loss(C, w + e, psi) - loss(C, w - e, psi)) / (2 * h)
+        assert abs(g[1 + i] - fd) < 1e-7 * max(1, abs(fd))
+    # state cotangent: d loss = 2 Re <lam0, d psi>
+    d = rng.standard_normal(space.total) + 1j * rng.standard_normal(space.total)
+    fd = (loss(C, w, psi + h * d) - loss(C, w, psi - h * d)) / (2 * h)
+    assert abs(2 * np.vdot(lam0, d).real - fd) < 1e-7 * max(1, abs(fd))
