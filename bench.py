@@ -1,0 +1,306 @@
+"""Benchmark: Fock-space H psi terms/s and RK4 steps/s on one GB300.
+
+Workload (default): the batched coherent state -- M=7 ring modes, w_p = p^2/2,
+contact coupling C = -0.05/n_tot, alpha = sqrt(n_tot/2) on p = -1 and p = +1 at
+n_tot = 16, every Poisson-weighted sector N <= n_tot + 6 sqrt(n_tot) = 40 (287
+sectors, 62,891,499 kets, complex128), advanced together.  A step is one RK4
+step of the whole state (four fused H psi stages over every sector).
+
+The state (1 GB) is larger than L2 (129 MB), so no L2 flush is needed between
+steps.  Prints ONE JSON line (rank 0).
+
+--impl reference times the CPU oracle (oracle/) as it stands, single-threaded,
+on a bounded sample of the same workload (one RK4 step of the N=16 sectors).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as wl  # noqa: E402
+
+MEASURED_FP64_TFLOPS = 1.0  # DFMA microbenchmark on this machine's GB300 (profiles/fp64_peak_probe.md)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int = 0):
+        self.rows = []
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(name: str):
+    if name == "batched_coherent":
+        W = wl.batched_coherent()
+        return W, dict(n_min=0, n_max=W.n_max, p_list=None)
+    if name == "large_sector":
+        W = wl.large_sector()
+        return W, dict(n_min=20, n_max=20, p_list=[0])
+    if name == "plain_single_sector":
+        W = wl.plain_single_sector()
+        return W, dict(n_min=6, n_max=6, p_list=[0])
+    raise SystemExit(f"unknown config {name}")
+
+
+def init_state(qs, W, psi):
+    if W.kind == "coherent":
+        qs.init_coherent(W.z, psi)
+    elif W.kind == "number":
+        qs.init_number(W.occ, psi)
+    else:
+        qs.init_field_number(W.z, W.n_tot, psi)
+
+
+def run_reference(args):
+    """The CPU oracle, single-threaded, one RK4 step per timed step on a bounded
+    sample of the workload."""
+    import oracle as orc
+
+    W, sp = workload(args.config)
+    if W.kind == "coherent":
+        Ns = [min(16, W.n_max)]
+    else:
+        Ns = [W.n_min]
+    sectors = [(N, P) for N in Ns for P in range(W.M) if orc.sector_dim(W.M, N, P) > 0]
+    space = orc.Space(W.M, sectors)
+    rng = np.random.default_rng(0)
+    psi = rng.standard_normal(space.total) + 1j * rng.standard_normal(space.total)
+    psi /= np.linalg.norm(psi)
+    terms = orc.count_terms(space, W.L)
+    for _ in range(args.warmup):
+        psi = orc.rk4(space, W.w, W.L, psi, W.dt, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        psi = orc.rk4(space, W.w, W.L, psi, W.dt, 1)
+    dt_s = (time.perf_counter() - t0) / args.steps
+    value = 4 * terms / dt_s
+    sample = f"one RK4 step (4 H psi) of the sectors N={Ns} (all P) of {W.name}: {space.total} kets, {terms} terms"
+    line = {
+        "impl": "reference", "metric": "H_psi_terms_per_s", "value": value, "unit": "terms/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": W.name, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "terms/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def cpu_baseline(W, seconds_cap: float = 20.0):
+    """Times the oracle on one RK4 step of one N layer of the workload (all P)."""
+    import oracle as orc
+
+    N = min(12, W.n_max) if W.kind == "coherent" else W.n_min
+    sectors = [(N, P) for P in range(W.M) if orc.sector_dim(W.M, N, P) > 0]
+    space = orc.Space(W.M, sectors)
+    if space.total > 300000:  # bound the sample: a slice of rows of the first sector
+        sectors = sectors[:1]
+        space = orc.Space(W.M, sectors)
+    rng = np.random.default_rng(0)
+    psi = rng.standard_normal(space.total) + 1j * rng.standard_normal(space.total)
+    terms = orc.count_terms(space, W.L)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        psi = orc.rk4(space, W.w, W.L, psi, W.dt, 1)
+        n += 1
+        if time.perf_counter() - t0 > min(seconds_cap, 5.0) or n >= 50:
+            break
+    el = (time.perf_counter() - t0) / n
+    return {"value": 4 * terms / el, "unit": "terms/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} RK4 step(s) of sectors N={N} ({space.total} kets, {terms} terms/H psi) of {W.name}"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="qb", choices=["qb", "reference"])
+    ap.add_argument("--config", default="batched_coherent")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    import paper_2111_00050_gb300 as qb
+
+    W, sp = workload(args.config)
+    qs = qb.Space(W.M, W.w, W.L, sp["n_min"], sp["n_max"], sp["p_list"])
+    terms, tuples = qs.terms()
+    psi = qs.empty_state()
+    init_state(qs, W, psi)
+    work = qs.workspace(1)
+    for _ in range(args.warmup):
+        qs.evolve(psi, W.dt, 1, work)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K RK4 steps of the whole state
+    stream = torch.cuda.current_stream()
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    qs.evolve(psi, W.dt, args.steps, work)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    clocks = clk.stop()
+    ms_step = ms / args.steps
+    value = world * 4 * terms / (ms_step * 1e-3)
+    steps_per_s = 1e3 / ms_step
+
+    # ---- dominant kernel: one fused RK4 stage == one H psi over every sector
+    out = qs.empty_state()
+    for _ in range(2):
+        qs.hpsi(psi, out)
+    torch.cuda.synchronize()
+    durs = []
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        qs.hpsi(psi, out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        durs.append(a.elapsed_time(b))
+    t_launch = statistics.median(durs) * 1e-3
+    stage_time = ms_step * 1e-3 / 4
+    flops = 4.0 * terms  # >= 2 DFMA per term (real coefficient x complex amplitude)
+    achieved = flops / stage_time / 1e12
+    peaks = _peaks()
+    hbm_bytes = 32.0 * qs.total
+    roofline = {
+        "bound": "alu", "achieved": achieved, "peak": MEASURED_FP64_TFLOPS, "unit": "TFLOP/s",
+        "frac": achieved / MEASURED_FP64_TFLOPS, "traffic": None,
+        "kernel": "hpsi_kernel<MODE_STAGE> (one RK4 stage = one H psi over all sectors)",
+        "hbm_GBps": hbm_bytes / stage_time / 1e9, "hbm_peak_GBps": peaks.get("hbm_gbs"),
+        "hbm_frac": (hbm_bytes / stage_time / 1e9) / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+        "hpsi_launch_ms": t_launch * 1e3,
+        "peak_note": "FP64 DFMA rate measured on this GB300 (nominal 1.25 TFLOP/s)",
+    }
+
+    # ---- end to end through the public API with host buffers
+    host_in = torch.empty(qs.total, dtype=torch.complex128).pin_memory()
+    host_in.copy_(psi.cpu())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    k_e2e = max(1, min(args.steps, 3))
+    for _ in range(k_e2e):
+        psi.copy_(host_in, non_blocking=True)
+        qs.evolve(psi, W.dt, 1, work)
+        ob = qs.observables(psi)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / k_e2e
+    nmom = 4 + 2 * W.M + 4 * W.M * W.M
+    e2e = {"value": 4 * terms / e2e_s, "unit": "terms/s", "h2d_bytes_per_step": 16 * qs.total,
+           "d2h_bytes_per_step": 8 * nmom + 8 * 2, "steps_per_s": 1.0 / e2e_s,
+           "note": "H2D of psi from pinned memory + one RK4 step + qb_observables (moments D2H) per step"}
+
+    line = {
+        "metric": "H_psi_terms_per_s", "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": W.name, "kets": qs.total, "sectors": qs.n_sectors, "terms_per_hpsi": terms,
+                   "ordered_tuples_per_hpsi": tuples, "dt": W.dt, "rk4_steps_per_s": steps_per_s,
+                   "l2": "state (16 B/ket, %.2f GB) larger than L2; no flush" % (16 * qs.total / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "rk4_steps_per_s": steps_per_s,
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks,
+        "roofline": roofline,
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(W)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * qb -- C ABI of a GB300 (sm_103a) solver for interacting bosonic momentum
+ * modes on a ring, after Eberhardt, Zamora, Kopp & Abel, "On the single
+ * classical field description of interacting scalar fields" (arXiv:2111.00050).
+ *
+ * The many-body state lives in the Fock basis, restricted to "special Hilbert
+ * spaces" (sectors) of fixed particle number N and momentum P modulo M
+ * (Sec. III B).  The Hamiltonian is Eq. (Ham),
+ *
+ *     H = sum_p w_p a_p^dag a_p + sum_{p,q,r,s} L_{pq;rs} a_p^dag a_q^dag a_r a_s,
+ *
+ * summed over ORDERED tuples with p + q = r + s (mod M), where L_{pq;rs} is the
+ * paper's Lambda^{rs}_{pq} / 2 (upper indices are annihilated).  Mode index i
+ * carries momentum label i - (M-1)/2 for odd M and i for even M.
+ *
+ * Conventions shared by every call:
+ *  - Complex numbers are interleaved (re, im) doubles; a state vector is a
+ *    contiguous complex128 array over all sectors of a space, concatenated in
+ *    the order qb_space_sectors() reports (N ascending, then P ascending).
+ *    Within a sector kets are in lexicographic order of (n_0, n_1, ...).
+ *  - Pointers named d_* are DEVICE pointers owned by the caller (e.g. torch
+ *    tensors).  They must be 16-byte aligned, on the current CUDA device, and
+ *    stay valid until the stream has finished the call's work.  The library
+ *    never frees them.  Other pointers are host pointers.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls that return host results synchronise on the stream before returning.
+ *  - Every call returns a status: QB_OK or one of the QB_E* codes below.  On
+ *    error, qb_last_error() gives a message (thread-local) and no output is
+ *    written unless stated otherwise.
+ */
+#ifndef QB_H
+#define QB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QB_OK 0
+#define QB_EINVAL 1       /* bad argument: size, alignment, range, non-Hermitian or non-conserving L */
+#define QB_ENOMEM 2       /* a device or host allocation failed */
+#define QB_ECUDA 3        /* a CUDA runtime call or kernel launch failed */
+#define QB_ETIMEOUT 4     /* a bounded device-side wait ran out */
+#define QB_EINTERNAL 5    /* a device-side consistency check failed (rank out of range, ...) */
+#define QB_EUNSUPPORTED 6 /* outside the compiled limits (M > QB_MAX_MODES, packed occupation > 64 bits) */
+
+#define QB_MAX_MODES 16
+
+/* Breaktime flags (qb_breaktime). */
+#define QB_CROSSED 0
+#define QB_AT_START 1
+#define QB_NOT_CROSSED 2
+
+typedef struct qb_space qb_space; /* opaque; created by qb_sector_build, freed by qb_space_free */
+
+/* Model of Eq. (Ham).  w: [M] host doubles.  L: [M^4] host complex values as
+ * (re, im) pairs, index ((p*M + q)*M + r)*M + s.  Entries on tuples that do
+ * not conserve momentum mod M must be zero (the Kronecker delta of
+ * Eq. Lambda).  The library uses only the part symmetric under p<->q and
+ * r<->s and requires the Hermiticity L_{pq;rs} = conj(L_{rs;pq}) of that part. */
+typedef struct {
+  int M;
+  const double* w;
+  const double* L;
+} qb_model;
+
+/* Observables of Sec. II C-E for one state, normalised by <psi|psi>.
+ * Arrays are sized for QB_MAX_MODES; only the first M (or M*M, row-major)
+ * entries are meaningful.  Complex entries are (re, im) pairs. */
+typedef struct {
+  double t;                                  /* time of the sample (set by qb_evolve_observe) */
+  double norm;                               /* <psi|psi> */
+  double N;                                  /* <N> */
+  double H;                                  /* <H> */
+  double n_tot;                              /* Tr M = sum_i <a_i^dag a_i> */
+  double Q;                                  /* Eq. (Qparam): sum_j <da_j^dag da_j> / n_tot */
+  double lam_p;                              /* principal eigenvalue of M (Eq. POcriterion) */
+  double PO;                                 /* 1 - lam_p / n_tot */
+  double gap;                                /* lam_p minus the second eigenvalue */
+  double Vminus_p;                           /* Eq. (generalVminus) for a^p = sum_k xi_k a_k (Eq. a_op) */
+  double a[2 * QB_MAX_MODES];                /* <a_i> */
+  double Mij[2 * QB_MAX_MODES * QB_MAX_MODES]; /* <a_i^dag a_j> */
+  double aa[2 * QB_MAX_MODES * QB_MAX_MODES];  /* <a_i a_j> */
+  double xi[2 * QB_MAX_MODES];               /* principal eigenvector of M (unit norm, phase arbitrary) */
+  double eig[QB_MAX_MODES];                  /* eigenvalues of M, ascending */
+  double Vminus[QB_MAX_MODES];               /* Eq. (generalVminus) for each a_i */
+} qb_obs;
+
+/* Thread-local message for the last failing call on this thread. */
+const char* qb_last_error(void);
+
+/* ---- sectors (Sec. III B "special Hilbert spaces", App. A) -------------- */
+
+/* Builds the space of all non-empty sectors (N, P) with n_min <= N <= n_max and
+ * P (a momentum label taken mod M, in [0, M)) in p_list[0..n_p), or every P
+ * when p_list is NULL.  Copies and validates the model (conservation,
+ * Hermiticity), builds the combinatorial ranking tables and uploads them to the
+ * current device.  Limits: 1 <= M <= QB_MAX_MODES; M * bits(n_max) <= 64;
+ * every sector dimension < 2^31.  *out receives the new space. */
+int qb_sector_build(const qb_model* model, int n_min, int n_max, const int* p_list, int n_p, qb_space** out);
+
+void qb_space_free(qb_space* space);
+
+/* total_states: length of a state vector; n_sectors: number of sectors;
+ * max_dim: largest sector dimension.  Any pointer may be NULL. */
+int qb_space_info(const qb_space* space, int64_t* total_states, int* n_sectors, int64_t* max_dim);
+
+/* Per-sector N, P label (mod M, in [0, M)), dimension and offset into the
+ * state vector; each array has n_sectors entries (host).  Any may be NULL. */
+int qb_space_sectors(const qb_space* space, int* N, int* P, int64_t* dim, int64_t* offset);
+
+/* Writes the occupation vectors of global kets [first, first + count) to
+ * d_occ, int32 [count][M] (device), by unranking on the GPU. */
+int qb_space_basis(const qb_space* space, int64_t first, int64_t count, int* d_occ, void* stream);
+
+/* Global index of each occupation vector d_occ[count][M] (device, int32), or
+ * -1 if it is not a ket of the space; written to d_index[count] (device). */
+int qb_space_rank(const qb_space* space, const int* d_occ, int64_t count, int64_t* d_index, void* stream);
+
+/* Exact number of distinct nonzero matrix elements of H (diagonal included)
+ * over all rows of the space: the work of one H psi.  Also returns the number
+ * of ordered (p,q,r,s) tuples acting nontrivially, if `tuples` is not NULL. */
+int qb_space_terms(const qb_space* space, int64_t* terms, int64_t* tuples, void* stream);
+
+/* ---- initial states (Sec. II B; Sec. III B weights w^j_k(0)) ------------ */
+
+/* |{n}> for the host occupation vector occ[M] (Eq. numEigenstate). */
+int qb_init_number(qb_space* space, const int* occ, void* d_psi, void* stream);
+
+/* Coherent state (Eq. coherentStates) with host amplitudes z[2M], restricted to
+ * the space and renormalised to 1; *kept_norm (host, may be NULL) receives the
+ * squared norm the space held before renormalising. */
+int qb_init_coherent(qb_space* space, const double* z, void* d_psi, double* kept_norm, void* stream);
+
+/* Field number state (Eq. fieldNumState) of n_tot particles: on kets with
+ * sum n = n_tot, sqrt(n_tot!) prod_i zeta_i^{n_i} / sqrt(n_i!) with
+ * zeta = z / |z|, zero elsewhere (normalised by the multinomial theorem). */
+int qb_init_field_number(qb_space* space, const double* z, int n_tot, void* d_psi, void* stream);
+
+/* ---- time evolution (Eq. Schr; the per-sector parallel scheme of Sec. III B) */
+
+/* Bytes of device workspace qb_evolve / qb_evolve_batch need for `batch`
+ * state vectors. */
+int64_t qb_workspace_bytes(const qb_space* space, int batch);
+
+/* out = H psi for one state vector (d_out and d_psi distinct, device). */
+int qb_hpsi(qb_space* space, const void* d_psi, void* d_out, void* stream);
+
+/* `steps` RK4 steps of size dt of d psi/dt = -i H psi, in place on d_psi.
+ * RK4 is applied in the Horner form psi <- psi + z(psi + z/2(psi + z/3(psi +
+ * z/4 psi))), z = -i dt H, which equals the classic four-stage scheme for a
+ * linear time-independent H.  d_work: qb_workspace_bytes(space, 1) bytes. */
+int qb_evolve(qb_space* space, void* d_psi, double dt, int64_t steps, void* d_work, void* stream);
+
+/* Batched sweep: `batch` state vectors d_psi[batch][total], member b evolving
+ * under H_b = H_w + scale[b] * H_L (one-body part unchanged, two-body part
+ * scaled).  All sectors of all members advance in one launch per RK4 stage.
+ * scale: host [batch].  d_work: qb_workspace_bytes(space, batch) bytes. */
+int qb_evolve_batch(qb_space* space, void* d_psi, int batch, const double* scale, double dt, int64_t steps,
+                    void* d_work, void* stream);
+
+/* ---- observables (Sec. II C-E) ------------------------------------------- */
+
+/* All observables of one state; out (host) is written after the stream syncs. */
+int qb_observables(qb_space* space, const void* d_psi, qb_obs* out, void* stream);
+
+/* Evolution with observation: series[0] is the initial state, series[k] the
+ * state after k * obs_every steps, for k = 0 .. steps / obs_every (host array of
+ * steps / obs_every + 1 entries; series[k].t = k * obs_every * dt). */
+int qb_evolve_observe(qb_space* space, void* d_psi, double dt, int64_t steps, int obs_every, qb_obs* series,
+                      void* d_work, void* stream);
+
+/* ---- breaktime and mean field (Sec. III A, IV C-D) ----------------------- */
+
+/* First sample k with values[k] >= thr; t_br interpolates linearly between
+ * samples k-1 and k spaced dt_obs apart.  flag: QB_CROSSED, QB_AT_START (k = 0,
+ * t_br = 0) or QB_NOT_CROSSED (t_br = NaN).  Host only. */
+int qb_breaktime(const double* values, int n, double dt_obs, double thr, double* t_br, int* flag);
+
+/* Classic RK4 of the mean-field equations (Eq. classicalFieldEqns):
+ * da_k/dt = -i (w_k a_k + sum_{q,r,s} (L_{kq;rs} + L_{qk;rs}) a_q^* a_r a_s).
+ * z0: [2M] host; traj: host [(steps/every + 1)][2M], row 0 = z0.  Host only. */
+int qb_meanfield(const qb_model* model, const double* z0, double dt, int64_t steps, int every, double* traj);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QB_H */

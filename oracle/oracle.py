@@ -60,6 +60,10 @@ def _L():
         lib.orc_apply_h.argtypes = [i32, i64, vp, vp, vp, vp, vp, i32]
         lib.orc_rk4.restype = i32
         lib.orc_rk4.argtypes = [i32, i64, vp, vp, vp, vp, ctypes.c_double, i64]
+        lib.orc_apply_h_row.restype = i32
+        lib.orc_apply_h_row.argtypes = [i32, i64, vp, vp, vp, vp, i64, vp]
+        lib.orc_count_terms.restype = i64
+        lib.orc_count_terms.argtypes = [i32, i64, vp, vp]
         lib.orc_moments.restype = None
         lib.orc_moments.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp]
         lib.orc_apply_mode_op.restype = None
@@ -166,6 +170,24 @@ def apply_h(space: Space, w, L, psi: np.ndarray, dagger: bool = False) -> np.nda
     return out
 
 
+def apply_h_rows(space: Space, s: int, w, L, psi_sector: np.ndarray, rows) -> np.ndarray:
+    """(H psi)_i for the given local rows i of sector s only (psi_sector is that
+    sector's slice), by applying the adjoint of each term to ket i."""
+    M = space.M
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    Lc = np.ascontiguousarray(L, dtype=np.complex128).reshape(-1)
+    b = np.ascontiguousarray(space.basis[space.sector_slice(s)])
+    x = np.ascontiguousarray(psi_sector, dtype=np.complex128)
+    out = np.zeros(len(rows), dtype=np.complex128)
+    buf = np.zeros(1, dtype=np.complex128)
+    lib = _L()
+    for k, i in enumerate(rows):
+        if lib.orc_apply_h_row(M, b.shape[0], _p(b), _p(w), _p(Lc), _p(x), int(i), _p(buf)) != 0:
+            raise ValueError("coupling maps a ket outside its sector")
+        out[k] = buf[0]
+    return out
+
+
 def rk4(space: Space, w, L, psi: np.ndarray, dt: float, steps: int) -> np.ndarray:
     """`steps` classic RK4 steps of d psi/dt = -i H psi (Eq. Schr), per sector."""
     M = space.M
@@ -182,6 +204,16 @@ def rk4(space: Space, w, L, psi: np.ndarray, dt: float, steps: int) -> np.ndarra
             raise ValueError("coupling maps a ket outside its sector")
         out[sl] = x
     return out
+
+
+def count_terms(space: Space, L) -> int:
+    """Distinct nonzero H matrix elements of all held sectors, diagonal included."""
+    Lc = np.ascontiguousarray(L, dtype=np.complex128).reshape(-1)
+    tot = 0
+    for s in range(len(space.sectors)):
+        b = np.ascontiguousarray(space.basis[space.sector_slice(s)])
+        tot += int(_L().orc_count_terms(space.M, b.shape[0], _p(b), _p(Lc)))
+    return tot
 
 
 def h_dense(space: Space, s: int, w, L) -> np.ndarray:

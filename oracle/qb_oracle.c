@@ -347,3 +347,100 @@ void orc_apply_mode_op(int M, int nsec, const int* secN, const int* secP, const 
     }
   }
 }
+
+/*
+ * (H psi)_i for the single ket i of one sector, by definition:
+ * (H psi)_i = sum_j <n_i|H|n_j> psi_j, and <n_i|H|n_j> = conj(<n_j|H^dag|n_i>),
+ * where H^dag = sum_p w_p n_p + sum conj(L_{pq;rs}) a_s^dag a_r^dag a_q a_p is
+ * applied literally to |n_i>.  Lets a test check sampled rows of a sector far
+ * too large for the push-form orc_apply_h.  Returns 0 or -1.
+ */
+int orc_apply_h_row(int M, int64_t D, const int* basis, const double* w, const double* L, const double* psi,
+                    int64_t i, double* out2) {
+  int tmp[64];
+  const int* n = basis + i * M;
+  double accr = 0.0, acci = 0.0;
+  double diag = 0.0;
+  for (int p = 0; p < M; ++p) diag += w[p] * n[p];
+  accr += diag * psi[2 * i];
+  acci += diag * psi[2 * i + 1];
+  for (int p = 0; p < M; ++p)
+    for (int q = 0; q < M; ++q)
+      for (int r = 0; r < M; ++r)
+        for (int s = 0; s < M; ++s) {
+          if (mod_pos(label_of(M, p) + label_of(M, q) - label_of(M, r) - label_of(M, s), M) != 0) continue;
+          int64_t t = (((int64_t)p * M + q) * M + r) * M + s;
+          double lr = L[2 * t], li = L[2 * t + 1];
+          if (lr == 0.0 && li == 0.0) continue;
+          memcpy(tmp, n, sizeof(int) * (size_t)M);
+          double coef = 1.0;
+          /* adjoint term conj(L) a_s^dag a_r^dag a_q a_p: a_p first */
+          if (tmp[p] == 0) continue;
+          coef *= sqrt((double)tmp[p]);
+          tmp[p] -= 1;
+          if (tmp[q] == 0) continue;
+          coef *= sqrt((double)tmp[q]);
+          tmp[q] -= 1;
+          tmp[r] += 1;
+          coef *= sqrt((double)tmp[r]);
+          tmp[s] += 1;
+          coef *= sqrt((double)tmp[s]);
+          int64_t j = find_ket(M, basis, D, tmp);
+          if (j < 0) return -1;
+          /* <n_j|H^dag|n_i> = conj(L) coef; <n_i|H|n_j> = L coef */
+          double cr = lr * coef, ci = li * coef;
+          double xr = psi[2 * j], xi = psi[2 * j + 1];
+          accr += cr * xr - ci * xi;
+          acci += cr * xi + ci * xr;
+        }
+  out2[0] = accr;
+  out2[1] = acci;
+  return 0;
+}
+
+/*
+ * Number of distinct nonzero matrix elements <n_i|H|n_j> over all columns j of
+ * one sector, diagonal included (structural count: every ket a term reaches
+ * with a nonzero coupling counts once per column).  Used to express the
+ * oracle's speed in H psi terms per second.
+ */
+int64_t orc_count_terms(int M, int64_t D, const int* basis, const double* L) {
+  int tmp[64];
+  int64_t total = 0;
+  int64_t cap = 1024, *tg = malloc(sizeof(int64_t) * (size_t)cap);
+  for (int64_t j = 0; j < D; ++j) {
+    const int* n = basis + j * M;
+    int64_t nt = 0;
+    tg[nt++] = j; /* the diagonal */
+    for (int p = 0; p < M; ++p)
+      for (int q = 0; q < M; ++q)
+        for (int r = 0; r < M; ++r)
+          for (int s = 0; s < M; ++s) {
+            if (mod_pos(label_of(M, p) + label_of(M, q) - label_of(M, r) - label_of(M, s), M) != 0) continue;
+            int64_t t = (((int64_t)p * M + q) * M + r) * M + s;
+            if (L[2 * t] == 0.0 && L[2 * t + 1] == 0.0) continue;
+            memcpy(tmp, n, sizeof(int) * (size_t)M);
+            if (tmp[s] == 0) continue;
+            tmp[s] -= 1;
+            if (tmp[r] == 0) continue;
+            tmp[r] -= 1;
+            tmp[q] += 1;
+            tmp[p] += 1;
+            int64_t i = find_ket(M, basis, D, tmp);
+            if (i < 0) continue;
+            int seen = 0;
+            for (int64_t k = 0; k < nt; ++k)
+              if (tg[k] == i) seen = 1;
+            if (!seen) {
+              if (nt == cap) {
+                cap *= 2;
+                tg = realloc(tg, sizeof(int64_t) * (size_t)cap);
+              }
+              tg[nt++] = i;
+            }
+          }
+    total += nt;
+  }
+  free(tg);
+  return total;
+}

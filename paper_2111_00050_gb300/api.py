@@ -1,0 +1,198 @@
+"""Thin Python binding of the qb C ABI (include/qb.h).
+
+Argument marshalling only: every step of the computation runs in libqb's CUDA
+kernels (or, for the tiny host-side pieces the ABI documents -- the M x M
+eigensolve, breaktime, mean field -- in its C++).  Device buffers are torch
+tensors; the current torch CUDA stream is passed to every call.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import QbModel, QbObs, check, lib
+
+
+def _stream() -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dptr(t: torch.Tensor) -> ctypes.c_void_p:
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _c128_as_f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.complex128)).view(np.float64)
+
+
+def _model(M: int, w, L):
+    w = _f64(w)
+    Lf = _c128_as_f64(np.asarray(L, dtype=np.complex128).reshape(-1))
+    if w.size != M or Lf.size != 2 * M ** 4:
+        raise ValueError("w must have M entries and L M^4")
+    m = QbModel(M, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                Lf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return m, (w, Lf)  # keep the arrays alive with the struct
+
+
+def obs_to_dict(o: QbObs, M: int) -> dict:
+    c = lambda arr, n: np.frombuffer(bytes(arr), dtype=np.float64)[: 2 * n].view(np.complex128).copy()
+    return {
+        "t": o.t,
+        "norm": o.norm,
+        "N": o.N,
+        "H": o.H,
+        "n_tot": o.n_tot,
+        "Q": o.Q,
+        "lam_p": o.lam_p,
+        "PO": o.PO,
+        "gap": o.gap,
+        "Vminus_p": o.Vminus_p,
+        "a": c(o.a, M),
+        "Mij": c(o.Mij, M * M).reshape(M, M),
+        "aa": c(o.aa, M * M).reshape(M, M),
+        "xi": c(o.xi, M),
+        "eigvals": np.array(o.eig[:M]),
+        "Vminus_modes": np.array(o.Vminus[:M]),
+    }
+
+
+class Space:
+    """qb_sector_build: all non-empty sectors (N, P) with n_min <= N <= n_max
+    and P in p_list (every P if None)."""
+
+    def __init__(self, M: int, w, L, n_min: int, n_max: int, p_list: Optional[Sequence[int]] = None):
+        self.M = int(M)
+        self._model, self._keep = _model(self.M, w, L)
+        h = ctypes.c_void_p()
+        if p_list is None:
+            check(lib().qb_sector_build(ctypes.byref(self._model), int(n_min), int(n_max), None, 0, ctypes.byref(h)))
+        else:
+            pl = np.ascontiguousarray(p_list, dtype=np.int32)
+            check(lib().qb_sector_build(ctypes.byref(self._model), int(n_min), int(n_max),
+                                        pl.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(pl.size),
+                                        ctypes.byref(h)))
+        self._h = h
+        tot, ns, mx = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int64()
+        check(lib().qb_space_info(h, ctypes.byref(tot), ctypes.byref(ns), ctypes.byref(mx)))
+        self.total, self.n_sectors, self.max_dim = int(tot.value), int(ns.value), int(mx.value)
+        N = np.zeros(self.n_sectors, np.int32)
+        P = np.zeros(self.n_sectors, np.int32)
+        dim = np.zeros(self.n_sectors, np.int64)
+        off = np.zeros(self.n_sectors, np.int64)
+        ip = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        lp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        check(lib().qb_space_sectors(h, ip(N), ip(P), lp(dim), lp(off)))
+        self.sectors = list(zip(N.tolist(), P.tolist()))
+        self.dims = dim
+        self.offsets = off
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib._lib is not None:
+            _lib._lib.qb_space_free(h)
+            self._h = None
+
+    # ---- basis
+    def basis(self, first: int = 0, count: Optional[int] = None, device="cuda") -> torch.Tensor:
+        count = self.total - first if count is None else count
+        out = torch.empty((count, self.M), dtype=torch.int32, device=device)
+        if count:
+            check(lib().qb_space_basis(self._h, int(first), int(count), _dptr(out), _stream()))
+        return out
+
+    def rank(self, occ: torch.Tensor) -> torch.Tensor:
+        occ = occ.to(torch.int32).contiguous()
+        out = torch.empty(occ.shape[0], dtype=torch.int64, device=occ.device)
+        if occ.shape[0]:
+            check(lib().qb_space_rank(self._h, _dptr(occ), int(occ.shape[0]), _dptr(out), _stream()))
+        return out
+
+    def terms(self):
+        t, u = ctypes.c_int64(), ctypes.c_int64()
+        check(lib().qb_space_terms(self._h, ctypes.byref(t), ctypes.byref(u), _stream()))
+        return int(t.value), int(u.value)
+
+    # ---- states
+    def empty_state(self, batch: int = 1) -> torch.Tensor:
+        shape = (self.total,) if batch == 1 else (batch, self.total)
+        return torch.empty(shape, dtype=torch.complex128, device="cuda")
+
+    def init_number(self, occ, psi: torch.Tensor) -> None:
+        o = np.ascontiguousarray(occ, dtype=np.int32)
+        check(lib().qb_init_number(self._h, o.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dptr(psi), _stream()))
+
+    def init_coherent(self, z, psi: torch.Tensor) -> float:
+        zf = _c128_as_f64(z)
+        kept = ctypes.c_double()
+        check(lib().qb_init_coherent(self._h, zf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _dptr(psi),
+                                     ctypes.byref(kept), _stream()))
+        return float(kept.value)
+
+    def init_field_number(self, z, n_tot: int, psi: torch.Tensor) -> None:
+        zf = _c128_as_f64(z)
+        check(lib().qb_init_field_number(self._h, zf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(n_tot),
+                                         _dptr(psi), _stream()))
+
+    # ---- evolution
+    def workspace(self, batch: int = 1) -> torch.Tensor:
+        n = int(lib().qb_workspace_bytes(self._h, int(batch)))
+        return torch.empty(n // 16, dtype=torch.complex128, device="cuda")
+
+    def hpsi(self, psi: torch.Tensor, out: torch.Tensor) -> None:
+        check(lib().qb_hpsi(self._h, _dptr(psi), _dptr(out), _stream()))
+
+    def evolve(self, psi: torch.Tensor, dt: float, steps: int, work: Optional[torch.Tensor] = None) -> None:
+        work = self.workspace(1) if work is None else work
+        check(lib().qb_evolve(self._h, _dptr(psi), float(dt), int(steps), _dptr(work), _stream()))
+
+    def evolve_batch(self, psi: torch.Tensor, scale, dt: float, steps: int,
+                     work: Optional[torch.Tensor] = None) -> None:
+        sc = _f64(scale)
+        work = self.workspace(sc.size) if work is None else work
+        check(lib().qb_evolve_batch(self._h, _dptr(psi), int(sc.size),
+                                    sc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(dt), int(steps),
+                                    _dptr(work), _stream()))
+
+    # ---- observables
+    def observables(self, psi: torch.Tensor) -> dict:
+        o = QbObs()
+        check(lib().qb_observables(self._h, _dptr(psi), ctypes.byref(o), _stream()))
+        return obs_to_dict(o, self.M)
+
+    def evolve_observe(self, psi: torch.Tensor, dt: float, steps: int, obs_every: int,
+                       work: Optional[torch.Tensor] = None) -> list:
+        work = self.workspace(1) if work is None else work
+        n = steps // obs_every + 1
+        arr = (QbObs * n)()
+        check(lib().qb_evolve_observe(self._h, _dptr(psi), float(dt), int(steps), int(obs_every), arr, _dptr(work),
+                                      _stream()))
+        return [obs_to_dict(arr[k], self.M) for k in range(n)]
+
+
+def breaktime(values, dt_obs: float, thr: float):
+    v = _f64(values)
+    t, f = ctypes.c_double(), ctypes.c_int()
+    check(lib().qb_breaktime(v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(v.size), float(dt_obs),
+                             float(thr), ctypes.byref(t), ctypes.byref(f)))
+    return float(t.value), int(f.value)
+
+
+def meanfield(M: int, w, L, z0, dt: float, steps: int, every: int = 1) -> np.ndarray:
+    m, keep = _model(M, w, L)
+    z = _c128_as_f64(z0)
+    rows = steps // every + 1
+    out = np.zeros(2 * M * rows, dtype=np.float64)
+    check(lib().qb_meanfield(ctypes.byref(m), z.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(dt),
+                             int(steps), int(every), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out.view(np.complex128).reshape(rows, M)

@@ -1,0 +1,97 @@
+// Internal structures shared by the host code (qb_host.cpp) and the CUDA
+// kernels (qb_kernels.cu).  Not part of the public ABI (include/qb.h).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qb.h"
+
+namespace qb {
+
+// Everything a kernel needs to walk one space, passed by value.
+//
+// Ranking of a ket n within its sector (N, K), K = sum_i i n_i mod M (mode
+// index momentum), in lexicographic order (n_0 most significant):
+//   rank(n) = D - 1 - sum_{m=1}^{M-1} E_m(rem_m, krem_m),
+//   rem_m = sum_{i>=m} n_i,  krem_m = sum_{i>=m} i n_i mod M,
+//   E_m(rem, k) = cnt[m-1][rem-1][(k - (m-1)) mod M]  (0 for rem < 1),
+// where cnt[m][n][k] counts the fillings of modes m..M-1 with n particles and
+// index momentum k.  E is stored as E[m][rem + 2][kk] for kk in [0, 2M) with
+// E[..][kk] = E_m(rem, kk mod M), so that shifting (rem, krem) by a term's
+// (dc, dk mod M) is one integer add on the flat index:
+//   idx(m, rem, krem) = (m * rem_w + rem + 2) * 2M + krem.
+struct Tables {
+  int M;
+  int nmax;      // largest N of the space
+  int rem_w;     // nmax + 5
+  int n_ann;     // M(M+1)/2 unordered annihilation pairs (r <= s)
+  int n_combo;   // (annihilation pair, creation pair) combinations with nonzero coupling
+  int is_complex;
+  int blob_bytes;  // size of the shared-memory image
+  // byte offsets of the sub-tables inside the image
+  int o_cnt;     // uint32 [(M+1)][nmax+1][M]
+  int o_E;       // int32  [M][rem_w][2M]
+  int o_sqrt;    // double [nmax+3]            sqrt(k)
+  int o_pq;      // uint32 [n_combo]           p | q<<8 | lo<<16 | hi<<24
+  int o_G;       // double [n_combo][2]        conj(mult * L^sym_{pq;rs}) (re, im)
+  int o_delta;   // int8   [16][n_combo]       flat-index shift of the suffix state at mode m
+  int o_ann;     // int32  [n_ann + 1]         first combo of annihilation pair a
+  int o_pairidx; // uint8  [16][16]            pair index of (r <= s)
+  int o_w;       // double [M]                 one-body w_p
+  int o_gd;      // double [n_ann]             diagonal two-body coefficient mult_rs^2 L^sym_{rs;rs}
+  const unsigned char* blob;  // device pointer to the image
+  // sectors
+  int n_sectors;
+  const int64_t* sec_off;  // [n_sectors + 1]
+  const int32_t* sec_N;    // [n_sectors]
+  const int32_t* sec_K;    // [n_sectors] index momentum
+  const int32_t* sec_of;   // [(nmax + 1) * M] sector id of (N, K) or -1
+  int64_t total;
+};
+
+struct Space {
+  int M = 0;
+  int nmax = 0, nmin = 0;
+  std::vector<double> w;                  // [M]
+  std::vector<double> Lsym;               // [M^4][2]
+  std::vector<int> secN, secP, secK;      // per sector
+  std::vector<int64_t> secDim, secOff;    // secOff has n_sectors + 1 entries
+  std::vector<uint64_t> cnt;              // host copy of the fill counts
+  std::vector<int> secOf;                 // [(nmax+1) * M]
+  std::vector<unsigned char> blob;        // host copy of the shared-memory image
+  int64_t maxDim = 0;
+  // device allocations owned by the space
+  unsigned char* d_blob = nullptr;
+  int64_t* d_secOff = nullptr;
+  int32_t* d_secN = nullptr;
+  int32_t* d_secK = nullptr;
+  int32_t* d_secOf = nullptr;
+  double* d_scratch = nullptr;  // reduction partials
+  int64_t scratch_doubles = 0;
+  Tables t{};
+  int device = 0;
+  int grid_hpsi = 0;  // persistent grid sizes per kernel family
+};
+
+// error handling
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+// launchers (qb_kernels.cu); all return a QB_* status
+int launch_hpsi(const Space& s, const void* d_v, void* d_out, void* stream);
+int launch_rk4(Space& s, void* d_psi, int batch, const double* scale, double dt, int64_t steps, void* d_work,
+               void* stream);
+int launch_unrank(const Space& s, int64_t first, int64_t count, int* d_occ, void* stream);
+int launch_rank(const Space& s, const int* d_occ, int64_t count, int64_t* d_index, void* stream);
+int launch_terms(const Space& s, int64_t* terms, int64_t* tuples, void* stream);
+int launch_init_table(const Space& s, const double* table_host, int only_N, void* d_psi, double* norm2,
+                      void* stream);
+int launch_scale(const Space& s, void* d_psi, double factor, void* stream);
+int launch_number(const Space& s, int64_t index, void* d_psi, void* stream);
+// raw moments: out[0]=norm, out[1]=<N>, out[2]=<H>, then a[M], Mij[M*M], aa[M*M] complex
+int launch_moments(Space& s, const void* d_psi, double* out_host, void* stream);
+int64_t workspace_bytes(const Space& s, int batch);
+int device_setup(Space& s);
+
+}  // namespace qb

@@ -1,0 +1,888 @@
+// sm_103a kernels of the qb library: matrix-free sector H psi fused into the
+// Horner-form RK4 stages, combinatorial unrank / rank, initial states,
+// observable moments with deterministic two-pass reductions.
+//
+// Paper: Eberhardt, Zamora, Kopp & Abel, arXiv:2111.00050.  The Hamiltonian is
+// Eq. (Ham); sectors are the special Hilbert spaces of Sec. III B; the state of
+// every sector evolves independently (Sec. III B), so one launch covers all
+// sectors of a space (and all members of a batched coupling sweep).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "qb_internal.h"
+
+namespace qb {
+
+#define QB_CUDA(x)                                                                            \
+  do {                                                                                        \
+    cudaError_t e_ = (x);                                                                     \
+    if (e_ != cudaSuccess) return fail(QB_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr int kBlock = 128;  // threads per CTA of the row kernels (one row per thread per pass)
+constexpr int kMaxM = QB_MAX_MODES;
+
+// ----------------------------------------------------------------- smem view
+
+struct View {
+  const uint32_t* cnt;
+  const int32_t* E;
+  const double* sq;
+  const uint32_t* pq;
+  const double* G;
+  const int8_t* delta;
+  const int32_t* ann;
+  const uint8_t* pairidx;
+  const double* w;
+  const double* gd;
+};
+
+__device__ __forceinline__ View make_view(const Tables& t, const unsigned char* s) {
+  View v;
+  v.cnt = (const uint32_t*)(s + t.o_cnt);
+  v.E = (const int32_t*)(s + t.o_E);
+  v.sq = (const double*)(s + t.o_sqrt);
+  v.pq = (const uint32_t*)(s + t.o_pq);
+  v.G = (const double*)(s + t.o_G);
+  v.delta = (const int8_t*)(s + t.o_delta);
+  v.ann = (const int32_t*)(s + t.o_ann);
+  v.pairidx = (const uint8_t*)(s + t.o_pairidx);
+  v.w = (const double*)(s + t.o_w);
+  v.gd = (const double*)(s + t.o_gd);
+  return v;
+}
+
+// Copies the table image into shared memory (16-byte vector copies).
+__device__ __forceinline__ void load_blob(const Tables& t, unsigned char* smem) {
+  const int4* src = reinterpret_cast<const int4*>(t.blob);
+  int4* dst = reinterpret_cast<int4*>(smem);
+  for (int i = threadIdx.x; i < t.blob_bytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+  __syncthreads();
+}
+
+// Per-thread scratch rows in shared memory, laid out [m][thread] so that the
+// lanes of a warp touching the same mode hit consecutive words.
+struct RowScratch {
+  uint8_t* occ;  // [kMaxM][kBlock]
+  int32_t* idx;  // [kMaxM][kBlock] flat E index of the suffix state at mode m
+  int32_t* pe;   // [kMaxM][kBlock] prefix sums of E over the row's own suffix states
+};
+
+__device__ __forceinline__ RowScratch row_scratch(unsigned char* base) {
+  RowScratch r;
+  r.idx = reinterpret_cast<int32_t*>(base);
+  r.pe = r.idx + kMaxM * kBlock;
+  r.occ = reinterpret_cast<uint8_t*>(r.pe + kMaxM * kBlock);
+  return r;
+}
+constexpr int kRowScratchBytes = kMaxM * kBlock * (4 + 4 + 1);
+
+__device__ __forceinline__ int find_sector(const Tables& t, int64_t g) {
+  int lo = 0, hi = t.n_sectors - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(t.sec_off + mid) <= g)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// Unranks local index i of sector (N, K) into the occupation vector and fills
+// the suffix-state indices and their prefix sums.  Returns rank(n) recomputed
+// from the suffix states (equals i for a consistent table).
+__device__ __forceinline__ int64_t setup_row(const Tables& t, const View& v, const RowScratch& rs, int N, int K,
+                                             int64_t D, int64_t i) {
+  const int M = t.M, tid = threadIdx.x, V = t.nmax + 1;
+  int rem = N, kr = K;
+  int64_t left = i;
+  for (int m = 0; m < M - 1; ++m) {
+    int val = 0, kk = kr;
+    const uint32_t* row = v.cnt + (size_t)(m + 1) * V * M;
+    while (true) {
+      uint32_t c = row[(rem - val) * M + kk];
+      if (left < (int64_t)c || val == rem) break;
+      left -= c;
+      ++val;
+      kk -= m;
+      if (kk < 0) kk += M;
+    }
+    rs.occ[m * kBlock + tid] = (uint8_t)val;
+    rem -= val;
+    kr = kk;
+  }
+  rs.occ[(M - 1) * kBlock + tid] = (uint8_t)rem;
+  // suffix states, from the top mode down
+  const int twoM = 2 * M;
+  int srem = 0, skr = 0;
+  for (int m = M - 1; m >= 1; --m) {
+    int nm = rs.occ[m * kBlock + tid];
+    srem += nm;
+    skr = (skr + m * nm) % M;
+    rs.idx[m * kBlock + tid] = (m * t.rem_w + srem + 2) * twoM + skr;
+  }
+  int32_t acc = 0;
+  rs.pe[tid] = 0;
+  for (int m = 1; m < M; ++m) {
+    acc += v.E[rs.idx[m * kBlock + tid]];
+    rs.pe[m * kBlock + tid] = acc;
+  }
+  return D - 1 - (int64_t)acc;
+}
+
+// Rank of the ket obtained from the row's ket by changing the occupations of
+// modes e[0..nch) by dn[0..nch), inside the sector of dimension Dt it lands in.
+__device__ __forceinline__ int64_t rank_changed(const Tables& t, const View& v, const RowScratch& rs, int nch,
+                                                const int* e, const int* dn, int64_t Dt) {
+  const int M = t.M, tid = threadIdx.x, twoM = 2 * M;
+  int top = 0;
+  for (int c = 0; c < nch; ++c) top = max(top, e[c]);
+  if (top > M - 1) top = M - 1;
+  int64_t sum = rs.pe[(M - 1) * kBlock + tid] - rs.pe[top * kBlock + tid];
+  int dc = 0, dk = 0;
+  for (int m = top; m >= 1; --m) {
+    for (int c = 0; c < nch; ++c)
+      if (e[c] == m) {
+        dc += dn[c];
+        dk += dn[c] * m;
+      }
+    int dkm = ((dk % M) + M) % M;
+    sum += v.E[rs.idx[m * kBlock + tid] + dc * twoM + dkm];
+  }
+  return Dt - 1 - sum;
+}
+
+// ------------------------------------------------------------ H psi kernels
+
+enum { MODE_HPSI = 0, MODE_STAGE = 1, MODE_DOT = 2 };
+
+struct StageArgs {
+  const double2* vin;  // gathered vector(s) [B][total]
+  const double2* psi;  // psi(s) [B][total] (stage mode)
+  double2* out;        // output(s) [B][total]
+  double scale[8];     // two-body scale per member
+  double zre;          // stage factor  -i dt / d  = (0, -dt/d): out = psi + (dt/d) * (Im Hv, -Re Hv)
+  double* partial;     // MODE_DOT: [gridDim.x][2]
+  int* status;         // device status word (bounds violations)
+};
+
+template <int MODE, int B, bool CPLX>
+__global__ void __launch_bounds__(kBlock) hpsi_kernel(const Tables t, const StageArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  load_blob(t, smem);
+  const View v = make_view(t, smem);
+  const RowScratch rs = row_scratch(smem + ((t.blob_bytes + 15) & ~15));
+  const int tid = threadIdx.x;
+  const int M = t.M;
+  const int64_t total = t.total;
+  double dot_re = 0.0, dot_im = 0.0;
+
+  for (int64_t base = (int64_t)blockIdx.x * kBlock; base < total; base += (int64_t)gridDim.x * kBlock) {
+    const int64_t g = base + tid;
+    if (g >= total) break;
+    const int sid = find_sector(t, g);
+    const int64_t off = __ldg(t.sec_off + sid);
+    const int64_t D = __ldg(t.sec_off + sid + 1) - off;
+    const int N = __ldg(t.sec_N + sid), K = __ldg(t.sec_K + sid);
+    const int64_t me = setup_row(t, v, rs, N, K, D, g - off);
+    if (me != g - off) atomicOr(a.status, 2);
+
+    const uint8_t* occ = rs.occ + tid;
+    const int32_t* idx = rs.idx + tid;
+    const int32_t* pe = rs.pe + tid;
+    uint32_t occmask = 0, twomask = 0;
+    double dw = 0.0;
+    for (int m = 0; m < M; ++m) {
+      int nm = occ[m * kBlock];
+      occmask |= (nm >= 1 ? 1u : 0u) << m;
+      twomask |= (nm >= 2 ? 1u : 0u) << m;
+      dw += v.w[m] * nm;
+    }
+    const int64_t rank_base = D - 1 - pe[(M - 1) * kBlock];
+    double dl = 0.0;
+    double acc_re[B], acc_im[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) acc_re[b] = acc_im[b] = 0.0;
+
+    // flattened iteration over annihilation pairs r <= s with n_r (n_s - [r==s]) > 0
+    uint32_t rm = occmask, sm = 0;
+    int r = 0;
+    while (true) {
+      if (sm == 0) {
+        if (rm == 0) break;
+        r = __ffs(rm) - 1;
+        rm &= rm - 1;
+        sm = occmask & (~0u << r);
+        if (!((twomask >> r) & 1u)) sm &= ~(1u << r);
+        if (sm == 0) continue;
+      }
+      const int s = __ffs(sm) - 1;
+      sm &= sm - 1;
+      const int ai = v.pairidx[r * 16 + s];
+      const int nr = occ[r * kBlock], ns = occ[s * kBlock];
+      const double A = v.sq[nr] * v.sq[ns - (r == s ? 1 : 0)];
+      dl += v.gd[ai] * (double)(nr * (ns - (r == s ? 1 : 0)));
+      double pr[B], pi[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) pr[b] = pi[b] = 0.0;
+      const int j1 = v.ann[ai + 1];
+      for (int j = v.ann[ai]; j < j1; ++j) {
+        const uint32_t w4 = v.pq[j];
+        const int p = w4 & 0xff, q = (w4 >> 8) & 0xff, lo = (w4 >> 16) & 0xff, hi = w4 >> 24;
+        const int np_ = occ[p * kBlock], nq = occ[q * kBlock];
+        const double Bf = v.sq[np_ + 1] * v.sq[nq + 1 + (p == q ? 1 : 0)];
+        int64_t rk = rank_base + pe[hi * kBlock] - pe[lo * kBlock];
+        for (int m = lo + 1; m <= hi; ++m) rk -= v.E[idx[m * kBlock] + v.delta[m * t.n_combo + j]];
+        if (rk < 0 || rk >= D) {
+          atomicOr(a.status, 1);
+          rk = 0;
+        }
+        const double cr = v.G[2 * j] * Bf;
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          const double2 x = __ldg(a.vin + (size_t)b * total + off + rk);
+          if (CPLX) {
+            const double ci = v.G[2 * j + 1] * Bf;
+            pr[b] += cr * x.x - ci * x.y;
+            pi[b] += cr * x.y + ci * x.x;
+          } else {
+            pr[b] += cr * x.x;
+            pi[b] += cr * x.y;
+          }
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        acc_re[b] += A * pr[b];
+        acc_im[b] += A * pi[b];
+      }
+    }
+
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const double sc = a.scale[b];
+      const double2 x = a.vin[(size_t)b * total + g];
+      const double dg = dw + sc * dl;
+      const double hr = dg * x.x + sc * acc_re[b];
+      const double hi = dg * x.y + sc * acc_im[b];
+      if (MODE == MODE_HPSI) {
+        a.out[(size_t)b * total + g] = make_double2(hr, hi);
+      } else if (MODE == MODE_STAGE) {
+        const double2 p0 = a.psi[(size_t)b * total + g];
+        // psi + (-i dt/d) * Hv,  zre = dt/d
+        a.out[(size_t)b * total + g] = make_double2(p0.x + a.zre * hi, p0.y - a.zre * hr);
+      } else {
+        // <x | Hx> contribution: conj(x) * Hx
+        dot_re += x.x * hr + x.y * hi;
+        dot_im += x.x * hi - x.y * hr;
+      }
+    }
+  }
+
+  if (MODE == MODE_DOT) {
+    __shared__ double red[2][kBlock / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+      dot_re += __shfl_down_sync(0xffffffffu, dot_re, o);
+      dot_im += __shfl_down_sync(0xffffffffu, dot_im, o);
+    }
+    if ((tid & 31) == 0) {
+      red[0][tid >> 5] = dot_re;
+      red[1][tid >> 5] = dot_im;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double sr = 0.0, si = 0.0;
+      for (int k = 0; k < kBlock / 32; ++k) {
+        sr += red[0][k];
+        si += red[1][k];
+      }
+      a.partial[2 * blockIdx.x] = sr;
+      a.partial[2 * blockIdx.x + 1] = si;
+    }
+  }
+}
+
+// ------------------------------------------------------------- small kernels
+
+__global__ void __launch_bounds__(kBlock) unrank_kernel(const Tables t, int64_t first, int64_t count, int* occ_out,
+                                                         int* status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  load_blob(t, smem);
+  const View v = make_view(t, smem);
+  const RowScratch rs = row_scratch(smem + ((t.blob_bytes + 15) & ~15));
+  const int tid = threadIdx.x;
+  for (int64_t base = (int64_t)blockIdx.x * kBlock; base < count; base += (int64_t)gridDim.x * kBlock) {
+    const int64_t k = base + tid;
+    if (k >= count) break;
+    const int64_t g = first + k;
+    const int sid = find_sector(t, g);
+    const int64_t off = __ldg(t.sec_off + sid);
+    const int64_t D = __ldg(t.sec_off + sid + 1) - off;
+    const int64_t me = setup_row(t, v, rs, __ldg(t.sec_N + sid), __ldg(t.sec_K + sid), D, g - off);
+    if (me != g - off) atomicOr(status, 2);
+    for (int m = 0; m < t.M; ++m) occ_out[k * t.M + m] = rs.occ[m * kBlock + tid];
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) rank_kernel(const Tables t, const int* occ_in, int64_t count,
+                                                       int64_t* index_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  load_blob(t, smem);
+  const View v = make_view(t, smem);
+  const int M = t.M, V = t.nmax + 1;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x) {
+    int N = 0, K = 0;
+    bool ok = true;
+    for (int m = 0; m < M; ++m) {
+      int nm = occ_in[k * M + m];
+      if (nm < 0 || nm > t.nmax) ok = false;
+      N += nm;
+      K = (K + m * (nm < 0 ? 0 : nm)) % M;
+    }
+    int64_t res = -1;
+    if (ok && N <= t.nmax) {
+      int sid = __ldg(t.sec_of + N * M + K);
+      if (sid >= 0) {
+        const int64_t off = __ldg(t.sec_off + sid), D = __ldg(t.sec_off + sid + 1) - off;
+        int64_t sum = 0;
+        int rem = 0, kr = 0;
+        for (int m = M - 1; m >= 1; --m) {
+          int nm = occ_in[k * M + m];
+          rem += nm;
+          kr = (kr + m * nm) % M;
+          if (rem >= 1) sum += v.cnt[((size_t)(m - 1) * V + rem - 1) * M + (((kr - (m - 1)) % M) + M) % M];
+        }
+        res = off + D - 1 - sum;
+      }
+    }
+    index_out[k] = res;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) terms_kernel(const Tables t, unsigned long long* out /*[2]*/) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  load_blob(t, smem);
+  const View v = make_view(t, smem);
+  const RowScratch rs = row_scratch(smem + ((t.blob_bytes + 15) & ~15));
+  const int tid = threadIdx.x, M = t.M;
+  unsigned long long terms = 0, tuples = 0;
+  for (int64_t base = (int64_t)blockIdx.x * kBlock; base < t.total; base += (int64_t)gridDim.x * kBlock) {
+    const int64_t g = base + tid;
+    if (g >= t.total) break;
+    const int sid = find_sector(t, g);
+    const int64_t off = __ldg(t.sec_off + sid);
+    const int64_t D = __ldg(t.sec_off + sid + 1) - off;
+    setup_row(t, v, rs, __ldg(t.sec_N + sid), __ldg(t.sec_K + sid), D, g - off);
+    terms += 1;  // diagonal element
+    for (int r = 0; r < M; ++r)
+      for (int s = r; s < M; ++s) {
+        int nr = rs.occ[r * kBlock + tid], ns = rs.occ[s * kBlock + tid];
+        if (nr < 1 || ns - (r == s ? 1 : 0) < 1) continue;
+        int ai = v.pairidx[r * 16 + s];
+        unsigned long long mrs = (r == s) ? 1 : 2;
+        if (v.gd[ai] != 0.0) tuples += mrs * mrs;
+        for (int j = v.ann[ai]; j < v.ann[ai + 1]; ++j) {
+          uint32_t w4 = v.pq[j];
+          int p = w4 & 0xff, q = (w4 >> 8) & 0xff;
+          terms += 1;
+          tuples += mrs * ((p == q) ? 1ull : 2ull);
+        }
+      }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    terms += __shfl_down_sync(0xffffffffu, terms, o);
+    tuples += __shfl_down_sync(0xffffffffu, tuples, o);
+  }
+  if ((tid & 31) == 0) {
+    atomicAdd(out, terms);
+    atomicAdd(out + 1, tuples);
+  }
+}
+
+// amplitude = prod_i table[i][n_i] (complex), zero outside N == only_N (if >= 0);
+// per-block partial sums of |amplitude|^2
+__global__ void __launch_bounds__(kBlock) init_table_kernel(const Tables t, const double2* table, int only_N,
+                                                             double2* psi, double* partial) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  load_blob(t, smem);
+  const View v = make_view(t, smem);
+  const RowScratch rs = row_scratch(smem + ((t.blob_bytes + 15) & ~15));
+  const int tid = threadIdx.x, M = t.M, V = t.nmax + 1;
+  double n2 = 0.0;
+  for (int64_t base = (int64_t)blockIdx.x * kBlock; base < t.total; base += (int64_t)gridDim.x * kBlock) {
+    const int64_t g = base + tid;
+    if (g >= t.total) break;
+    const int sid = find_sector(t, g);
+    const int64_t off = __ldg(t.sec_off + sid);
+    const int64_t D = __ldg(t.sec_off + sid + 1) - off;
+    const int N = __ldg(t.sec_N + sid);
+    double re = 0.0, im = 0.0;
+    if (only_N < 0 || N == only_N) {
+      setup_row(t, v, rs, N, __ldg(t.sec_K + sid), D, g - off);
+      re = 1.0;
+      for (int m = 0; m < M; ++m) {
+        const double2 f = __ldg(table + (size_t)m * V + rs.occ[m * kBlock + tid]);
+        const double nr = re * f.x - im * f.y;
+        im = re * f.y + im * f.x;
+        re = nr;
+      }
+    }
+    psi[g] = make_double2(re, im);
+    n2 += re * re + im * im;
+  }
+  __shared__ double red[kBlock / 32];
+  for (int o = 16; o > 0; o >>= 1) n2 += __shfl_down_sync(0xffffffffu, n2, o);
+  if ((tid & 31) == 0) red[tid >> 5] = n2;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int k = 0; k < kBlock / 32; ++k) s += red[k];
+    partial[blockIdx.x] = s;
+  }
+}
+
+// sums partial[0..n)[0..width) over the first index in a fixed order
+__global__ void reduce_partials_kernel(const double* partial, int n, int width, double* out) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < width; c += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += partial[(size_t)k * width + c];
+    out[c] = s;
+  }
+}
+
+__global__ void scale_kernel(double2* psi, int64_t n, double f) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    double2 x = psi[k];
+    psi[k] = make_double2(x.x * f, x.y * f);
+  }
+}
+
+__global__ void number_kernel(double2* psi, int64_t n, int64_t index) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    psi[k] = make_double2(k == index ? 1.0 : 0.0, 0.0);
+}
+
+// ---------------------------------------------------------------- moments
+//
+// Raw moments of Sec. II C-E: norm, <N>, <a_i>, <a_i^dag a_j>, <a_i a_j>.  Each
+// row (ket n with amplitude x) contributes conj(psi[target]) * c * x for every
+// operator that maps n to a held ket.  Contributions are reduced across the warp
+// by shuffles into per-warp shared accumulators, then across warps into one
+// partial per block, then over blocks in a fixed order: deterministic.
+
+__device__ __forceinline__ double warp_sum(double x) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  return x;
+}
+
+__global__ void __launch_bounds__(kBlock) moments_kernel(const Tables t, const double2* psi, double* partial,
+                                                          int nmom, int* status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  load_blob(t, smem);
+  const View v = make_view(t, smem);
+  const size_t blob_al = (t.blob_bytes + 15) & ~15;
+  const RowScratch rs = row_scratch(smem + blob_al);
+  double* acc = reinterpret_cast<double*>(smem + blob_al + ((kRowScratchBytes + 15) & ~15));  // [warps][nmom]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, M = t.M;
+  for (int k = tid; k < (kBlock / 32) * nmom; k += kBlock) acc[k] = 0.0;
+  __syncthreads();
+  double* wacc = acc + (size_t)warp * nmom;
+  // layout: [0] norm [1] N [2] H (unused here) [3] pad, a: 4.., Mij: 4+2M.., aa: 4+2M+2M^2..
+  const int oA = 4, oM = 4 + 2 * M, oAA = 4 + 2 * M + 2 * M * M;
+
+  for (int64_t base = (int64_t)blockIdx.x * kBlock; base < t.total; base += (int64_t)gridDim.x * kBlock) {
+    const int64_t g = base + tid;
+    const bool live = g < t.total;
+    int N = 0, K = 0;
+    double xr = 0.0, xi = 0.0;
+    if (live) {
+      const int sid = find_sector(t, g);
+      const int64_t off = __ldg(t.sec_off + sid);
+      const int64_t D = __ldg(t.sec_off + sid + 1) - off;
+      N = __ldg(t.sec_N + sid);
+      K = __ldg(t.sec_K + sid);
+      setup_row(t, v, rs, N, K, D, g - off);
+      const double2 x = psi[g];
+      xr = x.x;
+      xi = x.y;
+    }
+    const double p2 = xr * xr + xi * xi;
+    {
+      double c0 = warp_sum(p2), c1 = warp_sum(p2 * N);
+      if (lane == 0) {
+        wacc[0] += c0;
+        wacc[1] += c1;
+      }
+    }
+    // contribution conj(y) * c * x for target index tg (or none)
+    auto contrib = [&](int slot, bool has, int64_t tg, double c) {
+      double cr = 0.0, ci = 0.0;
+      if (has && (tg < 0 || tg >= t.total)) {
+        atomicOr(status, 1);
+        has = false;
+      }
+      if (has) {
+        const double2 y = psi[tg];
+        cr = c * (y.x * xr + y.y * xi);
+        ci = c * (y.x * xi - y.y * xr);
+      }
+      if (__any_sync(0xffffffffu, has)) {
+        cr = warp_sum(cr);
+        ci = warp_sum(ci);
+        if (lane == 0) {
+          wacc[slot] += cr;
+          wacc[slot + 1] += ci;
+        }
+      }
+    };
+    const uint8_t* occ = rs.occ + tid;
+    // <a_i>
+    for (int i = 0; i < M; ++i) {
+      bool has = false;
+      int64_t tg = 0;
+      double c = 0.0;
+      if (live && occ[i * kBlock] >= 1 && N >= 1) {
+        const int Kt = ((K - i) % M + M) % M;
+        const int sid = __ldg(t.sec_of + (N - 1) * M + Kt);
+        if (sid >= 0) {
+          const int64_t off = __ldg(t.sec_off + sid), D = __ldg(t.sec_off + sid + 1) - off;
+          int e[1] = {i}, dn[1] = {-1};
+          tg = off + rank_changed(t, v, rs, 1, e, dn, D);
+          c = v.sq[occ[i * kBlock]];
+          has = true;
+        }
+      }
+      contrib(oA + 2 * i, has, tg, c);
+    }
+    // <a_i^dag a_j>
+    for (int i = 0; i < M; ++i)
+      for (int j = 0; j < M; ++j) {
+        bool has = false;
+        int64_t tg = 0;
+        double c = 0.0;
+        if (live && occ[j * kBlock] >= 1) {
+          if (i == j) {
+            tg = g;
+            c = (double)occ[i * kBlock];
+            has = true;
+          } else {
+            const int Kt = ((K - j + i) % M + M) % M;
+            const int sid = __ldg(t.sec_of + N * M + Kt);
+            if (sid >= 0) {
+              const int64_t off = __ldg(t.sec_off + sid), D = __ldg(t.sec_off + sid + 1) - off;
+              int e[2] = {j, i}, dn[2] = {-1, 1};
+              tg = off + rank_changed(t, v, rs, 2, e, dn, D);
+              c = v.sq[occ[j * kBlock]] * v.sq[occ[i * kBlock] + 1];
+              has = true;
+            }
+          }
+        }
+        contrib(oM + 2 * (i * M + j), has, tg, c);
+      }
+    // <a_i a_j>, i <= j (the matrix is symmetric)
+    for (int i = 0; i < M; ++i)
+      for (int j = i; j < M; ++j) {
+        bool has = false;
+        int64_t tg = 0;
+        double c = 0.0;
+        if (live && N >= 2) {
+          const int ni = occ[i * kBlock], nj = occ[j * kBlock];
+          const bool ok = (i == j) ? (ni >= 2) : (ni >= 1 && nj >= 1);
+          if (ok) {
+            const int Kt = ((K - i - j) % M + M) % M;
+            const int sid = __ldg(t.sec_of + (N - 2) * M + Kt);
+            if (sid >= 0) {
+              const int64_t off = __ldg(t.sec_off + sid), D = __ldg(t.sec_off + sid + 1) - off;
+              int e[2] = {i, j}, dn[2] = {(i == j) ? -2 : -1, -1};
+              tg = off + rank_changed(t, v, rs, (i == j) ? 1 : 2, e, dn, D);
+              c = (i == j) ? v.sq[ni] * v.sq[ni - 1] : v.sq[ni] * v.sq[nj];
+              has = true;
+            }
+          }
+        }
+        contrib(oAA + 2 * (i * M + j), has, tg, c);
+      }
+  }
+  __syncthreads();
+  for (int k = tid; k < nmom; k += kBlock) {
+    double s = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) s += acc[(size_t)w * nmom + k];
+    partial[(size_t)blockIdx.x * nmom + k] = s;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+
+static size_t row_smem(const Tables& t) { return ((t.blob_bytes + 15) & ~15) + kRowScratchBytes; }
+
+static int nmoments(int M) { return 4 + 2 * M + 4 * M * M; }
+
+// grid of a persistent row kernel, capped by the scratch sizing
+
+
+template <typename K>
+static int persistent_grid(K kernel, size_t smem, int64_t rows, int* grid) {
+  int dev = 0, sms = 0, per = 0;
+  QB_CUDA(cudaGetDevice(&dev));
+  QB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  QB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  QB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kBlock, smem));
+  if (per < 1) return fail(QB_EUNSUPPORTED, "kernel does not fit on an SM with this table size");
+  int64_t want = (rows + kBlock - 1) / kBlock;
+  int64_t g = std::min<int64_t>((int64_t)sms * std::min(per, 16), std::max<int64_t>(1, want));
+  *grid = (int)g;
+  return QB_OK;
+}
+
+static int check_status(const Space& s, cudaStream_t st) {
+  int h = 0;
+  int* d = reinterpret_cast<int*>(s.d_scratch);  // status word lives at the head of the scratch area
+  QB_CUDA(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st));
+  QB_CUDA(cudaStreamSynchronize(st));
+  if (h) {
+    QB_CUDA(cudaMemsetAsync(d, 0, sizeof(int), st));
+    QB_CUDA(cudaStreamSynchronize(st));
+    return fail(QB_EINTERNAL, "device-side consistency check failed (status " + std::to_string(h) + ")");
+  }
+  return QB_OK;
+}
+
+// Scratch layout (doubles), sized at space setup for the largest persistent
+// grid G = sms * 16:  [0, 2) status word | partials [G * nmom] | final [nmom]
+// | dot partials [2 G] | dot final [2] | amplitude table [2 M (nmax+1)] | init final [2]
+static int nmoments(int M);
+static int64_t max_grid_of(const Space& s) { return s.scratch_doubles > 0 ? (int64_t)s.grid_hpsi : 0; }
+static double* partial_area(const Space& s) { return s.d_scratch + 2; }
+static double* final_area(const Space& s) { return partial_area(s) + max_grid_of(s) * nmoments(s.M); }
+static double* dot_area(const Space& s) { return final_area(s) + nmoments(s.M); }
+static double* dot_final(const Space& s) { return dot_area(s) + 2 * max_grid_of(s); }
+static double* table_area(const Space& s) { return dot_final(s) + 2; }
+static double* init_final(const Space& s) { return table_area(s) + 2 * (size_t)s.M * (s.nmax + 1); }
+
+int device_setup(Space& s) {
+  QB_CUDA(cudaGetDevice(&s.device));
+  const size_t nsec = s.secN.size();
+  QB_CUDA(cudaMalloc(&s.d_blob, s.blob.size()));
+  QB_CUDA(cudaMemcpy(s.d_blob, s.blob.data(), s.blob.size(), cudaMemcpyHostToDevice));
+  QB_CUDA(cudaMalloc(&s.d_secOff, sizeof(int64_t) * (nsec + 1)));
+  QB_CUDA(cudaMemcpy(s.d_secOff, s.secOff.data(), sizeof(int64_t) * (nsec + 1), cudaMemcpyHostToDevice));
+  QB_CUDA(cudaMalloc(&s.d_secN, sizeof(int32_t) * nsec));
+  QB_CUDA(cudaMemcpy(s.d_secN, s.secN.data(), sizeof(int32_t) * nsec, cudaMemcpyHostToDevice));
+  QB_CUDA(cudaMalloc(&s.d_secK, sizeof(int32_t) * nsec));
+  QB_CUDA(cudaMemcpy(s.d_secK, s.secK.data(), sizeof(int32_t) * nsec, cudaMemcpyHostToDevice));
+  QB_CUDA(cudaMalloc(&s.d_secOf, sizeof(int32_t) * s.secOf.size()));
+  QB_CUDA(cudaMemcpy(s.d_secOf, s.secOf.data(), sizeof(int32_t) * s.secOf.size(), cudaMemcpyHostToDevice));
+  Tables& t = s.t;
+  t.blob = s.d_blob;
+  t.n_sectors = (int)nsec;
+  t.sec_off = s.d_secOff;
+  t.sec_N = s.d_secN;
+  t.sec_K = s.d_secK;
+  t.sec_of = s.d_secOf;
+  t.total = s.secOff.back();
+  if (row_smem(t) + (size_t)(kBlock / 32) * nmoments(s.M) * 8 > 227 * 1024)
+    return fail(QB_EUNSUPPORTED, "tables too large for shared memory (reduce n_max or M)");
+  // scratch: status + partials for the largest persistent grid of any reduction
+  int sms = 0;
+  QB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s.device));
+  const int64_t max_grid = (int64_t)sms * 16;
+  s.grid_hpsi = (int)max_grid;
+  s.scratch_doubles = 2 + max_grid * nmoments(s.M) + nmoments(s.M) + 2 * max_grid + 2 +
+                      2 * (int64_t)s.M * (s.nmax + 1) + 2;
+  QB_CUDA(cudaMalloc(&s.d_scratch, sizeof(double) * s.scratch_doubles));
+  QB_CUDA(cudaMemset(s.d_scratch, 0, sizeof(double) * s.scratch_doubles));
+  return QB_OK;
+}
+
+int64_t workspace_bytes(const Space& s, int batch) { return 2 * (int64_t)batch * s.secOff.back() * 16; }
+
+template <int MODE, int B, bool CPLX>
+static int launch_stage(const Space& s, const StageArgs& a, cudaStream_t st, int* grid_out = nullptr) {
+  auto k = hpsi_kernel<MODE, B, CPLX>;
+  const size_t smem = row_smem(s.t);
+  int grid = 0;
+  int rc = persistent_grid(k, smem, s.t.total, &grid);
+  if (rc) return rc;
+  if (grid_out) *grid_out = grid;
+  k<<<grid, kBlock, smem, st>>>(s.t, a);
+  QB_CUDA(cudaGetLastError());
+  return QB_OK;
+}
+
+template <int MODE, int B>
+static int launch_stage_c(const Space& s, const StageArgs& a, cudaStream_t st, int* grid_out = nullptr) {
+  return s.t.is_complex ? launch_stage<MODE, B, true>(s, a, st, grid_out)
+                        : launch_stage<MODE, B, false>(s, a, st, grid_out);
+}
+
+int launch_hpsi(const Space& s, const void* d_v, void* d_out, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  StageArgs a{};
+  a.vin = (const double2*)d_v;
+  a.out = (double2*)d_out;
+  a.scale[0] = 1.0;
+  a.status = reinterpret_cast<int*>(s.d_scratch);
+  int rc = launch_stage_c<MODE_HPSI, 1>(s, a, st);
+  if (rc) return rc;
+  return check_status(s, st);
+}
+
+template <int B>
+static int rk4_loop(Space& s, double2* psi, const double* scale, double dt, int64_t steps, double2* w1, double2* w2,
+                    cudaStream_t st) {
+  StageArgs a{};
+  for (int b = 0; b < B; ++b) a.scale[b] = scale[b];
+  a.status = reinterpret_cast<int*>(s.d_scratch);
+  for (int64_t n = 0; n < steps; ++n) {
+    // Horner: v = psi + z/4 H psi; v = psi + z/3 H v; v = psi + z/2 H v; psi = psi + z H v
+    const double2* in[4] = {psi, w1, w2, w1};
+    double2* out[4] = {w1, w2, w1, psi};
+    for (int d = 4; d >= 1; --d) {
+      a.vin = in[4 - d];
+      a.out = out[4 - d];
+      a.psi = psi;
+      a.zre = dt / d;
+      int rc = launch_stage_c<MODE_STAGE, B>(s, a, st);
+      if (rc) return rc;
+    }
+  }
+  return QB_OK;
+}
+
+int launch_rk4(Space& s, void* d_psi, int batch, const double* scale, double dt, int64_t steps, void* d_work,
+               void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = (int64_t)batch * s.secOff.back();
+  double2* psi = (double2*)d_psi;
+  double2* w1 = (double2*)d_work;
+  double2* w2 = w1 + n;
+  int rc;
+  switch (batch) {
+    case 1: rc = rk4_loop<1>(s, psi, scale, dt, steps, w1, w2, st); break;
+    case 2: rc = rk4_loop<2>(s, psi, scale, dt, steps, w1, w2, st); break;
+    case 4: rc = rk4_loop<4>(s, psi, scale, dt, steps, w1, w2, st); break;
+    case 8: rc = rk4_loop<8>(s, psi, scale, dt, steps, w1, w2, st); break;
+    default: return fail(QB_EINVAL, "batch must be 1, 2, 4 or 8");
+  }
+  if (rc) return rc;
+  return check_status(s, st);
+}
+
+int launch_unrank(const Space& s, int64_t first, int64_t count, int* d_occ, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t smem = row_smem(s.t);
+  int grid = 0;
+  int rc = persistent_grid(unrank_kernel, smem, count, &grid);
+  if (rc) return rc;
+  unrank_kernel<<<grid, kBlock, smem, st>>>(s.t, first, count, d_occ, reinterpret_cast<int*>(s.d_scratch));
+  QB_CUDA(cudaGetLastError());
+  return check_status(s, st);
+}
+
+int launch_rank(const Space& s, const int* d_occ, int64_t count, int64_t* d_index, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t smem = (s.t.blob_bytes + 15) & ~15;
+  int grid = 0;
+  int rc = persistent_grid(rank_kernel, smem, count, &grid);
+  if (rc) return rc;
+  rank_kernel<<<grid, kBlock, smem, st>>>(s.t, d_occ, count, d_index);
+  QB_CUDA(cudaGetLastError());
+  QB_CUDA(cudaStreamSynchronize(st));
+  return QB_OK;
+}
+
+int launch_terms(const Space& s, int64_t* terms, int64_t* tuples, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t smem = row_smem(s.t);
+  int grid = 0;
+  int rc = persistent_grid(terms_kernel, smem, s.t.total, &grid);
+  if (rc) return rc;
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(partial_area(s));
+  QB_CUDA(cudaMemsetAsync(d, 0, 16, st));
+  terms_kernel<<<grid, kBlock, smem, st>>>(s.t, d);
+  QB_CUDA(cudaGetLastError());
+  unsigned long long h[2];
+  QB_CUDA(cudaMemcpyAsync(h, d, 16, cudaMemcpyDeviceToHost, st));
+  QB_CUDA(cudaStreamSynchronize(st));
+  *terms = (int64_t)h[0];
+  if (tuples) *tuples = (int64_t)h[1];
+  return QB_OK;
+}
+
+int launch_init_table(const Space& s, const double* table_host, int only_N, void* d_psi, double* norm2,
+                      void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t smem = row_smem(s.t);
+  int grid = 0;
+  int rc = persistent_grid(init_table_kernel, smem, s.t.total, &grid);
+  if (rc) return rc;
+  double* part = partial_area(s);
+  double* tab = table_area(s);
+  const size_t tab_bytes = sizeof(double) * 2 * (size_t)s.M * (s.nmax + 1);
+  QB_CUDA(cudaMemcpyAsync(tab, table_host, tab_bytes, cudaMemcpyHostToDevice, st));
+  init_table_kernel<<<grid, kBlock, smem, st>>>(s.t, (const double2*)tab, only_N, (double2*)d_psi, part);
+  QB_CUDA(cudaGetLastError());
+  double* fin = init_final(s);
+  reduce_partials_kernel<<<1, 32, 0, st>>>(part, grid, 1, fin);
+  QB_CUDA(cudaGetLastError());
+  QB_CUDA(cudaMemcpyAsync(norm2, fin, sizeof(double), cudaMemcpyDeviceToHost, st));
+  QB_CUDA(cudaStreamSynchronize(st));
+  return QB_OK;
+}
+
+int launch_scale(const Space& s, void* d_psi, double factor, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  scale_kernel<<<1216, 256, 0, st>>>((double2*)d_psi, s.t.total, factor);
+  QB_CUDA(cudaGetLastError());
+  return QB_OK;
+}
+
+int launch_number(const Space& s, int64_t index, void* d_psi, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  number_kernel<<<1216, 256, 0, st>>>((double2*)d_psi, s.t.total, index);
+  QB_CUDA(cudaGetLastError());
+  return QB_OK;
+}
+
+int launch_moments(Space& s, const void* d_psi, double* out_host, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nmom = nmoments(s.M);
+  const size_t smem = row_smem(s.t) + ((kRowScratchBytes + 15) & ~15) - kRowScratchBytes +
+                      (size_t)(kBlock / 32) * nmom * sizeof(double) + 16;
+  int grid = 0;
+  int rc = persistent_grid(moments_kernel, smem, s.t.total, &grid);
+  if (rc) return rc;
+  double* part = partial_area(s);
+  moments_kernel<<<grid, kBlock, smem, st>>>(s.t, (const double2*)d_psi, part, nmom,
+                                             reinterpret_cast<int*>(s.d_scratch));
+  QB_CUDA(cudaGetLastError());
+  double* fin = final_area(s);
+  reduce_partials_kernel<<<(nmom + 127) / 128, 128, 0, st>>>(part, grid, nmom, fin);
+  QB_CUDA(cudaGetLastError());
+  QB_CUDA(cudaMemcpyAsync(out_host, fin, sizeof(double) * nmom, cudaMemcpyDeviceToHost, st));
+  // <H> = <psi|H psi>
+  StageArgs a{};
+  a.vin = (const double2*)d_psi;
+  a.scale[0] = 1.0;
+  a.status = reinterpret_cast<int*>(s.d_scratch);
+  double* dpart = dot_area(s);
+  a.partial = dpart;
+  int g2 = 0;
+  rc = launch_stage_c<MODE_DOT, 1>(s, a, st, &g2);
+  if (rc) return rc;
+  double* hfin = dot_final(s);
+  reduce_partials_kernel<<<1, 32, 0, st>>>(dpart, g2, 2, hfin);
+  QB_CUDA(cudaGetLastError());
+  double h2[2];
+  QB_CUDA(cudaMemcpyAsync(h2, hfin, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  QB_CUDA(cudaStreamSynchronize(st));
+  out_host[2] = h2[0];
+  return check_status(s, st);
+}
+
+}  // namespace qb

@@ -1,0 +1,83 @@
+"""The C ABI library loads here (no GPU needed) and exports every function
+include/qb.h declares; host-only entry points work without a device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "qb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(qb_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2111_00050_gb300._lib as L
+
+    lib = L.lib()
+    names = declared_functions()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in L.SIGNATURES, n
+    assert set(L.SIGNATURES) == set(names)
+
+
+def test_obs_struct_layout_matches_header():
+    import paper_2111_00050_gb300._lib as L
+
+    M = L.QB_MAX_MODES
+    assert ctypes.sizeof(L.QbObs) == 8 * (10 + 2 * M + 4 * M * M + 2 * M + M + M)
+
+
+def test_host_only_entry_points():
+    import paper_2111_00050_gb300 as qb
+
+    assert qb.breaktime([0.0, 0.05, 0.08, 0.12, 0.3], 0.5, 0.1) == (1.25, qb.QB_CROSSED)
+    assert qb.breaktime([0.2, 0.3], 1.0, 0.1) == (0.0, qb.QB_AT_START)
+    t, f = qb.breaktime([0.0, 0.01], 1.0, 0.1)
+    assert f == qb.QB_NOT_CROSSED and np.isnan(t)
+
+
+def test_meanfield_matches_oracle():
+    import oracle as orc
+    import paper_2111_00050_gb300 as qb
+    import workloads as wl
+
+    M = 5
+    w = wl.dispersion_quadratic(M)
+    L = wl.long_range_coupling(M, 0.2)
+    z = np.array([0.2, 1.0 + 0.5j, 0.7j, -0.4, 0.1])
+    a = qb.meanfield(M, w, L, z, 1e-3, 500, 100)
+    b = orc.meanfield(w, L, z, 1e-3, 500, 100)
+    np.testing.assert_allclose(a, b, atol=1e-12)
+
+
+@pytest.mark.parametrize("bad", ["nonhermitian", "nonconserving", "too_many_modes", "too_deep"])
+def test_model_validation_without_device(bad):
+    import paper_2111_00050_gb300 as qb
+    import workloads as wl
+
+    M = 5
+    w = wl.dispersion_quadratic(M)
+    L = wl.contact_coupling(M, -0.1)
+    n_max = 4
+    if bad == "nonhermitian":
+        L = L.copy()
+        L[0, 1, 2, 4] = 0.3j
+    elif bad == "nonconserving":
+        L = L.copy()
+        L[0, 0, 0, 1] = 1.0
+    elif bad == "too_many_modes":
+        M = 17
+        w, L = np.zeros(M), np.zeros((M,) * 4)
+    else:
+        n_max = 1 << 13
+    with pytest.raises(qb.QbError) as e:
+        qb.Space(M, w, L, 0, n_max)
+    assert e.value.code in (1, 6)

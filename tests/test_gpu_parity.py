@@ -1,0 +1,267 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances:
+  * one H psi: relative 2-norm error <= 1e-13 (only the summation order differs);
+  * evolved states: relative 2-norm error <= 1e-10 (same discrete RK4 scheme);
+  * observables: absolute <= 1e-9 on normalised quantities (Q, PO, V_-), relative
+    <= 1e-9 on <a_i>, M_ij, <a_i a_j>.
+Bases are compared bit-exactly; sector order and ket order must agree.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as orc
+import workloads as wl
+from helpers import pair, rel_err, to_dev, to_host, random_state
+
+pytestmark = pytest.mark.gpu
+
+STATE_TOL = 1e-10
+HPSI_TOL = 1e-13
+OBS_TOL = 1e-9
+
+
+def _random_hermitian(M, seed, scale=0.1):
+    rng = np.random.default_rng(seed)
+    L = (rng.standard_normal((M,) * 4) + 1j * rng.standard_normal((M,) * 4)) * scale
+    L = L * wl._conserving(M)
+    L = 0.5 * (L + np.conj(L.transpose(3, 2, 1, 0)))
+    return rng.standard_normal(M), L
+
+
+def _case(name):
+    if name == "M5_N6_contact":
+        M = 5
+        return M, wl.dispersion_quadratic(M), wl.contact_coupling(M, -0.1), 6, 6, [0]
+    if name == "M7_N9_allP":
+        M = 7
+        return M, wl.dispersion_quadratic(M), wl.contact_coupling(M, -0.05), 9, 9, None
+    if name == "M9_long_range":
+        M = 9
+        return M, wl.dispersion_quadratic(M), wl.long_range_coupling(M, 0.1 / 8), 8, 8, [0, 3]
+    if name == "M5_complex_hermitian":
+        w, L = _random_hermitian(5, 11)
+        return 5, w, L, 0, 5, None
+    if name == "M3_multi_sector":
+        M = 3
+        return M, np.array([0.4, -0.2, 0.9]), wl.contact_coupling(M, 0.07), 0, 12, None
+    if name == "M1_kerr":
+        return 1, np.array([0.7]), np.full((1, 1, 1, 1), 0.13, dtype=np.complex128), 0, 30, None
+    if name == "M4_even_paper":
+        M = 4
+        rng = np.random.default_rng(3)
+        return M, rng.standard_normal(M), wl.paper_coupling(M, -0.2, 0.05), 0, 6, None
+    if name == "M11_N6":
+        M = 11
+        return M, wl.dispersion_abs(M), wl.contact_coupling(M, -0.02), 6, 6, [0, 5]
+    if name == "M5_N40_deep":
+        M = 5
+        return M, wl.dispersion_quadratic(M), wl.contact_coupling(M, -0.1), 40, 40, [1]
+    raise KeyError(name)
+
+
+CASES = ["M5_N6_contact", "M7_N9_allP", "M9_long_range", "M5_complex_hermitian", "M3_multi_sector", "M1_kerr",
+         "M4_even_paper", "M11_N6", "M5_N40_deep"]
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_basis_and_rank_match_oracle(name):
+    import torch
+
+    M, w, L, n0, n1, pl = _case(name)
+    qs, os_ = pair(M, w, L, n0, n1, pl)
+    b = qs.basis().cpu().numpy()
+    np.testing.assert_array_equal(b, os_.basis)
+    idx = qs.rank(torch.from_numpy(os_.basis).cuda()).cpu().numpy()
+    np.testing.assert_array_equal(idx, np.arange(qs.total))
+    # kets outside the space rank to -1
+    bad = os_.basis[:4].copy()
+    bad[:, 0] += 1
+    assert (qs.rank(torch.from_numpy(bad).cuda()).cpu().numpy() == -1).all()
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_hpsi_matches_oracle(name):
+    M, w, L, n0, n1, pl = _case(name)
+    qs, os_ = pair(M, w, L, n0, n1, pl)
+    x = random_state(qs.total, 5)
+    out = qs.empty_state()
+    qs.hpsi(to_dev(x), out)
+    ref = orc.apply_h(os_, w, L, x)
+    assert rel_err(to_host(out), ref) <= HPSI_TOL
+
+
+@pytest.mark.parametrize("name", ["M5_N6_contact", "M7_N9_allP", "M9_long_range", "M5_complex_hermitian",
+                                  "M3_multi_sector", "M4_even_paper"])
+def test_terms_count_matches_dense_nonzeros(name):
+    M, w, L, n0, n1, pl = _case(name)
+    qs, os_ = pair(M, w, L, n0, n1, pl)
+    nnz = 0
+    for s in range(len(os_.sectors)):
+        Hd = orc.h_dense(os_, s, w, L)
+        off = np.abs(Hd - np.diag(np.diag(Hd))) > 0
+        nnz += int(off.sum()) + Hd.shape[0]
+    terms, tuples = qs.terms()
+    assert terms == nnz
+
+
+def test_plain_single_sector_full_run():
+    """M=5, contact C=-0.1, |0,2,2,2,0>, RK4 dt=1e-3 to t=10, observables every
+    100 steps: every sample and the final state against the oracle."""
+    import torch
+
+    W = wl.plain_single_sector()
+    qs, os_ = pair(W.M, W.w, W.L, 6, 6, [0])
+    psi = qs.empty_state()
+    qs.init_number(W.occ, psi)
+    series = qs.evolve_observe(psi, W.dt, W.steps, W.obs_every)
+    ref = orc.number_state(os_, W.occ)
+    for k, ob in enumerate(series):
+        if k > 0:
+            ref = orc.rk4(os_, W.w, W.L, ref, W.dt, W.obs_every)
+        if k % 10 == 0 or k == len(series) - 1:
+            ro = orc.observables(os_, ref, W.w, W.L)
+            assert abs(ob["Q"] - ro["Q"]) <= OBS_TOL
+            assert abs(ob["lam_p"] - ro["lam_p"]) <= OBS_TOL * ro["n_tot"]
+            assert abs(ob["H"] - ro["H"]) <= OBS_TOL * abs(ro["H"])
+            np.testing.assert_allclose(ob["Mij"], ro["Mij"], atol=OBS_TOL * ro["n_tot"])
+            np.testing.assert_allclose(ob["aa"], ro["aa"], atol=OBS_TOL * ro["n_tot"])
+    assert rel_err(to_host(psi), ref) <= STATE_TOL
+    torch.cuda.synchronize()
+
+
+def _coherent_case(M, n_tot, nmax, C, seed):
+    rng = np.random.default_rng(seed)
+    z = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+    z *= math.sqrt(n_tot / np.sum(np.abs(z) ** 2))
+    return z, wl.dispersion_quadratic(M), wl.contact_coupling(M, C)
+
+
+def test_coherent_multi_sector_evolution_and_observables():
+    M = 5
+    z, w, L = _coherent_case(M, 3.0, 14, -0.08, 1)
+    qs, os_ = pair(M, w, L, 0, 14, None)
+    psi = qs.empty_state()
+    kept = qs.init_coherent(z, psi)
+    ref, kept_ref = orc.coherent_state(os_, z)
+    assert abs(kept - kept_ref) <= 1e-14
+    assert rel_err(to_host(psi), ref) <= 1e-14
+    ob0 = qs.observables(psi)
+    assert abs(ob0["Q"]) < 1e-9 and abs(ob0["Vminus_p"] - 1) < 1e-9
+    qs.evolve(psi, 2e-3, 400)
+    ref = orc.rk4(os_, w, L, ref, 2e-3, 400)
+    assert rel_err(to_host(psi), ref) <= STATE_TOL
+    ob = qs.observables(psi)
+    ro = orc.observables(os_, ref, w, L)
+    for key in ("Q", "PO", "Vminus_p"):
+        assert abs(ob[key] - ro[key]) <= OBS_TOL, key
+    np.testing.assert_allclose(ob["Vminus_modes"], ro["Vminus_modes"], atol=OBS_TOL)
+    np.testing.assert_allclose(ob["a"], ro["a"], atol=OBS_TOL * max(1, np.abs(ro["a"]).max()))
+    np.testing.assert_allclose(ob["Mij"], ro["Mij"], atol=OBS_TOL * ro["n_tot"])
+    np.testing.assert_allclose(ob["aa"], ro["aa"], atol=OBS_TOL * ro["n_tot"])
+    np.testing.assert_allclose(ob["eigvals"], ro["eigvals"], atol=OBS_TOL * ro["n_tot"])
+    assert abs(ob["H"] - ro["H"]) <= OBS_TOL * max(1, abs(ro["H"]))
+    assert abs(abs(np.vdot(ob["xi"], ro["xi"])) - 1) < 1e-9
+
+
+def test_field_number_long_range_window():
+    """Scaled-down gravity-like workload: M=9 long range, field number state."""
+    Wl = wl.long_range_field_number(M=9, seed=0, mean=1.0)
+    n_tot = Wl.n_tot
+    qs, os_ = pair(Wl.M, Wl.w, Wl.L, n_tot, n_tot, None)
+    psi = qs.empty_state()
+    qs.init_field_number(Wl.z, n_tot, psi)
+    ref = orc.field_number_state(os_, Wl.z, n_tot)
+    assert rel_err(to_host(psi), ref) <= 1e-13
+    ob = qs.observables(psi)
+    assert abs(ob["Q"] - 1) < 1e-9 and abs(ob["lam_p"] - n_tot) < 1e-9 * n_tot
+    qs.evolve(psi, Wl.dt, 200)
+    ref = orc.rk4(os_, Wl.w, Wl.L, ref, Wl.dt, 200)
+    assert rel_err(to_host(psi), ref) <= STATE_TOL
+    ro = orc.observables(os_, ref)
+    ob = qs.observables(psi)
+    assert abs(ob["PO"] - ro["PO"]) <= OBS_TOL
+
+
+def test_batched_sweep_matches_separate_members():
+    import torch
+
+    M = 5
+    z, w, L = _coherent_case(M, 2.5, 12, -0.1, 2)
+    scales = [0.5, 1.0, 2.0, -1.0]
+    qs, os_ = pair(M, w, L, 0, 12, None)
+    psi = torch.empty((4, qs.total), dtype=torch.complex128, device="cuda")
+    for b in range(4):
+        qs.init_coherent(z, psi[b])
+    qs.evolve_batch(psi, scales, 2e-3, 300)
+    ref0, _ = orc.coherent_state(os_, z)
+    for b, sc in enumerate(scales):
+        ref = orc.rk4(os_, w, sc * L, ref0, 2e-3, 300)
+        assert rel_err(to_host(psi[b]), ref) <= STATE_TOL
+
+
+def test_kerr_single_mode_gpu_matches_closed_form():
+    """M=1: <a(t)> = a0 e^{-iwt} exp(|a0|^2 (e^{-2iLt} - 1)) to the RK4 error."""
+    w, Lk, a0 = 0.5, 0.1, 1.1 + 0.3j
+    import paper_2111_00050_gb300 as qb
+
+    qs = qb.Space(1, [w], np.full((1, 1, 1, 1), Lk, dtype=np.complex128), 0, 40)
+    psi = qs.empty_state()
+    qs.init_coherent([a0], psi)
+    qs.evolve(psi, 1e-3, 1000)
+    a_ref = a0 * np.exp(-1j * w) * np.exp(abs(a0) ** 2 * (np.exp(-2j * Lk) - 1))
+    assert abs(qs.observables(psi)["a"][0] - a_ref) < 1e-9
+
+
+def test_large_sector_sampled_rows():
+    """M=11, N=20, P=0 (2,731,365 kets): sampled kets rank to their oracle index and
+    sampled rows of H psi match the oracle's per-row application; one RK4 step
+    conserves the norm to O(dt^6) and <H> to rounding."""
+    import torch
+
+    W = wl.large_sector()
+    qs, os_ = pair(W.M, W.w, W.L, 20, 20, [0])
+    assert qs.total == 2731365
+    rng = np.random.default_rng(9)
+    rows = np.sort(rng.choice(qs.total, 256, replace=False))
+    rows[0], rows[-1] = 0, qs.total - 1
+    got = qs.rank(torch.from_numpy(os_.basis[rows]).cuda()).cpu().numpy()
+    np.testing.assert_array_equal(got, rows)
+    b = qs.basis(int(rows[100]), 1).cpu().numpy()[0]
+    np.testing.assert_array_equal(b, os_.basis[rows[100]])
+    x = random_state(qs.total, 13)
+    out = qs.empty_state()
+    xd = to_dev(x)
+    qs.hpsi(xd, out)
+    ref = orc.apply_h_rows(os_, 0, W.w, W.L, x, rows)
+    got = to_host(out)[rows]
+    assert np.max(np.abs(got - ref)) <= HPSI_TOL * np.max(np.abs(ref)) * 10
+    psi = qs.empty_state()
+    qs.init_number(W.occ, psi)
+    e0 = qs.observables(psi)["H"]
+    qs.evolve(psi, W.dt, 4)
+    ob = qs.observables(psi)
+    assert abs(ob["norm"] - 1) < 1e-12
+    assert abs(ob["H"] - e0) < 1e-10 * abs(e0)
+
+
+def test_errors_are_reported():
+    import paper_2111_00050_gb300 as qb
+
+    M = 5
+    w = wl.dispersion_quadratic(M)
+    L = wl.contact_coupling(M, -0.1)
+    Lbad = L.copy()
+    Lbad[0, 1, 2, 4] = 0.3j  # breaks Hermiticity
+    Lbad = Lbad * wl._conserving(M)
+    with pytest.raises(qb.QbError) as e:
+        qb.Space(M, w, Lbad, 3, 3)
+    assert e.value.code == 1
+    with pytest.raises(qb.QbError) as e:
+        qb.Space(17, np.zeros(17), np.zeros((17,) * 4), 1, 1)
+    assert e.value.code == 6
+    qs = qb.Space(M, w, L, 3, 3)
+    with pytest.raises(qb.QbError):
+        qs.init_number([3, 0, 0, 0, 1], qs.empty_state())  # N=4 not held

@@ -464,3 +464,31 @@ def test_rk4_step_adjoint_matches_finite_differences():
     d = rng.standard_normal(space.total) + 1j * rng.standard_normal(space.total)
     fd = (loss(C, w, psi + h * d) - loss(C, w, psi - h * d)) / (2 * h)
     assert abs(2 * np.vdot(lam0, d).real - fd) < 1e-7 * max(1, abs(fd))
+
+
+def test_single_row_application_matches_push_form():
+    """The per-row form used for sampled checks of huge sectors equals the
+    push form, for a non-Hermitian coupling too (no symmetry is assumed)."""
+    rng = np.random.default_rng(7)
+    M = 5
+    L = random_hermitian_coupling(M, rng)
+    L[0, 1, 2, 4] += 0.3 - 0.1j
+    L = L * wl._conserving(M)
+    w = rng.standard_normal(M)
+    space = orc.Space(M, [(5, 2)])
+    psi = rng.standard_normal(space.total) + 1j * rng.standard_normal(space.total)
+    full = orc.apply_h(space, w, L, psi)
+    rows = [0, 3, space.total // 2, space.total - 1]
+    np.testing.assert_allclose(orc.apply_h_rows(space, 0, w, L, psi, rows), full[rows], atol=1e-12)
+
+
+def test_count_terms_equals_dense_structure():
+    M, N = 5, 4
+    w = wl.dispersion_quadratic(M)
+    L = wl.long_range_coupling(M, 0.3)
+    space = orc.Space(M, [(N, P) for P in range(M)])
+    nnz = 0
+    for s in range(M):
+        Hd = orc.h_dense(space, s, w, L)
+        nnz += int((np.abs(Hd - np.diag(np.diag(Hd))) > 0).sum()) + Hd.shape[0]
+    assert orc.count_terms(space, L) == nnz
