@@ -91,9 +91,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def workload(name: str):
+def workload(name: str, n_tot: int = 16):
     if name == "batched_coherent":
-        W = wl.batched_coherent()
+        W = wl.batched_coherent(n_tot=n_tot)
         return W, dict(n_min=0, n_max=W.n_max, p_list=None)
     if name == "large_sector":
         W = wl.large_sector()
@@ -118,7 +118,7 @@ def run_reference(args):
     sample of the workload."""
     import oracle as orc
 
-    W, sp = workload(args.config)
+    W, sp = workload(args.config, args.n_tot)
     if W.kind == "coherent":
         Ns = [min(16, W.n_max)]
     else:
@@ -180,6 +180,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="qb", choices=["qb", "reference"])
     ap.add_argument("--config", default="batched_coherent")
+    ap.add_argument("--n-tot", type=int, default=16, help="mean occupation of the batched coherent workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -200,7 +201,7 @@ def main():
         dist.init_process_group("nccl")
     import paper_2111_00050_gb300 as qb
 
-    W, sp = workload(args.config)
+    W, sp = workload(args.config, args.n_tot)
     qs = qb.Space(W.M, W.w, W.L, sp["n_min"], sp["n_max"], sp["p_list"])
     terms, tuples = qs.terms()
     psi = qs.empty_state()

@@ -189,6 +189,10 @@ static int build_tables(Space& sp) {
   off = align16(off + sizeof(double) * (size_t)M);
   t.o_gd = (int)off;
   off = align16(off + sizeof(double) * (size_t)t.n_ann);
+  t.o_sqf = (int)off;
+  off = align16(off + sizeof(float) * 2 * (size_t)(nmax + 3));
+  t.o_Gf = (int)off;
+  off = align16(off + sizeof(float) * 4 * (size_t)std::max(1, t.n_combo));
   t.blob_bytes = (int)off;
   sp.blob.assign(off, 0);
   unsigned char* b = sp.blob.data();
@@ -207,13 +211,26 @@ static int build_tables(Space& sp) {
   for (int k = 0; k < nmax + 3; ++k) sq[k] = std::sqrt((double)k);
   memcpy(b + t.o_pq, pq.data(), sizeof(uint32_t) * pq.size());
   memcpy(b + t.o_G, G.data(), sizeof(double) * G.size());
-  int8_t* dl = (int8_t*)(b + t.o_delta);
+  uint8_t* dl = (uint8_t*)(b + t.o_delta);
   for (int j = 0; j < t.n_combo; ++j)
-    for (int m = 0; m < 16; ++m) dl[(size_t)m * t.n_combo + j] = delta[j][m];
+    for (int m = 0; m < 16; ++m) dl[(size_t)j * 16 + m] = (uint8_t)(delta[j][m] + kDeltaBias);
   memcpy(b + t.o_ann, annStart.data(), sizeof(int32_t) * annStart.size());
   memcpy(b + t.o_pairidx, pairidx, 256);
   memcpy(b + t.o_w, sp.w.data(), sizeof(double) * M);
   memcpy(b + t.o_gd, gd.data(), sizeof(double) * gd.size());
+  // double-float copies: x = hi + lo with hi = fl32(x), lo = fl32(x - hi)
+  auto split = [](double x, float* out) {
+    float h = (float)x;
+    out[0] = h;
+    out[1] = (float)(x - (double)h);
+  };
+  float* sqf = (float*)(b + t.o_sqf);
+  for (int k = 0; k < nmax + 3; ++k) split(std::sqrt((double)k), sqf + 2 * k);
+  float* Gf = (float*)(b + t.o_Gf);
+  for (int j = 0; j < t.n_combo; ++j) {
+    split(G[2 * j], Gf + 4 * j);
+    split(G[2 * j + 1], Gf + 4 * j + 2);
+  }
   return QB_OK;
 }
 
@@ -460,6 +477,7 @@ void qb_space_free(qb_space* space) {
   cudaFree(sp->d_secK);
   cudaFree(sp->d_secOf);
   cudaFree(sp->d_scratch);
+  cudaFree(sp->d_diag);
   delete sp;
 }
 

@@ -5,9 +5,15 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "../../include/qb.h"
 
 namespace qb {
+
+// Shifts of a suffix-state index are stored as unsigned bytes offset by this bias
+// (a shift lies in [-4M, 5M) for M <= 16).
+constexpr int kDeltaBias = 64;
 
 // Everything a kernel needs to walk one space, passed by value.
 //
@@ -35,11 +41,13 @@ struct Tables {
   int o_sqrt;    // double [nmax+3]            sqrt(k)
   int o_pq;      // uint32 [n_combo]           p | q<<8 | lo<<16 | hi<<24
   int o_G;       // double [n_combo][2]        conj(mult * L^sym_{pq;rs}) (re, im)
-  int o_delta;   // int8   [16][n_combo]       flat-index shift of the suffix state at mode m
+  int o_delta;   // uint8  [n_combo][16]       kDeltaBias + flat-index shift of the suffix state at mode m
   int o_ann;     // int32  [n_ann + 1]         first combo of annihilation pair a
   int o_pairidx; // uint8  [16][16]            pair index of (r <= s)
   int o_w;       // double [M]                 one-body w_p
   int o_gd;      // double [n_ann]             diagonal two-body coefficient mult_rs^2 L^sym_{rs;rs}
+  int o_sqf;     // float2 [nmax+3]            sqrt(k) as a double-float pair (hi, lo)
+  int o_Gf;      // float4 [n_combo]           G as double-float pairs (re.hi, re.lo, im.hi, im.lo)
   const unsigned char* blob;  // device pointer to the image
   // sectors
   int n_sectors;
@@ -68,6 +76,7 @@ struct Space {
   int32_t* d_secK = nullptr;
   int32_t* d_secOf = nullptr;
   double* d_scratch = nullptr;  // reduction partials
+  float4* d_diag = nullptr;     // per ket: one-body and two-body diagonal as double-float pairs
   int64_t scratch_doubles = 0;
   Tables t{};
   int device = 0;

@@ -237,7 +237,8 @@ __global__ void __launch_bounds__(kBlock) hpsi_kernel(const Tables t, const Stag
         const int np_ = occ[p * kBlock], nq = occ[q * kBlock];
         const double Bf = v.sq[np_ + 1] * v.sq[nq + 1 + (p == q ? 1 : 0)];
         int64_t rk = rank_base + pe[hi * kBlock] - pe[lo * kBlock];
-        for (int m = lo + 1; m <= hi; ++m) rk -= v.E[idx[m * kBlock] + v.delta[m * t.n_combo + j]];
+        const uint8_t* dj = reinterpret_cast<const uint8_t*>(v.delta) + j * 16;
+        for (int m = lo + 1; m <= hi; ++m) rk -= v.E[idx[m * kBlock] + (int)dj[m] - kDeltaBias];
         if (rk < 0 || rk >= D) {
           atomicOr(a.status, 1);
           rk = 0;
@@ -304,6 +305,317 @@ __global__ void __launch_bounds__(kBlock) hpsi_kernel(const Tables t, const Stag
       a.partial[2 * blockIdx.x] = sr;
       a.partial[2 * blockIdx.x + 1] = si;
     }
+  }
+}
+
+
+// ------------------------------------------------ double-float RK4 stages
+//
+// GB300's FP64 pipe runs at about 1/74 of the FP32 rate, so the gather-heavy
+// stages accumulate in double-float arithmetic: a value is the unevaluated sum
+// hi + lo of two fp32 numbers (about 48 significant bits).  Products use the
+// exact fma-based error term, sums the branch-free TwoSum; the intrinsics
+// __fmul_rn / __fadd_rn keep the compiler from contracting them.  The state
+// psi itself stays FP64: the last stage of each step forms psi + z H v in FP64.
+
+struct dfl {
+  float h, l;
+};
+
+__device__ __forceinline__ dfl df_of(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(dfl a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.h, -a.l}; }
+
+// a * b, unnormalised (|l| is a few ulp of h)
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return {p, e};
+}
+
+// acc += c * x; acc.h carries the TwoSum, acc.l gathers every rounding error
+__device__ __forceinline__ void df_fma(dfl& acc, dfl c, dfl x) {
+  const float p = __fmul_rn(c.h, x.h);
+  float e = fmaf(c.h, x.h, -p);
+  e = fmaf(c.h, x.l, e);
+  e = fmaf(c.l, x.h, e);
+  const float s = __fadd_rn(acc.h, p);
+  const float bb = __fsub_rn(s, acc.h);
+  const float err = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  acc.h = s;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(err, e));
+}
+
+// a + b, renormalised
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float bb = __fsub_rn(s, a.h);
+  float err = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+  err = __fadd_rn(err, __fadd_rn(a.l, b.l));
+  const float h = __fadd_rn(s, err);
+  return {h, __fsub_rn(err, __fsub_rn(h, s))};
+}
+
+struct DfArgs {
+  const float4* vin;   // gathered stage vector(s), double-float [B][total]
+  const float4* psif;  // double-float copy of psi [B][total]
+  double2* psi;        // psi (FP64) [B][total]; updated in the final stage
+  float4* out;         // stage output, double-float [B][total] (final stage: new copy of psi)
+  const float4* diag;  // per ket (w.hi, w.lo, L.hi, L.lo)
+  float2 scale[8];     // two-body scale per member, double-float
+  double zre;          // dt / d: out = psi + (dt/d) (Im Hv, -Re Hv)
+  float2 zf;           // dt / d as double-float
+  int* status;
+};
+
+// Shared scratch of the double-float stage kernel, after the table image:
+//   sidx  int32 [M][kBlock]  flat E index of each row's suffix state at mode m,
+//                            minus kDeltaBias (so a stored shift byte adds directly)
+//   socc  uint8 [M][kBlock]  occupations
+//   sD    int32 [kBlock]     sector dimension of the row (-1: no row)
+//   sOff  int64 [kBlock]     sector offset of the row
+//   sperm int32 [kBlock]     processing order (rows sorted by work, most first)
+//   hist  int32 [2][n_ann+2] counting-sort buckets and cursors
+__host__ __device__ inline size_t df_scratch_bytes(int M, int n_ann) {
+  size_t b = (size_t)M * kBlock * 4 + (((size_t)M * kBlock + 15) & ~(size_t)15);
+  b += (size_t)kBlock * 4 + (size_t)kBlock * 8 + (size_t)kBlock * 4 + 2 * (size_t)(n_ann + 2) * 4;
+  return (b + 15) & ~(size_t)15;
+}
+
+template <int B, bool CPLX>
+__global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const DfArgs a, const int final_stage) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  load_blob(t, smem);
+  const View v = make_view(t, smem);
+  const float2* sqf = reinterpret_cast<const float2*>(smem + t.o_sqf);
+  const float4* Gf = reinterpret_cast<const float4*>(smem + t.o_Gf);
+  const uint4* dl4 = reinterpret_cast<const uint4*>(v.delta);
+  const int M = t.M, V = t.nmax + 1, twoM = 2 * M;
+  unsigned char* sp = smem + ((t.blob_bytes + 15) & ~15);
+  int32_t* sidx = reinterpret_cast<int32_t*>(sp);
+  uint8_t* socc = reinterpret_cast<uint8_t*>(sidx + M * kBlock);
+  int32_t* sD = reinterpret_cast<int32_t*>(socc + ((M * kBlock + 15) & ~15));
+  int64_t* sOff = reinterpret_cast<int64_t*>(sD + kBlock);
+  int32_t* sperm = reinterpret_cast<int32_t*>(sOff + kBlock);
+  int32_t* hist = sperm + kBlock;
+  int32_t* cursor = hist + (t.n_ann + 2);
+  const int tid = threadIdx.x;
+  const int64_t total = t.total;
+  const int nb = t.n_ann + 2;
+
+  for (int64_t base = (int64_t)blockIdx.x * kBlock; base < total; base += (int64_t)gridDim.x * kBlock) {
+    // ---- phase 1: own row -> occupations, suffix-state indices, work key
+    const int64_t g = base + tid;
+    int key = 0;
+    for (int k = tid; k < 2 * nb; k += kBlock) hist[k] = 0;
+    if (g < total) {
+      const int sid = find_sector(t, g);
+      const int64_t off = __ldg(t.sec_off + sid);
+      const int D = (int)(__ldg(t.sec_off + sid + 1) - off);
+      int rem = __ldg(t.sec_N + sid), kr = __ldg(t.sec_K + sid);
+      int64_t left = g - off;
+      for (int m = 0; m < M - 1; ++m) {
+        int val = 0, kk = kr;
+        const uint32_t* row = v.cnt + (size_t)(m + 1) * V * M;
+        while (true) {
+          const uint32_t c = row[(rem - val) * M + kk];
+          if (left < (int64_t)c || val == rem) break;
+          left -= c;
+          ++val;
+          kk -= m;
+          if (kk < 0) kk += M;
+        }
+        socc[m * kBlock + tid] = (uint8_t)val;
+        rem -= val;
+        kr = kk;
+      }
+      socc[(M - 1) * kBlock + tid] = (uint8_t)rem;
+      int srem = 0, skr = 0, esum = 0, np = 0, n2 = 0;
+      for (int m = M - 1; m >= 1; --m) {
+        const int nm = socc[m * kBlock + tid];
+        srem += nm;
+        skr = (skr + m * nm) % M;
+        const int ix = (m * t.rem_w + srem + 2) * twoM + skr;
+        esum += v.E[ix];
+        sidx[m * kBlock + tid] = ix - kDeltaBias;
+      }
+      if (D - 1 - esum != (int)(g - off)) atomicOr(a.status, 2);
+      for (int m = 0; m < M; ++m) {
+        const int nm = socc[m * kBlock + tid];
+        np += nm >= 1;
+        n2 += nm >= 2;
+      }
+      key = np * (np - 1) / 2 + n2;  // number of annihilation pairs r <= s acting on the row
+      sD[tid] = D;
+      sOff[tid] = off;
+    } else {
+      sD[tid] = -1;
+    }
+    // ---- phase 2: counting sort of the rows by work, largest first
+    __syncthreads();
+    atomicAdd(&hist[key], 1);
+    __syncthreads();
+    if (tid == 0) {
+      int run = 0;
+      for (int k = nb - 1; k >= 0; --k) {
+        cursor[k] = run;
+        run += hist[k];
+      }
+    }
+    __syncthreads();
+    sperm[atomicAdd(&cursor[key], 1)] = tid;
+    __syncthreads();
+
+    // ---- phase 3: the terms of row `row`
+    const int row = sperm[tid];
+    const int D = sD[row];
+    if (D >= 0) {
+      const int64_t off = sOff[row];
+      const int64_t gr = base + row;
+      const uint8_t* occ = socc + row;
+      int id[16];
+#pragma unroll
+      for (int m = 1; m < 16; ++m)
+        if (m < M) id[m] = sidx[m * kBlock + row];
+      uint32_t occmask = 0, twomask = 0;
+      for (int m = 0; m < M; ++m) {
+        const int nm = occ[m * kBlock];
+        occmask |= (nm >= 1 ? 1u : 0u) << m;
+        twomask |= (nm >= 2 ? 1u : 0u) << m;
+      }
+      const float4* vsec = a.vin + off;
+      dfl acc_r[B], acc_i[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) acc_r[b] = acc_i[b] = dfl{0.f, 0.f};
+
+      uint32_t rm = occmask, smask = 0;
+      int r = 0;
+      while (true) {
+        if (smask == 0) {
+          if (rm == 0) break;
+          r = __ffs(rm) - 1;
+          rm &= rm - 1;
+          smask = occmask & (~0u << r);
+          if (!((twomask >> r) & 1u)) smask &= ~(1u << r);
+          if (smask == 0) continue;
+        }
+        const int s = __ffs(smask) - 1;
+        smask &= smask - 1;
+        const int ai = v.pairidx[r * 16 + s];
+        const int nr = occ[r * kBlock], ns = occ[s * kBlock];
+        const float2 sa = sqf[nr], sb = sqf[ns - (r == s ? 1 : 0)];
+        const dfl A = df_mul(dfl{sa.x, sa.y}, dfl{sb.x, sb.y});
+        dfl pr[B], pim[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) pr[b] = pim[b] = dfl{0.f, 0.f};
+        const int j1 = v.ann[ai + 1];
+        for (int j = v.ann[ai]; j < j1; ++j) {
+          const uint32_t w4 = v.pq[j];
+          const int p = w4 & 0xff, q = (w4 >> 8) & 0xff;
+          const float2 bp = sqf[occ[p * kBlock] + 1], bq = sqf[occ[q * kBlock] + 1 + (p == q ? 1 : 0)];
+          const dfl Bv = df_mul(dfl{bp.x, bp.y}, dfl{bq.x, bq.y});
+          // rank of the target: D - 1 - sum over every mode of E at the shifted suffix state
+          const uint4 dd = dl4[j];
+          int esum = 0;
+#pragma unroll
+          for (int m = 1; m < 16; ++m) {
+            if (m >= M) break;
+            const uint32_t word = (m < 4) ? dd.x : (m < 8) ? dd.y : (m < 12) ? dd.z : dd.w;
+            esum += v.E[id[m] + (int)((word >> (8 * (m & 3))) & 0xffu)];
+          }
+          int rk = D - 1 - esum;
+          if ((unsigned)rk >= (unsigned)D) {
+            atomicOr(a.status, 1);
+            rk = 0;
+          }
+          const float4 gf = Gf[j];
+          const dfl cr = df_mul(dfl{gf.x, gf.y}, Bv);
+#pragma unroll
+          for (int b = 0; b < B; ++b) {
+            const float4 x = __ldg(vsec + (size_t)b * total + rk);
+            df_fma(pr[b], cr, dfl{x.x, x.y});
+            df_fma(pim[b], cr, dfl{x.z, x.w});
+            if (CPLX) {
+              const dfl ci = df_mul(dfl{gf.z, gf.w}, Bv);
+              df_fma(pr[b], df_neg(ci), dfl{x.z, x.w});
+              df_fma(pim[b], ci, dfl{x.x, x.y});
+            }
+          }
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          acc_r[b] = df_add(acc_r[b], df_mul(A, df_add(pr[b], dfl{0.f, 0.f})));
+          acc_i[b] = df_add(acc_i[b], df_mul(A, df_add(pim[b], dfl{0.f, 0.f})));
+        }
+      }
+
+      const float4 dg4 = a.diag[gr];
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const dfl sc{a.scale[b].x, a.scale[b].y};
+        const dfl dg = df_add(dfl{dg4.x, dg4.y}, df_mul(sc, dfl{dg4.z, dg4.w}));
+        const float4 xo = a.vin[(size_t)b * total + gr];
+        const dfl hr = df_add(df_mul(dg, dfl{xo.x, xo.y}), df_mul(sc, acc_r[b]));
+        const dfl hi = df_add(df_mul(dg, dfl{xo.z, xo.w}), df_mul(sc, acc_i[b]));
+        if (!final_stage) {
+          const float4 p0 = a.psif[(size_t)b * total + gr];
+          const dfl zf{a.zf.x, a.zf.y};
+          const dfl orr = df_add(dfl{p0.x, p0.y}, df_mul(zf, hi));
+          const dfl oi = df_add(dfl{p0.z, p0.w}, df_neg(df_mul(zf, hr)));
+          a.out[(size_t)b * total + gr] = make_float4(orr.h, orr.l, oi.h, oi.l);
+        } else {
+          const double2 p0 = a.psi[(size_t)b * total + gr];
+          const double nr = p0.x + a.zre * df_to(hi);
+          const double ni = p0.y - a.zre * df_to(hr);
+          a.psi[(size_t)b * total + gr] = make_double2(nr, ni);
+          const dfl fr = df_of(nr), fi = df_of(ni);
+          a.out[(size_t)b * total + gr] = make_float4(fr.h, fr.l, fi.h, fi.l);
+        }
+      }
+    }
+    __syncthreads();  // scratch is rewritten by the next tile
+  }
+}
+
+// psi (FP64) -> double-float copy
+__global__ void to_df_kernel(const double2* psi, float4* out, int64_t n) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const double2 x = psi[k];
+    const dfl r = df_of(x.x), i = df_of(x.y);
+    out[k] = make_float4(r.h, r.l, i.h, i.l);
+  }
+}
+
+// per-ket diagonal of H, one-body and two-body parts, as double-float pairs
+__global__ void __launch_bounds__(kBlock) diag_kernel(const Tables t, float4* diag) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  load_blob(t, smem);
+  const View v = make_view(t, smem);
+  const RowScratch rs = row_scratch(smem + ((t.blob_bytes + 15) & ~15));
+  const int tid = threadIdx.x, M = t.M;
+  for (int64_t base = (int64_t)blockIdx.x * kBlock; base < t.total; base += (int64_t)gridDim.x * kBlock) {
+    const int64_t g = base + tid;
+    if (g >= t.total) break;
+    const int sid = find_sector(t, g);
+    const int64_t off = __ldg(t.sec_off + sid);
+    const int64_t D = __ldg(t.sec_off + sid + 1) - off;
+    setup_row(t, v, rs, __ldg(t.sec_N + sid), __ldg(t.sec_K + sid), D, g - off);
+    double dw = 0.0, dl = 0.0;
+    for (int r = 0; r < M; ++r) {
+      const int nr = rs.occ[r * kBlock + tid];
+      dw += v.w[r] * nr;
+      for (int s2 = r; s2 < M; ++s2) {
+        const int ns = rs.occ[s2 * kBlock + tid] - (r == s2 ? 1 : 0);
+        if (nr >= 1 && ns >= 1) dl += v.gd[v.pairidx[r * 16 + s2]] * (double)(nr * ns);
+      }
+    }
+    const dfl a = df_of(dw), b = df_of(dl);
+    diag[g] = make_float4(a.h, a.l, b.h, b.l);
   }
 }
 
@@ -696,10 +1008,22 @@ int device_setup(Space& s) {
                       2 * (int64_t)s.M * (s.nmax + 1) + 2;
   QB_CUDA(cudaMalloc(&s.d_scratch, sizeof(double) * s.scratch_doubles));
   QB_CUDA(cudaMemset(s.d_scratch, 0, sizeof(double) * s.scratch_doubles));
+  QB_CUDA(cudaMalloc(&s.d_diag, sizeof(float4) * (size_t)t.total));
+  {
+    const size_t smem = row_smem(t);
+    int grid = 0;
+    int rc = persistent_grid(diag_kernel, smem, t.total, &grid);
+    if (rc) return rc;
+    diag_kernel<<<grid, kBlock, smem>>>(t, s.d_diag);
+    QB_CUDA(cudaGetLastError());
+    QB_CUDA(cudaDeviceSynchronize());
+  }
   return QB_OK;
 }
 
-int64_t workspace_bytes(const Space& s, int batch) { return 2 * (int64_t)batch * s.secOff.back() * 16; }
+// workspace: two double-float stage vectors and the double-float copy of psi,
+// each [batch][total] x 16 bytes
+int64_t workspace_bytes(const Space& s, int batch) { return 3 * (int64_t)batch * s.secOff.back() * 16; }
 
 template <int MODE, int B, bool CPLX>
 static int launch_stage(const Space& s, const StageArgs& a, cudaStream_t st, int* grid_out = nullptr) {
@@ -732,23 +1056,44 @@ int launch_hpsi(const Space& s, const void* d_v, void* d_out, void* stream) {
   return check_status(s, st);
 }
 
-template <int B>
-static int rk4_loop(Space& s, double2* psi, const double* scale, double dt, int64_t steps, double2* w1, double2* w2,
-                    cudaStream_t st) {
-  StageArgs a{};
-  for (int b = 0; b < B; ++b) a.scale[b] = scale[b];
+static size_t df_smem(const Tables& t) { return ((t.blob_bytes + 15) & ~15) + df_scratch_bytes(t.M, t.n_ann); }
+
+template <int B, bool CPLX>
+static int df_grid(const Space& s, int* grid) {
+  return persistent_grid(stage_df_kernel<B, CPLX>, df_smem(s.t), s.t.total, grid);
+}
+
+template <int B, bool CPLX>
+static int rk4_loop(Space& s, double2* psi, const double* scale, double dt, int64_t steps, float4* w1, float4* w2,
+                    float4* psif, cudaStream_t st) {
+  const int64_t n = (int64_t)B * s.t.total;
+  int grid = 0;
+  int rc = df_grid<B, CPLX>(s, &grid);
+  if (rc) return rc;
+  const size_t smem = df_smem(s.t);
+  to_df_kernel<<<1216, 256, 0, st>>>(psi, psif, n);
+  QB_CUDA(cudaGetLastError());
+  DfArgs a{};
+  for (int b = 0; b < B; ++b) {
+    const dfl x = {(float)scale[b], (float)(scale[b] - (double)(float)scale[b])};
+    a.scale[b] = make_float2(x.h, x.l);
+  }
+  a.diag = s.d_diag;
+  a.psi = psi;
+  a.psif = psif;
   a.status = reinterpret_cast<int*>(s.d_scratch);
-  for (int64_t n = 0; n < steps; ++n) {
+  for (int64_t it = 0; it < steps; ++it) {
     // Horner: v = psi + z/4 H psi; v = psi + z/3 H v; v = psi + z/2 H v; psi = psi + z H v
-    const double2* in[4] = {psi, w1, w2, w1};
-    double2* out[4] = {w1, w2, w1, psi};
+    const float4* in[4] = {psif, w1, w2, w1};
+    float4* out[4] = {w1, w2, w1, psif};
     for (int d = 4; d >= 1; --d) {
       a.vin = in[4 - d];
       a.out = out[4 - d];
-      a.psi = psi;
       a.zre = dt / d;
-      int rc = launch_stage_c<MODE_STAGE, B>(s, a, st);
-      if (rc) return rc;
+      const float zh = (float)a.zre;
+      a.zf = make_float2(zh, (float)(a.zre - (double)zh));
+      stage_df_kernel<B, CPLX><<<grid, kBlock, smem, st>>>(s.t, a, d == 1 ? 1 : 0);
+      QB_CUDA(cudaGetLastError());
     }
   }
   return QB_OK;
@@ -759,14 +1104,20 @@ int launch_rk4(Space& s, void* d_psi, int batch, const double* scale, double dt,
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = (int64_t)batch * s.secOff.back();
   double2* psi = (double2*)d_psi;
-  double2* w1 = (double2*)d_work;
-  double2* w2 = w1 + n;
+  float4* w1 = (float4*)d_work;
+  float4* w2 = w1 + n;
+  float4* psif = w2 + n;
+  const bool c = s.t.is_complex != 0;
   int rc;
   switch (batch) {
-    case 1: rc = rk4_loop<1>(s, psi, scale, dt, steps, w1, w2, st); break;
-    case 2: rc = rk4_loop<2>(s, psi, scale, dt, steps, w1, w2, st); break;
-    case 4: rc = rk4_loop<4>(s, psi, scale, dt, steps, w1, w2, st); break;
-    case 8: rc = rk4_loop<8>(s, psi, scale, dt, steps, w1, w2, st); break;
+    case 1: rc = c ? rk4_loop<1, true>(s, psi, scale, dt, steps, w1, w2, psif, st)
+                   : rk4_loop<1, false>(s, psi, scale, dt, steps, w1, w2, psif, st); break;
+    case 2: rc = c ? rk4_loop<2, true>(s, psi, scale, dt, steps, w1, w2, psif, st)
+                   : rk4_loop<2, false>(s, psi, scale, dt, steps, w1, w2, psif, st); break;
+    case 4: rc = c ? rk4_loop<4, true>(s, psi, scale, dt, steps, w1, w2, psif, st)
+                   : rk4_loop<4, false>(s, psi, scale, dt, steps, w1, w2, psif, st); break;
+    case 8: rc = c ? rk4_loop<8, true>(s, psi, scale, dt, steps, w1, w2, psif, st)
+                   : rk4_loop<8, false>(s, psi, scale, dt, steps, w1, w2, psif, st); break;
     default: return fail(QB_EINVAL, "batch must be 1, 2, 4 or 8");
   }
   if (rc) return rc;
