@@ -35,6 +35,14 @@ static int mod_pos(int a, int M) {
   return r < 0 ? r + M : r;
 }
 
+/* the mode index s whose label is congruent to k (mod M); unique for both label
+ * conventions */
+static int mode_of_residue(int M, int k) {
+  for (int i = 0; i < M; ++i)
+    if (mod_pos(label_of(M, i) - k, M) == 0) return i;
+  return -1;
+}
+
 static int momentum_of(int M, const int* n) {
   int k = 0;
   for (int i = 0; i < M; ++i) k += label_of(M, i) * n[i];
@@ -118,7 +126,8 @@ int orc_check_coupling(int M, const double* L) {
  */
 int orc_apply_h(int M, int64_t D, const int* basis, const double* w, const double* L, const double* psi,
                 double* out, int dagger) {
-  int tmp[64];
+  int tmp[64], r2m[64];
+  for (int k = 0; k < M; ++k) r2m[k] = mode_of_residue(M, k);
   memset(out, 0, sizeof(double) * 2 * (size_t)D);
   for (int64_t j = 0; j < D; ++j) {
     const int* n = basis + j * M;
@@ -128,12 +137,12 @@ int orc_apply_h(int M, int64_t D, const int* basis, const double* w, const doubl
     for (int p = 0; p < M; ++p) diag += w[p] * n[p];
     out[2 * j] += diag * pr;
     out[2 * j + 1] += diag * pi;
-    /* two-body part */
+    /* two-body part: every ordered tuple (p,q,r,s); momentum conservation mod M
+     * (the Kronecker delta of Eq. Lambda) leaves one s for each (p,q,r) */
     for (int p = 0; p < M; ++p)
       for (int q = 0; q < M; ++q)
-        for (int r = 0; r < M; ++r)
-          for (int s = 0; s < M; ++s) {
-            if (mod_pos(label_of(M, p) + label_of(M, q) - label_of(M, r) - label_of(M, s), M) != 0) continue;
+        for (int r = 0; r < M; ++r) {
+          int s = r2m[mod_pos(label_of(M, p) + label_of(M, q) - label_of(M, r), M)];
             int64_t t = (((int64_t)p * M + q) * M + r) * M + s;
             double lr = L[2 * t], li = L[2 * t + 1];
             if (lr == 0.0 && li == 0.0) continue;
@@ -364,11 +373,12 @@ int orc_apply_h_row(int M, int64_t D, const int* basis, const double* w, const d
   for (int p = 0; p < M; ++p) diag += w[p] * n[p];
   accr += diag * psi[2 * i];
   acci += diag * psi[2 * i + 1];
+  int r2m[64];
+  for (int k = 0; k < M; ++k) r2m[k] = mode_of_residue(M, k);
   for (int p = 0; p < M; ++p)
     for (int q = 0; q < M; ++q)
-      for (int r = 0; r < M; ++r)
-        for (int s = 0; s < M; ++s) {
-          if (mod_pos(label_of(M, p) + label_of(M, q) - label_of(M, r) - label_of(M, s), M) != 0) continue;
+      for (int r = 0; r < M; ++r) {
+        int s = r2m[mod_pos(label_of(M, p) + label_of(M, q) - label_of(M, r), M)];
           int64_t t = (((int64_t)p * M + q) * M + r) * M + s;
           double lr = L[2 * t], li = L[2 * t + 1];
           if (lr == 0.0 && li == 0.0) continue;
@@ -405,7 +415,8 @@ int orc_apply_h_row(int M, int64_t D, const int* basis, const double* w, const d
  * oracle's speed in H psi terms per second.
  */
 int64_t orc_count_terms(int M, int64_t D, const int* basis, const double* L) {
-  int tmp[64];
+  int tmp[64], r2m[64];
+  for (int k = 0; k < M; ++k) r2m[k] = mode_of_residue(M, k);
   int64_t total = 0;
   int64_t cap = 1024, *tg = malloc(sizeof(int64_t) * (size_t)cap);
   for (int64_t j = 0; j < D; ++j) {
@@ -414,9 +425,8 @@ int64_t orc_count_terms(int M, int64_t D, const int* basis, const double* L) {
     tg[nt++] = j; /* the diagonal */
     for (int p = 0; p < M; ++p)
       for (int q = 0; q < M; ++q)
-        for (int r = 0; r < M; ++r)
-          for (int s = 0; s < M; ++s) {
-            if (mod_pos(label_of(M, p) + label_of(M, q) - label_of(M, r) - label_of(M, s), M) != 0) continue;
+        for (int r = 0; r < M; ++r) {
+          int s = r2m[mod_pos(label_of(M, p) + label_of(M, q) - label_of(M, r), M)];
             int64_t t = (((int64_t)p * M + q) * M + r) * M + s;
             if (L[2 * t] == 0.0 && L[2 * t + 1] == 0.0) continue;
             memcpy(tmp, n, sizeof(int) * (size_t)M);

@@ -171,7 +171,7 @@ def test_coherent_multi_sector_evolution_and_observables():
 
 def test_field_number_long_range_window():
     """Scaled-down gravity-like workload: M=9 long range, field number state."""
-    Wl = wl.long_range_field_number(M=9, seed=0, mean=1.0)
+    Wl = wl.long_range_field_number(M=9, seed=0, mean=0.5)
     n_tot = Wl.n_tot
     qs, os_ = pair(Wl.M, Wl.w, Wl.L, n_tot, n_tot, None)
     psi = qs.empty_state()
@@ -180,8 +180,8 @@ def test_field_number_long_range_window():
     assert rel_err(to_host(psi), ref) <= 1e-13
     ob = qs.observables(psi)
     assert abs(ob["Q"] - 1) < 1e-9 and abs(ob["lam_p"] - n_tot) < 1e-9 * n_tot
-    qs.evolve(psi, Wl.dt, 200)
-    ref = orc.rk4(os_, Wl.w, Wl.L, ref, Wl.dt, 200)
+    qs.evolve(psi, Wl.dt, 100)
+    ref = orc.rk4(os_, Wl.w, Wl.L, ref, Wl.dt, 100)
     assert rel_err(to_host(psi), ref) <= STATE_TOL
     ro = orc.observables(os_, ref)
     ob = qs.observables(psi)
