@@ -348,10 +348,13 @@ static void derive(int M, const double* raw, qb_obs* o) {
   const double* AA = Mm + 2 * M * M;
   std::vector<cd> a(M), Mij((size_t)M * M), aa((size_t)M * M);
   for (int i = 0; i < M; ++i) a[i] = cd(A[2 * i], A[2 * i + 1]) / nrm;
-  for (int i = 0; i < M * M; ++i) {
-    Mij[i] = cd(Mm[2 * i], Mm[2 * i + 1]) / nrm;
-    aa[i] = cd(AA[2 * i], AA[2 * i + 1]) / nrm;
-  }
+  for (int i = 0; i < M * M; ++i) Mij[i] = cd(Mm[2 * i], Mm[2 * i + 1]) / nrm;
+  // <a_k a_l> is symmetric; the device fills k <= l only
+  for (int k = 0; k < M; ++k)
+    for (int l = 0; l < M; ++l) {
+      const int u = (k <= l) ? k * M + l : l * M + k;
+      aa[(size_t)k * M + l] = cd(AA[2 * u], AA[2 * u + 1]) / nrm;
+    }
   for (int i = 0; i < M; ++i) {
     o->a[2 * i] = a[i].real();
     o->a[2 * i + 1] = a[i].imag();
