@@ -17,8 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libqb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["qb_host.cpp", "qb_kernels.cu"]
-HEADERS = ["qb_internal.h", os.path.join("..", "..", "include", "qb.h")]
+SOURCES = ["qb_host.cpp", "qb_kernels.cu", "qb_stage_m5.cu", "qb_stage_m7.cu", "qb_stage_m9.cu", "qb_stage_m11.cu",
+           "qb_stage_any.cu"]
+HEADERS = ["qb_internal.h", "qb_device.cuh", "qb_stage.cuh", os.path.join("..", "..", "include", "qb.h")]
 
 
 def _nvcc() -> str:
@@ -57,7 +58,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             sys.stderr.write(r.stdout + r.stderr)
         return obj
 
-    with concurrent.futures.ThreadPoolExecutor(len(SOURCES)) as ex:
+    with concurrent.futures.ThreadPoolExecutor(min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]

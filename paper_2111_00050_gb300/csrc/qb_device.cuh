@@ -1,0 +1,253 @@
+// Device-side building blocks shared by the qb kernels: the shared-memory view
+// of a space's tables, row unranking into suffix states, double-float
+// arithmetic and the persistent-grid helper.  Internal; see qb_internal.h.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <string>
+
+#include "qb_internal.h"
+
+namespace qb {
+
+#define QB_CUDA(x)                                                                            \
+  do {                                                                                        \
+    cudaError_t e_ = (x);                                                                     \
+    if (e_ != cudaSuccess) return fail(QB_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr int kBlock = 128;  // threads per CTA of the row kernels (one row per thread per pass)
+constexpr int kMaxM = QB_MAX_MODES;
+
+// ----------------------------------------------------------------- smem view
+
+struct View {
+  const uint32_t* cnt;
+  const int32_t* E;
+  const double* sq;
+  const uint32_t* pq;
+  const double* G;
+  const int8_t* delta;
+  const int32_t* ann;
+  const uint8_t* pairidx;
+  const double* w;
+  const double* gd;
+};
+
+__device__ __forceinline__ View make_view(const Tables& t, const unsigned char* s) {
+  View v;
+  v.cnt = (const uint32_t*)(s + t.o_cnt);
+  v.E = (const int32_t*)(s + t.o_E);
+  v.sq = (const double*)(s + t.o_sqrt);
+  v.pq = (const uint32_t*)(s + t.o_pq);
+  v.G = (const double*)(s + t.o_G);
+  v.delta = (const int8_t*)(s + t.o_delta);
+  v.ann = (const int32_t*)(s + t.o_ann);
+  v.pairidx = (const uint8_t*)(s + t.o_pairidx);
+  v.w = (const double*)(s + t.o_w);
+  v.gd = (const double*)(s + t.o_gd);
+  return v;
+}
+
+// Copies the table image into shared memory (16-byte vector copies).
+__device__ __forceinline__ void load_blob(const Tables& t, unsigned char* smem) {
+  const int4* src = reinterpret_cast<const int4*>(t.blob);
+  int4* dst = reinterpret_cast<int4*>(smem);
+  for (int i = threadIdx.x; i < t.blob_bytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+  __syncthreads();
+}
+
+// Per-thread scratch rows in shared memory, laid out [m][thread] so that the
+// lanes of a warp touching the same mode hit consecutive words.
+struct RowScratch {
+  uint8_t* occ;  // [kMaxM][kBlock]
+  int32_t* idx;  // [kMaxM][kBlock] flat E index of the suffix state at mode m
+  int32_t* pe;   // [kMaxM][kBlock] prefix sums of E over the row's own suffix states
+};
+
+__device__ __forceinline__ RowScratch row_scratch(unsigned char* base) {
+  RowScratch r;
+  r.idx = reinterpret_cast<int32_t*>(base);
+  r.pe = r.idx + kMaxM * kBlock;
+  r.occ = reinterpret_cast<uint8_t*>(r.pe + kMaxM * kBlock);
+  return r;
+}
+constexpr int kRowScratchBytes = kMaxM * kBlock * (4 + 4 + 1);
+
+__device__ __forceinline__ int find_sector(const Tables& t, int64_t g) {
+  int lo = 0, hi = t.n_sectors - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(t.sec_off + mid) <= g)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// Unranks local index i of sector (N, K) into the occupation vector and fills
+// the suffix-state indices and their prefix sums.  Returns rank(n) recomputed
+// from the suffix states (equals i for a consistent table).
+__device__ __forceinline__ int64_t setup_row(const Tables& t, const View& v, const RowScratch& rs, int N, int K,
+                                             int64_t D, int64_t i) {
+  const int M = t.M, tid = threadIdx.x, V = t.nmax + 1;
+  int rem = N, kr = K;
+  int64_t left = i;
+  for (int m = 0; m < M - 1; ++m) {
+    int val = 0, kk = kr;
+    const uint32_t* row = v.cnt + (size_t)(m + 1) * V * M;
+    while (true) {
+      uint32_t c = row[(rem - val) * M + kk];
+      if (left < (int64_t)c || val == rem) break;
+      left -= c;
+      ++val;
+      kk -= m;
+      if (kk < 0) kk += M;
+    }
+    rs.occ[m * kBlock + tid] = (uint8_t)val;
+    rem -= val;
+    kr = kk;
+  }
+  rs.occ[(M - 1) * kBlock + tid] = (uint8_t)rem;
+  // suffix states, from the top mode down
+  const int twoM = 2 * M;
+  int srem = 0, skr = 0;
+  for (int m = M - 1; m >= 1; --m) {
+    int nm = rs.occ[m * kBlock + tid];
+    srem += nm;
+    skr = (skr + m * nm) % M;
+    rs.idx[m * kBlock + tid] = (m * t.rem_w + srem + 2) * twoM + skr;
+  }
+  int32_t acc = 0;
+  rs.pe[tid] = 0;
+  for (int m = 1; m < M; ++m) {
+    acc += v.E[rs.idx[m * kBlock + tid]];
+    rs.pe[m * kBlock + tid] = acc;
+  }
+  return D - 1 - (int64_t)acc;
+}
+
+// Rank of the ket obtained from the row's ket by changing the occupations of
+// modes e[0..nch) by dn[0..nch), inside the sector of dimension Dt it lands in.
+__device__ __forceinline__ int64_t rank_changed(const Tables& t, const View& v, const RowScratch& rs, int nch,
+                                                const int* e, const int* dn, int64_t Dt) {
+  const int M = t.M, tid = threadIdx.x, twoM = 2 * M;
+  int top = 0;
+  for (int c = 0; c < nch; ++c) top = max(top, e[c]);
+  if (top > M - 1) top = M - 1;
+  int64_t sum = rs.pe[(M - 1) * kBlock + tid] - rs.pe[top * kBlock + tid];
+  int dc = 0, dk = 0;
+  for (int m = top; m >= 1; --m) {
+    for (int c = 0; c < nch; ++c)
+      if (e[c] == m) {
+        dc += dn[c];
+        dk += dn[c] * m;
+      }
+    int dkm = ((dk % M) + M) % M;
+    sum += v.E[rs.idx[m * kBlock + tid] + dc * twoM + dkm];
+  }
+  return Dt - 1 - sum;
+}
+
+// ------------------------------------------------ double-float RK4 stages
+//
+// GB300's FP64 pipe runs at about 1/74 of the FP32 rate, so the gather-heavy
+// stages accumulate in double-float arithmetic: a value is the unevaluated sum
+// hi + lo of two fp32 numbers (about 48 significant bits).  Products use the
+// exact fma-based error term, sums the branch-free TwoSum; the intrinsics
+// __fmul_rn / __fadd_rn keep the compiler from contracting them.  The state
+// psi itself stays FP64: the last stage of each step forms psi + z H v in FP64.
+
+struct dfl {
+  float h, l;
+};
+
+__device__ __forceinline__ dfl df_of(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(dfl a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.h, -a.l}; }
+
+// a * b, unnormalised (|l| is a few ulp of h)
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return {p, e};
+}
+
+// acc += c * x; acc.h carries the TwoSum, acc.l gathers every rounding error
+__device__ __forceinline__ void df_fma(dfl& acc, dfl c, dfl x) {
+  const float p = __fmul_rn(c.h, x.h);
+  float e = fmaf(c.h, x.h, -p);
+  e = fmaf(c.h, x.l, e);
+  e = fmaf(c.l, x.h, e);
+  const float s = __fadd_rn(acc.h, p);
+  const float bb = __fsub_rn(s, acc.h);
+  const float err = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  acc.h = s;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(err, e));
+}
+
+// a + b, renormalised
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float bb = __fsub_rn(s, a.h);
+  float err = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+  err = __fadd_rn(err, __fadd_rn(a.l, b.l));
+  const float h = __fadd_rn(s, err);
+  return {h, __fsub_rn(err, __fsub_rn(h, s))};
+}
+
+// Fast two-sum renormalisation of a pair whose |l| may have grown to a few ulp of h
+__device__ __forceinline__ dfl df_renorm(dfl a) {
+  const float h = __fadd_rn(a.h, a.l);
+  return {h, __fsub_rn(a.l, __fsub_rn(h, a.h))};
+}
+
+struct DfArgs {
+  const float4* vin;   // gathered stage vector(s), double-float [B][total]
+  const float4* psif;  // double-float copy of psi [B][total]
+  double2* psi;        // psi (FP64) [B][total]; updated in the final stage
+  float4* out;         // stage output, double-float [B][total] (final stage: new copy of psi)
+  const float4* diag;  // per ket (w.hi, w.lo, L.hi, L.lo)
+  float2 scale[8];     // two-body scale per member, double-float
+  double zre;          // dt / d: out = psi + (dt/d) (Im Hv, -Re Hv)
+  float2 zf;           // dt / d as double-float
+  int* status;
+};
+
+// Shared scratch of the double-float stage kernel, after the table image:
+//   sidx  int32 [M][kBlock]  flat E index of each row's suffix state at mode m,
+//                            minus kDeltaBias (so a stored shift byte adds directly)
+//   socc  uint8 [M][kBlock]  occupations
+//   sD    int32 [kBlock]     sector dimension of the row (-1: no row)
+//   sOff  int64 [kBlock]     sector offset of the row
+//   sperm int32 [kBlock]     processing order (rows sorted by work, most first)
+//   hist  int32 [2][n_ann+2] counting-sort buckets and cursors
+__host__ __device__ inline size_t df_scratch_bytes(int M, int n_ann) {
+  size_t b = (size_t)M * kBlock * 4 + (((size_t)M * kBlock + 15) & ~(size_t)15);
+  b += (size_t)kBlock * 4 + (size_t)kBlock * 8 + (size_t)kBlock * 4 + 2 * (size_t)(n_ann + 2) * 4;
+  return (b + 15) & ~(size_t)15;
+}
+
+template <typename K>
+static int persistent_grid(K kernel, size_t smem, int64_t rows, int* grid) {
+  int dev = 0, sms = 0, per = 0;
+  QB_CUDA(cudaGetDevice(&dev));
+  QB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  QB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  QB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kBlock, smem));
+  if (per < 1) return fail(QB_EUNSUPPORTED, "kernel does not fit on an SM with this table size");
+  int64_t want = (rows + kBlock - 1) / kBlock;
+  int64_t g = std::min<int64_t>((int64_t)sms * std::min(per, 16), std::max<int64_t>(1, want));
+  *grid = (int)g;
+  return QB_OK;
+}
+
+}  // namespace qb

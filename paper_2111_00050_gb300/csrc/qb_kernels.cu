@@ -15,147 +15,10 @@
 
 #include "qb_internal.h"
 
+#include "qb_device.cuh"
+#include "qb_stage.cuh"
+
 namespace qb {
-
-#define QB_CUDA(x)                                                                            \
-  do {                                                                                        \
-    cudaError_t e_ = (x);                                                                     \
-    if (e_ != cudaSuccess) return fail(QB_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
-  } while (0)
-
-constexpr int kBlock = 128;  // threads per CTA of the row kernels (one row per thread per pass)
-constexpr int kMaxM = QB_MAX_MODES;
-
-// ----------------------------------------------------------------- smem view
-
-struct View {
-  const uint32_t* cnt;
-  const int32_t* E;
-  const double* sq;
-  const uint32_t* pq;
-  const double* G;
-  const int8_t* delta;
-  const int32_t* ann;
-  const uint8_t* pairidx;
-  const double* w;
-  const double* gd;
-};
-
-__device__ __forceinline__ View make_view(const Tables& t, const unsigned char* s) {
-  View v;
-  v.cnt = (const uint32_t*)(s + t.o_cnt);
-  v.E = (const int32_t*)(s + t.o_E);
-  v.sq = (const double*)(s + t.o_sqrt);
-  v.pq = (const uint32_t*)(s + t.o_pq);
-  v.G = (const double*)(s + t.o_G);
-  v.delta = (const int8_t*)(s + t.o_delta);
-  v.ann = (const int32_t*)(s + t.o_ann);
-  v.pairidx = (const uint8_t*)(s + t.o_pairidx);
-  v.w = (const double*)(s + t.o_w);
-  v.gd = (const double*)(s + t.o_gd);
-  return v;
-}
-
-// Copies the table image into shared memory (16-byte vector copies).
-__device__ __forceinline__ void load_blob(const Tables& t, unsigned char* smem) {
-  const int4* src = reinterpret_cast<const int4*>(t.blob);
-  int4* dst = reinterpret_cast<int4*>(smem);
-  for (int i = threadIdx.x; i < t.blob_bytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
-  __syncthreads();
-}
-
-// Per-thread scratch rows in shared memory, laid out [m][thread] so that the
-// lanes of a warp touching the same mode hit consecutive words.
-struct RowScratch {
-  uint8_t* occ;  // [kMaxM][kBlock]
-  int32_t* idx;  // [kMaxM][kBlock] flat E index of the suffix state at mode m
-  int32_t* pe;   // [kMaxM][kBlock] prefix sums of E over the row's own suffix states
-};
-
-__device__ __forceinline__ RowScratch row_scratch(unsigned char* base) {
-  RowScratch r;
-  r.idx = reinterpret_cast<int32_t*>(base);
-  r.pe = r.idx + kMaxM * kBlock;
-  r.occ = reinterpret_cast<uint8_t*>(r.pe + kMaxM * kBlock);
-  return r;
-}
-constexpr int kRowScratchBytes = kMaxM * kBlock * (4 + 4 + 1);
-
-__device__ __forceinline__ int find_sector(const Tables& t, int64_t g) {
-  int lo = 0, hi = t.n_sectors - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (__ldg(t.sec_off + mid) <= g)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
-
-// Unranks local index i of sector (N, K) into the occupation vector and fills
-// the suffix-state indices and their prefix sums.  Returns rank(n) recomputed
-// from the suffix states (equals i for a consistent table).
-__device__ __forceinline__ int64_t setup_row(const Tables& t, const View& v, const RowScratch& rs, int N, int K,
-                                             int64_t D, int64_t i) {
-  const int M = t.M, tid = threadIdx.x, V = t.nmax + 1;
-  int rem = N, kr = K;
-  int64_t left = i;
-  for (int m = 0; m < M - 1; ++m) {
-    int val = 0, kk = kr;
-    const uint32_t* row = v.cnt + (size_t)(m + 1) * V * M;
-    while (true) {
-      uint32_t c = row[(rem - val) * M + kk];
-      if (left < (int64_t)c || val == rem) break;
-      left -= c;
-      ++val;
-      kk -= m;
-      if (kk < 0) kk += M;
-    }
-    rs.occ[m * kBlock + tid] = (uint8_t)val;
-    rem -= val;
-    kr = kk;
-  }
-  rs.occ[(M - 1) * kBlock + tid] = (uint8_t)rem;
-  // suffix states, from the top mode down
-  const int twoM = 2 * M;
-  int srem = 0, skr = 0;
-  for (int m = M - 1; m >= 1; --m) {
-    int nm = rs.occ[m * kBlock + tid];
-    srem += nm;
-    skr = (skr + m * nm) % M;
-    rs.idx[m * kBlock + tid] = (m * t.rem_w + srem + 2) * twoM + skr;
-  }
-  int32_t acc = 0;
-  rs.pe[tid] = 0;
-  for (int m = 1; m < M; ++m) {
-    acc += v.E[rs.idx[m * kBlock + tid]];
-    rs.pe[m * kBlock + tid] = acc;
-  }
-  return D - 1 - (int64_t)acc;
-}
-
-// Rank of the ket obtained from the row's ket by changing the occupations of
-// modes e[0..nch) by dn[0..nch), inside the sector of dimension Dt it lands in.
-__device__ __forceinline__ int64_t rank_changed(const Tables& t, const View& v, const RowScratch& rs, int nch,
-                                                const int* e, const int* dn, int64_t Dt) {
-  const int M = t.M, tid = threadIdx.x, twoM = 2 * M;
-  int top = 0;
-  for (int c = 0; c < nch; ++c) top = max(top, e[c]);
-  if (top > M - 1) top = M - 1;
-  int64_t sum = rs.pe[(M - 1) * kBlock + tid] - rs.pe[top * kBlock + tid];
-  int dc = 0, dk = 0;
-  for (int m = top; m >= 1; --m) {
-    for (int c = 0; c < nch; ++c)
-      if (e[c] == m) {
-        dc += dn[c];
-        dk += dn[c] * m;
-      }
-    int dkm = ((dk % M) + M) % M;
-    sum += v.E[rs.idx[m * kBlock + tid] + dc * twoM + dkm];
-  }
-  return Dt - 1 - sum;
-}
 
 // ------------------------------------------------------------ H psi kernels
 
@@ -308,279 +171,6 @@ __global__ void __launch_bounds__(kBlock) hpsi_kernel(const Tables t, const Stag
   }
 }
 
-
-// ------------------------------------------------ double-float RK4 stages
-//
-// GB300's FP64 pipe runs at about 1/74 of the FP32 rate, so the gather-heavy
-// stages accumulate in double-float arithmetic: a value is the unevaluated sum
-// hi + lo of two fp32 numbers (about 48 significant bits).  Products use the
-// exact fma-based error term, sums the branch-free TwoSum; the intrinsics
-// __fmul_rn / __fadd_rn keep the compiler from contracting them.  The state
-// psi itself stays FP64: the last stage of each step forms psi + z H v in FP64.
-
-struct dfl {
-  float h, l;
-};
-
-__device__ __forceinline__ dfl df_of(double x) {
-  const float h = __double2float_rn(x);
-  return {h, __double2float_rn(x - (double)h)};
-}
-__device__ __forceinline__ double df_to(dfl a) { return (double)a.h + (double)a.l; }
-__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.h, -a.l}; }
-
-// a * b, unnormalised (|l| is a few ulp of h)
-__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
-  const float p = __fmul_rn(a.h, b.h);
-  float e = fmaf(a.h, b.h, -p);
-  e = fmaf(a.h, b.l, e);
-  e = fmaf(a.l, b.h, e);
-  return {p, e};
-}
-
-// acc += c * x; acc.h carries the TwoSum, acc.l gathers every rounding error
-__device__ __forceinline__ void df_fma(dfl& acc, dfl c, dfl x) {
-  const float p = __fmul_rn(c.h, x.h);
-  float e = fmaf(c.h, x.h, -p);
-  e = fmaf(c.h, x.l, e);
-  e = fmaf(c.l, x.h, e);
-  const float s = __fadd_rn(acc.h, p);
-  const float bb = __fsub_rn(s, acc.h);
-  const float err = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  acc.h = s;
-  acc.l = __fadd_rn(acc.l, __fadd_rn(err, e));
-}
-
-// a + b, renormalised
-__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
-  const float s = __fadd_rn(a.h, b.h);
-  const float bb = __fsub_rn(s, a.h);
-  float err = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
-  err = __fadd_rn(err, __fadd_rn(a.l, b.l));
-  const float h = __fadd_rn(s, err);
-  return {h, __fsub_rn(err, __fsub_rn(h, s))};
-}
-
-struct DfArgs {
-  const float4* vin;   // gathered stage vector(s), double-float [B][total]
-  const float4* psif;  // double-float copy of psi [B][total]
-  double2* psi;        // psi (FP64) [B][total]; updated in the final stage
-  float4* out;         // stage output, double-float [B][total] (final stage: new copy of psi)
-  const float4* diag;  // per ket (w.hi, w.lo, L.hi, L.lo)
-  float2 scale[8];     // two-body scale per member, double-float
-  double zre;          // dt / d: out = psi + (dt/d) (Im Hv, -Re Hv)
-  float2 zf;           // dt / d as double-float
-  int* status;
-};
-
-// Shared scratch of the double-float stage kernel, after the table image:
-//   sidx  int32 [M][kBlock]  flat E index of each row's suffix state at mode m,
-//                            minus kDeltaBias (so a stored shift byte adds directly)
-//   socc  uint8 [M][kBlock]  occupations
-//   sD    int32 [kBlock]     sector dimension of the row (-1: no row)
-//   sOff  int64 [kBlock]     sector offset of the row
-//   sperm int32 [kBlock]     processing order (rows sorted by work, most first)
-//   hist  int32 [2][n_ann+2] counting-sort buckets and cursors
-__host__ __device__ inline size_t df_scratch_bytes(int M, int n_ann) {
-  size_t b = (size_t)M * kBlock * 4 + (((size_t)M * kBlock + 15) & ~(size_t)15);
-  b += (size_t)kBlock * 4 + (size_t)kBlock * 8 + (size_t)kBlock * 4 + 2 * (size_t)(n_ann + 2) * 4;
-  return (b + 15) & ~(size_t)15;
-}
-
-template <int B, bool CPLX>
-__global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const DfArgs a, const int final_stage) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  load_blob(t, smem);
-  const View v = make_view(t, smem);
-  const float2* sqf = reinterpret_cast<const float2*>(smem + t.o_sqf);
-  const float4* Gf = reinterpret_cast<const float4*>(smem + t.o_Gf);
-  const uint4* dl4 = reinterpret_cast<const uint4*>(v.delta);
-  const int M = t.M, V = t.nmax + 1, twoM = 2 * M;
-  unsigned char* sp = smem + ((t.blob_bytes + 15) & ~15);
-  int32_t* sidx = reinterpret_cast<int32_t*>(sp);
-  uint8_t* socc = reinterpret_cast<uint8_t*>(sidx + M * kBlock);
-  int32_t* sD = reinterpret_cast<int32_t*>(socc + ((M * kBlock + 15) & ~15));
-  int64_t* sOff = reinterpret_cast<int64_t*>(sD + kBlock);
-  int32_t* sperm = reinterpret_cast<int32_t*>(sOff + kBlock);
-  int32_t* hist = sperm + kBlock;
-  int32_t* cursor = hist + (t.n_ann + 2);
-  const int tid = threadIdx.x;
-  const int64_t total = t.total;
-  const int nb = t.n_ann + 2;
-
-  for (int64_t base = (int64_t)blockIdx.x * kBlock; base < total; base += (int64_t)gridDim.x * kBlock) {
-    // ---- phase 1: own row -> occupations, suffix-state indices, work key
-    const int64_t g = base + tid;
-    int key = 0;
-    for (int k = tid; k < 2 * nb; k += kBlock) hist[k] = 0;
-    if (g < total) {
-      const int sid = find_sector(t, g);
-      const int64_t off = __ldg(t.sec_off + sid);
-      const int D = (int)(__ldg(t.sec_off + sid + 1) - off);
-      int rem = __ldg(t.sec_N + sid), kr = __ldg(t.sec_K + sid);
-      int64_t left = g - off;
-      for (int m = 0; m < M - 1; ++m) {
-        int val = 0, kk = kr;
-        const uint32_t* row = v.cnt + (size_t)(m + 1) * V * M;
-        while (true) {
-          const uint32_t c = row[(rem - val) * M + kk];
-          if (left < (int64_t)c || val == rem) break;
-          left -= c;
-          ++val;
-          kk -= m;
-          if (kk < 0) kk += M;
-        }
-        socc[m * kBlock + tid] = (uint8_t)val;
-        rem -= val;
-        kr = kk;
-      }
-      socc[(M - 1) * kBlock + tid] = (uint8_t)rem;
-      int srem = 0, skr = 0, esum = 0, np = 0, n2 = 0;
-      for (int m = M - 1; m >= 1; --m) {
-        const int nm = socc[m * kBlock + tid];
-        srem += nm;
-        skr = (skr + m * nm) % M;
-        const int ix = (m * t.rem_w + srem + 2) * twoM + skr;
-        esum += v.E[ix];
-        sidx[m * kBlock + tid] = ix - kDeltaBias;
-      }
-      if (D - 1 - esum != (int)(g - off)) atomicOr(a.status, 2);
-      for (int m = 0; m < M; ++m) {
-        const int nm = socc[m * kBlock + tid];
-        np += nm >= 1;
-        n2 += nm >= 2;
-      }
-      key = np * (np - 1) / 2 + n2;  // number of annihilation pairs r <= s acting on the row
-      sD[tid] = D;
-      sOff[tid] = off;
-    } else {
-      sD[tid] = -1;
-    }
-    // ---- phase 2: counting sort of the rows by work, largest first
-    __syncthreads();
-    atomicAdd(&hist[key], 1);
-    __syncthreads();
-    if (tid == 0) {
-      int run = 0;
-      for (int k = nb - 1; k >= 0; --k) {
-        cursor[k] = run;
-        run += hist[k];
-      }
-    }
-    __syncthreads();
-    sperm[atomicAdd(&cursor[key], 1)] = tid;
-    __syncthreads();
-
-    // ---- phase 3: the terms of row `row`
-    const int row = sperm[tid];
-    const int D = sD[row];
-    if (D >= 0) {
-      const int64_t off = sOff[row];
-      const int64_t gr = base + row;
-      const uint8_t* occ = socc + row;
-      int id[16];
-#pragma unroll
-      for (int m = 1; m < 16; ++m)
-        if (m < M) id[m] = sidx[m * kBlock + row];
-      uint32_t occmask = 0, twomask = 0;
-      for (int m = 0; m < M; ++m) {
-        const int nm = occ[m * kBlock];
-        occmask |= (nm >= 1 ? 1u : 0u) << m;
-        twomask |= (nm >= 2 ? 1u : 0u) << m;
-      }
-      const float4* vsec = a.vin + off;
-      dfl acc_r[B], acc_i[B];
-#pragma unroll
-      for (int b = 0; b < B; ++b) acc_r[b] = acc_i[b] = dfl{0.f, 0.f};
-
-      uint32_t rm = occmask, smask = 0;
-      int r = 0;
-      while (true) {
-        if (smask == 0) {
-          if (rm == 0) break;
-          r = __ffs(rm) - 1;
-          rm &= rm - 1;
-          smask = occmask & (~0u << r);
-          if (!((twomask >> r) & 1u)) smask &= ~(1u << r);
-          if (smask == 0) continue;
-        }
-        const int s = __ffs(smask) - 1;
-        smask &= smask - 1;
-        const int ai = v.pairidx[r * 16 + s];
-        const int nr = occ[r * kBlock], ns = occ[s * kBlock];
-        const float2 sa = sqf[nr], sb = sqf[ns - (r == s ? 1 : 0)];
-        const dfl A = df_mul(dfl{sa.x, sa.y}, dfl{sb.x, sb.y});
-        dfl pr[B], pim[B];
-#pragma unroll
-        for (int b = 0; b < B; ++b) pr[b] = pim[b] = dfl{0.f, 0.f};
-        const int j1 = v.ann[ai + 1];
-        for (int j = v.ann[ai]; j < j1; ++j) {
-          const uint32_t w4 = v.pq[j];
-          const int p = w4 & 0xff, q = (w4 >> 8) & 0xff;
-          const float2 bp = sqf[occ[p * kBlock] + 1], bq = sqf[occ[q * kBlock] + 1 + (p == q ? 1 : 0)];
-          const dfl Bv = df_mul(dfl{bp.x, bp.y}, dfl{bq.x, bq.y});
-          // rank of the target: D - 1 - sum over every mode of E at the shifted suffix state
-          const uint4 dd = dl4[j];
-          int esum = 0;
-#pragma unroll
-          for (int m = 1; m < 16; ++m) {
-            if (m >= M) break;
-            const uint32_t word = (m < 4) ? dd.x : (m < 8) ? dd.y : (m < 12) ? dd.z : dd.w;
-            esum += v.E[id[m] + (int)((word >> (8 * (m & 3))) & 0xffu)];
-          }
-          int rk = D - 1 - esum;
-          if ((unsigned)rk >= (unsigned)D) {
-            atomicOr(a.status, 1);
-            rk = 0;
-          }
-          const float4 gf = Gf[j];
-          const dfl cr = df_mul(dfl{gf.x, gf.y}, Bv);
-#pragma unroll
-          for (int b = 0; b < B; ++b) {
-            const float4 x = __ldg(vsec + (size_t)b * total + rk);
-            df_fma(pr[b], cr, dfl{x.x, x.y});
-            df_fma(pim[b], cr, dfl{x.z, x.w});
-            if (CPLX) {
-              const dfl ci = df_mul(dfl{gf.z, gf.w}, Bv);
-              df_fma(pr[b], df_neg(ci), dfl{x.z, x.w});
-              df_fma(pim[b], ci, dfl{x.x, x.y});
-            }
-          }
-        }
-#pragma unroll
-        for (int b = 0; b < B; ++b) {
-          acc_r[b] = df_add(acc_r[b], df_mul(A, df_add(pr[b], dfl{0.f, 0.f})));
-          acc_i[b] = df_add(acc_i[b], df_mul(A, df_add(pim[b], dfl{0.f, 0.f})));
-        }
-      }
-
-      const float4 dg4 = a.diag[gr];
-#pragma unroll
-      for (int b = 0; b < B; ++b) {
-        const dfl sc{a.scale[b].x, a.scale[b].y};
-        const dfl dg = df_add(dfl{dg4.x, dg4.y}, df_mul(sc, dfl{dg4.z, dg4.w}));
-        const float4 xo = a.vin[(size_t)b * total + gr];
-        const dfl hr = df_add(df_mul(dg, dfl{xo.x, xo.y}), df_mul(sc, acc_r[b]));
-        const dfl hi = df_add(df_mul(dg, dfl{xo.z, xo.w}), df_mul(sc, acc_i[b]));
-        if (!final_stage) {
-          const float4 p0 = a.psif[(size_t)b * total + gr];
-          const dfl zf{a.zf.x, a.zf.y};
-          const dfl orr = df_add(dfl{p0.x, p0.y}, df_mul(zf, hi));
-          const dfl oi = df_add(dfl{p0.z, p0.w}, df_neg(df_mul(zf, hr)));
-          a.out[(size_t)b * total + gr] = make_float4(orr.h, orr.l, oi.h, oi.l);
-        } else {
-          const double2 p0 = a.psi[(size_t)b * total + gr];
-          const double nr = p0.x + a.zre * df_to(hi);
-          const double ni = p0.y - a.zre * df_to(hr);
-          a.psi[(size_t)b * total + gr] = make_double2(nr, ni);
-          const dfl fr = df_of(nr), fi = df_of(ni);
-          a.out[(size_t)b * total + gr] = make_float4(fr.h, fr.l, fi.h, fi.l);
-        }
-      }
-    }
-    __syncthreads();  // scratch is rewritten by the next tile
-  }
-}
 
 // psi (FP64) -> double-float copy
 __global__ void to_df_kernel(const double2* psi, float4* out, int64_t n) {
@@ -937,20 +527,6 @@ static int nmoments(int M) { return 4 + 2 * M + 4 * M * M; }
 // grid of a persistent row kernel, capped by the scratch sizing
 
 
-template <typename K>
-static int persistent_grid(K kernel, size_t smem, int64_t rows, int* grid) {
-  int dev = 0, sms = 0, per = 0;
-  QB_CUDA(cudaGetDevice(&dev));
-  QB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  QB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  QB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kBlock, smem));
-  if (per < 1) return fail(QB_EUNSUPPORTED, "kernel does not fit on an SM with this table size");
-  int64_t want = (rows + kBlock - 1) / kBlock;
-  int64_t g = std::min<int64_t>((int64_t)sms * std::min(per, 16), std::max<int64_t>(1, want));
-  *grid = (int)g;
-  return QB_OK;
-}
-
 static int check_status(const Space& s, cudaStream_t st) {
   int h = 0;
   int* d = reinterpret_cast<int*>(s.d_scratch);  // status word lives at the head of the scratch area
@@ -1056,27 +632,17 @@ int launch_hpsi(const Space& s, const void* d_v, void* d_out, void* stream) {
   return check_status(s, st);
 }
 
-static size_t df_smem(const Tables& t) { return ((t.blob_bytes + 15) & ~15) + df_scratch_bytes(t.M, t.n_ann); }
-
-template <int B, bool CPLX>
-static int df_grid(const Space& s, int* grid) {
-  return persistent_grid(stage_df_kernel<B, CPLX>, df_smem(s.t), s.t.total, grid);
-}
-
-template <int B, bool CPLX>
+template <int B>
 static int rk4_loop(Space& s, double2* psi, const double* scale, double dt, int64_t steps, float4* w1, float4* w2,
                     float4* psif, cudaStream_t st) {
   const int64_t n = (int64_t)B * s.t.total;
-  int grid = 0;
-  int rc = df_grid<B, CPLX>(s, &grid);
-  if (rc) return rc;
-  const size_t smem = df_smem(s.t);
+  const bool cplx = s.t.is_complex != 0;
   to_df_kernel<<<1216, 256, 0, st>>>(psi, psif, n);
   QB_CUDA(cudaGetLastError());
   DfArgs a{};
   for (int b = 0; b < B; ++b) {
-    const dfl x = {(float)scale[b], (float)(scale[b] - (double)(float)scale[b])};
-    a.scale[b] = make_float2(x.h, x.l);
+    const float h = (float)scale[b];
+    a.scale[b] = make_float2(h, (float)(scale[b] - (double)h));
   }
   a.diag = s.d_diag;
   a.psi = psi;
@@ -1092,8 +658,8 @@ static int rk4_loop(Space& s, double2* psi, const double* scale, double dt, int6
       a.zre = dt / d;
       const float zh = (float)a.zre;
       a.zf = make_float2(zh, (float)(a.zre - (double)zh));
-      stage_df_kernel<B, CPLX><<<grid, kBlock, smem, st>>>(s.t, a, d == 1 ? 1 : 0);
-      QB_CUDA(cudaGetLastError());
+      int rc = stage_launch(s.t, a, d == 1 ? 1 : 0, B, cplx, st);
+      if (rc) return rc;
     }
   }
   return QB_OK;
@@ -1107,17 +673,12 @@ int launch_rk4(Space& s, void* d_psi, int batch, const double* scale, double dt,
   float4* w1 = (float4*)d_work;
   float4* w2 = w1 + n;
   float4* psif = w2 + n;
-  const bool c = s.t.is_complex != 0;
   int rc;
   switch (batch) {
-    case 1: rc = c ? rk4_loop<1, true>(s, psi, scale, dt, steps, w1, w2, psif, st)
-                   : rk4_loop<1, false>(s, psi, scale, dt, steps, w1, w2, psif, st); break;
-    case 2: rc = c ? rk4_loop<2, true>(s, psi, scale, dt, steps, w1, w2, psif, st)
-                   : rk4_loop<2, false>(s, psi, scale, dt, steps, w1, w2, psif, st); break;
-    case 4: rc = c ? rk4_loop<4, true>(s, psi, scale, dt, steps, w1, w2, psif, st)
-                   : rk4_loop<4, false>(s, psi, scale, dt, steps, w1, w2, psif, st); break;
-    case 8: rc = c ? rk4_loop<8, true>(s, psi, scale, dt, steps, w1, w2, psif, st)
-                   : rk4_loop<8, false>(s, psi, scale, dt, steps, w1, w2, psif, st); break;
+    case 1: rc = rk4_loop<1>(s, psi, scale, dt, steps, w1, w2, psif, st); break;
+    case 2: rc = rk4_loop<2>(s, psi, scale, dt, steps, w1, w2, psif, st); break;
+    case 4: rc = rk4_loop<4>(s, psi, scale, dt, steps, w1, w2, psif, st); break;
+    case 8: rc = rk4_loop<8>(s, psi, scale, dt, steps, w1, w2, psif, st); break;
     default: return fail(QB_EINVAL, "batch must be 1, 2, 4 or 8");
   }
   if (rc) return rc;

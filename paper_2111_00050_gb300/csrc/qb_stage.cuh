@@ -1,0 +1,275 @@
+// The hot kernel: one Horner RK4 stage of every sector (and every member of a
+// batched coupling sweep) in one launch, with the matrix-free sector H psi in
+// double-float arithmetic.
+//
+//   stage d (d = 4, 3, 2):  out = psi + (-i dt/d) H v     (double-float out)
+//   stage 1:                psi = psi + (-i dt) H v       (FP64 psi, plus its
+//                                                          double-float copy)
+//
+// H is Eq. (Ham) restricted to sectors of fixed N and momentum mod M
+// (Sec. III B).  Per row (ket n) the off-diagonal terms are the disjoint pairs
+// {r, s} -> {p, q} with p + q = r + s (mod M): coefficient
+// G_{pq,rs} sqrt(n_r (n_s - [r=s])) sqrt((n_p + 1)(n_q + 1 + [p=q])), G the
+// multiplicity-summed symmetrised coupling; the diagonal is precomputed per ket.
+//
+// Work layout: a CTA takes kBlock consecutive kets.  Phase 1 unranks each ket
+// (one per thread) into occupations and suffix-state indices; phase 2
+// counting-sorts the kets by their number of acting annihilation pairs and
+// deals them round-robin to the warps, so every warp gets kets of nearly equal
+// work and no warp idles at the tile barrier; phase 3 runs the terms.
+#pragma once
+#include "qb_device.cuh"
+
+namespace qb {
+
+template <int MT, int B, bool CPLX>
+__global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const DfArgs a, const int final_stage) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  load_blob(t, smem);
+  const View v = make_view(t, smem);
+  const float2* sqf = reinterpret_cast<const float2*>(smem + t.o_sqf);
+  const float4* Gf = reinterpret_cast<const float4*>(smem + t.o_Gf);
+  const uint4* dl4 = reinterpret_cast<const uint4*>(v.delta);
+  const int M = (MT > 0) ? MT : t.M;
+  const int V = t.nmax + 1, twoM = 2 * M;
+  unsigned char* sp = smem + ((t.blob_bytes + 15) & ~15);
+  int32_t* sidx = reinterpret_cast<int32_t*>(sp);
+  uint8_t* socc = reinterpret_cast<uint8_t*>(sidx + M * kBlock);
+  int32_t* sD = reinterpret_cast<int32_t*>(socc + ((M * kBlock + 15) & ~15));
+  int64_t* sOff = reinterpret_cast<int64_t*>(sD + kBlock);
+  int32_t* sperm = reinterpret_cast<int32_t*>(sOff + kBlock);
+  int32_t* hist = sperm + kBlock;
+  int32_t* cursor = hist + (t.n_ann + 2);
+  const int tid = threadIdx.x;
+  const int64_t total = t.total;
+  const int nb = t.n_ann + 2;
+  constexpr int kWarps = kBlock / 32;
+
+  for (int64_t base = (int64_t)blockIdx.x * kBlock; base < total; base += (int64_t)gridDim.x * kBlock) {
+    // ---- phase 1: own ket -> occupations, suffix-state indices, work key
+    const int64_t g = base + tid;
+    int key = 0;
+    for (int k = tid; k < 2 * nb; k += kBlock) hist[k] = 0;
+    if (g < total) {
+      const int sid = find_sector(t, g);
+      const int64_t off = __ldg(t.sec_off + sid);
+      const int D = (int)(__ldg(t.sec_off + sid + 1) - off);
+      int rem = __ldg(t.sec_N + sid), kr = __ldg(t.sec_K + sid);
+      int64_t left = g - off;
+      for (int m = 0; m < M - 1; ++m) {
+        int val = 0, kk = kr;
+        const uint32_t* row = v.cnt + (size_t)(m + 1) * V * M;
+        while (true) {
+          const uint32_t c = row[(rem - val) * M + kk];
+          if (left < (int64_t)c || val == rem) break;
+          left -= c;
+          ++val;
+          kk -= m;
+          if (kk < 0) kk += M;
+        }
+        socc[m * kBlock + tid] = (uint8_t)val;
+        rem -= val;
+        kr = kk;
+      }
+      socc[(M - 1) * kBlock + tid] = (uint8_t)rem;
+      int srem = 0, skr = 0, esum = 0, np = 0, n2 = 0;
+      for (int m = M - 1; m >= 1; --m) {
+        const int nm = socc[m * kBlock + tid];
+        srem += nm;
+        skr += m * nm;
+        while (skr >= M) skr -= M;
+        const int ix = (m * t.rem_w + srem + 2) * twoM + skr;
+        esum += v.E[ix];
+        sidx[m * kBlock + tid] = ix - kDeltaBias;
+      }
+      if (D - 1 - esum != (int)(g - off)) atomicOr(a.status, 2);
+      for (int m = 0; m < M; ++m) {
+        const int nm = socc[m * kBlock + tid];
+        np += nm >= 1;
+        n2 += nm >= 2;
+      }
+      key = np * (np - 1) / 2 + n2;  // annihilation pairs r <= s acting on the ket
+      sD[tid] = D;
+      sOff[tid] = off;
+    } else {
+      sD[tid] = -1;
+    }
+    // ---- phase 2: counting sort by work, dealt round-robin over the warps
+    __syncthreads();
+    atomicAdd(&hist[key], 1);
+    __syncthreads();
+    if (tid == 0) {
+      int run = 0;
+      for (int k = nb - 1; k >= 0; --k) {
+        cursor[k] = run;
+        run += hist[k];
+      }
+    }
+    __syncthreads();
+    {
+      const int k = atomicAdd(&cursor[key], 1);
+      sperm[(k % kWarps) * 32 + k / kWarps] = tid;
+    }
+    __syncthreads();
+
+    // ---- phase 3: the terms of ket `row`
+    const int row = sperm[tid];
+    const int D = sD[row];
+    if (D >= 0) {
+      const int64_t off = sOff[row];
+      const int64_t gr = base + row;
+      const uint8_t* occ = socc + row;
+      int id[16];
+#pragma unroll
+      for (int m = 1; m < 16; ++m)
+        if (m < M) id[m] = sidx[m * kBlock + row];
+      uint32_t occmask = 0, twomask = 0;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        if (m >= M) break;
+        const int nm = occ[m * kBlock];
+        occmask |= (nm >= 1 ? 1u : 0u) << m;
+        twomask |= (nm >= 2 ? 1u : 0u) << m;
+      }
+      const float4* vsec = a.vin + off;
+      dfl acc_r[B], acc_i[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) acc_r[b] = acc_i[b] = dfl{0.f, 0.f};
+
+      uint32_t rm = occmask, smask = 0;
+      int r = 0;
+      while (true) {
+        if (smask == 0) {
+          if (rm == 0) break;
+          r = __ffs(rm) - 1;
+          rm &= rm - 1;
+          smask = occmask & (~0u << r);
+          if (!((twomask >> r) & 1u)) smask &= ~(1u << r);
+          if (smask == 0) continue;
+        }
+        const int s = __ffs(smask) - 1;
+        smask &= smask - 1;
+        const int ai = v.pairidx[r * 16 + s];
+        const float2 sa = sqf[occ[r * kBlock]], sb = sqf[occ[s * kBlock] - (r == s ? 1 : 0)];
+        const dfl A = df_mul(dfl{sa.x, sa.y}, dfl{sb.x, sb.y});
+        const int j1 = v.ann[ai + 1];
+        for (int j = v.ann[ai]; j < j1; ++j) {
+          const uint32_t w4 = v.pq[j];
+          const int p = w4 & 0xff, q = (w4 >> 8) & 0xff;
+          const float2 bp = sqf[occ[p * kBlock] + 1], bq = sqf[occ[q * kBlock] + 1 + (p == q ? 1 : 0)];
+          const dfl AB = df_mul(A, df_mul(dfl{bp.x, bp.y}, dfl{bq.x, bq.y}));
+          // rank of the target: D - 1 - sum over every mode of E at the shifted suffix state
+          const uint4 dd = dl4[j];
+          int esum = 0;
+#pragma unroll
+          for (int m = 1; m < 16; ++m) {
+            if (m >= M) break;
+            const uint32_t word = (m < 4) ? dd.x : (m < 8) ? dd.y : (m < 12) ? dd.z : dd.w;
+            esum += v.E[id[m] + (int)((word >> (8 * (m & 3))) & 0xffu)];
+          }
+          int rk = D - 1 - esum;
+          if ((unsigned)rk >= (unsigned)D) {
+            atomicOr(a.status, 1);
+            rk = 0;
+          }
+          const float4 gf = Gf[j];
+          const dfl cr = df_mul(dfl{gf.x, gf.y}, AB);
+#pragma unroll
+          for (int b = 0; b < B; ++b) {
+            const float4 x = __ldg(vsec + (size_t)b * total + rk);
+            df_fma(acc_r[b], cr, dfl{x.x, x.y});
+            df_fma(acc_i[b], cr, dfl{x.z, x.w});
+            if (CPLX) {
+              const dfl ci = df_mul(dfl{gf.z, gf.w}, AB);
+              df_fma(acc_r[b], df_neg(ci), dfl{x.z, x.w});
+              df_fma(acc_i[b], ci, dfl{x.x, x.y});
+            }
+          }
+        }
+        // keep |lo| below an ulp of hi between pairs
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          acc_r[b] = df_renorm(acc_r[b]);
+          acc_i[b] = df_renorm(acc_i[b]);
+        }
+      }
+
+      const float4 dg4 = a.diag[gr];
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const dfl sc{a.scale[b].x, a.scale[b].y};
+        const dfl dg = df_add(dfl{dg4.x, dg4.y}, df_mul(sc, dfl{dg4.z, dg4.w}));
+        const float4 xo = a.vin[(size_t)b * total + gr];
+        const dfl hr = df_add(df_mul(dg, dfl{xo.x, xo.y}), df_mul(sc, acc_r[b]));
+        const dfl hi = df_add(df_mul(dg, dfl{xo.z, xo.w}), df_mul(sc, acc_i[b]));
+        if (!final_stage) {
+          const float4 p0 = a.psif[(size_t)b * total + gr];
+          const dfl zf{a.zf.x, a.zf.y};
+          const dfl orr = df_add(dfl{p0.x, p0.y}, df_mul(zf, hi));
+          const dfl oi = df_add(dfl{p0.z, p0.w}, df_neg(df_mul(zf, hr)));
+          a.out[(size_t)b * total + gr] = make_float4(orr.h, orr.l, oi.h, oi.l);
+        } else {
+          const double2 p0 = a.psi[(size_t)b * total + gr];
+          const double nr = p0.x + a.zre * df_to(hi);
+          const double ni = p0.y - a.zre * df_to(hr);
+          a.psi[(size_t)b * total + gr] = make_double2(nr, ni);
+          const dfl fr = df_of(nr), fi = df_of(ni);
+          a.out[(size_t)b * total + gr] = make_float4(fr.h, fr.l, fi.h, fi.l);
+        }
+      }
+    }
+    __syncthreads();  // scratch is rewritten by the next tile
+  }
+}
+
+// Launches one stage for mode count MT (0: any M) and the runtime batch size /
+// coupling type; *grid (if non-NULL) receives the persistent grid size.
+template <int MT>
+int stage_launch_t(const Tables& t, const DfArgs& a, int final_stage, int B, bool cplx, cudaStream_t st,
+                   int* grid_out) {
+  const size_t smem = ((t.blob_bytes + 15) & ~15) + df_scratch_bytes(t.M, t.n_ann);
+  int grid = 0, rc = QB_OK;
+#define QB_STAGE_CASE(BB, CC)                                                   \
+  {                                                                             \
+    auto k = stage_df_kernel<MT, BB, CC>;                                       \
+    rc = persistent_grid(k, smem, t.total, &grid);                              \
+    if (rc) return rc;                                                          \
+    k<<<grid, kBlock, smem, st>>>(t, a, final_stage);                           \
+  }
+  if (cplx) {
+    if (B != 1) return fail(QB_EUNSUPPORTED, "batched sweeps need a real coupling");
+    QB_STAGE_CASE(1, true)
+  } else {
+    switch (B) {
+      case 1: QB_STAGE_CASE(1, false) break;
+      case 2: QB_STAGE_CASE(2, false) break;
+      case 4: QB_STAGE_CASE(4, false) break;
+      case 8: QB_STAGE_CASE(8, false) break;
+      default: return fail(QB_EINVAL, "batch must be 1, 2, 4 or 8");
+    }
+  }
+#undef QB_STAGE_CASE
+  QB_CUDA(cudaGetLastError());
+  if (grid_out) *grid_out = grid;
+  return QB_OK;
+}
+
+// one explicit specialisation per translation unit (qb_stage_m*.cu)
+int stage_launch_m5(const Tables&, const DfArgs&, int, int, bool, cudaStream_t, int*);
+int stage_launch_m7(const Tables&, const DfArgs&, int, int, bool, cudaStream_t, int*);
+int stage_launch_m9(const Tables&, const DfArgs&, int, int, bool, cudaStream_t, int*);
+int stage_launch_m11(const Tables&, const DfArgs&, int, int, bool, cudaStream_t, int*);
+int stage_launch_any(const Tables&, const DfArgs&, int, int, bool, cudaStream_t, int*);
+
+inline int stage_launch(const Tables& t, const DfArgs& a, int final_stage, int B, bool cplx, cudaStream_t st,
+                        int* grid_out = nullptr) {
+  switch (t.M) {
+    case 5: return stage_launch_m5(t, a, final_stage, B, cplx, st, grid_out);
+    case 7: return stage_launch_m7(t, a, final_stage, B, cplx, st, grid_out);
+    case 9: return stage_launch_m9(t, a, final_stage, B, cplx, st, grid_out);
+    case 11: return stage_launch_m11(t, a, final_stage, B, cplx, st, grid_out);
+    default: return stage_launch_any(t, a, final_stage, B, cplx, st, grid_out);
+  }
+}
+
+}  // namespace qb
