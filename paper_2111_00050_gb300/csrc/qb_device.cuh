@@ -222,18 +222,25 @@ struct DfArgs {
   int* status;
 };
 
-// Shared scratch of the double-float stage kernel, after the table image:
-//   sidx  int32 [M][kBlock]  flat E index of each row's suffix state at mode m,
-//                            minus kDeltaBias (so a stored shift byte adds directly)
-//   socc  uint8 [M][kBlock]  occupations
-//   sD    int32 [kBlock]     sector dimension of the row (-1: no row)
-//   sOff  int64 [kBlock]     sector offset of the row
-//   sperm int32 [kBlock]     processing order (rows sorted by work, most first)
-//   hist  int32 [2][n_ann+2] counting-sort buckets and cursors
-__host__ __device__ inline size_t df_scratch_bytes(int M, int n_ann) {
-  size_t b = (size_t)M * kBlock * 4 + (((size_t)M * kBlock + 15) & ~(size_t)15);
-  b += (size_t)kBlock * 4 + (size_t)kBlock * 8 + (size_t)kBlock * 4 + 2 * (size_t)(n_ann + 2) * 4;
+// Shared scratch of the double-float stage kernel, after the table image, per
+// warp (each warp owns a tile of kWarpRows kets):
+//   sidx  int32 [M][kWarpRows]  flat E index of each ket's suffix state at mode m,
+//                               minus kDeltaBias (so a stored shift byte adds directly)
+//   socc  uint8 [M][kWarpRows]  occupations
+//   sD    int32 [kWarpRows]     sector dimension of the ket (-1: no ket)
+//   sOff  int64 [kWarpRows]     sector offset of the ket
+//   sperm uint8 [kWarpRows]     processing order (kets sorted by work, most first)
+//   hist  int32 [2][n_ann+2]    counting-sort buckets and cursors
+constexpr int kWarpRows = 128;
+
+__host__ __device__ inline size_t df_warp_scratch_bytes(int M, int n_ann) {
+  size_t b = (size_t)M * kWarpRows * 4 + (((size_t)M * kWarpRows + 15) & ~(size_t)15);
+  b += (size_t)kWarpRows * 4 + (size_t)kWarpRows * 8 + kWarpRows + 2 * (size_t)(n_ann + 2) * 4;
   return (b + 15) & ~(size_t)15;
+}
+
+__host__ __device__ inline size_t df_scratch_bytes(int M, int n_ann) {
+  return (size_t)(kBlock / 32) * df_warp_scratch_bytes(M, n_ann);
 }
 
 template <typename K>

@@ -12,11 +12,11 @@
 // G_{pq,rs} sqrt(n_r (n_s - [r=s])) sqrt((n_p + 1)(n_q + 1 + [p=q])), G the
 // multiplicity-summed symmetrised coupling; the diagonal is precomputed per ket.
 //
-// Work layout: a CTA takes kBlock consecutive kets.  Phase 1 unranks each ket
-// (one per thread) into occupations and suffix-state indices; phase 2
-// counting-sorts the kets by their number of acting annihilation pairs and
-// deals them round-robin to the warps, so every warp gets kets of nearly equal
-// work and no warp idles at the tile barrier; phase 3 runs the terms.
+// Work layout: every warp owns tiles of kWarpRows consecutive kets and runs
+// without CTA-wide barriers.  Phase 1 unranks the tile (4 kets per lane) into
+// occupations and suffix-state indices; phase 2 counting-sorts the tile by the
+// number of annihilation pairs acting on each ket; phase 3 runs the terms in
+// four rounds, the 32 lanes of a round taking 32 kets of nearly equal work.
 #pragma once
 #include "qb_device.cuh"
 
@@ -25,109 +25,115 @@ namespace qb {
 template <int MT, int B, bool CPLX>
 __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const DfArgs a, const int final_stage) {
   extern __shared__ __align__(16) unsigned char smem[];
-  load_blob(t, smem);
+  load_blob(t, smem);  // the only CTA-wide barrier: warps run independently afterwards
   const View v = make_view(t, smem);
   const float2* sqf = reinterpret_cast<const float2*>(smem + t.o_sqf);
   const float4* Gf = reinterpret_cast<const float4*>(smem + t.o_Gf);
   const uint4* dl4 = reinterpret_cast<const uint4*>(v.delta);
   const int M = (MT > 0) ? MT : t.M;
   const int V = t.nmax + 1, twoM = 2 * M;
-  unsigned char* sp = smem + ((t.blob_bytes + 15) & ~15);
+  constexpr int kWarps = kBlock / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* sp = smem + ((t.blob_bytes + 15) & ~15) + (size_t)warp * df_warp_scratch_bytes(M, t.n_ann);
   int32_t* sidx = reinterpret_cast<int32_t*>(sp);
-  uint8_t* socc = reinterpret_cast<uint8_t*>(sidx + M * kBlock);
-  int32_t* sD = reinterpret_cast<int32_t*>(socc + ((M * kBlock + 15) & ~15));
-  int64_t* sOff = reinterpret_cast<int64_t*>(sD + kBlock);
-  int32_t* sperm = reinterpret_cast<int32_t*>(sOff + kBlock);
-  int32_t* hist = sperm + kBlock;
+  uint8_t* socc = reinterpret_cast<uint8_t*>(sidx + M * kWarpRows);
+  int32_t* sD = reinterpret_cast<int32_t*>(socc + ((M * kWarpRows + 15) & ~15));
+  int64_t* sOff = reinterpret_cast<int64_t*>(sD + kWarpRows);
+  uint8_t* sperm = reinterpret_cast<uint8_t*>(sOff + kWarpRows);
+  int32_t* hist = reinterpret_cast<int32_t*>(sperm + kWarpRows);
   int32_t* cursor = hist + (t.n_ann + 2);
-  const int tid = threadIdx.x;
   const int64_t total = t.total;
   const int nb = t.n_ann + 2;
-  constexpr int kWarps = kBlock / 32;
 
-  for (int64_t base = (int64_t)blockIdx.x * kBlock; base < total; base += (int64_t)gridDim.x * kBlock) {
-    // ---- phase 1: own ket -> occupations, suffix-state indices, work key
-    const int64_t g = base + tid;
-    int key = 0;
-    for (int k = tid; k < 2 * nb; k += kBlock) hist[k] = 0;
-    if (g < total) {
-      const int sid = find_sector(t, g);
-      const int64_t off = __ldg(t.sec_off + sid);
-      const int D = (int)(__ldg(t.sec_off + sid + 1) - off);
-      int rem = __ldg(t.sec_N + sid), kr = __ldg(t.sec_K + sid);
-      int64_t left = g - off;
-      for (int m = 0; m < M - 1; ++m) {
-        int val = 0, kk = kr;
-        const uint32_t* row = v.cnt + (size_t)(m + 1) * V * M;
-        while (true) {
-          const uint32_t c = row[(rem - val) * M + kk];
-          if (left < (int64_t)c || val == rem) break;
-          left -= c;
-          ++val;
-          kk -= m;
-          if (kk < 0) kk += M;
+  for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * kWarpRows; base < total;
+       base += (int64_t)gridDim.x * kWarps * kWarpRows) {
+    // ---- phase 1: each lane unranks 4 kets into occupations and suffix-state indices
+    for (int k = lane; k < 2 * nb; k += 32) hist[k] = 0;
+    int key[kWarpRows / 32];
+#pragma unroll
+    for (int u = 0; u < kWarpRows / 32; ++u) {
+      const int row = u * 32 + lane;
+      const int64_t g = base + row;
+      key[u] = 0;
+      if (g < total) {
+        const int sid = find_sector(t, g);
+        const int64_t off = __ldg(t.sec_off + sid);
+        const int D = (int)(__ldg(t.sec_off + sid + 1) - off);
+        int rem = __ldg(t.sec_N + sid), kr = __ldg(t.sec_K + sid);
+        int left = (int)(g - off);
+        for (int m = 0; m < M - 1; ++m) {
+          int val = 0, kk = kr;
+          const uint32_t* crow = v.cnt + (size_t)(m + 1) * V * M;
+          while (true) {
+            const int c = (int)crow[(rem - val) * M + kk];
+            if (left < c || val == rem) break;
+            left -= c;
+            ++val;
+            kk -= m;
+            if (kk < 0) kk += M;
+          }
+          socc[m * kWarpRows + row] = (uint8_t)val;
+          rem -= val;
+          kr = kk;
         }
-        socc[m * kBlock + tid] = (uint8_t)val;
-        rem -= val;
-        kr = kk;
+        socc[(M - 1) * kWarpRows + row] = (uint8_t)rem;
+        int srem = 0, skr = 0, esum = 0, np = 0, n2 = 0;
+        for (int m = M - 1; m >= 1; --m) {
+          const int nm = socc[m * kWarpRows + row];
+          srem += nm;
+          skr += m * nm;
+          while (skr >= M) skr -= M;
+          const int ix = (m * t.rem_w + srem + 2) * twoM + skr;
+          esum += v.E[ix];
+          sidx[m * kWarpRows + row] = ix - kDeltaBias;
+        }
+        if (D - 1 - esum != (int)(g - off)) atomicOr(a.status, 2);
+        for (int m = 0; m < M; ++m) {
+          const int nm = socc[m * kWarpRows + row];
+          np += nm >= 1;
+          n2 += nm >= 2;
+        }
+        key[u] = np * (np - 1) / 2 + n2;  // annihilation pairs r <= s acting on the ket
+        sD[row] = D;
+        sOff[row] = off;
+      } else {
+        sD[row] = -1;
       }
-      socc[(M - 1) * kBlock + tid] = (uint8_t)rem;
-      int srem = 0, skr = 0, esum = 0, np = 0, n2 = 0;
-      for (int m = M - 1; m >= 1; --m) {
-        const int nm = socc[m * kBlock + tid];
-        srem += nm;
-        skr += m * nm;
-        while (skr >= M) skr -= M;
-        const int ix = (m * t.rem_w + srem + 2) * twoM + skr;
-        esum += v.E[ix];
-        sidx[m * kBlock + tid] = ix - kDeltaBias;
-      }
-      if (D - 1 - esum != (int)(g - off)) atomicOr(a.status, 2);
-      for (int m = 0; m < M; ++m) {
-        const int nm = socc[m * kBlock + tid];
-        np += nm >= 1;
-        n2 += nm >= 2;
-      }
-      key = np * (np - 1) / 2 + n2;  // annihilation pairs r <= s acting on the ket
-      sD[tid] = D;
-      sOff[tid] = off;
-    } else {
-      sD[tid] = -1;
     }
-    // ---- phase 2: counting sort by work, dealt round-robin over the warps
-    __syncthreads();
-    atomicAdd(&hist[key], 1);
-    __syncthreads();
-    if (tid == 0) {
+    // ---- phase 2: warp-local counting sort of the tile by work, largest first
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < kWarpRows / 32; ++u) atomicAdd(&hist[key[u]], 1);
+    __syncwarp();
+    if (lane == 0) {
       int run = 0;
       for (int k = nb - 1; k >= 0; --k) {
         cursor[k] = run;
         run += hist[k];
       }
     }
-    __syncthreads();
-    {
-      const int k = atomicAdd(&cursor[key], 1);
-      sperm[(k % kWarps) * 32 + k / kWarps] = tid;
-    }
-    __syncthreads();
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < kWarpRows / 32; ++u) sperm[atomicAdd(&cursor[key[u]], 1)] = (uint8_t)(u * 32 + lane);
+    __syncwarp();
 
-    // ---- phase 3: the terms of ket `row`
-    const int row = sperm[tid];
-    const int D = sD[row];
-    if (D >= 0) {
+    // ---- phase 3: four rounds; in each the 32 lanes take 32 kets of similar work
+    for (int round = 0; round < kWarpRows / 32; ++round) {
+      const int row = sperm[round * 32 + lane];
+      const int D = sD[row];
+      if (D < 0) continue;
       const int64_t off = sOff[row];
       const int64_t gr = base + row;
       const uint8_t* occ = socc + row;
       int id[16];
 #pragma unroll
       for (int m = 1; m < 16; ++m)
-        if (m < M) id[m] = sidx[m * kBlock + row];
+        if (m < M) id[m] = sidx[m * kWarpRows + row];
       uint32_t occmask = 0, twomask = 0;
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
         if (m >= M) break;
-        const int nm = occ[m * kBlock];
+        const int nm = occ[m * kWarpRows];
         occmask |= (nm >= 1 ? 1u : 0u) << m;
         twomask |= (nm >= 2 ? 1u : 0u) << m;
       }
@@ -150,13 +156,13 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
         const int s = __ffs(smask) - 1;
         smask &= smask - 1;
         const int ai = v.pairidx[r * 16 + s];
-        const float2 sa = sqf[occ[r * kBlock]], sb = sqf[occ[s * kBlock] - (r == s ? 1 : 0)];
+        const float2 sa = sqf[occ[r * kWarpRows]], sb = sqf[occ[s * kWarpRows] - (r == s ? 1 : 0)];
         const dfl A = df_mul(dfl{sa.x, sa.y}, dfl{sb.x, sb.y});
         const int j1 = v.ann[ai + 1];
         for (int j = v.ann[ai]; j < j1; ++j) {
           const uint32_t w4 = v.pq[j];
           const int p = w4 & 0xff, q = (w4 >> 8) & 0xff;
-          const float2 bp = sqf[occ[p * kBlock] + 1], bq = sqf[occ[q * kBlock] + 1 + (p == q ? 1 : 0)];
+          const float2 bp = sqf[occ[p * kWarpRows] + 1], bq = sqf[occ[q * kWarpRows] + 1 + (p == q ? 1 : 0)];
           const dfl AB = df_mul(A, df_mul(dfl{bp.x, bp.y}, dfl{bq.x, bq.y}));
           // rank of the target: D - 1 - sum over every mode of E at the shifted suffix state
           const uint4 dd = dl4[j];
@@ -218,7 +224,7 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
         }
       }
     }
-    __syncthreads();  // scratch is rewritten by the next tile
+    __syncwarp();  // the tile's scratch is rewritten by the next tile
   }
 }
 
