@@ -59,6 +59,15 @@ __device__ __forceinline__ void load_blob(const Tables& t, unsigned char* smem) 
   __syncthreads();
 }
 
+// Copies the table image from byte offset `from` on (16-byte aligned) into
+// shared memory; the stage kernels leave the fill counts in global memory.
+__device__ __forceinline__ void load_blob_from(const Tables& t, unsigned char* smem, int from) {
+  const int4* src = reinterpret_cast<const int4*>(t.blob + from);
+  int4* dst = reinterpret_cast<int4*>(smem);
+  for (int i = threadIdx.x; i < (t.blob_bytes - from) / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+  __syncthreads();
+}
+
 // Per-thread scratch rows in shared memory, laid out [m][thread] so that the
 // lanes of a warp touching the same mode hit consecutive words.
 struct RowScratch {
@@ -231,7 +240,7 @@ struct DfArgs {
 //   sOff  int64 [kWarpRows]     sector offset of the ket
 //   sperm uint8 [kWarpRows]     processing order (kets sorted by work, most first)
 //   hist  int32 [2][n_ann+2]    counting-sort buckets and cursors
-constexpr int kWarpRows = 128;
+constexpr int kWarpRows = 64;
 
 __host__ __device__ inline size_t df_warp_scratch_bytes(int M, int n_ann) {
   size_t b = (size_t)M * kWarpRows * 4 + (((size_t)M * kWarpRows + 15) & ~(size_t)15);

@@ -139,8 +139,9 @@ static int build_tables(Space& sp) {
         for (int q = p; q < M; ++q) {
           if ((p + q) % M != k || (p == r && q == s)) continue;
           double mpq = (p == q) ? 1.0 : 2.0;
+          // combos with a zero coupling are kept: for odd M every pair then has
+          // (M-1)/2 partners, which the specialised stage kernels unroll
           cd g = std::conj(mpq * mrs * LS(p, q, r, s));
-          if (g == cd(0, 0)) continue;
           if (g.imag() != 0.0) cplx = true;
           int lo = std::min(r, p), hi = std::max(s, q);
           pq.push_back((uint32_t)p | ((uint32_t)q << 8) | ((uint32_t)lo << 16) | ((uint32_t)hi << 24));

@@ -32,7 +32,7 @@ struct Tables {
   int nmax;      // largest N of the space
   int rem_w;     // nmax + 5
   int n_ann;     // M(M+1)/2 unordered annihilation pairs (r <= s)
-  int n_combo;   // (annihilation pair, creation pair) combinations with nonzero coupling
+  int n_combo;   // (annihilation pair, creation pair) combinations, zero couplings included
   int is_complex;
   int blob_bytes;  // size of the shared-memory image
   // byte offsets of the sub-tables inside the image

@@ -289,6 +289,7 @@ __global__ void __launch_bounds__(kBlock) terms_kernel(const Tables t, unsigned 
         unsigned long long mrs = (r == s) ? 1 : 2;
         if (v.gd[ai] != 0.0) tuples += mrs * mrs;
         for (int j = v.ann[ai]; j < v.ann[ai + 1]; ++j) {
+          if (v.G[2 * j] == 0.0 && v.G[2 * j + 1] == 0.0) continue;
           uint32_t w4 = v.pq[j];
           int p = w4 & 0xff, q = (w4 >> 8) & 0xff;
           terms += 1;

@@ -13,10 +13,12 @@
 // multiplicity-summed symmetrised coupling; the diagonal is precomputed per ket.
 //
 // Work layout: every warp owns tiles of kWarpRows consecutive kets and runs
-// without CTA-wide barriers.  Phase 1 unranks the tile (4 kets per lane) into
-// occupations and suffix-state indices; phase 2 counting-sorts the tile by the
-// number of annihilation pairs acting on each ket; phase 3 runs the terms in
-// four rounds, the 32 lanes of a round taking 32 kets of nearly equal work.
+// without CTA-wide barriers.  Phase 1 unranks the tile (kWarpRows/32 kets per
+// lane) into occupations and suffix-state indices; phase 2 counting-sorts the
+// tile by the number of annihilation pairs acting on each ket; phase 3 runs the
+// terms in rounds, the 32 lanes of a round taking 32 kets of nearly equal work.
+// For odd M every annihilation pair has exactly (M-1)/2 creation partners; the
+// specialised kernels unroll them so that their ranks and gathers overlap.
 #pragma once
 #include "qb_device.cuh"
 
@@ -24,9 +26,12 @@ namespace qb {
 
 template <int MT, int B, bool CPLX>
 __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const DfArgs a, const int final_stage) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  load_blob(t, smem);  // the only CTA-wide barrier: warps run independently afterwards
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // the image from the ranking table E on; the fill counts stay in global memory
+  load_blob_from(t, smem_raw, t.o_E);  // the only CTA-wide barrier: warps run independently afterwards
+  unsigned char* smem = smem_raw - t.o_E;
   const View v = make_view(t, smem);
+  const uint32_t* gcnt = reinterpret_cast<const uint32_t*>(t.blob + t.o_cnt);
   const float2* sqf = reinterpret_cast<const float2*>(smem + t.o_sqf);
   const float4* Gf = reinterpret_cast<const float4*>(smem + t.o_Gf);
   const uint4* dl4 = reinterpret_cast<const uint4*>(v.delta);
@@ -34,7 +39,7 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
   const int V = t.nmax + 1, twoM = 2 * M;
   constexpr int kWarps = kBlock / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned char* sp = smem + ((t.blob_bytes + 15) & ~15) + (size_t)warp * df_warp_scratch_bytes(M, t.n_ann);
+  unsigned char* sp = smem_raw + ((t.blob_bytes - t.o_E + 15) & ~15) + (size_t)warp * df_warp_scratch_bytes(M, t.n_ann);
   int32_t* sidx = reinterpret_cast<int32_t*>(sp);
   uint8_t* socc = reinterpret_cast<uint8_t*>(sidx + M * kWarpRows);
   int32_t* sD = reinterpret_cast<int32_t*>(socc + ((M * kWarpRows + 15) & ~15));
@@ -47,7 +52,7 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
 
   for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * kWarpRows; base < total;
        base += (int64_t)gridDim.x * kWarps * kWarpRows) {
-    // ---- phase 1: each lane unranks 4 kets into occupations and suffix-state indices
+    // ---- phase 1: each lane unranks kWarpRows/32 kets into occupations and suffix-state indices
     for (int k = lane; k < 2 * nb; k += 32) hist[k] = 0;
     int key[kWarpRows / 32];
 #pragma unroll
@@ -63,9 +68,9 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
         int left = (int)(g - off);
         for (int m = 0; m < M - 1; ++m) {
           int val = 0, kk = kr;
-          const uint32_t* crow = v.cnt + (size_t)(m + 1) * V * M;
+          const uint32_t* crow = gcnt + (size_t)(m + 1) * V * M;
           while (true) {
-            const int c = (int)crow[(rem - val) * M + kk];
+            const int c = (int)__ldg(crow + (rem - val) * M + kk);
             if (left < c || val == rem) break;
             left -= c;
             ++val;
@@ -117,7 +122,7 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
     for (int u = 0; u < kWarpRows / 32; ++u) sperm[atomicAdd(&cursor[key[u]], 1)] = (uint8_t)(u * 32 + lane);
     __syncwarp();
 
-    // ---- phase 3: four rounds; in each the 32 lanes take 32 kets of similar work
+    // ---- phase 3: rounds of 32 kets of similar work, one per lane
     for (int round = 0; round < kWarpRows / 32; ++round) {
       const int row = sperm[round * 32 + lane];
       const int D = sD[row];
@@ -158,37 +163,80 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
         const int ai = v.pairidx[r * 16 + s];
         const float2 sa = sqf[occ[r * kWarpRows]], sb = sqf[occ[s * kWarpRows] - (r == s ? 1 : 0)];
         const dfl A = df_mul(dfl{sa.x, sa.y}, dfl{sb.x, sb.y});
-        const int j1 = v.ann[ai + 1];
-        for (int j = v.ann[ai]; j < j1; ++j) {
-          const uint32_t w4 = v.pq[j];
-          const int p = w4 & 0xff, q = (w4 >> 8) & 0xff;
-          const float2 bp = sqf[occ[p * kWarpRows] + 1], bq = sqf[occ[q * kWarpRows] + 1 + (p == q ? 1 : 0)];
-          const dfl AB = df_mul(A, df_mul(dfl{bp.x, bp.y}, dfl{bq.x, bq.y}));
-          // rank of the target: D - 1 - sum over every mode of E at the shifted suffix state
-          const uint4 dd = dl4[j];
-          int esum = 0;
+        constexpr int kC = (!CPLX && MT > 0 && (MT % 2) == 1) ? (MT - 1) / 2 : 0;
+        if (kC > 0) {
+          // fixed partner count: all ranks first, then all gathers, then the sums
+          const int j0 = v.ann[ai];
+          int rkc[kC > 0 ? kC : 1];
+          dfl crc[kC > 0 ? kC : 1];
 #pragma unroll
-          for (int m = 1; m < 16; ++m) {
-            if (m >= M) break;
-            const uint32_t word = (m < 4) ? dd.x : (m < 8) ? dd.y : (m < 12) ? dd.z : dd.w;
-            esum += v.E[id[m] + (int)((word >> (8 * (m & 3))) & 0xffu)];
+          for (int c = 0; c < kC; ++c) {
+            const int j = j0 + c;
+            const uint32_t w4 = v.pq[j];
+            const int p = w4 & 0xff, q = (w4 >> 8) & 0xff;
+            const float2 bp = sqf[occ[p * kWarpRows] + 1], bq = sqf[occ[q * kWarpRows] + 1 + (p == q ? 1 : 0)];
+            const dfl AB = df_mul(A, df_mul(dfl{bp.x, bp.y}, dfl{bq.x, bq.y}));
+            const uint4 dd = dl4[j];
+            int esum = 0;
+#pragma unroll
+            for (int m = 1; m < 16; ++m) {
+              if (m >= M) break;
+              const uint32_t word = (m < 4) ? dd.x : (m < 8) ? dd.y : (m < 12) ? dd.z : dd.w;
+              esum += v.E[id[m] + (int)((word >> (8 * (m & 3))) & 0xffu)];
+            }
+            int rk = D - 1 - esum;
+            if ((unsigned)rk >= (unsigned)D) {
+              atomicOr(a.status, 1);
+              rk = 0;
+            }
+            rkc[c] = rk;
+            const float4 gf = Gf[j];
+            crc[c] = df_mul(dfl{gf.x, gf.y}, AB);
           }
-          int rk = D - 1 - esum;
-          if ((unsigned)rk >= (unsigned)D) {
-            atomicOr(a.status, 1);
-            rk = 0;
-          }
-          const float4 gf = Gf[j];
-          const dfl cr = df_mul(dfl{gf.x, gf.y}, AB);
 #pragma unroll
           for (int b = 0; b < B; ++b) {
-            const float4 x = __ldg(vsec + (size_t)b * total + rk);
-            df_fma(acc_r[b], cr, dfl{x.x, x.y});
-            df_fma(acc_i[b], cr, dfl{x.z, x.w});
-            if (CPLX) {
-              const dfl ci = df_mul(dfl{gf.z, gf.w}, AB);
-              df_fma(acc_r[b], df_neg(ci), dfl{x.z, x.w});
-              df_fma(acc_i[b], ci, dfl{x.x, x.y});
+            float4 x[kC > 0 ? kC : 1];
+#pragma unroll
+            for (int c = 0; c < kC; ++c) x[c] = __ldg(vsec + (size_t)b * total + rkc[c]);
+#pragma unroll
+            for (int c = 0; c < kC; ++c) {
+              df_fma(acc_r[b], crc[c], dfl{x[c].x, x[c].y});
+              df_fma(acc_i[b], crc[c], dfl{x[c].z, x[c].w});
+            }
+          }
+        } else {
+          const int j1 = v.ann[ai + 1];
+          for (int j = v.ann[ai]; j < j1; ++j) {
+            const uint32_t w4 = v.pq[j];
+            const int p = w4 & 0xff, q = (w4 >> 8) & 0xff;
+            const float2 bp = sqf[occ[p * kWarpRows] + 1], bq = sqf[occ[q * kWarpRows] + 1 + (p == q ? 1 : 0)];
+            const dfl AB = df_mul(A, df_mul(dfl{bp.x, bp.y}, dfl{bq.x, bq.y}));
+            // rank of the target: D - 1 - sum over every mode of E at the shifted suffix state
+            const uint4 dd = dl4[j];
+            int esum = 0;
+  #pragma unroll
+            for (int m = 1; m < 16; ++m) {
+              if (m >= M) break;
+              const uint32_t word = (m < 4) ? dd.x : (m < 8) ? dd.y : (m < 12) ? dd.z : dd.w;
+              esum += v.E[id[m] + (int)((word >> (8 * (m & 3))) & 0xffu)];
+            }
+            int rk = D - 1 - esum;
+            if ((unsigned)rk >= (unsigned)D) {
+              atomicOr(a.status, 1);
+              rk = 0;
+            }
+            const float4 gf = Gf[j];
+            const dfl cr = df_mul(dfl{gf.x, gf.y}, AB);
+  #pragma unroll
+            for (int b = 0; b < B; ++b) {
+              const float4 x = __ldg(vsec + (size_t)b * total + rk);
+              df_fma(acc_r[b], cr, dfl{x.x, x.y});
+              df_fma(acc_i[b], cr, dfl{x.z, x.w});
+              if (CPLX) {
+                const dfl ci = df_mul(dfl{gf.z, gf.w}, AB);
+                df_fma(acc_r[b], df_neg(ci), dfl{x.z, x.w});
+                df_fma(acc_i[b], ci, dfl{x.x, x.y});
+              }
             }
           }
         }
@@ -233,7 +281,7 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
 template <int MT>
 int stage_launch_t(const Tables& t, const DfArgs& a, int final_stage, int B, bool cplx, cudaStream_t st,
                    int* grid_out) {
-  const size_t smem = ((t.blob_bytes + 15) & ~15) + df_scratch_bytes(t.M, t.n_ann);
+  const size_t smem = ((t.blob_bytes - t.o_E + 15) & ~15) + df_scratch_bytes(t.M, t.n_ann);
   int grid = 0, rc = QB_OK;
 #define QB_STAGE_CASE(BB, CC)                                                   \
   {                                                                             \
