@@ -37,12 +37,24 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, out_dir: str = None,
+          defines=()) -> str:
+    """Compiles libqb.so into `out_dir` (default: the in-tree _build/).  `defines`
+    are extra -D macros (tuning switches of the stage kernel)."""
+    global OUT_DIR, LIB
+    if out_dir is not None:
+        OUT_DIR_, LIB_ = OUT_DIR, LIB
+        OUT_DIR, LIB = out_dir, os.path.join(out_dir, "libqb.so")
+        try:
+            return build(True, verbose, ptxas_info, None, defines)
+        finally:
+            OUT_DIR, LIB = OUT_DIR_, LIB_
     if not force and not _stale():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = _nvcc()
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+    common += [f"-D{d}" for d in defines]
 
     def compile_one(src: str) -> str:
         obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")

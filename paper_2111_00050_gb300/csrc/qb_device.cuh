@@ -240,7 +240,10 @@ struct DfArgs {
 //   sOff  int64 [kWarpRows]     sector offset of the ket
 //   sperm uint8 [kWarpRows]     processing order (kets sorted by work, most first)
 //   hist  int32 [2][n_ann+2]    counting-sort buckets and cursors
-constexpr int kWarpRows = 64;
+#ifndef QB_WARP_ROWS
+#define QB_WARP_ROWS 128
+#endif
+constexpr int kWarpRows = QB_WARP_ROWS;
 
 __host__ __device__ inline size_t df_warp_scratch_bytes(int M, int n_ann) {
   size_t b = (size_t)M * kWarpRows * 4 + (((size_t)M * kWarpRows + 15) & ~(size_t)15);

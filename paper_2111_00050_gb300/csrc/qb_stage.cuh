@@ -22,16 +22,32 @@
 #pragma once
 #include "qb_device.cuh"
 
+#ifndef QB_CNT_GLOBAL
+#define QB_CNT_GLOBAL 0
+#endif
+#ifndef QB_UNROLL_PARTNERS
+#define QB_UNROLL_PARTNERS 1
+#endif
+
 namespace qb {
+
+// first byte of the table image the stage kernels stage in shared memory
+__host__ __device__ inline int kSmemFrom(const Tables& t) { return QB_CNT_GLOBAL ? t.o_E : 0; }
 
 template <int MT, int B, bool CPLX>
 __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const DfArgs a, const int final_stage) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+#if QB_CNT_GLOBAL
   // the image from the ranking table E on; the fill counts stay in global memory
   load_blob_from(t, smem_raw, t.o_E);  // the only CTA-wide barrier: warps run independently afterwards
   unsigned char* smem = smem_raw - t.o_E;
-  const View v = make_view(t, smem);
   const uint32_t* gcnt = reinterpret_cast<const uint32_t*>(t.blob + t.o_cnt);
+#else
+  load_blob(t, smem_raw);  // the only CTA-wide barrier: warps run independently afterwards
+  unsigned char* smem = smem_raw;
+  const uint32_t* gcnt = reinterpret_cast<const uint32_t*>(smem + t.o_cnt);
+#endif
+  const View v = make_view(t, smem);
   const float2* sqf = reinterpret_cast<const float2*>(smem + t.o_sqf);
   const float4* Gf = reinterpret_cast<const float4*>(smem + t.o_Gf);
   const uint4* dl4 = reinterpret_cast<const uint4*>(v.delta);
@@ -39,7 +55,7 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
   const int V = t.nmax + 1, twoM = 2 * M;
   constexpr int kWarps = kBlock / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned char* sp = smem_raw + ((t.blob_bytes - t.o_E + 15) & ~15) + (size_t)warp * df_warp_scratch_bytes(M, t.n_ann);
+  unsigned char* sp = smem_raw + ((t.blob_bytes - kSmemFrom(t) + 15) & ~15) + (size_t)warp * df_warp_scratch_bytes(M, t.n_ann);
   int32_t* sidx = reinterpret_cast<int32_t*>(sp);
   uint8_t* socc = reinterpret_cast<uint8_t*>(sidx + M * kWarpRows);
   int32_t* sD = reinterpret_cast<int32_t*>(socc + ((M * kWarpRows + 15) & ~15));
@@ -70,7 +86,7 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
           int val = 0, kk = kr;
           const uint32_t* crow = gcnt + (size_t)(m + 1) * V * M;
           while (true) {
-            const int c = (int)__ldg(crow + (rem - val) * M + kk);
+            const int c = (int)crow[(rem - val) * M + kk];
             if (left < c || val == rem) break;
             left -= c;
             ++val;
@@ -163,7 +179,7 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
         const int ai = v.pairidx[r * 16 + s];
         const float2 sa = sqf[occ[r * kWarpRows]], sb = sqf[occ[s * kWarpRows] - (r == s ? 1 : 0)];
         const dfl A = df_mul(dfl{sa.x, sa.y}, dfl{sb.x, sb.y});
-        constexpr int kC = (!CPLX && MT > 0 && (MT % 2) == 1) ? (MT - 1) / 2 : 0;
+        constexpr int kC = (QB_UNROLL_PARTNERS && !CPLX && MT > 0 && (MT % 2) == 1) ? (MT - 1) / 2 : 0;
         if (kC > 0) {
           // fixed partner count: all ranks first, then all gathers, then the sums
           const int j0 = v.ann[ai];
@@ -281,7 +297,7 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
 template <int MT>
 int stage_launch_t(const Tables& t, const DfArgs& a, int final_stage, int B, bool cplx, cudaStream_t st,
                    int* grid_out) {
-  const size_t smem = ((t.blob_bytes - t.o_E + 15) & ~15) + df_scratch_bytes(t.M, t.n_ann);
+  const size_t smem = ((t.blob_bytes - kSmemFrom(t) + 15) & ~15) + df_scratch_bytes(t.M, t.n_ann);
   int grid = 0, rc = QB_OK;
 #define QB_STAGE_CASE(BB, CC)                                                   \
   {                                                                             \
