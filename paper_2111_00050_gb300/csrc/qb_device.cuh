@@ -241,7 +241,7 @@ struct DfArgs {
 //   sperm uint8 [kWarpRows]     processing order (kets sorted by work, most first)
 //   hist  int32 [2][n_ann+2]    counting-sort buckets and cursors
 #ifndef QB_WARP_ROWS
-#define QB_WARP_ROWS 128
+#define QB_WARP_ROWS 64
 #endif
 constexpr int kWarpRows = QB_WARP_ROWS;
 

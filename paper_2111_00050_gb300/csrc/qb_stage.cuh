@@ -23,7 +23,7 @@
 #include "qb_device.cuh"
 
 #ifndef QB_CNT_GLOBAL
-#define QB_CNT_GLOBAL 0
+#define QB_CNT_GLOBAL 1
 #endif
 #ifndef QB_UNROLL_PARTNERS
 #define QB_UNROLL_PARTNERS 1
