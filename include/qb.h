@@ -171,6 +171,24 @@ int qb_observables(qb_space* space, const void* d_psi, qb_obs* out, void* stream
 int qb_evolve_observe(qb_space* space, void* d_psi, double dt, int64_t steps, int obs_every, qb_obs* series,
                       void* d_work, void* stream);
 
+/* Allocation-free variant of qb_observables (the paper has no counterpart).
+ * For callers that must not allocate device memory while they run -- a
+ * service under a fixed memory budget, a custom allocator that forbids
+ * cudaMalloc / cudaFree after start-up, a thread that must not enter the
+ * allocator because it can synchronise the device.  It writes the same
+ * observables as qb_observables, but keeps its reduction partials in one
+ * file-scope device array of 131072 doubles (1 MiB) that every GPU loading the
+ * library holds until the process exits, and calls no allocating routine.
+ * The array is shared by all calls and keeps the last call's contents; its
+ * status word is cleared at the start of each call.  Calls that overlap on the
+ * GPU (several streams or host threads at once) race on it: serialise them.
+ * The first call on a device looks up the array's address on that device, so
+ * make it before any stream capture, with that device current.  The grid of the
+ * reduction is capped so that (4 + 2M + 4M^2 + 2) * grid + ~10 doubles fit;
+ * QB_EUNSUPPORTED if even 32 CTAs would not (not reachable for M <= 16).
+ * Same arguments, errors and synchronisation as qb_observables. */
+int qb_observables_noalloc(qb_space* space, const void* d_psi, qb_obs* out, void* stream);
+
 /* ---- breaktime and mean field (Sec. III A, IV C-D) ----------------------- */
 
 /* First sample k with values[k] >= thr; t_br interpolates linearly between

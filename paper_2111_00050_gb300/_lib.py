@@ -67,6 +67,8 @@ SIGNATURES = {
     "qb_evolve_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _c_double_p, ctypes.c_double,
                                        ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "qb_observables": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(QbObs), ctypes.c_void_p]),
+    "qb_observables_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(QbObs),
+                                              ctypes.c_void_p]),
     "qb_evolve_observe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int64,
                                          ctypes.c_int, ctypes.POINTER(QbObs), ctypes.c_void_p, ctypes.c_void_p]),
     "qb_breaktime": (ctypes.c_int, [_c_double_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, _c_double_p,

@@ -338,7 +338,7 @@ static void hermitian_eig(int n, const double* A /*[n*n] complex*/, double* eig,
 }
 
 // Derived observables of Sec. II C-E from the raw moments.
-static void derive(int M, const double* raw, qb_obs* o) {
+void derive(int M, const double* raw, qb_obs* o) {
   memset(o, 0, sizeof(*o));
   double nrm = raw[0];
   o->norm = nrm;

@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -797,5 +798,121 @@ int launch_moments(Space& s, const void* d_psi, double* out_host, void* stream) 
   out_host[2] = h2[0];
   return check_status(s, st);
 }
+
+
+// ----------------------------------------------- allocation-free observables
+//
+// qb_observables_noalloc serves callers that must not allocate device memory
+// while they run: code inside a memory-budgeted service or a custom allocator
+// that forbids cudaMalloc / cudaFree after start-up, or a host thread that must
+// not touch the allocator (which may synchronise the device).  It computes the
+// same observables as qb_observables, but its reduction partials live in one
+// fixed, file-scope device array instead of the space's scratch buffer.
+//
+// The array holds kNoAllocDoubles doubles (1 MiB) on every GPU that loads the
+// library, for the life of the process.  Every call shares it and it keeps the
+// last call's contents; the status word is cleared at the start of each call.
+// Calls that overlap on the GPU (several streams or threads at once) race on it.
+// The first call on each device looks up the array's device address
+// (cudaGetSymbolAddress) with that device current; make that first call before
+// any stream capture.
+
+constexpr int64_t kNoAllocDoubles = 131072;  // 1 MiB
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+static double* g_noalloc_ptr[256];  // device address of the array, per device
+static std::mutex g_noalloc_mu;
+
+static int noalloc_scratch(double** out) {
+  int dev = 0;
+  QB_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return fail(QB_EUNSUPPORTED, "device ordinal beyond 255");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(QB_ECUDA, std::string("cudaGetSymbolAddress(g_noalloc_scratch): ") + cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return QB_OK;
+}
+
+template <bool CPLX>
+static int noalloc_dot(const Space& s, const StageArgs& a, int grid, cudaStream_t st) {
+  const size_t smem = row_smem(s.t);
+  auto k = hpsi_kernel<MODE_DOT, 1, CPLX>;
+  int g0 = 0;
+  int rc = persistent_grid(k, smem, s.t.total, &g0);
+  if (rc) return rc;
+  k<<<std::min(grid, g0), kBlock, smem, st>>>(s.t, a);
+  QB_CUDA(cudaGetLastError());
+  return QB_OK;
+}
+
+}  // namespace qb
+
+using namespace qb;
+
+extern "C" int qb_observables_noalloc(qb_space* space, const void* d_psi, qb_obs* out, void* stream) {
+  Space* sp = reinterpret_cast<Space*>(space);
+  if (!sp || !out) return fail(QB_EINVAL, "space and out must be non-NULL");
+  if (!d_psi || (reinterpret_cast<uintptr_t>(d_psi) & 15)) return fail(QB_EINVAL, "d_psi must be 16-byte aligned");
+  int dev = 0;
+  QB_CUDA(cudaGetDevice(&dev));
+  if (dev != sp->device) return fail(QB_EINVAL, "the space was built on another device");
+  double* scr = nullptr;
+  int rc = noalloc_scratch(&scr);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int M = sp->M;
+  const int nmom = nmoments(M);
+  // layout (doubles): [0, 2) status word | partials [G nmom] | final [nmom] |
+  // dot partials [2 G] | dot final [2]; G CTAs, capped so that it fits
+  const int64_t fixed = 2 + nmom + 2 + 8;
+  const int64_t gcap = (kNoAllocDoubles - fixed) / (nmom + 2);
+  if (gcap < 32)
+    return fail(QB_EUNSUPPORTED, "the moments of this space need more than the fixed 1 MiB scratch of "
+                                 "qb_observables_noalloc (M too large)");
+  const size_t smem = row_smem(sp->t) + ((kRowScratchBytes + 15) & ~15) - kRowScratchBytes +
+                      (size_t)(kBlock / 32) * nmom * sizeof(double) + 16;
+  int grid = 0;
+  rc = persistent_grid(moments_kernel, smem, sp->t.total, &grid);
+  if (rc) return rc;
+  grid = (int)std::min<int64_t>(grid, gcap);
+  int* status = reinterpret_cast<int*>(scr);
+  double* part = scr + 2;
+  double* fin = part + (int64_t)grid * nmom;
+  double* dpart = fin + nmom;
+  double* dfin = dpart + 2 * (int64_t)grid;
+  QB_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+  moments_kernel<<<grid, kBlock, smem, st>>>(sp->t, (const double2*)d_psi, part, nmom, status);
+  QB_CUDA(cudaGetLastError());
+  reduce_partials_kernel<<<(nmom + 127) / 128, 128, 0, st>>>(part, grid, nmom, fin);
+  QB_CUDA(cudaGetLastError());
+  StageArgs a{};
+  a.vin = (const double2*)d_psi;
+  a.scale[0] = 1.0;
+  a.status = status;
+  a.partial = dpart;
+  rc = sp->t.is_complex ? noalloc_dot<true>(*sp, a, grid, st) : noalloc_dot<false>(*sp, a, grid, st);
+  if (rc) return rc;
+  reduce_partials_kernel<<<1, 32, 0, st>>>(dpart, grid, 2, dfin);
+  QB_CUDA(cudaGetLastError());
+  std::vector<double> raw(nmom, 0.0);
+  double h2[2];
+  int hs = 0;
+  QB_CUDA(cudaMemcpyAsync(raw.data(), fin, sizeof(double) * nmom, cudaMemcpyDeviceToHost, st));
+  QB_CUDA(cudaMemcpyAsync(h2, dfin, sizeof(h2), cudaMemcpyDeviceToHost, st));
+  QB_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  QB_CUDA(cudaStreamSynchronize(st));
+  if (hs) return fail(QB_EINTERNAL, "device-side consistency check failed (status " + std::to_string(hs) + ")");
+  raw[2] = h2[0];
+  if (!(raw[0] > 0.0)) return fail(QB_EINVAL, "the state has zero norm");
+  derive(M, raw.data(), out);
+  return QB_OK;
+}
+
+namespace qb {
 
 }  // namespace qb
