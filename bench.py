@@ -31,7 +31,12 @@ import numpy as np  # noqa: E402
 
 import workloads as wl  # noqa: E402
 
-MEASURED_FP64_TFLOPS = 1.0  # DFMA microbenchmark on this machine's GB300 (profiles/fp64_peak_probe.md)
+# FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+# (a DFMA microbenchmark measured 1.00 TFLOP/s: python -m paper_2111_00050_gb300.probe)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes per ket of one stage launch, from an ncu capture of the current stage kernel
+# (batched coherent at n_tot=12: 727.8 MB over 15,380,937 kets); scaled by kets
+STAGE_DRAM_BYTES_PER_KET = 727.8e6 / 15380937
 
 
 def _peaks():
@@ -235,33 +240,36 @@ def main():
     value = world * 4 * terms / (ms_step * 1e-3)
     steps_per_s = 1e3 / ms_step
 
-    # ---- dominant kernel: one fused RK4 stage == one H psi over every sector
-    out = qs.empty_state()
-    for _ in range(2):
-        qs.hpsi(psi, out)
-    torch.cuda.synchronize()
-    durs = []
-    for _ in range(5):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        qs.hpsi(psi, out)
-        b.record(stream)
-        torch.cuda.synchronize()
-        durs.append(a.elapsed_time(b))
-    t_launch = statistics.median(durs) * 1e-3
+    # ---- dominant kernel: one fused RK4 stage == one H psi over all sectors; a step is
+    # four launches of it, timed above with CUDA events on the launching stream
     stage_time = ms_step * 1e-3 / 4
-    flops = 4.0 * terms  # >= 2 DFMA per term (real coefficient x complex amplitude)
+    flops = 4.0 * terms  # >= 2 FP64 FMA per term (real coefficient x complex amplitude)
     achieved = flops / stage_time / 1e12
     peaks = _peaks()
-    hbm_bytes = 32.0 * qs.total
+    hbm_bytes = 32.0 * qs.total  # read v once, write the stage output once
+    # FP64 H psi (qb_hpsi) for comparison with the double-float stage
+    out = qs.empty_state()
+    qs.hpsi(psi, out)
+    torch.cuda.synchronize()
+    a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a_ev.record(stream)
+    qs.hpsi(psi, out)
+    b_ev.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = a_ev.elapsed_time(b_ev)
+    del out
     roofline = {
-        "bound": "alu", "achieved": achieved, "peak": MEASURED_FP64_TFLOPS, "unit": "TFLOP/s",
-        "frac": achieved / MEASURED_FP64_TFLOPS, "traffic": None,
-        "kernel": "hpsi_kernel<MODE_STAGE> (one RK4 stage = one H psi over all sectors)",
+        "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "frac": achieved / FP64_PEAK_TFLOPS,
+        "traffic": STAGE_DRAM_BYTES_PER_KET * qs.total if args.config == "batched_coherent" else None,
+        "kernel": f"stage_df_kernel<{W.M},1,0> (one RK4 stage = one H psi over all sectors)",
+        "stage_ms": stage_time * 1e3,
+        "peak_note": "FP64-equivalent flops (2 FMA/term) vs the FP64 pipe peak from unit counts "
+                     "(152 SMs x 2 FMA/clk x 2.07 GHz); the kernel itself runs double-float on the FP32/ALU "
+                     "pipes; traffic scaled from an ncu capture at n_tot=12",
         "hbm_GBps": hbm_bytes / stage_time / 1e9, "hbm_peak_GBps": peaks.get("hbm_gbs"),
         "hbm_frac": (hbm_bytes / stage_time / 1e9) / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
-        "hpsi_launch_ms": t_launch * 1e3,
-        "peak_note": "FP64 DFMA rate measured on this GB300 (nominal 1.25 TFLOP/s)",
+        "fp64_hpsi_ms": fp64_ms,
     }
 
     # ---- end to end through the public API with host buffers
