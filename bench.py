@@ -272,6 +272,17 @@ def main():
         "fp64_hpsi_ms": fp64_ms,
     }
 
+    # ---- plain path: one launch per sector per stage, same workload and arithmetic
+    k_plain = max(1, min(args.steps, 3))
+    e0p, e1p = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0p.record(stream)
+    qs.evolve_plain(psi, W.dt, k_plain, work)
+    e1p.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0p.elapsed_time(e1p) / k_plain
+    plain = {"ms_per_step": plain_ms, "terms_per_s": 4 * terms / (plain_ms * 1e-3), "steps": k_plain,
+             "launches_per_step": 4 * qs.n_sectors, "batched_speedup": plain_ms / ms_step}
+
     # ---- end to end through the public API with host buffers
     host_in = torch.empty(qs.total, dtype=torch.complex128).pin_memory()
     host_in.copy_(psi.cpu())
@@ -298,6 +309,7 @@ def main():
                    "l2": "state (16 B/ket, %.2f GB) larger than L2; no flush" % (16 * qs.total / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "rk4_steps_per_s": steps_per_s,
+        "plain_per_sector": plain,
         "gpu_launches": 4 * args.steps,
         "clocks": clocks,
         "roofline": roofline,

@@ -160,6 +160,12 @@ int qb_evolve(qb_space* space, void* d_psi, double dt, int64_t steps, void* d_wo
 int qb_evolve_batch(qb_space* space, void* d_psi, int batch, const double* scale, double dt, int64_t steps,
                     void* d_work, void* stream);
 
+/* The same RK4 evolution as qb_evolve with one kernel launch per sector per
+ * stage instead of one per stage for every sector: the per-sector scheme of
+ * Sec. III B taken literally, kept as the comparison baseline of the batched
+ * path.  Same arguments, workspace and results as qb_evolve. */
+int qb_evolve_plain(qb_space* space, void* d_psi, double dt, int64_t steps, void* d_work, void* stream);
+
 /* ---- observables (Sec. II C-E) ------------------------------------------- */
 
 /* All observables of one state; out (host) is written after the stream syncs. */

@@ -156,6 +156,10 @@ class Space:
         work = self.workspace(1) if work is None else work
         check(lib().qb_evolve(self._h, _dptr(psi), float(dt), int(steps), _dptr(work), _stream()))
 
+    def evolve_plain(self, psi: torch.Tensor, dt: float, steps: int, work: Optional[torch.Tensor] = None) -> None:
+        work = self.workspace(1) if work is None else work
+        check(lib().qb_evolve_plain(self._h, _dptr(psi), float(dt), int(steps), _dptr(work), _stream()))
+
     def evolve_batch(self, psi: torch.Tensor, scale, dt: float, steps: int,
                      work: Optional[torch.Tensor] = None) -> None:
         sc = _f64(scale)

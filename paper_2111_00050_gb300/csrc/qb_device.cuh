@@ -226,6 +226,7 @@ struct DfArgs {
   float4* out;         // stage output, double-float [B][total] (final stage: new copy of psi)
   const float4* diag;  // per ket (w.hi, w.lo, L.hi, L.lo)
   float2 scale[8];     // two-body scale per member, double-float
+  int64_t row0, row1;  // kets [row0, row1) of the launch (every sector: 0, total)
   double zre;          // dt / d: out = psi + (dt/d) (Im Hv, -Re Hv)
   float2 zf;           // dt / d as double-float
   int* status;
@@ -255,14 +256,46 @@ __host__ __device__ inline size_t df_scratch_bytes(int M, int n_ann) {
   return (size_t)(kBlock / 32) * df_warp_scratch_bytes(M, n_ann);
 }
 
+// Resident CTAs per SM of `kernel` with `smem` dynamic shared memory, cached
+// per (kernel, smem) so that launch loops do not repeat the occupancy query.
 template <typename K>
-static int persistent_grid(K kernel, size_t smem, int64_t rows, int* grid) {
-  int dev = 0, sms = 0, per = 0;
+static int occupancy_cached(K kernel, size_t smem, int* per_sm, int* sms) {
+  struct Entry {
+    const void* fn;
+    size_t smem;
+    int dev, per, sms;
+  };
+  static thread_local Entry cache[64];
+  static thread_local int used = 0;
+  int dev = 0;
   QB_CUDA(cudaGetDevice(&dev));
-  QB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const void* fn = reinterpret_cast<const void*>(kernel);
+  for (int i = 0; i < used; ++i)
+    if (cache[i].fn == fn && cache[i].smem == smem && cache[i].dev == dev) {
+      *per_sm = cache[i].per;
+      *sms = cache[i].sms;
+      return QB_OK;
+    }
+  int s = 0, per = 0;
+  QB_CUDA(cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev));
   QB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   QB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kBlock, smem));
   if (per < 1) return fail(QB_EUNSUPPORTED, "kernel does not fit on an SM with this table size");
+  Entry e{fn, smem, dev, per, s};
+  cache[used < 64 ? used++ : 63] = e;
+  *per_sm = per;
+  *sms = s;
+  return QB_OK;
+}
+
+// Persistent grid of a row kernel: at most one wave of resident CTAs (capped at
+// 16 per SM, the size the reduction scratch is planned for), no more CTAs than
+// there are kBlock-row tiles.
+template <typename K>
+static int persistent_grid(K kernel, size_t smem, int64_t rows, int* grid) {
+  int per = 0, sms = 0;
+  int rc = occupancy_cached(kernel, smem, &per, &sms);
+  if (rc) return rc;
   int64_t want = (rows + kBlock - 1) / kBlock;
   int64_t g = std::min<int64_t>((int64_t)sms * std::min(per, 16), std::max<int64_t>(1, want));
   *grid = (int)g;

@@ -658,6 +658,20 @@ int qb_evolve_batch(qb_space* space, void* d_psi, int batch, const double* scale
   return launch_rk4(*sp, d_psi, batch, scale, dt, steps, d_work, stream);
 }
 
+int qb_evolve_plain(qb_space* space, void* d_psi, double dt, int64_t steps, void* d_work, void* stream) {
+  Space* sp = reinterpret_cast<Space*>(space);
+  if (!sp) return fail(QB_EINVAL, "space is NULL");
+  if (steps < 0) return fail(QB_EINVAL, "steps < 0");
+  if (!std::isfinite(dt)) return fail(QB_EINVAL, "dt is not finite");
+  int rc = check_state_ptr(d_psi);
+  if (rc) return rc;
+  if (steps == 0) return QB_OK;
+  rc = check_state_ptr(d_work);
+  if (rc) return rc;
+  double one = 1.0;
+  return launch_rk4(*sp, d_psi, 1, &one, dt, steps, d_work, stream, true);
+}
+
 int qb_observables(qb_space* space, const void* d_psi, qb_obs* out, void* stream) {
   Space* sp = reinterpret_cast<Space*>(space);
   if (!sp || !out) return fail(QB_EINVAL, "space and out must be non-NULL");

@@ -90,7 +90,7 @@ int fail(int code, const std::string& msg);
 // launchers (qb_kernels.cu); all return a QB_* status
 int launch_hpsi(const Space& s, const void* d_v, void* d_out, void* stream);
 int launch_rk4(Space& s, void* d_psi, int batch, const double* scale, double dt, int64_t steps, void* d_work,
-               void* stream);
+               void* stream, bool plain = false);
 int launch_unrank(const Space& s, int64_t first, int64_t count, int* d_occ, void* stream);
 int launch_rank(const Space& s, const int* d_occ, int64_t count, int64_t* d_index, void* stream);
 int launch_terms(const Space& s, int64_t* terms, int64_t* tuples, void* stream);

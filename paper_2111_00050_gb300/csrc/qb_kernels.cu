@@ -634,9 +634,11 @@ int launch_hpsi(const Space& s, const void* d_v, void* d_out, void* stream) {
   return check_status(s, st);
 }
 
+// plain = true: one launch per sector per stage (the comparison baseline of
+// qb_evolve_plain); otherwise one launch per stage covers every sector.
 template <int B>
 static int rk4_loop(Space& s, double2* psi, const double* scale, double dt, int64_t steps, float4* w1, float4* w2,
-                    float4* psif, cudaStream_t st) {
+                    float4* psif, cudaStream_t st, bool plain = false) {
   const int64_t n = (int64_t)B * s.t.total;
   const bool cplx = s.t.is_complex != 0;
   to_df_kernel<<<1216, 256, 0, st>>>(psi, psif, n);
@@ -660,15 +662,26 @@ static int rk4_loop(Space& s, double2* psi, const double* scale, double dt, int6
       a.zre = dt / d;
       const float zh = (float)a.zre;
       a.zf = make_float2(zh, (float)(a.zre - (double)zh));
-      int rc = stage_launch(s.t, a, d == 1 ? 1 : 0, B, cplx, st);
-      if (rc) return rc;
+      if (!plain) {
+        a.row0 = 0;
+        a.row1 = s.t.total;
+        int rc = stage_launch(s.t, a, d == 1 ? 1 : 0, B, cplx, st);
+        if (rc) return rc;
+      } else {
+        for (size_t sec = 0; sec + 1 < s.secOff.size(); ++sec) {
+          a.row0 = s.secOff[sec];
+          a.row1 = s.secOff[sec + 1];
+          int rc = stage_launch(s.t, a, d == 1 ? 1 : 0, B, cplx, st);
+          if (rc) return rc;
+        }
+      }
     }
   }
   return QB_OK;
 }
 
 int launch_rk4(Space& s, void* d_psi, int batch, const double* scale, double dt, int64_t steps, void* d_work,
-               void* stream) {
+               void* stream, bool plain) {
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = (int64_t)batch * s.secOff.back();
   double2* psi = (double2*)d_psi;
@@ -677,10 +690,10 @@ int launch_rk4(Space& s, void* d_psi, int batch, const double* scale, double dt,
   float4* psif = w2 + n;
   int rc;
   switch (batch) {
-    case 1: rc = rk4_loop<1>(s, psi, scale, dt, steps, w1, w2, psif, st); break;
-    case 2: rc = rk4_loop<2>(s, psi, scale, dt, steps, w1, w2, psif, st); break;
-    case 4: rc = rk4_loop<4>(s, psi, scale, dt, steps, w1, w2, psif, st); break;
-    case 8: rc = rk4_loop<8>(s, psi, scale, dt, steps, w1, w2, psif, st); break;
+    case 1: rc = rk4_loop<1>(s, psi, scale, dt, steps, w1, w2, psif, st, plain); break;
+    case 2: rc = rk4_loop<2>(s, psi, scale, dt, steps, w1, w2, psif, st, plain); break;
+    case 4: rc = rk4_loop<4>(s, psi, scale, dt, steps, w1, w2, psif, st, plain); break;
+    case 8: rc = rk4_loop<8>(s, psi, scale, dt, steps, w1, w2, psif, st, plain); break;
     default: return fail(QB_EINVAL, "batch must be 1, 2, 4 or 8");
   }
   if (rc) return rc;

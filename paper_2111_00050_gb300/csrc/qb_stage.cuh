@@ -63,10 +63,11 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
   uint8_t* sperm = reinterpret_cast<uint8_t*>(sOff + kWarpRows);
   int32_t* hist = reinterpret_cast<int32_t*>(sperm + kWarpRows);
   int32_t* cursor = hist + (t.n_ann + 2);
-  const int64_t total = t.total;
+  const int64_t total = t.total;  // stride between sweep members
+  const int64_t row1 = a.row1;
   const int nb = t.n_ann + 2;
 
-  for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * kWarpRows; base < total;
+  for (int64_t base = a.row0 + ((int64_t)blockIdx.x * kWarps + warp) * kWarpRows; base < row1;
        base += (int64_t)gridDim.x * kWarps * kWarpRows) {
     // ---- phase 1: each lane unranks kWarpRows/32 kets into occupations and suffix-state indices
     for (int k = lane; k < 2 * nb; k += 32) hist[k] = 0;
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
       const int row = u * 32 + lane;
       const int64_t g = base + row;
       key[u] = 0;
-      if (g < total) {
+      if (g < row1) {
         const int sid = find_sector(t, g);
         const int64_t off = __ldg(t.sec_off + sid);
         const int D = (int)(__ldg(t.sec_off + sid + 1) - off);
@@ -302,7 +303,7 @@ int stage_launch_t(const Tables& t, const DfArgs& a, int final_stage, int B, boo
 #define QB_STAGE_CASE(BB, CC)                                                   \
   {                                                                             \
     auto k = stage_df_kernel<MT, BB, CC>;                                       \
-    rc = persistent_grid(k, smem, t.total, &grid);                              \
+    rc = persistent_grid(k, smem, a.row1 - a.row0, &grid);                      \
     if (rc) return rc;                                                          \
     k<<<grid, kBlock, smem, st>>>(t, a, final_stage);                           \
   }

@@ -265,3 +265,19 @@ def test_errors_are_reported():
     qs = qb.Space(M, w, L, 3, 3)
     with pytest.raises(qb.QbError):
         qs.init_number([3, 0, 0, 0, 1], qs.empty_state())  # N=4 not held
+
+
+def test_plain_per_sector_path_is_bit_identical_to_batched():
+    """One launch per sector per stage and one launch for all sectors compute every
+    ket with the same arithmetic: the states must agree bit for bit."""
+    M = 5
+    z, w, L = _coherent_case(M, 2.0, 11, -0.1, 3)
+    import paper_2111_00050_gb300 as qb
+
+    qs = qb.Space(M, w, L, 0, 11)
+    a = qs.empty_state()
+    qs.init_coherent(z, a)
+    b = a.clone()
+    qs.evolve(a, 2e-3, 40)
+    qs.evolve_plain(b, 2e-3, 40)
+    assert bool((a == b).all())
