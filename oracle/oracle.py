@@ -434,3 +434,60 @@ def rk4_step_adjoint(space: Space, w, L, psi_n: np.ndarray, lam_next: np.ndarray
             g += 2.0 * np.vdot(gk, dA(uk)).real
         grads.append(g)
     return lam_n, grads
+
+
+def loss_and_seed(space: Space, psi: np.ndarray, kind: str = "Q"):
+    """Loss at the final state and its Wirtinger gradient d loss / d psi^*, by
+    definition.  kind "Q": Eq. (Qparam) with n_tot = Tr M; kind "PO": the
+    principal eigenvalue lam_p of M (Eq. POcriterion), d lam_p = xi^dag dM xi."""
+    ob = observables(space, psi)
+    nu = ob["norm"]
+    if kind == "Q":
+        a = ob["a"]
+        Nexp = ob["n_tot"]
+        S = float(np.sum(np.abs(a) ** 2))
+        lam = (S / Nexp) * psi
+        Npsi = np.zeros_like(psi)
+        for j in range(space.M):
+            Npsi += apply_mode_op(space, psi, "n", j)
+            lam -= (np.conj(a[j]) * apply_mode_op(space, psi, "a", j)
+                    + a[j] * apply_mode_op(space, psi, "adag", j)) / Nexp
+        lam += (S / Nexp ** 2) * Npsi
+        return ob["Q"], lam / nu
+    xi = ob["xi"]
+    lam = -ob["lam_p"] * psi
+    for i in range(space.M):
+        for j in range(space.M):
+            lam += np.conj(xi[i]) * xi[j] * apply_mode_op(space, apply_mode_op(space, psi, "a", j), "adag", i)
+    return ob["lam_p"], lam / nu
+
+
+def adjoint_gradient(space: Space, w, L0, scale: float, z, dt: float, steps: int, kind: str = "Q"):
+    """Exact discrete adjoint of `steps` classic RK4 steps of H = H_w + scale H_{L0}
+    from the renormalised truncated coherent state of z; every state is stored.
+    Returns (loss, d/dscale, d/dw [M], d/dz [M] as d/dRe z + i d/dIm z)."""
+    M = space.M
+    L = scale * np.asarray(L0, dtype=np.complex128)
+    psi0, _ = coherent_state(space, z)
+    states = [psi0]
+    for _ in range(steps):
+        states.append(rk4(space, w, L, states[-1], dt, 1))
+    loss, lam = loss_and_seed(space, states[-1], kind)
+    dHs = lambda v: apply_h(space, np.zeros(M), L0, v)
+    dHw = [lambda v, q=q: apply_mode_op(space, v, "n", q) for q in range(M)]
+    g_s, g_w = 0.0, np.zeros(M)
+    for n in range(steps - 1, -1, -1):
+        lam, g = rk4_step_adjoint(space, w, L, states[n], lam, dt, [dHs] + dHw)
+        g_s += g[0]
+        g_w += np.array(g[1:])
+    psi0 = states[0]
+    c = np.vdot(lam, psi0)
+    gz = np.zeros(M, dtype=np.complex128)
+    for k in range(M):
+        ak_dag_psi = apply_mode_op(space, psi0, "adag", k)
+        Gk = np.vdot(lam, ak_dag_psi)    # <lam, d psi0/d z_k> before renormalisation
+        Hk = np.vdot(psi0, ak_dag_psi)
+        dx = 2 * Gk.real - 2 * c.real * Hk.real
+        dy = -2 * Gk.imag + 2 * c.real * Hk.imag
+        gz[k] = dx + 1j * dy
+    return loss, g_s, g_w, gz

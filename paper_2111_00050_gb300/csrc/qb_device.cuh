@@ -219,16 +219,29 @@ __device__ __forceinline__ dfl df_renorm(dfl a) {
   return {h, __fsub_rn(a.l, __fsub_rn(h, a.h))};
 }
 
+// Arguments of one stage launch.  With z = -i zre and x the gathered vector
+// (vin), the epilogue writes, by `mode`:
+//   0  out  = psif + z H x                        (forward Horner stage, d > 1)
+//   1  psi += z H x;          out = df(psi)       (forward final stage, FP64 psi)
+//   2  out  = z H x                               (adjoint: costate stage vector)
+//   3  psi += sum_k basef[k] + z H x; out = df(psi)  (adjoint: new costate, FP64)
+// For the adjoint pass zre = -c dt, i.e. z = +i c dt.  With bilinears on, every
+// row also adds Im <pair_i, H_L x_i> and n_q(i) Im(conj(x_i) pair_i) to per-CTA
+// sums written to partial[block][M + 1] (H_L: the two-body part at scale 1).
 struct DfArgs {
   const float4* vin;   // gathered stage vector(s), double-float [B][total]
-  const float4* psif;  // double-float copy of psi [B][total]
-  double2* psi;        // psi (FP64) [B][total]; updated in the final stage
-  float4* out;         // stage output, double-float [B][total] (final stage: new copy of psi)
+  const float4* psif;  // double-float copy of psi [B][total] (mode 0)
+  double2* psi;        // FP64 vector updated in place (modes 1, 3)
+  float4* out;         // double-float output [B][total]
+  const float4* basef[3];  // mode 3: double-float vectors added to psi
+  int nbasef;
+  const float4* pair;  // bilinear pair vector (double-float), own row only
+  double* partial;     // bilinear sums [gridDim.x][M + 1]
   const float4* diag;  // per ket (w.hi, w.lo, L.hi, L.lo)
   float2 scale[8];     // two-body scale per member, double-float
   int64_t row0, row1;  // kets [row0, row1) of the launch (every sector: 0, total)
-  double zre;          // dt / d: out = psi + (dt/d) (Im Hv, -Re Hv)
-  float2 zf;           // dt / d as double-float
+  double zre;          // z = -i zre
+  float2 zf;           // zre as double-float
   int* status;
 };
 

@@ -652,6 +652,7 @@ static int rk4_loop(Space& s, double2* psi, const double* scale, double dt, int6
   a.psi = psi;
   a.psif = psif;
   a.status = reinterpret_cast<int*>(s.d_scratch);
+  a.nbasef = 0;
   for (int64_t it = 0; it < steps; ++it) {
     // Horner: v = psi + z/4 H psi; v = psi + z/3 H v; v = psi + z/2 H v; psi = psi + z H v
     const float4* in[4] = {psif, w1, w2, w1};

@@ -34,8 +34,8 @@ namespace qb {
 // first byte of the table image the stage kernels stage in shared memory
 __host__ __device__ inline int kSmemFrom(const Tables& t) { return QB_CNT_GLOBAL ? t.o_E : 0; }
 
-template <int MT, int B, bool CPLX>
-__global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const DfArgs a, const int final_stage) {
+template <int MT, int B, bool CPLX, bool BIL>
+__global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const DfArgs a, const int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
 #if QB_CNT_GLOBAL
   // the image from the ranking table E on; the fill counts stay in global memory
@@ -66,6 +66,11 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
   const int64_t total = t.total;  // stride between sweep members
   const int64_t row1 = a.row1;
   const int nb = t.n_ann + 2;
+  constexpr int kMB = (MT > 0) ? MT : 16;  // bilinear accumulators: one per mode + H_L
+  dfl bil_l{0.f, 0.f};
+  dfl bil_w[BIL ? kMB : 1];
+#pragma unroll
+  for (int q = 0; q < (BIL ? kMB : 1); ++q) bil_w[q] = dfl{0.f, 0.f};
 
   for (int64_t base = a.row0 + ((int64_t)blockIdx.x * kWarps + warp) * kWarpRows; base < row1;
        base += (int64_t)gridDim.x * kWarps * kWarpRows) {
@@ -266,6 +271,7 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
       }
 
       const float4 dg4 = a.diag[gr];
+      const dfl zf{a.zf.x, a.zf.y};
 #pragma unroll
       for (int b = 0; b < B; ++b) {
         const dfl sc{a.scale[b].x, a.scale[b].y};
@@ -273,16 +279,40 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
         const float4 xo = a.vin[(size_t)b * total + gr];
         const dfl hr = df_add(df_mul(dg, dfl{xo.x, xo.y}), df_mul(sc, acc_r[b]));
         const dfl hi = df_add(df_mul(dg, dfl{xo.z, xo.w}), df_mul(sc, acc_i[b]));
-        if (!final_stage) {
-          const float4 p0 = a.psif[(size_t)b * total + gr];
-          const dfl zf{a.zf.x, a.zf.y};
-          const dfl orr = df_add(dfl{p0.x, p0.y}, df_mul(zf, hi));
-          const dfl oi = df_add(dfl{p0.z, p0.w}, df_neg(df_mul(zf, hr)));
+        if (BIL && b == 0) {
+          // H_L x (two-body part at scale 1) and the pair vector of this row
+          const float4 pp = a.pair[gr];
+          const dfl lr = df_add(df_mul(dfl{dg4.z, dg4.w}, dfl{xo.x, xo.y}), acc_r[0]);
+          const dfl li = df_add(df_mul(dfl{dg4.z, dg4.w}, dfl{xo.z, xo.w}), acc_i[0]);
+          // Im(conj(p) h) = p.re h.im - p.im h.re
+          bil_l = df_add(bil_l, df_add(df_mul(dfl{pp.x, pp.y}, li), df_neg(df_mul(dfl{pp.z, pp.w}, lr))));
+          // Im(conj(x) p) = x.re p.im - x.im p.re, weighted by each occupation
+          const dfl tx = df_add(df_mul(dfl{xo.x, xo.y}, dfl{pp.z, pp.w}), df_neg(df_mul(dfl{xo.z, xo.w}, dfl{pp.x, pp.y})));
+#pragma unroll
+          for (int q = 0; q < kMB; ++q) {
+            if (q >= M) break;
+            bil_w[q] = df_add(bil_w[q], df_mul(dfl{(float)occ[q * kWarpRows], 0.f}, tx));
+          }
+        }
+        if (mode == 0 || mode == 2) {
+          dfl orr = df_mul(zf, hi), oi = df_neg(df_mul(zf, hr));  // z H x with z = -i zre
+          if (mode == 0) {
+            const float4 p0 = a.psif[(size_t)b * total + gr];
+            orr = df_add(dfl{p0.x, p0.y}, orr);
+            oi = df_add(dfl{p0.z, p0.w}, oi);
+          }
           a.out[(size_t)b * total + gr] = make_float4(orr.h, orr.l, oi.h, oi.l);
         } else {
           const double2 p0 = a.psi[(size_t)b * total + gr];
-          const double nr = p0.x + a.zre * df_to(hi);
-          const double ni = p0.y - a.zre * df_to(hr);
+          double nr = p0.x + a.zre * df_to(hi);
+          double ni = p0.y - a.zre * df_to(hr);
+          if (mode == 3) {
+            for (int k = 0; k < a.nbasef; ++k) {
+              const float4 e = a.basef[k][(size_t)b * total + gr];
+              nr += df_to(dfl{e.x, e.y});
+              ni += df_to(dfl{e.z, e.w});
+            }
+          }
           a.psi[(size_t)b * total + gr] = make_double2(nr, ni);
           const dfl fr = df_of(nr), fi = df_of(ni);
           a.out[(size_t)b * total + gr] = make_float4(fr.h, fr.l, fi.h, fi.l);
@@ -291,31 +321,56 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
     }
     __syncwarp();  // the tile's scratch is rewritten by the next tile
   }
+  if (BIL) {
+    // per-CTA sums of the bilinears in a fixed order: lanes by shuffles, warps in turn
+    __shared__ double red[kBlock / 32][17];
+    const int nq = M + 1;
+    for (int q = 0; q < nq; ++q) {
+      double v = (q == 0) ? df_to(bil_l) : 0.0;
+#pragma unroll
+      for (int u = 0; u < kMB; ++u)
+        if (q == u + 1) v = df_to(bil_w[u]);
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < nq) {
+      double sum = 0.0;
+      for (int w = 0; w < kWarps; ++w) sum += red[w][threadIdx.x];
+      a.partial[(size_t)blockIdx.x * nq + threadIdx.x] = sum;
+    }
+  }
 }
 
 // Launches one stage for mode count MT (0: any M) and the runtime batch size /
-// coupling type; *grid (if non-NULL) receives the persistent grid size.
+// coupling type / bilinear flag; *grid (if non-NULL) receives the grid size.
 template <int MT>
-int stage_launch_t(const Tables& t, const DfArgs& a, int final_stage, int B, bool cplx, cudaStream_t st,
+int stage_launch_t(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, bool bil, cudaStream_t st,
                    int* grid_out) {
   const size_t smem = ((t.blob_bytes - kSmemFrom(t) + 15) & ~15) + df_scratch_bytes(t.M, t.n_ann);
   int grid = 0, rc = QB_OK;
-#define QB_STAGE_CASE(BB, CC)                                                   \
+#define QB_STAGE_CASE(BB, CC, LL)                                               \
   {                                                                             \
-    auto k = stage_df_kernel<MT, BB, CC>;                                       \
+    auto k = stage_df_kernel<MT, BB, CC, LL>;                                   \
     rc = persistent_grid(k, smem, a.row1 - a.row0, &grid);                      \
     if (rc) return rc;                                                          \
-    k<<<grid, kBlock, smem, st>>>(t, a, final_stage);                           \
+    k<<<grid, kBlock, smem, st>>>(t, a, mode);                                  \
   }
-  if (cplx) {
+  if (bil) {
+    if (B != 1) return fail(QB_EUNSUPPORTED, "bilinear stages run one state at a time");
+    if (cplx)
+      QB_STAGE_CASE(1, true, true)
+    else
+      QB_STAGE_CASE(1, false, true)
+  } else if (cplx) {
     if (B != 1) return fail(QB_EUNSUPPORTED, "batched sweeps need a real coupling");
-    QB_STAGE_CASE(1, true)
+    QB_STAGE_CASE(1, true, false)
   } else {
     switch (B) {
-      case 1: QB_STAGE_CASE(1, false) break;
-      case 2: QB_STAGE_CASE(2, false) break;
-      case 4: QB_STAGE_CASE(4, false) break;
-      case 8: QB_STAGE_CASE(8, false) break;
+      case 1: QB_STAGE_CASE(1, false, false) break;
+      case 2: QB_STAGE_CASE(2, false, false) break;
+      case 4: QB_STAGE_CASE(4, false, false) break;
+      case 8: QB_STAGE_CASE(8, false, false) break;
       default: return fail(QB_EINVAL, "batch must be 1, 2, 4 or 8");
     }
   }
@@ -326,20 +381,20 @@ int stage_launch_t(const Tables& t, const DfArgs& a, int final_stage, int B, boo
 }
 
 // one explicit specialisation per translation unit (qb_stage_m*.cu)
-int stage_launch_m5(const Tables&, const DfArgs&, int, int, bool, cudaStream_t, int*);
-int stage_launch_m7(const Tables&, const DfArgs&, int, int, bool, cudaStream_t, int*);
-int stage_launch_m9(const Tables&, const DfArgs&, int, int, bool, cudaStream_t, int*);
-int stage_launch_m11(const Tables&, const DfArgs&, int, int, bool, cudaStream_t, int*);
-int stage_launch_any(const Tables&, const DfArgs&, int, int, bool, cudaStream_t, int*);
+int stage_launch_m5(const Tables&, const DfArgs&, int, int, bool, bool, cudaStream_t, int*);
+int stage_launch_m7(const Tables&, const DfArgs&, int, int, bool, bool, cudaStream_t, int*);
+int stage_launch_m9(const Tables&, const DfArgs&, int, int, bool, bool, cudaStream_t, int*);
+int stage_launch_m11(const Tables&, const DfArgs&, int, int, bool, bool, cudaStream_t, int*);
+int stage_launch_any(const Tables&, const DfArgs&, int, int, bool, bool, cudaStream_t, int*);
 
-inline int stage_launch(const Tables& t, const DfArgs& a, int final_stage, int B, bool cplx, cudaStream_t st,
-                        int* grid_out = nullptr) {
+inline int stage_launch(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, cudaStream_t st,
+                        int* grid_out = nullptr, bool bil = false) {
   switch (t.M) {
-    case 5: return stage_launch_m5(t, a, final_stage, B, cplx, st, grid_out);
-    case 7: return stage_launch_m7(t, a, final_stage, B, cplx, st, grid_out);
-    case 9: return stage_launch_m9(t, a, final_stage, B, cplx, st, grid_out);
-    case 11: return stage_launch_m11(t, a, final_stage, B, cplx, st, grid_out);
-    default: return stage_launch_any(t, a, final_stage, B, cplx, st, grid_out);
+    case 5: return stage_launch_m5(t, a, mode, B, cplx, bil, st, grid_out);
+    case 7: return stage_launch_m7(t, a, mode, B, cplx, bil, st, grid_out);
+    case 9: return stage_launch_m9(t, a, mode, B, cplx, bil, st, grid_out);
+    case 11: return stage_launch_m11(t, a, mode, B, cplx, bil, st, grid_out);
+    default: return stage_launch_any(t, a, mode, B, cplx, bil, st, grid_out);
   }
 }
 

@@ -2,8 +2,8 @@
 #include "qb_stage.cuh"
 
 namespace qb {
-int stage_launch_m11(const Tables& t, const DfArgs& a, int final_stage, int B, bool cplx, cudaStream_t st,
+int stage_launch_m11(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, bool bil, cudaStream_t st,
                    int* grid) {
-  return stage_launch_t<11>(t, a, final_stage, B, cplx, st, grid);
+  return stage_launch_t<11>(t, a, mode, B, cplx, bil, st, grid);
 }
 }  // namespace qb

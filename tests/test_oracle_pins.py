@@ -492,3 +492,38 @@ def test_count_terms_equals_dense_structure():
         Hd = orc.h_dense(space, s, w, L)
         nnz += int((np.abs(Hd - np.diag(np.diag(Hd))) > 0).sum()) + Hd.shape[0]
     assert orc.count_terms(space, L) == nnz
+
+
+@pytest.mark.parametrize("kind", ["Q", "PO"])
+def test_oracle_adjoint_gradient_matches_finite_differences(kind):
+    """The oracle's exact discrete adjoint (every state stored) against central
+    differences of the oracle's own loss, for the coupling scale, every w_p and
+    every Re z_k, Im z_k."""
+    M = 3
+    L0 = wl.contact_coupling(M, 1.0)
+    w = np.array([0.3, -0.2, 0.7])
+    z = np.array([0.6 + 0.2j, -0.4j, 0.5])
+    scale, dt, steps = -0.3, 0.02, 12
+    space = orc.Space(M, orc.all_sectors(M, 0, 9))
+
+    def loss_of(sc, wv, zv):
+        psi, _ = orc.coherent_state(space, zv)
+        psi = orc.rk4(space, wv, sc * L0, psi, dt, steps)
+        return orc.loss_and_seed(space, psi, kind)[0]
+
+    loss, gs, gw, gz = orc.adjoint_gradient(space, w, L0, scale, z, dt, steps, kind)
+    assert abs(loss - loss_of(scale, w, z)) < 1e-14
+    h = 1e-6
+    fd = (loss_of(scale + h, w, z) - loss_of(scale - h, w, z)) / (2 * h)
+    assert abs(gs - fd) < 1e-7 * max(1, abs(fd))
+    for q in range(M):
+        e = np.zeros(M)
+        e[q] = h
+        fd = (loss_of(scale, w + e, z) - loss_of(scale, w - e, z)) / (2 * h)
+        assert abs(gw[q] - fd) < 1e-7 * max(1, abs(fd))
+    for k in range(M):
+        for unit, part in ((1.0, gz[k].real), (1j, gz[k].imag)):
+            e = np.zeros(M, dtype=np.complex128)
+            e[k] = unit * h
+            fd = (loss_of(scale, w, z + e) - loss_of(scale, w, z - e)) / (2 * h)
+            assert abs(part - fd) < 1e-7 * max(1, abs(fd))
