@@ -47,6 +47,10 @@ extern "C" {
 
 #define QB_MAX_MODES 16
 
+/* Losses of qb_adjoint. */
+#define QB_LOSS_Q 0  /* Q at t_f (Eq. Qparam) */
+#define QB_LOSS_PO 1 /* principal eigenvalue lam_p of M_ij = <a_i^dag a_j> at t_f (Eq. POcriterion) */
+
 /* Breaktime flags (qb_breaktime). */
 #define QB_CROSSED 0
 #define QB_AT_START 1
@@ -194,6 +198,29 @@ int qb_evolve_observe(qb_space* space, void* d_psi, double dt, int64_t steps, in
  * QB_EUNSUPPORTED if even 32 CTAs would not (not reachable for M <= 16).
  * Same arguments, errors and synchronisation as qb_observables. */
 int qb_observables_noalloc(qb_space* space, const void* d_psi, qb_obs* out, void* stream);
+
+/* ---- adjoint gradients ---------------------------------------------------- */
+
+/* Bytes of device workspace qb_adjoint needs (256-byte aligned buffer): the
+ * checkpoints, steps / ckpt_every + 1 state vectors, plus 12 state-sized
+ * buffers and small reduction areas. */
+int64_t qb_adjoint_workspace_bytes(const qb_space* space, int64_t steps, int ckpt_every);
+
+/* Loss and gradients of a run from a coherent state.  The run: psi_0 = the
+ * coherent state of z[2M] (Eq. coherentStates) restricted to the space and
+ * renormalised; `steps` Horner RK4 steps of size dt under H = H_w + scale * H_L
+ * (the space's one-body part plus `scale` times its two-body part); the loss is
+ * Q (QB_LOSS_Q) or lam_p (QB_LOSS_PO) of the final state.  Outputs (host):
+ * *loss; *grad_scale = d loss / d scale; grad_w[M] = d loss / d w_p;
+ * grad_z[2M] = (d loss / d Re z_k, d loss / d Im z_k).  The gradient is the
+ * exact discrete adjoint of the RK4 map, run backwards with the costate;
+ * forward states are rebuilt by time reversal, psi_n ~ RK4 step of size -dt from
+ * psi_{n+1}, restarted from a stored checkpoint every ckpt_every steps
+ * (ckpt_every = 1 stores every state and reverses nothing).  d_work:
+ * qb_adjoint_workspace_bytes(space, steps, ckpt_every) bytes, 256-byte aligned. */
+int qb_adjoint(qb_space* space, const double* z, double scale, double dt, int64_t steps, int ckpt_every,
+               int loss_kind, double* loss, double* grad_scale, double* grad_w, double* grad_z, void* d_work,
+               void* stream);
 
 /* ---- breaktime and mean field (Sec. III A, IV C-D) ----------------------- */
 

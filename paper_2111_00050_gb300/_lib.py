@@ -9,6 +9,7 @@ from . import build as _build
 QB_OK, QB_EINVAL, QB_ENOMEM, QB_ECUDA, QB_ETIMEOUT, QB_EINTERNAL, QB_EUNSUPPORTED = range(7)
 QB_MAX_MODES = 16
 QB_CROSSED, QB_AT_START, QB_NOT_CROSSED = 0, 1, 2
+QB_LOSS_Q, QB_LOSS_PO = 0, 1
 
 _c_double_p = ctypes.POINTER(ctypes.c_double)
 _c_int_p = ctypes.POINTER(ctypes.c_int)
@@ -73,6 +74,10 @@ SIGNATURES = {
                                               ctypes.c_void_p]),
     "qb_evolve_observe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int64,
                                          ctypes.c_int, ctypes.POINTER(QbObs), ctypes.c_void_p, ctypes.c_void_p]),
+    "qb_adjoint_workspace_bytes": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]),
+    "qb_adjoint": (ctypes.c_int, [ctypes.c_void_p, _c_double_p, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                  ctypes.c_int, ctypes.c_int, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
+                                  ctypes.c_void_p, ctypes.c_void_p]),
     "qb_breaktime": (ctypes.c_int, [_c_double_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, _c_double_p,
                                     _c_int_p]),
     "qb_meanfield": (ctypes.c_int, [ctypes.POINTER(QbModel), _c_double_p, ctypes.c_double, ctypes.c_int64,

@@ -168,6 +168,27 @@ class Space:
                                     sc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(dt), int(steps),
                                     _dptr(work), _stream()))
 
+    # ---- adjoint
+    def adjoint(self, z, scale: float, dt: float, steps: int, ckpt_every: int = 1, loss: str = "Q",
+                work: Optional[torch.Tensor] = None) -> dict:
+        """qb_adjoint: loss (Q or PO = lam_p) at t_f and its gradients with respect to
+        the two-body scale, w_p and the coherent amplitudes z (d/dRe z + i d/dIm z)."""
+        kind = {"Q": _lib.QB_LOSS_Q, "PO": _lib.QB_LOSS_PO}[loss]
+        nbytes = int(lib().qb_adjoint_workspace_bytes(self._h, int(steps), int(ckpt_every)))
+        if work is None:
+            work = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        if work.numel() < nbytes or work.data_ptr() % 256:
+            raise ValueError("workspace too small or not 256-byte aligned")
+        zf = _c128_as_f64(z)
+        out_loss, gs = ctypes.c_double(), ctypes.c_double()
+        gw = np.zeros(self.M)
+        gz = np.zeros(2 * self.M)
+        dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        check(lib().qb_adjoint(self._h, dp(zf), float(scale), float(dt), int(steps), int(ckpt_every), kind,
+                               ctypes.byref(out_loss), ctypes.byref(gs), dp(gw), dp(gz), _dptr(work), _stream()))
+        return {"loss": out_loss.value, "grad_scale": gs.value, "grad_w": gw,
+                "grad_z": gz[0::2] + 1j * gz[1::2]}
+
     # ---- observables
     def observables(self, psi: torch.Tensor) -> dict:
         o = QbObs()

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libqb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["qb_host.cpp", "qb_kernels.cu", "qb_stage_m5.cu", "qb_stage_m7.cu", "qb_stage_m9.cu", "qb_stage_m11.cu",
+SOURCES = ["qb_host.cpp", "qb_kernels.cu", "qb_adjoint.cu", "qb_stage_m5.cu", "qb_stage_m7.cu", "qb_stage_m9.cu", "qb_stage_m11.cu",
            "qb_stage_any.cu"]
 HEADERS = ["qb_internal.h", "qb_device.cuh", "qb_stage.cuh", os.path.join("..", "..", "include", "qb.h")]
 

@@ -101,6 +101,8 @@ int launch_number(const Space& s, int64_t index, void* d_psi, void* stream);
 // raw moments: out[0]=norm, out[1]=<N>, out[2]=<H>, then a[M], Mij[M*M], aa[M*M] complex
 int launch_moments(Space& s, const void* d_psi, double* out_host, void* stream);
 int64_t workspace_bytes(const Space& s, int batch);
+// psi (FP64 complex) -> double-float copy (float4 per ket)
+int launch_to_df(const void* psi, void* psif, int64_t n, void* stream);
 // observables of Sec. II C-E from the raw moments (host)
 void derive(int M, const double* raw, qb_obs* out);
 int device_setup(Space& s);

@@ -701,6 +701,12 @@ int launch_rk4(Space& s, void* d_psi, int batch, const double* scale, double dt,
   return check_status(s, st);
 }
 
+int launch_to_df(const void* psi, void* psif, int64_t n, void* stream) {
+  to_df_kernel<<<1216, 256, 0, (cudaStream_t)stream>>>((const double2*)psi, (float4*)psif, n);
+  QB_CUDA(cudaGetLastError());
+  return QB_OK;
+}
+
 int launch_unrank(const Space& s, int64_t first, int64_t count, int* d_occ, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const size_t smem = row_smem(s.t);

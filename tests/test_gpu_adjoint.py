@@ -1,0 +1,73 @@
+"""Adjoint gradients (qb_adjoint) against the oracle's exact discrete adjoint
+(every state stored) and against central differences of the GPU loss.
+
+Tolerances: relative 1e-8 against the oracle with every state stored
+(ckpt_every = 1) and 1e-7 with time reversal between checkpoints; 1e-6 against
+central differences with h = 1e-6.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as orc
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _case():
+    M = 5
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((M, 2))
+    z = x[:, 0] + 1j * x[:, 1]
+    z *= math.sqrt(2.5 / np.sum(np.abs(z) ** 2))
+    w = wl.dispersion_quadratic(M)
+    L0 = wl.contact_coupling(M, 1.0)
+    return M, w, L0, z, -0.2, 2e-3, 60
+
+
+def _rel(a, b):
+    a, b = np.atleast_1d(a), np.atleast_1d(b)
+    return float(np.max(np.abs(a - b)) / max(1e-300, np.max(np.abs(b))))
+
+
+@pytest.mark.parametrize("kind", ["Q", "PO"])
+@pytest.mark.parametrize("ckpt", [1, 20])
+def test_adjoint_matches_oracle_discrete_adjoint(kind, ckpt):
+    import paper_2111_00050_gb300 as qb
+
+    M, w, L0, z, scale, dt, steps = _case()
+    qs = qb.Space(M, w, L0, 0, 10)
+    got = qs.adjoint(z, scale, dt, steps, ckpt_every=ckpt, loss=kind)
+    os_ = orc.Space(M, qs.sectors)
+    loss, gs, gw, gz = orc.adjoint_gradient(os_, w, L0, scale, z, dt, steps, kind)
+    tol = 1e-8 if ckpt == 1 else 1e-7
+    assert abs(got["loss"] - loss) <= 1e-10 * max(1, abs(loss))
+    assert _rel(got["grad_scale"], gs) <= tol
+    assert _rel(got["grad_w"], gw) <= tol
+    assert _rel(got["grad_z"], gz) <= tol
+
+
+def test_adjoint_matches_gpu_central_differences():
+    import paper_2111_00050_gb300 as qb
+
+    M, w, L0, z, scale, dt, steps = _case()
+    qs = qb.Space(M, w, L0, 0, 10)
+    got = qs.adjoint(z, scale, dt, steps, ckpt_every=10, loss="Q")
+    h = 1e-6
+
+    def loss(sc=scale, ww=w, zz=z):
+        sp = qb.Space(M, ww, L0, 0, 10)
+        return sp.adjoint(zz, sc, dt, steps, ckpt_every=steps, loss="Q")["loss"]
+
+    fd = (loss(sc=scale + h) - loss(sc=scale - h)) / (2 * h)
+    assert abs(got["grad_scale"] - fd) <= 1e-6 * max(1e-3, abs(fd))
+    e = np.zeros(M)
+    e[2] = h
+    fd = (loss(ww=w + e) - loss(ww=w - e)) / (2 * h)
+    assert abs(got["grad_w"][2] - fd) <= 1e-6 * max(1e-3, abs(fd))
+    ez = np.zeros(M, dtype=np.complex128)
+    ez[1] = 1j * h
+    fd = (loss(zz=z + ez) - loss(zz=z - ez)) / (2 * h)
+    assert abs(got["grad_z"][1].imag - fd) <= 1e-6 * max(1e-3, abs(fd))
