@@ -289,9 +289,17 @@ static int occupancy_cached(K kernel, size_t smem, int* per_sm, int* sms) {
       *sms = cache[i].sms;
       return QB_OK;
     }
-  int s = 0, per = 0;
+  int s = 0, per = 0, optin = 0;
   QB_CUDA(cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev));
-  QB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // The dynamic shared-memory limit is a property of the function shared by every
+  // space: raise it once to the device maximum so that no later call lowers it.
+  QB_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa;
+  QB_CUDA(cudaFuncGetAttributes(&fa, kernel));
+  if (smem + fa.sharedSizeBytes > (size_t)optin)
+    return fail(QB_EUNSUPPORTED, "tables too large for shared memory (reduce n_max or M)");
+  QB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin - (int)fa.sharedSizeBytes));
   QB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kBlock, smem));
   if (per < 1) return fail(QB_EUNSUPPORTED, "kernel does not fit on an SM with this table size");
   Entry e{fn, smem, dev, per, s};
