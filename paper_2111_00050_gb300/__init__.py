@@ -2,4 +2,4 @@
 restricted Fock space (arXiv:2111.00050).  The compute lives in libqb
 (csrc/, C ABI in include/qb.h); this package is its thin Python binding."""
 from ._lib import (QB_AT_START, QB_CROSSED, QB_NOT_CROSSED, QbError, lib)  # noqa: F401
-from .api import Space, breaktime, meanfield  # noqa: F401
+from .api import AdjointLoss, Space, adjoint_loss, breaktime, meanfield  # noqa: F401

@@ -221,3 +221,32 @@ def meanfield(M: int, w, L, z0, dt: float, steps: int, every: int = 1) -> np.nda
     check(lib().qb_meanfield(ctypes.byref(m), z.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(dt),
                              int(steps), int(every), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return out.view(np.complex128).reshape(rows, M)
+
+
+class AdjointLoss(torch.autograd.Function):
+    """Loss (Q or lam_p at t_f) of an RK4 run from a coherent state, with gradients
+    by qb_adjoint.  Inputs: the two-body scale (0-d float64 tensor), the dispersion
+    w (float64 [M]) and the coherent amplitudes z (complex128 [M]); the space holds
+    the unit coupling L0.  z.grad follows torch's convention for real losses,
+    d loss / d Re z + i d loss / d Im z."""
+
+    @staticmethod
+    def forward(ctx, scale, w, z, spec):
+        space = Space(spec["M"], w.detach().cpu().numpy(), spec["L0"], spec["n_min"], spec["n_max"],
+                      spec.get("p_list"))
+        r = space.adjoint(z.detach().cpu().numpy(), float(scale), spec["dt"], spec["steps"],
+                          spec.get("ckpt_every", 1), spec.get("loss", "Q"))
+        ctx.grads = (torch.tensor(r["grad_scale"], dtype=torch.float64),
+                     torch.from_numpy(np.asarray(r["grad_w"], dtype=np.float64)),
+                     torch.from_numpy(np.asarray(r["grad_z"], dtype=np.complex128)))
+        return torch.tensor(r["loss"], dtype=torch.float64)
+
+    @staticmethod
+    def backward(ctx, g):
+        gs, gw, gz = ctx.grads
+        return g * gs, g * gw, g * gz, None
+
+
+def adjoint_loss(scale, w, z, **spec):
+    """Differentiable loss of a coherent-state run: see AdjointLoss."""
+    return AdjointLoss.apply(scale, w, z, spec)

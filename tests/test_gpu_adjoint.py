@@ -71,3 +71,23 @@ def test_adjoint_matches_gpu_central_differences():
     ez[1] = 1j * h
     fd = (loss(zz=z + ez) - loss(zz=z - ez)) / (2 * h)
     assert abs(got["grad_z"][1].imag - fd) <= 1e-6 * max(1e-3, abs(fd))
+
+
+def test_autograd_function_returns_adjoint_gradients():
+    import torch
+
+    import paper_2111_00050_gb300 as qb
+
+    M, w, L0, z, scale, dt, steps = _case()
+    s_t = torch.tensor(scale, dtype=torch.float64, requires_grad=True)
+    w_t = torch.tensor(w, dtype=torch.float64, requires_grad=True)
+    z_t = torch.tensor(z, dtype=torch.complex128, requires_grad=True)
+    loss = qb.adjoint_loss(s_t, w_t, z_t, M=M, L0=L0, n_min=0, n_max=10, dt=dt, steps=steps, ckpt_every=20,
+                           loss="Q")
+    loss.backward()
+    os_ = orc.Space(M, qb.Space(M, w, L0, 0, 10).sectors)
+    ref = orc.adjoint_gradient(os_, w, L0, scale, z, dt, steps, "Q")
+    assert abs(loss.item() - ref[0]) <= 1e-10
+    assert _rel(s_t.grad.item(), ref[1]) <= 1e-7
+    assert _rel(w_t.grad.numpy(), ref[2]) <= 1e-7
+    assert _rel(z_t.grad.numpy(), ref[3]) <= 1e-7
