@@ -178,6 +178,76 @@ def cpu_baseline(W, seconds_cap: float = 20.0):
             "sample": f"{n} RK4 step(s) of sectors N={N} ({space.total} kets, {terms} terms/H psi) of {W.name}"}
 
 
+def adjoint_extra(qb, torch, steps: int = 20, ckpt_every: int = 10):
+    """Adjoint workload (M=5, contact C=-0.1, complex-Gaussian alpha scaled to n_tot=40,
+    N <= 77: 390 sectors, 27.3M kets): forward RK4 time per step against the time per
+    step of qb_adjoint (forward pass with checkpoints + loss + backward costate pass)."""
+    W = wl.adjoint_coherent()
+    L0 = wl.contact_coupling(W.M, 1.0)
+    qs = qb.Space(W.M, W.w, L0, 0, W.n_max)
+    psi = qs.empty_state()
+    qs.init_coherent(W.z, psi)
+    work = qs.workspace(1)
+    qs.evolve_batch(psi, [-0.1], W.dt, 2, work)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    qs.evolve_batch(psi, [-0.1], W.dt, steps, work)
+    torch.cuda.synchronize()
+    fwd = (time.perf_counter() - t0) / steps
+    del psi, work
+    nbytes = int(qb.lib().qb_adjoint_workspace_bytes(qs._h, steps, ckpt_every))
+    aw = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    qs.adjoint(W.z, -0.1, W.dt, 2, ckpt_every=2, loss="Q", work=aw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = qs.adjoint(W.z, -0.1, W.dt, steps, ckpt_every=ckpt_every, loss="Q", work=aw)
+    torch.cuda.synchronize()
+    adj = (time.perf_counter() - t0) / steps
+    out = {"workload": W.name, "kets": qs.total, "sectors": qs.n_sectors, "steps": steps, "ckpt_every": ckpt_every,
+           "forward_ms_per_step": fwd * 1e3, "adjoint_ms_per_step": adj * 1e3, "adjoint_over_forward": adj / fwd,
+           "loss_Q": r["loss"], "grad_scale": r["grad_scale"]}
+    del aw, qs
+    torch.cuda.empty_cache()
+    return out
+
+
+def sweep_extra(qb, torch, steps: int = 3):
+    """8-member coupling sweep on the M=11, N=20, P=0 sector (2,731,365 kets, number state
+    (...,7,6,7,...), w=|p|, C_k = -0.005 k): one batched launch per stage for all 8
+    members against the members one at a time."""
+    W = wl.large_sector()
+    qs = qb.Space(W.M, W.w, W.L, 20, 20, [0])
+    terms = qs.terms()[0]
+    B = len(W.sweep)
+    psi = torch.empty((B, qs.total), dtype=torch.complex128, device="cuda")
+    for b in range(B):
+        qs.init_number(W.occ, psi[b])
+    work = qs.workspace(B)
+    qs.evolve_batch(psi, W.sweep, W.dt, 1, work)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    qs.evolve_batch(psi, W.sweep, W.dt, steps, work)
+    e1.record()
+    torch.cuda.synchronize()
+    batched = e0.elapsed_time(e1) / steps
+    one = psi[0].clone()
+    w1 = qs.workspace(1)
+    e0.record()
+    for b in range(B):
+        qs.evolve_batch(one, [W.sweep[b]], W.dt, steps, w1)
+    e1.record()
+    torch.cuda.synchronize()
+    separate = e0.elapsed_time(e1) / steps
+    out = {"workload": W.name + "_sweep8", "kets": qs.total, "members": B, "terms_per_hpsi": terms,
+           "batched_ms_per_step": batched, "separate_ms_per_step": separate,
+           "batched_member_terms_per_s": 4 * terms * B / (batched * 1e-3),
+           "separate_member_terms_per_s": 4 * terms * B / (separate * 1e-3), "batched_speedup": separate / batched}
+    del psi, work, one, w1, qs
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -187,6 +257,7 @@ def main():
     ap.add_argument("--config", default="batched_coherent")
     ap.add_argument("--n-tot", type=int, default=16, help="mean occupation of the batched coherent workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the adjoint and sweep measurements")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -315,6 +386,11 @@ def main():
         "roofline": roofline,
         "e2e": e2e,
     }
+    if not args.no_extras:
+        del work, psi
+        torch.cuda.empty_cache()
+        line["adjoint"] = adjoint_extra(qb, torch)
+        line["sweep"] = sweep_extra(qb, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W)
     if rank == 0:
