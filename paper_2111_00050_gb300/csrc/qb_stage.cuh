@@ -28,6 +28,9 @@
 #ifndef QB_UNROLL_PARTNERS
 #define QB_UNROLL_PARTNERS 1
 #endif
+#ifndef QB_CONVERGENT_PAIRS
+#define QB_CONVERGENT_PAIRS 1
+#endif
 
 namespace qb {
 
@@ -169,6 +172,23 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
 #pragma unroll
       for (int b = 0; b < B; ++b) acc_r[b] = acc_i[b] = dfl{0.f, 0.f};
 
+#if QB_CONVERGENT_PAIRS
+      // One annihilation pair (r <= s, n_r (n_s - [r=s]) > 0) per iteration.  Kets of
+      // a round have (nearly) the same pair count, so the iterations line up across
+      // the warp; the search for the next r is a short inner loop.
+      const int np = __popc(occmask);
+      const int npairs = np * (np - 1) / 2 + __popc(twomask);
+      uint32_t rm = occmask, smask = 0;
+      int r = 0;
+      for (int it = 0; it < npairs; ++it) {
+        while (smask == 0 && rm != 0) {
+          r = __ffs(rm) - 1;
+          rm &= rm - 1;
+          smask = occmask & (~0u << r);
+          if (!((twomask >> r) & 1u)) smask &= ~(1u << r);
+        }
+        if (smask == 0) break;  // not reached: npairs counts exactly the pairs found here
+#else
       uint32_t rm = occmask, smask = 0;
       int r = 0;
       while (true) {
@@ -180,6 +200,7 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
           if (!((twomask >> r) & 1u)) smask &= ~(1u << r);
           if (smask == 0) continue;
         }
+#endif
         const int s = __ffs(smask) - 1;
         smask &= smask - 1;
         const int ai = v.pairidx[r * 16 + s];
