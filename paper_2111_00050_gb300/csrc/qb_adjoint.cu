@@ -133,8 +133,7 @@ __global__ void __launch_bounds__(kBlock) seed_kernel(const Tables t, const Seed
     r.x *= a.inv_norm;
     r.y *= a.inv_norm;
     a.lam[g] = r;
-    const float hr = __double2float_rn(r.x), hi = __double2float_rn(r.y);
-    a.lamf[g] = make_float4(hr, __double2float_rn(r.x - (double)hr), hi, __double2float_rn(r.y - (double)hi));
+    a.lamf[g] = df_pack(df_of(r.x), df_of(r.y));
   }
 }
 

@@ -219,6 +219,69 @@ __device__ __forceinline__ dfl df_renorm(dfl a) {
   return {h, __fsub_rn(a.l, __fsub_rn(h, a.h))};
 }
 
+// A double-float complex value is stored as float4 (re.hi, im.hi, re.lo, im.lo),
+// so that a load yields the packed pairs (re.hi, im.hi) and (re.lo, im.lo).
+__device__ __forceinline__ float4 df_pack(dfl re, dfl im) { return make_float4(re.h, im.h, re.l, im.l); }
+__device__ __forceinline__ dfl df_re(float4 v) { return {v.x, v.z}; }
+__device__ __forceinline__ dfl df_im(float4 v) { return {v.y, v.w}; }
+
+// Packed pairs of fp32 (lane 0 in the low word) and the correctly rounded
+// two-lane arithmetic of sm_100+ (add/sub/mul/fma .rn.f32x2).
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2_pack(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f2 v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+  f2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// Two double-float numbers side by side: hi words (lane0, lane1), lo words likewise.
+struct dfc {
+  f2 h, l;
+};
+
+// acc += c * x lane by lane, with per-lane double-float coefficient c = (ch, cl)
+// (nch = -ch) and double-float x = (xh, xl): the fma-based exact product error and
+// TwoSum of the scalar df_fma, two lanes per instruction.
+__device__ __forceinline__ void dfc_fma(dfc& acc, f2 ch, f2 nch, f2 cl, f2 xh, f2 xl) {
+  const f2 pn = f2_mul(nch, xh);  // -fl(c.h x.h)
+  f2 e = f2_fma(ch, xh, pn);      // exact error of that product
+  e = f2_fma(ch, xl, e);
+  e = f2_fma(cl, xh, e);
+  const f2 s = f2_sub(acc.h, pn);  // acc.h + p
+  const f2 bb = f2_sub(s, acc.h);
+  const f2 err = f2_sub(f2_sub(acc.h, f2_sub(s, bb)), f2_add(pn, bb));  // (a - (s - bb)) + (p - bb)
+  acc.h = s;
+  acc.l = f2_add(acc.l, f2_add(err, e));
+}
+
+__device__ __forceinline__ dfc dfc_renorm(dfc a) {
+  const f2 h = f2_add(a.h, a.l);
+  return {h, f2_sub(a.l, f2_sub(h, a.h))};
+}
+
 // Arguments of one stage launch.  With z = -i zre and x the gathered vector
 // (vin), the epilogue writes, by `mode`:
 //   0  out  = psif + z H x                        (forward Horner stage, d > 1)

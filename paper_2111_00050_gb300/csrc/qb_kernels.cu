@@ -177,8 +177,7 @@ __global__ void __launch_bounds__(kBlock) hpsi_kernel(const Tables t, const Stag
 __global__ void to_df_kernel(const double2* psi, float4* out, int64_t n) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     const double2 x = psi[k];
-    const dfl r = df_of(x.x), i = df_of(x.y);
-    out[k] = make_float4(r.h, r.l, i.h, i.l);
+    out[k] = df_pack(df_of(x.x), df_of(x.y));
   }
 }
 

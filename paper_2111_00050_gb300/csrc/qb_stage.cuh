@@ -31,6 +31,9 @@
 #ifndef QB_CONVERGENT_PAIRS
 #define QB_CONVERGENT_PAIRS 1
 #endif
+#ifndef QB_UNRANK_FROM_E
+#define QB_UNRANK_FROM_E 1
+#endif
 
 namespace qb {
 
@@ -45,6 +48,7 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
   load_blob_from(t, smem_raw, t.o_E);  // the only CTA-wide barrier: warps run independently afterwards
   unsigned char* smem = smem_raw - t.o_E;
   const uint32_t* gcnt = reinterpret_cast<const uint32_t*>(t.blob + t.o_cnt);
+  (void)gcnt;
 #else
   load_blob(t, smem_raw);  // the only CTA-wide barrier: warps run independently afterwards
   unsigned char* smem = smem_raw;
@@ -56,6 +60,7 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
   const uint4* dl4 = reinterpret_cast<const uint4*>(v.delta);
   const int M = (MT > 0) ? MT : t.M;
   const int V = t.nmax + 1, twoM = 2 * M;
+  (void)V;
   constexpr int kWarps = kBlock / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char* sp = smem_raw + ((t.blob_bytes - kSmemFrom(t) + 15) & ~15) + (size_t)warp * df_warp_scratch_bytes(M, t.n_ann);
@@ -93,9 +98,17 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
         int left = (int)(g - off);
         for (int m = 0; m < M - 1; ++m) {
           int val = 0, kk = kr;
+#if QB_UNRANK_FROM_E
+          // cnt[m+1][n][k] = E_{m+2}(n + 1, k + m + 1), already in shared memory; for
+          // the last step cnt[M-1][n][k] = [n + k = 0 mod M] (one mode left)
+          const int32_t* erow = v.E + (min(m + 2, M - 1) * t.rem_w + 3) * twoM + m + 1;  // used for m + 2 < M
+          while (true) {
+            const int c = (m + 2 < M) ? erow[(rem - val) * twoM + kk] : (((rem - val + kk) % M) == 0 ? 1 : 0);
+#else
           const uint32_t* crow = gcnt + (size_t)(m + 1) * V * M;
           while (true) {
             const int c = (int)crow[(rem - val) * M + kk];
+#endif
             if (left < c || val == rem) break;
             left -= c;
             ++val;
@@ -168,9 +181,9 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
         twomask |= (nm >= 2 ? 1u : 0u) << m;
       }
       const float4* vsec = a.vin + off;
-      dfl acc_r[B], acc_i[B];
+      dfc acc[B];  // (re, im) of the off-diagonal sum, double-float, packed
 #pragma unroll
-      for (int b = 0; b < B; ++b) acc_r[b] = acc_i[b] = dfl{0.f, 0.f};
+      for (int b = 0; b < B; ++b) acc[b] = dfc{0ull, 0ull};
 
 #if QB_CONVERGENT_PAIRS
       // One annihilation pair (r <= s, n_r (n_s - [r=s]) > 0) per iteration.  Kets of
@@ -242,10 +255,9 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
 #pragma unroll
             for (int c = 0; c < kC; ++c) x[c] = __ldg(vsec + (size_t)b * total + rkc[c]);
 #pragma unroll
-            for (int c = 0; c < kC; ++c) {
-              df_fma(acc_r[b], crc[c], dfl{x[c].x, x[c].y});
-              df_fma(acc_i[b], crc[c], dfl{x[c].z, x[c].w});
-            }
+            for (int c = 0; c < kC; ++c)
+              dfc_fma(acc[b], f2_pack(crc[c].h, crc[c].h), f2_pack(-crc[c].h, -crc[c].h),
+                      f2_pack(crc[c].l, crc[c].l), f2_pack(x[c].x, x[c].y), f2_pack(x[c].z, x[c].w));
           }
         } else {
           const int j1 = v.ann[ai + 1];
@@ -273,42 +285,43 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
   #pragma unroll
             for (int b = 0; b < B; ++b) {
               const float4 x = __ldg(vsec + (size_t)b * total + rk);
-              df_fma(acc_r[b], cr, dfl{x.x, x.y});
-              df_fma(acc_i[b], cr, dfl{x.z, x.w});
+              const f2 xh = f2_pack(x.x, x.y), xl = f2_pack(x.z, x.w);
+              dfc_fma(acc[b], f2_pack(cr.h, cr.h), f2_pack(-cr.h, -cr.h), f2_pack(cr.l, cr.l), xh, xl);
               if (CPLX) {
+                // + (-c_i x_im, c_i x_re): lanes of x swapped, coefficient (-c_i, c_i)
                 const dfl ci = df_mul(dfl{gf.z, gf.w}, AB);
-                df_fma(acc_r[b], df_neg(ci), dfl{x.z, x.w});
-                df_fma(acc_i[b], ci, dfl{x.x, x.y});
+                dfc_fma(acc[b], f2_pack(-ci.h, ci.h), f2_pack(ci.h, -ci.h), f2_pack(-ci.l, ci.l),
+                        f2_pack(x.y, x.x), f2_pack(x.w, x.z));
               }
             }
           }
         }
         // keep |lo| below an ulp of hi between pairs
 #pragma unroll
-        for (int b = 0; b < B; ++b) {
-          acc_r[b] = df_renorm(acc_r[b]);
-          acc_i[b] = df_renorm(acc_i[b]);
-        }
+        for (int b = 0; b < B; ++b) acc[b] = dfc_renorm(acc[b]);
       }
 
       const float4 dg4 = a.diag[gr];
       const dfl zf{a.zf.x, a.zf.y};
 #pragma unroll
       for (int b = 0; b < B; ++b) {
+        dfl acc_r, acc_i;
+        f2_unpack(acc[b].h, acc_r.h, acc_i.h);
+        f2_unpack(acc[b].l, acc_r.l, acc_i.l);
         const dfl sc{a.scale[b].x, a.scale[b].y};
         const dfl dg = df_add(dfl{dg4.x, dg4.y}, df_mul(sc, dfl{dg4.z, dg4.w}));
         const float4 xo = a.vin[(size_t)b * total + gr];
-        const dfl hr = df_add(df_mul(dg, dfl{xo.x, xo.y}), df_mul(sc, acc_r[b]));
-        const dfl hi = df_add(df_mul(dg, dfl{xo.z, xo.w}), df_mul(sc, acc_i[b]));
+        const dfl hr = df_add(df_mul(dg, df_re(xo)), df_mul(sc, acc_r));
+        const dfl hi = df_add(df_mul(dg, df_im(xo)), df_mul(sc, acc_i));
         if (BIL && b == 0) {
           // H_L x (two-body part at scale 1) and the pair vector of this row
           const float4 pp = a.pair[gr];
-          const dfl lr = df_add(df_mul(dfl{dg4.z, dg4.w}, dfl{xo.x, xo.y}), acc_r[0]);
-          const dfl li = df_add(df_mul(dfl{dg4.z, dg4.w}, dfl{xo.z, xo.w}), acc_i[0]);
+          const dfl lr = df_add(df_mul(dfl{dg4.z, dg4.w}, df_re(xo)), acc_r);
+          const dfl li = df_add(df_mul(dfl{dg4.z, dg4.w}, df_im(xo)), acc_i);
           // Im(conj(p) h) = p.re h.im - p.im h.re
-          bil_l = df_add(bil_l, df_add(df_mul(dfl{pp.x, pp.y}, li), df_neg(df_mul(dfl{pp.z, pp.w}, lr))));
+          bil_l = df_add(bil_l, df_add(df_mul(df_re(pp), li), df_neg(df_mul(df_im(pp), lr))));
           // Im(conj(x) p) = x.re p.im - x.im p.re, weighted by each occupation
-          const dfl tx = df_add(df_mul(dfl{xo.x, xo.y}, dfl{pp.z, pp.w}), df_neg(df_mul(dfl{xo.z, xo.w}, dfl{pp.x, pp.y})));
+          const dfl tx = df_add(df_mul(df_re(xo), df_im(pp)), df_neg(df_mul(df_im(xo), df_re(pp))));
 #pragma unroll
           for (int q = 0; q < kMB; ++q) {
             if (q >= M) break;
@@ -319,10 +332,10 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
           dfl orr = df_mul(zf, hi), oi = df_neg(df_mul(zf, hr));  // z H x with z = -i zre
           if (mode == 0) {
             const float4 p0 = a.psif[(size_t)b * total + gr];
-            orr = df_add(dfl{p0.x, p0.y}, orr);
-            oi = df_add(dfl{p0.z, p0.w}, oi);
+            orr = df_add(df_re(p0), orr);
+            oi = df_add(df_im(p0), oi);
           }
-          a.out[(size_t)b * total + gr] = make_float4(orr.h, orr.l, oi.h, oi.l);
+          a.out[(size_t)b * total + gr] = df_pack(orr, oi);
         } else {
           const double2 p0 = a.psi[(size_t)b * total + gr];
           double nr = p0.x + a.zre * df_to(hi);
@@ -330,13 +343,12 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
           if (mode == 3) {
             for (int k = 0; k < a.nbasef; ++k) {
               const float4 e = a.basef[k][(size_t)b * total + gr];
-              nr += df_to(dfl{e.x, e.y});
-              ni += df_to(dfl{e.z, e.w});
+              nr += df_to(df_re(e));
+              ni += df_to(df_im(e));
             }
           }
           a.psi[(size_t)b * total + gr] = make_double2(nr, ni);
-          const dfl fr = df_of(nr), fi = df_of(ni);
-          a.out[(size_t)b * total + gr] = make_float4(fr.h, fr.l, fi.h, fi.l);
+          a.out[(size_t)b * total + gr] = df_pack(df_of(nr), df_of(ni));
         }
       }
     }
