@@ -482,6 +482,7 @@ void qb_space_free(qb_space* space) {
   cudaFree(sp->d_secOf);
   cudaFree(sp->d_scratch);
   cudaFree(sp->d_diag);
+  if (sp->capture_stream) cudaStreamDestroy(sp->capture_stream);
   delete sp;
 }
 

@@ -79,6 +79,7 @@ struct Space {
   float4* d_diag = nullptr;     // per ket: one-body and two-body diagonal as double-float pairs
   int64_t scratch_doubles = 0;
   Tables t{};
+  cudaStream_t capture_stream = nullptr;  // private stream on which RK4 chunks are captured into graphs
   int device = 0;
   int grid_hpsi = 0;  // persistent grid sizes per kernel family
 };

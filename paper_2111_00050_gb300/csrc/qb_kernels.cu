@@ -635,23 +635,18 @@ int launch_hpsi(const Space& s, const void* d_v, void* d_out, void* stream) {
 
 // plain = true: one launch per sector per stage (the comparison baseline of
 // qb_evolve_plain); otherwise one launch per stage covers every sector.
+// Steps are issued one launch per stage for every sector (plain = false) or one
+// launch per sector per stage (plain = true, the comparison baseline of
+// qb_evolve_plain).  The batched path captures chunks of kGraphSteps steps into
+// a CUDA graph once the first step has run (and the launch geometry is cached),
+// and replays the graph; a capture that the runtime refuses falls back to issuing
+// the launches directly.
+constexpr int64_t kGraphSteps = 32;
+
 template <int B>
-static int rk4_loop(Space& s, double2* psi, const double* scale, double dt, int64_t steps, float4* w1, float4* w2,
-                    float4* psif, cudaStream_t st, bool plain = false) {
-  const int64_t n = (int64_t)B * s.t.total;
+static int rk4_issue(Space& s, DfArgs& a, double dt, int64_t steps, float4* w1, float4* w2, float4* psif,
+                     cudaStream_t st, bool plain) {
   const bool cplx = s.t.is_complex != 0;
-  to_df_kernel<<<1216, 256, 0, st>>>(psi, psif, n);
-  QB_CUDA(cudaGetLastError());
-  DfArgs a{};
-  for (int b = 0; b < B; ++b) {
-    const float h = (float)scale[b];
-    a.scale[b] = make_float2(h, (float)(scale[b] - (double)h));
-  }
-  a.diag = s.d_diag;
-  a.psi = psi;
-  a.psif = psif;
-  a.status = reinterpret_cast<int*>(s.d_scratch);
-  a.nbasef = 0;
   for (int64_t it = 0; it < steps; ++it) {
     // Horner: v = psi + z/4 H psi; v = psi + z/3 H v; v = psi + z/2 H v; psi = psi + z H v
     const float4* in[4] = {psif, w1, w2, w1};
@@ -678,6 +673,60 @@ static int rk4_loop(Space& s, double2* psi, const double* scale, double dt, int6
     }
   }
   return QB_OK;
+}
+
+template <int B>
+static int rk4_loop(Space& s, double2* psi, const double* scale, double dt, int64_t steps, float4* w1, float4* w2,
+                    float4* psif, cudaStream_t st, bool plain = false) {
+  const int64_t n = (int64_t)B * s.t.total;
+  to_df_kernel<<<1216, 256, 0, st>>>(psi, psif, n);
+  QB_CUDA(cudaGetLastError());
+  DfArgs a{};
+  for (int b = 0; b < B; ++b) {
+    const float h = (float)scale[b];
+    a.scale[b] = make_float2(h, (float)(scale[b] - (double)h));
+  }
+  a.diag = s.d_diag;
+  a.psi = psi;
+  a.psif = psif;
+  a.status = reinterpret_cast<int*>(s.d_scratch);
+  a.nbasef = 0;
+  if (plain || steps < 2 * kGraphSteps) return rk4_issue<B>(s, a, dt, steps, w1, w2, psif, st, plain);
+  // first step directly: fills the launch-geometry cache outside any capture
+  int rc = rk4_issue<B>(s, a, dt, 1, w1, w2, psif, st, false);
+  if (rc) return rc;
+  int64_t left = steps - 1;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool captured = false;
+  // capture on the space's private stream (the caller's may be the legacy default
+  // stream, which cannot capture); the graph is launched on the caller's stream
+  if (!s.capture_stream) QB_CUDA(cudaStreamCreateWithFlags(&s.capture_stream, cudaStreamNonBlocking));
+  if (cudaStreamBeginCapture(s.capture_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    rc = rk4_issue<B>(s, a, dt, kGraphSteps, w1, w2, psif, s.capture_stream, false);
+    const cudaError_t ec = cudaStreamEndCapture(s.capture_stream, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (ec == cudaSuccess && graph && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) captured = true;
+  }
+  cudaGetLastError();  // a refused capture leaves a sticky-free error; clear it
+  if (captured) {
+    for (; left >= kGraphSteps; left -= kGraphSteps) {
+      const cudaError_t e = cudaGraphLaunch(exec, st);
+      if (e != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        return fail(QB_ECUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+      }
+    }
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+  } else if (graph) {
+    cudaGraphDestroy(graph);
+  }
+  return rk4_issue<B>(s, a, dt, left, w1, w2, psif, st, false);
 }
 
 int launch_rk4(Space& s, void* d_psi, int batch, const double* scale, double dt, int64_t steps, void* d_work,
