@@ -164,6 +164,16 @@ int qb_evolve(qb_space* space, void* d_psi, double dt, int64_t steps, void* d_wo
 int qb_evolve_batch(qb_space* space, void* d_psi, int batch, const double* scale, double dt, int64_t steps,
                     void* d_work, void* stream);
 
+/* Execution tuning of qb_evolve for one state vector.  Leading sectors (in the
+ * order of qb_space_sectors) of at most resident_max_kets kets run
+ * shared-memory resident: each CTA takes such sectors from a work list and
+ * advances them through every step of the call in one launch, on a side stream
+ * beside the stage-by-stage launches of the larger sectors (which are captured
+ * into CUDA graphs in chunks of 32 steps).  0 disables the resident path; the
+ * default is 1024; values above what shared memory holds are clipped.  Results
+ * do not depend on the setting: every ket goes through the same arithmetic. */
+int qb_space_set_resident_max(qb_space* space, int resident_max_kets);
+
 /* The same RK4 evolution as qb_evolve with one kernel launch per sector per
  * stage instead of one per stage for every sector: the per-sector scheme of
  * Sec. III B taken literally, kept as the comparison baseline of the batched

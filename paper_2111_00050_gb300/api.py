@@ -156,6 +156,33 @@ class Space:
         work = self.workspace(1) if work is None else work
         check(lib().qb_evolve(self._h, _dptr(psi), float(dt), int(steps), _dptr(work), _stream()))
 
+    def set_resident_max(self, kets: int) -> None:
+        """qb_space_set_resident_max: sectors up to `kets` kets run shared-memory resident (0: never)."""
+        check(lib().qb_space_set_resident_max(self._h, int(kets)))
+
+    def autotune(self, dt: float, psi: torch.Tensor, candidates=(0, 256, 1024, 4096), steps: int = 2,
+                 work: Optional[torch.Tensor] = None) -> int:
+        """Times `steps` RK4 steps from a copy of psi for each resident threshold in
+        `candidates` (CUDA events) and keeps the fastest; returns it."""
+        work = self.workspace(1) if work is None else work
+        trial = psi.clone()
+        best, best_ms = None, float("inf")
+        for kets in candidates:
+            self.set_resident_max(kets)
+            trial.copy_(psi)
+            self.evolve(trial, dt, 1, work)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            trial.copy_(psi)
+            e0.record()
+            self.evolve(trial, dt, steps, work)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            if ms < best_ms:
+                best, best_ms = kets, ms
+        self.set_resident_max(best)
+        return best
+
     def evolve_plain(self, psi: torch.Tensor, dt: float, steps: int, work: Optional[torch.Tensor] = None) -> None:
         work = self.workspace(1) if work is None else work
         check(lib().qb_evolve_plain(self._h, _dptr(psi), float(dt), int(steps), _dptr(work), _stream()))

@@ -483,6 +483,9 @@ void qb_space_free(qb_space* space) {
   cudaFree(sp->d_scratch);
   cudaFree(sp->d_diag);
   if (sp->capture_stream) cudaStreamDestroy(sp->capture_stream);
+  if (sp->side_stream) cudaStreamDestroy(sp->side_stream);
+  if (sp->ev_fork) cudaEventDestroy(sp->ev_fork);
+  if (sp->ev_join) cudaEventDestroy(sp->ev_join);
   delete sp;
 }
 
@@ -657,6 +660,14 @@ int qb_evolve_batch(qb_space* space, void* d_psi, int batch, const double* scale
   for (int b = 0; b < batch; ++b)
     if (!std::isfinite(scale[b])) return fail(QB_EINVAL, "scale has a non-finite entry");
   return launch_rk4(*sp, d_psi, batch, scale, dt, steps, d_work, stream);
+}
+
+int qb_space_set_resident_max(qb_space* space, int resident_max_kets) {
+  Space* sp = reinterpret_cast<Space*>(space);
+  if (!sp) return fail(QB_EINVAL, "space is NULL");
+  if (resident_max_kets < 0) return fail(QB_EINVAL, "resident_max_kets must be >= 0");
+  sp->resident_max_kets = resident_max_kets;
+  return QB_OK;
 }
 
 int qb_evolve_plain(qb_space* space, void* d_psi, double dt, int64_t steps, void* d_work, void* stream) {

@@ -80,6 +80,9 @@ struct Space {
   int64_t scratch_doubles = 0;
   Tables t{};
   cudaStream_t capture_stream = nullptr;  // private stream on which RK4 chunks are captured into graphs
+  cudaStream_t side_stream = nullptr;     // resident small sectors run here, beside the large ones
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int resident_max_kets = 1024;           // sectors up to this size run shared-memory resident
   int device = 0;
   int grid_hpsi = 0;  // persistent grid sizes per kernel family
 };

@@ -645,7 +645,7 @@ constexpr int64_t kGraphSteps = 32;
 
 template <int B>
 static int rk4_issue(Space& s, DfArgs& a, double dt, int64_t steps, float4* w1, float4* w2, float4* psif,
-                     cudaStream_t st, bool plain) {
+                     cudaStream_t st, bool plain, int64_t row0 = 0) {
   const bool cplx = s.t.is_complex != 0;
   for (int64_t it = 0; it < steps; ++it) {
     // Horner: v = psi + z/4 H psi; v = psi + z/3 H v; v = psi + z/2 H v; psi = psi + z H v
@@ -658,7 +658,7 @@ static int rk4_issue(Space& s, DfArgs& a, double dt, int64_t steps, float4* w1, 
       const float zh = (float)a.zre;
       a.zf = make_float2(zh, (float)(a.zre - (double)zh));
       if (!plain) {
-        a.row0 = 0;
+        a.row0 = row0;
         a.row1 = s.t.total;
         int rc = stage_launch(s.t, a, d == 1 ? 1 : 0, B, cplx, st);
         if (rc) return rc;
@@ -691,9 +691,56 @@ static int rk4_loop(Space& s, double2* psi, const double* scale, double dt, int6
   a.psif = psif;
   a.status = reinterpret_cast<int*>(s.d_scratch);
   a.nbasef = 0;
-  if (plain || steps < 2 * kGraphSteps) return rk4_issue<B>(s, a, dt, steps, w1, w2, psif, st, plain);
+  if (plain) return rk4_issue<B>(s, a, dt, steps, w1, w2, psif, st, true);
+  // Leading sectors small enough to sit in shared memory run resident on a side
+  // stream, all steps in one launch, while the rest advances stage by stage.
+  int64_t row0 = 0;
+  bool forked = false;
+  if (B == 1) {
+    int n_small = 0;
+    const int nsec = (int)s.secDim.size();
+    int optin = 0;
+    QB_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s.device));
+    const size_t base_smem = resident_smem(s.t, 0);
+    const int64_t room = optin > (int)base_smem ? (optin - (int64_t)base_smem - 1024) / 64 : 0;
+    const int64_t limit = std::min<int64_t>(room, s.resident_max_kets);
+    int cap = 0;
+    while (n_small < nsec && s.secDim[n_small] <= limit) cap = std::max<int>(cap, (int)s.secDim[n_small++]);
+    if (n_small > 0) {
+      if (!s.side_stream) QB_CUDA(cudaStreamCreateWithFlags(&s.side_stream, cudaStreamNonBlocking));
+      if (!s.ev_fork) QB_CUDA(cudaEventCreateWithFlags(&s.ev_fork, cudaEventDisableTiming));
+      if (!s.ev_join) QB_CUDA(cudaEventCreateWithFlags(&s.ev_join, cudaEventDisableTiming));
+      QB_CUDA(cudaEventRecord(s.ev_fork, st));
+      QB_CUDA(cudaStreamWaitEvent(s.side_stream, s.ev_fork, 0));
+      ResArgs r{};
+      r.psi = psi;
+      r.psif = psif;
+      r.diag = s.d_diag;
+      r.scale = a.scale[0];
+      r.dt = dt;
+      r.steps = steps;
+      r.n_small = n_small;
+      r.cap = cap;
+      r.status = a.status;
+      int rc = resident_launch(s.t, r, s.t.is_complex != 0, s.side_stream);
+      if (rc) return rc;
+      QB_CUDA(cudaEventRecord(s.ev_join, s.side_stream));
+      forked = true;
+      row0 = s.secOff[n_small];
+    }
+  }
+  auto join = [&]() -> int {
+    if (forked) QB_CUDA(cudaStreamWaitEvent(st, s.ev_join, 0));
+    return QB_OK;
+  };
+  if (row0 >= s.t.total) return join();
+  if (steps < 2 * kGraphSteps) {
+    int rc = rk4_issue<B>(s, a, dt, steps, w1, w2, psif, st, false, row0);
+    if (rc) return rc;
+    return join();
+  }
   // first step directly: fills the launch-geometry cache outside any capture
-  int rc = rk4_issue<B>(s, a, dt, 1, w1, w2, psif, st, false);
+  int rc = rk4_issue<B>(s, a, dt, 1, w1, w2, psif, st, false, row0);
   if (rc) return rc;
   int64_t left = steps - 1;
   cudaGraph_t graph = nullptr;
@@ -703,7 +750,7 @@ static int rk4_loop(Space& s, double2* psi, const double* scale, double dt, int6
   // stream, which cannot capture); the graph is launched on the caller's stream
   if (!s.capture_stream) QB_CUDA(cudaStreamCreateWithFlags(&s.capture_stream, cudaStreamNonBlocking));
   if (cudaStreamBeginCapture(s.capture_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-    rc = rk4_issue<B>(s, a, dt, kGraphSteps, w1, w2, psif, s.capture_stream, false);
+    rc = rk4_issue<B>(s, a, dt, kGraphSteps, w1, w2, psif, s.capture_stream, false, row0);
     const cudaError_t ec = cudaStreamEndCapture(s.capture_stream, &graph);
     if (rc) {
       if (graph) cudaGraphDestroy(graph);
@@ -726,7 +773,9 @@ static int rk4_loop(Space& s, double2* psi, const double* scale, double dt, int6
   } else if (graph) {
     cudaGraphDestroy(graph);
   }
-  return rk4_issue<B>(s, a, dt, left, w1, w2, psif, st, false);
+  rc = rk4_issue<B>(s, a, dt, left, w1, w2, psif, st, false, row0);
+  if (rc) return rc;
+  return join();
 }
 
 int launch_rk4(Space& s, void* d_psi, int batch, const double* scale, double dt, int64_t steps, void* d_work,

@@ -40,40 +40,346 @@ namespace qb {
 // first byte of the table image the stage kernels stage in shared memory
 __host__ __device__ inline int kSmemFrom(const Tables& t) { return QB_CNT_GLOBAL ? t.o_E : 0; }
 
+// One warp tile: kets [base, min(base + kWarpRows, row1)) of the launch.  With
+// LOCAL the state vectors of DfArgs are the shared-memory copies of one sector
+// starting at ket local_off (gathers and own-row accesses are sector-local);
+// otherwise they are the global vectors.  The per-ket diagonal is always global.
+template <int MT, int B, bool CPLX, bool BIL, bool LOCAL>
+__device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const float2* sqf, const float4* Gf,
+                                           const uint4* dl4, const DfArgs& a, const int mode, const int64_t base,
+                                           const int64_t row1, const int64_t local_off, int32_t* sidx, uint8_t* socc,
+                                           int32_t* sD, int64_t* sOff, uint8_t* sperm, int32_t* hist,
+                                           int32_t* cursor, dfl& bil_l, dfl* bil_w) {
+  const int M = (MT > 0) ? MT : t.M;
+  const int twoM = 2 * M;
+  const int lane = threadIdx.x & 31;
+  const int64_t total = t.total;  // stride between sweep members
+  const int nb = t.n_ann + 2;
+  constexpr int kMB = (MT > 0) ? MT : 16;
+  // ---- phase 1: each lane unranks kWarpRows/32 kets into occupations and suffix-state indices
+  for (int k = lane; k < 2 * nb; k += 32) hist[k] = 0;
+  int key[kWarpRows / 32];
+#pragma unroll
+  for (int u = 0; u < kWarpRows / 32; ++u) {
+    const int row = u * 32 + lane;
+    const int64_t g = base + row;
+    key[u] = 0;
+    if (g < row1) {
+      const int sid = find_sector(t, g);
+      const int64_t off = __ldg(t.sec_off + sid);
+      const int D = (int)(__ldg(t.sec_off + sid + 1) - off);
+      int rem = __ldg(t.sec_N + sid), kr = __ldg(t.sec_K + sid);
+      int left = (int)(g - off);
+      for (int m = 0; m < M - 1; ++m) {
+        int val = 0, kk = kr;
+#if QB_UNRANK_FROM_E
+        // cnt[m+1][n][k] = E_{m+2}(n + 1, k + m + 1), already in shared memory; for
+        // the last step cnt[M-1][n][k] = [n + k = 0 mod M] (one mode left)
+        const int32_t* erow = v.E + (min(m + 2, M - 1) * t.rem_w + 3) * twoM + m + 1;  // used for m + 2 < M
+        while (true) {
+          const int c = (m + 2 < M) ? erow[(rem - val) * twoM + kk] : (((rem - val + kk) % M) == 0 ? 1 : 0);
+#else
+        const uint32_t* crow = gcnt + (size_t)(m + 1) * V * M;
+        while (true) {
+          const int c = (int)crow[(rem - val) * M + kk];
+#endif
+          if (left < c || val == rem) break;
+          left -= c;
+          ++val;
+          kk -= m;
+          if (kk < 0) kk += M;
+        }
+        socc[m * kWarpRows + row] = (uint8_t)val;
+        rem -= val;
+        kr = kk;
+      }
+      socc[(M - 1) * kWarpRows + row] = (uint8_t)rem;
+      int srem = 0, skr = 0, esum = 0, np = 0, n2 = 0;
+      for (int m = M - 1; m >= 1; --m) {
+        const int nm = socc[m * kWarpRows + row];
+        srem += nm;
+        skr += m * nm;
+        while (skr >= M) skr -= M;
+        const int ix = (m * t.rem_w + srem + 2) * twoM + skr;
+        esum += v.E[ix];
+        sidx[m * kWarpRows + row] = ix - kDeltaBias;
+      }
+      if (D - 1 - esum != (int)(g - off)) atomicOr(a.status, 2);
+      for (int m = 0; m < M; ++m) {
+        const int nm = socc[m * kWarpRows + row];
+        np += nm >= 1;
+        n2 += nm >= 2;
+      }
+      key[u] = np * (np - 1) / 2 + n2;  // annihilation pairs r <= s acting on the ket
+      sD[row] = D;
+      sOff[row] = off;
+    } else {
+      sD[row] = -1;
+    }
+  }
+  // ---- phase 2: warp-local counting sort of the tile by work, largest first
+  __syncwarp();
+#pragma unroll
+  for (int u = 0; u < kWarpRows / 32; ++u) atomicAdd(&hist[key[u]], 1);
+  __syncwarp();
+  if (lane == 0) {
+    int run = 0;
+    for (int k = nb - 1; k >= 0; --k) {
+      cursor[k] = run;
+      run += hist[k];
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int u = 0; u < kWarpRows / 32; ++u) sperm[atomicAdd(&cursor[key[u]], 1)] = (uint8_t)(u * 32 + lane);
+  __syncwarp();
+
+  // ---- phase 3: rounds of 32 kets of similar work, one per lane
+  for (int round = 0; round < kWarpRows / 32; ++round) {
+    const int row = sperm[round * 32 + lane];
+    const int D = sD[row];
+    if (D < 0) continue;
+    const int64_t off = sOff[row];
+    const int64_t gr = base + row;
+    const int64_t ri = LOCAL ? gr - local_off : gr;  // own-row index into the state vectors
+    const uint8_t* occ = socc + row;
+    int id[16];
+#pragma unroll
+    for (int m = 1; m < 16; ++m)
+      if (m < M) id[m] = sidx[m * kWarpRows + row];
+    uint32_t occmask = 0, twomask = 0;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      if (m >= M) break;
+      const int nm = occ[m * kWarpRows];
+      occmask |= (nm >= 1 ? 1u : 0u) << m;
+      twomask |= (nm >= 2 ? 1u : 0u) << m;
+    }
+    const float4* vsec = a.vin + (LOCAL ? 0 : off);  // gathers
+    dfc acc[B];  // (re, im) of the off-diagonal sum, double-float, packed
+#pragma unroll
+    for (int b = 0; b < B; ++b) acc[b] = dfc{0ull, 0ull};
+
+#if QB_CONVERGENT_PAIRS
+    // One annihilation pair (r <= s, n_r (n_s - [r=s]) > 0) per iteration.  Kets of
+    // a round have (nearly) the same pair count, so the iterations line up across
+    // the warp; the search for the next r is a short inner loop.
+    const int np = __popc(occmask);
+    const int npairs = np * (np - 1) / 2 + __popc(twomask);
+    uint32_t rm = occmask, smask = 0;
+    int r = 0;
+    for (int it = 0; it < npairs; ++it) {
+      while (smask == 0 && rm != 0) {
+        r = __ffs(rm) - 1;
+        rm &= rm - 1;
+        smask = occmask & (~0u << r);
+        if (!((twomask >> r) & 1u)) smask &= ~(1u << r);
+      }
+      if (smask == 0) break;  // not reached: npairs counts exactly the pairs found here
+#else
+    uint32_t rm = occmask, smask = 0;
+    int r = 0;
+    while (true) {
+      if (smask == 0) {
+        if (rm == 0) break;
+        r = __ffs(rm) - 1;
+        rm &= rm - 1;
+        smask = occmask & (~0u << r);
+        if (!((twomask >> r) & 1u)) smask &= ~(1u << r);
+        if (smask == 0) continue;
+      }
+#endif
+      const int s = __ffs(smask) - 1;
+      smask &= smask - 1;
+      const int ai = v.pairidx[r * 16 + s];
+      const float2 sa = sqf[occ[r * kWarpRows]], sb = sqf[occ[s * kWarpRows] - (r == s ? 1 : 0)];
+      const dfl A = df_mul(dfl{sa.x, sa.y}, dfl{sb.x, sb.y});
+      constexpr int kC = (QB_UNROLL_PARTNERS && !CPLX && MT > 0 && (MT % 2) == 1) ? (MT - 1) / 2 : 0;
+      if (kC > 0) {
+        // fixed partner count: all ranks first, then all gathers, then the sums
+        const int j0 = v.ann[ai];
+        int rkc[kC > 0 ? kC : 1];
+        dfl crc[kC > 0 ? kC : 1];
+#pragma unroll
+        for (int c = 0; c < kC; ++c) {
+          const int j = j0 + c;
+          const uint32_t w4 = v.pq[j];
+          const int p = w4 & 0xff, q = (w4 >> 8) & 0xff;
+          const float2 bp = sqf[occ[p * kWarpRows] + 1], bq = sqf[occ[q * kWarpRows] + 1 + (p == q ? 1 : 0)];
+          const dfl AB = df_mul(A, df_mul(dfl{bp.x, bp.y}, dfl{bq.x, bq.y}));
+          const uint4 dd = dl4[j];
+          int esum = 0;
+#pragma unroll
+          for (int m = 1; m < 16; ++m) {
+            if (m >= M) break;
+            const uint32_t word = (m < 4) ? dd.x : (m < 8) ? dd.y : (m < 12) ? dd.z : dd.w;
+            esum += v.E[id[m] + (int)((word >> (8 * (m & 3))) & 0xffu)];
+          }
+          int rk = D - 1 - esum;
+          if ((unsigned)rk >= (unsigned)D) {
+            atomicOr(a.status, 1);
+            rk = 0;
+          }
+          rkc[c] = rk;
+          const float4 gf = Gf[j];
+          crc[c] = df_mul(dfl{gf.x, gf.y}, AB);
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          float4 x[kC > 0 ? kC : 1];
+#pragma unroll
+          for (int c = 0; c < kC; ++c) x[c] = __ldg(vsec + (size_t)b * total + rkc[c]);
+#pragma unroll
+          for (int c = 0; c < kC; ++c)
+            dfc_fma(acc[b], f2_pack(crc[c].h, crc[c].h), f2_pack(-crc[c].h, -crc[c].h),
+                    f2_pack(crc[c].l, crc[c].l), f2_pack(x[c].x, x[c].y), f2_pack(x[c].z, x[c].w));
+        }
+      } else {
+        const int j1 = v.ann[ai + 1];
+        for (int j = v.ann[ai]; j < j1; ++j) {
+          const uint32_t w4 = v.pq[j];
+          const int p = w4 & 0xff, q = (w4 >> 8) & 0xff;
+          const float2 bp = sqf[occ[p * kWarpRows] + 1], bq = sqf[occ[q * kWarpRows] + 1 + (p == q ? 1 : 0)];
+          const dfl AB = df_mul(A, df_mul(dfl{bp.x, bp.y}, dfl{bq.x, bq.y}));
+          // rank of the target: D - 1 - sum over every mode of E at the shifted suffix state
+          const uint4 dd = dl4[j];
+          int esum = 0;
+  #pragma unroll
+          for (int m = 1; m < 16; ++m) {
+            if (m >= M) break;
+            const uint32_t word = (m < 4) ? dd.x : (m < 8) ? dd.y : (m < 12) ? dd.z : dd.w;
+            esum += v.E[id[m] + (int)((word >> (8 * (m & 3))) & 0xffu)];
+          }
+          int rk = D - 1 - esum;
+          if ((unsigned)rk >= (unsigned)D) {
+            atomicOr(a.status, 1);
+            rk = 0;
+          }
+          const float4 gf = Gf[j];
+          const dfl cr = df_mul(dfl{gf.x, gf.y}, AB);
+  #pragma unroll
+          for (int b = 0; b < B; ++b) {
+            const float4 x = __ldg(vsec + (size_t)b * total + rk);
+            const f2 xh = f2_pack(x.x, x.y), xl = f2_pack(x.z, x.w);
+            dfc_fma(acc[b], f2_pack(cr.h, cr.h), f2_pack(-cr.h, -cr.h), f2_pack(cr.l, cr.l), xh, xl);
+            if (CPLX) {
+              // + (-c_i x_im, c_i x_re): lanes of x swapped, coefficient (-c_i, c_i)
+              const dfl ci = df_mul(dfl{gf.z, gf.w}, AB);
+              dfc_fma(acc[b], f2_pack(-ci.h, ci.h), f2_pack(ci.h, -ci.h), f2_pack(-ci.l, ci.l),
+                      f2_pack(x.y, x.x), f2_pack(x.w, x.z));
+            }
+          }
+        }
+      }
+      // keep |lo| below an ulp of hi between pairs
+#pragma unroll
+      for (int b = 0; b < B; ++b) acc[b] = dfc_renorm(acc[b]);
+    }
+
+    const float4 dg4 = a.diag[gr];
+    const dfl zf{a.zf.x, a.zf.y};
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      dfl acc_r, acc_i;
+      f2_unpack(acc[b].h, acc_r.h, acc_i.h);
+      f2_unpack(acc[b].l, acc_r.l, acc_i.l);
+      const dfl sc{a.scale[b].x, a.scale[b].y};
+      const dfl dg = df_add(dfl{dg4.x, dg4.y}, df_mul(sc, dfl{dg4.z, dg4.w}));
+      const float4 xo = a.vin[(size_t)b * total + ri];
+      const dfl hr = df_add(df_mul(dg, df_re(xo)), df_mul(sc, acc_r));
+      const dfl hi = df_add(df_mul(dg, df_im(xo)), df_mul(sc, acc_i));
+      if (BIL && b == 0) {
+        // H_L x (two-body part at scale 1) and the pair vector of this row
+        const float4 pp = a.pair[ri];
+        const dfl lr = df_add(df_mul(dfl{dg4.z, dg4.w}, df_re(xo)), acc_r);
+        const dfl li = df_add(df_mul(dfl{dg4.z, dg4.w}, df_im(xo)), acc_i);
+        // Im(conj(p) h) = p.re h.im - p.im h.re
+        bil_l = df_add(bil_l, df_add(df_mul(df_re(pp), li), df_neg(df_mul(df_im(pp), lr))));
+        // Im(conj(x) p) = x.re p.im - x.im p.re, weighted by each occupation
+        const dfl tx = df_add(df_mul(df_re(xo), df_im(pp)), df_neg(df_mul(df_im(xo), df_re(pp))));
+#pragma unroll
+        for (int q = 0; q < kMB; ++q) {
+          if (q >= M) break;
+          bil_w[q] = df_add(bil_w[q], df_mul(dfl{(float)occ[q * kWarpRows], 0.f}, tx));
+        }
+      }
+      if (mode == 0 || mode == 2) {
+        dfl orr = df_mul(zf, hi), oi = df_neg(df_mul(zf, hr));  // z H x with z = -i zre
+        if (mode == 0) {
+          const float4 p0 = a.psif[(size_t)b * total + ri];
+          orr = df_add(df_re(p0), orr);
+          oi = df_add(df_im(p0), oi);
+        }
+        a.out[(size_t)b * total + ri] = df_pack(orr, oi);
+      } else {
+        const double2 p0 = a.psi[(size_t)b * total + ri];
+        double nr = p0.x + a.zre * df_to(hi);
+        double ni = p0.y - a.zre * df_to(hr);
+        if (mode == 3) {
+          for (int k = 0; k < a.nbasef; ++k) {
+            const float4 e = a.basef[k][(size_t)b * total + ri];
+            nr += df_to(df_re(e));
+            ni += df_to(df_im(e));
+          }
+        }
+        a.psi[(size_t)b * total + ri] = make_double2(nr, ni);
+        a.out[(size_t)b * total + ri] = df_pack(df_of(nr), df_of(ni));
+      }
+    }
+  }
+  __syncwarp();  // the tile's scratch is rewritten by the next tile
+}
+
+// Shared-memory view of a stage CTA: the table image (from the ranking table on)
+// and the per-warp tile scratch; sets up every pointer stage_tile needs.
+struct StageSmem {
+  View v;
+  const float2* sqf;
+  const float4* Gf;
+  const uint4* dl4;
+  int32_t* sidx;
+  uint8_t* socc;
+  int32_t* sD;
+  int64_t* sOff;
+  uint8_t* sperm;
+  int32_t* hist;
+  int32_t* cursor;
+  unsigned char* after;  // first byte after every warp's scratch
+};
+
+// Stages the table image (a CTA-wide barrier) and lays out the warp scratch.
+__device__ __forceinline__ StageSmem stage_smem(const Tables& t, unsigned char* smem_raw, int M) {
+  StageSmem S;
+  load_blob_from(t, smem_raw, kSmemFrom(t));
+  unsigned char* smem = smem_raw - kSmemFrom(t);
+  S.v = make_view(t, smem);
+  S.sqf = reinterpret_cast<const float2*>(smem + t.o_sqf);
+  S.Gf = reinterpret_cast<const float4*>(smem + t.o_Gf);
+  S.dl4 = reinterpret_cast<const uint4*>(S.v.delta);
+  const int warp = threadIdx.x >> 5;
+  const size_t wbytes = df_warp_scratch_bytes(M, t.n_ann);
+  unsigned char* base = smem_raw + ((t.blob_bytes - kSmemFrom(t) + 15) & ~15);
+  unsigned char* sp = base + (size_t)warp * wbytes;
+  S.sidx = reinterpret_cast<int32_t*>(sp);
+  S.socc = reinterpret_cast<uint8_t*>(S.sidx + M * kWarpRows);
+  S.sD = reinterpret_cast<int32_t*>(S.socc + ((M * kWarpRows + 15) & ~15));
+  S.sOff = reinterpret_cast<int64_t*>(S.sD + kWarpRows);
+  S.sperm = reinterpret_cast<uint8_t*>(S.sOff + kWarpRows);
+  S.hist = reinterpret_cast<int32_t*>(S.sperm + kWarpRows);
+  S.cursor = S.hist + (t.n_ann + 2);
+  S.after = base + (size_t)(kBlock / 32) * wbytes;
+  return S;
+}
+
 template <int MT, int B, bool CPLX, bool BIL>
 __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const DfArgs a, const int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-#if QB_CNT_GLOBAL
-  // the image from the ranking table E on; the fill counts stay in global memory
-  load_blob_from(t, smem_raw, t.o_E);  // the only CTA-wide barrier: warps run independently afterwards
-  unsigned char* smem = smem_raw - t.o_E;
-  const uint32_t* gcnt = reinterpret_cast<const uint32_t*>(t.blob + t.o_cnt);
-  (void)gcnt;
-#else
-  load_blob(t, smem_raw);  // the only CTA-wide barrier: warps run independently afterwards
-  unsigned char* smem = smem_raw;
-  const uint32_t* gcnt = reinterpret_cast<const uint32_t*>(smem + t.o_cnt);
-#endif
-  const View v = make_view(t, smem);
-  const float2* sqf = reinterpret_cast<const float2*>(smem + t.o_sqf);
-  const float4* Gf = reinterpret_cast<const float4*>(smem + t.o_Gf);
-  const uint4* dl4 = reinterpret_cast<const uint4*>(v.delta);
   const int M = (MT > 0) ? MT : t.M;
-  const int V = t.nmax + 1, twoM = 2 * M;
-  (void)V;
+  // the only CTA-wide barrier: warps run independently afterwards
+  const StageSmem S = stage_smem(t, smem_raw, M);
   constexpr int kWarps = kBlock / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned char* sp = smem_raw + ((t.blob_bytes - kSmemFrom(t) + 15) & ~15) + (size_t)warp * df_warp_scratch_bytes(M, t.n_ann);
-  int32_t* sidx = reinterpret_cast<int32_t*>(sp);
-  uint8_t* socc = reinterpret_cast<uint8_t*>(sidx + M * kWarpRows);
-  int32_t* sD = reinterpret_cast<int32_t*>(socc + ((M * kWarpRows + 15) & ~15));
-  int64_t* sOff = reinterpret_cast<int64_t*>(sD + kWarpRows);
-  uint8_t* sperm = reinterpret_cast<uint8_t*>(sOff + kWarpRows);
-  int32_t* hist = reinterpret_cast<int32_t*>(sperm + kWarpRows);
-  int32_t* cursor = hist + (t.n_ann + 2);
-  const int64_t total = t.total;  // stride between sweep members
   const int64_t row1 = a.row1;
-  const int nb = t.n_ann + 2;
   constexpr int kMB = (MT > 0) ? MT : 16;  // bilinear accumulators: one per mode + H_L
   dfl bil_l{0.f, 0.f};
   dfl bil_w[BIL ? kMB : 1];
@@ -81,279 +387,9 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
   for (int q = 0; q < (BIL ? kMB : 1); ++q) bil_w[q] = dfl{0.f, 0.f};
 
   for (int64_t base = a.row0 + ((int64_t)blockIdx.x * kWarps + warp) * kWarpRows; base < row1;
-       base += (int64_t)gridDim.x * kWarps * kWarpRows) {
-    // ---- phase 1: each lane unranks kWarpRows/32 kets into occupations and suffix-state indices
-    for (int k = lane; k < 2 * nb; k += 32) hist[k] = 0;
-    int key[kWarpRows / 32];
-#pragma unroll
-    for (int u = 0; u < kWarpRows / 32; ++u) {
-      const int row = u * 32 + lane;
-      const int64_t g = base + row;
-      key[u] = 0;
-      if (g < row1) {
-        const int sid = find_sector(t, g);
-        const int64_t off = __ldg(t.sec_off + sid);
-        const int D = (int)(__ldg(t.sec_off + sid + 1) - off);
-        int rem = __ldg(t.sec_N + sid), kr = __ldg(t.sec_K + sid);
-        int left = (int)(g - off);
-        for (int m = 0; m < M - 1; ++m) {
-          int val = 0, kk = kr;
-#if QB_UNRANK_FROM_E
-          // cnt[m+1][n][k] = E_{m+2}(n + 1, k + m + 1), already in shared memory; for
-          // the last step cnt[M-1][n][k] = [n + k = 0 mod M] (one mode left)
-          const int32_t* erow = v.E + (min(m + 2, M - 1) * t.rem_w + 3) * twoM + m + 1;  // used for m + 2 < M
-          while (true) {
-            const int c = (m + 2 < M) ? erow[(rem - val) * twoM + kk] : (((rem - val + kk) % M) == 0 ? 1 : 0);
-#else
-          const uint32_t* crow = gcnt + (size_t)(m + 1) * V * M;
-          while (true) {
-            const int c = (int)crow[(rem - val) * M + kk];
-#endif
-            if (left < c || val == rem) break;
-            left -= c;
-            ++val;
-            kk -= m;
-            if (kk < 0) kk += M;
-          }
-          socc[m * kWarpRows + row] = (uint8_t)val;
-          rem -= val;
-          kr = kk;
-        }
-        socc[(M - 1) * kWarpRows + row] = (uint8_t)rem;
-        int srem = 0, skr = 0, esum = 0, np = 0, n2 = 0;
-        for (int m = M - 1; m >= 1; --m) {
-          const int nm = socc[m * kWarpRows + row];
-          srem += nm;
-          skr += m * nm;
-          while (skr >= M) skr -= M;
-          const int ix = (m * t.rem_w + srem + 2) * twoM + skr;
-          esum += v.E[ix];
-          sidx[m * kWarpRows + row] = ix - kDeltaBias;
-        }
-        if (D - 1 - esum != (int)(g - off)) atomicOr(a.status, 2);
-        for (int m = 0; m < M; ++m) {
-          const int nm = socc[m * kWarpRows + row];
-          np += nm >= 1;
-          n2 += nm >= 2;
-        }
-        key[u] = np * (np - 1) / 2 + n2;  // annihilation pairs r <= s acting on the ket
-        sD[row] = D;
-        sOff[row] = off;
-      } else {
-        sD[row] = -1;
-      }
-    }
-    // ---- phase 2: warp-local counting sort of the tile by work, largest first
-    __syncwarp();
-#pragma unroll
-    for (int u = 0; u < kWarpRows / 32; ++u) atomicAdd(&hist[key[u]], 1);
-    __syncwarp();
-    if (lane == 0) {
-      int run = 0;
-      for (int k = nb - 1; k >= 0; --k) {
-        cursor[k] = run;
-        run += hist[k];
-      }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int u = 0; u < kWarpRows / 32; ++u) sperm[atomicAdd(&cursor[key[u]], 1)] = (uint8_t)(u * 32 + lane);
-    __syncwarp();
-
-    // ---- phase 3: rounds of 32 kets of similar work, one per lane
-    for (int round = 0; round < kWarpRows / 32; ++round) {
-      const int row = sperm[round * 32 + lane];
-      const int D = sD[row];
-      if (D < 0) continue;
-      const int64_t off = sOff[row];
-      const int64_t gr = base + row;
-      const uint8_t* occ = socc + row;
-      int id[16];
-#pragma unroll
-      for (int m = 1; m < 16; ++m)
-        if (m < M) id[m] = sidx[m * kWarpRows + row];
-      uint32_t occmask = 0, twomask = 0;
-#pragma unroll
-      for (int m = 0; m < 16; ++m) {
-        if (m >= M) break;
-        const int nm = occ[m * kWarpRows];
-        occmask |= (nm >= 1 ? 1u : 0u) << m;
-        twomask |= (nm >= 2 ? 1u : 0u) << m;
-      }
-      const float4* vsec = a.vin + off;
-      dfc acc[B];  // (re, im) of the off-diagonal sum, double-float, packed
-#pragma unroll
-      for (int b = 0; b < B; ++b) acc[b] = dfc{0ull, 0ull};
-
-#if QB_CONVERGENT_PAIRS
-      // One annihilation pair (r <= s, n_r (n_s - [r=s]) > 0) per iteration.  Kets of
-      // a round have (nearly) the same pair count, so the iterations line up across
-      // the warp; the search for the next r is a short inner loop.
-      const int np = __popc(occmask);
-      const int npairs = np * (np - 1) / 2 + __popc(twomask);
-      uint32_t rm = occmask, smask = 0;
-      int r = 0;
-      for (int it = 0; it < npairs; ++it) {
-        while (smask == 0 && rm != 0) {
-          r = __ffs(rm) - 1;
-          rm &= rm - 1;
-          smask = occmask & (~0u << r);
-          if (!((twomask >> r) & 1u)) smask &= ~(1u << r);
-        }
-        if (smask == 0) break;  // not reached: npairs counts exactly the pairs found here
-#else
-      uint32_t rm = occmask, smask = 0;
-      int r = 0;
-      while (true) {
-        if (smask == 0) {
-          if (rm == 0) break;
-          r = __ffs(rm) - 1;
-          rm &= rm - 1;
-          smask = occmask & (~0u << r);
-          if (!((twomask >> r) & 1u)) smask &= ~(1u << r);
-          if (smask == 0) continue;
-        }
-#endif
-        const int s = __ffs(smask) - 1;
-        smask &= smask - 1;
-        const int ai = v.pairidx[r * 16 + s];
-        const float2 sa = sqf[occ[r * kWarpRows]], sb = sqf[occ[s * kWarpRows] - (r == s ? 1 : 0)];
-        const dfl A = df_mul(dfl{sa.x, sa.y}, dfl{sb.x, sb.y});
-        constexpr int kC = (QB_UNROLL_PARTNERS && !CPLX && MT > 0 && (MT % 2) == 1) ? (MT - 1) / 2 : 0;
-        if (kC > 0) {
-          // fixed partner count: all ranks first, then all gathers, then the sums
-          const int j0 = v.ann[ai];
-          int rkc[kC > 0 ? kC : 1];
-          dfl crc[kC > 0 ? kC : 1];
-#pragma unroll
-          for (int c = 0; c < kC; ++c) {
-            const int j = j0 + c;
-            const uint32_t w4 = v.pq[j];
-            const int p = w4 & 0xff, q = (w4 >> 8) & 0xff;
-            const float2 bp = sqf[occ[p * kWarpRows] + 1], bq = sqf[occ[q * kWarpRows] + 1 + (p == q ? 1 : 0)];
-            const dfl AB = df_mul(A, df_mul(dfl{bp.x, bp.y}, dfl{bq.x, bq.y}));
-            const uint4 dd = dl4[j];
-            int esum = 0;
-#pragma unroll
-            for (int m = 1; m < 16; ++m) {
-              if (m >= M) break;
-              const uint32_t word = (m < 4) ? dd.x : (m < 8) ? dd.y : (m < 12) ? dd.z : dd.w;
-              esum += v.E[id[m] + (int)((word >> (8 * (m & 3))) & 0xffu)];
-            }
-            int rk = D - 1 - esum;
-            if ((unsigned)rk >= (unsigned)D) {
-              atomicOr(a.status, 1);
-              rk = 0;
-            }
-            rkc[c] = rk;
-            const float4 gf = Gf[j];
-            crc[c] = df_mul(dfl{gf.x, gf.y}, AB);
-          }
-#pragma unroll
-          for (int b = 0; b < B; ++b) {
-            float4 x[kC > 0 ? kC : 1];
-#pragma unroll
-            for (int c = 0; c < kC; ++c) x[c] = __ldg(vsec + (size_t)b * total + rkc[c]);
-#pragma unroll
-            for (int c = 0; c < kC; ++c)
-              dfc_fma(acc[b], f2_pack(crc[c].h, crc[c].h), f2_pack(-crc[c].h, -crc[c].h),
-                      f2_pack(crc[c].l, crc[c].l), f2_pack(x[c].x, x[c].y), f2_pack(x[c].z, x[c].w));
-          }
-        } else {
-          const int j1 = v.ann[ai + 1];
-          for (int j = v.ann[ai]; j < j1; ++j) {
-            const uint32_t w4 = v.pq[j];
-            const int p = w4 & 0xff, q = (w4 >> 8) & 0xff;
-            const float2 bp = sqf[occ[p * kWarpRows] + 1], bq = sqf[occ[q * kWarpRows] + 1 + (p == q ? 1 : 0)];
-            const dfl AB = df_mul(A, df_mul(dfl{bp.x, bp.y}, dfl{bq.x, bq.y}));
-            // rank of the target: D - 1 - sum over every mode of E at the shifted suffix state
-            const uint4 dd = dl4[j];
-            int esum = 0;
-  #pragma unroll
-            for (int m = 1; m < 16; ++m) {
-              if (m >= M) break;
-              const uint32_t word = (m < 4) ? dd.x : (m < 8) ? dd.y : (m < 12) ? dd.z : dd.w;
-              esum += v.E[id[m] + (int)((word >> (8 * (m & 3))) & 0xffu)];
-            }
-            int rk = D - 1 - esum;
-            if ((unsigned)rk >= (unsigned)D) {
-              atomicOr(a.status, 1);
-              rk = 0;
-            }
-            const float4 gf = Gf[j];
-            const dfl cr = df_mul(dfl{gf.x, gf.y}, AB);
-  #pragma unroll
-            for (int b = 0; b < B; ++b) {
-              const float4 x = __ldg(vsec + (size_t)b * total + rk);
-              const f2 xh = f2_pack(x.x, x.y), xl = f2_pack(x.z, x.w);
-              dfc_fma(acc[b], f2_pack(cr.h, cr.h), f2_pack(-cr.h, -cr.h), f2_pack(cr.l, cr.l), xh, xl);
-              if (CPLX) {
-                // + (-c_i x_im, c_i x_re): lanes of x swapped, coefficient (-c_i, c_i)
-                const dfl ci = df_mul(dfl{gf.z, gf.w}, AB);
-                dfc_fma(acc[b], f2_pack(-ci.h, ci.h), f2_pack(ci.h, -ci.h), f2_pack(-ci.l, ci.l),
-                        f2_pack(x.y, x.x), f2_pack(x.w, x.z));
-              }
-            }
-          }
-        }
-        // keep |lo| below an ulp of hi between pairs
-#pragma unroll
-        for (int b = 0; b < B; ++b) acc[b] = dfc_renorm(acc[b]);
-      }
-
-      const float4 dg4 = a.diag[gr];
-      const dfl zf{a.zf.x, a.zf.y};
-#pragma unroll
-      for (int b = 0; b < B; ++b) {
-        dfl acc_r, acc_i;
-        f2_unpack(acc[b].h, acc_r.h, acc_i.h);
-        f2_unpack(acc[b].l, acc_r.l, acc_i.l);
-        const dfl sc{a.scale[b].x, a.scale[b].y};
-        const dfl dg = df_add(dfl{dg4.x, dg4.y}, df_mul(sc, dfl{dg4.z, dg4.w}));
-        const float4 xo = a.vin[(size_t)b * total + gr];
-        const dfl hr = df_add(df_mul(dg, df_re(xo)), df_mul(sc, acc_r));
-        const dfl hi = df_add(df_mul(dg, df_im(xo)), df_mul(sc, acc_i));
-        if (BIL && b == 0) {
-          // H_L x (two-body part at scale 1) and the pair vector of this row
-          const float4 pp = a.pair[gr];
-          const dfl lr = df_add(df_mul(dfl{dg4.z, dg4.w}, df_re(xo)), acc_r);
-          const dfl li = df_add(df_mul(dfl{dg4.z, dg4.w}, df_im(xo)), acc_i);
-          // Im(conj(p) h) = p.re h.im - p.im h.re
-          bil_l = df_add(bil_l, df_add(df_mul(df_re(pp), li), df_neg(df_mul(df_im(pp), lr))));
-          // Im(conj(x) p) = x.re p.im - x.im p.re, weighted by each occupation
-          const dfl tx = df_add(df_mul(df_re(xo), df_im(pp)), df_neg(df_mul(df_im(xo), df_re(pp))));
-#pragma unroll
-          for (int q = 0; q < kMB; ++q) {
-            if (q >= M) break;
-            bil_w[q] = df_add(bil_w[q], df_mul(dfl{(float)occ[q * kWarpRows], 0.f}, tx));
-          }
-        }
-        if (mode == 0 || mode == 2) {
-          dfl orr = df_mul(zf, hi), oi = df_neg(df_mul(zf, hr));  // z H x with z = -i zre
-          if (mode == 0) {
-            const float4 p0 = a.psif[(size_t)b * total + gr];
-            orr = df_add(df_re(p0), orr);
-            oi = df_add(df_im(p0), oi);
-          }
-          a.out[(size_t)b * total + gr] = df_pack(orr, oi);
-        } else {
-          const double2 p0 = a.psi[(size_t)b * total + gr];
-          double nr = p0.x + a.zre * df_to(hi);
-          double ni = p0.y - a.zre * df_to(hr);
-          if (mode == 3) {
-            for (int k = 0; k < a.nbasef; ++k) {
-              const float4 e = a.basef[k][(size_t)b * total + gr];
-              nr += df_to(df_re(e));
-              ni += df_to(df_im(e));
-            }
-          }
-          a.psi[(size_t)b * total + gr] = make_double2(nr, ni);
-          a.out[(size_t)b * total + gr] = df_pack(df_of(nr), df_of(ni));
-        }
-      }
-    }
-    __syncwarp();  // the tile's scratch is rewritten by the next tile
-  }
+       base += (int64_t)gridDim.x * kWarps * kWarpRows)
+    stage_tile<MT, B, CPLX, BIL, false>(t, S.v, S.sqf, S.Gf, S.dl4, a, mode, base, row1, 0, S.sidx, S.socc, S.sD,
+                                        S.sOff, S.sperm, S.hist, S.cursor, bil_l, bil_w);
   if (BIL) {
     // per-CTA sums of the bilinears in a fixed order: lanes by shuffles, warps in turn
     __shared__ double red[kBlock / 32][17];
@@ -373,6 +409,104 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
       a.partial[(size_t)blockIdx.x * nq + threadIdx.x] = sum;
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Resident small sectors: each CTA takes sectors [0, n_small) from a static work
+// list (sector c, c + gridDim.x, ...), copies the sector's psi into shared
+// memory and runs all `steps` RK4 steps there, with only CTA barriers between
+// stages -- the sectors are independent, so no CTA ever waits on another.  The
+// final psi and its double-float copy are written back to global memory.
+struct ResArgs {
+  double2* psi;        // global psi [total]
+  float4* psif;        // global double-float copy of psi [total] (written back)
+  const float4* diag;  // per-ket diagonal
+  float2 scale;        // two-body scale, double-float
+  double dt;
+  int64_t steps;
+  int n_small;         // sectors [0, n_small) are resident
+  int cap;             // kets per sector the shared buffers hold
+  int* status;
+};
+
+template <int MT, bool CPLX>
+__global__ void __launch_bounds__(kBlock) resident_kernel(const Tables t, const ResArgs r) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int M = (MT > 0) ? MT : t.M;
+  const StageSmem S = stage_smem(t, smem_raw, M);
+  double2* spsi = reinterpret_cast<double2*>(S.after);
+  float4* spsif = reinterpret_cast<float4*>(spsi + r.cap);
+  float4* sw1 = spsif + r.cap;
+  float4* sw2 = sw1 + r.cap;
+  constexpr int kWarps = kBlock / 32;
+  const int warp = threadIdx.x >> 5;
+  dfl bil_l{0.f, 0.f}, bil_w[1] = {dfl{0.f, 0.f}};
+  for (int sid = blockIdx.x; sid < r.n_small; sid += gridDim.x) {
+    const int64_t off = __ldg(t.sec_off + sid);
+    const int D = (int)(__ldg(t.sec_off + sid + 1) - off);
+    if (D > r.cap) {  // not reached: the host lists only sectors that fit
+      if (threadIdx.x == 0) atomicOr(r.status, 4);
+      continue;
+    }
+    for (int i = threadIdx.x; i < D; i += kBlock) {
+      const double2 x = r.psi[off + i];
+      spsi[i] = x;
+      spsif[i] = df_pack(df_of(x.x), df_of(x.y));
+    }
+    __syncthreads();
+    DfArgs a{};
+    a.diag = r.diag;
+    a.scale[0] = r.scale;
+    a.status = r.status;
+    a.psi = spsi;
+    a.psif = spsif;
+    a.nbasef = 0;
+    for (int64_t it = 0; it < r.steps; ++it) {
+      const float4* in[4] = {spsif, sw1, sw2, sw1};
+      float4* out[4] = {sw1, sw2, sw1, spsif};
+      for (int d = 4; d >= 1; --d) {
+        a.vin = in[4 - d];
+        a.out = out[4 - d];
+        a.zre = r.dt / d;
+        const float zh = (float)a.zre;
+        a.zf = make_float2(zh, (float)(a.zre - (double)zh));
+        for (int64_t base = off + (int64_t)warp * kWarpRows; base < off + D; base += (int64_t)kWarps * kWarpRows)
+          stage_tile<MT, 1, CPLX, false, true>(t, S.v, S.sqf, S.Gf, S.dl4, a, d == 1 ? 1 : 0, base, off + D, off,
+                                               S.sidx, S.socc, S.sD, S.sOff, S.sperm, S.hist, S.cursor, bil_l,
+                                               bil_w);
+        __syncthreads();
+      }
+    }
+    for (int i = threadIdx.x; i < D; i += kBlock) {
+      r.psi[off + i] = spsi[i];
+      r.psif[off + i] = spsif[i];
+    }
+    __syncthreads();
+  }
+}
+
+// Shared memory of the resident kernel holding `cap` kets per sector.
+inline size_t resident_smem(const Tables& t, int cap) {
+  return ((t.blob_bytes - kSmemFrom(t) + 15) & ~15) + df_scratch_bytes(t.M, t.n_ann) + (size_t)cap * 64;
+}
+
+template <int MT>
+int resident_launch_t(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t st) {
+  const size_t smem = resident_smem(t, r.cap);
+  int grid = 0, rc = QB_OK;
+  if (cplx) {
+    auto k = resident_kernel<MT, true>;
+    rc = persistent_grid(k, smem, (int64_t)r.n_small * kBlock, &grid);
+    if (rc) return rc;
+    k<<<grid, kBlock, smem, st>>>(t, r);
+  } else {
+    auto k = resident_kernel<MT, false>;
+    rc = persistent_grid(k, smem, (int64_t)r.n_small * kBlock, &grid);
+    if (rc) return rc;
+    k<<<grid, kBlock, smem, st>>>(t, r);
+  }
+  QB_CUDA(cudaGetLastError());
+  return QB_OK;
 }
 
 // Launches one stage for mode count MT (0: any M) and the runtime batch size /
@@ -419,6 +553,22 @@ int stage_launch_m7(const Tables&, const DfArgs&, int, int, bool, bool, cudaStre
 int stage_launch_m9(const Tables&, const DfArgs&, int, int, bool, bool, cudaStream_t, int*);
 int stage_launch_m11(const Tables&, const DfArgs&, int, int, bool, bool, cudaStream_t, int*);
 int stage_launch_any(const Tables&, const DfArgs&, int, int, bool, bool, cudaStream_t, int*);
+
+int resident_launch_m5(const Tables&, const ResArgs&, bool, cudaStream_t);
+int resident_launch_m7(const Tables&, const ResArgs&, bool, cudaStream_t);
+int resident_launch_m9(const Tables&, const ResArgs&, bool, cudaStream_t);
+int resident_launch_m11(const Tables&, const ResArgs&, bool, cudaStream_t);
+int resident_launch_any(const Tables&, const ResArgs&, bool, cudaStream_t);
+
+inline int resident_launch(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t st) {
+  switch (t.M) {
+    case 5: return resident_launch_m5(t, r, cplx, st);
+    case 7: return resident_launch_m7(t, r, cplx, st);
+    case 9: return resident_launch_m9(t, r, cplx, st);
+    case 11: return resident_launch_m11(t, r, cplx, st);
+    default: return resident_launch_any(t, r, cplx, st);
+  }
+}
 
 inline int stage_launch(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, cudaStream_t st,
                         int* grid_out = nullptr, bool bil = false) {

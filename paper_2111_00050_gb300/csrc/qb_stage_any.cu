@@ -6,4 +6,7 @@ int stage_launch_any(const Tables& t, const DfArgs& a, int mode, int B, bool cpl
                    int* grid) {
   return stage_launch_t<0>(t, a, mode, B, cplx, bil, st, grid);
 }
+int resident_launch_any(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t st) {
+  return resident_launch_t<0>(t, r, cplx, st);
+}
 }  // namespace qb

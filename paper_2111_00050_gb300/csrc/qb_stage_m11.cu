@@ -6,4 +6,7 @@ int stage_launch_m11(const Tables& t, const DfArgs& a, int mode, int B, bool cpl
                    int* grid) {
   return stage_launch_t<11>(t, a, mode, B, cplx, bil, st, grid);
 }
+int resident_launch_m11(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t st) {
+  return resident_launch_t<11>(t, r, cplx, st);
+}
 }  // namespace qb

@@ -6,4 +6,7 @@ int stage_launch_m7(const Tables& t, const DfArgs& a, int mode, int B, bool cplx
                    int* grid) {
   return stage_launch_t<7>(t, a, mode, B, cplx, bil, st, grid);
 }
+int resident_launch_m7(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t st) {
+  return resident_launch_t<7>(t, r, cplx, st);
+}
 }  // namespace qb

@@ -281,3 +281,81 @@ def test_plain_per_sector_path_is_bit_identical_to_batched():
     qs.evolve(a, 2e-3, 40)
     qs.evolve_plain(b, 2e-3, 40)
     assert bool((a == b).all())
+
+
+def test_breaktime_pipeline_matches_oracle():
+    """Observation series on the GPU -> breaktimes, against the oracle's series:
+    Q breaktime of a coherent start, PO breaktime of a field-number start (whose
+    Q is 1 from t = 0 and is flagged AT_START), and the mean-field companion."""
+    import paper_2111_00050_gb300 as qb
+
+    M, dt, steps, every = 5, 2e-3, 400, 20
+    w = wl.dispersion_quadratic(M)
+    L = wl.long_range_coupling(M, 0.6)
+    z, _, _ = _coherent_case(M, 3.0, 13, -0.1, 4)
+    qs, os_ = pair(M, w, L, 0, 13, None)
+    psi = qs.empty_state()
+    qs.init_coherent(z, psi)
+    series = qs.evolve_observe(psi, dt, steps, every)
+    ref = orc.coherent_state(os_, z)[0]
+    ref_Q = [orc.observables(os_, ref)["Q"]]
+    for _ in range(steps // every):
+        ref = orc.rk4(os_, w, L, ref, dt, every)
+        ref_Q.append(orc.observables(os_, ref)["Q"])
+    gpu_Q = [s["Q"] for s in series]
+    np.testing.assert_allclose(gpu_Q, ref_Q, atol=OBS_TOL)
+    thr = ref_Q[0] + 0.5 * (max(ref_Q) - ref_Q[0])
+    t_gpu, f_gpu = qb.breaktime(gpu_Q, dt * every, thr)
+    t_ref, f_ref = orc.breaktime(ref_Q, dt * every, thr)
+    assert f_gpu == f_ref == qb.QB_CROSSED
+    assert abs(t_gpu - t_ref) < 1e-6
+    traj = qb.meanfield(M, w, L, z, dt, steps, every)
+    np.testing.assert_allclose(traj, orc.meanfield(w, L, z, dt, steps, every), atol=1e-11)
+
+    n = np.array([0, 2, 1, 3, 0])
+    zf = np.sqrt(n) * np.exp(1j * np.array([0.0, 0.4, 2.0, -1.1, 0.0]))
+    qf, of = pair(M, w, L, 6, 6, None)
+    pf = qf.empty_state()
+    qf.init_field_number(zf, 6, pf)
+    sf = qf.evolve_observe(pf, dt, steps, every)
+    reff = orc.field_number_state(of, zf, 6)
+    ref_PO = [orc.observables(of, reff)["PO"]]
+    for _ in range(steps // every):
+        reff = orc.rk4(of, w, L, reff, dt, every)
+        ref_PO.append(orc.observables(of, reff)["PO"])
+    gpu_PO = [s["PO"] for s in sf]
+    np.testing.assert_allclose(gpu_PO, ref_PO, atol=OBS_TOL)
+    assert qb.breaktime([s["Q"] for s in sf], dt * every, 0.15)[1] == qb.QB_AT_START
+    thr = 0.5 * max(ref_PO)
+    t_gpu, f_gpu = qb.breaktime(gpu_PO, dt * every, thr)
+    t_ref, f_ref = orc.breaktime(ref_PO, dt * every, thr)
+    assert f_gpu == f_ref == qb.QB_CROSSED and abs(t_gpu - t_ref) < 1e-6
+
+
+@pytest.mark.parametrize("steps", [5, 70])
+def test_resident_small_sectors_bit_identical_to_stage_launches(steps):
+    """M=7, N <= 12: the leading sectors (up to 1024 kets) run shared-memory
+    resident beside the stage launches of the larger ones; the state must equal
+    the all-stage-launch run bit for bit, and the oracle to 1e-10.  70 steps also
+    cover the CUDA-graph replay of the stage launches."""
+    import paper_2111_00050_gb300 as qb
+
+    M = 7
+    z, w, L = _coherent_case(M, 3.0, 12, -0.05, 5)
+    qs = qb.Space(M, w, L, 0, 12)
+    assert qs.dims.min() <= 1024 < qs.dims.max()
+    a = qs.empty_state()
+    qs.init_coherent(z, a)
+    b = a.clone()
+    c = a.clone()
+    qs.set_resident_max(1024)
+    qs.evolve(a, 1e-3, steps)
+    qs.set_resident_max(0)
+    qs.evolve(b, 1e-3, steps)
+    assert bool((a == b).all())
+    qs.evolve_plain(c, 1e-3, steps)
+    assert bool((a == c).all())
+    if steps == 5:
+        os_ = orc.Space(M, qs.sectors)
+        ref = orc.rk4(os_, w, L, orc.coherent_state(os_, z)[0], 1e-3, steps)
+        assert rel_err(to_host(a), ref) <= STATE_TOL
