@@ -40,6 +40,15 @@ namespace qb {
 // first byte of the table image the stage kernels stage in shared memory
 __host__ __device__ inline int kSmemFrom(const Tables& t) { return QB_CNT_GLOBAL ? t.o_E : 0; }
 
+// Gathered stage-vector entry: read-only global load, or a generic load when the
+// vector is a shared-memory copy (LOCAL; the non-coherent global path does not
+// accept shared addresses).
+template <bool LOCAL>
+__device__ __forceinline__ float4 gather(const float4* p) {
+  if (LOCAL) return *p;
+  return __ldg(p);
+}
+
 // One warp tile: kets [base, min(base + kWarpRows, row1)) of the launch.  With
 // LOCAL the state vectors of DfArgs are the shared-memory copies of one sector
 // starting at ket local_off (gathers and own-row accesses are sector-local);
@@ -228,7 +237,7 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
         for (int b = 0; b < B; ++b) {
           float4 x[kC > 0 ? kC : 1];
 #pragma unroll
-          for (int c = 0; c < kC; ++c) x[c] = __ldg(vsec + (size_t)b * total + rkc[c]);
+          for (int c = 0; c < kC; ++c) x[c] = gather<LOCAL>(vsec + (size_t)b * total + rkc[c]);
 #pragma unroll
           for (int c = 0; c < kC; ++c)
             dfc_fma(acc[b], f2_pack(crc[c].h, crc[c].h), f2_pack(-crc[c].h, -crc[c].h),
@@ -259,7 +268,7 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
           const dfl cr = df_mul(dfl{gf.x, gf.y}, AB);
   #pragma unroll
           for (int b = 0; b < B; ++b) {
-            const float4 x = __ldg(vsec + (size_t)b * total + rk);
+            const float4 x = gather<LOCAL>(vsec + (size_t)b * total + rk);
             const f2 xh = f2_pack(x.x, x.y), xl = f2_pack(x.z, x.w);
             dfc_fma(acc[b], f2_pack(cr.h, cr.h), f2_pack(-cr.h, -cr.h), f2_pack(cr.l, cr.l), xh, xl);
             if (CPLX) {
@@ -470,10 +479,13 @@ __global__ void __launch_bounds__(kBlock) resident_kernel(const Tables t, const 
         a.zre = r.dt / d;
         const float zh = (float)a.zre;
         a.zf = make_float2(zh, (float)(a.zre - (double)zh));
-        for (int64_t base = off + (int64_t)warp * kWarpRows; base < off + D; base += (int64_t)kWarps * kWarpRows)
-          stage_tile<MT, 1, CPLX, false, true>(t, S.v, S.sqf, S.Gf, S.dl4, a, d == 1 ? 1 : 0, base, off + D, off,
-                                               S.sidx, S.socc, S.sD, S.sOff, S.sperm, S.hist, S.cursor, bil_l,
-                                               bil_w);
+        // the sector's kets are dealt to the warps in chunks of at most kWarpRows,
+        // evenly, so that a small sector still keeps every warp busy
+        const int64_t chunk = min((int64_t)kWarpRows, ((int64_t)D + kWarps - 1) / kWarps);
+        for (int64_t base = off + (int64_t)warp * chunk; base < off + D; base += (int64_t)kWarps * chunk)
+          stage_tile<MT, 1, CPLX, false, true>(t, S.v, S.sqf, S.Gf, S.dl4, a, d == 1 ? 1 : 0, base,
+                                               min(base + chunk, off + (int64_t)D), off, S.sidx, S.socc, S.sD,
+                                               S.sOff, S.sperm, S.hist, S.cursor, bil_l, bil_w);
         __syncthreads();
       }
     }
