@@ -211,6 +211,29 @@ def adjoint_extra(qb, torch, steps: int = 20, ckpt_every: int = 10):
     return out
 
 
+def small_extra(qb, torch):
+    """The plain single-sector workload (M=5, |0,2,2,2,0>, 42 kets), the full run of
+    10^4 RK4 steps: resident (one launch for every step) against one launch per stage."""
+    W = wl.plain_single_sector()
+    qs = qb.Space(W.M, W.w, W.L, 6, 6, [0])
+    psi = qs.empty_state()
+    work = qs.workspace(1)
+    out = {"workload": W.name, "kets": qs.total, "steps": W.steps}
+    for label, kets in (("resident", 1024), ("stage_launches", 0)):
+        qs.set_resident_max(kets)
+        qs.init_number(W.occ, psi)
+        qs.evolve(psi, W.dt, 50, work)
+        qs.init_number(W.occ, psi)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        qs.evolve(psi, W.dt, W.steps, work)
+        e1.record()
+        torch.cuda.synchronize()
+        out[label + "_steps_per_s"] = W.steps / (e0.elapsed_time(e1) * 1e-3)
+    return out
+
+
 def sweep_extra(qb, torch, steps: int = 3):
     """8-member coupling sweep on the M=11, N=20, P=0 sector (2,731,365 kets, number state
     (...,7,6,7,...), w=|p|, C_k = -0.005 k): one batched launch per stage for all 8
@@ -283,6 +306,7 @@ def main():
     psi = qs.empty_state()
     init_state(qs, W, psi)
     work = qs.workspace(1)
+    resident_max = qs.autotune(W.dt, psi, steps=1, work=work)
     for _ in range(args.warmup):
         qs.evolve(psi, W.dt, 1, work)
     torch.cuda.synchronize()
@@ -378,6 +402,7 @@ def main():
         "config": {"workload": W.name, "kets": qs.total, "sectors": qs.n_sectors, "terms_per_hpsi": terms,
                    "ordered_tuples_per_hpsi": tuples, "dt": W.dt, "rk4_steps_per_s": steps_per_s,
                    "l2": "state (16 B/ket, %.2f GB) larger than L2; no flush" % (16 * qs.total / 1e9),
+                   "resident_max_kets": resident_max,
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "rk4_steps_per_s": steps_per_s,
         "plain_per_sector": plain,
@@ -391,6 +416,7 @@ def main():
         torch.cuda.empty_cache()
         line["adjoint"] = adjoint_extra(qb, torch)
         line["sweep"] = sweep_extra(qb, torch)
+        line["small_sector"] = small_extra(qb, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W)
     if rank == 0:
