@@ -35,8 +35,8 @@ import workloads as wl  # noqa: E402
 # (a DFMA microbenchmark measured 1.00 TFLOP/s: python -m paper_2111_00050_gb300.probe)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per ket of one stage launch, from an ncu capture of the current stage kernel
-# (batched coherent at n_tot=12: 727.8 MB over 15,380,937 kets); scaled by kets
-STAGE_DRAM_BYTES_PER_KET = 727.8e6 / 15380937
+# (batched coherent at n_tot=12: 729.9 MB over 15,380,937 kets); scaled by kets
+STAGE_DRAM_BYTES_PER_KET = 729.9e6 / 15380937
 
 
 def _peaks():

@@ -288,6 +288,7 @@ __device__ __forceinline__ dfc dfc_renorm(dfc a) {
 //   1  psi += z H x;          out = df(psi)       (forward final stage, FP64 psi)
 //   2  out  = z H x                               (adjoint: costate stage vector)
 //   3  psi += sum_k basef[k] + z H x; out = df(psi)  (adjoint: new costate, FP64)
+//   4  no output; with bilinears on, partial[block][0] = sum Re(conj(x_i) (H x)_i)
 // For the adjoint pass zre = -c dt, i.e. z = +i c dt.  With bilinears on, every
 // row also adds Im <pair_i, H_L x_i> and n_q(i) Im(conj(x_i) pair_i) to per-CTA
 // sums written to partial[block][M + 1] (H_L: the two-body part at scale 1).

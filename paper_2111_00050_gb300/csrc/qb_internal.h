@@ -77,6 +77,7 @@ struct Space {
   int32_t* d_secOf = nullptr;
   double* d_scratch = nullptr;  // reduction partials
   float4* d_diag = nullptr;     // per ket: one-body and two-body diagonal as double-float pairs
+  float4* d_obsf = nullptr;     // double-float copy of the state being observed (qb_observables)
   int64_t scratch_doubles = 0;
   Tables t{};
   cudaStream_t capture_stream = nullptr;  // private stream on which RK4 chunks are captured into graphs

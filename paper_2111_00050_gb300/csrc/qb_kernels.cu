@@ -519,6 +519,186 @@ __global__ void __launch_bounds__(kBlock) moments_kernel(const Tables t, const d
   }
 }
 
+
+// Double-float moments: the same sums as moments_kernel from the double-float copy
+// of the state (no FP64 arithmetic per target); each warp's 32 kets are summed in
+// double-float by shuffles and added to the per-warp FP64 accumulators once.
+
+// rank of the ket reached by changing mode e0 by dn0 and (nch = 2) mode e1 by dn1
+__device__ __forceinline__ int64_t rank_moved(const Tables& t, const View& v, const RowScratch& rs, int nch, int e0,
+                                              int dn0, int e1, int dn1, int64_t Dt) {
+  const int M = t.M, tid = threadIdx.x, twoM = 2 * M;
+  if (nch < 2) {
+    e1 = 0;
+    dn1 = 0;
+  }
+  const int top = max(e0, e1);
+  int64_t sum = rs.pe[(M - 1) * kBlock + tid] - rs.pe[top * kBlock + tid];
+  int dc = 0, dk = 0;
+  for (int m = top; m >= 1; --m) {
+    if (m == e0) {
+      dc += dn0;
+      dk += dn0 * m;
+    }
+    if (m == e1) {
+      dc += dn1;
+      dk += dn1 * m;
+    }
+    int dkm = dk % M;
+    if (dkm < 0) dkm += M;
+    sum += v.E[rs.idx[m * kBlock + tid] + dc * twoM + dkm];
+  }
+  return Dt - 1 - sum;
+}
+
+__device__ __forceinline__ dfl warp_sum_df(dfl x) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const dfl y{__shfl_down_sync(0xffffffffu, x.h, o), __shfl_down_sync(0xffffffffu, x.l, o)};
+    x = df_add(x, y);
+  }
+  return x;
+}
+
+__global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, const float4* psif, double* partial,
+                                                             int nmom, int* status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  load_blob(t, smem);
+  const View v = make_view(t, smem);
+  const float2* sqf = reinterpret_cast<const float2*>(smem + t.o_sqf);
+  const size_t blob_al = (t.blob_bytes + 15) & ~15;
+  const RowScratch rs = row_scratch(smem + blob_al);
+  double* acc = reinterpret_cast<double*>(smem + blob_al + ((kRowScratchBytes + 15) & ~15));  // [warps][nmom]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, M = t.M;
+  for (int k = tid; k < (kBlock / 32) * nmom; k += kBlock) acc[k] = 0.0;
+  __syncthreads();
+  double* wacc = acc + (size_t)warp * nmom;
+  const int oA = 4, oM = 4 + 2 * M, oAA = 4 + 2 * M + 2 * M * M;
+  const dfl zero{0.f, 0.f};
+
+  for (int64_t base = (int64_t)blockIdx.x * kBlock; base < t.total; base += (int64_t)gridDim.x * kBlock) {
+    const int64_t g = base + tid;
+    const bool live = g < t.total;
+    int N = 0, K = 0;
+    dfl xr = zero, xi = zero;
+    if (live) {
+      const int sid = find_sector(t, g);
+      const int64_t off = __ldg(t.sec_off + sid);
+      const int64_t D = __ldg(t.sec_off + sid + 1) - off;
+      N = __ldg(t.sec_N + sid);
+      K = __ldg(t.sec_K + sid);
+      setup_row(t, v, rs, N, K, D, g - off);
+      const float4 x = psif[g];
+      xr = df_re(x);
+      xi = df_im(x);
+    }
+    {
+      const dfl p2 = df_add(df_mul(xr, xr), df_mul(xi, xi));
+      const dfl c0 = warp_sum_df(p2), c1 = warp_sum_df(df_mul(p2, dfl{(float)N, 0.f}));
+      if (lane == 0) {
+        wacc[0] += df_to(c0);
+        wacc[1] += df_to(c1);
+      }
+    }
+    // adds c conj(y) x for the target ket tg to moment slot `slot`
+    auto contrib = [&](int slot, bool has, int64_t tg, dfl c) {
+      dfl cr = zero, ci = zero;
+      if (has && (tg < 0 || tg >= t.total)) {
+        atomicOr(status, 1);
+        has = false;
+      }
+      if (has) {
+        const float4 y = psif[tg];
+        const dfl yr = df_re(y), yi = df_im(y);
+        cr = df_mul(c, df_add(df_mul(yr, xr), df_mul(yi, xi)));
+        ci = df_mul(c, df_add(df_mul(yr, xi), df_neg(df_mul(yi, xr))));
+      }
+      if (__any_sync(0xffffffffu, has)) {
+        cr = warp_sum_df(cr);
+        ci = warp_sum_df(ci);
+        if (lane == 0) {
+          wacc[slot] += df_to(cr);
+          wacc[slot + 1] += df_to(ci);
+        }
+      }
+    };
+    const uint8_t* occ = rs.occ + tid;
+    auto sq = [&](int k) {
+      const float2 f = sqf[k];
+      return dfl{f.x, f.y};
+    };
+    // <a_i>
+    for (int i = 0; i < M; ++i) {
+      bool has = false;
+      int64_t tg = 0;
+      dfl c = zero;
+      if (live && occ[i * kBlock] >= 1 && N >= 1) {
+        const int Kt = ((K - i) % M + M) % M;
+        const int sid = __ldg(t.sec_of + (N - 1) * M + Kt);
+        if (sid >= 0) {
+          const int64_t off = __ldg(t.sec_off + sid), D = __ldg(t.sec_off + sid + 1) - off;
+          tg = off + rank_moved(t, v, rs, 1, i, -1, 0, 0, D);
+          c = sq(occ[i * kBlock]);
+          has = true;
+        }
+      }
+      contrib(oA + 2 * i, has, tg, c);
+    }
+    // <a_i^dag a_j>
+    for (int i = 0; i < M; ++i)
+      for (int j = 0; j < M; ++j) {
+        bool has = false;
+        int64_t tg = 0;
+        dfl c = zero;
+        if (live && occ[j * kBlock] >= 1) {
+          if (i == j) {
+            tg = g;
+            c = dfl{(float)occ[i * kBlock], 0.f};
+            has = true;
+          } else {
+            const int Kt = ((K - j + i) % M + M) % M;
+            const int sid = __ldg(t.sec_of + N * M + Kt);
+            if (sid >= 0) {
+              const int64_t off = __ldg(t.sec_off + sid), D = __ldg(t.sec_off + sid + 1) - off;
+              tg = off + rank_moved(t, v, rs, 2, j, -1, i, 1, D);
+              c = df_mul(sq(occ[j * kBlock]), sq(occ[i * kBlock] + 1));
+              has = true;
+            }
+          }
+        }
+        contrib(oM + 2 * (i * M + j), has, tg, c);
+      }
+    // <a_i a_j>, i <= j (the matrix is symmetric)
+    for (int i = 0; i < M; ++i)
+      for (int j = i; j < M; ++j) {
+        bool has = false;
+        int64_t tg = 0;
+        dfl c = zero;
+        if (live && N >= 2) {
+          const int ni = occ[i * kBlock], nj = occ[j * kBlock];
+          const bool ok = (i == j) ? (ni >= 2) : (ni >= 1 && nj >= 1);
+          if (ok) {
+            const int Kt = ((K - i - j) % M + M) % M;
+            const int sid = __ldg(t.sec_of + (N - 2) * M + Kt);
+            if (sid >= 0) {
+              const int64_t off = __ldg(t.sec_off + sid), D = __ldg(t.sec_off + sid + 1) - off;
+              tg = off + ((i == j) ? rank_moved(t, v, rs, 1, i, -2, 0, 0, D)
+                                   : rank_moved(t, v, rs, 2, i, -1, j, -1, D));
+              c = (i == j) ? df_mul(sq(ni), sq(ni - 1)) : df_mul(sq(ni), sq(nj));
+              has = true;
+            }
+          }
+        }
+        contrib(oAA + 2 * (i * M + j), has, tg, c);
+      }
+  }
+  __syncthreads();
+  for (int k = tid; k < nmom; k += kBlock) {
+    double s = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) s += acc[(size_t)w * nmom + k];
+    partial[(size_t)blockIdx.x * nmom + k] = s;
+  }
+}
+
 // ------------------------------------------------------------------ host side
 
 static size_t row_smem(const Tables& t) { return ((t.blob_bytes + 15) & ~15) + kRowScratchBytes; }
@@ -543,14 +723,14 @@ static int check_status(const Space& s, cudaStream_t st) {
 
 // Scratch layout (doubles), sized at space setup for the largest persistent
 // grid G = sms * 16:  [0, 2) status word | partials [G * nmom] | final [nmom]
-// | dot partials [2 G] | dot final [2] | amplitude table [2 M (nmax+1)] | init final [2]
+// | dot partials [(M + 1) G] | dot final [QB_MAX_MODES + 2] | amplitude table [2 M (nmax+1)] | init final [2]
 static int nmoments(int M);
 static int64_t max_grid_of(const Space& s) { return s.scratch_doubles > 0 ? (int64_t)s.grid_hpsi : 0; }
 static double* partial_area(const Space& s) { return s.d_scratch + 2; }
 static double* final_area(const Space& s) { return partial_area(s) + max_grid_of(s) * nmoments(s.M); }
 static double* dot_area(const Space& s) { return final_area(s) + nmoments(s.M); }
-static double* dot_final(const Space& s) { return dot_area(s) + 2 * max_grid_of(s); }
-static double* table_area(const Space& s) { return dot_final(s) + 2; }
+static double* dot_final(const Space& s) { return dot_area(s) + (int64_t)(s.M + 1) * max_grid_of(s); }
+static double* table_area(const Space& s) { return dot_final(s) + kMaxM + 2; }
 static double* init_final(const Space& s) { return table_area(s) + 2 * (size_t)s.M * (s.nmax + 1); }
 
 int device_setup(Space& s) {
@@ -581,11 +761,12 @@ int device_setup(Space& s) {
   QB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s.device));
   const int64_t max_grid = (int64_t)sms * 16;
   s.grid_hpsi = (int)max_grid;
-  s.scratch_doubles = 2 + max_grid * nmoments(s.M) + nmoments(s.M) + 2 * max_grid + 2 +
+  s.scratch_doubles = 2 + max_grid * nmoments(s.M) + nmoments(s.M) + (int64_t)(s.M + 1) * max_grid + kMaxM + 2 +
                       2 * (int64_t)s.M * (s.nmax + 1) + 2;
   QB_CUDA(cudaMalloc(&s.d_scratch, sizeof(double) * s.scratch_doubles));
   QB_CUDA(cudaMemset(s.d_scratch, 0, sizeof(double) * s.scratch_doubles));
   QB_CUDA(cudaMalloc(&s.d_diag, sizeof(float4) * (size_t)t.total));
+  QB_CUDA(cudaMalloc(&s.d_obsf, sizeof(float4) * (size_t)t.total));
   {
     const size_t smem = row_smem(t);
     int grid = 0;
@@ -883,38 +1064,42 @@ int launch_number(const Space& s, int64_t index, void* d_psi, void* stream) {
 int launch_moments(Space& s, const void* d_psi, double* out_host, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const int nmom = nmoments(s.M);
+  int rc = launch_to_df(d_psi, s.d_obsf, s.t.total, stream);
+  if (rc) return rc;
   const size_t smem = row_smem(s.t) + ((kRowScratchBytes + 15) & ~15) - kRowScratchBytes +
                       (size_t)(kBlock / 32) * nmom * sizeof(double) + 16;
   int grid = 0;
-  int rc = persistent_grid(moments_kernel, smem, s.t.total, &grid);
+  rc = persistent_grid(moments_df_kernel, smem, s.t.total, &grid);
   if (rc) return rc;
   double* part = partial_area(s);
-  moments_kernel<<<grid, kBlock, smem, st>>>(s.t, (const double2*)d_psi, part, nmom,
-                                             reinterpret_cast<int*>(s.d_scratch));
+  moments_df_kernel<<<grid, kBlock, smem, st>>>(s.t, s.d_obsf, part, nmom, reinterpret_cast<int*>(s.d_scratch));
   QB_CUDA(cudaGetLastError());
   double* fin = final_area(s);
   reduce_partials_kernel<<<(nmom + 127) / 128, 128, 0, st>>>(part, grid, nmom, fin);
   QB_CUDA(cudaGetLastError());
   QB_CUDA(cudaMemcpyAsync(out_host, fin, sizeof(double) * nmom, cudaMemcpyDeviceToHost, st));
-  // <H> = <psi|H psi>
-  StageArgs a{};
-  a.vin = (const double2*)d_psi;
-  a.scale[0] = 1.0;
+  // <H> = <psi|H psi>: the double-float stage kernel in its reduction-only mode
+  DfArgs a{};
+  a.vin = s.d_obsf;
+  a.diag = s.d_diag;
+  a.scale[0] = make_float2(1.0f, 0.0f);
+  a.row0 = 0;
+  a.row1 = s.t.total;
   a.status = reinterpret_cast<int*>(s.d_scratch);
-  double* dpart = dot_area(s);
-  a.partial = dpart;
+  a.partial = dot_area(s);
   int g2 = 0;
-  rc = launch_stage_c<MODE_DOT, 1>(s, a, st, &g2);
+  rc = stage_launch(s.t, a, 4, 1, s.t.is_complex != 0, st, &g2, true);
   if (rc) return rc;
   double* hfin = dot_final(s);
-  reduce_partials_kernel<<<1, 32, 0, st>>>(dpart, g2, 2, hfin);
+  reduce_partials_kernel<<<1, 32, 0, st>>>(a.partial, g2, s.M + 1, hfin);
   QB_CUDA(cudaGetLastError());
-  double h2[2];
-  QB_CUDA(cudaMemcpyAsync(h2, hfin, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  double h2[1];
+  QB_CUDA(cudaMemcpyAsync(h2, hfin, sizeof(double), cudaMemcpyDeviceToHost, st));
   QB_CUDA(cudaStreamSynchronize(st));
   out_host[2] = h2[0];
   return check_status(s, st);
 }
+
 
 
 // ----------------------------------------------- allocation-free observables

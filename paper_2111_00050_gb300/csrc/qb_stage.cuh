@@ -297,6 +297,10 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
       const float4 xo = a.vin[(size_t)b * total + ri];
       const dfl hr = df_add(df_mul(dg, df_re(xo)), df_mul(sc, acc_r));
       const dfl hi = df_add(df_mul(dg, df_im(xo)), df_mul(sc, acc_i));
+      if (BIL && mode == 4) {  // <x|H|x>: Re(conj(x) Hx) of this row, no output
+        bil_l = df_add(bil_l, df_add(df_mul(df_re(xo), hr), df_mul(df_im(xo), hi)));
+        continue;
+      }
       if (BIL && b == 0) {
         // H_L x (two-body part at scale 1) and the pair vector of this row
         const float4 pp = a.pair[ri];
