@@ -182,7 +182,9 @@ int qb_evolve_plain(qb_space* space, void* d_psi, double dt, int64_t steps, void
 
 /* ---- observables (Sec. II C-E) ------------------------------------------- */
 
-/* All observables of one state; out (host) is written after the stream syncs. */
+/* All observables of one state; out (host) is written after the stream syncs.
+ * The moments are summed in double-float arithmetic from a double-float copy of
+ * the state (about 48 significant bits): absolute errors of order 1e-14 n_tot. */
 int qb_observables(qb_space* space, const void* d_psi, qb_obs* out, void* stream);
 
 /* Evolution with observation: series[0] is the initial state, series[k] the

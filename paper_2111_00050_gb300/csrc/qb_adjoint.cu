@@ -289,9 +289,15 @@ extern "C" int qb_adjoint(qb_space* space, const double* z, double scale, double
   }
 
   // ---- loss and seed lam_N = d loss / d psi^*
+  // the loss in FP64 arithmetic throughout (qb_observables works in double-float)
   qb_obs ob;
-  rc = qb_observables(space, L.psi, &ob, stream);
-  if (rc) return rc;
+  {
+    std::vector<double> raw(4 + 2 * M + 4 * (size_t)M * M, 0.0);
+    rc = launch_moments_fp64(*sp, L.psi, raw.data(), stream);
+    if (rc) return rc;
+    if (!(raw[0] > 0.0)) return fail(QB_EINVAL, "the final state has zero norm");
+    derive(M, raw.data(), &ob);
+  }
   SeedArgs sa{};
   sa.psi = L.psi;
   sa.lam = L.lam;
