@@ -521,8 +521,25 @@ __global__ void __launch_bounds__(kBlock) moments_kernel(const Tables t, const d
 
 
 // Double-float moments: the same sums as moments_kernel from the double-float copy
-// of the state (no FP64 arithmetic per target); each warp's 32 kets are summed in
-// double-float by shuffles and added to the per-warp FP64 accumulators once.
+// of the state (no FP64 arithmetic per target).
+//
+// Every tile of 32 kets (one per lane) emits the same sequence of values: norm,
+// N norm, Re and Im of each <a_i> term, the diagonal n_i |psi|^2, Re and Im of
+// each <a_i^dag a_j> term with i < j (the i > j half follows by Hermiticity) and
+// of each <a_i a_j> term with i <= j (the matrix is symmetric).  A lane writes its
+// value into column `lane` of a per-warp 16 x 32 buffer; once 16 values are in,
+// lane r < 16 sums row r over the warp's 32 kets and adds the sum to the warp's
+// double-float accumulator of that value.  The sector offsets and the (N, K) ->
+// sector map are staged in shared memory when they are small.
+
+// x mod M for x in (-2M, 3M), by conditional adds (no integer division)
+__device__ __forceinline__ int mod_small(int x, int M) {
+  if (x < 0) x += M;
+  if (x < 0) x += M;
+  if (x >= M) x -= M;
+  if (x >= M) x -= M;
+  return x;
+}
 
 // rank of the ket reached by changing mode e0 by dn0 and (nch = 2) mode e1 by dn1
 __device__ __forceinline__ int64_t rank_moved(const Tables& t, const View& v, const RowScratch& rs, int nch, int e0,
@@ -534,46 +551,152 @@ __device__ __forceinline__ int64_t rank_moved(const Tables& t, const View& v, co
   }
   const int top = max(e0, e1);
   int64_t sum = rs.pe[(M - 1) * kBlock + tid] - rs.pe[top * kBlock + tid];
-  int dc = 0, dk = 0;
+  int dc = 0, dkm = 0;  // dkm = (momentum change) mod M, kept in [0, M) without a division
   for (int m = top; m >= 1; --m) {
     if (m == e0) {
       dc += dn0;
-      dk += dn0 * m;
+      dkm = mod_small(dkm + dn0 * m, M);
     }
     if (m == e1) {
       dc += dn1;
-      dk += dn1 * m;
+      dkm = mod_small(dkm + dn1 * m, M);
     }
-    int dkm = dk % M;
-    if (dkm < 0) dkm += M;
     sum += v.E[rs.idx[m * kBlock + tid] + dc * twoM + dkm];
   }
   return Dt - 1 - sum;
 }
 
-__device__ __forceinline__ dfl warp_sum_df(dfl x) {
-  for (int o = 16; o > 0; o >>= 1) {
-    const dfl y{__shfl_down_sync(0xffffffffu, x.h, o), __shfl_down_sync(0xffffffffu, x.l, o)};
-    x = df_add(x, y);
+// number of values a tile emits
+__host__ __device__ inline int moment_values(int M) { return 2 + 3 * M + 2 * M * M; }
+
+// moment slot(s) of value e: out[k1] += x and, when k2 >= 0, out[k2] += s2 x
+__device__ inline void moment_fold(int e, int M, int& k1, int& k2, double& s2) {
+  const int oA = 4, oM = 4 + 2 * M, oAA = 4 + 2 * M + 2 * M * M;
+  k2 = -1;
+  s2 = 1.0;
+  if (e < 2) {
+    k1 = e;
+    return;
   }
-  return x;
+  e -= 2;
+  if (e < 2 * M) {
+    k1 = oA + e;
+    return;
+  }
+  e -= 2 * M;
+  if (e < M) {
+    k1 = oM + 2 * (e * M + e);
+    return;
+  }
+  e -= M;
+  if (e < M * (M - 1)) {
+    int u = e >> 1, i = 0;
+    const int part = e & 1;
+    while (u >= M - 1 - i) {
+      u -= M - 1 - i;
+      ++i;
+    }
+    const int j = i + 1 + u;
+    k1 = oM + 2 * (i * M + j) + part;
+    k2 = oM + 2 * (j * M + i) + part;  // <a_j^dag a_i> = conj <a_i^dag a_j>
+    s2 = part ? -1.0 : 1.0;
+    return;
+  }
+  e -= M * (M - 1);
+  int u = e >> 1, i = 0;
+  const int part = e & 1;
+  while (u >= M - i) {
+    u -= M - i;
+    ++i;
+  }
+  k1 = oAA + 2 * (i * M + i + u) + part;
+}
+
+constexpr int kTrRows = 16;    // values per flush of the per-warp transpose buffer
+constexpr int kTrStride = 33;  // row stride (float2) of that buffer
+// the block's FP64 moment row reuses the transpose buffers at the end
+static_assert((kBlock / 32) * kTrRows * kTrStride * sizeof(float2) >=
+                  (4 + 2 * kMaxM + 4 * kMaxM * kMaxM) * sizeof(double),
+              "moment row does not fit the transpose buffers");
+constexpr size_t kMomSecSmemMax = 16384;  // sector tables larger than this stay in global memory
+
+static size_t mom_sec_bytes(const Tables& t) {
+  return ((sizeof(int64_t) * (size_t)(t.n_sectors + 1) + 15) & ~(size_t)15) +
+         ((sizeof(int32_t) * (size_t)(t.nmax + 1) * t.M + 15) & ~(size_t)15);
+}
+
+__device__ __forceinline__ int find_sector_in(const int64_t* off, int n, int64_t g) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= g)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
 }
 
 __global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, const float4* psif, double* partial,
-                                                             int nmom, int* status) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  load_blob(t, smem);
-  const View v = make_view(t, smem);
+                                                             int nmom, int sec_smem, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  load_blob_from(t, smem_raw, t.o_E);
+  unsigned char* smem = smem_raw - t.o_E;
+  View v = make_view(t, smem);
+  v.cnt = reinterpret_cast<const uint32_t*>(t.blob + t.o_cnt);  // fill counts stay in global memory
   const float2* sqf = reinterpret_cast<const float2*>(smem + t.o_sqf);
-  const size_t blob_al = (t.blob_bytes + 15) & ~15;
-  const RowScratch rs = row_scratch(smem + blob_al);
-  double* acc = reinterpret_cast<double*>(smem + blob_al + ((kRowScratchBytes + 15) & ~15));  // [warps][nmom]
+  unsigned char* cur = smem_raw + ((t.blob_bytes - t.o_E + 15) & ~15);
+  const RowScratch rs = row_scratch(cur);
+  cur += (kRowScratchBytes + 15) & ~15;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, M = t.M;
-  for (int k = tid; k < (kBlock / 32) * nmom; k += kBlock) acc[k] = 0.0;
+  const int64_t* soff = t.sec_off;
+  const int32_t* sof = t.sec_of;
+  if (sec_smem) {
+    int64_t* o = reinterpret_cast<int64_t*>(cur);
+    for (int k = tid; k <= t.n_sectors; k += kBlock) o[k] = __ldg(t.sec_off + k);
+    cur += (sizeof(int64_t) * (size_t)(t.n_sectors + 1) + 15) & ~(size_t)15;
+    int32_t* f = reinterpret_cast<int32_t*>(cur);
+    for (int k = tid; k < (t.nmax + 1) * M; k += kBlock) f[k] = __ldg(t.sec_of + k);
+    cur += (sizeof(int32_t) * (size_t)(t.nmax + 1) * M + 15) & ~(size_t)15;
+    soff = o;
+    sof = f;
+  }
+  const int nval = moment_values(M), nval_pad = (nval + 31) & ~31;
+  float2* tr = reinterpret_cast<float2*>(cur);               // [warps][kTrRows][kTrStride]
+  float2* wacc = tr + (kBlock / 32) * kTrRows * kTrStride;  // [warps][nval_pad]
+  float2* wb = tr + warp * kTrRows * kTrStride;
+  float2* wa = wacc + warp * nval_pad;
+  for (int k = lane; k < nval_pad; k += 32) wa[k] = make_float2(0.f, 0.f);
   __syncthreads();
-  double* wacc = acc + (size_t)warp * nmom;
-  const int oA = 4, oM = 4 + 2 * M, oAA = 4 + 2 * M + 2 * M * M;
   const dfl zero{0.f, 0.f};
+
+  int ecount = 0;  // warp-uniform: values emitted in this tile
+  // lanes r < n add the sum of buffer row r to accumulator e0 + r
+  auto flush = [&](int n, int e0) {
+    __syncwarp();
+    if (lane < n) {
+      const float2* row = wb + lane * kTrStride;
+      float h = row[0].x, l = row[0].y;
+#pragma unroll 8
+      for (int k = 1; k < 32; ++k) {
+        const float2 x = row[k];
+        const float s = __fadd_rn(h, x.x);
+        const float bb = __fsub_rn(s, h);
+        const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(x.x, bb));
+        h = s;
+        l = __fadd_rn(l, __fadd_rn(err, x.y));
+      }
+      const float2 a0 = wa[e0 + lane];
+      const dfl r = df_add(dfl{a0.x, a0.y}, df_renorm(dfl{h, l}));
+      wa[e0 + lane] = make_float2(r.h, r.l);
+    }
+    __syncwarp();
+  };
+  auto emit = [&](dfl x) {
+    wb[(ecount % kTrRows) * kTrStride + lane] = make_float2(x.h, x.l);
+    ++ecount;
+    if (ecount % kTrRows == 0) flush(kTrRows, ecount - kTrRows);
+  };
 
   for (int64_t base = (int64_t)blockIdx.x * kBlock; base < t.total; base += (int64_t)gridDim.x * kBlock) {
     const int64_t g = base + tid;
@@ -581,9 +704,9 @@ __global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, cons
     int N = 0, K = 0;
     dfl xr = zero, xi = zero;
     if (live) {
-      const int sid = find_sector(t, g);
-      const int64_t off = __ldg(t.sec_off + sid);
-      const int64_t D = __ldg(t.sec_off + sid + 1) - off;
+      const int sid = find_sector_in(soff, t.n_sectors, g);
+      const int64_t off = soff[sid];
+      const int64_t D = soff[sid + 1] - off;
       N = __ldg(t.sec_N + sid);
       K = __ldg(t.sec_K + sid);
       setup_row(t, v, rs, N, K, D, g - off);
@@ -591,16 +714,13 @@ __global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, cons
       xr = df_re(x);
       xi = df_im(x);
     }
-    {
-      const dfl p2 = df_add(df_mul(xr, xr), df_mul(xi, xi));
-      const dfl c0 = warp_sum_df(p2), c1 = warp_sum_df(df_mul(p2, dfl{(float)N, 0.f}));
-      if (lane == 0) {
-        wacc[0] += df_to(c0);
-        wacc[1] += df_to(c1);
-      }
-    }
-    // adds c conj(y) x for the target ket tg to moment slot `slot`
-    auto contrib = [&](int slot, bool has, int64_t tg, dfl c) {
+    const uint8_t* occ = rs.occ + tid;
+    ecount = 0;
+    const dfl p2 = df_add(df_mul(xr, xr), df_mul(xi, xi));
+    emit(p2);
+    emit(df_mul(p2, dfl{(float)N, 0.f}));
+    // emits c conj(y) x for the target ket tg
+    auto contrib = [&](bool has, int64_t tg, dfl c) {
       dfl cr = zero, ci = zero;
       if (has && (tg < 0 || tg >= t.total)) {
         atomicOr(status, 1);
@@ -612,62 +732,49 @@ __global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, cons
         cr = df_mul(c, df_add(df_mul(yr, xr), df_mul(yi, xi)));
         ci = df_mul(c, df_add(df_mul(yr, xi), df_neg(df_mul(yi, xr))));
       }
-      if (__any_sync(0xffffffffu, has)) {
-        cr = warp_sum_df(cr);
-        ci = warp_sum_df(ci);
-        if (lane == 0) {
-          wacc[slot] += df_to(cr);
-          wacc[slot + 1] += df_to(ci);
-        }
-      }
+      emit(cr);
+      emit(ci);
     };
-    const uint8_t* occ = rs.occ + tid;
     auto sq = [&](int k) {
       const float2 f = sqf[k];
       return dfl{f.x, f.y};
     };
-    // <a_i>
+    // <a_i>: target (N - 1, K - i)
     for (int i = 0; i < M; ++i) {
       bool has = false;
       int64_t tg = 0;
       dfl c = zero;
-      if (live && occ[i * kBlock] >= 1 && N >= 1) {
-        const int Kt = ((K - i) % M + M) % M;
-        const int sid = __ldg(t.sec_of + (N - 1) * M + Kt);
+      if (live && occ[i * kBlock] >= 1) {
+        const int sid = sof[(N - 1) * M + mod_small(K - i, M)];
         if (sid >= 0) {
-          const int64_t off = __ldg(t.sec_off + sid), D = __ldg(t.sec_off + sid + 1) - off;
+          const int64_t off = soff[sid], D = soff[sid + 1] - off;
           tg = off + rank_moved(t, v, rs, 1, i, -1, 0, 0, D);
           c = sq(occ[i * kBlock]);
           has = true;
         }
       }
-      contrib(oA + 2 * i, has, tg, c);
+      contrib(has, tg, c);
     }
-    // <a_i^dag a_j>
+    // <a_i^dag a_i> = n_i
+    for (int i = 0; i < M; ++i) emit(df_mul(p2, dfl{(float)occ[i * kBlock], 0.f}));
+    // <a_i^dag a_j>, i < j: target (N, K + i - j)
     for (int i = 0; i < M; ++i)
-      for (int j = 0; j < M; ++j) {
+      for (int j = i + 1; j < M; ++j) {
         bool has = false;
         int64_t tg = 0;
         dfl c = zero;
         if (live && occ[j * kBlock] >= 1) {
-          if (i == j) {
-            tg = g;
-            c = dfl{(float)occ[i * kBlock], 0.f};
+          const int sid = sof[N * M + mod_small(K - j + i, M)];
+          if (sid >= 0) {
+            const int64_t off = soff[sid], D = soff[sid + 1] - off;
+            tg = off + rank_moved(t, v, rs, 2, j, -1, i, 1, D);
+            c = df_mul(sq(occ[j * kBlock]), sq(occ[i * kBlock] + 1));
             has = true;
-          } else {
-            const int Kt = ((K - j + i) % M + M) % M;
-            const int sid = __ldg(t.sec_of + N * M + Kt);
-            if (sid >= 0) {
-              const int64_t off = __ldg(t.sec_off + sid), D = __ldg(t.sec_off + sid + 1) - off;
-              tg = off + rank_moved(t, v, rs, 2, j, -1, i, 1, D);
-              c = df_mul(sq(occ[j * kBlock]), sq(occ[i * kBlock] + 1));
-              has = true;
-            }
           }
         }
-        contrib(oM + 2 * (i * M + j), has, tg, c);
+        contrib(has, tg, c);
       }
-    // <a_i a_j>, i <= j (the matrix is symmetric)
+    // <a_i a_j>, i <= j: target (N - 2, K - i - j)
     for (int i = 0; i < M; ++i)
       for (int j = i; j < M; ++j) {
         bool has = false;
@@ -677,10 +784,9 @@ __global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, cons
           const int ni = occ[i * kBlock], nj = occ[j * kBlock];
           const bool ok = (i == j) ? (ni >= 2) : (ni >= 1 && nj >= 1);
           if (ok) {
-            const int Kt = ((K - i - j) % M + M) % M;
-            const int sid = __ldg(t.sec_of + (N - 2) * M + Kt);
+            const int sid = sof[(N - 2) * M + mod_small(K - i - j, M)];
             if (sid >= 0) {
-              const int64_t off = __ldg(t.sec_off + sid), D = __ldg(t.sec_off + sid + 1) - off;
+              const int64_t off = soff[sid], D = soff[sid + 1] - off;
               tg = off + ((i == j) ? rank_moved(t, v, rs, 1, i, -2, 0, 0, D)
                                    : rank_moved(t, v, rs, 2, i, -1, j, -1, D));
               c = (i == j) ? df_mul(sq(ni), sq(ni - 1)) : df_mul(sq(ni), sq(nj));
@@ -688,15 +794,29 @@ __global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, cons
             }
           }
         }
-        contrib(oAA + 2 * (i * M + j), has, tg, c);
+        contrib(has, tg, c);
       }
+    if (ecount % kTrRows) flush(ecount % kTrRows, ecount - ecount % kTrRows);
   }
   __syncthreads();
-  for (int k = tid; k < nmom; k += kBlock) {
-    double s = 0.0;
-    for (int w = 0; w < kBlock / 32; ++w) s += acc[(size_t)w * nmom + k];
-    partial[(size_t)blockIdx.x * nmom + k] = s;
+  // the warps' accumulators into one FP64 row per block (the transpose buffers are free now)
+  double* acc = reinterpret_cast<double*>(tr);
+  for (int k = tid; k < nmom; k += kBlock) acc[k] = 0.0;
+  __syncthreads();
+  for (int w = 0; w < kBlock / 32; ++w) {
+    if (warp == w)
+      for (int e = lane; e < nval; e += 32) {
+        const float2 a0 = wacc[w * nval_pad + e];
+        const double x = (double)a0.x + (double)a0.y;
+        int k1, k2;
+        double s2;
+        moment_fold(e, M, k1, k2, s2);
+        acc[k1] += x;
+        if (k2 >= 0) acc[k2] += s2 * x;
+      }
+    __syncthreads();
   }
+  for (int k = tid; k < nmom; k += kBlock) partial[(size_t)blockIdx.x * nmom + k] = acc[k];
 }
 
 // ------------------------------------------------------------------ host side
@@ -1104,13 +1224,17 @@ int launch_moments(Space& s, const void* d_psi, double* out_host, void* stream) 
   const int nmom = nmoments(s.M);
   int rc = launch_to_df(d_psi, s.d_obsf, s.t.total, stream);
   if (rc) return rc;
-  const size_t smem = row_smem(s.t) + ((kRowScratchBytes + 15) & ~15) - kRowScratchBytes +
-                      (size_t)(kBlock / 32) * nmom * sizeof(double) + 16;
+  const size_t tr_bytes = (size_t)(kBlock / 32) * kTrRows * kTrStride * sizeof(float2);
+  const int sec_smem = mom_sec_bytes(s.t) <= kMomSecSmemMax ? 1 : 0;
+  const size_t smem = ((size_t)(s.t.blob_bytes - s.t.o_E + 15) & ~(size_t)15) + ((kRowScratchBytes + 15) & ~15) +
+                      (sec_smem ? mom_sec_bytes(s.t) : 0) + tr_bytes +
+                      (size_t)(kBlock / 32) * ((moment_values(s.M) + 31) & ~31) * sizeof(float2);
   int grid = 0;
   rc = persistent_grid(moments_df_kernel, smem, s.t.total, &grid);
   if (rc) return rc;
   double* part = partial_area(s);
-  moments_df_kernel<<<grid, kBlock, smem, st>>>(s.t, s.d_obsf, part, nmom, reinterpret_cast<int*>(s.d_scratch));
+  moments_df_kernel<<<grid, kBlock, smem, st>>>(s.t, s.d_obsf, part, nmom, sec_smem,
+                                                 reinterpret_cast<int*>(s.d_scratch));
   QB_CUDA(cudaGetLastError());
   double* fin = final_area(s);
   reduce_partials_kernel<<<(nmom + 127) / 128, 128, 0, st>>>(part, grid, nmom, fin);
