@@ -336,7 +336,7 @@ __host__ __device__ inline size_t df_scratch_bytes(int M, int n_ann) {
 // Resident CTAs per SM of `kernel` with `smem` dynamic shared memory, cached
 // per (kernel, smem) so that launch loops do not repeat the occupancy query.
 template <typename K>
-static int occupancy_cached(K kernel, size_t smem, int* per_sm, int* sms) {
+static int occupancy_cached(K kernel, size_t smem, int* per_sm, int* sms, int block = kBlock) {
   struct Entry {
     const void* fn;
     size_t smem;
@@ -364,7 +364,7 @@ static int occupancy_cached(K kernel, size_t smem, int* per_sm, int* sms) {
     return fail(QB_EUNSUPPORTED, "tables too large for shared memory (reduce n_max or M)");
   QB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                optin - (int)fa.sharedSizeBytes));
-  QB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kBlock, smem));
+  QB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, block, smem));
   if (per < 1) return fail(QB_EUNSUPPORTED, "kernel does not fit on an SM with this table size");
   Entry e{fn, smem, dev, per, s};
   cache[used < 64 ? used++ : 63] = e;
@@ -375,13 +375,13 @@ static int occupancy_cached(K kernel, size_t smem, int* per_sm, int* sms) {
 
 // Persistent grid of a row kernel: at most one wave of resident CTAs (capped at
 // 16 per SM, the size the reduction scratch is planned for), no more CTAs than
-// there are kBlock-row tiles.
+// there are block-row tiles.
 template <typename K>
-static int persistent_grid(K kernel, size_t smem, int64_t rows, int* grid) {
+static int persistent_grid(K kernel, size_t smem, int64_t rows, int* grid, int block = kBlock) {
   int per = 0, sms = 0;
-  int rc = occupancy_cached(kernel, smem, &per, &sms);
+  int rc = occupancy_cached(kernel, smem, &per, &sms, block);
   if (rc) return rc;
-  int64_t want = (rows + kBlock - 1) / kBlock;
+  int64_t want = (rows + block - 1) / block;
   int64_t g = std::min<int64_t>((int64_t)sms * std::min(per, 16), std::max<int64_t>(1, want));
   *grid = (int)g;
   return QB_OK;

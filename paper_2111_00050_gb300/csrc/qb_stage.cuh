@@ -37,6 +37,14 @@
 
 namespace qb {
 
+// Warps per CTA of the stage kernel.  The CTA's warps share one copy of the
+// ranking table in shared memory, so larger CTAs leave room for more warps per SM.
+#ifndef QB_STAGE_WARPS
+#define QB_STAGE_WARPS 12
+#endif
+constexpr int kStageWarps = QB_STAGE_WARPS;
+constexpr int kStageBlock = 32 * kStageWarps;
+
 // first byte of the table image the stage kernels stage in shared memory
 __host__ __device__ inline int kSmemFrom(const Tables& t) { return QB_CNT_GLOBAL ? t.o_E : 0; }
 
@@ -361,7 +369,7 @@ struct StageSmem {
 };
 
 // Stages the table image (a CTA-wide barrier) and lays out the warp scratch.
-__device__ __forceinline__ StageSmem stage_smem(const Tables& t, unsigned char* smem_raw, int M) {
+__device__ __forceinline__ StageSmem stage_smem(const Tables& t, unsigned char* smem_raw, int M, int warps) {
   StageSmem S;
   load_blob_from(t, smem_raw, kSmemFrom(t));
   unsigned char* smem = smem_raw - kSmemFrom(t);
@@ -380,17 +388,17 @@ __device__ __forceinline__ StageSmem stage_smem(const Tables& t, unsigned char* 
   S.sperm = reinterpret_cast<uint8_t*>(S.sOff + kWarpRows);
   S.hist = reinterpret_cast<int32_t*>(S.sperm + kWarpRows);
   S.cursor = S.hist + (t.n_ann + 2);
-  S.after = base + (size_t)(kBlock / 32) * wbytes;
+  S.after = base + (size_t)warps * wbytes;
   return S;
 }
 
 template <int MT, int B, bool CPLX, bool BIL>
-__global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const DfArgs a, const int mode) {
+__global__ void __launch_bounds__(kStageBlock) stage_df_kernel(const Tables t, const DfArgs a, const int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int M = (MT > 0) ? MT : t.M;
   // the only CTA-wide barrier: warps run independently afterwards
-  const StageSmem S = stage_smem(t, smem_raw, M);
-  constexpr int kWarps = kBlock / 32;
+  const StageSmem S = stage_smem(t, smem_raw, M, kStageWarps);
+  constexpr int kWarps = kStageWarps;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t row1 = a.row1;
   constexpr int kMB = (MT > 0) ? MT : 16;  // bilinear accumulators: one per mode + H_L
@@ -405,7 +413,7 @@ __global__ void __launch_bounds__(kBlock) stage_df_kernel(const Tables t, const 
                                         S.sOff, S.sperm, S.hist, S.cursor, bil_l, bil_w);
   if (BIL) {
     // per-CTA sums of the bilinears in a fixed order: lanes by shuffles, warps in turn
-    __shared__ double red[kBlock / 32][17];
+    __shared__ double red[kStageWarps][17];
     const int nq = M + 1;
     for (int q = 0; q < nq; ++q) {
       double v = (q == 0) ? df_to(bil_l) : 0.0;
@@ -446,7 +454,7 @@ template <int MT, bool CPLX>
 __global__ void __launch_bounds__(kBlock) resident_kernel(const Tables t, const ResArgs r) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int M = (MT > 0) ? MT : t.M;
-  const StageSmem S = stage_smem(t, smem_raw, M);
+  const StageSmem S = stage_smem(t, smem_raw, M, kBlock / 32);
   double2* spsi = reinterpret_cast<double2*>(S.after);
   float4* spsif = reinterpret_cast<float4*>(spsi + r.cap);
   float4* sw1 = spsif + r.cap;
@@ -530,14 +538,15 @@ int resident_launch_t(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t
 template <int MT>
 int stage_launch_t(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, bool bil, cudaStream_t st,
                    int* grid_out) {
-  const size_t smem = ((t.blob_bytes - kSmemFrom(t) + 15) & ~15) + df_scratch_bytes(t.M, t.n_ann);
+  const size_t smem = ((t.blob_bytes - kSmemFrom(t) + 15) & ~15) +
+                      (size_t)kStageWarps * df_warp_scratch_bytes(t.M, t.n_ann);
   int grid = 0, rc = QB_OK;
 #define QB_STAGE_CASE(BB, CC, LL)                                               \
   {                                                                             \
     auto k = stage_df_kernel<MT, BB, CC, LL>;                                   \
-    rc = persistent_grid(k, smem, a.row1 - a.row0, &grid);                      \
+    rc = persistent_grid(k, smem, a.row1 - a.row0, &grid, kStageBlock);         \
     if (rc) return rc;                                                          \
-    k<<<grid, kBlock, smem, st>>>(t, a, mode);                                  \
+    k<<<grid, kStageBlock, smem, st>>>(t, a, mode);                             \
   }
   if (bil) {
     if (B != 1) return fail(QB_EUNSUPPORTED, "bilinear stages run one state at a time");
