@@ -362,7 +362,10 @@ extern "C" int qb_adjoint(qb_space* space, const double* z, double scale, double
       rc = launch_to_df(L.psi, L.psif, n, stream);
       if (rc) return rc;
     } else {
-      rc = launch_rk4(*sp, L.psi, 1, sc, -dt, 1, L.w1, stream);  // leaves the double-float copy in psif
+      rc = launch_rk4(*sp, L.psi, 1, sc, -dt, 1, L.w1, stream);
+      if (rc) return rc;
+      // the stages below work in the plain basis: a plain double-float copy of psi
+      rc = launch_to_df(L.psi, L.psif, n, stream);
       if (rc) return rc;
     }
     // forward stage vectors of this step

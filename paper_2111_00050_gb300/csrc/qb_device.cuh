@@ -139,6 +139,32 @@ __device__ __forceinline__ int64_t setup_row(const Tables& t, const View& v, con
   return D - 1 - (int64_t)acc;
 }
 
+// Ket weight w(n) = sqrt(N! / prod_m n_m!) and 1/w in FP64, from the occupations
+// occ[m * stride]: the product over modes of sqrt(C(rem_m, n_m)).  In the weighted
+// basis f = psi / w the two-body matrix element of a pair (r, s) -> (p, q) loses its
+// creation factor sqrt((n_p + 1)(n_q + 1 + [p = q])) (see the stage kernel).
+template <int MT>
+__device__ __forceinline__ double2 ket_weight(const Tables& t, const uint8_t* occ, int stride) {
+  const int M = (MT > 0) ? MT : t.M;
+  constexpr int kMB = (MT > 0) ? MT : 16;
+  int rem = 0;
+#pragma unroll
+  for (int m = 0; m < kMB; ++m)
+    if (m < M) rem += occ[m * stride];
+  const int V = t.nmax + 1;
+  double w = 1.0, wi = 1.0;
+#pragma unroll
+  for (int m = 0; m < kMB - 1; ++m) {
+    if (m >= M - 1) break;
+    const int nm = occ[m * stride];
+    const double2 f = __ldg(t.wtab + rem * V + nm);
+    w *= f.x;
+    wi *= f.y;
+    rem -= nm;
+  }
+  return make_double2(w, wi);
+}
+
 // Rank of the ket obtained from the row's ket by changing the occupations of
 // modes e[0..nch) by dn[0..nch), inside the sector of dimension Dt it lands in.
 __device__ __forceinline__ int64_t rank_changed(const Tables& t, const View& v, const RowScratch& rs, int nch,
@@ -180,6 +206,14 @@ __device__ __forceinline__ dfl df_of(double x) {
 }
 __device__ __forceinline__ double df_to(dfl a) { return (double)a.h + (double)a.l; }
 __device__ __forceinline__ dfl df_neg(dfl a) { return {-a.h, -a.l}; }
+
+// a * k for a float k that is an exact small integer, unnormalised
+__device__ __forceinline__ dfl df_mul_f(dfl a, float k) {
+  const float p = __fmul_rn(a.h, k);
+  float e = fmaf(a.h, k, -p);
+  e = fmaf(a.l, k, e);
+  return {p, e};
+}
 
 // a * b, unnormalised (|l| is a few ulp of h)
 __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {

@@ -56,6 +56,9 @@ struct Tables {
   const int32_t* sec_K;    // [n_sectors] index momentum
   const int32_t* sec_of;   // [(nmax + 1) * M] sector id of (N, K) or -1
   int64_t total;
+  // ket weights w(n) = sqrt(N! / prod_m n_m!) = prod_m sqrt(C(rem_m, n_m)), rem_m the
+  // particles in modes m..M-1: entry [rem * (nmax + 1) + k] = (sqrt(C(rem, k)), its inverse)
+  const double2* wtab;
 };
 
 struct Space {
@@ -78,6 +81,7 @@ struct Space {
   double* d_scratch = nullptr;  // reduction partials
   float4* d_diag = nullptr;     // per ket: one-body and two-body diagonal as double-float pairs
   float4* d_obsf = nullptr;     // double-float copy of the state being observed (qb_observables)
+  double2* d_wtab = nullptr;    // ket-weight factors (Tables::wtab)
   int64_t scratch_doubles = 0;
   Tables t{};
   cudaStream_t capture_stream = nullptr;  // private stream on which RK4 chunks are captured into graphs

@@ -181,6 +181,28 @@ __global__ void to_df_kernel(const double2* psi, float4* out, int64_t n) {
   }
 }
 
+// psi (FP64, [B][total]) -> double-float copy in the weighted basis, f = psi / w(n)
+__global__ void __launch_bounds__(kBlock) to_dfw_kernel(const Tables t, const double2* psi, float4* out, int B) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  load_blob(t, smem);
+  const View v = make_view(t, smem);
+  const RowScratch rs = row_scratch(smem + ((t.blob_bytes + 15) & ~15));
+  const int tid = threadIdx.x;
+  for (int64_t base = (int64_t)blockIdx.x * kBlock; base < t.total; base += (int64_t)gridDim.x * kBlock) {
+    const int64_t g = base + tid;
+    if (g >= t.total) break;
+    const int sid = find_sector(t, g);
+    const int64_t off = __ldg(t.sec_off + sid);
+    const int64_t D = __ldg(t.sec_off + sid + 1) - off;
+    setup_row(t, v, rs, __ldg(t.sec_N + sid), __ldg(t.sec_K + sid), D, g - off);
+    const double wi = ket_weight<0>(t, rs.occ + tid, kBlock).y;
+    for (int b = 0; b < B; ++b) {
+      const double2 x = psi[(size_t)b * t.total + g];
+      out[(size_t)b * t.total + g] = df_pack(df_of(x.x * wi), df_of(x.y * wi));
+    }
+  }
+}
+
 // per-ket diagonal of H, one-body and two-body parts, as double-float pairs
 __global__ void __launch_bounds__(kBlock) diag_kernel(const Tables t, float4* diag) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -888,6 +910,23 @@ int device_setup(Space& s) {
   QB_CUDA(cudaMalloc(&s.d_diag, sizeof(float4) * (size_t)t.total));
   QB_CUDA(cudaMalloc(&s.d_obsf, sizeof(float4) * (size_t)t.total));
   {
+    // sqrt(C(rem, k)) from the exact binomial (C(77, 38) < 2^75 fits 128 bits), then
+    // one rounding to double, one correctly rounded sqrt and one division
+    const int V = s.nmax + 1;
+    std::vector<double2> wt((size_t)V * V, make_double2(0.0, 0.0));
+    for (int rem = 0; rem < V; ++rem) {
+      unsigned __int128 c = 1;
+      for (int k = 0; k <= rem; ++k) {
+        if (k > 0) c = c * (unsigned __int128)(rem - k + 1) / (unsigned __int128)k;
+        const double r = std::sqrt((double)c);
+        wt[(size_t)rem * V + k] = make_double2(r, 1.0 / r);
+      }
+    }
+    QB_CUDA(cudaMalloc(&s.d_wtab, sizeof(double2) * wt.size()));
+    QB_CUDA(cudaMemcpy(s.d_wtab, wt.data(), sizeof(double2) * wt.size(), cudaMemcpyHostToDevice));
+    t.wtab = s.d_wtab;
+  }
+  {
     const size_t smem = row_smem(t);
     int grid = 0;
     int rc = persistent_grid(diag_kernel, smem, t.total, &grid);
@@ -961,13 +1000,13 @@ static int rk4_issue(Space& s, DfArgs& a, double dt, int64_t steps, float4* w1, 
       if (!plain) {
         a.row0 = row0;
         a.row1 = s.t.total;
-        int rc = stage_launch(s.t, a, d == 1 ? 1 : 0, B, cplx, st);
+        int rc = stage_launch(s.t, a, d == 1 ? 1 : 0, B, cplx, st, nullptr, false, true);
         if (rc) return rc;
       } else {
         for (size_t sec = 0; sec + 1 < s.secOff.size(); ++sec) {
           a.row0 = s.secOff[sec];
           a.row1 = s.secOff[sec + 1];
-          int rc = stage_launch(s.t, a, d == 1 ? 1 : 0, B, cplx, st);
+          int rc = stage_launch(s.t, a, d == 1 ? 1 : 0, B, cplx, st, nullptr, false, true);
           if (rc) return rc;
         }
       }
@@ -979,9 +1018,15 @@ static int rk4_issue(Space& s, DfArgs& a, double dt, int64_t steps, float4* w1, 
 template <int B>
 static int rk4_loop(Space& s, double2* psi, const double* scale, double dt, int64_t steps, float4* w1, float4* w2,
                     float4* psif, cudaStream_t st, bool plain = false) {
-  const int64_t n = (int64_t)B * s.t.total;
-  to_df_kernel<<<1216, 256, 0, st>>>(psi, psif, n);
-  QB_CUDA(cudaGetLastError());
+  {
+    // the stages run in the weighted basis f = psi / w
+    const size_t smem = row_smem(s.t);
+    int grid = 0;
+    int rc = persistent_grid(to_dfw_kernel, smem, s.t.total, &grid);
+    if (rc) return rc;
+    to_dfw_kernel<<<grid, kBlock, smem, st>>>(s.t, psi, psif, B);
+    QB_CUDA(cudaGetLastError());
+  }
   DfArgs a{};
   for (int b = 0; b < B; ++b) {
     const float h = (float)scale[b];

@@ -61,7 +61,15 @@ __device__ __forceinline__ float4 gather(const float4* p) {
 // LOCAL the state vectors of DfArgs are the shared-memory copies of one sector
 // starting at ket local_off (gathers and own-row accesses are sector-local);
 // otherwise they are the global vectors.  The per-ket diagonal is always global.
-template <int MT, int B, bool CPLX, bool BIL, bool LOCAL>
+//
+// SIM: the double-float vectors hold f = psi / w in the weighted basis of the ket
+// weights w(n) = sqrt(N! / prod n_m!) (modes 0 and 1 only).  The similar matrix
+// W^-1 H W has the same diagonal, and for the target n' = n - e_r - e_s + e_p + e_q
+// of a term, w(n') / w(n) = sqrt(n_r (n_s - [r = s]) / ((n_p + 1)(n_q + 1 + [p = q]))),
+// so its element is G n_r (n_s - [r = s]): an integer times the coupling, with no
+// creation-side square roots and no lookup of n_p, n_q.  The last stage (mode 1)
+// maps back: psi += z w (W^-1 H W f) in FP64, and writes f = psi_new / w.
+template <int MT, int B, bool CPLX, bool BIL, bool LOCAL, bool SIM>
 __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const float2* sqf, const float4* Gf,
                                            const uint4* dl4, const DfArgs& a, const int mode, const int64_t base,
                                            const int64_t row1, const int64_t local_off, int32_t* sidx, uint8_t* socc,
@@ -209,8 +217,14 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
       const int s = __ffs(smask) - 1;
       smask &= smask - 1;
       const int ai = v.pairidx[r * 16 + s];
-      const float2 sa = sqf[occ[r * kWarpRows]], sb = sqf[occ[s * kWarpRows] - (r == s ? 1 : 0)];
-      const dfl A = df_mul(dfl{sa.x, sa.y}, dfl{sb.x, sb.y});
+      dfl A{0.f, 0.f};  // sqrt(n_r (n_s - [r = s]))
+      float Af = 0.f;   // n_r (n_s - [r = s]), exact (SIM)
+      if (SIM) {
+        Af = (float)(occ[r * kWarpRows] * (occ[s * kWarpRows] - (r == s ? 1 : 0)));
+      } else {
+        const float2 sa = sqf[occ[r * kWarpRows]], sb = sqf[occ[s * kWarpRows] - (r == s ? 1 : 0)];
+        A = df_mul(dfl{sa.x, sa.y}, dfl{sb.x, sb.y});
+      }
       constexpr int kC = (QB_UNROLL_PARTNERS && !CPLX && MT > 0 && (MT % 2) == 1) ? (MT - 1) / 2 : 0;
       if (kC > 0) {
         // fixed partner count: all ranks first, then all gathers, then the sums
@@ -220,10 +234,13 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
 #pragma unroll
         for (int c = 0; c < kC; ++c) {
           const int j = j0 + c;
-          const uint32_t w4 = v.pq[j];
-          const int p = w4 & 0xff, q = (w4 >> 8) & 0xff;
-          const float2 bp = sqf[occ[p * kWarpRows] + 1], bq = sqf[occ[q * kWarpRows] + 1 + (p == q ? 1 : 0)];
-          const dfl AB = df_mul(A, df_mul(dfl{bp.x, bp.y}, dfl{bq.x, bq.y}));
+          dfl AB{0.f, 0.f};
+          if (!SIM) {
+            const uint32_t w4 = v.pq[j];
+            const int p = w4 & 0xff, q = (w4 >> 8) & 0xff;
+            const float2 bp = sqf[occ[p * kWarpRows] + 1], bq = sqf[occ[q * kWarpRows] + 1 + (p == q ? 1 : 0)];
+            AB = df_mul(A, df_mul(dfl{bp.x, bp.y}, dfl{bq.x, bq.y}));
+          }
           const uint4 dd = dl4[j];
           int esum = 0;
 #pragma unroll
@@ -239,7 +256,7 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
           }
           rkc[c] = rk;
           const float4 gf = Gf[j];
-          crc[c] = df_mul(dfl{gf.x, gf.y}, AB);
+          crc[c] = SIM ? df_mul_f(dfl{gf.x, gf.y}, Af) : df_mul(dfl{gf.x, gf.y}, AB);
         }
 #pragma unroll
         for (int b = 0; b < B; ++b) {
@@ -254,10 +271,13 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
       } else {
         const int j1 = v.ann[ai + 1];
         for (int j = v.ann[ai]; j < j1; ++j) {
-          const uint32_t w4 = v.pq[j];
-          const int p = w4 & 0xff, q = (w4 >> 8) & 0xff;
-          const float2 bp = sqf[occ[p * kWarpRows] + 1], bq = sqf[occ[q * kWarpRows] + 1 + (p == q ? 1 : 0)];
-          const dfl AB = df_mul(A, df_mul(dfl{bp.x, bp.y}, dfl{bq.x, bq.y}));
+          dfl AB{0.f, 0.f};
+          if (!SIM) {
+            const uint32_t w4 = v.pq[j];
+            const int p = w4 & 0xff, q = (w4 >> 8) & 0xff;
+            const float2 bp = sqf[occ[p * kWarpRows] + 1], bq = sqf[occ[q * kWarpRows] + 1 + (p == q ? 1 : 0)];
+            AB = df_mul(A, df_mul(dfl{bp.x, bp.y}, dfl{bq.x, bq.y}));
+          }
           // rank of the target: D - 1 - sum over every mode of E at the shifted suffix state
           const uint4 dd = dl4[j];
           int esum = 0;
@@ -273,7 +293,7 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
             rk = 0;
           }
           const float4 gf = Gf[j];
-          const dfl cr = df_mul(dfl{gf.x, gf.y}, AB);
+          const dfl cr = SIM ? df_mul_f(dfl{gf.x, gf.y}, Af) : df_mul(dfl{gf.x, gf.y}, AB);
   #pragma unroll
           for (int b = 0; b < B; ++b) {
             const float4 x = gather<LOCAL>(vsec + (size_t)b * total + rk);
@@ -281,7 +301,7 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
             dfc_fma(acc[b], f2_pack(cr.h, cr.h), f2_pack(-cr.h, -cr.h), f2_pack(cr.l, cr.l), xh, xl);
             if (CPLX) {
               // + (-c_i x_im, c_i x_re): lanes of x swapped, coefficient (-c_i, c_i)
-              const dfl ci = df_mul(dfl{gf.z, gf.w}, AB);
+              const dfl ci = SIM ? df_mul_f(dfl{gf.z, gf.w}, Af) : df_mul(dfl{gf.z, gf.w}, AB);
               dfc_fma(acc[b], f2_pack(-ci.h, ci.h), f2_pack(ci.h, -ci.h), f2_pack(-ci.l, ci.l),
                       f2_pack(x.y, x.x), f2_pack(x.w, x.z));
             }
@@ -332,6 +352,14 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
           oi = df_add(df_im(p0), oi);
         }
         a.out[(size_t)b * total + ri] = df_pack(orr, oi);
+      } else if (SIM) {  // mode 1: back to psi, one FP64 weight per ket
+        const double2 wk = ket_weight<MT>(t, occ, kWarpRows);
+        const double2 p0 = a.psi[(size_t)b * total + ri];
+        const double zw = a.zre * wk.x;
+        const double nr = p0.x + zw * df_to(hi);
+        const double ni = p0.y - zw * df_to(hr);
+        a.psi[(size_t)b * total + ri] = make_double2(nr, ni);
+        a.out[(size_t)b * total + ri] = df_pack(df_of(nr * wk.y), df_of(ni * wk.y));
       } else {
         const double2 p0 = a.psi[(size_t)b * total + ri];
         double nr = p0.x + a.zre * df_to(hi);
@@ -392,7 +420,7 @@ __device__ __forceinline__ StageSmem stage_smem(const Tables& t, unsigned char* 
   return S;
 }
 
-template <int MT, int B, bool CPLX, bool BIL>
+template <int MT, int B, bool CPLX, bool BIL, bool SIM>
 __global__ void __launch_bounds__(kStageBlock) stage_df_kernel(const Tables t, const DfArgs a, const int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int M = (MT > 0) ? MT : t.M;
@@ -409,8 +437,8 @@ __global__ void __launch_bounds__(kStageBlock) stage_df_kernel(const Tables t, c
 
   for (int64_t base = a.row0 + ((int64_t)blockIdx.x * kWarps + warp) * kWarpRows; base < row1;
        base += (int64_t)gridDim.x * kWarps * kWarpRows)
-    stage_tile<MT, B, CPLX, BIL, false>(t, S.v, S.sqf, S.Gf, S.dl4, a, mode, base, row1, 0, S.sidx, S.socc, S.sD,
-                                        S.sOff, S.sperm, S.hist, S.cursor, bil_l, bil_w);
+    stage_tile<MT, B, CPLX, BIL, false, SIM>(t, S.v, S.sqf, S.Gf, S.dl4, a, mode, base, row1, 0, S.sidx, S.socc,
+                                             S.sD, S.sOff, S.sperm, S.hist, S.cursor, bil_l, bil_w);
   if (BIL) {
     // per-CTA sums of the bilinears in a fixed order: lanes by shuffles, warps in turn
     __shared__ double red[kStageWarps][17];
@@ -440,7 +468,7 @@ __global__ void __launch_bounds__(kStageBlock) stage_df_kernel(const Tables t, c
 // final psi and its double-float copy are written back to global memory.
 struct ResArgs {
   double2* psi;        // global psi [total]
-  float4* psif;        // global double-float copy of psi [total] (written back)
+  float4* psif;        // global double-float copy of psi in the weighted basis [total] (read, written back)
   const float4* diag;  // per-ket diagonal
   float2 scale;        // two-body scale, double-float
   double dt;
@@ -470,9 +498,8 @@ __global__ void __launch_bounds__(kBlock) resident_kernel(const Tables t, const 
       continue;
     }
     for (int i = threadIdx.x; i < D; i += kBlock) {
-      const double2 x = r.psi[off + i];
-      spsi[i] = x;
-      spsif[i] = df_pack(df_of(x.x), df_of(x.y));
+      spsi[i] = r.psi[off + i];
+      spsif[i] = r.psif[off + i];  // the weighted double-float copy
     }
     __syncthreads();
     DfArgs a{};
@@ -495,7 +522,7 @@ __global__ void __launch_bounds__(kBlock) resident_kernel(const Tables t, const 
         // evenly, so that a small sector still keeps every warp busy
         const int64_t chunk = min((int64_t)kWarpRows, ((int64_t)D + kWarps - 1) / kWarps);
         for (int64_t base = off + (int64_t)warp * chunk; base < off + D; base += (int64_t)kWarps * chunk)
-          stage_tile<MT, 1, CPLX, false, true>(t, S.v, S.sqf, S.Gf, S.dl4, a, d == 1 ? 1 : 0, base,
+          stage_tile<MT, 1, CPLX, false, true, true>(t, S.v, S.sqf, S.Gf, S.dl4, a, d == 1 ? 1 : 0, base,
                                                min(base + chunk, off + (int64_t)D), off, S.sidx, S.socc, S.sD,
                                                S.sOff, S.sperm, S.hist, S.cursor, bil_l, bil_w);
         __syncthreads();
@@ -534,36 +561,46 @@ int resident_launch_t(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t
 }
 
 // Launches one stage for mode count MT (0: any M) and the runtime batch size /
-// coupling type / bilinear flag; *grid (if non-NULL) receives the grid size.
+// coupling type / bilinear flag / basis (sim: the weighted basis of the RK4 path,
+// modes 0 and 1 only); *grid (if non-NULL) receives the grid size.
 template <int MT>
-int stage_launch_t(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, bool bil, cudaStream_t st,
+int stage_launch_t(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, bool bil, bool sim, cudaStream_t st,
                    int* grid_out) {
   const size_t smem = ((t.blob_bytes - kSmemFrom(t) + 15) & ~15) +
                       (size_t)kStageWarps * df_warp_scratch_bytes(t.M, t.n_ann);
   int grid = 0, rc = QB_OK;
-#define QB_STAGE_CASE(BB, CC, LL)                                               \
+#define QB_STAGE_CASE(BB, CC, LL, SS)                                           \
   {                                                                             \
-    auto k = stage_df_kernel<MT, BB, CC, LL>;                                   \
+    auto k = stage_df_kernel<MT, BB, CC, LL, SS>;                               \
     rc = persistent_grid(k, smem, a.row1 - a.row0, &grid, kStageBlock);         \
     if (rc) return rc;                                                          \
     k<<<grid, kStageBlock, smem, st>>>(t, a, mode);                             \
   }
-  if (bil) {
-    if (B != 1) return fail(QB_EUNSUPPORTED, "bilinear stages run one state at a time");
-    if (cplx)
-      QB_STAGE_CASE(1, true, true)
-    else
-      QB_STAGE_CASE(1, false, true)
-  } else if (cplx) {
-    if (B != 1) return fail(QB_EUNSUPPORTED, "batched sweeps need a real coupling");
-    QB_STAGE_CASE(1, true, false)
+  if (sim) {
+    if (bil || (mode != 0 && mode != 1)) return fail(QB_EINTERNAL, "the weighted basis serves RK4 stages only");
+    if (cplx) {
+      if (B != 1) return fail(QB_EUNSUPPORTED, "batched sweeps need a real coupling");
+      QB_STAGE_CASE(1, true, false, true)
+    } else {
+      switch (B) {
+        case 1: QB_STAGE_CASE(1, false, false, true) break;
+        case 2: QB_STAGE_CASE(2, false, false, true) break;
+        case 4: QB_STAGE_CASE(4, false, false, true) break;
+        case 8: QB_STAGE_CASE(8, false, false, true) break;
+        default: return fail(QB_EINVAL, "batch must be 1, 2, 4 or 8");
+      }
+    }
   } else {
-    switch (B) {
-      case 1: QB_STAGE_CASE(1, false, false) break;
-      case 2: QB_STAGE_CASE(2, false, false) break;
-      case 4: QB_STAGE_CASE(4, false, false) break;
-      case 8: QB_STAGE_CASE(8, false, false) break;
-      default: return fail(QB_EINVAL, "batch must be 1, 2, 4 or 8");
+    if (B != 1) return fail(QB_EUNSUPPORTED, "plain-basis stages run one state at a time");
+    if (bil) {
+      if (cplx)
+        QB_STAGE_CASE(1, true, true, false)
+      else
+        QB_STAGE_CASE(1, false, true, false)
+    } else if (cplx) {
+      QB_STAGE_CASE(1, true, false, false)
+    } else {
+      QB_STAGE_CASE(1, false, false, false)
     }
   }
 #undef QB_STAGE_CASE
@@ -573,11 +610,11 @@ int stage_launch_t(const Tables& t, const DfArgs& a, int mode, int B, bool cplx,
 }
 
 // one explicit specialisation per translation unit (qb_stage_m*.cu)
-int stage_launch_m5(const Tables&, const DfArgs&, int, int, bool, bool, cudaStream_t, int*);
-int stage_launch_m7(const Tables&, const DfArgs&, int, int, bool, bool, cudaStream_t, int*);
-int stage_launch_m9(const Tables&, const DfArgs&, int, int, bool, bool, cudaStream_t, int*);
-int stage_launch_m11(const Tables&, const DfArgs&, int, int, bool, bool, cudaStream_t, int*);
-int stage_launch_any(const Tables&, const DfArgs&, int, int, bool, bool, cudaStream_t, int*);
+int stage_launch_m5(const Tables&, const DfArgs&, int, int, bool, bool, bool, cudaStream_t, int*);
+int stage_launch_m7(const Tables&, const DfArgs&, int, int, bool, bool, bool, cudaStream_t, int*);
+int stage_launch_m9(const Tables&, const DfArgs&, int, int, bool, bool, bool, cudaStream_t, int*);
+int stage_launch_m11(const Tables&, const DfArgs&, int, int, bool, bool, bool, cudaStream_t, int*);
+int stage_launch_any(const Tables&, const DfArgs&, int, int, bool, bool, bool, cudaStream_t, int*);
 
 int resident_launch_m5(const Tables&, const ResArgs&, bool, cudaStream_t);
 int resident_launch_m7(const Tables&, const ResArgs&, bool, cudaStream_t);
@@ -596,13 +633,13 @@ inline int resident_launch(const Tables& t, const ResArgs& r, bool cplx, cudaStr
 }
 
 inline int stage_launch(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, cudaStream_t st,
-                        int* grid_out = nullptr, bool bil = false) {
+                        int* grid_out = nullptr, bool bil = false, bool sim = false) {
   switch (t.M) {
-    case 5: return stage_launch_m5(t, a, mode, B, cplx, bil, st, grid_out);
-    case 7: return stage_launch_m7(t, a, mode, B, cplx, bil, st, grid_out);
-    case 9: return stage_launch_m9(t, a, mode, B, cplx, bil, st, grid_out);
-    case 11: return stage_launch_m11(t, a, mode, B, cplx, bil, st, grid_out);
-    default: return stage_launch_any(t, a, mode, B, cplx, bil, st, grid_out);
+    case 5: return stage_launch_m5(t, a, mode, B, cplx, bil, sim, st, grid_out);
+    case 7: return stage_launch_m7(t, a, mode, B, cplx, bil, sim, st, grid_out);
+    case 9: return stage_launch_m9(t, a, mode, B, cplx, bil, sim, st, grid_out);
+    case 11: return stage_launch_m11(t, a, mode, B, cplx, bil, sim, st, grid_out);
+    default: return stage_launch_any(t, a, mode, B, cplx, bil, sim, st, grid_out);
   }
 }
 
