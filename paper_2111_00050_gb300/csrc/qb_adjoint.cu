@@ -133,7 +133,8 @@ __global__ void __launch_bounds__(kBlock) seed_kernel(const Tables t, const Seed
     r.x *= a.inv_norm;
     r.y *= a.inv_norm;
     a.lam[g] = r;
-    a.lamf[g] = df_pack(df_of(r.x), df_of(r.y));
+    const double wi = ket_weight<0>(t, rs.occ + tid, kBlock).y;  // weighted copy, as the stages use
+    a.lamf[g] = df_pack(df_of(r.x * wi), df_of(r.y * wi));
   }
 }
 
@@ -346,7 +347,7 @@ extern "C" int qb_adjoint(qb_space* space, const double* z, double scale, double
   };
   auto run = [&](int mode, bool bil, double weight) -> int {
     int grid = 0;
-    int r = stage_launch(sp->t, a, mode, 1, cplx, st, &grid, bil);
+    int r = stage_launch(sp->t, a, mode, 1, cplx, st, &grid, bil, true);
     if (r) return r;
     if (bil) {
       accumulate_kernel<<<1, 32, 0, st>>>(L.partial, grid, M + 1, weight, L.acc);
@@ -359,13 +360,10 @@ extern "C" int qb_adjoint(qb_space* space, const double* z, double scale, double
     // psi_step: a checkpoint, or one RK4 step backwards in time from psi_{step+1}
     if (step % ckpt_every == 0) {
       QB_CUDA(cudaMemcpyAsync(L.psi, L.ckpt + (step / ckpt_every) * n, n * 16, cudaMemcpyDeviceToDevice, st));
-      rc = launch_to_df(L.psi, L.psif, n, stream);
+      rc = launch_to_dfw(*sp, L.psi, L.psif, 1, stream);
       if (rc) return rc;
     } else {
-      rc = launch_rk4(*sp, L.psi, 1, sc, -dt, 1, L.w1, stream);
-      if (rc) return rc;
-      // the stages below work in the plain basis: a plain double-float copy of psi
-      rc = launch_to_df(L.psi, L.psif, n, stream);
+      rc = launch_rk4(*sp, L.psi, 1, sc, -dt, 1, L.w1, stream);  // leaves the weighted copy in psif
       if (rc) return rc;
     }
     // forward stage vectors of this step

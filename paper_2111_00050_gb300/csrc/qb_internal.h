@@ -114,6 +114,8 @@ int launch_moments_fp64(Space& s, const void* d_psi, double* out_host, void* str
 int64_t workspace_bytes(const Space& s, int batch);
 // psi (FP64 complex) -> double-float copy (float4 per ket)
 int launch_to_df(const void* psi, void* psif, int64_t n, void* stream);
+// psi [B][total] -> double-float copy in the weighted basis f = psi / w(n) (the stages' basis)
+int launch_to_dfw(const Space& s, const void* psi, void* psif, int B, void* stream);
 // observables of Sec. II C-E from the raw moments (host)
 void derive(int M, const double* raw, qb_obs* out);
 int device_setup(Space& s);

@@ -1020,12 +1020,8 @@ static int rk4_loop(Space& s, double2* psi, const double* scale, double dt, int6
                     float4* psif, cudaStream_t st, bool plain = false) {
   {
     // the stages run in the weighted basis f = psi / w
-    const size_t smem = row_smem(s.t);
-    int grid = 0;
-    int rc = persistent_grid(to_dfw_kernel, smem, s.t.total, &grid);
+    int rc = launch_to_dfw(s, psi, psif, B, st);
     if (rc) return rc;
-    to_dfw_kernel<<<grid, kBlock, smem, st>>>(s.t, psi, psif, B);
-    QB_CUDA(cudaGetLastError());
   }
   DfArgs a{};
   for (int b = 0; b < B; ++b) {
@@ -1142,6 +1138,16 @@ int launch_rk4(Space& s, void* d_psi, int batch, const double* scale, double dt,
   }
   if (rc) return rc;
   return check_status(s, st);
+}
+
+int launch_to_dfw(const Space& s, const void* psi, void* psif, int B, void* stream) {
+  const size_t smem = row_smem(s.t);
+  int grid = 0;
+  int rc = persistent_grid(to_dfw_kernel, smem, s.t.total, &grid);
+  if (rc) return rc;
+  to_dfw_kernel<<<grid, kBlock, smem, (cudaStream_t)stream>>>(s.t, (const double2*)psi, (float4*)psif, B);
+  QB_CUDA(cudaGetLastError());
+  return QB_OK;
 }
 
 int launch_to_df(const void* psi, void* psif, int64_t n, void* stream) {

@@ -63,12 +63,13 @@ __device__ __forceinline__ float4 gather(const float4* p) {
 // otherwise they are the global vectors.  The per-ket diagonal is always global.
 //
 // SIM: the double-float vectors hold f = psi / w in the weighted basis of the ket
-// weights w(n) = sqrt(N! / prod n_m!) (modes 0 and 1 only).  The similar matrix
+// weights w(n) = sqrt(N! / prod n_m!) (modes 0 to 3).  The similar matrix
 // W^-1 H W has the same diagonal, and for the target n' = n - e_r - e_s + e_p + e_q
 // of a term, w(n') / w(n) = sqrt(n_r (n_s - [r = s]) / ((n_p + 1)(n_q + 1 + [p = q]))),
 // so its element is G n_r (n_s - [r = s]): an integer times the coupling, with no
-// creation-side square roots and no lookup of n_p, n_q.  The last stage (mode 1)
-// maps back: psi += z w (W^-1 H W f) in FP64, and writes f = psi_new / w.
+// creation-side square roots and no lookup of n_p, n_q.  Modes 1 and 3 map back:
+// psi += w (z W^-1 H W f + sum of basef) in FP64, and write f = psi_new / w; the
+// bilinears multiply each factor by w.
 template <int MT, int B, bool CPLX, bool BIL, bool LOCAL, bool SIM>
 __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const float2* sqf, const float4* Gf,
                                            const uint4* dl4, const DfArgs& a, const int mode, const int64_t base,
@@ -315,6 +316,9 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
 
     const float4 dg4 = a.diag[gr];
     const dfl zf{a.zf.x, a.zf.y};
+    // the ket weight where true values are formed (weighted basis)
+    const double2 wk = (SIM && (BIL || mode == 1 || mode == 3)) ? ket_weight<MT>(t, occ, kWarpRows)
+                                                                 : make_double2(1.0, 1.0);
 #pragma unroll
     for (int b = 0; b < B; ++b) {
       dfl acc_r, acc_i;
@@ -332,12 +336,22 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
       if (BIL && b == 0) {
         // H_L x (two-body part at scale 1) and the pair vector of this row
         const float4 pp = a.pair[ri];
-        const dfl lr = df_add(df_mul(dfl{dg4.z, dg4.w}, df_re(xo)), acc_r);
-        const dfl li = df_add(df_mul(dfl{dg4.z, dg4.w}, df_im(xo)), acc_i);
+        dfl lr = df_add(df_mul(dfl{dg4.z, dg4.w}, df_re(xo)), acc_r);
+        dfl li = df_add(df_mul(dfl{dg4.z, dg4.w}, df_im(xo)), acc_i);
+        dfl pr = df_re(pp), pi = df_im(pp), xr = df_re(xo), xi = df_im(xo);
+        if (SIM) {  // true values: each factor times w (w^2 alone may leave the fp32 range)
+          const dfl wd = df_of(wk.x);
+          lr = df_mul(wd, lr);
+          li = df_mul(wd, li);
+          pr = df_mul(wd, pr);
+          pi = df_mul(wd, pi);
+          xr = df_mul(wd, xr);
+          xi = df_mul(wd, xi);
+        }
         // Im(conj(p) h) = p.re h.im - p.im h.re
-        bil_l = df_add(bil_l, df_add(df_mul(df_re(pp), li), df_neg(df_mul(df_im(pp), lr))));
+        bil_l = df_add(bil_l, df_add(df_mul(pr, li), df_neg(df_mul(pi, lr))));
         // Im(conj(x) p) = x.re p.im - x.im p.re, weighted by each occupation
-        const dfl tx = df_add(df_mul(df_re(xo), df_im(pp)), df_neg(df_mul(df_im(xo), df_re(pp))));
+        const dfl tx = df_add(df_mul(xr, pi), df_neg(df_mul(xi, pr)));
 #pragma unroll
         for (int q = 0; q < kMB; ++q) {
           if (q >= M) break;
@@ -352,12 +366,17 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
           oi = df_add(df_im(p0), oi);
         }
         a.out[(size_t)b * total + ri] = df_pack(orr, oi);
-      } else if (SIM) {  // mode 1: back to psi, one FP64 weight per ket
-        const double2 wk = ket_weight<MT>(t, occ, kWarpRows);
+      } else if (SIM) {  // modes 1 and 3: back to the FP64 vector, one weight per ket
+        double sr = a.zre * df_to(hi), si = -a.zre * df_to(hr);
+        if (mode == 3) {
+          for (int k = 0; k < a.nbasef; ++k) {
+            const float4 e = a.basef[k][(size_t)b * total + ri];
+            sr += df_to(df_re(e));
+            si += df_to(df_im(e));
+          }
+        }
         const double2 p0 = a.psi[(size_t)b * total + ri];
-        const double zw = a.zre * wk.x;
-        const double nr = p0.x + zw * df_to(hi);
-        const double ni = p0.y - zw * df_to(hr);
+        const double nr = p0.x + wk.x * sr, ni = p0.y + wk.x * si;
         a.psi[(size_t)b * total + ri] = make_double2(nr, ni);
         a.out[(size_t)b * total + ri] = df_pack(df_of(nr * wk.y), df_of(ni * wk.y));
       } else {
@@ -561,8 +580,9 @@ int resident_launch_t(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t
 }
 
 // Launches one stage for mode count MT (0: any M) and the runtime batch size /
-// coupling type / bilinear flag / basis (sim: the weighted basis of the RK4 path,
-// modes 0 and 1 only); *grid (if non-NULL) receives the grid size.
+// coupling type / bilinear flag / basis (sim: the weighted basis of the RK4 and
+// adjoint stages, modes 0 to 3; plain: the <H> reduction, mode 4); *grid (if
+// non-NULL) receives the grid size.
 template <int MT>
 int stage_launch_t(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, bool bil, bool sim, cudaStream_t st,
                    int* grid_out) {
@@ -577,8 +597,14 @@ int stage_launch_t(const Tables& t, const DfArgs& a, int mode, int B, bool cplx,
     k<<<grid, kStageBlock, smem, st>>>(t, a, mode);                             \
   }
   if (sim) {
-    if (bil || (mode != 0 && mode != 1)) return fail(QB_EINTERNAL, "the weighted basis serves RK4 stages only");
-    if (cplx) {
+    if (mode < 0 || mode > 3) return fail(QB_EINTERNAL, "the weighted basis serves modes 0 to 3");
+    if (bil) {
+      if (B != 1) return fail(QB_EUNSUPPORTED, "bilinear stages run one state at a time");
+      if (cplx)
+        QB_STAGE_CASE(1, true, true, true)
+      else
+        QB_STAGE_CASE(1, false, true, true)
+    } else if (cplx) {
       if (B != 1) return fail(QB_EUNSUPPORTED, "batched sweeps need a real coupling");
       QB_STAGE_CASE(1, true, false, true)
     } else {
@@ -591,17 +617,12 @@ int stage_launch_t(const Tables& t, const DfArgs& a, int mode, int B, bool cplx,
       }
     }
   } else {
-    if (B != 1) return fail(QB_EUNSUPPORTED, "plain-basis stages run one state at a time");
-    if (bil) {
-      if (cplx)
-        QB_STAGE_CASE(1, true, true, false)
-      else
-        QB_STAGE_CASE(1, false, true, false)
-    } else if (cplx) {
-      QB_STAGE_CASE(1, true, false, false)
-    } else {
-      QB_STAGE_CASE(1, false, false, false)
-    }
+    // the plain basis serves the <x|H|x> reduction of the observables
+    if (!bil || mode != 4 || B != 1) return fail(QB_EINTERNAL, "the plain basis serves the <H> reduction only");
+    if (cplx)
+      QB_STAGE_CASE(1, true, true, false)
+    else
+      QB_STAGE_CASE(1, false, true, false)
   }
 #undef QB_STAGE_CASE
   QB_CUDA(cudaGetLastError());
