@@ -34,9 +34,10 @@ import workloads as wl  # noqa: E402
 # FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 # (a DFMA microbenchmark measured 1.00 TFLOP/s: python -m paper_2111_00050_gb300.probe)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# DRAM bytes per ket of one stage launch, from an ncu capture of the current stage kernel
-# (batched coherent at n_tot=12: 729.9 MB over 15,380,937 kets); scaled by kets
-STAGE_DRAM_BYTES_PER_KET = 729.9e6 / 15380937
+# DRAM bytes per ket of one stage launch (the first stage of a step), from an ncu capture
+# of the current stage kernel (batched coherent at n_tot=12: 576.1 MB read + 229.4 MB
+# written over 15,380,937 kets); scaled by kets
+STAGE_DRAM_BYTES_PER_KET = (576.1e6 + 229.4e6) / 15380937
 
 
 def _peaks():
@@ -341,7 +342,10 @@ def main():
     flops = 4.0 * terms  # >= 2 FP64 FMA per term (real coefficient x complex amplitude)
     achieved = flops / stage_time / 1e12
     peaks = _peaks()
-    hbm_bytes = 32.0 * qs.total  # read v once, write the stage output once
+    # algorithmic bytes per ket and stage, averaged over the four stages of a step: the
+    # gathered input (16 B), the diagonal (16 B), the output (16 B), the psi copy of the
+    # inner stages (16 B, d = 3, 2) and the FP64 psi read + write of the last (32 B)
+    hbm_bytes = (48.0 + 64.0 + 64.0 + 80.0) / 4 * qs.total
     # FP64 H psi (qb_hpsi) for comparison with the double-float stage
     out = qs.empty_state()
     qs.hpsi(psi, out)
@@ -357,7 +361,7 @@ def main():
         "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
         "frac": achieved / FP64_PEAK_TFLOPS,
         "traffic": STAGE_DRAM_BYTES_PER_KET * qs.total if args.config == "batched_coherent" else None,
-        "kernel": f"stage_df_kernel<{W.M},1,0> (one RK4 stage = one H psi over all sectors)",
+        "kernel": f"stage_df_kernel<{W.M},1,0,0,1> (one RK4 stage = one H psi over all sectors, weighted basis)",
         "stage_ms": stage_time * 1e3,
         "peak_note": "FP64-equivalent flops (2 FMA/term) vs the FP64 pipe peak from unit counts "
                      "(152 SMs x 2 FMA/clk x 2.07 GHz); the kernel itself runs double-float on the FP32/ALU "
