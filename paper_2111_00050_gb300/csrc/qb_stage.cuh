@@ -42,8 +42,12 @@ namespace qb {
 #ifndef QB_STAGE_WARPS
 #define QB_STAGE_WARPS 12
 #endif
+#ifndef QB_STAGE_MIN_BLOCKS
+#define QB_STAGE_MIN_BLOCKS 1
+#endif
 constexpr int kStageWarps = QB_STAGE_WARPS;
 constexpr int kStageBlock = 32 * kStageWarps;
+constexpr int kStageMinBlocks = QB_STAGE_MIN_BLOCKS;  // resident CTAs per SM the register budget is planned for
 
 // first byte of the table image the stage kernels stage in shared memory
 __host__ __device__ inline int kSmemFrom(const Tables& t) { return QB_CNT_GLOBAL ? t.o_E : 0; }
@@ -440,7 +444,7 @@ __device__ __forceinline__ StageSmem stage_smem(const Tables& t, unsigned char* 
 }
 
 template <int MT, int B, bool CPLX, bool BIL, bool SIM>
-__global__ void __launch_bounds__(kStageBlock) stage_df_kernel(const Tables t, const DfArgs a, const int mode) {
+__global__ void __launch_bounds__(kStageBlock, kStageMinBlocks) stage_df_kernel(const Tables t, const DfArgs a, const int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int M = (MT > 0) ? MT : t.M;
   // the only CTA-wide barrier: warps run independently afterwards
