@@ -206,6 +206,22 @@ def rk4(space: Space, w, L, psi: np.ndarray, dt: float, steps: int) -> np.ndarra
     return out
 
 
+def taylor(space: Space, w, L, psi: np.ndarray, dt: float, steps: int, order: int) -> np.ndarray:
+    """`steps` Taylor steps of order K of d psi/dt = -i H psi: each step is
+    psi <- sum_{k=0}^{K} (-i dt H)^k / k! psi, the terms formed one after the
+    other as t_k = (-i dt / k) H t_{k-1} (Sec. III B's scheme is K = 2, with the
+    1/2 of the second-order term; K = 4 equals classic RK4 for a linear H)."""
+    out = np.array(psi, dtype=np.complex128, copy=True)
+    for _ in range(steps):
+        term = out.copy()
+        acc = out.copy()
+        for k in range(1, order + 1):
+            term = (-1j * dt / k) * apply_h(space, w, L, term)
+            acc = acc + term
+        out = acc
+    return out
+
+
 def count_terms(space: Space, L) -> int:
     """Distinct nonzero H matrix elements of all held sectors, diagonal included."""
     Lc = np.ascontiguousarray(L, dtype=np.complex128).reshape(-1)

@@ -218,6 +218,48 @@ def test_rk4_equals_matrix_polynomial_on_interacting_sector():
     assert np.linalg.norm(got - ref) < 1e-12 * np.linalg.norm(ref)
 
 
+def test_taylor_order4_equals_classic_rk4():
+    """For a linear H the order-4 Taylor step and the classic four stages are one polynomial."""
+    M = 5
+    w = wl.dispersion_quadratic(M)
+    L = wl.contact_coupling(M, -0.3)
+    sp_ = orc.Space(M, orc.all_sectors(M, 2, 4))
+    rng = np.random.default_rng(11)
+    psi0 = rng.standard_normal(sp_.total) + 1j * rng.standard_normal(sp_.total)
+    got = orc.taylor(sp_, w, L, psi0, 3e-3, 40, 4)
+    ref = orc.rk4(sp_, w, L, psi0, 3e-3, 40)
+    assert np.linalg.norm(got - ref) < 1e-13 * np.linalg.norm(ref)
+
+
+def test_taylor_order2_discrete_exact_on_diagonal_hamiltonian():
+    """Second-order Taylor (Sec. III B's step with the 1/2 restored) multiplies each
+    amplitude of a diagonal H by 1 + x + x^2/2, x = -i E dt, per step."""
+    M = 3
+    w = np.array([0.7, -1.3, 2.1])
+    L = np.zeros((M,) * 4, dtype=np.complex128)
+    sp_ = orc.Space(M, orc.all_sectors(M, 0, 6))
+    rng = np.random.default_rng(12)
+    psi0 = rng.standard_normal(sp_.total) + 1j * rng.standard_normal(sp_.total)
+    x = -1j * (sp_.basis @ w) * 1e-2
+    ref = psi0 * (1 + x + x * x / 2) ** 200
+    got = orc.taylor(sp_, w, L, psi0, 1e-2, 200, 2)
+    assert np.linalg.norm(got - ref) < 1e-12 * np.linalg.norm(ref)
+
+
+def test_taylor_order3_equals_matrix_polynomial_on_interacting_sector():
+    M, N = 5, 4
+    w = wl.dispersion_quadratic(M)
+    L = wl.contact_coupling(M, -0.4)
+    sp_ = orc.Space(M, [(N, 1)])
+    lam, V = np.linalg.eigh(orc.h_dense(sp_, 0, w, L))
+    rng = np.random.default_rng(13)
+    psi0 = rng.standard_normal(sp_.total) + 1j * rng.standard_normal(sp_.total)
+    x = -1j * lam * 2e-3
+    ref = V @ ((1 + x + x ** 2 / 2 + x ** 3 / 6) ** 300 * (V.conj().T @ psi0))
+    got = orc.taylor(sp_, w, L, psi0, 2e-3, 300, 3)
+    assert np.linalg.norm(got - ref) < 1e-12 * np.linalg.norm(ref)
+
+
 def test_norm_decay_and_energy_under_rk4():
     """|R(iy)|^2 = 1 - y^6/72 + y^8/576 per eigencomponent: norm decays only at O(dt^6)."""
     y = 0.3
