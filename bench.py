@@ -302,10 +302,19 @@ def main():
     import paper_2111_00050_gb300 as qb
 
     W, sp = workload(args.config, args.n_tot)
+    t_setup = time.perf_counter()
     qs = qb.Space(W.M, W.w, W.L, sp["n_min"], sp["n_max"], sp["p_list"])
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
     terms, tuples = qs.terms()
     psi = qs.empty_state()
+    torch.cuda.synchronize()
+    ei0, ei1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ei0.record()
     init_state(qs, W, psi)
+    ei1.record()
+    torch.cuda.synchronize()
+    init_ms = ei0.elapsed_time(ei1)
     work = qs.workspace(1)
     resident_max = qs.autotune(W.dt, psi, steps=1, work=work)
     for _ in range(args.warmup):
@@ -382,6 +391,19 @@ def main():
     plain = {"ms_per_step": plain_ms, "terms_per_s": 4 * terms / (plain_ms * 1e-3), "steps": k_plain,
              "launches_per_step": 4 * qs.n_sectors, "batched_speedup": plain_ms / ms_step}
 
+    # ---- the second-order Taylor step of Sec. III B (two stage launches per step)
+    qs.set_order(2)
+    qs.evolve(psi, W.dt, 1, work)
+    e0t, e1t = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0t.record(stream)
+    qs.evolve(psi, W.dt, k_plain, work)
+    e1t.record(stream)
+    torch.cuda.synchronize()
+    qs.set_order(4)
+    t2_ms = e0t.elapsed_time(e1t) / k_plain
+    taylor2 = {"ms_per_step": t2_ms, "steps_per_s": 1e3 / t2_ms, "terms_per_s": 2 * terms / (t2_ms * 1e-3),
+               "steps": k_plain}
+
     # ---- end to end through the public API with host buffers
     host_in = torch.empty(qs.total, dtype=torch.complex128).pin_memory()
     host_in.copy_(psi.cpu())
@@ -399,6 +421,32 @@ def main():
            "d2h_bytes_per_step": 8 * nmom + 8 * 2, "steps_per_s": 1.0 / e2e_s,
            "note": "H2D of psi from pinned memory + one RK4 step + qb_observables (moments D2H) per step"}
 
+    # ---- the other rows of the path, each timed once: sector build + device tables (host
+    # wall clock), initial state, one observables call, observation steps + breaktime,
+    # the mean-field trajectory of the workload's full length
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    qs.observables(psi)
+    obs_ms = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    series = qs.evolve_observe(psi, W.dt, 2, 1, work)
+    torch.cuda.synchronize()
+    evobs_ms = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    bt = qb.breaktime([o["Q"] for o in series], W.dt, 0.1)
+    bt_us = (time.perf_counter() - t0) * 1e6
+    t0 = time.perf_counter()
+    qb.meanfield(W.M, W.w, W.L, W.z if W.z is not None else np.sqrt(W.occ), W.dt, W.steps, W.obs_every)
+    mf_ms = (time.perf_counter() - t0) * 1e3
+    rows = {"sector_build_and_tables_s": setup_s, "init_state_ms": init_ms,
+            "observables_ms": obs_ms, "observables_kets_per_s": qs.total / (obs_ms * 1e-3),
+            "evolve_observe_2_steps_3_obs_ms": evobs_ms, "breaktime_us": bt_us, "breaktime_flag": bt[1],
+            "meanfield_ms": mf_ms, "meanfield_steps": W.steps}
+    # kernel launches of the timed call: four stage launches per step, the weighted copy,
+    # and the resident kernel when some sector is small enough
+    resident = resident_max > 0 and int(qs.dims[0]) <= resident_max  # leading sectors run resident
+    launches = 4 * args.steps + 1 + (1 if resident else 0)
+
     line = {
         "metric": "H_psi_terms_per_s", "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -410,10 +458,12 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "rk4_steps_per_s": steps_per_s,
         "plain_per_sector": plain,
-        "gpu_launches": 4 * args.steps,
+        "taylor2": taylor2,
+        "gpu_launches": launches,
         "clocks": clocks,
         "roofline": roofline,
         "e2e": e2e,
+        "path_rows": rows,
     }
     if not args.no_extras:
         del work, psi

@@ -174,6 +174,14 @@ int qb_evolve_batch(qb_space* space, void* d_psi, int batch, const double* scale
  * do not depend on the setting: every ket goes through the same arithmetic. */
 int qb_space_set_resident_max(qb_space* space, int resident_max_kets);
 
+/* Order K of the time step of qb_evolve, qb_evolve_batch, qb_evolve_plain and
+ * qb_evolve_observe: psi <- sum_{k=0..K} (z H)^k / k! psi, z = -i dt, applied in
+ * the Horner form psi + z(psi + z/2(psi + ... + z/K psi)), K launches per step.
+ * K = 4 (the default) is RK4; K = 2 is the second-order Taylor step of Sec. III B
+ * (Eq. Q_int with the 1/2 of the second-order term).  Accepts 2, 3 or 4;
+ * QB_EINVAL otherwise.  qb_adjoint requires 4 (QB_EUNSUPPORTED otherwise). */
+int qb_space_set_order(qb_space* space, int order);
+
 /* The same RK4 evolution as qb_evolve with one kernel launch per sector per
  * stage instead of one per stage for every sector: the per-sector scheme of
  * Sec. III B taken literally, kept as the comparison baseline of the batched

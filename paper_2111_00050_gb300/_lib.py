@@ -66,6 +66,7 @@ SIGNATURES = {
     "qb_evolve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_void_p,
                                  ctypes.c_void_p]),
     "qb_space_set_resident_max": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "qb_space_set_order": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "qb_evolve_plain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_void_p,
                                        ctypes.c_void_p]),
     "qb_evolve_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _c_double_p, ctypes.c_double,

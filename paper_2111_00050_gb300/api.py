@@ -96,6 +96,7 @@ class Space:
         self.sectors = list(zip(N.tolist(), P.tolist()))
         self.dims = dim
         self.offsets = off
+        self.order = 4
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -159,6 +160,11 @@ class Space:
     def set_resident_max(self, kets: int) -> None:
         """qb_space_set_resident_max: sectors up to `kets` kets run shared-memory resident (0: never)."""
         check(lib().qb_space_set_resident_max(self._h, int(kets)))
+
+    def set_order(self, order: int) -> None:
+        """Taylor order of a time step (4: RK4, the default; 2: the second-order Taylor step)."""
+        check(lib().qb_space_set_order(self._h, int(order)))
+        self.order = int(order)
 
     def autotune(self, dt: float, psi: torch.Tensor, candidates=(0, 256, 1024, 4096), steps: int = 2,
                  work: Optional[torch.Tensor] = None) -> int:

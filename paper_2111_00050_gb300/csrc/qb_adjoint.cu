@@ -268,6 +268,7 @@ extern "C" int qb_adjoint(qb_space* space, const double* z, double scale, double
   if (loss_kind != QB_LOSS_Q && loss_kind != QB_LOSS_PO) return fail(QB_EINVAL, "unknown loss kind");
   if (!std::isfinite(dt) || !std::isfinite(scale)) return fail(QB_EINVAL, "dt and scale must be finite");
   if (!d_work || (reinterpret_cast<uintptr_t>(d_work) & 255)) return fail(QB_EINVAL, "d_work must be 256-byte aligned");
+  if (sp->order != 4) return fail(QB_EUNSUPPORTED, "the adjoint is the discrete adjoint of RK4 (order 4)");
   cudaStream_t st = (cudaStream_t)stream;
   const int M = sp->M;
   const AdjointLayout L = adjoint_layout(*sp, steps, ckpt_every, static_cast<unsigned char*>(d_work));

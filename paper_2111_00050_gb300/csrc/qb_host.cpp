@@ -672,6 +672,14 @@ int qb_space_set_resident_max(qb_space* space, int resident_max_kets) {
   return QB_OK;
 }
 
+int qb_space_set_order(qb_space* space, int order) {
+  Space* sp = reinterpret_cast<Space*>(space);
+  if (!sp) return fail(QB_EINVAL, "space is NULL");
+  if (order < 2 || order > 4) return fail(QB_EINVAL, "order must be 2, 3 or 4");
+  sp->order = order;
+  return QB_OK;
+}
+
 int qb_evolve_plain(qb_space* space, void* d_psi, double dt, int64_t steps, void* d_work, void* stream) {
   Space* sp = reinterpret_cast<Space*>(space);
   if (!sp) return fail(QB_EINVAL, "space is NULL");

@@ -88,6 +88,7 @@ struct Space {
   cudaStream_t side_stream = nullptr;     // resident small sectors run here, beside the large ones
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int resident_max_kets = 1024;           // sectors up to this size run shared-memory resident
+  int order = 4;                          // Taylor order of a time step (4: RK4)
   int device = 0;
   int grid_hpsi = 0;  // persistent grid sizes per kernel family
 };

@@ -987,13 +987,15 @@ template <int B>
 static int rk4_issue(Space& s, DfArgs& a, double dt, int64_t steps, float4* w1, float4* w2, float4* psif,
                      cudaStream_t st, bool plain, int64_t row0 = 0) {
   const bool cplx = s.t.is_complex != 0;
+  const int K = s.order;
   for (int64_t it = 0; it < steps; ++it) {
-    // Horner: v = psi + z/4 H psi; v = psi + z/3 H v; v = psi + z/2 H v; psi = psi + z H v
-    const float4* in[4] = {psif, w1, w2, w1};
-    float4* out[4] = {w1, w2, w1, psif};
-    for (int d = 4; d >= 1; --d) {
-      a.vin = in[4 - d];
-      a.out = out[4 - d];
+    // Horner (order K = 4): v = psi + z/4 H psi; v = psi + z/3 H v; v = psi + z/2 H v;
+    // psi = psi + z H v; stage j of K reads the previous output and writes w1 / w2
+    // alternately, the last one the weighted copy of psi
+    for (int d = K; d >= 1; --d) {
+      const int j = K - d;
+      a.vin = (j == 0) ? psif : ((j - 1) % 2 == 0 ? w1 : w2);
+      a.out = (d == 1) ? psif : (j % 2 == 0 ? w1 : w2);
       a.zre = dt / d;
       const float zh = (float)a.zre;
       a.zf = make_float2(zh, (float)(a.zre - (double)zh));
@@ -1061,6 +1063,7 @@ static int rk4_loop(Space& s, double2* psi, const double* scale, double dt, int6
       r.scale = a.scale[0];
       r.dt = dt;
       r.steps = steps;
+      r.order = s.order;
       r.n_small = n_small;
       r.cap = cap;
       r.status = a.status;

@@ -496,6 +496,7 @@ struct ResArgs {
   float2 scale;        // two-body scale, double-float
   double dt;
   int64_t steps;
+  int order;           // Taylor order of a step (stages per step)
   int n_small;         // sectors [0, n_small) are resident
   int cap;             // kets per sector the shared buffers hold
   int* status;
@@ -533,11 +534,10 @@ __global__ void __launch_bounds__(kBlock) resident_kernel(const Tables t, const 
     a.psif = spsif;
     a.nbasef = 0;
     for (int64_t it = 0; it < r.steps; ++it) {
-      const float4* in[4] = {spsif, sw1, sw2, sw1};
-      float4* out[4] = {sw1, sw2, sw1, spsif};
-      for (int d = 4; d >= 1; --d) {
-        a.vin = in[4 - d];
-        a.out = out[4 - d];
+      for (int d = r.order; d >= 1; --d) {
+        const int j = r.order - d;
+        a.vin = (j == 0) ? spsif : ((j - 1) % 2 == 0 ? sw1 : sw2);
+        a.out = (d == 1) ? spsif : (j % 2 == 0 ? sw1 : sw2);
         a.zre = r.dt / d;
         const float zh = (float)a.zre;
         a.zf = make_float2(zh, (float)(a.zre - (double)zh));

@@ -359,3 +359,58 @@ def test_resident_small_sectors_bit_identical_to_stage_launches(steps):
         os_ = orc.Space(M, qs.sectors)
         ref = orc.rk4(os_, w, L, orc.coherent_state(os_, z)[0], 1e-3, steps)
         assert rel_err(to_host(a), ref) <= STATE_TOL
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_taylor_order_matches_oracle(order):
+    """Selectable step order (Sec. III B's second-order Taylor step, and third order) on
+    a coherent multi-sector space, against the oracle's Taylor steps; the resident and
+    graph-replayed paths (70 steps) stay bit-identical to plain stage launches."""
+    import paper_2111_00050_gb300 as qb
+
+    M = 5
+    z, w, L = _coherent_case(M, 3.0, 13, -0.08, 1)
+    qs, os_ = pair(M, w, L, 0, 13, None)
+    qs.set_order(order)
+    psi = qs.empty_state()
+    qs.init_coherent(z, psi)
+    ref, _ = orc.coherent_state(os_, z)
+    b = psi.clone()
+    qs.evolve(psi, 2e-3, 70)
+    ref = orc.taylor(os_, w, L, ref, 2e-3, 70, order)
+    assert rel_err(to_host(psi), ref) <= STATE_TOL
+    qs.set_resident_max(0)
+    qs.evolve_plain(b, 2e-3, 70)
+    assert bool((psi == b).all())
+    with pytest.raises(qb.QbError):
+        qs.adjoint(z, 1.0, 2e-3, 2)  # the adjoint is RK4's
+    with pytest.raises(qb.QbError):
+        qs.set_order(5)
+
+
+def test_taylor_order_error_vs_exact_flow():
+    """Global error against the exact flow exp(-iHt) at t = 10 on the 42-ket sector of
+    |0,2,2,2,0>: the GPU's order-2, -3 and -4 runs (10^4 steps of 1e-3) land on the
+    eigenbasis prediction sum_k (-i E dt)^k / k! per step, i.e. ~1.04e-5, 1.04e-8, 1.03e-11."""
+    import math
+
+    import paper_2111_00050_gb300 as qb
+
+    W = wl.plain_single_sector()
+    qs = qb.Space(W.M, W.w, W.L, 6, 6, [0])
+    os_ = orc.Space(W.M, [(6, 0)])
+    lam, V = np.linalg.eigh(orc.h_dense(os_, 0, W.w, W.L))
+    psi0 = orc.number_state(os_, W.occ)
+    c0 = V.conj().T @ psi0
+    exact = V @ (np.exp(-1j * lam * W.steps * W.dt) * c0)
+    for order in (2, 3, 4):
+        x = -1j * lam * W.dt
+        pred = V @ (sum(x ** k / math.factorial(k) for k in range(order + 1)) ** W.steps * c0)
+        qs.set_order(order)
+        psi = qs.empty_state()
+        qs.init_number(W.occ, psi)
+        qs.evolve(psi, W.dt, W.steps)
+        got = to_host(psi)
+        assert rel_err(got, pred) <= STATE_TOL
+        e_pred = np.linalg.norm(pred - exact)
+        assert abs(np.linalg.norm(got - exact) - e_pred) <= 1e-3 * e_pred + STATE_TOL
