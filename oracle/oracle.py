@@ -51,11 +51,11 @@ def _L():
         lib = ctypes.CDLL(_LIB_PATH)
         i64, i32, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
         lib.orc_sector_basis.restype = i64
-        lib.orc_sector_basis.argtypes = [i32, i32, i32, vp, i64]
+        lib.orc_sector_basis.argtypes = [i32, i32, i32, i32, vp, i64]
         lib.orc_find.restype = i64
         lib.orc_find.argtypes = [i32, vp, i64, vp]
         lib.orc_check_coupling.restype = i32
-        lib.orc_check_coupling.argtypes = [i32, vp]
+        lib.orc_check_coupling.argtypes = [i32, vp, i32]
         lib.orc_apply_h.restype = i32
         lib.orc_apply_h.argtypes = [i32, i64, vp, vp, vp, vp, vp, i32]
         lib.orc_rk4.restype = i32
@@ -65,9 +65,9 @@ def _L():
         lib.orc_count_terms.restype = i64
         lib.orc_count_terms.argtypes = [i32, i64, vp, vp]
         lib.orc_moments.restype = None
-        lib.orc_moments.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp]
+        lib.orc_moments.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, i32]
         lib.orc_apply_mode_op.restype = None
-        lib.orc_apply_mode_op.argtypes = [i32, i32, vp, vp, vp, vp, vp, i32, i32, vp]
+        lib.orc_apply_mode_op.argtypes = [i32, i32, vp, vp, vp, vp, vp, i32, i32, vp, i32]
         _lib = lib
     return _lib
 
@@ -85,39 +85,42 @@ def labels(M: int) -> np.ndarray:
     return np.array([label(M, i) for i in range(M)], dtype=np.int64)
 
 
-def sector_of(occ) -> tuple[int, int]:
-    """(N, P) of an occupation vector (Sec. III B)."""
+def sector_of(occ, exact: bool = False) -> tuple[int, int]:
+    """(N, P) of an occupation vector (Sec. III B); P mod M unless exact."""
     occ = np.asarray(occ, dtype=np.int64)
     M = occ.size
-    return int(occ.sum()), int(np.dot(labels(M), occ) % M)
+    P = int(np.dot(labels(M), occ))
+    return int(occ.sum()), (P if exact else P % M)
 
 
-def sector_basis(M: int, N: int, P: int) -> np.ndarray:
+def sector_basis(M: int, N: int, P: int, exact: bool = False) -> np.ndarray:
     """All occupation vectors of sector (N, P), lexicographic, shape [D, M]."""
     lib = _L()
-    D = lib.orc_sector_basis(M, N, P, None, 0)
+    D = lib.orc_sector_basis(M, N, P, int(exact), None, 0)
     out = np.zeros((max(D, 0), M), dtype=np.int32)
     if D > 0:
-        lib.orc_sector_basis(M, N, P, _p(out), D)
+        lib.orc_sector_basis(M, N, P, int(exact), _p(out), D)
     return out
 
 
-def sector_dim(M: int, N: int, P: int) -> int:
-    return int(_L().orc_sector_basis(M, N, P, None, 0))
+def sector_dim(M: int, N: int, P: int, exact: bool = False) -> int:
+    return int(_L().orc_sector_basis(M, N, P, int(exact), None, 0))
 
 
-def check_coupling(M: int, L: np.ndarray) -> bool:
+def check_coupling(M: int, L: np.ndarray, exact: bool = False) -> bool:
     Lc = np.ascontiguousarray(L, dtype=np.complex128).reshape(-1)
-    return _L().orc_check_coupling(M, _p(Lc)) == 0
+    return _L().orc_check_coupling(M, _p(Lc), int(exact)) == 0
 
 
 class Space:
-    """A list of sectors with their concatenated lexicographic bases."""
+    """A list of sectors with their concatenated lexicographic bases; exact:
+    sectors of exact total momentum (the plain label sum) instead of mod M."""
 
-    def __init__(self, M: int, sectors):
+    def __init__(self, M: int, sectors, exact: bool = False):
         self.M = M
-        self.sectors = [(int(N), int(P) % M) for N, P in sectors]
-        bases = [sector_basis(M, N, P) for N, P in self.sectors]
+        self.exact = bool(exact)
+        self.sectors = [(int(N), int(P) if exact else int(P) % M) for N, P in sectors]
+        bases = [sector_basis(M, N, P, exact) for N, P in self.sectors]
         self.dims = np.array([b.shape[0] for b in bases], dtype=np.int64)
         self.off = np.zeros(len(bases) + 1, dtype=np.int64)
         self.off[1:] = np.cumsum(self.dims)
@@ -132,7 +135,7 @@ class Space:
     def index_of(self, occ) -> int:
         """Global index of an occupation vector, or -1."""
         occ = np.ascontiguousarray(occ, dtype=np.int32)
-        N, P = sector_of(occ)
+        N, P = sector_of(occ, self.exact)
         for s, (sN, sP) in enumerate(self.sectors):
             if (sN, sP) == (N, P):
                 b = self.basis[self.off[s]:self.off[s + 1]]
@@ -144,8 +147,13 @@ class Space:
         return slice(int(self.off[s]), int(self.off[s + 1]))
 
 
-def all_sectors(M: int, n_min: int, n_max: int):
-    return [(N, P) for N in range(n_min, n_max + 1) for P in range(M) if sector_dim(M, N, P) > 0]
+def all_sectors(M: int, n_min: int, n_max: int, exact: bool = False):
+    """Non-empty sectors, N ascending then P ascending (exact: every label sum)."""
+    out = []
+    for N in range(n_min, n_max + 1):
+        Ps = range(int(labels(M).min()) * N, int(labels(M).max()) * N + 1) if exact else range(M)
+        out += [(N, P) for P in Ps if sector_dim(M, N, P, exact) > 0]
+    return out
 
 
 # --------------------------------------------------------------------------- H
@@ -236,7 +244,7 @@ def h_dense(space: Space, s: int, w, L) -> np.ndarray:
     """Dense matrix of H restricted to sector s, column j = H e_j."""
     sl = space.sector_slice(s)
     D = sl.stop - sl.start
-    sub = Space(space.M, [space.sectors[s]])
+    sub = Space(space.M, [space.sectors[s]], space.exact)
     Hm = np.zeros((D, D), dtype=np.complex128)
     for j in range(D):
         e = np.zeros(D, dtype=np.complex128)
@@ -302,7 +310,7 @@ def moments(space: Space, psi: np.ndarray) -> dict:
     psi = np.ascontiguousarray(psi, dtype=np.complex128)
     out = np.zeros(2 + 2 * M + 4 * M * M, dtype=np.float64)
     _L().orc_moments(M, len(space.sectors), _p(space.secN), _p(space.secP), _p(space.off), _p(space.basis),
-                     _p(psi), _p(out))
+                     _p(psi), _p(out), int(space.exact))
     c = out[2:].view(np.complex128)
     return {
         "norm": out[0],
@@ -319,7 +327,7 @@ def apply_mode_op(space: Space, psi: np.ndarray, kind: str, i: int) -> np.ndarra
     psi = np.ascontiguousarray(psi, dtype=np.complex128)
     out = np.zeros_like(psi)
     _L().orc_apply_mode_op(space.M, len(space.sectors), _p(space.secN), _p(space.secP), _p(space.off),
-                           _p(space.basis), _p(psi), k, int(i), _p(out))
+                           _p(space.basis), _p(psi), k, int(i), _p(out), int(space.exact))
     return out
 
 

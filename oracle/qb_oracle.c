@@ -21,7 +21,8 @@
  *
  * Complex numbers are stored as interleaved (re, im) doubles.
  * Mode labels: for odd M, mode index i carries momentum label i - (M-1)/2; for
- * even M the label is i.  Momentum is conserved modulo M.
+ * even M the label is i.  Momentum is conserved modulo M, or exactly (the plain
+ * label sum, Sec. III B) where a function takes exact = 1.
  */
 #include <math.h>
 #include <stdint.h>
@@ -43,18 +44,22 @@ static int mode_of_residue(int M, int k) {
   return -1;
 }
 
-static int momentum_of(int M, const int* n) {
+/* total momentum of a ket: the label sum, reduced mod M unless exact */
+static int momentum_of(int M, const int* n, int exact) {
   int k = 0;
   for (int i = 0; i < M; ++i) k += label_of(M, i) * n[i];
-  return mod_pos(k, M);
+  return exact ? k : mod_pos(k, M);
 }
+
+/* a momentum label sum, reduced mod M unless exact */
+static int pwrap(int k, int M, int exact) { return exact ? k : mod_pos(k, M); }
 
 /* ---- basis enumeration (Sec. III B: the special Hilbert space of (N, P)) ---- */
 
-static void enum_rec(int M, int m, int rem, int P, int* cur, int64_t* count, int* out, int64_t cap) {
+static void enum_rec(int M, int m, int rem, int P, int exact, int* cur, int64_t* count, int* out, int64_t cap) {
   if (m == M - 1) {
     cur[m] = rem;
-    if (momentum_of(M, cur) == P) {
+    if (momentum_of(M, cur, exact) == P) {
       if (out && *count < cap) memcpy(out + (*count) * M, cur, sizeof(int) * (size_t)M);
       ++*count;
     }
@@ -62,18 +67,18 @@ static void enum_rec(int M, int m, int rem, int P, int* cur, int64_t* count, int
   }
   for (int v = 0; v <= rem; ++v) {
     cur[m] = v;
-    enum_rec(M, m + 1, rem - v, P, cur, count, out, cap);
+    enum_rec(M, m + 1, rem - v, P, exact, cur, count, out, cap);
   }
 }
 
-/* Number of kets with sum n = N and momentum P (mod M); if out != NULL the first
- * `cap` occupation vectors are written row-major [count][M] in lexicographic
- * order (n_0 ascending, then n_1, ...).  Returns the total count. */
-int64_t orc_sector_basis(int M, int N, int P, int* out, int64_t cap) {
+/* Number of kets with sum n = N and momentum P (mod M, or exactly); if out !=
+ * NULL the first `cap` occupation vectors are written row-major [count][M] in
+ * lexicographic order (n_0 ascending, then n_1, ...).  Returns the total count. */
+int64_t orc_sector_basis(int M, int N, int P, int exact, int* out, int64_t cap) {
   int cur[64];
   int64_t count = 0;
   if (M < 1 || M > 64 || N < 0) return -1;
-  enum_rec(M, 0, N, mod_pos(P, M), cur, &count, out, cap);
+  enum_rec(M, 0, N, pwrap(P, M, exact), exact, cur, &count, out, cap);
   return count;
 }
 
@@ -104,14 +109,15 @@ static int64_t find_ket(int M, const int* basis, int64_t D, const int* occ) {
 int64_t orc_find(int M, const int* basis, int64_t D, const int* occ) { return find_ket(M, basis, D, occ); }
 
 /* Rejects a coupling tensor with a nonzero entry on a tuple that does not
- * conserve momentum mod M (the delta in Eq. Lambda).  Returns 0 if valid. */
-int orc_check_coupling(int M, const double* L) {
+ * conserve momentum (mod M, or exactly; the delta in Eq. Lambda).  Returns 0 if
+ * valid. */
+int orc_check_coupling(int M, const double* L, int exact) {
   for (int p = 0; p < M; ++p)
     for (int q = 0; q < M; ++q)
       for (int r = 0; r < M; ++r)
         for (int s = 0; s < M; ++s) {
           int64_t t = (((int64_t)p * M + q) * M + r) * M + s;
-          int cons = mod_pos(label_of(M, p) + label_of(M, q) - label_of(M, r) - label_of(M, s), M) == 0;
+          int cons = pwrap(label_of(M, p) + label_of(M, q) - label_of(M, r) - label_of(M, s), M, exact) == 0;
           if (!cons && (L[2 * t] != 0.0 || L[2 * t + 1] != 0.0)) return -1;
         }
   return 0;
@@ -240,7 +246,7 @@ static int find_sector(int nsec, const int* secN, const int* secP, int N, int P)
  * sectors contributes zero (truncated space).
  */
 void orc_moments(int M, int nsec, const int* secN, const int* secP, const int64_t* off, const int* basis,
-                 const double* psi, double* out) {
+                 const double* psi, double* out, int exact) {
   int tmp[64];
   int nout = 2 + 2 * M + 4 * M * M;
   memset(out, 0, sizeof(double) * (size_t)nout);
@@ -262,7 +268,7 @@ void orc_moments(int M, int nsec, const int* secN, const int* secP, const int64_
         memcpy(tmp, n, sizeof(int) * (size_t)M);
         double c = sqrt((double)tmp[i]);
         tmp[i] -= 1;
-        int t = find_sector(nsec, secN, secP, secN[s] - 1, mod_pos(secP[s] - label_of(M, i), M));
+        int t = find_sector(nsec, secN, secP, secN[s] - 1, pwrap(secP[s] - label_of(M, i), M, exact));
         if (t < 0) continue;
         int64_t k = find_ket(M, basis + off[t] * M, off[t + 1] - off[t], tmp);
         if (k < 0) continue;
@@ -281,7 +287,7 @@ void orc_moments(int M, int nsec, const int* secN, const int* secP, const int64_
           tmp[jj] -= 1;
           tmp[i] += 1;
           c *= sqrt((double)tmp[i]);
-          int t = find_sector(nsec, secN, secP, secN[s], mod_pos(secP[s] - label_of(M, jj) + label_of(M, i), M));
+          int t = find_sector(nsec, secN, secP, secN[s], pwrap(secP[s] - label_of(M, jj) + label_of(M, i), M, exact));
           if (t < 0) continue;
           int64_t k = find_ket(M, basis + off[t] * M, off[t + 1] - off[t], tmp);
           if (k < 0) continue;
@@ -301,7 +307,7 @@ void orc_moments(int M, int nsec, const int* secN, const int* secP, const int64_
           c *= sqrt((double)tmp[i]);
           tmp[i] -= 1;
           int t = find_sector(nsec, secN, secP, secN[s] - 2,
-                              mod_pos(secP[s] - label_of(M, jj) - label_of(M, i), M));
+                              pwrap(secP[s] - label_of(M, jj) - label_of(M, i), M, exact));
           if (t < 0) continue;
           int64_t k = find_ket(M, basis + off[t] * M, off[t + 1] - off[t], tmp);
           if (k < 0) continue;
@@ -320,7 +326,7 @@ void orc_moments(int M, int nsec, const int* secN, const int* secP, const int64_
  * dropped).  Used to form gradients of moment-based losses.
  */
 void orc_apply_mode_op(int M, int nsec, const int* secN, const int* secP, const int64_t* off, const int* basis,
-                       const double* psi, int kind, int i, double* out) {
+                       const double* psi, int kind, int i, double* out, int exact) {
   int tmp[64];
   memset(out, 0, sizeof(double) * 2 * (size_t)off[nsec]);
   for (int s = 0; s < nsec; ++s) {
@@ -339,12 +345,12 @@ void orc_apply_mode_op(int M, int nsec, const int* secN, const int* secP, const 
         c = sqrt((double)tmp[i]);
         tmp[i] -= 1;
         tN = secN[s] - 1;
-        tP = mod_pos(secP[s] - label_of(M, i), M);
+        tP = pwrap(secP[s] - label_of(M, i), M, exact);
       } else {
         tmp[i] += 1;
         c = sqrt((double)tmp[i]);
         tN = secN[s] + 1;
-        tP = mod_pos(secP[s] + label_of(M, i), M);
+        tP = pwrap(secP[s] + label_of(M, i), M, exact);
       }
       int t = find_sector(nsec, secN, secP, tN, tP);
       if (t < 0) continue;

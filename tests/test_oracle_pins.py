@@ -119,6 +119,99 @@ def test_sector_dim_scaling_appendix():
             assert abs(orc.sector_dim(M, N, P) * M / comp - 1) < 0.01
 
 
+def gen_function_dims_exact(M, N):
+    """Exact-momentum sector sizes from prod_i 1/(1 - t x^{label_i}) without any
+    modulus: dict P -> #kets with N particles and label sum P."""
+    lab = [int(x) for x in wl.mode_labels(M)]
+    c = {(0, 0): 1}
+    for i in range(M):
+        new = {}
+        for (n, k), cnt in c.items():
+            for v in range(0, N - n + 1):
+                key = (n + v, k + v * lab[i])
+                new[key] = new.get(key, 0) + cnt
+        c = new
+    return {k: cnt for (n, k), cnt in c.items() if n == N}
+
+
+def test_exact_sector_dims_match_generating_function_and_residue_classes():
+    """Exact momentum (Sec. III B): sizes from the generating function, and the
+    exact sectors with P = P0 (mod M) partition the mod-M sector P0."""
+    for M, N in [(1, 4), (3, 6), (5, 6), (5, 9), (7, 5), (4, 5)]:
+        ref = gen_function_dims_exact(M, N)
+        lab = wl.mode_labels(M)
+        for P in range(int(lab.min()) * N - 2, int(lab.max()) * N + 3):
+            assert orc.sector_dim(M, N, P, exact=True) == ref.get(P, 0), (M, N, P)
+        for P0 in range(M):
+            assert sum(d for P, d in ref.items() if (P - P0) % M == 0) == orc.sector_dim(M, N, P0)
+
+
+def test_exact_basis_is_sorted_and_in_sector():
+    b = orc.sector_basis(5, 6, 1, exact=True)
+    keys = [tuple(r) for r in b]
+    assert len(keys) > 0 and keys == sorted(keys) and len(set(keys)) == len(keys)
+    for r in b:
+        assert orc.sector_of(r, exact=True) == (6, 1)
+    sp_ = orc.Space(5, orc.all_sectors(5, 0, 4, exact=True), exact=True)
+    assert sp_.total == sum(math.comb(N + 4, 4) for N in range(5))  # every ket once
+    for k in (0, 17, sp_.total - 1):
+        assert sp_.index_of(sp_.basis[k]) == k
+
+
+def test_exact_coupling_rule():
+    M = 5
+    assert orc.check_coupling(M, wl.contact_coupling(M, 0.1, exact=True), exact=True)
+    assert not orc.check_coupling(M, wl.contact_coupling(M, 0.1), exact=True)  # umklapp terms
+    assert orc.check_coupling(M, wl.contact_coupling(M, 0.1, exact=True))  # exact implies mod M
+
+
+@pytest.mark.parametrize("case", ["contact", "long_range"])
+def test_exact_sector_hamiltonian_and_moments_match_tensor_product(case):
+    """Exact-momentum sectors are closed under an exactly conserving H, which the
+    oracle applies literally; moments of a multi-sector exact space follow the
+    full Fock-space operators."""
+    M, N = 5, 4
+    w = wl.dispersion_quadratic(M)
+    L = wl.contact_coupling(M, -0.3, exact=True) if case == "contact" else wl.long_range_coupling(M, 0.7, exact=True)
+    Hf = fock_hamiltonian(M, N, w, L)
+    for P in range(-2 * N, 2 * N + 1):
+        sp_ = orc.Space(M, [(N, P)], exact=True)
+        if sp_.total == 0:
+            continue
+        Hs = orc.h_dense(sp_, 0, w, L)
+        idx = [full_index(o, N) for o in sp_.basis]
+        ref = Hf[idx][:, idx].toarray()
+        np.testing.assert_allclose(Hs, ref, atol=1e-13, rtol=0)
+        col_mass = np.asarray(abs(Hf[:, idx]).sum(axis=0)).ravel()
+        np.testing.assert_allclose(col_mass, np.abs(ref).sum(axis=0), atol=1e-12)
+    # moments on all exact sectors with N <= 3 against the tensor-product operators
+    cut = 3
+    sp_ = orc.Space(M, orc.all_sectors(M, 0, cut, exact=True), exact=True)
+    rng = np.random.default_rng(8)
+    psi = rng.standard_normal(sp_.total) + 1j * rng.standard_normal(sp_.total)
+    full = np.zeros((cut + 1) ** M, dtype=np.complex128)
+    full[[full_index(o, cut) for o in sp_.basis]] = psi
+    a = fock_ops(M, cut)
+    mo = orc.moments(sp_, psi)
+    for i in range(M):
+        assert abs(mo["a"][i] - np.vdot(full, a[i] @ full)) < 1e-12
+        for j in range(M):
+            assert abs(mo["Mij"][i, j] - np.vdot(full, a[i].conj().T @ (a[j] @ full))) < 1e-12
+            assert abs(mo["aa"][i, j] - np.vdot(full, a[i] @ (a[j] @ full))) < 1e-12
+
+
+def test_minimal_image_long_range():
+    """Minimal image on the ring: |d| <= M/2, so labels -3 and 3 of M = 7 are one apart."""
+    M = 7
+    L = wl.long_range_coupling(M, 1.0, min_image=True)
+    lab = list(wl.mode_labels(M))
+    p, r = lab.index(-3), lab.index(3)
+    q = lab.index(0)
+    s = [i for i in range(M) if (lab[p] + lab[q] - lab[r] - lab[i]) % M == 0][0]
+    assert abs(L[p, q, r, s] - (-1.0 / M)) < 1e-15
+    assert abs(wl.long_range_coupling(M, 1.0)[p, q, r, s] - (-1.0 / (M * 36))) < 1e-15
+
+
 def test_basis_is_sorted_and_in_sector():
     b = orc.sector_basis(5, 6, 0)
     assert b.shape == (42, 5)

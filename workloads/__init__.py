@@ -8,8 +8,10 @@ time stepping, no observables) lives here.
 
 Coupling tensors are complex arrays L[p, q, r, s] (mode indices) with
 L_{pq;rs} = Lambda^{rs}_{pq} / 2, the coefficient of a_p^dag a_q^dag a_r a_s in
-the ordered sum of Eq. (Ham); entries that do not conserve momentum modulo M are
-zero.  Mode index i carries momentum label i - (M-1)/2 for odd M (i for even M).
+the ordered sum of Eq. (Ham); entries that do not conserve momentum are zero
+(modulo M by default; exactly, the plain label sum of Sec. III B, with
+exact=True).  Mode index i carries momentum label i - (M-1)/2 for odd M (i for
+even M).
 """
 from __future__ import annotations
 
@@ -24,10 +26,10 @@ def mode_labels(M: int) -> np.ndarray:
     return np.arange(M) - (M - 1) // 2 if M % 2 else np.arange(M)
 
 
-def _conserving(M: int) -> np.ndarray:
+def _conserving(M: int, exact: bool = False) -> np.ndarray:
     lab = mode_labels(M)
     s = lab[:, None, None, None] + lab[None, :, None, None] - lab[None, None, :, None] - lab[None, None, None, :]
-    return (s % M) == 0
+    return (s == 0) if exact else (s % M) == 0
 
 
 def dispersion_quadratic(M: int) -> np.ndarray:
@@ -40,20 +42,23 @@ def dispersion_abs(M: int) -> np.ndarray:
     return np.abs(mode_labels(M)).astype(np.float64)
 
 
-def contact_coupling(M: int, C: float) -> np.ndarray:
+def contact_coupling(M: int, C: float, exact: bool = False) -> np.ndarray:
     """Contact interaction L_{pq;rs} = C / M on every momentum-conserving tuple."""
-    return np.where(_conserving(M), C / M, 0.0).astype(np.complex128)
+    return np.where(_conserving(M, exact), C / M, 0.0).astype(np.complex128)
 
 
-def long_range_coupling(M: int, G: float) -> np.ndarray:
-    """Gravity-like L_{pq;rs} = -G / (M (p - r)^2) for labels p != r, else 0
-    (the raw label difference; the divergent p = r term is dropped)."""
+def long_range_coupling(M: int, G: float, exact: bool = False, min_image: bool = False) -> np.ndarray:
+    """Gravity-like L_{pq;rs} = -G / (M d^2) for labels p != r, else 0, with
+    d = p - r the raw label difference, or (min_image) its minimal image on the
+    ring of M momenta, |d| <= M/2; the divergent p = r term is dropped."""
     lab = mode_labels(M).astype(np.float64)
     d = lab[:, None, None, None] - lab[None, None, :, None]
+    if min_image:
+        d = d - M * np.round(d / M)
     d = np.broadcast_to(d, (M, M, M, M))
     with np.errstate(divide="ignore"):
         val = np.where(d != 0, -G / (M * np.where(d != 0, d, 1.0) ** 2), 0.0)
-    return np.where(_conserving(M), val, 0.0).astype(np.complex128)
+    return np.where(_conserving(M, exact), val, 0.0).astype(np.complex128)
 
 
 def paper_coupling(M: int, C: float, Lambda0: float) -> np.ndarray:
