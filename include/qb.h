@@ -60,13 +60,16 @@ typedef struct qb_space qb_space; /* opaque; created by qb_sector_build, freed b
 
 /* Model of Eq. (Ham).  w: [M] host doubles.  L: [M^4] host complex values as
  * (re, im) pairs, index ((p*M + q)*M + r)*M + s.  Entries on tuples that do
- * not conserve momentum mod M must be zero (the Kronecker delta of
- * Eq. Lambda).  The library uses only the part symmetric under p<->q and
- * r<->s and requires the Hermiticity L_{pq;rs} = conj(L_{rs;pq}) of that part. */
+ * not conserve momentum must be zero (the Kronecker delta of Eq. Lambda):
+ * momentum mod M when exact_momentum is 0, the plain sum of the labels
+ * (Sec. III B) when exact_momentum is 1.  The library uses only the part
+ * symmetric under p<->q and r<->s and requires the Hermiticity
+ * L_{pq;rs} = conj(L_{rs;pq}) of that part. */
 typedef struct {
   int M;
   const double* w;
   const double* L;
+  int exact_momentum; /* 0: P is conserved mod M (umklapp terms allowed); 1: exactly */
 } qb_model;
 
 /* Observables of Sec. II C-E for one state, normalised by <psi|psi>.
@@ -97,8 +100,10 @@ const char* qb_last_error(void);
 /* ---- sectors (Sec. III B "special Hilbert spaces", App. A) -------------- */
 
 /* Builds the space of all non-empty sectors (N, P) with n_min <= N <= n_max and
- * P (a momentum label taken mod M, in [0, M)) in p_list[0..n_p), or every P
- * when p_list is NULL.  Copies and validates the model (conservation,
+ * P in p_list[0..n_p), or every P when p_list is NULL.  P is the total
+ * momentum label sum_i p_i n_i: taken mod M, in [0, M), for a model with
+ * exact_momentum = 0, the exact (possibly negative) sum otherwise; sectors come
+ * in the order N ascending, then P ascending.  Copies and validates the model (conservation,
  * Hermiticity), builds the combinatorial ranking tables and uploads them to the
  * current device.  Limits: 1 <= M <= QB_MAX_MODES; M * bits(n_max) <= 64;
  * every sector dimension < 2^31.  *out receives the new space. */

@@ -17,7 +17,7 @@ _c_i64_p = ctypes.POINTER(ctypes.c_int64)
 
 
 class QbModel(ctypes.Structure):
-    _fields_ = [("M", ctypes.c_int), ("w", _c_double_p), ("L", _c_double_p)]
+    _fields_ = [("M", ctypes.c_int), ("w", _c_double_p), ("L", _c_double_p), ("exact_momentum", ctypes.c_int)]
 
 
 MX = QB_MAX_MODES

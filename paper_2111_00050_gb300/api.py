@@ -35,13 +35,13 @@ def _c128_as_f64(a) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(a, dtype=np.complex128)).view(np.float64)
 
 
-def _model(M: int, w, L):
+def _model(M: int, w, L, exact: bool = False):
     w = _f64(w)
     Lf = _c128_as_f64(np.asarray(L, dtype=np.complex128).reshape(-1))
     if w.size != M or Lf.size != 2 * M ** 4:
         raise ValueError("w must have M entries and L M^4")
     m = QbModel(M, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                Lf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+                Lf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1 if exact else 0)
     return m, (w, Lf)  # keep the arrays alive with the struct
 
 
@@ -69,11 +69,14 @@ def obs_to_dict(o: QbObs, M: int) -> dict:
 
 class Space:
     """qb_sector_build: all non-empty sectors (N, P) with n_min <= N <= n_max
-    and P in p_list (every P if None)."""
+    and P in p_list (every P if None).  exact: momentum conserved exactly (P the
+    plain label sum) instead of mod M."""
 
-    def __init__(self, M: int, w, L, n_min: int, n_max: int, p_list: Optional[Sequence[int]] = None):
+    def __init__(self, M: int, w, L, n_min: int, n_max: int, p_list: Optional[Sequence[int]] = None,
+                 exact: bool = False):
         self.M = int(M)
-        self._model, self._keep = _model(self.M, w, L)
+        self.exact = bool(exact)
+        self._model, self._keep = _model(self.M, w, L, self.exact)
         h = ctypes.c_void_p()
         if p_list is None:
             check(lib().qb_sector_build(ctypes.byref(self._model), int(n_min), int(n_max), None, 0, ctypes.byref(h)))
@@ -246,8 +249,8 @@ def breaktime(values, dt_obs: float, thr: float):
     return float(t.value), int(f.value)
 
 
-def meanfield(M: int, w, L, z0, dt: float, steps: int, every: int = 1) -> np.ndarray:
-    m, keep = _model(M, w, L)
+def meanfield(M: int, w, L, z0, dt: float, steps: int, every: int = 1, exact: bool = False) -> np.ndarray:
+    m, keep = _model(M, w, L, exact)
     z = _c128_as_f64(z0)
     rows = steps // every + 1
     out = np.zeros(2 * M * rows, dtype=np.float64)

@@ -60,8 +60,8 @@ __device__ __forceinline__ double2 psi_at(const Tables& t, const View& v, const 
   }
   const int Nt = N + dN;
   if (Nt < 0 || Nt > t.nmax) return make_double2(0.0, 0.0);
-  const int Kt = (((K + dK) % t.M) + t.M) % t.M;
-  const int sid = __ldg(t.sec_of + Nt * t.M + Kt);
+  const int Kt = (((K + dK) % t.Q) + t.Q) % t.Q;
+  const int sid = __ldg(t.sec_of + Nt * t.Q + Kt);
   if (sid < 0) return make_double2(0.0, 0.0);
   const int64_t off = __ldg(t.sec_off + sid), D = __ldg(t.sec_off + sid + 1) - off;
   const int64_t r = rank_changed(t, v, rs, nch, e, dn, D);
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kBlock) seed_kernel(const Tables t, const Seed
   extern __shared__ __align__(16) unsigned char smem[];
   load_blob(t, smem);
   const View v = make_view(t, smem);
-  const RowScratch rs = row_scratch(smem + ((t.blob_bytes + 15) & ~15));
+  const RowScratch rs = row_scratch(smem + blob_smem(t));
   const int tid = threadIdx.x, M = t.M;
   for (int64_t base = (int64_t)blockIdx.x * kBlock; base < t.total; base += (int64_t)gridDim.x * kBlock) {
     const int64_t g = base + tid;
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kBlock) mixed_kernel(const Tables t, const dou
   extern __shared__ __align__(16) unsigned char smem[];
   load_blob(t, smem);
   const View v = make_view(t, smem);
-  const RowScratch rs = row_scratch(smem + ((t.blob_bytes + 15) & ~15));
+  const RowScratch rs = row_scratch(smem + blob_smem(t));
   const int tid = threadIdx.x, M = t.M;
   double acc[2 * (kMaxM + 1)];
   for (int k = 0; k < 2 * (kMaxM + 1); ++k) acc[k] = 0.0;
@@ -324,7 +324,7 @@ extern "C" int qb_adjoint(qb_space* space, const double* z, double scale, double
     sa.lamp = ob.lam_p;
   }
   {
-    const size_t smem = ((sp->t.blob_bytes + 15) & ~15) + kRowScratchBytes;
+    const size_t smem = blob_smem(sp->t) + kRowScratchBytes;
     int grid = 0;
     rc = persistent_grid(seed_kernel, smem, n, &grid);
     if (rc) return rc;
@@ -415,7 +415,7 @@ extern "C" int qb_adjoint(qb_space* space, const double* z, double scale, double
   QB_CUDA(cudaMemcpyAsync(hacc, L.acc, 8 * (M + 1), cudaMemcpyDeviceToHost, st));
   std::vector<double> lamps(2 * (M + 1)), psips(2 * (M + 1));
   {
-    const size_t smem = ((sp->t.blob_bytes + 15) & ~15) + kRowScratchBytes;
+    const size_t smem = blob_smem(sp->t) + kRowScratchBytes;
     int grid = 0;
     rc = persistent_grid(mixed_kernel, smem, n, &grid);
     if (rc) return rc;

@@ -36,7 +36,8 @@ struct View {
   const double* gd;
 };
 
-__device__ __forceinline__ View make_view(const Tables& t, const unsigned char* s) {
+// Table pointers for an image whose byte 0 is at s (pointer arithmetic only).
+__device__ __forceinline__ View view_at(const Tables& t, const unsigned char* s) {
   View v;
   v.cnt = (const uint32_t*)(s + t.o_cnt);
   v.E = (const int32_t*)(s + t.o_E);
@@ -51,12 +52,36 @@ __device__ __forceinline__ View make_view(const Tables& t, const unsigned char* 
   return v;
 }
 
-// Copies the table image into shared memory (16-byte vector copies).
+// Bytes of the table image a row kernel stages in shared memory: everything from
+// t.sm_from on (the fill counts and the ranking table stay in global memory for
+// exact momentum, where they are large).
+__host__ __device__ inline size_t blob_smem(const Tables& t) {
+  return ((size_t)(t.blob_bytes - t.sm_from) + 15) & ~(size_t)15;
+}
+
+// Copies the row kernels' part of the table image into shared memory (16-byte
+// vector copies).
 __device__ __forceinline__ void load_blob(const Tables& t, unsigned char* smem) {
-  const int4* src = reinterpret_cast<const int4*>(t.blob);
+  const int4* src = reinterpret_cast<const int4*>(t.blob + t.sm_from);
   int4* dst = reinterpret_cast<int4*>(smem);
-  for (int i = threadIdx.x; i < t.blob_bytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+  for (int i = threadIdx.x; i < (t.blob_bytes - t.sm_from) / 16; i += blockDim.x) dst[i] = __ldg(src + i);
   __syncthreads();
+}
+
+// Table pointers of a row kernel after load_blob: the staged tables in shared
+// memory, the ones below t.sm_from in global memory.
+__device__ __forceinline__ View make_view(const Tables& t, const unsigned char* staged) {
+  View v = view_at(t, staged - t.sm_from);
+  if (t.o_cnt < t.sm_from) v.cnt = reinterpret_cast<const uint32_t*>(t.blob + t.o_cnt);
+  if (t.o_E < t.sm_from) v.E = reinterpret_cast<const int32_t*>(t.blob + t.o_E);
+  return v;
+}
+
+// Flat-index shift of term j's target suffix state at mode m (biased bytes, or
+// plain int16 for exact momentum).
+__device__ __forceinline__ int delta_shift(const Tables& t, const View& v, int j, int m) {
+  if (t.exact) return (int)reinterpret_cast<const int16_t*>(v.delta)[j * 16 + m];
+  return (int)reinterpret_cast<const uint8_t*>(v.delta)[j * 16 + m] - kDeltaBias;
 }
 
 // Copies the table image from byte offset `from` on (16-byte aligned) into
@@ -102,19 +127,19 @@ __device__ __forceinline__ int find_sector(const Tables& t, int64_t g) {
 // from the suffix states (equals i for a consistent table).
 __device__ __forceinline__ int64_t setup_row(const Tables& t, const View& v, const RowScratch& rs, int N, int K,
                                              int64_t D, int64_t i) {
-  const int M = t.M, tid = threadIdx.x, V = t.nmax + 1;
+  const int M = t.M, Q = t.Q, tid = threadIdx.x, V = t.nmax + 1;
   int rem = N, kr = K;
   int64_t left = i;
   for (int m = 0; m < M - 1; ++m) {
     int val = 0, kk = kr;
-    const uint32_t* row = v.cnt + (size_t)(m + 1) * V * M;
+    const uint32_t* row = v.cnt + (size_t)(m + 1) * V * Q;
     while (true) {
-      uint32_t c = row[(rem - val) * M + kk];
+      uint32_t c = row[(rem - val) * Q + kk];
       if (left < (int64_t)c || val == rem) break;
       left -= c;
       ++val;
       kk -= m;
-      if (kk < 0) kk += M;
+      if (kk < 0) kk += Q;
     }
     rs.occ[m * kBlock + tid] = (uint8_t)val;
     rem -= val;
@@ -122,13 +147,13 @@ __device__ __forceinline__ int64_t setup_row(const Tables& t, const View& v, con
   }
   rs.occ[(M - 1) * kBlock + tid] = (uint8_t)rem;
   // suffix states, from the top mode down
-  const int twoM = 2 * M;
+  const int twoQ = 2 * Q;
   int srem = 0, skr = 0;
   for (int m = M - 1; m >= 1; --m) {
     int nm = rs.occ[m * kBlock + tid];
     srem += nm;
-    skr = (skr + m * nm) % M;
-    rs.idx[m * kBlock + tid] = (m * t.rem_w + srem + 2) * twoM + skr;
+    skr = (skr + m * nm) % Q;
+    rs.idx[m * kBlock + tid] = (m * t.rem_w + srem + 2) * twoQ + skr;
   }
   int32_t acc = 0;
   rs.pe[tid] = 0;
@@ -169,7 +194,7 @@ __device__ __forceinline__ double2 ket_weight(const Tables& t, const uint8_t* oc
 // modes e[0..nch) by dn[0..nch), inside the sector of dimension Dt it lands in.
 __device__ __forceinline__ int64_t rank_changed(const Tables& t, const View& v, const RowScratch& rs, int nch,
                                                 const int* e, const int* dn, int64_t Dt) {
-  const int M = t.M, tid = threadIdx.x, twoM = 2 * M;
+  const int M = t.M, Q = t.Q, tid = threadIdx.x, twoQ = 2 * Q;
   int top = 0;
   for (int c = 0; c < nch; ++c) top = max(top, e[c]);
   if (top > M - 1) top = M - 1;
@@ -181,8 +206,8 @@ __device__ __forceinline__ int64_t rank_changed(const Tables& t, const View& v, 
         dc += dn[c];
         dk += dn[c] * m;
       }
-    int dkm = ((dk % M) + M) % M;
-    sum += v.E[rs.idx[m * kBlock + tid] + dc * twoM + dkm];
+    int dkm = ((dk % Q) + Q) % Q;
+    sum += v.E[rs.idx[m * kBlock + tid] + dc * twoQ + dkm];
   }
   return Dt - 1 - sum;
 }

@@ -56,9 +56,11 @@ static int prepare_model(const qb_model* model, std::vector<double>& w, std::vec
           cd v = Lat(p, q, r, s);
           if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) return fail(QB_EINVAL, "L has a non-finite entry");
           lmax = std::max(lmax, std::abs(v));
-          bool cons = modp((long long)(p - c) + (q - c) - (r - c) - (s - c), M) == 0;
+          const long long dP = (long long)(p - c) + (q - c) - (r - c) - (s - c);
+          bool cons = model->exact_momentum ? dP == 0 : modp(dP, M) == 0;
           if (!cons && v != cd(0, 0))
-            return fail(QB_EINVAL, "L is nonzero on a tuple that does not conserve momentum mod M");
+            return fail(QB_EINVAL, model->exact_momentum ? "L is nonzero on a tuple that does not conserve momentum"
+                                                         : "L is nonzero on a tuple that does not conserve momentum mod M");
         }
   Lsym.assign(2 * M4, 0.0);
   for (int p = 0; p < M; ++p)
@@ -86,17 +88,20 @@ static int prepare_model(const qb_model* model, std::vector<double>& w, std::vec
 // Builds the fill counts, ranking table, coupling combinations and the
 // shared-memory image of the space.
 static int build_tables(Space& sp) {
-  const int M = sp.M, nmax = sp.nmax;
-  // cnt[m][n][k]: fillings of modes m..M-1 with n particles, sum_i i n_i = k mod M
-  auto CI = [&](int m, int n, int k) { return ((size_t)m * (nmax + 1) + n) * M + k; };
-  sp.cnt.assign((size_t)(M + 1) * (nmax + 1) * M, 0);
+  const int M = sp.M, nmax = sp.nmax, Q = sp.Q;
+  // cnt[m][n][k]: fillings of modes m..M-1 with n particles, sum_i i n_i = k mod Q.
+  // With Q = (M-1) nmax + 1 no momentum sum of the space wraps: the counts, the
+  // ranking table and the coupling combinations below are those of exact
+  // conservation, and a wrapped (negative) index lands on a zero count.
+  auto CI = [&](int m, int n, int k) { return ((size_t)m * (nmax + 1) + n) * Q + k; };
+  sp.cnt.assign((size_t)(M + 1) * (nmax + 1) * Q, 0);
   sp.cnt[CI(M, 0, 0)] = 1;
   for (int m = M - 1; m >= 0; --m)
     for (int n = 0; n <= nmax; ++n)
-      for (int k = 0; k < M; ++k) {
+      for (int k = 0; k < Q; ++k) {
         uint64_t acc = 0;
         for (int v = 0; v <= n; ++v) {
-          acc += sp.cnt[CI(m + 1, n - v, modp((long long)k - (long long)m * v, M))];
+          acc += sp.cnt[CI(m + 1, n - v, modp((long long)k - (long long)m * v, Q))];
           if (acc >= (1ull << 62)) acc = (1ull << 62);
         }
         sp.cnt[CI(m, n, k)] = acc;
@@ -106,10 +111,12 @@ static int build_tables(Space& sp) {
 
   Tables& t = sp.t;
   t.M = M;
+  t.Q = Q;
+  t.exact = sp.exact;
   t.nmax = nmax;
   t.rem_w = nmax + 5;
   t.n_ann = M * (M + 1) / 2;
-  const int twoM = 2 * M;
+  const int twoQ = 2 * Q;
 
   // annihilation pairs (r <= s) and their creation partners (p <= q) in the same
   // momentum class, excluding the pair itself (those are diagonal)
@@ -120,7 +127,7 @@ static int build_tables(Space& sp) {
   std::vector<int> annR, annS, annStart;
   std::vector<uint32_t> pq;
   std::vector<double> G;
-  std::vector<std::vector<int8_t>> delta;  // [combo][16]
+  std::vector<std::vector<int>> delta;  // [combo][16]
   std::vector<double> gd;
   unsigned char pairidx[16][16];
   memset(pairidx, 0xff, sizeof(pairidx));
@@ -134,10 +141,10 @@ static int build_tables(Space& sp) {
       annStart.push_back((int)pq.size());
       double mrs = (r == s) ? 1.0 : 2.0;
       gd.push_back(mrs * mrs * LS(r, s, r, s).real());
-      int k = (r + s) % M;
+      int k = (r + s) % Q;
       for (int p = 0; p < M; ++p)
         for (int q = p; q < M; ++q) {
-          if ((p + q) % M != k || (p == r && q == s)) continue;
+          if ((p + q) % Q != k || (p == r && q == s)) continue;
           double mpq = (p == q) ? 1.0 : 2.0;
           // combos with a zero coupling are kept: for odd M every pair then has
           // (M-1)/2 partners, which the specialised stage kernels unroll
@@ -147,7 +154,7 @@ static int build_tables(Space& sp) {
           pq.push_back((uint32_t)p | ((uint32_t)q << 8) | ((uint32_t)lo << 16) | ((uint32_t)hi << 24));
           G.push_back(g.real());
           G.push_back(g.imag());
-          std::vector<int8_t> d(16, 0);
+          std::vector<int> d(16, 0);
           int dn[16] = {0};
           dn[r] -= 1;
           dn[s] -= 1;
@@ -159,7 +166,7 @@ static int build_tables(Space& sp) {
               dc += dn[e];
               dk += dn[e] * e;
             }
-            d[m] = (int8_t)(dc * twoM + modp(dk, M));
+            d[m] = dc * twoQ + modp(dk, Q);
           }
           delta.push_back(d);
         }
@@ -171,9 +178,9 @@ static int build_tables(Space& sp) {
   // shared-memory image
   size_t off = 0;
   t.o_cnt = (int)off;
-  off = align16(off + sizeof(uint32_t) * (size_t)(M + 1) * (nmax + 1) * M);
+  off = align16(off + sizeof(uint32_t) * (size_t)(M + 1) * (nmax + 1) * Q);
   t.o_E = (int)off;
-  off = align16(off + sizeof(int32_t) * (size_t)M * t.rem_w * twoM);
+  off = align16(off + sizeof(int32_t) * (size_t)M * t.rem_w * twoQ);
   t.o_sqrt = (int)off;
   off = align16(off + sizeof(double) * (size_t)(nmax + 3));
   t.o_pq = (int)off;
@@ -181,7 +188,7 @@ static int build_tables(Space& sp) {
   t.o_G = (int)off;
   off = align16(off + sizeof(double) * 2 * (size_t)std::max(1, t.n_combo));
   t.o_delta = (int)off;
-  off = align16(off + (size_t)16 * std::max(1, t.n_combo));
+  off = align16(off + (size_t)(sp.exact ? 32 : 16) * std::max(1, t.n_combo));
   t.o_ann = (int)off;
   off = align16(off + sizeof(int32_t) * (size_t)(t.n_ann + 1));
   t.o_pairidx = (int)off;
@@ -195,6 +202,9 @@ static int build_tables(Space& sp) {
   t.o_Gf = (int)off;
   off = align16(off + sizeof(float) * 4 * (size_t)std::max(1, t.n_combo));
   t.blob_bytes = (int)off;
+  // exact momentum: the fill counts and the ranking table grow with (M-1) n_max
+  // and stay in global memory for every kernel
+  t.sm_from = sp.exact ? t.o_sqrt : 0;
   sp.blob.assign(off, 0);
   unsigned char* b = sp.blob.data();
   uint32_t* cnt32 = (uint32_t*)(b + t.o_cnt);
@@ -202,19 +212,26 @@ static int build_tables(Space& sp) {
   int32_t* E = (int32_t*)(b + t.o_E);
   for (int m = 0; m < M; ++m)
     for (int rr = 0; rr < t.rem_w; ++rr)
-      for (int kk = 0; kk < twoM; ++kk) {
+      for (int kk = 0; kk < twoQ; ++kk) {
         int rem = rr - 2;
         int32_t v = 0;
-        if (m >= 1 && rem >= 1 && rem - 1 <= nmax) v = (int32_t)sp.cnt[CI(m - 1, rem - 1, modp(kk - (m - 1), M))];
-        E[((size_t)m * t.rem_w + rr) * twoM + kk] = v;
+        if (m >= 1 && rem >= 1 && rem - 1 <= nmax) v = (int32_t)sp.cnt[CI(m - 1, rem - 1, modp(kk - (m - 1), Q))];
+        E[((size_t)m * t.rem_w + rr) * twoQ + kk] = v;
       }
   double* sq = (double*)(b + t.o_sqrt);
   for (int k = 0; k < nmax + 3; ++k) sq[k] = std::sqrt((double)k);
   memcpy(b + t.o_pq, pq.data(), sizeof(uint32_t) * pq.size());
   memcpy(b + t.o_G, G.data(), sizeof(double) * G.size());
-  uint8_t* dl = (uint8_t*)(b + t.o_delta);
-  for (int j = 0; j < t.n_combo; ++j)
-    for (int m = 0; m < 16; ++m) dl[(size_t)j * 16 + m] = (uint8_t)(delta[j][m] + kDeltaBias);
+  if (sp.exact) {  // int16 shifts (|shift| <= 5Q)
+    if (5LL * Q > 32767) return fail(QB_EUNSUPPORTED, "exact momentum: (M-1) n_max too large for 16-bit shifts");
+    int16_t* dl = (int16_t*)(b + t.o_delta);
+    for (int j = 0; j < t.n_combo; ++j)
+      for (int m = 0; m < 16; ++m) dl[(size_t)j * 16 + m] = (int16_t)delta[j][m];
+  } else {
+    uint8_t* dl = (uint8_t*)(b + t.o_delta);
+    for (int j = 0; j < t.n_combo; ++j)
+      for (int m = 0; m < 16; ++m) dl[(size_t)j * 16 + m] = (uint8_t)(delta[j][m] + kDeltaBias);
+  }
   memcpy(b + t.o_ann, annStart.data(), sizeof(int32_t) * annStart.size());
   memcpy(b + t.o_pairidx, pairidx, 256);
   memcpy(b + t.o_w, sp.w.data(), sizeof(double) * M);
@@ -247,17 +264,18 @@ static int64_t host_rank(const Space& sp, const int* occ) {
     K += (long long)i * occ[i];
   }
   if (N > sp.nmax || N < 0) return -1;
-  int Kk = modp(K, M);
-  int sid = sp.secOf[(size_t)N * M + Kk];
+  const int Q = sp.Q;
+  int Kk = modp(K, Q);
+  int sid = sp.secOf[(size_t)N * Q + Kk];
   if (sid < 0) return -1;
-  auto CI = [&](int m, int n, int k) { return ((size_t)m * (sp.nmax + 1) + n) * M + k; };
+  auto CI = [&](int m, int n, int k) { return ((size_t)m * (sp.nmax + 1) + n) * Q + k; };
   int64_t sum = 0;
   int rem = 0;
   long long kr = 0;
   for (int m = M - 1; m >= 1; --m) {
     rem += occ[m];
     kr += (long long)m * occ[m];
-    if (rem >= 1) sum += (int64_t)sp.cnt[CI(m - 1, rem - 1, modp(kr - (m - 1), M))];
+    if (rem >= 1) sum += (int64_t)sp.cnt[CI(m - 1, rem - 1, modp(kr - (m - 1), Q))];
   }
   return sp.secOff[sid] + sp.secDim[sid] - 1 - sum;
 }
@@ -426,6 +444,10 @@ int qb_sector_build(const qb_model* model, int n_min, int n_max, const int* p_li
   }
   sp->nmin = n_min;
   sp->nmax = n_max;
+  sp->exact = model->exact_momentum ? 1 : 0;
+  // exact: a modulus above every momentum sum (and above 2(M-1), so that pair
+  // momenta never wrap either)
+  sp->Q = sp->exact ? std::max((M - 1) * n_max + 1, 2 * M - 1) : M;
   rc = build_tables(*sp);
   if (rc) {
     delete sp;
@@ -437,21 +459,29 @@ int qb_sector_build(const qb_model* model, int n_min, int n_max, const int* p_li
       delete sp;
       return fail(QB_EINVAL, "n_p must be >= 0");
     }
-    for (int i = 0; i < n_p; ++i) Ps.push_back(modp(p_list[i], M));
+    for (int i = 0; i < n_p; ++i) Ps.push_back(sp->exact ? p_list[i] : modp(p_list[i], M));
     std::sort(Ps.begin(), Ps.end());
     Ps.erase(std::unique(Ps.begin(), Ps.end()), Ps.end());
+  } else if (sp->exact) {
+    // every label sum reachable with N <= n_max: sum_i (i - c) n_i in [-c n_max, (M-1-c) n_max]
+    const int c0 = label_shift(M);
+    for (int P = -c0 * n_max; P <= (M - 1 - c0) * n_max; ++P) Ps.push_back(P);
   } else {
     for (int P = 0; P < M; ++P) Ps.push_back(P);
   }
   const int c = label_shift(M);
-  sp->secOf.assign((size_t)(n_max + 1) * M, -1);
+  const int Q = sp->Q;
+  sp->secOf.assign((size_t)(n_max + 1) * Q, -1);
   sp->secOff.push_back(0);
   for (int N = n_min; N <= n_max; ++N)
     for (int P : Ps) {
-      int K = modp((long long)P + (long long)c * N, M);
-      uint64_t D = sp->cnt[((size_t)0 * (n_max + 1) + N) * M + K];
+      // index momentum K = sum_i i n_i = P + c N; exact: must lie in [0, (M-1) N]
+      const long long Kx = (long long)P + (long long)c * N;
+      if (sp->exact && (Kx < 0 || Kx > (long long)(M - 1) * N)) continue;
+      int K = modp(Kx, Q);
+      uint64_t D = sp->cnt[((size_t)0 * (n_max + 1) + N) * Q + K];
       if (D == 0) continue;
-      sp->secOf[(size_t)N * M + K] = (int)sp->secN.size();
+      sp->secOf[(size_t)N * Q + K] = (int)sp->secN.size();
       sp->secN.push_back(N);
       sp->secP.push_back(P);
       sp->secK.push_back(K);

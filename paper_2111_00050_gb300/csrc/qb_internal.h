@@ -29,6 +29,9 @@ constexpr int kDeltaBias = 64;
 //   idx(m, rem, krem) = (m * rem_w + rem + 2) * 2M + krem.
 struct Tables {
   int M;
+  int Q;         // momentum modulus of the tables: M (mod-M conservation) or (M-1) nmax + 1 (exact)
+  int exact;     // 1: momentum conserved exactly (Q exceeds every momentum sum)
+  int sm_from;   // first byte of the image the row kernels stage in shared memory (cnt, E stay global below it)
   int nmax;      // largest N of the space
   int rem_w;     // nmax + 5
   int n_ann;     // M(M+1)/2 unordered annihilation pairs (r <= s)
@@ -36,12 +39,13 @@ struct Tables {
   int is_complex;
   int blob_bytes;  // size of the shared-memory image
   // byte offsets of the sub-tables inside the image
-  int o_cnt;     // uint32 [(M+1)][nmax+1][M]
-  int o_E;       // int32  [M][rem_w][2M]
+  int o_cnt;     // uint32 [(M+1)][nmax+1][Q]
+  int o_E;       // int32  [M][rem_w][2Q]
   int o_sqrt;    // double [nmax+3]            sqrt(k)
   int o_pq;      // uint32 [n_combo]           p | q<<8 | lo<<16 | hi<<24
   int o_G;       // double [n_combo][2]        conj(mult * L^sym_{pq;rs}) (re, im)
   int o_delta;   // uint8  [n_combo][16]       kDeltaBias + flat-index shift of the suffix state at mode m
+                 //   (exact: int16 [n_combo][16], the shift itself)
   int o_ann;     // int32  [n_ann + 1]         first combo of annihilation pair a
   int o_pairidx; // uint8  [16][16]            pair index of (r <= s)
   int o_w;       // double [M]                 one-body w_p
@@ -54,7 +58,7 @@ struct Tables {
   const int64_t* sec_off;  // [n_sectors + 1]
   const int32_t* sec_N;    // [n_sectors]
   const int32_t* sec_K;    // [n_sectors] index momentum
-  const int32_t* sec_of;   // [(nmax + 1) * M] sector id of (N, K) or -1
+  const int32_t* sec_of;   // [(nmax + 1) * Q] sector id of (N, K) or -1
   int64_t total;
   // ket weights w(n) = sqrt(N! / prod_m n_m!) = prod_m sqrt(C(rem_m, n_m)), rem_m the
   // particles in modes m..M-1: entry [rem * (nmax + 1) + k] = (sqrt(C(rem, k)), its inverse)
@@ -63,13 +67,15 @@ struct Tables {
 
 struct Space {
   int M = 0;
+  int Q = 0;       // momentum modulus (Tables::Q)
+  int exact = 0;   // momentum conserved exactly
   int nmax = 0, nmin = 0;
   std::vector<double> w;                  // [M]
   std::vector<double> Lsym;               // [M^4][2]
   std::vector<int> secN, secP, secK;      // per sector
   std::vector<int64_t> secDim, secOff;    // secOff has n_sectors + 1 entries
   std::vector<uint64_t> cnt;              // host copy of the fill counts
-  std::vector<int> secOf;                 // [(nmax+1) * M]
+  std::vector<int> secOf;                 // [(nmax+1) * Q]
   std::vector<unsigned char> blob;        // host copy of the shared-memory image
   int64_t maxDim = 0;
   // device allocations owned by the space

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kBlock) hpsi_kernel(const Tables t, const Stag
   extern __shared__ __align__(16) unsigned char smem[];
   load_blob(t, smem);
   const View v = make_view(t, smem);
-  const RowScratch rs = row_scratch(smem + ((t.blob_bytes + 15) & ~15));
+  const RowScratch rs = row_scratch(smem + blob_smem(t));
   const int tid = threadIdx.x;
   const int M = t.M;
   const int64_t total = t.total;
@@ -101,8 +101,7 @@ __global__ void __launch_bounds__(kBlock) hpsi_kernel(const Tables t, const Stag
         const int np_ = occ[p * kBlock], nq = occ[q * kBlock];
         const double Bf = v.sq[np_ + 1] * v.sq[nq + 1 + (p == q ? 1 : 0)];
         int64_t rk = rank_base + pe[hi * kBlock] - pe[lo * kBlock];
-        const uint8_t* dj = reinterpret_cast<const uint8_t*>(v.delta) + j * 16;
-        for (int m = lo + 1; m <= hi; ++m) rk -= v.E[idx[m * kBlock] + (int)dj[m] - kDeltaBias];
+        for (int m = lo + 1; m <= hi; ++m) rk -= v.E[idx[m * kBlock] + delta_shift(t, v, j, m)];
         if (rk < 0 || rk >= D) {
           atomicOr(a.status, 1);
           rk = 0;
@@ -186,7 +185,7 @@ __global__ void __launch_bounds__(kBlock) to_dfw_kernel(const Tables t, const do
   extern __shared__ __align__(16) unsigned char smem[];
   load_blob(t, smem);
   const View v = make_view(t, smem);
-  const RowScratch rs = row_scratch(smem + ((t.blob_bytes + 15) & ~15));
+  const RowScratch rs = row_scratch(smem + blob_smem(t));
   const int tid = threadIdx.x;
   for (int64_t base = (int64_t)blockIdx.x * kBlock; base < t.total; base += (int64_t)gridDim.x * kBlock) {
     const int64_t g = base + tid;
@@ -208,7 +207,7 @@ __global__ void __launch_bounds__(kBlock) diag_kernel(const Tables t, float4* di
   extern __shared__ __align__(16) unsigned char smem[];
   load_blob(t, smem);
   const View v = make_view(t, smem);
-  const RowScratch rs = row_scratch(smem + ((t.blob_bytes + 15) & ~15));
+  const RowScratch rs = row_scratch(smem + blob_smem(t));
   const int tid = threadIdx.x, M = t.M;
   for (int64_t base = (int64_t)blockIdx.x * kBlock; base < t.total; base += (int64_t)gridDim.x * kBlock) {
     const int64_t g = base + tid;
@@ -238,7 +237,7 @@ __global__ void __launch_bounds__(kBlock) unrank_kernel(const Tables t, int64_t 
   extern __shared__ __align__(16) unsigned char smem[];
   load_blob(t, smem);
   const View v = make_view(t, smem);
-  const RowScratch rs = row_scratch(smem + ((t.blob_bytes + 15) & ~15));
+  const RowScratch rs = row_scratch(smem + blob_smem(t));
   const int tid = threadIdx.x;
   for (int64_t base = (int64_t)blockIdx.x * kBlock; base < count; base += (int64_t)gridDim.x * kBlock) {
     const int64_t k = base + tid;
@@ -266,11 +265,11 @@ __global__ void __launch_bounds__(kBlock) rank_kernel(const Tables t, const int*
       int nm = occ_in[k * M + m];
       if (nm < 0 || nm > t.nmax) ok = false;
       N += nm;
-      K = (K + m * (nm < 0 ? 0 : nm)) % M;
+      K = (K + m * (nm < 0 ? 0 : nm)) % t.Q;
     }
     int64_t res = -1;
     if (ok && N <= t.nmax) {
-      int sid = __ldg(t.sec_of + N * M + K);
+      int sid = __ldg(t.sec_of + N * t.Q + K);
       if (sid >= 0) {
         const int64_t off = __ldg(t.sec_off + sid), D = __ldg(t.sec_off + sid + 1) - off;
         int64_t sum = 0;
@@ -278,8 +277,9 @@ __global__ void __launch_bounds__(kBlock) rank_kernel(const Tables t, const int*
         for (int m = M - 1; m >= 1; --m) {
           int nm = occ_in[k * M + m];
           rem += nm;
-          kr = (kr + m * nm) % M;
-          if (rem >= 1) sum += v.cnt[((size_t)(m - 1) * V + rem - 1) * M + (((kr - (m - 1)) % M) + M) % M];
+          kr = (kr + m * nm) % t.Q;
+          if (rem >= 1)
+            sum += v.cnt[((size_t)(m - 1) * V + rem - 1) * t.Q + (((kr - (m - 1)) % t.Q) + t.Q) % t.Q];
         }
         res = off + D - 1 - sum;
       }
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(kBlock) terms_kernel(const Tables t, unsigned 
   extern __shared__ __align__(16) unsigned char smem[];
   load_blob(t, smem);
   const View v = make_view(t, smem);
-  const RowScratch rs = row_scratch(smem + ((t.blob_bytes + 15) & ~15));
+  const RowScratch rs = row_scratch(smem + blob_smem(t));
   const int tid = threadIdx.x, M = t.M;
   unsigned long long terms = 0, tuples = 0;
   for (int64_t base = (int64_t)blockIdx.x * kBlock; base < t.total; base += (int64_t)gridDim.x * kBlock) {
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(kBlock) init_table_kernel(const Tables t, cons
   extern __shared__ __align__(16) unsigned char smem[];
   load_blob(t, smem);
   const View v = make_view(t, smem);
-  const RowScratch rs = row_scratch(smem + ((t.blob_bytes + 15) & ~15));
+  const RowScratch rs = row_scratch(smem + blob_smem(t));
   const int tid = threadIdx.x, M = t.M, V = t.nmax + 1;
   double n2 = 0.0;
   for (int64_t base = (int64_t)blockIdx.x * kBlock; base < t.total; base += (int64_t)gridDim.x * kBlock) {
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(kBlock) moments_kernel(const Tables t, const d
   extern __shared__ __align__(16) unsigned char smem[];
   load_blob(t, smem);
   const View v = make_view(t, smem);
-  const size_t blob_al = (t.blob_bytes + 15) & ~15;
+  const size_t blob_al = blob_smem(t);
   const RowScratch rs = row_scratch(smem + blob_al);
   double* acc = reinterpret_cast<double*>(smem + blob_al + ((kRowScratchBytes + 15) & ~15));  // [warps][nmom]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, M = t.M;
@@ -472,8 +472,8 @@ __global__ void __launch_bounds__(kBlock) moments_kernel(const Tables t, const d
       int64_t tg = 0;
       double c = 0.0;
       if (live && occ[i * kBlock] >= 1 && N >= 1) {
-        const int Kt = ((K - i) % M + M) % M;
-        const int sid = __ldg(t.sec_of + (N - 1) * M + Kt);
+        const int Kt = ((K - i) % t.Q + t.Q) % t.Q;
+        const int sid = __ldg(t.sec_of + (N - 1) * t.Q + Kt);
         if (sid >= 0) {
           const int64_t off = __ldg(t.sec_off + sid), D = __ldg(t.sec_off + sid + 1) - off;
           int e[1] = {i}, dn[1] = {-1};
@@ -496,8 +496,8 @@ __global__ void __launch_bounds__(kBlock) moments_kernel(const Tables t, const d
             c = (double)occ[i * kBlock];
             has = true;
           } else {
-            const int Kt = ((K - j + i) % M + M) % M;
-            const int sid = __ldg(t.sec_of + N * M + Kt);
+            const int Kt = ((K - j + i) % t.Q + t.Q) % t.Q;
+            const int sid = __ldg(t.sec_of + N * t.Q + Kt);
             if (sid >= 0) {
               const int64_t off = __ldg(t.sec_off + sid), D = __ldg(t.sec_off + sid + 1) - off;
               int e[2] = {j, i}, dn[2] = {-1, 1};
@@ -519,8 +519,8 @@ __global__ void __launch_bounds__(kBlock) moments_kernel(const Tables t, const d
           const int ni = occ[i * kBlock], nj = occ[j * kBlock];
           const bool ok = (i == j) ? (ni >= 2) : (ni >= 1 && nj >= 1);
           if (ok) {
-            const int Kt = ((K - i - j) % M + M) % M;
-            const int sid = __ldg(t.sec_of + (N - 2) * M + Kt);
+            const int Kt = ((K - i - j) % t.Q + t.Q) % t.Q;
+            const int sid = __ldg(t.sec_of + (N - 2) * t.Q + Kt);
             if (sid >= 0) {
               const int64_t off = __ldg(t.sec_off + sid), D = __ldg(t.sec_off + sid + 1) - off;
               int e[2] = {i, j}, dn[2] = {(i == j) ? -2 : -1, -1};
@@ -554,7 +554,7 @@ __global__ void __launch_bounds__(kBlock) moments_kernel(const Tables t, const d
 // double-float accumulator of that value.  The sector offsets and the (N, K) ->
 // sector map are staged in shared memory when they are small.
 
-// x mod M for x in (-2M, 3M), by conditional adds (no integer division)
+// x mod Q for x in (-2Q, 3Q), by conditional adds (no integer division)
 __device__ __forceinline__ int mod_small(int x, int M) {
   if (x < 0) x += M;
   if (x < 0) x += M;
@@ -566,24 +566,24 @@ __device__ __forceinline__ int mod_small(int x, int M) {
 // rank of the ket reached by changing mode e0 by dn0 and (nch = 2) mode e1 by dn1
 __device__ __forceinline__ int64_t rank_moved(const Tables& t, const View& v, const RowScratch& rs, int nch, int e0,
                                               int dn0, int e1, int dn1, int64_t Dt) {
-  const int M = t.M, tid = threadIdx.x, twoM = 2 * M;
+  const int M = t.M, Q = t.Q, tid = threadIdx.x, twoQ = 2 * Q;
   if (nch < 2) {
     e1 = 0;
     dn1 = 0;
   }
   const int top = max(e0, e1);
   int64_t sum = rs.pe[(M - 1) * kBlock + tid] - rs.pe[top * kBlock + tid];
-  int dc = 0, dkm = 0;  // dkm = (momentum change) mod M, kept in [0, M) without a division
+  int dc = 0, dkm = 0;  // dkm = (momentum change) mod Q, kept in [0, Q) without a division
   for (int m = top; m >= 1; --m) {
     if (m == e0) {
       dc += dn0;
-      dkm = mod_small(dkm + dn0 * m, M);
+      dkm = mod_small(dkm + dn0 * m, Q);
     }
     if (m == e1) {
       dc += dn1;
-      dkm = mod_small(dkm + dn1 * m, M);
+      dkm = mod_small(dkm + dn1 * m, Q);
     }
-    sum += v.E[rs.idx[m * kBlock + tid] + dc * twoM + dkm];
+    sum += v.E[rs.idx[m * kBlock + tid] + dc * twoQ + dkm];
   }
   return Dt - 1 - sum;
 }
@@ -644,7 +644,7 @@ constexpr size_t kMomSecSmemMax = 16384;  // sector tables larger than this stay
 
 static size_t mom_sec_bytes(const Tables& t) {
   return ((sizeof(int64_t) * (size_t)(t.n_sectors + 1) + 15) & ~(size_t)15) +
-         ((sizeof(int32_t) * (size_t)(t.nmax + 1) * t.M + 15) & ~(size_t)15);
+         ((sizeof(int32_t) * (size_t)(t.nmax + 1) * t.Q + 15) & ~(size_t)15);
 }
 
 __device__ __forceinline__ int find_sector_in(const int64_t* off, int n, int64_t g) {
@@ -659,15 +659,21 @@ __device__ __forceinline__ int find_sector_in(const int64_t* off, int n, int64_t
   return lo;
 }
 
+// first byte of the image the double-float moments kernel stages in shared memory
+__host__ __device__ inline int moments_from(const Tables& t, bool exact) { return exact ? t.o_sqrt : t.o_E; }
+
+template <bool EXACT>
 __global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, const float4* psif, double* partial,
                                                              int nmom, int sec_smem, int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  load_blob_from(t, smem_raw, t.o_E);
-  unsigned char* smem = smem_raw - t.o_E;
-  View v = make_view(t, smem);
+  const int from = moments_from(t, EXACT);
+  load_blob_from(t, smem_raw, from);
+  unsigned char* smem = smem_raw - from;
+  View v = view_at(t, smem);
   v.cnt = reinterpret_cast<const uint32_t*>(t.blob + t.o_cnt);  // fill counts stay in global memory
+  if (EXACT) v.E = reinterpret_cast<const int32_t*>(t.blob + t.o_E);  // and the (large) ranking table
   const float2* sqf = reinterpret_cast<const float2*>(smem + t.o_sqf);
-  unsigned char* cur = smem_raw + ((t.blob_bytes - t.o_E + 15) & ~15);
+  unsigned char* cur = smem_raw + ((t.blob_bytes - from + 15) & ~15);
   const RowScratch rs = row_scratch(cur);
   cur += (kRowScratchBytes + 15) & ~15;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, M = t.M;
@@ -678,8 +684,8 @@ __global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, cons
     for (int k = tid; k <= t.n_sectors; k += kBlock) o[k] = __ldg(t.sec_off + k);
     cur += (sizeof(int64_t) * (size_t)(t.n_sectors + 1) + 15) & ~(size_t)15;
     int32_t* f = reinterpret_cast<int32_t*>(cur);
-    for (int k = tid; k < (t.nmax + 1) * M; k += kBlock) f[k] = __ldg(t.sec_of + k);
-    cur += (sizeof(int32_t) * (size_t)(t.nmax + 1) * M + 15) & ~(size_t)15;
+    for (int k = tid; k < (t.nmax + 1) * t.Q; k += kBlock) f[k] = __ldg(t.sec_of + k);
+    cur += (sizeof(int32_t) * (size_t)(t.nmax + 1) * t.Q + 15) & ~(size_t)15;
     soff = o;
     sof = f;
   }
@@ -767,7 +773,7 @@ __global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, cons
       int64_t tg = 0;
       dfl c = zero;
       if (live && occ[i * kBlock] >= 1) {
-        const int sid = sof[(N - 1) * M + mod_small(K - i, M)];
+        const int sid = sof[(N - 1) * t.Q + mod_small(K - i, t.Q)];
         if (sid >= 0) {
           const int64_t off = soff[sid], D = soff[sid + 1] - off;
           tg = off + rank_moved(t, v, rs, 1, i, -1, 0, 0, D);
@@ -786,7 +792,7 @@ __global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, cons
         int64_t tg = 0;
         dfl c = zero;
         if (live && occ[j * kBlock] >= 1) {
-          const int sid = sof[N * M + mod_small(K - j + i, M)];
+          const int sid = sof[N * t.Q + mod_small(K - j + i, t.Q)];
           if (sid >= 0) {
             const int64_t off = soff[sid], D = soff[sid + 1] - off;
             tg = off + rank_moved(t, v, rs, 2, j, -1, i, 1, D);
@@ -806,7 +812,7 @@ __global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, cons
           const int ni = occ[i * kBlock], nj = occ[j * kBlock];
           const bool ok = (i == j) ? (ni >= 2) : (ni >= 1 && nj >= 1);
           if (ok) {
-            const int sid = sof[(N - 2) * M + mod_small(K - i - j, M)];
+            const int sid = sof[(N - 2) * t.Q + mod_small(K - i - j, t.Q)];
             if (sid >= 0) {
               const int64_t off = soff[sid], D = soff[sid + 1] - off;
               tg = off + ((i == j) ? rank_moved(t, v, rs, 1, i, -2, 0, 0, D)
@@ -843,7 +849,7 @@ __global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, cons
 
 // ------------------------------------------------------------------ host side
 
-static size_t row_smem(const Tables& t) { return ((t.blob_bytes + 15) & ~15) + kRowScratchBytes; }
+static size_t row_smem(const Tables& t) { return blob_smem(t) + kRowScratchBytes; }
 
 static int nmoments(int M) { return 4 + 2 * M + 4 * M * M; }
 
@@ -1172,7 +1178,7 @@ int launch_unrank(const Space& s, int64_t first, int64_t count, int* d_occ, void
 
 int launch_rank(const Space& s, const int* d_occ, int64_t count, int64_t* d_index, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t smem = (s.t.blob_bytes + 15) & ~15;
+  const size_t smem = blob_smem(s.t);
   int grid = 0;
   int rc = persistent_grid(rank_kernel, smem, count, &grid);
   if (rc) return rc;
@@ -1280,15 +1286,17 @@ int launch_moments(Space& s, const void* d_psi, double* out_host, void* stream) 
   if (rc) return rc;
   const size_t tr_bytes = (size_t)(kBlock / 32) * kTrRows * kTrStride * sizeof(float2);
   const int sec_smem = mom_sec_bytes(s.t) <= kMomSecSmemMax ? 1 : 0;
-  const size_t smem = ((size_t)(s.t.blob_bytes - s.t.o_E + 15) & ~(size_t)15) + ((kRowScratchBytes + 15) & ~15) +
+  const bool ex = s.t.exact != 0;
+  const size_t smem = ((size_t)(s.t.blob_bytes - moments_from(s.t, ex) + 15) & ~(size_t)15) +
+                      ((kRowScratchBytes + 15) & ~15) +
                       (sec_smem ? mom_sec_bytes(s.t) : 0) + tr_bytes +
                       (size_t)(kBlock / 32) * ((moment_values(s.M) + 31) & ~31) * sizeof(float2);
   int grid = 0;
-  rc = persistent_grid(moments_df_kernel, smem, s.t.total, &grid);
+  auto kern = ex ? moments_df_kernel<true> : moments_df_kernel<false>;
+  rc = persistent_grid(kern, smem, s.t.total, &grid);
   if (rc) return rc;
   double* part = partial_area(s);
-  moments_df_kernel<<<grid, kBlock, smem, st>>>(s.t, s.d_obsf, part, nmom, sec_smem,
-                                                 reinterpret_cast<int*>(s.d_scratch));
+  kern<<<grid, kBlock, smem, st>>>(s.t, s.d_obsf, part, nmom, sec_smem, reinterpret_cast<int*>(s.d_scratch));
   QB_CUDA(cudaGetLastError());
   double* fin = final_area(s);
   reduce_partials_kernel<<<(nmom + 127) / 128, 128, 0, st>>>(part, grid, nmom, fin);

@@ -50,7 +50,10 @@ constexpr int kStageBlock = 32 * kStageWarps;
 constexpr int kStageMinBlocks = QB_STAGE_MIN_BLOCKS;  // resident CTAs per SM the register budget is planned for
 
 // first byte of the table image the stage kernels stage in shared memory
-__host__ __device__ inline int kSmemFrom(const Tables& t) { return QB_CNT_GLOBAL ? t.o_E : 0; }
+// (exact momentum: the ranking table too stays in global memory)
+__host__ __device__ inline int kSmemFrom(const Tables& t, bool exact = false) {
+  return exact ? t.o_sqrt : (QB_CNT_GLOBAL ? t.o_E : 0);
+}
 
 // Gathered stage-vector entry: read-only global load, or a generic load when the
 // vector is a shared-memory copy (LOCAL; the non-coherent global path does not
@@ -74,14 +77,19 @@ __device__ __forceinline__ float4 gather(const float4* p) {
 // creation-side square roots and no lookup of n_p, n_q.  Modes 1 and 3 map back:
 // psi += w (z W^-1 H W f + sum of basef) in FP64, and write f = psi_new / w; the
 // bilinears multiply each factor by w.
-template <int MT, int B, bool CPLX, bool BIL, bool LOCAL, bool SIM>
+//
+// EXACT: momentum conserved exactly (the generic kernel, MT = 0): momentum
+// arithmetic modulo t.Q > every momentum sum, shifts stored as int16, the
+// ranking table in global memory.
+template <int MT, int B, bool CPLX, bool BIL, bool LOCAL, bool SIM, bool EXACT>
 __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const float2* sqf, const float4* Gf,
                                            const uint4* dl4, const DfArgs& a, const int mode, const int64_t base,
                                            const int64_t row1, const int64_t local_off, int32_t* sidx, uint8_t* socc,
                                            int32_t* sD, int64_t* sOff, uint8_t* sperm, int32_t* hist,
                                            int32_t* cursor, dfl& bil_l, dfl* bil_w) {
   const int M = (MT > 0) ? MT : t.M;
-  const int twoM = 2 * M;
+  const int Qm = EXACT ? t.Q : M;  // momentum modulus
+  const int twoM = 2 * Qm;         // row width of the ranking table
   const int lane = threadIdx.x & 31;
   const int64_t total = t.total;  // stride between sweep members
   const int nb = t.n_ann + 2;
@@ -107,7 +115,9 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
         // the last step cnt[M-1][n][k] = [n + k = 0 mod M] (one mode left)
         const int32_t* erow = v.E + (min(m + 2, M - 1) * t.rem_w + 3) * twoM + m + 1;  // used for m + 2 < M
         while (true) {
-          const int c = (m + 2 < M) ? erow[(rem - val) * twoM + kk] : (((rem - val + kk) % M) == 0 ? 1 : 0);
+          const int c = (m + 2 < M)  ? erow[(rem - val) * twoM + kk]
+                        : EXACT      ? ((M - 1) * (rem - val) == kk ? 1 : 0)
+                                     : (((rem - val + kk) % M) == 0 ? 1 : 0);
 #else
         const uint32_t* crow = gcnt + (size_t)(m + 1) * V * M;
         while (true) {
@@ -117,7 +127,7 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
           left -= c;
           ++val;
           kk -= m;
-          if (kk < 0) kk += M;
+          if (kk < 0) kk += Qm;
         }
         socc[m * kWarpRows + row] = (uint8_t)val;
         rem -= val;
@@ -129,10 +139,10 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
         const int nm = socc[m * kWarpRows + row];
         srem += nm;
         skr += m * nm;
-        while (skr >= M) skr -= M;
+        while (skr >= Qm) skr -= Qm;
         const int ix = (m * t.rem_w + srem + 2) * twoM + skr;
         esum += v.E[ix];
-        sidx[m * kWarpRows + row] = ix - kDeltaBias;
+        sidx[m * kWarpRows + row] = ix - (EXACT ? 0 : kDeltaBias);
       }
       if (D - 1 - esum != (int)(g - off)) atomicOr(a.status, 2);
       for (int m = 0; m < M; ++m) {
@@ -284,13 +294,24 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
             AB = df_mul(A, df_mul(dfl{bp.x, bp.y}, dfl{bq.x, bq.y}));
           }
           // rank of the target: D - 1 - sum over every mode of E at the shifted suffix state
-          const uint4 dd = dl4[j];
           int esum = 0;
+          if (EXACT) {  // int16 shifts, two modes per word
+            const uint4 d0 = dl4[2 * j], d1 = dl4[2 * j + 1];
   #pragma unroll
-          for (int m = 1; m < 16; ++m) {
-            if (m >= M) break;
-            const uint32_t word = (m < 4) ? dd.x : (m < 8) ? dd.y : (m < 12) ? dd.z : dd.w;
-            esum += v.E[id[m] + (int)((word >> (8 * (m & 3))) & 0xffu)];
+            for (int m = 1; m < 16; ++m) {
+              if (m >= M) break;
+              const uint32_t word = (m < 2) ? d0.x : (m < 4) ? d0.y : (m < 6) ? d0.z : (m < 8) ? d0.w
+                                  : (m < 10) ? d1.x : (m < 12) ? d1.y : (m < 14) ? d1.z : d1.w;
+              esum += v.E[id[m] + (int)(int16_t)(word >> (16 * (m & 1)))];
+            }
+          } else {
+            const uint4 dd = dl4[j];
+  #pragma unroll
+            for (int m = 1; m < 16; ++m) {
+              if (m >= M) break;
+              const uint32_t word = (m < 4) ? dd.x : (m < 8) ? dd.y : (m < 12) ? dd.z : dd.w;
+              esum += v.E[id[m] + (int)((word >> (8 * (m & 3))) & 0xffu)];
+            }
           }
           int rk = D - 1 - esum;
           if ((unsigned)rk >= (unsigned)D) {
@@ -420,17 +441,20 @@ struct StageSmem {
 };
 
 // Stages the table image (a CTA-wide barrier) and lays out the warp scratch.
+template <bool EXACT>
 __device__ __forceinline__ StageSmem stage_smem(const Tables& t, unsigned char* smem_raw, int M, int warps) {
   StageSmem S;
-  load_blob_from(t, smem_raw, kSmemFrom(t));
-  unsigned char* smem = smem_raw - kSmemFrom(t);
-  S.v = make_view(t, smem);
+  const int from = kSmemFrom(t, EXACT);
+  load_blob_from(t, smem_raw, from);
+  unsigned char* smem = smem_raw - from;
+  S.v = view_at(t, smem);
+  if (EXACT) S.v.E = reinterpret_cast<const int32_t*>(t.blob + t.o_E);
   S.sqf = reinterpret_cast<const float2*>(smem + t.o_sqf);
   S.Gf = reinterpret_cast<const float4*>(smem + t.o_Gf);
   S.dl4 = reinterpret_cast<const uint4*>(S.v.delta);
   const int warp = threadIdx.x >> 5;
   const size_t wbytes = df_warp_scratch_bytes(M, t.n_ann);
-  unsigned char* base = smem_raw + ((t.blob_bytes - kSmemFrom(t) + 15) & ~15);
+  unsigned char* base = smem_raw + ((t.blob_bytes - from + 15) & ~15);
   unsigned char* sp = base + (size_t)warp * wbytes;
   S.sidx = reinterpret_cast<int32_t*>(sp);
   S.socc = reinterpret_cast<uint8_t*>(S.sidx + M * kWarpRows);
@@ -443,12 +467,12 @@ __device__ __forceinline__ StageSmem stage_smem(const Tables& t, unsigned char* 
   return S;
 }
 
-template <int MT, int B, bool CPLX, bool BIL, bool SIM>
+template <int MT, int B, bool CPLX, bool BIL, bool SIM, bool EXACT>
 __global__ void __launch_bounds__(kStageBlock, kStageMinBlocks) stage_df_kernel(const Tables t, const DfArgs a, const int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int M = (MT > 0) ? MT : t.M;
   // the only CTA-wide barrier: warps run independently afterwards
-  const StageSmem S = stage_smem(t, smem_raw, M, kStageWarps);
+  const StageSmem S = stage_smem<EXACT>(t, smem_raw, M, kStageWarps);
   constexpr int kWarps = kStageWarps;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t row1 = a.row1;
@@ -460,7 +484,7 @@ __global__ void __launch_bounds__(kStageBlock, kStageMinBlocks) stage_df_kernel(
 
   for (int64_t base = a.row0 + ((int64_t)blockIdx.x * kWarps + warp) * kWarpRows; base < row1;
        base += (int64_t)gridDim.x * kWarps * kWarpRows)
-    stage_tile<MT, B, CPLX, BIL, false, SIM>(t, S.v, S.sqf, S.Gf, S.dl4, a, mode, base, row1, 0, S.sidx, S.socc,
+    stage_tile<MT, B, CPLX, BIL, false, SIM, EXACT>(t, S.v, S.sqf, S.Gf, S.dl4, a, mode, base, row1, 0, S.sidx, S.socc,
                                              S.sD, S.sOff, S.sperm, S.hist, S.cursor, bil_l, bil_w);
   if (BIL) {
     // per-CTA sums of the bilinears in a fixed order: lanes by shuffles, warps in turn
@@ -502,11 +526,11 @@ struct ResArgs {
   int* status;
 };
 
-template <int MT, bool CPLX>
+template <int MT, bool CPLX, bool EXACT>
 __global__ void __launch_bounds__(kBlock) resident_kernel(const Tables t, const ResArgs r) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int M = (MT > 0) ? MT : t.M;
-  const StageSmem S = stage_smem(t, smem_raw, M, kBlock / 32);
+  const StageSmem S = stage_smem<EXACT>(t, smem_raw, M, kBlock / 32);
   double2* spsi = reinterpret_cast<double2*>(S.after);
   float4* spsif = reinterpret_cast<float4*>(spsi + r.cap);
   float4* sw1 = spsif + r.cap;
@@ -545,7 +569,7 @@ __global__ void __launch_bounds__(kBlock) resident_kernel(const Tables t, const 
         // evenly, so that a small sector still keeps every warp busy
         const int64_t chunk = min((int64_t)kWarpRows, ((int64_t)D + kWarps - 1) / kWarps);
         for (int64_t base = off + (int64_t)warp * chunk; base < off + D; base += (int64_t)kWarps * chunk)
-          stage_tile<MT, 1, CPLX, false, true, true>(t, S.v, S.sqf, S.Gf, S.dl4, a, d == 1 ? 1 : 0, base,
+          stage_tile<MT, 1, CPLX, false, true, true, EXACT>(t, S.v, S.sqf, S.Gf, S.dl4, a, d == 1 ? 1 : 0, base,
                                                min(base + chunk, off + (int64_t)D), off, S.sidx, S.socc, S.sD,
                                                S.sOff, S.sperm, S.hist, S.cursor, bil_l, bil_w);
         __syncthreads();
@@ -561,20 +585,21 @@ __global__ void __launch_bounds__(kBlock) resident_kernel(const Tables t, const 
 
 // Shared memory of the resident kernel holding `cap` kets per sector.
 inline size_t resident_smem(const Tables& t, int cap) {
-  return ((t.blob_bytes - kSmemFrom(t) + 15) & ~15) + df_scratch_bytes(t.M, t.n_ann) + (size_t)cap * 64;
+  return ((t.blob_bytes - kSmemFrom(t, t.exact != 0) + 15) & ~15) + df_scratch_bytes(t.M, t.n_ann) +
+         (size_t)cap * 64;
 }
 
-template <int MT>
-int resident_launch_t(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t st) {
+template <int MT, bool EXACT>
+int resident_launch_e(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t st) {
   const size_t smem = resident_smem(t, r.cap);
   int grid = 0, rc = QB_OK;
   if (cplx) {
-    auto k = resident_kernel<MT, true>;
+    auto k = resident_kernel<MT, true, EXACT>;
     rc = persistent_grid(k, smem, (int64_t)r.n_small * kBlock, &grid);
     if (rc) return rc;
     k<<<grid, kBlock, smem, st>>>(t, r);
   } else {
-    auto k = resident_kernel<MT, false>;
+    auto k = resident_kernel<MT, false, EXACT>;
     rc = persistent_grid(k, smem, (int64_t)r.n_small * kBlock, &grid);
     if (rc) return rc;
     k<<<grid, kBlock, smem, st>>>(t, r);
@@ -583,19 +608,30 @@ int resident_launch_t(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t
   return QB_OK;
 }
 
+// Exact momentum runs the generic kernels (MT = 0) only.
+template <int MT>
+int resident_launch_t(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t st) {
+  if (t.exact) {
+    if constexpr (MT == 0) return resident_launch_e<0, true>(t, r, cplx, st);
+    return fail(QB_EINTERNAL, "exact momentum runs the generic kernels");
+  }
+  return resident_launch_e<MT, false>(t, r, cplx, st);
+}
+
 // Launches one stage for mode count MT (0: any M) and the runtime batch size /
 // coupling type / bilinear flag / basis (sim: the weighted basis of the RK4 and
 // adjoint stages, modes 0 to 3; plain: the <H> reduction, mode 4); *grid (if
-// non-NULL) receives the grid size.
-template <int MT>
-int stage_launch_t(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, bool bil, bool sim, cudaStream_t st,
+// non-NULL) receives the grid size.  Exact momentum (MT = 0 only): one state at
+// a time.
+template <int MT, bool EXACT>
+int stage_launch_e(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, bool bil, bool sim, cudaStream_t st,
                    int* grid_out) {
-  const size_t smem = ((t.blob_bytes - kSmemFrom(t) + 15) & ~15) +
+  const size_t smem = ((t.blob_bytes - kSmemFrom(t, EXACT) + 15) & ~15) +
                       (size_t)kStageWarps * df_warp_scratch_bytes(t.M, t.n_ann);
   int grid = 0, rc = QB_OK;
 #define QB_STAGE_CASE(BB, CC, LL, SS)                                           \
   {                                                                             \
-    auto k = stage_df_kernel<MT, BB, CC, LL, SS>;                               \
+    auto k = stage_df_kernel<MT, BB, CC, LL, SS, EXACT>;                        \
     rc = persistent_grid(k, smem, a.row1 - a.row0, &grid, kStageBlock);         \
     if (rc) return rc;                                                          \
     k<<<grid, kStageBlock, smem, st>>>(t, a, mode);                             \
@@ -612,12 +648,17 @@ int stage_launch_t(const Tables& t, const DfArgs& a, int mode, int B, bool cplx,
       if (B != 1) return fail(QB_EUNSUPPORTED, "batched sweeps need a real coupling");
       QB_STAGE_CASE(1, true, false, true)
     } else {
-      switch (B) {
-        case 1: QB_STAGE_CASE(1, false, false, true) break;
-        case 2: QB_STAGE_CASE(2, false, false, true) break;
-        case 4: QB_STAGE_CASE(4, false, false, true) break;
-        case 8: QB_STAGE_CASE(8, false, false, true) break;
-        default: return fail(QB_EINVAL, "batch must be 1, 2, 4 or 8");
+      if constexpr (EXACT) {
+        if (B != 1) return fail(QB_EUNSUPPORTED, "exact momentum: batched sweeps are not built");
+        QB_STAGE_CASE(1, false, false, true)
+      } else {
+        switch (B) {
+          case 1: QB_STAGE_CASE(1, false, false, true) break;
+          case 2: QB_STAGE_CASE(2, false, false, true) break;
+          case 4: QB_STAGE_CASE(4, false, false, true) break;
+          case 8: QB_STAGE_CASE(8, false, false, true) break;
+          default: return fail(QB_EINVAL, "batch must be 1, 2, 4 or 8");
+        }
       }
     }
   } else {
@@ -634,6 +675,16 @@ int stage_launch_t(const Tables& t, const DfArgs& a, int mode, int B, bool cplx,
   return QB_OK;
 }
 
+template <int MT>
+int stage_launch_t(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, bool bil, bool sim, cudaStream_t st,
+                   int* grid_out) {
+  if (t.exact) {
+    if constexpr (MT == 0) return stage_launch_e<0, true>(t, a, mode, B, cplx, bil, sim, st, grid_out);
+    return fail(QB_EINTERNAL, "exact momentum runs the generic kernels");
+  }
+  return stage_launch_e<MT, false>(t, a, mode, B, cplx, bil, sim, st, grid_out);
+}
+
 // one explicit specialisation per translation unit (qb_stage_m*.cu)
 int stage_launch_m5(const Tables&, const DfArgs&, int, int, bool, bool, bool, cudaStream_t, int*);
 int stage_launch_m7(const Tables&, const DfArgs&, int, int, bool, bool, bool, cudaStream_t, int*);
@@ -648,6 +699,7 @@ int resident_launch_m11(const Tables&, const ResArgs&, bool, cudaStream_t);
 int resident_launch_any(const Tables&, const ResArgs&, bool, cudaStream_t);
 
 inline int resident_launch(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t st) {
+  if (t.exact) return resident_launch_any(t, r, cplx, st);
   switch (t.M) {
     case 5: return resident_launch_m5(t, r, cplx, st);
     case 7: return resident_launch_m7(t, r, cplx, st);
@@ -659,6 +711,7 @@ inline int resident_launch(const Tables& t, const ResArgs& r, bool cplx, cudaStr
 
 inline int stage_launch(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, cudaStream_t st,
                         int* grid_out = nullptr, bool bil = false, bool sim = false) {
+  if (t.exact) return stage_launch_any(t, a, mode, B, cplx, bil, sim, st, grid_out);
   switch (t.M) {
     case 5: return stage_launch_m5(t, a, mode, B, cplx, bil, sim, st, grid_out);
     case 7: return stage_launch_m7(t, a, mode, B, cplx, bil, sim, st, grid_out);
