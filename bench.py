@@ -235,6 +235,34 @@ def small_extra(qb, torch):
     return out
 
 
+def exact_extra(qb, torch, steps: int = 3):
+    """The batched coherent workload (M=7, n_tot=16, N <= 40) with momentum conserved
+    exactly (the contact coupling restricted to p+q = r+s): every exact (N, P) sector
+    in one launch per stage, with the ranking tables in global memory."""
+    W = wl.batched_coherent()
+    L = wl.contact_coupling(W.M, -0.05 / 16, exact=True)
+    qs = qb.Space(W.M, W.w, L, 0, W.n_max, exact=True)
+    terms, _ = qs.terms()
+    psi = qs.empty_state()
+    qs.init_coherent(W.z, psi)
+    work = qs.workspace(1)
+    resident_max = qs.autotune(W.dt, psi, steps=1, work=work)
+    qs.evolve(psi, W.dt, 1, work)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    qs.evolve(psi, W.dt, steps, work)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    out = {"workload": W.name + "_exact_momentum", "kets": qs.total, "sectors": qs.n_sectors,
+           "terms_per_hpsi": terms, "ms_per_step": ms, "terms_per_s": 4 * terms / (ms * 1e-3),
+           "rk4_steps_per_s": 1e3 / ms, "resident_max_kets": resident_max}
+    del psi, work, qs
+    torch.cuda.empty_cache()
+    return out
+
+
 def sweep_extra(qb, torch, steps: int = 3):
     """8-member coupling sweep on the M=11, N=20, P=0 sector (2,731,365 kets, number state
     (...,7,6,7,...), w=|p|, C_k = -0.005 k): one batched launch per stage for all 8
@@ -471,6 +499,7 @@ def main():
         line["adjoint"] = adjoint_extra(qb, torch)
         line["sweep"] = sweep_extra(qb, torch)
         line["small_sector"] = small_extra(qb, torch)
+        line["exact_momentum"] = exact_extra(qb, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W)
     if rank == 0:

@@ -42,12 +42,16 @@ namespace qb {
 #ifndef QB_STAGE_WARPS
 #define QB_STAGE_WARPS 12
 #endif
+// Resident CTAs per SM that the register budget of the single-state stage kernel
+// is planned for: 3 x 384 threads leave 56 registers per thread (36 warps per SM).
+// Batched and bilinear instantiations hold more state per lane and keep the
+// compiler's choice (planned for one CTA).
 #ifndef QB_STAGE_MIN_BLOCKS
-#define QB_STAGE_MIN_BLOCKS 1
+#define QB_STAGE_MIN_BLOCKS 3
 #endif
 constexpr int kStageWarps = QB_STAGE_WARPS;
 constexpr int kStageBlock = 32 * kStageWarps;
-constexpr int kStageMinBlocks = QB_STAGE_MIN_BLOCKS;  // resident CTAs per SM the register budget is planned for
+constexpr int kStageMinBlocks = QB_STAGE_MIN_BLOCKS;
 
 // first byte of the table image the stage kernels stage in shared memory
 // (exact momentum: the ranking table too stays in global memory)
@@ -78,9 +82,8 @@ __device__ __forceinline__ float4 gather(const float4* p) {
 // psi += w (z W^-1 H W f + sum of basef) in FP64, and write f = psi_new / w; the
 // bilinears multiply each factor by w.
 //
-// EXACT: momentum conserved exactly (the generic kernel, MT = 0): momentum
-// arithmetic modulo t.Q > every momentum sum, shifts stored as int16, the
-// ranking table in global memory.
+// EXACT: momentum conserved exactly: momentum arithmetic modulo t.Q > every
+// momentum sum, shifts stored as int16, the ranking table in global memory.
 template <int MT, int B, bool CPLX, bool BIL, bool LOCAL, bool SIM, bool EXACT>
 __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const float2* sqf, const float4* Gf,
                                            const uint4* dl4, const DfArgs& a, const int mode, const int64_t base,
@@ -240,7 +243,8 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
         const float2 sa = sqf[occ[r * kWarpRows]], sb = sqf[occ[s * kWarpRows] - (r == s ? 1 : 0)];
         A = df_mul(dfl{sa.x, sa.y}, dfl{sb.x, sb.y});
       }
-      constexpr int kC = (QB_UNROLL_PARTNERS && !CPLX && MT > 0 && (MT % 2) == 1) ? (MT - 1) / 2 : 0;
+      // (exact momentum: the partner count varies from pair to pair)
+      constexpr int kC = (QB_UNROLL_PARTNERS && !CPLX && !EXACT && MT > 0 && (MT % 2) == 1) ? (MT - 1) / 2 : 0;
       if (kC > 0) {
         // fixed partner count: all ranks first, then all gathers, then the sums
         const int j0 = v.ann[ai];
@@ -468,7 +472,8 @@ __device__ __forceinline__ StageSmem stage_smem(const Tables& t, unsigned char* 
 }
 
 template <int MT, int B, bool CPLX, bool BIL, bool SIM, bool EXACT>
-__global__ void __launch_bounds__(kStageBlock, kStageMinBlocks) stage_df_kernel(const Tables t, const DfArgs a, const int mode) {
+__global__ void __launch_bounds__(kStageBlock, (B == 1 && !BIL) ? kStageMinBlocks : 1)
+    stage_df_kernel(const Tables t, const DfArgs a, const int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int M = (MT > 0) ? MT : t.M;
   // the only CTA-wide barrier: warps run independently afterwards
@@ -608,21 +613,16 @@ int resident_launch_e(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t
   return QB_OK;
 }
 
-// Exact momentum runs the generic kernels (MT = 0) only.
 template <int MT>
 int resident_launch_t(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t st) {
-  if (t.exact) {
-    if constexpr (MT == 0) return resident_launch_e<0, true>(t, r, cplx, st);
-    return fail(QB_EINTERNAL, "exact momentum runs the generic kernels");
-  }
+  if (t.exact) return resident_launch_e<MT, true>(t, r, cplx, st);
   return resident_launch_e<MT, false>(t, r, cplx, st);
 }
 
 // Launches one stage for mode count MT (0: any M) and the runtime batch size /
 // coupling type / bilinear flag / basis (sim: the weighted basis of the RK4 and
 // adjoint stages, modes 0 to 3; plain: the <H> reduction, mode 4); *grid (if
-// non-NULL) receives the grid size.  Exact momentum (MT = 0 only): one state at
-// a time.
+// non-NULL) receives the grid size.  Exact momentum: one state at a time.
 template <int MT, bool EXACT>
 int stage_launch_e(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, bool bil, bool sim, cudaStream_t st,
                    int* grid_out) {
@@ -678,10 +678,7 @@ int stage_launch_e(const Tables& t, const DfArgs& a, int mode, int B, bool cplx,
 template <int MT>
 int stage_launch_t(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, bool bil, bool sim, cudaStream_t st,
                    int* grid_out) {
-  if (t.exact) {
-    if constexpr (MT == 0) return stage_launch_e<0, true>(t, a, mode, B, cplx, bil, sim, st, grid_out);
-    return fail(QB_EINTERNAL, "exact momentum runs the generic kernels");
-  }
+  if (t.exact) return stage_launch_e<MT, true>(t, a, mode, B, cplx, bil, sim, st, grid_out);
   return stage_launch_e<MT, false>(t, a, mode, B, cplx, bil, sim, st, grid_out);
 }
 
@@ -699,7 +696,6 @@ int resident_launch_m11(const Tables&, const ResArgs&, bool, cudaStream_t);
 int resident_launch_any(const Tables&, const ResArgs&, bool, cudaStream_t);
 
 inline int resident_launch(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t st) {
-  if (t.exact) return resident_launch_any(t, r, cplx, st);
   switch (t.M) {
     case 5: return resident_launch_m5(t, r, cplx, st);
     case 7: return resident_launch_m7(t, r, cplx, st);
@@ -711,7 +707,6 @@ inline int resident_launch(const Tables& t, const ResArgs& r, bool cplx, cudaStr
 
 inline int stage_launch(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, cudaStream_t st,
                         int* grid_out = nullptr, bool bil = false, bool sim = false) {
-  if (t.exact) return stage_launch_any(t, a, mode, B, cplx, bil, sim, st, grid_out);
   switch (t.M) {
     case 5: return stage_launch_m5(t, a, mode, B, cplx, bil, sim, st, grid_out);
     case 7: return stage_launch_m7(t, a, mode, B, cplx, bil, sim, st, grid_out);

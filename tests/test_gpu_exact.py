@@ -167,3 +167,21 @@ def test_exact_rejects_umklapp_coupling_and_batches():
     psi = torch.zeros((2, qs.total), dtype=torch.complex128, device="cuda")
     with pytest.raises(qb.QbError):
         qs.evolve_batch(psi, [1.0, 0.5], 1e-3, 1)
+
+
+def test_minimal_image_long_range_evolution():
+    """The minimal-image variant of the long-range kernel (distance on the ring of
+    M momenta) on mod-M sectors, against the oracle."""
+    from helpers import pair
+
+    M = 9
+    L = wl.long_range_coupling(M, 0.1 / 8, min_image=True)
+    w = wl.dispersion_quadratic(M)
+    qs, os_ = pair(M, w, L, 8, 8, [0, 4])
+    x = random_state(qs.total, 3)
+    out = qs.empty_state()
+    qs.hpsi(to_dev(x), out)
+    assert rel_err(to_host(out), orc.apply_h(os_, w, L, x)) <= HPSI_TOL
+    psi = to_dev(x)
+    qs.evolve(psi, 1e-3, 30)
+    assert rel_err(to_host(psi), orc.rk4(os_, w, L, x, 1e-3, 30)) <= STATE_TOL
