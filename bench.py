@@ -35,9 +35,9 @@ import workloads as wl  # noqa: E402
 # (a DFMA microbenchmark measured 1.00 TFLOP/s: python -m paper_2111_00050_gb300.probe)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per ket of one stage launch (the first stage of a step), from an ncu capture
-# of the current stage kernel (batched coherent at n_tot=12: 576.1 MB read + 229.4 MB
+# of the current stage kernel (batched coherent at n_tot=12: 636.2 MB read + 230.6 MB
 # written over 15,380,937 kets); scaled by kets
-STAGE_DRAM_BYTES_PER_KET = (576.1e6 + 229.4e6) / 15380937
+STAGE_DRAM_BYTES_PER_KET = (636.2e6 + 230.6e6) / 15380937
 
 
 def _peaks():
@@ -263,6 +263,39 @@ def exact_extra(qb, torch, steps: int = 3):
     return out
 
 
+def squeezing_extra(qb, torch, n_list=(4, 8, 12)):
+    """Sec. IV E's squeezing analysis (the paper's n_tot sweep, scaled down): for each
+    n_tot the M=7 long-range coherent system with |n_tot chi| = 0.242 runs to t = 1.6
+    with observables every 10 steps (qb_evolve_observe); onset t_sqz (V_- <= 0.8)
+    and maximal squeezing (V_min, tau_min = |n_tot chi| t_min) from qb_squeezing,
+    beside the one-mode estimates, then the fits V_min = c0 n^c1 and
+    tau_min = c0 + c1 log n over the runs (qb_fit)."""
+    runs = []
+    for n in n_list:
+        W = wl.squeezing_coherent(n)
+        qs = qb.Space(W.M, W.w, W.L, W.n_min, W.n_max)
+        psi = qs.empty_state()
+        qs.init_coherent(W.z, psi)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        series = qs.evolve_observe(psi, W.dt, W.steps, W.obs_every)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        sq = qb.api.squeezing([o["Vminus_p"] for o in series], W.dt * W.obs_every, 0.8)
+        chi = abs(qb.api.interaction_per_occupation(W.M, W.w, W.L, W.z))
+        runs.append({"n_tot": n, "kets": qs.total, "steps": W.steps, "wall_s": wall, "t_sqz": sq["t_sqz"],
+                     "crossed": sq["flag"] == qb.QB_CROSSED, "v_min": sq["v_min"], "t_min": sq["t_min"],
+                     "tau_min": chi * sq["t_min"], "t_sqz_one_mode": 0.05 / chi,
+                     "v_min_one_mode": n ** (-1.0 / 3.0), "ntot_chi": chi})
+        del qs, psi
+        torch.cuda.empty_cache()
+    ns = [r["n_tot"] for r in runs]
+    vfit = qb.api.fit(ns, [r["v_min"] for r in runs], "power")
+    tfit = qb.api.fit(ns, [r["tau_min"] for r in runs], "log")
+    return {"runs": runs, "v_min_power_law": {"c0": vfit[0], "c1": vfit[1]},
+            "tau_min_log_law": {"c0": tfit[0], "c1": tfit[1]}}
+
+
 def sweep_extra(qb, torch, steps: int = 3):
     """8-member coupling sweep on the M=11, N=20, P=0 sector (2,731,365 kets, number state
     (...,7,6,7,...), w=|p|, C_k = -0.005 k): one batched launch per stage for all 8
@@ -398,7 +431,7 @@ def main():
         "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
         "frac": achieved / FP64_PEAK_TFLOPS,
         "traffic": STAGE_DRAM_BYTES_PER_KET * qs.total if args.config == "batched_coherent" else None,
-        "kernel": f"stage_df_kernel<{W.M},1,0,0,1> (one RK4 stage = one H psi over all sectors, weighted basis)",
+        "kernel": f"stage_df_kernel<{W.M},1,0,0,1,0> (one RK4 stage = one H psi over all sectors, weighted basis)",
         "stage_ms": stage_time * 1e3,
         "peak_note": "FP64-equivalent flops (2 FMA/term) vs the FP64 pipe peak from unit counts "
                      "(152 SMs x 2 FMA/clk x 2.07 GHz); the kernel itself runs double-float on the FP32/ALU "
@@ -500,6 +533,7 @@ def main():
         line["sweep"] = sweep_extra(qb, torch)
         line["small_sector"] = small_extra(qb, torch)
         line["exact_momentum"] = exact_extra(qb, torch)
+        line["squeezing"] = squeezing_extra(qb, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W)
     if rank == 0:

@@ -254,6 +254,29 @@ int qb_adjoint(qb_space* space, const double* z, double scale, double dt, int64_
  * t_br = 0) or QB_NOT_CROSSED (t_br = NaN).  Host only. */
 int qb_breaktime(const double* values, int n, double dt_obs, double thr, double* t_br, int* flag);
 
+/* ---- squeezing-time analysis (Sec. II E, Sec. IV E) ---------------------- */
+
+/* Squeezing of a series vminus[0..n) of V_- samples spaced dt_obs apart
+ * (normally Vminus_p, Eq. generalVminus for a^p).  Onset: the first sample k with
+ * vminus[k] <= thr (the paper takes 0.8), *t_sqz interpolated linearly between
+ * samples k-1 and k; *flag as for qb_breaktime (QB_AT_START if k = 0,
+ * QB_NOT_CROSSED and NaN if never).  Maximal squeezing: the smallest sample,
+ * refined by the vertex of the parabola through it and its two neighbours
+ * (the sample itself at either end of the series): *v_min and *t_min.  Host only. */
+int qb_squeezing(const double* vminus, int n, double dt_obs, double thr, double* t_sqz, int* flag, double* v_min,
+                 double* t_min);
+
+/* Mean interaction energy per occupation of the coherent amplitudes z[2M]
+ * (Sec. II E): n_tot chi = n_tot^-1 sum_{pqrs} L_{pq;rs} z_p^* z_q^* z_r z_s with
+ * n_tot = sum |z_p|^2 (real for a Hermitian coupling).  The paper's onset estimate
+ * is t_sqz ~ 0.05 / |n_tot chi| and tau = |n_tot chi| t.  Host only. */
+int qb_interaction_per_occupation(const qb_model* model, const double* z, double* ntot_chi);
+
+/* Least-squares fit over runs (x[k], y[k]), k < n >= 2: kind 0, the power law
+ * y = c0 x^c1 (a line in log x, log y; x, y > 0); kind 1, y = c0 + c1 log x
+ * (x > 0).  Host only. */
+int qb_fit(const double* x, const double* y, int n, int kind, double* c0, double* c1);
+
 /* Classic RK4 of the mean-field equations (Eq. classicalFieldEqns):
  * da_k/dt = -i (w_k a_k + sum_{q,r,s} (L_{kq;rs} + L_{qk;rs}) a_q^* a_r a_s).
  * z0: [2M] host; traj: host [(steps/every + 1)][2M], row 0 = z0.  Host only. */

@@ -422,6 +422,52 @@ def breaktime(values, dt_obs: float, thr: float):
     return float("nan"), NOT_CROSSED
 
 
+# -------------------------------------------------------------- squeezing times
+
+def squeezing(values, dt_obs: float, thr: float = 0.8) -> dict:
+    """Squeezing analysis of a V_- series (Sec. II E): the onset t_sqz, first
+    sample with V_- <= thr (0.8 in the paper) interpolated linearly with the
+    previous one; the smallest sample refined by the quadratic through it and its
+    two neighbours (numpy.polyfit), or the sample itself at an end of the series."""
+    v = np.asarray(values, dtype=np.float64)
+    t_sqz, flag = float("nan"), NOT_CROSSED
+    for k in range(v.size):
+        if v[k] <= thr:
+            if k == 0:
+                t_sqz, flag = 0.0, AT_START
+            else:
+                t_sqz, flag = (k - 1 + (v[k - 1] - thr) / (v[k - 1] - v[k])) * dt_obs, CROSSED
+            break
+    k = int(np.argmin(v))
+    v_min, t_min = float(v[k]), k * dt_obs
+    if 0 < k < v.size - 1:
+        c = np.polyfit([-1.0, 0.0, 1.0], v[k - 1:k + 2], 2)
+        if c[0] > 0:
+            u = -c[1] / (2 * c[0])
+            t_min, v_min = (k + u) * dt_obs, float(np.polyval(c, u))
+    return {"t_sqz": t_sqz, "flag": flag, "v_min": v_min, "t_min": t_min}
+
+
+def interaction_per_occupation(L, z) -> float:
+    """n_tot chi = n_tot^-1 sum_{pqrs} L_{pq;rs} z_p^* z_q^* z_r z_s, n_tot = sum |z|^2
+    (Sec. II E, with L = Lambda/2)."""
+    z = np.asarray(z, dtype=np.complex128)
+    e = np.einsum("pqrs,p,q,r,s->", np.asarray(L, dtype=np.complex128), z.conj(), z.conj(), z, z)
+    return float(e.real / np.sum(np.abs(z) ** 2))
+
+
+def fit(x, y, kind: str = "power"):
+    """Least squares over runs: y = c0 x^c1 ("power", a line in log-log) or
+    y = c0 + c1 log x ("log"); returns (c0, c1)."""
+    lx = np.log(np.asarray(x, dtype=np.float64))
+    y = np.asarray(y, dtype=np.float64)
+    if kind == "power":
+        c1, lc0 = np.polyfit(lx, np.log(y), 1)
+        return float(np.exp(lc0)), float(c1)
+    c1, c0 = np.polyfit(lx, y, 1)
+    return float(c0), float(c1)
+
+
 # ---------------------------------------------------------------------- adjoint
 
 def rk4_step_adjoint(space: Space, w, L, psi_n: np.ndarray, lam_next: np.ndarray, dt: float, dH_list):

@@ -82,6 +82,10 @@ SIGNATURES = {
                                   ctypes.c_void_p, ctypes.c_void_p]),
     "qb_breaktime": (ctypes.c_int, [_c_double_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, _c_double_p,
                                     _c_int_p]),
+    "qb_squeezing": (ctypes.c_int, [_c_double_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, _c_double_p,
+                                     _c_int_p, _c_double_p, _c_double_p]),
+    "qb_interaction_per_occupation": (ctypes.c_int, [ctypes.POINTER(QbModel), _c_double_p, _c_double_p]),
+    "qb_fit": (ctypes.c_int, [_c_double_p, _c_double_p, ctypes.c_int, ctypes.c_int, _c_double_p, _c_double_p]),
     "qb_meanfield": (ctypes.c_int, [ctypes.POINTER(QbModel), _c_double_p, ctypes.c_double, ctypes.c_int64,
                                     ctypes.c_int, _c_double_p]),
 }

@@ -249,6 +249,38 @@ def breaktime(values, dt_obs: float, thr: float):
     return float(t.value), int(f.value)
 
 
+def squeezing(values, dt_obs: float, thr: float = 0.8) -> dict:
+    """Onset (first V_- <= thr) and maximal squeezing of a V_- series (qb_squeezing)."""
+    v = _f64(values)
+    t, f, vm, tm = ctypes.c_double(), ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    dp = ctypes.POINTER(ctypes.c_double)
+    check(lib().qb_squeezing(v.ctypes.data_as(dp), int(v.size), float(dt_obs), float(thr), ctypes.byref(t),
+                             ctypes.byref(f), ctypes.byref(vm), ctypes.byref(tm)))
+    return {"t_sqz": float(t.value), "flag": int(f.value), "v_min": float(vm.value), "t_min": float(tm.value)}
+
+
+def interaction_per_occupation(M: int, w, L, z, exact: bool = False) -> float:
+    """n_tot chi = n_tot^-1 sum L_{pq;rs} z_p^* z_q^* z_r z_s (qb_interaction_per_occupation)."""
+    m, keep = _model(M, w, L, exact)
+    zz = _c128_as_f64(z)
+    out = ctypes.c_double()
+    check(lib().qb_interaction_per_occupation(ctypes.byref(m), zz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                              ctypes.byref(out)))
+    return float(out.value)
+
+
+def fit(x, y, kind: str = "power"):
+    """(c0, c1) of y = c0 x^c1 (kind "power") or y = c0 + c1 log x (kind "log") (qb_fit)."""
+    xs, ys = _f64(x), _f64(y)
+    if xs.size != ys.size:
+        raise ValueError("x and y differ in length")
+    c0, c1 = ctypes.c_double(), ctypes.c_double()
+    dp = ctypes.POINTER(ctypes.c_double)
+    check(lib().qb_fit(xs.ctypes.data_as(dp), ys.ctypes.data_as(dp), int(xs.size), {"power": 0, "log": 1}[kind],
+                       ctypes.byref(c0), ctypes.byref(c1)))
+    return float(c0.value), float(c1.value)
+
+
 def meanfield(M: int, w, L, z0, dt: float, steps: int, every: int = 1, exact: bool = False) -> np.ndarray:
     m, keep = _model(M, w, L, exact)
     z = _c128_as_f64(z0)

@@ -777,6 +777,88 @@ int qb_breaktime(const double* values, int n, double dt_obs, double thr, double*
   return QB_OK;
 }
 
+int qb_squeezing(const double* vminus, int n, double dt_obs, double thr, double* t_sqz, int* flag, double* v_min,
+                 double* t_min) {
+  if (!vminus || !t_sqz || !flag || !v_min || !t_min || n < 1 || !(dt_obs > 0.0))
+    return fail(QB_EINVAL, "bad arguments");
+  *t_sqz = NAN;
+  *flag = QB_NOT_CROSSED;
+  for (int k = 0; k < n; ++k) {
+    if (vminus[k] <= thr) {
+      if (k == 0) {
+        *t_sqz = 0.0;
+        *flag = QB_AT_START;
+      } else {
+        const double f = (vminus[k - 1] - thr) / (vminus[k - 1] - vminus[k]);
+        *t_sqz = ((double)(k - 1) + f) * dt_obs;
+        *flag = QB_CROSSED;
+      }
+      break;
+    }
+  }
+  int kmin = 0;
+  for (int k = 1; k < n; ++k)
+    if (vminus[k] < vminus[kmin]) kmin = k;
+  *v_min = vminus[kmin];
+  *t_min = kmin * dt_obs;
+  if (kmin > 0 && kmin < n - 1) {
+    // vertex of the parabola through (-1, a), (0, b), (1, c) in units of dt_obs
+    const double a = vminus[kmin - 1], b = vminus[kmin], c = vminus[kmin + 1];
+    const double den = a - 2.0 * b + c;
+    if (den > 0.0) {
+      const double u = 0.5 * (a - c) / den;  // in [-1/2, 1/2] since b is the smallest
+      *t_min = (kmin + u) * dt_obs;
+      *v_min = b - 0.25 * (a - c) * u;
+    }
+  }
+  return QB_OK;
+}
+
+int qb_interaction_per_occupation(const qb_model* model, const double* z, double* ntot_chi) {
+  if (!model || !z || !ntot_chi) return fail(QB_EINVAL, "bad arguments");
+  std::vector<double> w, Ls;
+  int rc = prepare_model(model, w, Ls);
+  if (rc) return rc;
+  const int M = model->M;
+  std::vector<cd> zz(M);
+  double n = 0.0;
+  for (int p = 0; p < M; ++p) {
+    if (!std::isfinite(z[2 * p]) || !std::isfinite(z[2 * p + 1])) return fail(QB_EINVAL, "z has a non-finite entry");
+    zz[p] = cd(z[2 * p], z[2 * p + 1]);
+    n += std::norm(zz[p]);
+  }
+  if (!(n > 0.0)) return fail(QB_EINVAL, "z must be nonzero");
+  cd acc = 0.0;
+  for (int p = 0; p < M; ++p)
+    for (int q = 0; q < M; ++q)
+      for (int r = 0; r < M; ++r)
+        for (int s = 0; s < M; ++s) {
+          const size_t t = (((size_t)p * M + q) * M + r) * M + s;
+          acc += cd(Ls[2 * t], Ls[2 * t + 1]) * std::conj(zz[p]) * std::conj(zz[q]) * zz[r] * zz[s];
+        }
+  *ntot_chi = acc.real() / n;
+  return QB_OK;
+}
+
+int qb_fit(const double* x, const double* y, int n, int kind, double* c0, double* c1) {
+  if (!x || !y || !c0 || !c1 || n < 2 || (kind != 0 && kind != 1)) return fail(QB_EINVAL, "bad arguments");
+  double sx = 0.0, sy = 0.0, sxx = 0.0, sxy = 0.0;
+  for (int k = 0; k < n; ++k) {
+    if (!(x[k] > 0.0) || (kind == 0 && !(y[k] > 0.0))) return fail(QB_EINVAL, "the fit needs positive data");
+    const double u = std::log(x[k]), v = kind == 0 ? std::log(y[k]) : y[k];
+    sx += u;
+    sy += v;
+    sxx += u * u;
+    sxy += u * v;
+  }
+  const double det = n * sxx - sx * sx;
+  if (!(det > 0.0)) return fail(QB_EINVAL, "the fit needs two distinct x");
+  const double slope = (n * sxy - sx * sy) / det, icpt = (sy - slope * sx) / n;
+  *c1 = slope;
+  *c0 = kind == 0 ? std::exp(icpt) : icpt;
+  return QB_OK;
+}
+
 int qb_meanfield(const qb_model* model, const double* z0, double dt, int64_t steps, int every, double* traj) {
   if (!model || !model->w || !model->L || !z0 || !traj || every < 1 || steps < 0)
     return fail(QB_EINVAL, "bad arguments");

@@ -81,3 +81,29 @@ def test_model_validation_without_device(bad):
     with pytest.raises(qb.QbError) as e:
         qb.Space(M, w, L, 0, n_max)
     assert e.value.code in (1, 6)
+
+
+def test_squeezing_analysis_matches_oracle():
+    """qb_squeezing, qb_interaction_per_occupation and qb_fit (host only) against
+    the oracle's restatements on noisy series, random couplings and runs."""
+    import oracle as orc
+    import paper_2111_00050_gb300.api as api
+    import workloads as wl
+
+    rng = np.random.default_rng(4)
+    dt = 0.02
+    t = np.arange(60) * dt
+    for k in range(5):
+        v = 1 - 3 * t + 4 * t * t + 0.01 * rng.standard_normal(t.size)
+        got, ref = api.squeezing(v, dt, 0.8), orc.squeezing(v, dt, 0.8)
+        assert got["flag"] == ref["flag"] and abs(got["t_sqz"] - ref["t_sqz"]) < 1e-13
+        assert abs(got["t_min"] - ref["t_min"]) < 1e-12 and abs(got["v_min"] - ref["v_min"]) < 1e-12
+    M = 7
+    for L in (wl.long_range_coupling(M, 0.3), wl.contact_coupling(M, -0.2), wl.long_range_coupling(M, 0.3, min_image=True)):
+        z = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+        got = api.interaction_per_occupation(M, wl.dispersion_quadratic(M), L, z)
+        assert abs(got - orc.interaction_per_occupation(L, z)) < 1e-13 * max(1, abs(got))
+    x = np.array([4.0, 6.0, 8.0, 12.0, 20.0])
+    y = 0.9 * x ** -0.2 * np.exp(0.01 * rng.standard_normal(x.size))
+    for kind in ("power", "log"):
+        np.testing.assert_allclose(api.fit(x, y, kind), orc.fit(x, y, kind), rtol=1e-12)

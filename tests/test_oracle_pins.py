@@ -445,6 +445,66 @@ def test_vminus_bajer_approximation_and_squeezing_onset():
     assert abs(tau_sqz - 0.05) < 0.01
 
 
+def test_squeezing_analysis_on_known_series():
+    """Onset of a line (exact under linear interpolation), the vertex of a sampled
+    parabola, an end minimum, and the never-squeezed case."""
+    dt = 0.01
+    t = np.arange(100) * dt
+    r = orc.squeezing(1 - 4 * t, dt, 0.8)
+    assert r["flag"] == orc.CROSSED and abs(r["t_sqz"] - 0.05) < 1e-12
+    r = orc.squeezing((t - 0.3137) ** 2 + 0.25, dt, 0.8)
+    assert r["flag"] == orc.AT_START and abs(r["t_min"] - 0.3137) < 1e-12 and abs(r["v_min"] - 0.25) < 1e-12
+    r = orc.squeezing(1 - t, dt, 0.0)
+    assert r["flag"] == orc.NOT_CROSSED and math.isnan(r["t_sqz"])
+    assert r["t_min"] == t[-1] and r["v_min"] == 1 - t[-1]
+
+
+def test_interaction_per_occupation_closed_forms():
+    """Single mode: n_tot chi = L n_tot (chi = L, Sec. II E).  Contact C/M on two
+    modes p = -1, +1 with amplitude a: six conserving tuples, n_tot chi = 3 C a^2 / M."""
+    assert abs(orc.interaction_per_occupation(np.full((1,) * 4, -0.004), [5.0]) - (-0.004 * 25.0)) < 1e-15
+    M, C, a = 7, -0.3, 1.7
+    z = np.zeros(M, dtype=np.complex128)
+    lab = list(wl.mode_labels(M))
+    z[lab.index(-1)] = z[lab.index(1)] = a * np.exp(0.4j)
+    got = orc.interaction_per_occupation(wl.contact_coupling(M, C), z)
+    assert abs(got - 3 * C * a * a / M) < 1e-14
+
+
+def test_squeezing_workload_holds_interaction_per_occupation():
+    """The squeezing workloads keep |n_tot chi| = 0.242 for every n_tot (Sec. IV E)."""
+    for n, M in ((3, 5), (8, 7), (20, 7), (12, 9)):
+        W = wl.squeezing_coherent(n, M=M)
+        assert abs(orc.interaction_per_occupation(W.L, W.z) + 0.242) < 1e-13
+
+
+def test_fits_recover_exact_laws():
+    x = np.array([20.0, 40.0, 80.0, 160.0])
+    c0, c1 = orc.fit(x, 0.919 * x ** -0.194, "power")
+    assert abs(c0 - 0.919) < 1e-12 and abs(c1 + 0.194) < 1e-12
+    c0, c1 = orc.fit(x, 0.0120 + 0.0833 * np.log(x), "log")
+    assert abs(c0 - 0.0120) < 1e-12 and abs(c1 - 0.0833) < 1e-12
+
+
+def test_single_mode_squeezing_onset_from_series():
+    """The exact single-mode evolution sampled in time: the onset of the series
+    lands at tau = n_tot |chi| t ~ 0.05 (Sec. II E), and t_min follows Eq.
+    (VminusBajer)'s minimum to within the sampling."""
+    n_tot, Lk = 25.0, -0.004
+    L = np.full((1, 1, 1, 1), Lk, dtype=np.complex128)
+    space = orc.Space(1, [(N, 0) for N in range(0, 100)])
+    psi0, _ = orc.coherent_state(space, [math.sqrt(n_tot)])
+    chi = abs(orc.interaction_per_occupation(L, [math.sqrt(n_tot)])) / n_tot
+    dtau = 0.005
+    taus = np.arange(0, 0.4, dtau)
+    vs = [orc.observables(space, kerr_exact(space, [0.0], L, psi0, tau / (n_tot * chi)))["Vminus_p"] for tau in taus]
+    r = orc.squeezing(vs, dtau, 0.8)
+    assert r["flag"] == orc.CROSSED and abs(r["t_sqz"] - 0.05) < 0.01
+    s = np.sqrt(1 + 4 * taus ** 2)
+    vb = 1 - 4 * taus * s + 8 * taus ** 2 + 8 * taus ** 3 * (5 + 12 * taus ** 2) / (n_tot * s) - 16 * taus ** 4 / n_tot
+    assert abs(r["t_min"] - taus[int(np.argmin(vb))]) < 2 * dtau
+
+
 # ------------------------------------------------------------- initial states
 
 def test_coherent_layer_weights_are_poisson():

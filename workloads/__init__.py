@@ -178,3 +178,19 @@ def large_field_number(M: int = 11, N: int = 20, seed: int = 0) -> Workload:
         z[i] = math.sqrt(N / 3) * np.exp(1j * th[k])
     return Workload(f"large_field_number_M{M}_N{N}", M, dispersion_abs(M), contact_coupling(M, -0.02),
                     "field_number", 5e-4, 20000, 100, z=z, n_tot=N, n_min=N, n_max=N)
+
+
+def squeezing_coherent(n_tot: float, M: int = 7, ntot_chi: float = 0.242, dt: float = 2e-3,
+                       t_end: float = 1.6, obs_every: int = 10) -> Workload:
+    """Sec. IV E's squeezing systems: quadratic dispersion, gravity-like long-range
+    coupling, coherent state alpha = sqrt(n_tot/2) on p = -1 and p = +1, with the
+    strength chosen so that the mean interaction energy per occupation stays at
+    |n_tot chi| = 0.242 for every n_tot.  On these two modes only the tuples
+    (-1,+1;+1,-1) and (+1,-1;-1,+1) of L = -G/(M (p-r)^2) act, each -G/(4M), so
+    n_tot chi = -G n_tot / (8 M) and G = 8 M ntot_chi / n_tot."""
+    z = np.zeros(M, dtype=np.complex128)
+    lab = list(mode_labels(M))
+    z[lab.index(-1)] = z[lab.index(1)] = math.sqrt(n_tot / 2)
+    G = 8 * M * ntot_chi / n_tot
+    return Workload(f"squeezing_coherent_M{M}_ntot{n_tot:g}", M, dispersion_quadratic(M), long_range_coupling(M, G),
+                    "coherent", dt, int(round(t_end / dt)), obs_every, z=z, n_min=0, n_max=poisson_nmax(n_tot))
