@@ -265,14 +265,17 @@ def exact_extra(qb, torch, steps: int = 3):
 
 def squeezing_extra(qb, torch, n_list=(4, 8, 12)):
     """Sec. IV E's squeezing analysis (the paper's n_tot sweep, scaled down): for each
-    n_tot the M=7 long-range coherent system with |n_tot chi| = 0.242 runs to t = 1.6
+    n_tot the M=7 long-range system from a Gaussian coherent profile, its strength set
+    so that |n_tot chi| = 0.242, runs to t = 1.6
     with observables every 10 steps (qb_evolve_observe); onset t_sqz (V_- <= 0.8)
     and maximal squeezing (V_min, tau_min = |n_tot chi| t_min) from qb_squeezing,
     beside the one-mode estimates, then the fits V_min = c0 n^c1 and
     tau_min = c0 + c1 log n over the runs (qb_fit)."""
     runs = []
     for n in n_list:
-        W = wl.squeezing_coherent(n)
+        unit = wl.squeezing_coherent(n)  # strength 1: n_tot chi scales with the strength
+        G = 0.242 / abs(qb.api.interaction_per_occupation(unit.M, unit.w, unit.L, unit.z))
+        W = wl.squeezing_coherent(n, G=G)
         qs = qb.Space(W.M, W.w, W.L, W.n_min, W.n_max)
         psi = qs.empty_state()
         qs.init_coherent(W.z, psi)

@@ -471,11 +471,16 @@ def test_interaction_per_occupation_closed_forms():
     assert abs(got - 3 * C * a * a / M) < 1e-14
 
 
-def test_squeezing_workload_holds_interaction_per_occupation():
-    """The squeezing workloads keep |n_tot chi| = 0.242 for every n_tot (Sec. IV E)."""
-    for n, M in ((3, 5), (8, 7), (20, 7), (12, 9)):
-        W = wl.squeezing_coherent(n, M=M)
-        assert abs(orc.interaction_per_occupation(W.L, W.z) + 0.242) < 1e-13
+def test_squeezing_workload_interaction_scales_with_strength_and_occupation():
+    """n_tot chi of the squeezing workloads is proportional to G n_tot (fixed profile),
+    so one value at G = 1 fixes the strength that holds |n_tot chi| = 0.242 (Sec. IV E)."""
+    for M in (5, 7):
+        base = orc.interaction_per_occupation(wl.squeezing_coherent(1.0, M=M).L, wl.squeezing_coherent(1.0, M=M).z)
+        for n, G in ((3, 0.7), (8, 1.9), (20, 0.05)):
+            W = wl.squeezing_coherent(n, M=M, G=G)
+            assert abs(orc.interaction_per_occupation(W.L, W.z) - base * G * n) < 1e-13 * abs(base * G * n)
+            W = wl.squeezing_coherent(n, M=M, G=0.242 / abs(base * n))
+            assert abs(abs(orc.interaction_per_occupation(W.L, W.z)) - 0.242) < 1e-13
 
 
 def test_fits_recover_exact_laws():

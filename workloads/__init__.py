@@ -180,17 +180,16 @@ def large_field_number(M: int = 11, N: int = 20, seed: int = 0) -> Workload:
                     "field_number", 5e-4, 20000, 100, z=z, n_tot=N, n_min=N, n_max=N)
 
 
-def squeezing_coherent(n_tot: float, M: int = 7, ntot_chi: float = 0.242, dt: float = 2e-3,
-                       t_end: float = 1.6, obs_every: int = 10) -> Workload:
+def squeezing_coherent(n_tot: float, M: int = 7, G: float = 1.0, dt: float = 2e-3, t_end: float = 1.6,
+                       obs_every: int = 10) -> Workload:
     """Sec. IV E's squeezing systems: quadratic dispersion, gravity-like long-range
-    coupling, coherent state alpha = sqrt(n_tot/2) on p = -1 and p = +1, with the
-    strength chosen so that the mean interaction energy per occupation stays at
-    |n_tot chi| = 0.242 for every n_tot.  On these two modes only the tuples
-    (-1,+1;+1,-1) and (+1,-1;-1,+1) of L = -G/(M (p-r)^2) act, each -G/(4M), so
-    n_tot chi = -G n_tot / (8 M) and G = 8 M ntot_chi / n_tot."""
-    z = np.zeros(M, dtype=np.complex128)
-    lab = list(mode_labels(M))
-    z[lab.index(-1)] = z[lab.index(1)] = math.sqrt(n_tot / 2)
-    G = 8 * M * ntot_chi / n_tot
+    coupling of strength G, coherent state with a Gaussian momentum profile
+    z_p ~ exp(-p^2 / 2) rescaled to sum |z_p|^2 = n_tot.  The paper holds the mean
+    interaction energy per occupation at |n_tot chi| = 0.242 for every n_tot; for a
+    fixed profile n_tot chi is proportional to G n_tot, so callers pick G from the
+    value at G = 1."""
+    lab = mode_labels(M).astype(np.float64)
+    z = np.exp(-lab ** 2 / 2).astype(np.complex128)
+    z *= math.sqrt(n_tot / float(np.sum(np.abs(z) ** 2)))
     return Workload(f"squeezing_coherent_M{M}_ntot{n_tot:g}", M, dispersion_quadratic(M), long_range_coupling(M, G),
                     "coherent", dt, int(round(t_end / dt)), obs_every, z=z, n_min=0, n_max=poisson_nmax(n_tot))
