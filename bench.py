@@ -299,6 +299,55 @@ def squeezing_extra(qb, torch, n_list=(4, 8, 12)):
             "tau_min_log_law": {"c0": tfit[0], "c1": tfit[1]}}
 
 
+def breaktime_sweep(qb, torch, r_list=(1, 2, 3, 4, 6), chunk: int = 1000):
+    """Sec. IV C-D's breaktime scaling with n_tot (run with --breaktime-sweep): for each
+    average mode occupation r the M=5 long-range coherent system evolves with
+    observables every 20 steps until Q >= 0.15 and 1 - lam_p / n_tot >= 0.1 have both
+    been crossed (or t = 30); breaktimes from qb_breaktime, then logarithmic and
+    power-law fits of t_br against n_tot (qb_fit) with their rms residuals."""
+    runs = []
+    for r in r_list:
+        W = wl.breaktime_coherent(r)
+        qs = qb.Space(W.M, W.w, W.L, W.n_min, W.n_max)
+        psi = qs.empty_state()
+        qs.init_coherent(W.z, psi)
+        work = qs.workspace(1)
+        Q, PO = [], []
+        t0 = time.perf_counter()
+        done = 0
+        while done < W.steps:
+            k = min(chunk, W.steps - done)
+            ser = qs.evolve_observe(psi, W.dt, k, W.obs_every, work)
+            part = ser if done == 0 else ser[1:]  # the first sample repeats the last of the previous chunk
+            Q += [o["Q"] for o in part]
+            PO += [o["PO"] for o in part]
+            done += k
+            if max(Q) >= 0.15 and max(PO) >= 0.1:
+                break
+        torch.cuda.synchronize()
+        dt_obs = W.dt * W.obs_every
+        tq, fq = qb.breaktime(Q, dt_obs, 0.15)
+        tp, fp = qb.breaktime(PO, dt_obs, 0.1)
+        runs.append({"r": r, "n_tot": W.n_tot, "kets": qs.total, "steps": done, "wall_s": time.perf_counter() - t0,
+                     "t_br_Q": tq, "Q_crossed": fq == qb.QB_CROSSED, "t_br_PO": tp, "PO_crossed": fp == qb.QB_CROSSED})
+        del qs, psi, work
+        torch.cuda.empty_cache()
+    fits = {}
+    for key in ("t_br_Q", "t_br_PO"):
+        pts = [(x["n_tot"], x[key]) for x in runs if x[key] == x[key]]
+        if len(pts) < 2:
+            continue
+        n = np.array([p[0] for p in pts], dtype=float)
+        t = np.array([p[1] for p in pts], dtype=float)
+        out = {}
+        for kind in ("log", "power"):
+            c0, c1 = qb.api.fit(n, t, kind)
+            pred = c0 + c1 * np.log(n) if kind == "log" else c0 * n ** c1
+            out[kind] = {"c0": c0, "c1": c1, "rms": float(np.sqrt(np.mean((pred - t) ** 2)))}
+        fits[key] = out
+    return {"workload": "breaktime_coherent_M5", "runs": runs, "fits": fits}
+
+
 def sweep_extra(qb, torch, steps: int = 3):
     """8-member coupling sweep on the M=11, N=20, P=0 sector (2,731,365 kets, number state
     (...,7,6,7,...), w=|p|, C_k = -0.005 k): one batched launch per stage for all 8
@@ -346,6 +395,8 @@ def main():
     ap.add_argument("--n-tot", type=int, default=16, help="mean occupation of the batched coherent workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint and sweep measurements")
+    ap.add_argument("--breaktime-sweep", action="store_true",
+                    help="run only the breaktime scaling experiment (Sec. IV C-D) and print its JSON line")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -365,6 +416,10 @@ def main():
         dist.init_process_group("nccl")
     import paper_2111_00050_gb300 as qb
 
+    if args.breaktime_sweep:
+        if rank == 0:
+            print(json.dumps(breaktime_sweep(qb, torch)))
+        return
     W, sp = workload(args.config, args.n_tot)
     t_setup = time.perf_counter()
     qs = qb.Space(W.M, W.w, W.L, sp["n_min"], sp["n_max"], sp["p_list"])

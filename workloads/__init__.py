@@ -193,3 +193,18 @@ def squeezing_coherent(n_tot: float, M: int = 7, G: float = 1.0, dt: float = 2e-
     z *= math.sqrt(n_tot / float(np.sum(np.abs(z) ** 2)))
     return Workload(f"squeezing_coherent_M{M}_ntot{n_tot:g}", M, dispersion_quadratic(M), long_range_coupling(M, G),
                     "coherent", dt, int(round(t_end / dt)), obs_every, z=z, n_min=0, n_max=poisson_nmax(n_tot))
+
+
+def breaktime_coherent(r: float, M: int = 5, g: float = 0.5, seed: int = 0, dt: float = 5e-3,
+                       t_end: float = 30.0, obs_every: int = 20) -> Workload:
+    """Sec. IV C-D's breaktime systems: quadratic dispersion, gravity-like long range,
+    coherent state with average mode occupation r (|z_p|^2 = r on every mode, phases
+    from numpy default_rng(seed).uniform(0, 2 pi, M)), n_tot = M r, and strength
+    G = g / n_tot so that the mean-field dynamics is the same for every n_tot."""
+    rng = np.random.default_rng(seed)
+    th = rng.uniform(0.0, 2 * math.pi, M)
+    z = math.sqrt(r) * np.exp(1j * th)
+    n_tot = M * r
+    return Workload(f"breaktime_coherent_M{M}_r{r:g}", M, dispersion_quadratic(M), long_range_coupling(M, g / n_tot),
+                    "coherent", dt, int(round(t_end / dt)), obs_every, z=z, n_tot=n_tot, n_min=0,
+                    n_max=poisson_nmax(n_tot))
