@@ -44,8 +44,9 @@ namespace qb {
 #endif
 // Resident CTAs per SM that the register budget of the single-state stage kernel
 // is planned for: 3 x 384 threads leave 56 registers per thread (36 warps per SM).
-// Batched and bilinear instantiations hold more state per lane and keep the
-// compiler's choice (planned for one CTA).
+// The bilinear instantiations (more accumulators per lane) of the specialised mode
+// counts are planned for 2 CTAs (80 registers); the batched ones and the generic
+// bilinear ones (16 accumulators) keep the compiler's choice (one CTA).
 #ifndef QB_STAGE_MIN_BLOCKS
 #define QB_STAGE_MIN_BLOCKS 3
 #endif
@@ -472,7 +473,7 @@ __device__ __forceinline__ StageSmem stage_smem(const Tables& t, unsigned char* 
 }
 
 template <int MT, int B, bool CPLX, bool BIL, bool SIM, bool EXACT>
-__global__ void __launch_bounds__(kStageBlock, (B == 1 && !BIL) ? kStageMinBlocks : 1)
+__global__ void __launch_bounds__(kStageBlock, (B == 1 && !BIL) ? kStageMinBlocks : ((BIL && MT > 0) ? 2 : 1))
     stage_df_kernel(const Tables t, const DfArgs a, const int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int M = (MT > 0) ? MT : t.M;
