@@ -545,14 +545,17 @@ __global__ void __launch_bounds__(kBlock) moments_kernel(const Tables t, const d
 // Double-float moments: the same sums as moments_kernel from the double-float copy
 // of the state (no FP64 arithmetic per target).
 //
+// The moments are organised as slots, each one operator acting on the row's ket:
+// a_i (M slots), n_i (M), a_i^dag a_j for i < j (the i > j half follows by
+// Hermiticity) and a_i a_j for i <= j (the matrix is symmetric).  A slot changes at
+// most two occupations, (e0, dn0) and (e1, dn1), so one loop over a shared slot
+// table serves them all: target sector, rank, gather and the product c conj(y) x.
 // Every tile of 32 kets (one per lane) emits the same sequence of values: norm,
-// N norm, Re and Im of each <a_i> term, the diagonal n_i |psi|^2, Re and Im of
-// each <a_i^dag a_j> term with i < j (the i > j half follows by Hermiticity) and
-// of each <a_i a_j> term with i <= j (the matrix is symmetric).  A lane writes its
-// value into column `lane` of a per-warp 16 x 32 buffer; once 16 values are in,
-// lane r < 16 sums row r over the warp's 32 kets and adds the sum to the warp's
-// double-float accumulator of that value.  The sector offsets and the (N, K) ->
-// sector map are staged in shared memory when they are small.
+// N norm, then Re and Im of each slot.  A lane writes its value into column `lane`
+// of a per-warp 16 x 32 buffer; once 16 values are in, lane r < 16 sums row r over
+// the warp's 32 kets and adds the sum to the warp's double-float accumulator of
+// that value.  The sector offsets and the (N, K) -> sector map are staged in shared
+// memory when they are small, and the per-thread row scratch is sized for M modes.
 
 // x mod Q for x in (-2Q, 3Q), by conditional adds (no integer division)
 __device__ __forceinline__ int mod_small(int x, int M) {
@@ -588,11 +591,37 @@ __device__ __forceinline__ int64_t rank_moved(const Tables& t, const View& v, co
   return Dt - 1 - sum;
 }
 
-// number of values a tile emits
-__host__ __device__ inline int moment_values(int M) { return 2 + 3 * M + 2 * M * M; }
+// slots per ket (M a_i, M n_i, M(M-1)/2 a_i^dag a_j with i < j, M(M+1)/2 a_i a_j
+// with i <= j) and values a tile emits (norm, N norm, Re and Im of every slot)
+__host__ __device__ inline int moment_slots(int M) { return 2 * M + M * M; }
+__host__ __device__ inline int moment_values(int M) { return 2 + 2 * moment_slots(M); }
+
+enum { kSlotA = 0, kSlotN = 1, kSlotAdA = 2, kSlotAA = 3 };
+
+// kind | i << 8 | j << 16 of slot s
+__device__ inline uint32_t moment_slot_desc(int s, int M) {
+  if (s < M) return kSlotA | (uint32_t)s << 8 | (uint32_t)s << 16;
+  s -= M;
+  if (s < M) return kSlotN | (uint32_t)s << 8 | (uint32_t)s << 16;
+  s -= M;
+  int i = 0;
+  if (s < M * (M - 1) / 2) {
+    while (s >= M - 1 - i) {
+      s -= M - 1 - i;
+      ++i;
+    }
+    return kSlotAdA | (uint32_t)i << 8 | (uint32_t)(i + 1 + s) << 16;
+  }
+  s -= M * (M - 1) / 2;
+  while (s >= M - i) {
+    s -= M - i;
+    ++i;
+  }
+  return kSlotAA | (uint32_t)i << 8 | (uint32_t)(i + s) << 16;
+}
 
 // moment slot(s) of value e: out[k1] += x and, when k2 >= 0, out[k2] += s2 x
-__device__ inline void moment_fold(int e, int M, int& k1, int& k2, double& s2) {
+__device__ inline void moment_fold(int e, uint32_t desc, int M, int& k1, int& k2, double& s2) {
   const int oA = 4, oM = 4 + 2 * M, oAA = 4 + 2 * M + 2 * M * M;
   k2 = -1;
   s2 = 1.0;
@@ -600,38 +629,18 @@ __device__ inline void moment_fold(int e, int M, int& k1, int& k2, double& s2) {
     k1 = e;
     return;
   }
-  e -= 2;
-  if (e < 2 * M) {
-    k1 = oA + e;
-    return;
-  }
-  e -= 2 * M;
-  if (e < M) {
-    k1 = oM + 2 * (e * M + e);
-    return;
-  }
-  e -= M;
-  if (e < M * (M - 1)) {
-    int u = e >> 1, i = 0;
-    const int part = e & 1;
-    while (u >= M - 1 - i) {
-      u -= M - 1 - i;
-      ++i;
-    }
-    const int j = i + 1 + u;
+  const int part = (e - 2) & 1, kind = desc & 0xff, i = (desc >> 8) & 0xff, j = (desc >> 16) & 0xff;
+  if (kind == kSlotA) {
+    k1 = oA + 2 * i + part;
+  } else if (kind == kSlotN) {
+    k1 = oM + 2 * (i * M + i) + part;  // the imaginary part is zero
+  } else if (kind == kSlotAdA) {
     k1 = oM + 2 * (i * M + j) + part;
     k2 = oM + 2 * (j * M + i) + part;  // <a_j^dag a_i> = conj <a_i^dag a_j>
     s2 = part ? -1.0 : 1.0;
-    return;
+  } else {
+    k1 = oAA + 2 * (i * M + j) + part;
   }
-  e -= M * (M - 1);
-  int u = e >> 1, i = 0;
-  const int part = e & 1;
-  while (u >= M - i) {
-    u -= M - i;
-    ++i;
-  }
-  k1 = oAA + 2 * (i * M + i + u) + part;
 }
 
 constexpr int kTrRows = 16;    // values per flush of the per-warp transpose buffer
@@ -662,21 +671,30 @@ __device__ __forceinline__ int find_sector_in(const int64_t* off, int n, int64_t
 // first byte of the image the double-float moments kernel stages in shared memory
 __host__ __device__ inline int moments_from(const Tables& t, bool exact) { return exact ? t.o_sqrt : t.o_E; }
 
+// Row scratch of a moments CTA sized for M modes: idx [M][kBlock], pe [M][kBlock],
+// occ [M][kBlock] (setup_row and rank_moved touch modes below M only).
+__host__ __device__ inline size_t row_scratch_m_bytes(int M) { return ((size_t)M * kBlock * 9 + 15) & ~(size_t)15; }
+__device__ __forceinline__ RowScratch row_scratch_m(unsigned char* base, int M) {
+  RowScratch r;
+  r.idx = reinterpret_cast<int32_t*>(base);
+  r.pe = r.idx + M * kBlock;
+  r.occ = reinterpret_cast<uint8_t*>(r.pe + M * kBlock);
+  return r;
+}
+
 template <bool EXACT>
 __global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, const float4* psif, double* partial,
                                                              int nmom, int sec_smem, int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int from = moments_from(t, EXACT);
-  load_blob_from(t, smem_raw, from);
-  unsigned char* smem = smem_raw - from;
-  View v = view_at(t, smem);
-  v.cnt = reinterpret_cast<const uint32_t*>(t.blob + t.o_cnt);  // fill counts stay in global memory
-  if (EXACT) v.E = reinterpret_cast<const int32_t*>(t.blob + t.o_E);  // and the (large) ranking table
-  const float2* sqf = reinterpret_cast<const float2*>(smem + t.o_sqf);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, M = t.M, Q = t.Q;
+  const int nslot = moment_slots(M);
   unsigned char* cur = smem_raw + ((t.blob_bytes - from + 15) & ~15);
-  const RowScratch rs = row_scratch(cur);
-  cur += (kRowScratchBytes + 15) & ~15;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, M = t.M;
+  const RowScratch rs = row_scratch_m(cur, M);
+  cur += row_scratch_m_bytes(M);
+  uint32_t* slot_tab = reinterpret_cast<uint32_t*>(cur);
+  cur += ((size_t)nslot * 4 + 15) & ~(size_t)15;
+  for (int k = tid; k < nslot; k += kBlock) slot_tab[k] = moment_slot_desc(k, M);
   const int64_t* soff = t.sec_off;
   const int32_t* sof = t.sec_of;
   if (sec_smem) {
@@ -684,8 +702,8 @@ __global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, cons
     for (int k = tid; k <= t.n_sectors; k += kBlock) o[k] = __ldg(t.sec_off + k);
     cur += (sizeof(int64_t) * (size_t)(t.n_sectors + 1) + 15) & ~(size_t)15;
     int32_t* f = reinterpret_cast<int32_t*>(cur);
-    for (int k = tid; k < (t.nmax + 1) * t.Q; k += kBlock) f[k] = __ldg(t.sec_of + k);
-    cur += (sizeof(int32_t) * (size_t)(t.nmax + 1) * t.Q + 15) & ~(size_t)15;
+    for (int k = tid; k < (t.nmax + 1) * Q; k += kBlock) f[k] = __ldg(t.sec_of + k);
+    cur += (sizeof(int32_t) * (size_t)(t.nmax + 1) * Q + 15) & ~(size_t)15;
     soff = o;
     sof = f;
   }
@@ -695,7 +713,12 @@ __global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, cons
   float2* wb = tr + warp * kTrRows * kTrStride;
   float2* wa = wacc + warp * nval_pad;
   for (int k = lane; k < nval_pad; k += 32) wa[k] = make_float2(0.f, 0.f);
-  __syncthreads();
+  load_blob_from(t, smem_raw, from);  // ends with a CTA barrier
+  unsigned char* smem = smem_raw - from;
+  View v = view_at(t, smem);
+  v.cnt = reinterpret_cast<const uint32_t*>(t.blob + t.o_cnt);  // fill counts stay in global memory
+  if (EXACT) v.E = reinterpret_cast<const int32_t*>(t.blob + t.o_E);  // and the (large) ranking table
+  const float2* sqf = reinterpret_cast<const float2*>(smem + t.o_sqf);
   const dfl zero{0.f, 0.f};
 
   int ecount = 0;  // warp-uniform: values emitted in this tile
@@ -720,11 +743,14 @@ __global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, cons
     }
     __syncwarp();
   };
-  auto emit = [&](dfl x) {
-    wb[(ecount % kTrRows) * kTrStride + lane] = make_float2(x.h, x.l);
-    ++ecount;
+  // writes the pair (x0, x1) as the next two values
+  auto emit2 = [&](dfl x0, dfl x1) {
+    wb[(ecount % kTrRows) * kTrStride + lane] = make_float2(x0.h, x0.l);
+    wb[((ecount + 1) % kTrRows) * kTrStride + lane] = make_float2(x1.h, x1.l);
+    ecount += 2;
     if (ecount % kTrRows == 0) flush(kTrRows, ecount - kTrRows);
   };
+  static_assert(kTrRows % 2 == 0, "values are emitted in pairs");
 
   for (int64_t base = (int64_t)blockIdx.x * kBlock; base < t.total; base += (int64_t)gridDim.x * kBlock) {
     const int64_t g = base + tid;
@@ -745,85 +771,63 @@ __global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, cons
     const uint8_t* occ = rs.occ + tid;
     ecount = 0;
     const dfl p2 = df_add(df_mul(xr, xr), df_mul(xi, xi));
-    emit(p2);
-    emit(df_mul(p2, dfl{(float)N, 0.f}));
-    // emits c conj(y) x for the target ket tg
-    auto contrib = [&](bool has, int64_t tg, dfl c) {
-      dfl cr = zero, ci = zero;
-      if (has && (tg < 0 || tg >= t.total)) {
-        atomicOr(status, 1);
-        has = false;
+    emit2(p2, df_mul(p2, dfl{(float)N, 0.f}));
+    for (int sl = 0; sl < nslot; ++sl) {
+      const uint32_t d = slot_tab[sl];
+      const int kind = d & 0xff, i = (d >> 8) & 0xff, j = (d >> 16) & 0xff;
+      if (kind == kSlotN) {  // <n_i>: no other ket involved
+        emit2(df_mul(p2, dfl{(float)(live ? occ[i * kBlock] : 0), 0.f}), zero);
+        continue;
       }
+      // the slot's occupation changes and the two square-root factors of its coefficient
+      int e0 = i, dn0 = -1, e1 = i, dn1 = 0, a0 = 0, a1 = 1;
+      if (live) {
+        const int ni = occ[i * kBlock], nj = occ[j * kBlock];
+        if (kind == kSlotA) {
+          a0 = ni;  // sqrt(n_i)
+        } else if (kind == kSlotAdA) {  // annihilate j, create i (i < j)
+          e0 = j;
+          e1 = i;
+          dn1 = 1;
+          a0 = nj;
+          a1 = ni + 1;
+        } else if (i == j) {  // a_i a_i
+          dn0 = -2;
+          a0 = ni;
+          a1 = ni - 1;
+        } else {
+          e1 = j;
+          dn1 = -1;
+          a0 = ni;
+          a1 = nj;
+        }
+      }
+      const int dN = dn0 + dn1, dK = dn0 * e0 + dn1 * e1;
+      bool has = live && a0 >= 1 && a1 >= 1;  // the ket survives the annihilations
+      int64_t tg = 0;
       if (has) {
+        const int sid = sof[(N + dN) * Q + mod_small(K + dK, Q)];
+        has = sid >= 0;
+        if (has) {
+          const int64_t off = soff[sid], D = soff[sid + 1] - off;
+          tg = off + rank_moved(t, v, rs, 2, e0, dn0, e1, dn1, D);
+          if (tg < 0 || tg >= t.total) {
+            atomicOr(status, 1);
+            has = false;
+          }
+        }
+      }
+      dfl cr = zero, ci = zero;
+      if (has) {
+        const float2 f0 = sqf[a0], f1 = sqf[a1];
+        const dfl c = df_mul(dfl{f0.x, f0.y}, dfl{f1.x, f1.y});
         const float4 y = psif[tg];
         const dfl yr = df_re(y), yi = df_im(y);
         cr = df_mul(c, df_add(df_mul(yr, xr), df_mul(yi, xi)));
         ci = df_mul(c, df_add(df_mul(yr, xi), df_neg(df_mul(yi, xr))));
       }
-      emit(cr);
-      emit(ci);
-    };
-    auto sq = [&](int k) {
-      const float2 f = sqf[k];
-      return dfl{f.x, f.y};
-    };
-    // <a_i>: target (N - 1, K - i)
-    for (int i = 0; i < M; ++i) {
-      bool has = false;
-      int64_t tg = 0;
-      dfl c = zero;
-      if (live && occ[i * kBlock] >= 1) {
-        const int sid = sof[(N - 1) * t.Q + mod_small(K - i, t.Q)];
-        if (sid >= 0) {
-          const int64_t off = soff[sid], D = soff[sid + 1] - off;
-          tg = off + rank_moved(t, v, rs, 1, i, -1, 0, 0, D);
-          c = sq(occ[i * kBlock]);
-          has = true;
-        }
-      }
-      contrib(has, tg, c);
+      emit2(cr, ci);
     }
-    // <a_i^dag a_i> = n_i
-    for (int i = 0; i < M; ++i) emit(df_mul(p2, dfl{(float)occ[i * kBlock], 0.f}));
-    // <a_i^dag a_j>, i < j: target (N, K + i - j)
-    for (int i = 0; i < M; ++i)
-      for (int j = i + 1; j < M; ++j) {
-        bool has = false;
-        int64_t tg = 0;
-        dfl c = zero;
-        if (live && occ[j * kBlock] >= 1) {
-          const int sid = sof[N * t.Q + mod_small(K - j + i, t.Q)];
-          if (sid >= 0) {
-            const int64_t off = soff[sid], D = soff[sid + 1] - off;
-            tg = off + rank_moved(t, v, rs, 2, j, -1, i, 1, D);
-            c = df_mul(sq(occ[j * kBlock]), sq(occ[i * kBlock] + 1));
-            has = true;
-          }
-        }
-        contrib(has, tg, c);
-      }
-    // <a_i a_j>, i <= j: target (N - 2, K - i - j)
-    for (int i = 0; i < M; ++i)
-      for (int j = i; j < M; ++j) {
-        bool has = false;
-        int64_t tg = 0;
-        dfl c = zero;
-        if (live && N >= 2) {
-          const int ni = occ[i * kBlock], nj = occ[j * kBlock];
-          const bool ok = (i == j) ? (ni >= 2) : (ni >= 1 && nj >= 1);
-          if (ok) {
-            const int sid = sof[(N - 2) * t.Q + mod_small(K - i - j, t.Q)];
-            if (sid >= 0) {
-              const int64_t off = soff[sid], D = soff[sid + 1] - off;
-              tg = off + ((i == j) ? rank_moved(t, v, rs, 1, i, -2, 0, 0, D)
-                                   : rank_moved(t, v, rs, 2, i, -1, j, -1, D));
-              c = (i == j) ? df_mul(sq(ni), sq(ni - 1)) : df_mul(sq(ni), sq(nj));
-              has = true;
-            }
-          }
-        }
-        contrib(has, tg, c);
-      }
     if (ecount % kTrRows) flush(ecount % kTrRows, ecount - ecount % kTrRows);
   }
   __syncthreads();
@@ -838,7 +842,7 @@ __global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, cons
         const double x = (double)a0.x + (double)a0.y;
         int k1, k2;
         double s2;
-        moment_fold(e, M, k1, k2, s2);
+        moment_fold(e, e < 2 ? 0u : slot_tab[(e - 2) >> 1], M, k1, k2, s2);
         acc[k1] += x;
         if (k2 >= 0) acc[k2] += s2 * x;
       }
@@ -1288,7 +1292,7 @@ int launch_moments(Space& s, const void* d_psi, double* out_host, void* stream) 
   const int sec_smem = mom_sec_bytes(s.t) <= kMomSecSmemMax ? 1 : 0;
   const bool ex = s.t.exact != 0;
   const size_t smem = ((size_t)(s.t.blob_bytes - moments_from(s.t, ex) + 15) & ~(size_t)15) +
-                      ((kRowScratchBytes + 15) & ~15) +
+                      row_scratch_m_bytes(s.M) + (((size_t)moment_slots(s.M) * 4 + 15) & ~(size_t)15) +
                       (sec_smem ? mom_sec_bytes(s.t) : 0) + tr_bytes +
                       (size_t)(kBlock / 32) * ((moment_values(s.M) + 31) & ~31) * sizeof(float2);
   int grid = 0;
