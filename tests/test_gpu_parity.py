@@ -59,11 +59,17 @@ def _case(name):
     if name == "M5_N40_deep":
         M = 5
         return M, wl.dispersion_quadratic(M), wl.contact_coupling(M, -0.1), 40, 40, [1]
+    if name == "M16_max_modes":  # QB_MAX_MODES (even M: labels 0..15), every P, N up to 3
+        M = 16
+        return M, wl.dispersion_abs(M), wl.contact_coupling(M, 0.05), 0, 3, None
+    if name == "M13_generic":  # odd M without a specialised kernel
+        M = 13
+        return M, wl.dispersion_quadratic(M), wl.long_range_coupling(M, 0.02), 4, 4, [0, 6]
     raise KeyError(name)
 
 
 CASES = ["M5_N6_contact", "M7_N9_allP", "M9_long_range", "M5_complex_hermitian", "M3_multi_sector", "M1_kerr",
-         "M4_even_paper", "M11_N6", "M5_N40_deep"]
+         "M4_even_paper", "M11_N6", "M5_N40_deep", "M16_max_modes", "M13_generic"]
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -447,3 +453,39 @@ def test_squeezing_times_match_oracle():
     for key in ("t_sqz", "t_min", "v_min"):
         assert abs(got[key] - exp[key]) <= 1e-6, key
     assert 0.8 < got["t_sqz"] * abs(chi) / 0.05 < 1.6
+
+
+@pytest.mark.parametrize("name", ["M16_max_modes", "M13_generic"])
+def test_evolution_at_the_mode_limits(name):
+    """RK4 on the largest mode count and on an odd M without a specialised kernel."""
+    M, w, L, n0, n1, pl = _case(name)
+    qs, os_ = pair(M, w, L, n0, n1, pl)
+    x = random_state(qs.total, 9)
+    psi = to_dev(x)
+    qs.evolve(psi, 2e-3, 25)
+    assert rel_err(to_host(psi), orc.rk4(os_, w, L, x, 2e-3, 25)) <= STATE_TOL
+
+
+def test_degenerate_inputs():
+    """Zero steps leave the state untouched; a space of the single empty ket (N = 0)
+    evolves by the phase of its zero energy, i.e. not at all; an H psi of the zero
+    vector is zero."""
+    import paper_2111_00050_gb300 as qb
+
+    M = 5
+    w = wl.dispersion_quadratic(M)
+    L = wl.contact_coupling(M, -0.1)
+    qs = qb.Space(M, w, L, 0, 4)
+    x = random_state(qs.total, 2)
+    psi = to_dev(x)
+    qs.evolve(psi, 1e-3, 0)
+    assert bool((to_host(psi) == x).all())
+    out = qs.empty_state()
+    qs.hpsi(to_dev(np.zeros(qs.total)), out)
+    assert not to_host(out).any()
+    q0 = qb.Space(M, w, L, 0, 0)
+    assert q0.total == 1 and q0.n_sectors == 1
+    p0 = q0.empty_state()
+    q0.init_number([0] * M, p0)
+    q0.evolve(p0, 1e-3, 70)
+    assert to_host(p0)[0] == 1.0
