@@ -694,7 +694,33 @@ __global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, cons
   cur += row_scratch_m_bytes(M);
   uint32_t* slot_tab = reinterpret_cast<uint32_t*>(cur);
   cur += ((size_t)nslot * 4 + 15) & ~(size_t)15;
-  for (int k = tid; k < nslot; k += kBlock) slot_tab[k] = moment_slot_desc(k, M);
+  // per slot, ket-independent: kind, the occupation changes (e0, dn0), (e1, dn1), and
+  // the second square-root argument a1 = m1 n_{e1} + c1 (the first is n_{e0})
+  char4* slot_op = reinterpret_cast<char4*>(cur);  // [nslot][2]
+  cur += ((size_t)nslot * 8 + 15) & ~(size_t)15;
+  for (int k = tid; k < nslot; k += kBlock) {
+    const uint32_t d = moment_slot_desc(k, M);
+    slot_tab[k] = d;
+    const int kind = d & 0xff, i = (d >> 8) & 0xff, j = (d >> 16) & 0xff;
+    int e0 = i, dn0 = -1, e1 = i, dn1 = 0, m1 = 0, c1 = 1;  // a_i: sqrt(n_i)
+    if (kind == kSlotAdA) {  // annihilate j, create i: sqrt(n_j) sqrt(n_i + 1)
+      e0 = j;
+      e1 = i;
+      dn1 = 1;
+      m1 = 1;
+    } else if (kind == kSlotAA && i == j) {  // sqrt(n_i) sqrt(n_i - 1)
+      dn0 = -2;
+      m1 = 1;
+      c1 = -1;
+    } else if (kind == kSlotAA) {  // sqrt(n_i) sqrt(n_j)
+      e1 = j;
+      dn1 = -1;
+      m1 = 1;
+      c1 = 0;
+    }
+    slot_op[2 * k] = make_char4((char)kind, (char)e0, (char)dn0, (char)e1);
+    slot_op[2 * k + 1] = make_char4((char)dn1, (char)m1, (char)c1, 0);
+  }
   const int64_t* soff = t.sec_off;
   const int32_t* sof = t.sec_of;
   if (sec_smem) {
@@ -773,35 +799,14 @@ __global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, cons
     const dfl p2 = df_add(df_mul(xr, xr), df_mul(xi, xi));
     emit2(p2, df_mul(p2, dfl{(float)N, 0.f}));
     for (int sl = 0; sl < nslot; ++sl) {
-      const uint32_t d = slot_tab[sl];
-      const int kind = d & 0xff, i = (d >> 8) & 0xff, j = (d >> 16) & 0xff;
+      const char4 o0 = slot_op[2 * sl], o1 = slot_op[2 * sl + 1];
+      const int kind = o0.x, e0 = o0.y, dn0 = o0.z, e1 = o0.w, dn1 = o1.x;
       if (kind == kSlotN) {  // <n_i>: no other ket involved
-        emit2(df_mul(p2, dfl{(float)(live ? occ[i * kBlock] : 0), 0.f}), zero);
+        emit2(df_mul(p2, dfl{(float)(live ? occ[e0 * kBlock] : 0), 0.f}), zero);
         continue;
       }
-      // the slot's occupation changes and the two square-root factors of its coefficient
-      int e0 = i, dn0 = -1, e1 = i, dn1 = 0, a0 = 0, a1 = 1;
-      if (live) {
-        const int ni = occ[i * kBlock], nj = occ[j * kBlock];
-        if (kind == kSlotA) {
-          a0 = ni;  // sqrt(n_i)
-        } else if (kind == kSlotAdA) {  // annihilate j, create i (i < j)
-          e0 = j;
-          e1 = i;
-          dn1 = 1;
-          a0 = nj;
-          a1 = ni + 1;
-        } else if (i == j) {  // a_i a_i
-          dn0 = -2;
-          a0 = ni;
-          a1 = ni - 1;
-        } else {
-          e1 = j;
-          dn1 = -1;
-          a0 = ni;
-          a1 = nj;
-        }
-      }
+      const int a0 = live ? occ[e0 * kBlock] : 0;
+      const int a1 = o1.y ? occ[e1 * kBlock] + o1.z : o1.z;
       const int dN = dn0 + dn1, dK = dn0 * e0 + dn1 * e1;
       bool has = live && a0 >= 1 && a1 >= 1;  // the ket survives the annihilations
       int64_t tg = 0;
@@ -1293,6 +1298,7 @@ int launch_moments(Space& s, const void* d_psi, double* out_host, void* stream) 
   const bool ex = s.t.exact != 0;
   const size_t smem = ((size_t)(s.t.blob_bytes - moments_from(s.t, ex) + 15) & ~(size_t)15) +
                       row_scratch_m_bytes(s.M) + (((size_t)moment_slots(s.M) * 4 + 15) & ~(size_t)15) +
+                      (((size_t)moment_slots(s.M) * 8 + 15) & ~(size_t)15) +
                       (sec_smem ? mom_sec_bytes(s.t) : 0) + tr_bytes +
                       (size_t)(kBlock / 32) * ((moment_values(s.M) + 31) & ~31) * sizeof(float2);
   int grid = 0;
