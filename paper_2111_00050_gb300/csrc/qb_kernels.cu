@@ -566,29 +566,29 @@ __device__ __forceinline__ int mod_small(int x, int M) {
   return x;
 }
 
-// rank of the ket reached by changing mode e0 by dn0 and (nch = 2) mode e1 by dn1
+// rank of the ket reached by changing mode e0 by dn0 and (nch = 2) mode e1 by dn1.
+// The suffix state at mode m holds the changes of the modes >= m, so the shift of
+// its table index is constant on three runs of m: none above hi = max(e0, e1) (the
+// row's own prefix sums), the change at hi alone on (lo, hi], both on [1, lo].
 __device__ __forceinline__ int64_t rank_moved(const Tables& t, const View& v, const RowScratch& rs, int nch, int e0,
                                               int dn0, int e1, int dn1, int64_t Dt) {
   const int M = t.M, Q = t.Q, tid = threadIdx.x, twoQ = 2 * Q;
-  if (nch < 2) {
-    e1 = 0;
+  if (nch < 2 || dn1 == 0) {
+    e1 = e0;
     dn1 = 0;
   }
-  const int top = max(e0, e1);
-  int64_t sum = rs.pe[(M - 1) * kBlock + tid] - rs.pe[top * kBlock + tid];
-  int dc = 0, dkm = 0;  // dkm = (momentum change) mod Q, kept in [0, Q) without a division
-  for (int m = top; m >= 1; --m) {
-    if (m == e0) {
-      dc += dn0;
-      dkm = mod_small(dkm + dn0 * m, Q);
-    }
-    if (m == e1) {
-      dc += dn1;
-      dkm = mod_small(dkm + dn1 * m, Q);
-    }
-    sum += v.E[rs.idx[m * kBlock + tid] + dc * twoQ + dkm];
+  const int hi = max(e0, e1), lo = min(e0, e1);
+  int sum = rs.pe[(M - 1) * kBlock + tid] - rs.pe[hi * kBlock + tid];
+  const int* idx = rs.idx + tid;
+  if (lo < hi) {  // two distinct modes: the one at hi alone on (lo, hi]
+    const int dh = (hi == e0) ? dn0 : dn1;
+    const int sh = dh * twoQ + mod_small(dh * hi, Q);
+    for (int m = hi; m > lo; --m) sum += v.E[idx[m * kBlock] + sh];
   }
-  return Dt - 1 - sum;
+  const int dc = dn0 + dn1;
+  const int sb = dc * twoQ + mod_small(dn0 * e0 + dn1 * e1, Q);
+  for (int m = lo; m >= 1; --m) sum += v.E[idx[m * kBlock] + sb];
+  return Dt - 1 - (int64_t)sum;
 }
 
 // slots per ket (M a_i, M n_i, M(M-1)/2 a_i^dag a_j with i < j, M(M+1)/2 a_i a_j
