@@ -489,3 +489,55 @@ def test_degenerate_inputs():
     q0.init_number([0] * M, p0)
     q0.evolve(p0, 1e-3, 70)
     assert to_host(p0)[0] == 1.0
+
+
+def test_bench_workload_full_size_sampled_rows_and_one_step():
+    """The benchmark's workload at full size (M=7 coherent, n_tot=16, N <= 40: 281
+    sectors, 62,891,499 kets) in the launch configuration the benchmark times:
+    sampled rows of H psi (FP64 kernel) against the oracle's per-row application in
+    three sectors (the smallest, the coherent peak N = 16 and the largest N = 40),
+    then one RK4 step of the double-float batched path (autotuned resident
+    threshold, every sector per launch) against the classic four stages composed
+    from that FP64 H psi, and the norm after the step."""
+    import torch
+
+    import paper_2111_00050_gb300 as qb
+
+    W = wl.batched_coherent()
+    qs = qb.Space(W.M, W.w, W.L, 0, W.n_max)
+    assert qs.total == 62891499 and qs.n_sectors == 281
+    psi = qs.empty_state()
+    qs.init_coherent(W.z, psi)
+    out = qs.empty_state()
+    qs.hpsi(psi, out)
+    x_host = to_host(psi)
+    rng = np.random.default_rng(17)
+    for N, P in ((1, 0), (16, 0), (40, 3)):
+        s = qs.sectors.index((N, P))
+        off, dim = int(qs.offsets[s]), int(qs.dims[s])
+        os_ = orc.Space(W.M, [(N, P)])
+        assert os_.total == dim
+        rows = np.unique(np.concatenate([[0, dim - 1], rng.choice(dim, min(dim, 64), replace=False)]))
+        ref = orc.apply_h_rows(os_, 0, W.w, W.L, x_host[off:off + dim], rows)
+        got = to_host(out[off:off + dim])[rows]
+        assert np.max(np.abs(got - ref)) <= HPSI_TOL * 10 * max(1e-300, np.max(np.abs(ref)))
+    # classic RK4 from the FP64 operator, in plain torch arithmetic
+    dt = W.dt
+
+    def A(v):
+        r = qs.empty_state()
+        qs.hpsi(v, r)
+        return -1j * dt * r
+
+    k1 = A(psi)
+    k2 = A(psi + 0.5 * k1)
+    k3 = A(psi + 0.5 * k2)
+    k4 = A(psi + k3)
+    ref = psi + (k1 + 2 * k2 + 2 * k3 + k4) / 6
+    del k1, k2, k3, k4, out
+    work = qs.workspace(1)
+    qs.autotune(dt, psi, steps=1, work=work)
+    qs.evolve(psi, dt, 1, work)
+    err = float(torch.linalg.vector_norm(psi - ref) / torch.linalg.vector_norm(ref))
+    assert err <= STATE_TOL
+    assert abs(float(torch.vdot(psi, psi).real) - 1) < 1e-12
