@@ -91,3 +91,38 @@ def test_autograd_function_returns_adjoint_gradients():
     assert _rel(s_t.grad.item(), ref[1]) <= 1e-7
     assert _rel(w_t.grad.numpy(), ref[2]) <= 1e-7
     assert _rel(z_t.grad.numpy(), ref[3]) <= 1e-7
+
+
+def test_adjoint_full_size_against_central_differences():
+    """The adjoint benchmark workload at full size (M=5, contact, complex-Gaussian
+    amplitudes with n_tot = 40, N <= 77: 390 sectors, 27,285,336 kets), 4 steps with
+    checkpoints every 2: d Q / d scale, d Q / d w_2 and d Q / d Im z_1 against central
+    differences of the loss.  After 4 steps Q and its w-derivatives are small (~5e-9),
+    so the steps are sized for the loss's rounding: h = 1e-4 for the scale, 1e-2 for
+    w, 1e-3 for z, and a relative tolerance of 1e-4 on the last two."""
+    import paper_2111_00050_gb300 as qb
+
+    W = wl.adjoint_coherent()
+    L0 = wl.contact_coupling(W.M, 1.0)
+    scale, steps = -0.1, 4
+    qs = qb.Space(W.M, W.w, L0, 0, W.n_max)
+    assert qs.total == 27285336
+    got = qs.adjoint(W.z, scale, W.dt, steps, ckpt_every=2, loss="Q")
+
+    def loss(sc=scale, ww=None, zz=None):
+        sp = qs if ww is None else qb.Space(W.M, ww, L0, 0, W.n_max)
+        return sp.adjoint(W.z if zz is None else zz, sc, W.dt, steps, ckpt_every=steps, loss="Q")["loss"]
+
+    h = 1e-4
+    fd = (loss(sc=scale + h) - loss(sc=scale - h)) / (2 * h)
+    assert abs(got["grad_scale"] - fd) <= 1e-5 * abs(fd)
+    h = 1e-2
+    e = np.zeros(W.M)
+    e[2] = h
+    fd = (loss(ww=W.w + e) - loss(ww=W.w - e)) / (2 * h)
+    assert abs(got["grad_w"][2] - fd) <= 1e-4 * abs(fd)
+    h = 1e-3
+    ez = np.zeros(W.M, dtype=np.complex128)
+    ez[1] = 1j * h
+    fd = (loss(zz=W.z + ez) - loss(zz=W.z - ez)) / (2 * h)
+    assert abs(got["grad_z"][1].imag - fd) <= 1e-4 * abs(fd)
