@@ -106,7 +106,10 @@ const char* qb_last_error(void);
  * in the order N ascending, then P ascending.  Copies and validates the model (conservation,
  * Hermiticity), builds the combinatorial ranking tables and uploads them to the
  * current device.  Limits: 1 <= M <= QB_MAX_MODES; M * bits(n_max) <= 64;
- * every sector dimension < 2^31.  *out receives the new space. */
+ * every sector dimension < 2^31; with exact momentum (M-1) n_max + 1 <= 6553
+ * (the term shifts are 16-bit), and batched sweeps (batch > 1) are not built.
+ * Errors: QB_EINVAL for a bad model or range, QB_EUNSUPPORTED beyond the limits,
+ * QB_ECUDA / QB_ENOMEM from the device set-up.  *out receives the new space. */
 int qb_sector_build(const qb_model* model, int n_min, int n_max, const int* p_list, int n_p, qb_space** out);
 
 void qb_space_free(qb_space* space);
