@@ -314,7 +314,7 @@ def squeezing_extra(qb, torch, n_list=(4, 8, 12)):
             "tau_min_log_law": {"c0": tfit[0], "c1": tfit[1]}}
 
 
-def breaktime_sweep(qb, torch, r_list=(1, 2, 3, 4, 6), chunk: int = 1000):
+def breaktime_sweep(qb, torch, r_list=(1, 2, 3, 4, 6, 8), chunk: int = 1000):
     """Sec. IV C-D's breaktime scaling with n_tot (run with --breaktime-sweep): for each
     average mode occupation r the M=5 long-range coherent system evolves with
     observables every 20 steps until Q >= 0.15 and 1 - lam_p / n_tot >= 0.1 have both
