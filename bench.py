@@ -35,9 +35,9 @@ import workloads as wl  # noqa: E402
 # (a DFMA microbenchmark measured 1.00 TFLOP/s: python -m paper_2111_00050_gb300.probe)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per ket of one stage launch (the first stage of a step), from an ncu capture
-# of the current stage kernel (batched coherent at n_tot=12: 636.2 MB read + 230.6 MB
+# of the current stage kernel (batched coherent at n_tot=12: 757.5 MB read + 232.1 MB
 # written over 15,380,937 kets); scaled by kets
-STAGE_DRAM_BYTES_PER_KET = (636.2e6 + 230.6e6) / 15380937
+STAGE_DRAM_BYTES_PER_KET = (757.470208e6 + 232.080128e6) / 15380937
 
 
 def _peaks():

@@ -514,6 +514,7 @@ void qb_space_free(qb_space* space) {
   cudaFree(sp->d_diag);
   cudaFree(sp->d_obsf);
   cudaFree(sp->d_wtab);
+  cudaFree(sp->d_occ);
   if (sp->capture_stream) cudaStreamDestroy(sp->capture_stream);
   if (sp->side_stream) cudaStreamDestroy(sp->side_stream);
   if (sp->ev_fork) cudaEventDestroy(sp->ev_fork);

@@ -63,6 +63,10 @@ struct Tables {
   // ket weights w(n) = sqrt(N! / prod_m n_m!) = prod_m sqrt(C(rem_m, n_m)), rem_m the
   // particles in modes m..M-1: entry [rem * (nmax + 1) + k] = (sqrt(C(rem, k)), its inverse)
   const double2* wtab;
+  // packed occupation vector of every ket (written with the diagonal): n_m in bits
+  // [m * occ_bits, (m + 1) * occ_bits), occ_bits the bit length of nmax
+  int occ_bits;
+  const uint64_t* occ;  // [total]
 };
 
 struct Space {
@@ -88,6 +92,7 @@ struct Space {
   float4* d_diag = nullptr;     // per ket: one-body and two-body diagonal as double-float pairs
   float4* d_obsf = nullptr;     // double-float copy of the state being observed (qb_observables)
   double2* d_wtab = nullptr;    // ket-weight factors (Tables::wtab)
+  uint64_t* d_occ = nullptr;    // packed occupation vectors (Tables::occ)
   int64_t scratch_doubles = 0;
   Tables t{};
   cudaStream_t capture_stream = nullptr;  // private stream on which RK4 chunks are captured into graphs

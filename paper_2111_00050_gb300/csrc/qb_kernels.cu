@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kBlock) to_dfw_kernel(const Tables t, const do
 }
 
 // per-ket diagonal of H, one-body and two-body parts, as double-float pairs
-__global__ void __launch_bounds__(kBlock) diag_kernel(const Tables t, float4* diag) {
+__global__ void __launch_bounds__(kBlock) diag_kernel(const Tables t, float4* diag, uint64_t* occ) {
   extern __shared__ __align__(16) unsigned char smem[];
   load_blob(t, smem);
   const View v = make_view(t, smem);
@@ -217,8 +217,10 @@ __global__ void __launch_bounds__(kBlock) diag_kernel(const Tables t, float4* di
     const int64_t D = __ldg(t.sec_off + sid + 1) - off;
     setup_row(t, v, rs, __ldg(t.sec_N + sid), __ldg(t.sec_K + sid), D, g - off);
     double dw = 0.0, dl = 0.0;
+    uint64_t word = 0;
     for (int r = 0; r < M; ++r) {
       const int nr = rs.occ[r * kBlock + tid];
+      word |= (uint64_t)nr << (r * t.occ_bits);
       dw += v.w[r] * nr;
       for (int s2 = r; s2 < M; ++s2) {
         const int ns = rs.occ[s2 * kBlock + tid] - (r == s2 ? 1 : 0);
@@ -227,6 +229,7 @@ __global__ void __launch_bounds__(kBlock) diag_kernel(const Tables t, float4* di
     }
     const dfl a = df_of(dw), b = df_of(dl);
     diag[g] = make_float4(a.h, a.l, b.h, b.l);
+    occ[g] = word;
   }
 }
 
@@ -924,6 +927,10 @@ int device_setup(Space& s) {
   QB_CUDA(cudaMemset(s.d_scratch, 0, sizeof(double) * s.scratch_doubles));
   QB_CUDA(cudaMalloc(&s.d_diag, sizeof(float4) * (size_t)t.total));
   QB_CUDA(cudaMalloc(&s.d_obsf, sizeof(float4) * (size_t)t.total));
+  QB_CUDA(cudaMalloc(&s.d_occ, sizeof(uint64_t) * (size_t)t.total));
+  t.occ_bits = 1;
+  while ((1 << t.occ_bits) <= s.nmax) ++t.occ_bits;  // M * occ_bits <= 64 (checked by qb_sector_build)
+  t.occ = s.d_occ;
   {
     // sqrt(C(rem, k)) from the exact binomial (C(77, 38) < 2^75 fits 128 bits), then
     // one rounding to double, one correctly rounded sqrt and one division
@@ -946,7 +953,7 @@ int device_setup(Space& s) {
     int grid = 0;
     int rc = persistent_grid(diag_kernel, smem, t.total, &grid);
     if (rc) return rc;
-    diag_kernel<<<grid, kBlock, smem>>>(t, s.d_diag);
+    diag_kernel<<<grid, kBlock, smem>>>(t, s.d_diag, s.d_occ);
     QB_CUDA(cudaGetLastError());
     QB_CUDA(cudaDeviceSynchronize());
   }

@@ -34,6 +34,12 @@
 #ifndef QB_UNRANK_FROM_E
 #define QB_UNRANK_FROM_E 1
 #endif
+// 1: a ket's occupations are unpacked from the packed table Tables::occ (8 B per ket
+// read, coalesced); 0: unranked through the counting table (a data-dependent walk of
+// about N + M steps per ket)
+#ifndef QB_OCC_TABLE
+#define QB_OCC_TABLE 1
+#endif
 
 namespace qb {
 
@@ -107,7 +113,7 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
   const int64_t total = t.total;  // stride between sweep members
   const int nb = t.n_ann + 2;
   constexpr int kMB = (MT > 0) ? MT : 16;
-  // ---- phase 1: each lane unranks kWarpRows/32 kets into occupations and suffix-state indices
+  // ---- phase 1: each lane unpacks (or unranks) kWarpRows/32 kets into occupations and suffix-state indices
   for (int k = lane; k < 2 * nb; k += 32) hist[k] = 0;
   int key[kWarpRows / 32];
 #pragma unroll
@@ -119,6 +125,14 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
       const int sid = find_sector(t, g);
       const int64_t off = __ldg(t.sec_off + sid);
       const int D = (int)(__ldg(t.sec_off + sid + 1) - off);
+#if QB_OCC_TABLE
+      {
+        const uint64_t word = __ldg(t.occ + g);
+        const int ob = t.occ_bits;
+        const uint32_t omask = (1u << ob) - 1u;
+        for (int m = 0; m < M; ++m) socc[m * kWarpRows + row] = (uint8_t)((uint32_t)(word >> (m * ob)) & omask);
+      }
+#else
       int rem = __ldg(t.sec_N + sid), kr = __ldg(t.sec_K + sid);
       int left = (int)(g - off);
       for (int m = 0; m < M - 1; ++m) {
@@ -147,6 +161,7 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
         kr = kk;
       }
       socc[(M - 1) * kWarpRows + row] = (uint8_t)rem;
+#endif
       int srem = 0, skr = 0, esum = 0, np = 0, n2 = 0;
       for (int m = M - 1; m >= 1; --m) {
         const int nm = socc[m * kWarpRows + row];
