@@ -105,7 +105,10 @@ const char* qb_last_error(void);
  * exact_momentum = 0, the exact (possibly negative) sum otherwise; sectors come
  * in the order N ascending, then P ascending.  Copies and validates the model (conservation,
  * Hermiticity), builds the combinatorial ranking tables and uploads them to the
- * current device.  Limits: 1 <= M <= QB_MAX_MODES; M * bits(n_max) <= 64;
+ * current device, with two per-ket tables the space owns: the diagonal of H
+ * (16 B per ket) and the occupation vector packed into 64 bits (8 B per ket),
+ * plus a double-float copy of an observed state (16 B per ket).
+ * Limits: 1 <= M <= QB_MAX_MODES; M * bits(n_max) <= 64;
  * every sector dimension < 2^31; with exact momentum (M-1) n_max + 1 <= 6553
  * (the term shifts are 16-bit), and batched sweeps (batch > 1) are not built.
  * Errors: QB_EINVAL for a bad model or range, QB_EUNSUPPORTED beyond the limits,
