@@ -652,6 +652,10 @@ constexpr int kTrStride = 33;  // row stride (float2) of that buffer
 static_assert((kBlock / 32) * kTrRows * kTrStride * sizeof(float2) >=
                   (4 + 2 * kMaxM + 4 * kMaxM * kMaxM) * sizeof(double),
               "moment row does not fit the transpose buffers");
+// 1: qb_observables runs moments_wc_kernel (lanes over the moment slots); 0: moments_df_kernel
+#ifndef QB_MOMENTS_WC
+#define QB_MOMENTS_WC 1
+#endif
 constexpr size_t kMomSecSmemMax = 16384;  // sector tables larger than this stay in global memory
 
 static size_t mom_sec_bytes(const Tables& t) {
@@ -857,6 +861,227 @@ __global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, cons
     __syncthreads();
   }
   for (int k = tid; k < nmom; k += kBlock) partial[(size_t)blockIdx.x * nmom + k] = acc[k];
+}
+
+// ------------------------------------------- warp-cooperative double-float moments
+//
+// The same sums as moments_df_kernel, organised the other way round: the lanes of
+// a warp take the entries of a slot list (entry 0 the norm and <N>, entry 1 + k
+// slot k of moment_slot_desc), and the 32 kets of a tile are visited in turn, each
+// one's amplitude, packed occupations, sector and suffix-state indices broadcast
+// by shuffle from the lane that loaded them.  A lane keeps its entries' sums in
+// double-float registers over every tile of its warp, so no value is emitted per
+// ket.  The target rank is the fixed-length sum D - 1 - sum_{m=1}^{M-1}
+// E[idx_m + shift_m]; the shift of an entry is constant on the three runs of
+// rank_moved (0 above hi, the change at hi alone on (lo, hi], both changes on
+// [1, lo]) and is tabulated per entry and mode at the start of the CTA.
+
+constexpr int kMomWarps = 8;
+constexpr int kMomBlock = 32 * kMomWarps;
+constexpr int kSlotP = 4;  // entry 0: the norm (real part) and <N> (imaginary part)
+
+__host__ __device__ inline int mom_entries(int M) { return moment_slots(M) + 1; }
+__host__ __device__ inline int mom_entries_pad(int M) { return (mom_entries(M) + 31) & ~31; }
+
+// shared memory of moments_wc_kernel after the staged table image: entry headers,
+// entry shifts [M-1][entries], the CTA's FP64 moment row
+__host__ __device__ inline size_t mom_wc_bytes(int M, int nmom) {
+  const size_t np = (size_t)mom_entries_pad(M);
+  return np * sizeof(int4) + (size_t)(M > 1 ? M - 1 : 1) * np * sizeof(int32_t) +
+         (((size_t)nmom * sizeof(double) + 15) & ~(size_t)15);
+}
+
+template <int MT, bool EXACT>
+__global__ void __launch_bounds__(kMomBlock) moments_wc_kernel(const Tables t, const float4* psif, double* partial,
+                                                               int nmom, int sec_smem, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int kMB = (MT > 0) ? MT : kMaxM;
+  constexpr int kSPL = (2 * kMB + kMB * kMB + 1 + 31) / 32;  // entries per lane
+  const int from = moments_from(t, EXACT);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int M = (MT > 0) ? MT : t.M, Q = t.Q, twoQ = 2 * Q;
+  const int nent = mom_entries(M), np = mom_entries_pad(M);
+  unsigned char* cur = smem_raw + ((t.blob_bytes - from + 15) & ~15);
+  int4* hdr = reinterpret_cast<int4*>(cur);  // kind | e0 << 8 | e1 << 16 | m1 << 24, c1, dN, dK mod Q
+  cur += (size_t)np * sizeof(int4);
+  int32_t* shf = reinterpret_cast<int32_t*>(cur);  // [M-1][np] shift of the suffix index at mode m
+  cur += (size_t)(M > 1 ? M - 1 : 1) * np * sizeof(int32_t);
+  double* row = reinterpret_cast<double*>(cur);  // [nmom]
+  cur += ((size_t)nmom * sizeof(double) + 15) & ~(size_t)15;
+  for (int s = tid; s < np; s += kMomBlock) {
+    // a0 = n_{e0}, a1 = m1 n_{e1} + c1: the operator's square-root arguments; the
+    // target changes mode e0 by dn0 and mode e1 by dn1 (kinds as in moments_df_kernel)
+    int kind = 7, e0 = 0, dn0 = 0, e1 = 0, dn1 = 0, m1 = 0, c1 = 0;
+    if (s == 0) {
+      kind = kSlotP;
+    } else if (s < nent) {
+      const uint32_t d = moment_slot_desc(s - 1, M);
+      kind = d & 0xff;
+      const int i = (d >> 8) & 0xff, j = (d >> 16) & 0xff;
+      e0 = i;
+      dn0 = -1;
+      e1 = i;
+      c1 = 1;
+      if (kind == kSlotAdA) {  // annihilate j, create i
+        e0 = j;
+        dn1 = 1;
+        m1 = 1;
+      } else if (kind == kSlotAA && i == j) {
+        dn0 = -2;
+        m1 = 1;
+        c1 = -1;
+      } else if (kind == kSlotAA) {
+        e1 = j;
+        dn1 = -1;
+        m1 = 1;
+        c1 = 0;
+      }
+    }
+    const bool moves = kind == kSlotA || kind == kSlotAdA || kind == kSlotAA;
+    const int f1 = (dn1 == 0) ? e0 : e1;  // a zero second change acts on e0
+    const int hi = max(e0, f1), lo = min(e0, f1);
+    const int dh = (hi == e0) ? dn0 : dn1;
+    const int sh = dh * twoQ + mod_small(dh * hi, Q);
+    const int dc = dn0 + dn1, dk = mod_small(dn0 * e0 + dn1 * f1, Q);
+    const int sb = dc * twoQ + dk;
+    for (int m = 1; m < M; ++m) shf[(m - 1) * np + s] = !moves ? 0 : (m > hi ? 0 : (m > lo ? sh : sb));
+    hdr[s] = make_int4(kind | (e0 << 8) | (e1 << 16) | (m1 << 24), c1, dc, dk);
+  }
+  const int64_t* soff = t.sec_off;
+  const int32_t* sof = t.sec_of;
+  if (sec_smem) {
+    int64_t* o = reinterpret_cast<int64_t*>(cur);
+    for (int k = tid; k <= t.n_sectors; k += kMomBlock) o[k] = __ldg(t.sec_off + k);
+    cur += (sizeof(int64_t) * (size_t)(t.n_sectors + 1) + 15) & ~(size_t)15;
+    int32_t* f = reinterpret_cast<int32_t*>(cur);
+    for (int k = tid; k < (t.nmax + 1) * Q; k += kMomBlock) f[k] = __ldg(t.sec_of + k);
+    soff = o;
+    sof = f;
+  }
+  for (int k = tid; k < nmom; k += kMomBlock) row[k] = 0.0;
+  load_blob_from(t, smem_raw, from);  // ends with a CTA barrier
+  unsigned char* smem = smem_raw - from;
+  View v = view_at(t, smem);
+  if (EXACT) v.E = reinterpret_cast<const int32_t*>(t.blob + t.o_E);  // the (large) ranking table stays global
+  const float2* sqf = reinterpret_cast<const float2*>(smem + t.o_sqf);
+  const int ob = t.occ_bits;
+  const uint32_t omask = (1u << ob) - 1u;
+  const int64_t total = t.total;
+  const int64_t ntiles = (total + 31) / 32;
+
+  dfl acc_r[kSPL], acc_i[kSPL];
+#pragma unroll
+  for (int r = 0; r < kSPL; ++r) acc_r[r] = acc_i[r] = dfl{0.f, 0.f};
+
+  for (int64_t tile = (int64_t)blockIdx.x * kMomWarps + warp; tile < ntiles; tile += (int64_t)gridDim.x * kMomWarps) {
+    // this lane's ket: amplitude, |x|^2, packed occupations, (N, K), suffix-state indices
+    const int64_t g = tile * 32 + lane;
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    dfl p2{0.f, 0.f};
+    uint64_t word = 0;
+    int nk = 0;
+    int idx[kMB];
+#pragma unroll
+    for (int m = 0; m < kMB; ++m) idx[m] = 0;
+    if (g < total) {
+      const int sid = find_sector_in(soff, t.n_sectors, g);
+      nk = __ldg(t.sec_N + sid) | (__ldg(t.sec_K + sid) << 8);
+      word = __ldg(t.occ + g);
+      x = psif[g];
+      p2 = df_add(df_mul(df_re(x), df_re(x)), df_mul(df_im(x), df_im(x)));
+      int srem = 0, skr = 0;
+#pragma unroll
+      for (int m = kMB - 1; m >= 1; --m) {
+        if (m < M) {
+          const int nm = (int)((uint32_t)(word >> (m * ob)) & omask);
+          srem += nm;
+          skr += m * nm;
+          while (skr >= Q) skr -= Q;
+          idx[m] = (m * t.rem_w + srem + 2) * twoQ + skr;
+        }
+      }
+    }
+    const int nt = (int)min((int64_t)32, total - tile * 32);
+    for (int j = 0; j < nt; ++j) {
+      const float4 xj = make_float4(__shfl_sync(~0u, x.x, j), __shfl_sync(~0u, x.y, j), __shfl_sync(~0u, x.z, j),
+                                    __shfl_sync(~0u, x.w, j));
+      const dfl p2j{__shfl_sync(~0u, p2.h, j), __shfl_sync(~0u, p2.l, j)};
+      const uint64_t wj = ((uint64_t)__shfl_sync(~0u, (uint32_t)(word >> 32), j) << 32) |
+                          (uint64_t)__shfl_sync(~0u, (uint32_t)word, j);
+      const int nkj = __shfl_sync(~0u, nk, j);
+      const int N = nkj & 0xff, K = nkj >> 8;
+      int id[kMB];
+#pragma unroll
+      for (int m = 1; m < kMB; ++m)
+        if (m < M) id[m] = __shfl_sync(~0u, idx[m], j);
+      const dfl xr = df_re(xj), xi = df_im(xj);
+#pragma unroll
+      for (int r = 0; r < kSPL; ++r) {
+        const int s = r * 32 + lane;
+        if (s >= nent) continue;
+        const int4 h = hdr[s];
+        const int kind = h.x & 0xff, e0 = (h.x >> 8) & 0xff, e1 = (h.x >> 16) & 0xff, m1 = (h.x >> 24) & 0xff;
+        if (kind == kSlotP) {
+          acc_r[r] = df_add(acc_r[r], p2j);
+          acc_i[r] = df_add(acc_i[r], df_mul(p2j, dfl{(float)N, 0.f}));
+          continue;
+        }
+        const int a0 = (int)((uint32_t)(wj >> (e0 * ob)) & omask);
+        if (kind == kSlotN) {
+          acc_r[r] = df_add(acc_r[r], df_mul(p2j, dfl{(float)a0, 0.f}));
+          continue;
+        }
+        const int a1 = m1 * (int)((uint32_t)(wj >> (e1 * ob)) & omask) + h.y;
+        if (a0 < 1 || a1 < 1) continue;  // the operator annihilates this ket
+        int Kt = K + h.w;
+        if (Kt >= Q) Kt -= Q;
+        const int sid = sof[(N + h.z) * Q + Kt];
+        if (sid < 0) continue;  // target sector outside the space
+        const int64_t off = soff[sid];
+        const int Dt = (int)(soff[sid + 1] - off);
+        int esum = 0;
+#pragma unroll
+        for (int m = 1; m < kMB; ++m)
+          if (m < M) esum += v.E[id[m] + shf[(m - 1) * np + s]];
+        const int rk = Dt - 1 - esum;
+        if ((unsigned)rk >= (unsigned)Dt) {
+          atomicOr(status, 1);
+          continue;
+        }
+        const float4 y = psif[off + rk];
+        const float2 f0 = sqf[a0], f1 = sqf[a1];
+        const dfl c = df_mul(dfl{f0.x, f0.y}, dfl{f1.x, f1.y});
+        const dfl yr = df_re(y), yi = df_im(y);
+        acc_r[r] = df_add(acc_r[r], df_mul(c, df_add(df_mul(yr, xr), df_mul(yi, xi))));
+        acc_i[r] = df_add(acc_i[r], df_mul(c, df_add(df_mul(yr, xi), df_neg(df_mul(yi, xr)))));
+      }
+    }
+  }
+  // the lanes' sums into the CTA's FP64 row, one warp at a time (a fixed order); the
+  // entries of a warp land on distinct moments
+  for (int w = 0; w < kMomWarps; ++w) {
+    if (warp == w) {
+#pragma unroll
+      for (int r = 0; r < kSPL; ++r) {
+        const int s = r * 32 + lane;
+        if (s < nent) {
+          const uint32_t desc = (s == 0) ? 0u : moment_slot_desc(s - 1, M);
+          for (int part = 0; part < 2; ++part) {
+            const dfl a = part ? acc_i[r] : acc_r[r];
+            const int e = (s == 0) ? part : 2 + 2 * (s - 1) + part;
+            int k1, k2;
+            double s2;
+            moment_fold(e, desc, M, k1, k2, s2);
+            const double xv = (double)a.h + (double)a.l;
+            row[k1] += xv;
+            if (k2 >= 0) row[k2] += s2 * xv;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int k = tid; k < nmom; k += kMomBlock) partial[(size_t)blockIdx.x * nmom + k] = row[k];
 }
 
 // ------------------------------------------------------------------ host side
@@ -1300,20 +1525,39 @@ int launch_moments(Space& s, const void* d_psi, double* out_host, void* stream) 
   const int nmom = nmoments(s.M);
   int rc = launch_to_df(d_psi, s.d_obsf, s.t.total, stream);
   if (rc) return rc;
-  const size_t tr_bytes = (size_t)(kBlock / 32) * kTrRows * kTrStride * sizeof(float2);
   const int sec_smem = mom_sec_bytes(s.t) <= kMomSecSmemMax ? 1 : 0;
   const bool ex = s.t.exact != 0;
-  const size_t smem = ((size_t)(s.t.blob_bytes - moments_from(s.t, ex) + 15) & ~(size_t)15) +
-                      row_scratch_m_bytes(s.M) + (((size_t)moment_slots(s.M) * 4 + 15) & ~(size_t)15) +
-                      (((size_t)moment_slots(s.M) * 8 + 15) & ~(size_t)15) +
-                      (sec_smem ? mom_sec_bytes(s.t) : 0) + tr_bytes +
-                      (size_t)(kBlock / 32) * ((moment_values(s.M) + 31) & ~31) * sizeof(float2);
+  const size_t image = (size_t)(s.t.blob_bytes - moments_from(s.t, ex) + 15) & ~(size_t)15;
   int grid = 0;
-  auto kern = ex ? moments_df_kernel<true> : moments_df_kernel<false>;
-  rc = persistent_grid(kern, smem, s.t.total, &grid);
-  if (rc) return rc;
   double* part = partial_area(s);
-  kern<<<grid, kBlock, smem, st>>>(s.t, s.d_obsf, part, nmom, sec_smem, reinterpret_cast<int*>(s.d_scratch));
+#if QB_MOMENTS_WC
+  {
+    const size_t smem = image + mom_wc_bytes(s.M, nmom) + (sec_smem ? mom_sec_bytes(s.t) : 0);
+    decltype(&moments_wc_kernel<0, false>) kern;
+    switch (s.M) {
+      case 5: kern = ex ? moments_wc_kernel<5, true> : moments_wc_kernel<5, false>; break;
+      case 7: kern = ex ? moments_wc_kernel<7, true> : moments_wc_kernel<7, false>; break;
+      case 9: kern = ex ? moments_wc_kernel<9, true> : moments_wc_kernel<9, false>; break;
+      case 11: kern = ex ? moments_wc_kernel<11, true> : moments_wc_kernel<11, false>; break;
+      default: kern = ex ? moments_wc_kernel<0, true> : moments_wc_kernel<0, false>; break;
+    }
+    rc = persistent_grid(kern, smem, s.t.total, &grid, kMomBlock);
+    if (rc) return rc;
+    kern<<<grid, kMomBlock, smem, st>>>(s.t, s.d_obsf, part, nmom, sec_smem, reinterpret_cast<int*>(s.d_scratch));
+  }
+#else
+  {
+    const size_t tr_bytes = (size_t)(kBlock / 32) * kTrRows * kTrStride * sizeof(float2);
+    const size_t smem = image + row_scratch_m_bytes(s.M) + (((size_t)moment_slots(s.M) * 4 + 15) & ~(size_t)15) +
+                        (((size_t)moment_slots(s.M) * 8 + 15) & ~(size_t)15) +
+                        (sec_smem ? mom_sec_bytes(s.t) : 0) + tr_bytes +
+                        (size_t)(kBlock / 32) * ((moment_values(s.M) + 31) & ~31) * sizeof(float2);
+    auto kern = ex ? moments_df_kernel<true> : moments_df_kernel<false>;
+    rc = persistent_grid(kern, smem, s.t.total, &grid);
+    if (rc) return rc;
+    kern<<<grid, kBlock, smem, st>>>(s.t, s.d_obsf, part, nmom, sec_smem, reinterpret_cast<int*>(s.d_scratch));
+  }
+#endif
   QB_CUDA(cudaGetLastError());
   double* fin = final_area(s);
   reduce_partials_kernel<<<(nmom + 127) / 128, 128, 0, st>>>(part, grid, nmom, fin);
