@@ -539,9 +539,14 @@ def main():
     # ---- end to end through the public API with host buffers
     host_in = torch.empty(qs.total, dtype=torch.complex128).pin_memory()
     host_in.copy_(psi.cpu())
+    # one untimed pass first: the first call of a kernel pays its module load and
+    # launch-attribute set-up
+    psi.copy_(host_in, non_blocking=True)
+    qs.evolve(psi, W.dt, 1, work)
+    qs.observables(psi)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    k_e2e = max(1, min(args.steps, 3))
+    k_e2e = max(1, min(args.steps, 5))
     for _ in range(k_e2e):
         psi.copy_(host_in, non_blocking=True)
         qs.evolve(psi, W.dt, 1, work)
