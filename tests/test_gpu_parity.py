@@ -455,6 +455,26 @@ def test_squeezing_times_match_oracle():
     assert 0.8 < got["t_sqz"] * abs(chi) / 0.05 < 1.6
 
 
+@pytest.mark.parametrize("name", CASES)
+def test_observables_match_oracle(name):
+    """The moments of a random normalised state on every parity case: the kernels
+    specialised for M = 5, 7, 9, 11 and the generic one (M = 1, 3, 4, 13, 16),
+    complex couplings, single and multi-sector spaces."""
+    M, w, L, n0, n1, pl = _case(name)
+    qs, os_ = pair(M, w, L, n0, n1, pl)
+    x = random_state(qs.total, 17)
+    x = x / np.linalg.norm(x)
+    ob = qs.observables(to_dev(x))
+    ro = orc.observables(os_, x, w, L)
+    n = max(1.0, ro["n_tot"])
+    assert abs(ob["norm"] - 1) <= 1e-12
+    assert abs(ob["n_tot"] - ro["n_tot"]) <= OBS_TOL * n
+    np.testing.assert_allclose(ob["a"], ro["a"], atol=OBS_TOL * n)
+    np.testing.assert_allclose(ob["Mij"], ro["Mij"], atol=OBS_TOL * n)
+    np.testing.assert_allclose(ob["aa"], ro["aa"], atol=OBS_TOL * n)
+    assert abs(ob["H"] - ro["H"]) <= OBS_TOL * max(1, abs(ro["H"]))
+
+
 @pytest.mark.parametrize("name", ["M16_max_modes", "M13_generic"])
 def test_evolution_at_the_mode_limits(name):
     """RK4 on the largest mode count and on an odd M without a specialised kernel."""
