@@ -727,3 +727,178 @@ def test_oracle_adjoint_gradient_matches_finite_differences(kind):
             e[k] = unit * h
             fd = (loss_of(scale, w, z + e) - loss_of(scale, w, z - e)) / (2 * h)
             assert abs(part - fd) < 1e-7 * max(1, abs(fd))
+
+
+# ------------------------------------ principal-mode squeezing with a complex xi
+
+def principal_kerr_state(space, phi, a0, w, Lk, t):
+    """A state of one effective mode b = (a_0 + e^{i phi} a_1) / sqrt(2) (the
+    other modes empty) whose amplitudes on |n>_b = (b^dag)^n / sqrt(n!) |0> are
+    the single-mode Kerr ones c_n(t) = e^{-|a0|^2/2} a0^n / sqrt(n!)
+    e^{-i (w n + Lk n (n - 1)) t}.  Expanded in the Fock basis of the M modes,
+    (b^dag)^n / sqrt(n!) |0> = 2^{-n/2} sum_k sqrt(C(n, k)) e^{-i phi (n - k)}
+    |k, n - k, 0, ...>, so the state spreads over every (N, P) sector it meets."""
+    psi = np.zeros(space.total, dtype=np.complex128)
+    n_max = int(space.basis.sum(axis=1).max())
+    for n in range(n_max + 1):
+        cn = (np.exp(-abs(a0) ** 2 / 2) * a0 ** n / math.sqrt(math.factorial(n))
+              * np.exp(-1j * (w * n + Lk * n * (n - 1)) * t))
+        for k in range(n + 1):
+            occ = np.zeros(space.M, dtype=np.int32)
+            occ[0], occ[1] = k, n - k
+            psi[space.index_of(occ)] += cn * 2.0 ** (-n / 2) * math.sqrt(math.comb(n, k)) * np.exp(-1j * phi * (n - k))
+    return psi
+
+
+def principal_squeezing_errors(ob, phi, a0, w, Lk, t):
+    """Deviations of an observables dict from the one-mode closed forms of b:
+    V_-(a^p) (Eq. generalVminus with a^p of Eq. a_op), lam_p = <b^dag b> = |a0|^2
+    and xi^p ~ (1, e^{i phi}, 0, ...) / sqrt(2) up to a phase."""
+    n0 = abs(a0) ** 2
+    b = a0 * np.exp(-1j * w * t) * np.exp(n0 * (np.exp(-2j * Lk * t) - 1))
+    bb = a0 ** 2 * np.exp(-1j * (2 * w + 2 * Lk) * t) * np.exp(n0 * (np.exp(-4j * Lk * t) - 1))
+    v_ref = 1 + 2 * (n0 - abs(b) ** 2) - 2 * abs(bb - b ** 2)
+    xi_ref = np.zeros(len(ob["xi"]), dtype=np.complex128)
+    xi_ref[0], xi_ref[1] = 1 / math.sqrt(2), np.exp(1j * phi) / math.sqrt(2)
+    return (abs(ob["Vminus_p"] - v_ref), abs(ob["lam_p"] - n0), abs(abs(np.vdot(xi_ref, ob["xi"])) - 1))
+
+
+PRINCIPAL_CASES = [(1.1, 1.3 * np.exp(0.4j), 0.7, 0.13, 0.9), (2.3, 0.9 - 1.1j, -0.2, -0.05, 3.1)]
+
+
+@pytest.mark.parametrize("phi,a0,w,Lk,t", PRINCIPAL_CASES)
+def test_principal_mode_squeezing_with_complex_eigenvector(phi, a0, w, Lk, t):
+    """Eq. (a_op) with a non-real principal eigenvector: for a state that lives in
+    the single mode b = (a_0 + e^{i phi} a_1) / sqrt(2), M_ij = <b^dag b> v_i^* v_j
+    with v = (1, e^{-i phi}, 0) / sqrt(2) conjugated, so xi^p = (1, e^{i phi}, 0) /
+    sqrt(2) (Sec. II D: xi^p is z^* / |z| for M_ij = z_i^* z_j) and a^p = b.
+    V_-(a^p) must then equal the single-mode Kerr closed form; a conjugate slip on
+    xi in either <dO^dag dO> or Var O gives V_- of another operator."""
+    M = 3
+    space = orc.Space(M, orc.all_sectors(M, 0, 34))
+    psi = principal_kerr_state(space, phi, a0, w, Lk, t)
+    assert abs(np.vdot(psi, psi).real - 1) < 1e-13  # Poisson tail beyond N = 34 below 1e-15
+    ob = orc.observables(space, psi)
+    dv, dl, dx = principal_squeezing_errors(ob, phi, a0, w, Lk, t)
+    assert dv < 1e-11 and dl < 1e-11 and dx < 1e-11
+    # xi is not real up to a phase: its two components differ in phase by phi
+    assert abs(ob["xi"][1] / ob["xi"][0] - np.exp(1j * phi)) < 1e-9 and abs(np.sin(phi)) > 0.5
+    # several (N, P) sectors carry weight: the three residues of P and many N
+    held = {space.sectors[s] for s in range(len(space.sectors)) if np.linalg.norm(psi[space.sector_slice(s)]) > 1e-3}
+    assert len({P for _, P in held}) == M and len({N for N, _ in held}) > 5
+
+
+def test_principal_mode_pin_rejects_conjugated_eigenvector(monkeypatch):
+    """The pin above fails when the oracle's principal eigenvector is conjugated
+    (a^p = sum_k conj(xi_k) a_k instead of Eq. a_op): planted in the oracle by
+    conjugating what its eigensolver returns."""
+    phi, a0, w, Lk, t = PRINCIPAL_CASES[0]
+    space = orc.Space(3, orc.all_sectors(3, 0, 34))
+    psi = principal_kerr_state(space, phi, a0, w, Lk, t)
+    eigh = np.linalg.eigh
+    monkeypatch.setattr(orc.np.linalg, "eigh", lambda m: (eigh(m)[0], np.conj(eigh(m)[1])))
+    dv, _, dx = principal_squeezing_errors(orc.observables(space, psi), phi, a0, w, Lk, t)
+    assert dv > 1e-3 and dx > 1e-3
+
+
+# ---------------------------------------- interacting multi-mode mean field
+
+def classical_energy(w, L, a):
+    """E(a) = sum_k w_k |a_k|^2 + sum_{pqrs} L_{pq;rs} a_p^* a_q^* a_r a_s: Eq. (Ham)
+    with every operator replaced by its classical field value (Sec. III A)."""
+    a = np.asarray(a, dtype=np.complex128)
+    return (np.sum(np.asarray(w) * np.abs(a) ** 2)
+            + np.einsum("pqrs,p,q,r,s->", np.asarray(L, dtype=np.complex128), a.conj(), a.conj(), a, a)).real
+
+
+def meanfield_gradient_error(rhs, w, L, a, h=1e-5):
+    """Largest deviation of i * rhs(a) from the Wirtinger gradient dE/da_k^* =
+    (dE/dRe a_k + i dE/dIm a_k) / 2, by central differences of the classical
+    energy: Eq. (classicalFieldEqns) is Hamilton's equation i da_k/dt = dE/da_k^*."""
+    g = np.zeros(len(a), dtype=np.complex128)
+    for k in range(len(a)):
+        for unit, part in ((1.0, 1.0), (1j, 1j)):
+            e = np.zeros(len(a), dtype=np.complex128)
+            e[k] = unit * h
+            g[k] += part * (classical_energy(w, L, a + e) - classical_energy(w, L, a - e)) / (4 * h)
+    return float(np.max(np.abs(1j * rhs(w, L, a) - g)))
+
+
+def long_range_asymmetric(M):
+    """The gravity-like coupling on raw label differences: Hermitian, but neither
+    symmetric under p <-> q nor under r <-> s, so the symmetrisation of Eq.
+    (classicalFieldEqns) matters."""
+    L = wl.long_range_coupling(M, 0.4)
+    assert np.abs(L - L.transpose(1, 0, 2, 3)).max() > 1e-3 and np.abs(L - L.transpose(0, 1, 3, 2)).max() > 1e-3
+    return L
+
+
+def test_meanfield_rhs_is_the_energy_gradient():
+    """The mean-field right-hand side at random points equals -i times the
+    Wirtinger gradient of the classical energy, for the asymmetric long-range
+    coupling (M = 5) and a random complex Hermitian coupling (M = 4)."""
+    rng = np.random.default_rng(11)
+    for M, L in ((5, long_range_asymmetric(5)), (4, random_hermitian_coupling(4, rng, 0.3))):
+        w = rng.standard_normal(M)
+        for _ in range(3):
+            a = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+            assert meanfield_gradient_error(orc.mf_rhs, w, L, a) < 1e-8
+
+
+def test_meanfield_conserves_occupation_and_energy():
+    """Along an interacting M = 5 trajectory under the asymmetric long-range
+    coupling, sum_k |a_k|^2 and the classical energy stay constant up to the RK4
+    error, which falls as dt^4 (the energy drift halves dt -> ~1/16)."""
+    M = 5
+    w = wl.dispersion_quadratic(M)
+    L = long_range_asymmetric(M)
+    a0 = np.array([0.3 + 0.1j, 1.2j, 0.9, -0.7 + 0.4j, 0.2])
+    N0, E0 = float(np.sum(np.abs(a0) ** 2)), classical_energy(w, L, a0)
+    drift = []
+    for dt in (4e-3, 2e-3):
+        traj = orc.meanfield(w, L, a0, dt, int(round(8.0 / dt)), every=int(round(0.5 / dt)))
+        # the interaction moves occupation between modes (the run is not trivial)
+        assert np.abs(np.abs(traj[-1]) ** 2 - np.abs(a0) ** 2).max() > 0.05
+        assert max(abs(float(np.sum(np.abs(x) ** 2)) - N0) for x in traj) < 1e-9
+        drift.append(max(abs(classical_energy(w, L, x) - E0) for x in traj))
+    assert drift[0] < 1e-7 and 8 < drift[0] / drift[1] < 40
+
+
+def _rhs_unsymmetrised(w, L, a):
+    return -1j * (np.asarray(w) * a + 2 * np.einsum("kqrs,q,r,s->k", L, np.conj(a), a, a))
+
+
+def _rhs_wrong_axis(w, L, a):
+    G = L + L.transpose(0, 1, 3, 2)
+    return -1j * (np.asarray(w) * a + np.einsum("kqrs,q,r,s->k", G, np.conj(a), a, a))
+
+
+def _rhs_conjugate_slip(w, L, a):
+    G = L + L.transpose(1, 0, 2, 3)
+    return -1j * (np.asarray(w) * a + np.einsum("kqrs,q,r,s->k", G, a, np.conj(a), a))
+
+
+@pytest.mark.parametrize("mutant", [_rhs_unsymmetrised, _rhs_wrong_axis, _rhs_conjugate_slip])
+def test_meanfield_pins_reject_planted_mistakes(mutant):
+    """Mistakes planted in the oracle's mean-field right-hand side (the p <-> q
+    symmetrisation dropped, symmetrised over r <-> s instead, a conjugate on the
+    wrong field) fail the gradient pin and break energy conservation."""
+    M = 5
+    rng = np.random.default_rng(12)
+    w = wl.dispersion_quadratic(M)
+    L = long_range_asymmetric(M)
+    a = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+    assert meanfield_gradient_error(mutant, w, L, a) > 1e-3
+    a0 = np.array([0.3 + 0.1j, 1.2j, 0.9, -0.7 + 0.4j, 0.2])
+    E0 = classical_energy(w, L, a0)
+    x = a0.copy()
+    dt = 2e-3
+    for _ in range(2000):  # classic RK4 with the mutant right-hand side
+        k1 = mutant(w, L, x)
+        k2 = mutant(w, L, x + 0.5 * dt * k1)
+        k3 = mutant(w, L, x + 0.5 * dt * k2)
+        k4 = mutant(w, L, x + dt * k3)
+        x = x + dt / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+    drift_e = abs(classical_energy(w, L, x) - E0)
+    drift_n = abs(float(np.sum(np.abs(x) ** 2)) - float(np.sum(np.abs(a0) ** 2)))
+    assert drift_e > 1e-4 or drift_n > 1e-4
