@@ -2,15 +2,16 @@
 
 Workload (default): the batched coherent state -- M=7 ring modes, w_p = p^2/2,
 contact coupling C = -0.05/n_tot, alpha = sqrt(n_tot/2) on p = -1 and p = +1 at
-n_tot = 16, every Poisson-weighted sector N <= n_tot + 6 sqrt(n_tot) = 40 (287
-sectors, 62,891,499 kets, complex128), advanced together.  A step is one RK4
+n_tot = 16, every Poisson-weighted sector N <= n_tot + 6 sqrt(n_tot) = 40 (281
+non-empty sectors, 62,891,499 kets, complex128), advanced together.  A step is one RK4
 step of the whole state (four fused H psi stages over every sector).
 
 The state (1 GB) is larger than L2 (129 MB), so no L2 flush is needed between
 steps.  Prints ONE JSON line (rank 0).
 
---impl reference times the CPU oracle (oracle/) as it stands, single-threaded,
-on a bounded sample of the same workload (one RK4 step of the N=16 sectors).
+--impl reference times the CPU oracle (oracle/) as it stands, its rows on every
+host core (OpenMP), on a bounded sample of the same workload (RK4 steps of the N=16
+sectors).
 """
 from __future__ import annotations
 
@@ -31,8 +32,8 @@ import numpy as np  # noqa: E402
 
 import workloads as wl  # noqa: E402
 
-# FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
-# (a DFMA microbenchmark measured 1.00 TFLOP/s: python -m paper_2111_00050_gb300.probe)
+# FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz; the
+# roofline uses the DFMA rate measured on the GPU by the run itself (qb_measure_fp64_fma)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per ket of one stage launch (the first stage of a step), from an ncu capture
 # of the current stage kernel (batched coherent at n_tot=12: 757.5 MB read + 232.1 MB
@@ -135,8 +136,8 @@ def init_state(qs, W, psi):
 
 
 def run_reference(args):
-    """The CPU oracle, single-threaded, one RK4 step per timed step on a bounded
-    sample of the workload."""
+    """The CPU oracle on every host core (its row-parallel RK4), one RK4 step per
+    timed step on a bounded sample of the workload."""
     import oracle as orc
 
     W, sp = workload(args.config, args.n_tot)
@@ -151,10 +152,10 @@ def run_reference(args):
     psi /= np.linalg.norm(psi)
     terms = orc.count_terms(space, W.L)
     for _ in range(args.warmup):
-        psi = orc.rk4(space, W.w, W.L, psi, W.dt, 1)
+        psi = orc.rk4_rows(space, W.w, W.L, psi, W.dt, 1)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        psi = orc.rk4(space, W.w, W.L, psi, W.dt, 1)
+        psi = orc.rk4_rows(space, W.w, W.L, psi, W.dt, 1)
     dt_s = (time.perf_counter() - t0) / args.steps
     value = 4 * terms / dt_s
     sample = f"one RK4 step (4 H psi) of the sectors N={Ns} (all P) of {W.name}: {space.total} kets, {terms} terms"
@@ -163,20 +164,22 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt_s * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": W.name, "sample": sample},
-        "cpu_baseline": {"value": value, "unit": "terms/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "terms/s", "cores": orc.threads(), "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": value, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
 
 
-def cpu_baseline(W, seconds_cap: float = 20.0):
-    """Times the oracle on one RK4 step of one N layer of the workload (all P)."""
+def cpu_baseline(W, seconds_cap: float = 15.0):
+    """Times the oracle's row-parallel RK4 on every host core (OpenMP) on one N layer
+    of the workload (all P): RK4 steps until about seconds_cap of wall time."""
     import oracle as orc
 
-    N = min(12, W.n_max) if W.kind == "coherent" else W.n_min
+    N = min(16, W.n_max) if W.kind == "coherent" else W.n_min
     sectors = [(N, P) for P in range(W.M) if orc.sector_dim(W.M, N, P) > 0]
     space = orc.Space(W.M, sectors)
-    if space.total > 300000:  # bound the sample: a slice of rows of the first sector
+    if space.total > 300000:  # bound the sample: the first sector only
         sectors = sectors[:1]
         space = orc.Space(W.M, sectors)
     rng = np.random.default_rng(0)
@@ -185,13 +188,14 @@ def cpu_baseline(W, seconds_cap: float = 20.0):
     t0 = time.perf_counter()
     n = 0
     while True:
-        psi = orc.rk4(space, W.w, W.L, psi, W.dt, 1)
+        psi = orc.rk4_rows(space, W.w, W.L, psi, W.dt, 1)
         n += 1
-        if time.perf_counter() - t0 > min(seconds_cap, 5.0) or n >= 50:
+        if time.perf_counter() - t0 > seconds_cap or n >= 50:
             break
     el = (time.perf_counter() - t0) / n
-    return {"value": 4 * terms / el, "unit": "terms/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} RK4 step(s) of sectors N={N} ({space.total} kets, {terms} terms/H psi) of {W.name}"}
+    return {"value": 4 * terms / el, "unit": "terms/s", "cores": orc.threads(), "kind": "oracle",
+            "sample": f"{n} RK4 step(s) of sectors N={N} ({space.total} kets, {terms} terms/H psi) of {W.name}, "
+                      f"rows of each H psi on {orc.threads()} host threads"}
 
 
 def adjoint_extra(qb, torch, steps: int = 20, ckpt_every: int = 10):
@@ -363,6 +367,39 @@ def breaktime_sweep(qb, torch, r_list=(1, 2, 3, 4, 6, 8), chunk: int = 1000):
     return {"workload": "breaktime_coherent_M5", "runs": runs, "fits": fits}
 
 
+def large_sector_roofline(qb, torch, peaks, dfma_tflops, steps: int = 20):
+    """One H psi of the largest single sector of the workloads: M=11, w=|p|, contact
+    C=-0.02, N=20, P=0 (2,731,365 kets), timed as RK4 steps of the single state (four
+    stage launches each, the first weighted copy of the call amortised over `steps`),
+    against the algorithmic 32 B per ket and H psi (read psi, write the output) and
+    the FP64-equivalent 4 flop per term."""
+    W = wl.large_sector()
+    qs = qb.Space(W.M, W.w, W.L, 20, 20, [0])
+    terms = qs.terms()[0]
+    psi = qs.empty_state()
+    qs.init_number(W.occ, psi)
+    work = qs.workspace(1)
+    qs.autotune(W.dt, psi, steps=2, work=work)
+    qs.evolve(psi, W.dt, 2, work)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    qs.evolve(psi, W.dt, steps, work)
+    e1.record()
+    torch.cuda.synchronize()
+    stage_s = e0.elapsed_time(e1) * 1e-3 / steps / 4
+    hbm_gbs = 32.0 * qs.total / stage_s / 1e9
+    achieved = 4.0 * terms / stage_s / 1e12
+    out = {"workload": W.name + "_P0", "kets": qs.total, "terms_per_hpsi": terms, "stage_ms": stage_s * 1e3,
+           "terms_per_s": terms / stage_s, "bound": "alu", "achieved_tflops_fp64_equiv": achieved,
+           "peak_dfma_tflops": dfma_tflops, "frac": achieved / dfma_tflops,
+           "hbm_GBps_algorithmic": hbm_gbs, "hbm_peak_GBps": peaks.get("hbm_gbs"),
+           "hbm_frac": hbm_gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+           "bytes_per_ket_algorithmic": 32, "tile_shape": qs.tile_shape, "tuning": qs.tuning}
+    del psi, work, qs
+    torch.cuda.empty_cache()
+    return out
+
+
 def sweep_extra(qb, torch, steps: int = 3):
     """8-member coupling sweep on the M=11, N=20, P=0 sector (2,731,365 kets, number state
     (...,7,6,7,...), w=|p|, C_k = -0.005 k): one batched launch per stage for all 8
@@ -498,15 +535,17 @@ def main():
     torch.cuda.synchronize()
     fp64_ms = a_ev.elapsed_time(b_ev)
     del out
+    dfma_tflops = qb.api.measure_fp64_fma(3)
     roofline = {
-        "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-        "frac": achieved / FP64_PEAK_TFLOPS,
+        "bound": "alu", "achieved": achieved, "peak": dfma_tflops, "unit": "TFLOP/s",
+        "frac": achieved / dfma_tflops, "peak_kind": "measured DFMA rate of this GPU (qb_measure_fp64_fma)",
+        "peak_unit_count": FP64_PEAK_TFLOPS, "frac_of_unit_count": achieved / FP64_PEAK_TFLOPS,
         "traffic": STAGE_DRAM_BYTES_PER_KET * qs.total if args.config == "batched_coherent" else None,
         "kernel": f"stage_df_kernel<{W.M},1,0,0,1,0> (one RK4 stage = one H psi over all sectors, weighted basis)",
         "stage_ms": stage_time * 1e3,
-        "peak_note": "FP64-equivalent flops (2 FMA/term) vs the FP64 pipe peak from unit counts "
-                     "(152 SMs x 2 FMA/clk x 2.07 GHz); the kernel itself runs double-float on the FP32/ALU "
-                     "pipes; traffic scaled from an ncu capture at n_tot=12",
+        "peak_note": "FP64-equivalent flops (2 FMA/term) vs the FP64 FMA rate measured on this GPU; the "
+                     "kernel itself runs double-float on the FP32/ALU pipes (FP64 pipe idle), so frac > 1 "
+                     "is its speed-up over native FP64; traffic scaled from an ncu capture at n_tot=12",
         "hbm_GBps": hbm_bytes / stage_time / 1e9, "hbm_peak_GBps": peaks.get("hbm_gbs"),
         "hbm_frac": (hbm_bytes / stage_time / 1e9) / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
         "fp64_hpsi_ms": fp64_ms,
@@ -536,30 +575,47 @@ def main():
     taylor2 = {"ms_per_step": t2_ms, "steps_per_s": 1e3 / t2_ms, "terms_per_s": 2 * terms / (t2_ms * 1e-3),
                "steps": k_plain}
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers: every step copies its
+    # input state from pinned host memory (on a copy stream, into the buffer the
+    # previous step is not using, so that the copy of step k+1 overlaps step k),
+    # runs one RK4 step and reads the observables back to the host
     host_in = torch.empty(qs.total, dtype=torch.complex128).pin_memory()
     host_in.copy_(psi.cpu())
+    bufs = [psi, torch.empty_like(psi)]
+    copy_stream = torch.cuda.Stream()
+    ready = [torch.cuda.Event(), torch.cuda.Event()]
     # one untimed pass first: the first call of a kernel pays its module load and
     # launch-attribute set-up
-    psi.copy_(host_in, non_blocking=True)
-    qs.evolve(psi, W.dt, 1, work)
-    qs.observables(psi)
+    bufs[1].copy_(host_in, non_blocking=True)
+    qs.evolve(bufs[1], W.dt, 1, work)
+    qs.observables(bufs[1])
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
     k_e2e = max(1, min(args.steps, 5))
-    for _ in range(k_e2e):
-        psi.copy_(host_in, non_blocking=True)
-        qs.evolve(psi, W.dt, 1, work)
-        ob = qs.observables(psi)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(copy_stream):
+        bufs[0].copy_(host_in, non_blocking=True)
+        ready[0].record(copy_stream)
+    for k in range(k_e2e):
+        cur = bufs[k % 2]
+        if k + 1 < k_e2e:
+            with torch.cuda.stream(copy_stream):
+                bufs[(k + 1) % 2].copy_(host_in, non_blocking=True)
+                ready[(k + 1) % 2].record(copy_stream)
+        torch.cuda.current_stream().wait_event(ready[k % 2])
+        qs.evolve(cur, W.dt, 1, work)
+        ob = qs.observables(cur)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / k_e2e
+    psi = bufs[(k_e2e - 1) % 2]
+    del bufs
     if dist is not None:  # replicas: the job's step is its slowest rank's
         e2e_s = max_over_ranks(dist, e2e_s, "cuda")
     nmom = 4 + 2 * W.M + 4 * W.M * W.M
     e2e = {"value": job_throughput(world, 4 * terms, e2e_s * 1e3), "unit": "terms/s",
            "h2d_bytes_per_step": 16 * qs.total,
            "d2h_bytes_per_step": 8 * nmom + 8 * 2, "steps_per_s": 1.0 / e2e_s,
-           "note": "H2D of psi from pinned memory + one RK4 step + qb_observables (moments D2H) per step"}
+           "note": "per step: H2D of psi from pinned memory (copy stream, overlapping the previous step), "
+                   "one RK4 step, qb_observables (moments D2H, host sync)"}
 
     # ---- the other rows of the path, each timed once: sector build + device tables (host
     # wall clock), initial state, one observables call, observation steps + breaktime,
@@ -590,11 +646,11 @@ def main():
     line = {
         "metric": "H_psi_terms_per_s", "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64 (H psi in double-float: fp32 pairs)", "data": "synthetic",
         "config": {"workload": W.name, "kets": qs.total, "sectors": qs.n_sectors, "terms_per_hpsi": terms,
                    "ordered_tuples_per_hpsi": tuples, "dt": W.dt, "rk4_steps_per_s": steps_per_s,
                    "l2": "state (16 B/ket, %.2f GB) larger than L2; no flush" % (16 * qs.total / 1e9),
-                   "resident_max_kets": resident_max,
+                   "resident_max_kets": resident_max, "tile_shape": qs.tile_shape, "tuning": qs.tuning,
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "rk4_steps_per_s": steps_per_s,
         "plain_per_sector": plain,
@@ -605,9 +661,11 @@ def main():
         "e2e": e2e,
         "path_rows": rows,
     }
+    line["large_sector_roofline"] = None
     if not args.no_extras:
         del work, psi
         torch.cuda.empty_cache()
+        line["large_sector_roofline"] = large_sector_roofline(qb, torch, peaks, dfma_tflops)
         line["adjoint"] = adjoint_extra(qb, torch)
         line["sweep"] = sweep_extra(qb, torch)
         line["small_sector"] = small_extra(qb, torch)

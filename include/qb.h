@@ -46,6 +46,7 @@ extern "C" {
 #define QB_EUNSUPPORTED 6 /* outside the compiled limits (M > QB_MAX_MODES, packed occupation > 64 bits) */
 
 #define QB_MAX_MODES 16
+#define QB_TILE_SHAPES 5  /* compiled tile shapes of the RK4 stage kernel (qb_space_set_tile_shape) */
 
 /* Losses of qb_adjoint. */
 #define QB_LOSS_Q 0  /* Q at t_f (Eq. Qparam) */
@@ -108,9 +109,13 @@ const char* qb_last_error(void);
  * current device, with two per-ket tables the space owns: the diagonal of H
  * (16 B per ket) and the occupation vector packed into 64 bits (8 B per ket),
  * plus a double-float copy of an observed state (16 B per ket).
- * Limits: 1 <= M <= QB_MAX_MODES; M * bits(n_max) <= 64;
- * every sector dimension < 2^31; with exact momentum (M-1) n_max + 1 <= 6553
- * (the term shifts are 16-bit), and batched sweeps (batch > 1) are not built.
+ * Limits: 1 <= M <= QB_MAX_MODES; M * bits(n_max) <= 64; n_max <= 250;
+ * the largest ket weight sqrt(n_max! / prod_m n_m!) over occupations of n_max
+ * particles at most 2^160 (the RK4 stages hold psi / w(n) as fp32 pairs, with the
+ * weights of each N centred on 1 by a power of two; e.g. n_max <= 206 for M = 3,
+ * n_max <= 143 for M = 5); every sector dimension < 2^31; with exact momentum
+ * (M-1) n_max + 1 <= 6553 (the term shifts are 16-bit), and batched sweeps
+ * (batch > 1) are not built.
  * Errors: QB_EINVAL for a bad model or range, QB_EUNSUPPORTED beyond the limits,
  * QB_ECUDA / QB_ENOMEM from the device set-up.  *out receives the new space. */
 int qb_sector_build(const qb_model* model, int n_min, int n_max, const int* p_list, int n_p, qb_space** out);
@@ -185,6 +190,18 @@ int qb_evolve_batch(qb_space* space, void* d_psi, int batch, const double* scale
  * do not depend on the setting: every ket goes through the same arithmetic. */
 int qb_space_set_resident_max(qb_space* space, int resident_max_kets);
 
+/* Execution tuning of the RK4 stages of qb_evolve, qb_evolve_plain and
+ * qb_evolve_observe for one state vector (the per-sector parallel scheme of
+ * Sec. III B, mapped onto thread blocks): the tile shape of the stage kernel, one of
+ * QB_TILE_SHAPES compiled shapes given as (warps per thread block, kets per warp
+ * tile, thread blocks per SM the register budget is planned for):
+ *   0 (12, 64, 3) the default;  1 (8, 64, 4);  2 (16, 64, 2);  3 (12, 128, 3);
+ *   4 (8, 32, 4).
+ * Every ket sums its terms in the same order under every shape, so results are
+ * bit-identical; only the time differs (the Python binding's Space.autotune times
+ * them on the caller's workload).  QB_EINVAL outside [0, QB_TILE_SHAPES). */
+int qb_space_set_tile_shape(qb_space* space, int shape);
+
 /* Order K of the time step of qb_evolve, qb_evolve_batch, qb_evolve_plain and
  * qb_evolve_observe: psi <- sum_{k=0..K} (z H)^k / k! psi, z = -i dt, applied in
  * the Horner form psi + z(psi + z/2(psi + ... + z/K psi)), K launches per step.
@@ -202,8 +219,13 @@ int qb_evolve_plain(qb_space* space, void* d_psi, double dt, int64_t steps, void
 /* ---- observables (Sec. II C-E) ------------------------------------------- */
 
 /* All observables of one state; out (host) is written after the stream syncs.
- * The moments are summed in double-float arithmetic from a double-float copy of
- * the state (about 48 significant bits): absolute errors of order 1e-14 n_tot. */
+ * Every sum over kets is accumulated in FP64: the norm, <N> and <n_i> directly
+ * from the FP64 state; the moments that move a ket (<a_i>, <a_i^dag a_j>,
+ * <a_i a_j>) as double-float products (about 48 significant bits) of the state and
+ * its weighted double-float copy, summed in double-float over 32 kets at a time and
+ * added in FP64; <H> from the weighted double-float H psi, each row's contribution
+ * formed and summed in FP64.  The space's weighted-copy buffer (16 B per ket) is
+ * overwritten.  Relative errors are of order 1e-14. */
 int qb_observables(qb_space* space, const void* d_psi, qb_obs* out, void* stream);
 
 /* Evolution with observation: series[0] is the initial state, series[k] the

@@ -30,17 +30,27 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_OMP_PATH = os.path.join(_HERE, "_build", "liboracle_omp.so")  # the same source built with OpenMP
 _lib = None
+_omp = None
 
 
 def build(force: bool = False) -> str:
-    """Compile qb_oracle.c into a shared library with the host C compiler."""
+    """Compile qb_oracle.c into a shared library with the host C compiler, and the
+    same file with OpenMP (the row-parallel RK4 of the timed CPU baseline) if the
+    compiler supports it."""
     src = os.path.join(_HERE, "qb_oracle.c")
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", src, "-o", tmp, "-lm"])
-        os.replace(tmp, _LIB_PATH)
+    for path, extra in ((_LIB_PATH, []), (_OMP_PATH, ["-fopenmp"])):
+        if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(src):
+            tmp = path + f".tmp{os.getpid()}"
+            r = subprocess.run(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", *extra, src, "-o", tmp, "-lm"],
+                               capture_output=True, text=True)
+            if r.returncode != 0:
+                if extra:  # no OpenMP: the baseline falls back to the single-threaded build
+                    continue
+                raise RuntimeError(f"gcc failed on the oracle:\n{r.stderr}")
+            os.replace(tmp, path)
     return _LIB_PATH
 
 
@@ -70,6 +80,26 @@ def _L():
         lib.orc_apply_mode_op.argtypes = [i32, i32, vp, vp, vp, vp, vp, i32, i32, vp, i32]
         _lib = lib
     return _lib
+
+
+def _omp_lib():
+    """The OpenMP build (rk4_rows), or the plain one where OpenMP is not available."""
+    global _omp
+    if _omp is None:
+        _L()
+        path = _OMP_PATH if os.path.exists(_OMP_PATH) else _LIB_PATH
+        lib = ctypes.CDLL(path)
+        lib.orc_rk4_rows.restype = ctypes.c_int
+        lib.orc_rk4_rows.argtypes = [ctypes.c_int, ctypes.c_int64] + [ctypes.c_void_p] * 4 + [ctypes.c_double,
+                                                                                              ctypes.c_int64]
+        lib.orc_threads.restype = ctypes.c_int
+        _omp = lib
+    return _omp
+
+
+def threads() -> int:
+    """Host threads rk4_rows uses."""
+    return int(_omp_lib().orc_threads())
 
 
 def _p(a: np.ndarray):
@@ -209,6 +239,24 @@ def rk4(space: Space, w, L, psi: np.ndarray, dt: float, steps: int) -> np.ndarra
         x = np.ascontiguousarray(out[sl])
         rc = lib.orc_rk4(M, b.shape[0], _p(b), _p(w), _p(Lc), _p(x), float(dt), int(steps))
         if rc != 0:
+            raise ValueError("coupling maps a ket outside its sector")
+        out[sl] = x
+    return out
+
+
+def rk4_rows(space: Space, w, L, psi: np.ndarray, dt: float, steps: int) -> np.ndarray:
+    """rk4 with H psi formed row by row, the rows of a sector on every host core
+    (OpenMP build); the arithmetic of each row is that of apply_h_rows."""
+    M = space.M
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    Lc = np.ascontiguousarray(L, dtype=np.complex128).reshape(-1)
+    out = np.array(psi, dtype=np.complex128, copy=True)
+    lib = _omp_lib()
+    for s in range(len(space.sectors)):
+        sl = space.sector_slice(s)
+        b = np.ascontiguousarray(space.basis[sl])
+        x = np.ascontiguousarray(out[sl])
+        if lib.orc_rk4_rows(M, b.shape[0], _p(b), _p(w), _p(Lc), _p(x), float(dt), int(steps)) != 0:
             raise ValueError("coupling maps a ket outside its sector")
         out[sl] = x
     return out

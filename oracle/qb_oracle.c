@@ -28,6 +28,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 static int label_of(int M, int i) { return (M % 2) ? i - (M - 1) / 2 : i; }
 
@@ -459,4 +462,61 @@ int64_t orc_count_terms(int M, int64_t D, const int* basis, const double* L) {
   }
   free(tg);
   return total;
+}
+
+/* f = -i H v row by row (orc_apply_h_row, the pull form, which the tests pin to
+   the push form).  The rows are independent: a build with OpenMP (-fopenmp) runs
+   them on every host core, which is the timed CPU baseline; without it this is the
+   same loop on one core. */
+static int deriv_rows(int M, int64_t D, const int* basis, const double* w, const double* L, const double* v,
+                      double* f) {
+  int rc = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64) reduction(| : rc)
+#endif
+  for (int64_t i = 0; i < D; ++i) {
+    double h[2];
+    rc |= orc_apply_h_row(M, D, basis, w, L, v, i, h);
+    f[2 * i] = h[1];
+    f[2 * i + 1] = -h[0];
+  }
+  return rc;
+}
+
+/* orc_rk4 with H psi formed row by row (deriv_rows). */
+int orc_rk4_rows(int M, int64_t D, const int* basis, const double* w, const double* L, double* psi, double dt,
+                 int64_t steps) {
+  size_t bytes = sizeof(double) * 2 * (size_t)D;
+  double* k1 = malloc(bytes);
+  double* k2 = malloc(bytes);
+  double* k3 = malloc(bytes);
+  double* k4 = malloc(bytes);
+  double* u = malloc(bytes);
+  int rc = 0;
+  if (!k1 || !k2 || !k3 || !k4 || !u) rc = -2;
+  for (int64_t st = 0; st < steps && rc == 0; ++st) {
+    rc |= deriv_rows(M, D, basis, w, L, psi, k1);
+    for (int64_t k = 0; k < 2 * D; ++k) u[k] = psi[k] + 0.5 * dt * k1[k];
+    rc |= deriv_rows(M, D, basis, w, L, u, k2);
+    for (int64_t k = 0; k < 2 * D; ++k) u[k] = psi[k] + 0.5 * dt * k2[k];
+    rc |= deriv_rows(M, D, basis, w, L, u, k3);
+    for (int64_t k = 0; k < 2 * D; ++k) u[k] = psi[k] + dt * k3[k];
+    rc |= deriv_rows(M, D, basis, w, L, u, k4);
+    for (int64_t k = 0; k < 2 * D; ++k) psi[k] += dt / 6.0 * (k1[k] + 2.0 * k2[k] + 2.0 * k3[k] + k4[k]);
+  }
+  free(k1);
+  free(k2);
+  free(k3);
+  free(k4);
+  free(u);
+  return rc;
+}
+
+/* threads a parallel region of this build uses (1 without OpenMP) */
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }

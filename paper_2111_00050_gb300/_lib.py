@@ -1,4 +1,5 @@
-"""ctypes declarations of the C ABI in include/qb.h (argument marshalling only)."""
+"""ctypes declarations of the C ABI in include/qb.h and include/qb_diag.h
+(argument marshalling only)."""
 from __future__ import annotations
 
 import ctypes
@@ -8,6 +9,7 @@ from . import build as _build
 
 QB_OK, QB_EINVAL, QB_ENOMEM, QB_ECUDA, QB_ETIMEOUT, QB_EINTERNAL, QB_EUNSUPPORTED = range(7)
 QB_MAX_MODES = 16
+QB_TILE_SHAPES = 5
 QB_CROSSED, QB_AT_START, QB_NOT_CROSSED = 0, 1, 2
 QB_LOSS_Q, QB_LOSS_PO = 0, 1
 
@@ -44,7 +46,7 @@ class QbObs(ctypes.Structure):
     ]
 
 
-# name -> (restype, argtypes); must list every function include/qb.h declares
+# name -> (restype, argtypes); must list every function include/*.h declares
 SIGNATURES = {
     "qb_last_error": (ctypes.c_char_p, []),
     "qb_sector_build": (ctypes.c_int, [ctypes.POINTER(QbModel), ctypes.c_int, ctypes.c_int, _c_int_p, ctypes.c_int,
@@ -67,6 +69,7 @@ SIGNATURES = {
                                  ctypes.c_void_p]),
     "qb_space_set_resident_max": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "qb_space_set_order": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "qb_space_set_tile_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "qb_evolve_plain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_void_p,
                                        ctypes.c_void_p]),
     "qb_evolve_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _c_double_p, ctypes.c_double,
@@ -88,6 +91,9 @@ SIGNATURES = {
     "qb_fit": (ctypes.c_int, [_c_double_p, _c_double_p, ctypes.c_int, ctypes.c_int, _c_double_p, _c_double_p]),
     "qb_meanfield": (ctypes.c_int, [ctypes.POINTER(QbModel), _c_double_p, ctypes.c_double, ctypes.c_int64,
                                     ctypes.c_int, _c_double_p]),
+    # include/qb_diag.h
+    "qb_space_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_int_p, ctypes.c_void_p]),
+    "qb_measure_fp64_fma": (ctypes.c_int, [ctypes.c_int, _c_double_p, ctypes.c_void_p]),
 }
 
 _lib = None

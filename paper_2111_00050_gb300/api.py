@@ -100,6 +100,8 @@ class Space:
         self.dims = dim
         self.offsets = off
         self.order = 4
+        self.tile_shape = 0
+        self.tuning = None
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -121,6 +123,13 @@ class Space:
         if occ.shape[0]:
             check(lib().qb_space_rank(self._h, _dptr(occ), int(occ.shape[0]), _dptr(out), _stream()))
         return out
+
+    def status(self, set_bits: int = 0) -> int:
+        """qb_space_status: ORs set_bits into the space's device status word and
+        returns the word (nonzero: the next synchronising call fails with QB_EINTERNAL)."""
+        st = ctypes.c_int()
+        check(lib().qb_space_status(self._h, int(set_bits), ctypes.byref(st), _stream()))
+        return int(st.value)
 
     def terms(self):
         t, u = ctypes.c_int64(), ctypes.c_int64()
@@ -169,27 +178,47 @@ class Space:
         check(lib().qb_space_set_order(self._h, int(order)))
         self.order = int(order)
 
+    def set_tile_shape(self, shape: int) -> None:
+        """qb_space_set_tile_shape: tile shape of the RK4 stage kernel (0 .. QB_TILE_SHAPES-1)."""
+        check(lib().qb_space_set_tile_shape(self._h, int(shape)))
+        self.tile_shape = int(shape)
+
+    def _time_evolve(self, dt, psi, trial, steps, work) -> float:
+        trial.copy_(psi)
+        self.evolve(trial, dt, 1, work)  # first launches of a setting pay their set-up
+        trial.copy_(psi)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        self.evolve(trial, dt, steps, work)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
     def autotune(self, dt: float, psi: torch.Tensor, candidates=(0, 256, 1024, 4096), steps: int = 2,
-                 work: Optional[torch.Tensor] = None) -> int:
-        """Times `steps` RK4 steps from a copy of psi for each resident threshold in
-        `candidates` (CUDA events) and keeps the fastest; returns it."""
+                 work: Optional[torch.Tensor] = None, shapes=None) -> int:
+        """Picks the execution settings of qb_evolve for this space by timing `steps`
+        RK4 steps from a copy of psi (CUDA events): first the tile shape of the stage
+        kernel (every compiled shape, or `shapes`; resident threshold 0, so that every
+        sector runs through the stage kernel), then the resident threshold among
+        `candidates`.  Keeps the fastest of each and returns the threshold; the chosen
+        shape is in self.tile_shape and both, with every timing, in self.tuning."""
         work = self.workspace(1) if work is None else work
         trial = psi.clone()
-        best, best_ms = None, float("inf")
+        shapes = range(_lib.QB_TILE_SHAPES) if shapes is None else shapes
+        self.set_resident_max(0)
+        shape_ms = {}
+        for sh in shapes:
+            self.set_tile_shape(sh)
+            shape_ms[int(sh)] = self._time_evolve(dt, psi, trial, steps, work)
+        self.set_tile_shape(min(shape_ms, key=shape_ms.get))
+        res_ms = {}
         for kets in candidates:
             self.set_resident_max(kets)
-            trial.copy_(psi)
-            self.evolve(trial, dt, 1, work)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            trial.copy_(psi)
-            e0.record()
-            self.evolve(trial, dt, steps, work)
-            e1.record()
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1)
-            if ms < best_ms:
-                best, best_ms = kets, ms
+            res_ms[int(kets)] = self._time_evolve(dt, psi, trial, steps, work)
+        best = min(res_ms, key=res_ms.get)
         self.set_resident_max(best)
+        self.tuning = {"tile_shape": self.tile_shape, "resident_max_kets": best, "tile_shape_ms": shape_ms,
+                       "resident_ms": res_ms, "steps": steps}
         return best
 
     def evolve_plain(self, psi: torch.Tensor, dt: float, steps: int, work: Optional[torch.Tensor] = None) -> None:
@@ -239,6 +268,13 @@ class Space:
         check(lib().qb_evolve_observe(self._h, _dptr(psi), float(dt), int(steps), int(obs_every), arr, _dptr(work),
                                       _stream()))
         return [obs_to_dict(arr[k], self.M) for k in range(n)]
+
+
+def measure_fp64_fma(reps: int = 3) -> float:
+    """qb_measure_fp64_fma: the GPU's FP64 FMA rate in TFLOP/s (2 flop per FMA)."""
+    out = ctypes.c_double()
+    check(lib().qb_measure_fp64_fma(int(reps), ctypes.byref(out), _stream()))
+    return float(out.value)
 
 
 def breaktime(values, dt_obs: float, thr: float):
@@ -291,19 +327,51 @@ def meanfield(M: int, w, L, z0, dt: float, steps: int, every: int = 1, exact: bo
     return out.view(np.complex128).reshape(rows, M)
 
 
+_SPACE_CACHE: "dict" = {}
+_SPACE_CACHE_SIZE = 2
+
+
+def _cached_space(M: int, w, L0, n_min: int, n_max: int, p_list) -> Space:
+    """A Space for (M, w, L0, N range, P list), reused across calls: building one
+    (sector tables, per-ket diagonal and occupations) costs a device pass over every
+    ket.  The few most recent ones are kept."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    L0 = np.ascontiguousarray(L0, dtype=np.complex128)
+    key = (int(M), w.tobytes(), L0.tobytes(), int(n_min), int(n_max),
+           None if p_list is None else tuple(int(p) for p in p_list))
+    sp = _SPACE_CACHE.pop(key, None)
+    if sp is None:
+        sp = Space(M, w, L0, n_min, n_max, p_list)
+    _SPACE_CACHE[key] = sp  # most recent last
+    while len(_SPACE_CACHE) > _SPACE_CACHE_SIZE:
+        _SPACE_CACHE.pop(next(iter(_SPACE_CACHE)))
+    return sp
+
+
 class AdjointLoss(torch.autograd.Function):
     """Loss (Q or lam_p at t_f) of an RK4 run from a coherent state, with gradients
     by qb_adjoint.  Inputs: the two-body scale (0-d float64 tensor), the dispersion
     w (float64 [M]) and the coherent amplitudes z (complex128 [M]); the space holds
-    the unit coupling L0.  z.grad follows torch's convention for real losses,
+    the unit coupling L0 and is reused across calls with the same model and range.
+    When no input requires a gradient (or autograd is off) only the forward run and
+    the loss are computed; otherwise qb_adjoint runs once, in forward, and backward
+    returns its gradients.  z.grad follows torch's convention for real losses,
     d loss / d Re z + i d loss / d Im z."""
 
     @staticmethod
     def forward(ctx, scale, w, z, spec):
-        space = Space(spec["M"], w.detach().cpu().numpy(), spec["L0"], spec["n_min"], spec["n_max"],
-                      spec.get("p_list"))
-        r = space.adjoint(z.detach().cpu().numpy(), float(scale), spec["dt"], spec["steps"],
-                          spec.get("ckpt_every", 1), spec.get("loss", "Q"))
+        space = _cached_space(spec["M"], w.detach().cpu().numpy(), spec["L0"], spec["n_min"], spec["n_max"],
+                              spec.get("p_list"))
+        zz = z.detach().cpu().numpy()
+        kind = spec.get("loss", "Q")
+        if not any(ctx.needs_input_grad[:3]):
+            psi = space.empty_state()
+            space.init_coherent(zz, psi)
+            space.evolve_batch(psi, [float(scale)], spec["dt"], spec["steps"])
+            ob = space.observables(psi)
+            ctx.grads = None
+            return torch.tensor(ob["Q"] if kind == "Q" else ob["lam_p"], dtype=torch.float64)
+        r = space.adjoint(zz, float(scale), spec["dt"], spec["steps"], spec.get("ckpt_every", 1), kind)
         ctx.grads = (torch.tensor(r["grad_scale"], dtype=torch.float64),
                      torch.from_numpy(np.asarray(r["grad_w"], dtype=np.float64)),
                      torch.from_numpy(np.asarray(r["grad_z"], dtype=np.complex128)))

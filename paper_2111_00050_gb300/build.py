@@ -1,6 +1,6 @@
 """Builds libqb.so (the C ABI of include/qb.h) for sm_103a with nvcc, in-tree.
 
-The two translation units compile in parallel; the result lands in
+The translation units compile in parallel; the result lands in
 paper_2111_00050_gb300/_build/libqb.so.  Rebuilds only when a source changed.
 """
 from __future__ import annotations
@@ -18,8 +18,9 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libqb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["qb_host.cpp", "qb_kernels.cu", "qb_adjoint.cu", "qb_stage_m5.cu", "qb_stage_m7.cu", "qb_stage_m9.cu", "qb_stage_m11.cu",
-           "qb_stage_any.cu"]
-HEADERS = ["qb_internal.h", "qb_device.cuh", "qb_stage.cuh", os.path.join("..", "..", "include", "qb.h")]
+           "qb_stage_any.cu", "qb_diag.cu", "qb_observe.cu"]
+HEADERS = ["qb_internal.h", "qb_device.cuh", "qb_stage.cuh", os.path.join("..", "..", "include", "qb.h"),
+           os.path.join("..", "..", "include", "qb_diag.h")]
 
 
 def _nvcc() -> str:

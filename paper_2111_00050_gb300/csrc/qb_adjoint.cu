@@ -348,7 +348,7 @@ extern "C" int qb_adjoint(qb_space* space, const double* z, double scale, double
   };
   auto run = [&](int mode, bool bil, double weight) -> int {
     int grid = 0;
-    int r = stage_launch(sp->t, a, mode, 1, cplx, st, &grid, bil, true);
+    int r = stage_launch(sp->t, a, mode, 1, cplx, st, &grid, bil, 0);
     if (r) return r;
     if (bil) {
       accumulate_kernel<<<1, 32, 0, st>>>(L.partial, grid, M + 1, weight, L.acc);

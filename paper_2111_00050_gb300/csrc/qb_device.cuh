@@ -164,10 +164,11 @@ __device__ __forceinline__ int64_t setup_row(const Tables& t, const View& v, con
   return D - 1 - (int64_t)acc;
 }
 
-// Ket weight w(n) = sqrt(N! / prod_m n_m!) and 1/w in FP64, from the occupations
-// occ[m * stride]: the product over modes of sqrt(C(rem_m, n_m)).  In the weighted
-// basis f = psi / w the two-body matrix element of a pair (r, s) -> (p, q) loses its
-// creation factor sqrt((n_p + 1)(n_q + 1 + [p = q])) (see the stage kernel).
+// Ket weight w(n) = sqrt(N! / prod_m n_m!) 2^-e_N and its inverse in FP64, from the
+// occupations occ[m * stride]: the product over modes of sqrt(C(rem_m, n_m)), times the
+// power of two that centres the weights of N particles on 1 (Tables::wscale).  In the
+// weighted basis f = psi / w the two-body matrix element of a pair (r, s) -> (p, q)
+// loses its creation factor sqrt((n_p + 1)(n_q + 1 + [p = q])) (see the stage kernel).
 template <int MT>
 __device__ __forceinline__ double2 ket_weight(const Tables& t, const uint8_t* occ, int stride) {
   const int M = (MT > 0) ? MT : t.M;
@@ -177,6 +178,7 @@ __device__ __forceinline__ double2 ket_weight(const Tables& t, const uint8_t* oc
   for (int m = 0; m < kMB; ++m)
     if (m < M) rem += occ[m * stride];
   const int V = t.nmax + 1;
+  const double2 c = __ldg(t.wscale + rem);  // rem = N here
   double w = 1.0, wi = 1.0;
 #pragma unroll
   for (int m = 0; m < kMB - 1; ++m) {
@@ -187,7 +189,37 @@ __device__ __forceinline__ double2 ket_weight(const Tables& t, const uint8_t* oc
     wi *= f.y;
     rem -= nm;
   }
-  return make_double2(w, wi);
+  return make_double2(w * c.x, wi * c.y);
+}
+
+// n_m of a packed occupation word (Tables::occ)
+__device__ __forceinline__ int occ_of(uint64_t word, int m, int ob) {
+  return (int)((uint32_t)(word >> (m * ob)) & ((1u << ob) - 1u));
+}
+
+// ket_weight from a packed occupation word: the same products in the same order
+template <int MT>
+__device__ __forceinline__ double2 ket_weight_word(const Tables& t, uint64_t word) {
+  const int M = (MT > 0) ? MT : t.M;
+  constexpr int kMB = (MT > 0) ? MT : 16;
+  const int ob = t.occ_bits;
+  int rem = 0;
+#pragma unroll
+  for (int m = 0; m < kMB; ++m)
+    if (m < M) rem += occ_of(word, m, ob);
+  const int V = t.nmax + 1;
+  const double2 c = __ldg(t.wscale + rem);
+  double w = 1.0, wi = 1.0;
+#pragma unroll
+  for (int m = 0; m < kMB - 1; ++m) {
+    if (m >= M - 1) break;
+    const int nm = occ_of(word, m, ob);
+    const double2 f = __ldg(t.wtab + rem * V + nm);
+    w *= f.x;
+    wi *= f.y;
+    rem -= nm;
+  }
+  return make_double2(w * c.x, wi * c.y);
 }
 
 // Rank of the ket obtained from the row's ket by changing the occupations of
@@ -367,30 +399,6 @@ struct DfArgs {
   float2 zf;           // zre as double-float
   int* status;
 };
-
-// Shared scratch of the double-float stage kernel, after the table image, per
-// warp (each warp owns a tile of kWarpRows kets):
-//   sidx  int32 [M][kWarpRows]  flat E index of each ket's suffix state at mode m,
-//                               minus kDeltaBias (so a stored shift byte adds directly)
-//   socc  uint8 [M][kWarpRows]  occupations
-//   sD    int32 [kWarpRows]     sector dimension of the ket (-1: no ket)
-//   sOff  int64 [kWarpRows]     sector offset of the ket
-//   sperm uint8 [kWarpRows]     processing order (kets sorted by work, most first)
-//   hist  int32 [2][n_ann+2]    counting-sort buckets and cursors
-#ifndef QB_WARP_ROWS
-#define QB_WARP_ROWS 64
-#endif
-constexpr int kWarpRows = QB_WARP_ROWS;
-
-__host__ __device__ inline size_t df_warp_scratch_bytes(int M, int n_ann) {
-  size_t b = (size_t)M * kWarpRows * 4 + (((size_t)M * kWarpRows + 15) & ~(size_t)15);
-  b += (size_t)kWarpRows * 4 + (size_t)kWarpRows * 8 + kWarpRows + 2 * (size_t)(n_ann + 2) * 4;
-  return (b + 15) & ~(size_t)15;
-}
-
-__host__ __device__ inline size_t df_scratch_bytes(int M, int n_ann) {
-  return (size_t)(kBlock / 32) * df_warp_scratch_bytes(M, n_ann);
-}
 
 // Resident CTAs per SM of `kernel` with `smem` dynamic shared memory, cached
 // per (kernel, smem) so that launch loops do not repeat the occupancy query.

@@ -201,7 +201,11 @@ static int build_tables(Space& sp) {
   off = align16(off + sizeof(float) * 2 * (size_t)(nmax + 3));
   t.o_Gf = (int)off;
   off = align16(off + sizeof(float) * 4 * (size_t)std::max(1, t.n_combo));
+  t.o_dsw = (int)off;
+  off = align16(off + sizeof(int32_t) * 8 * (size_t)std::max(1, t.n_combo));
   t.blob_bytes = (int)off;
+  // two ranking-table byte offsets share one 32-bit word when the table spans < 64 KB
+  t.sw_ok = (!sp.exact && (int64_t)M * t.rem_w * twoQ * 4 <= 65536) ? 1 : 0;
   // exact momentum: the fill counts and the ranking table grow with (M-1) n_max
   // and stay in global memory for every kernel
   t.sm_from = sp.exact ? t.o_sqrt : 0;
@@ -231,6 +235,14 @@ static int build_tables(Space& sp) {
     uint8_t* dl = (uint8_t*)(b + t.o_delta);
     for (int j = 0; j < t.n_combo; ++j)
       for (int m = 0; m < 16; ++m) dl[(size_t)j * 16 + m] = (uint8_t)(delta[j][m] + kDeltaBias);
+  }
+  {  // packed byte shifts: a signed sum, so that the low half's borrow is part of the value
+    int32_t* dw = (int32_t*)(b + t.o_dsw);
+    for (int j = 0; j < t.n_combo; ++j)
+      for (int k = 0; k < 8; ++k) {
+        const int lo = delta[j][2 * k + 1], hi = (2 * k + 2 < 16) ? delta[j][2 * k + 2] : 0;
+        dw[(size_t)j * 8 + k] = (int32_t)(4 * lo + 65536 * 4 * hi);
+      }
   }
   memcpy(b + t.o_ann, annStart.data(), sizeof(int32_t) * annStart.size());
   memcpy(b + t.o_pairidx, pairidx, 256);
@@ -412,6 +424,14 @@ void derive(int M, const double* raw, qb_obs* o) {
   o->Vminus_p = 1.0 + 2.0 * dd.real() - 2.0 * std::abs(var);
 }
 
+double log2_max_ket_weight(int M, int N) {
+  // N! / prod n_m! is largest for the most even occupation: N mod M modes hold
+  // floor(N / M) + 1 particles, the rest floor(N / M)
+  const int q = N / M, r = N % M;
+  const double ln = std::lgamma(N + 1.0) - r * std::lgamma(q + 2.0) - (M - r) * std::lgamma(q + 1.0);
+  return 0.5 * ln / std::log(2.0);
+}
+
 }  // namespace qb
 
 using namespace qb;
@@ -441,6 +461,13 @@ int qb_sector_build(const qb_model* model, int n_min, int n_max, const int* p_li
   if (M * bits > 64 || n_max > 250) {
     delete sp;
     return fail(QB_EUNSUPPORTED, "occupation vectors do not pack into 64 bits (M * bits(n_max) > 64)");
+  }
+  // the stages hold psi / w(n) as fp32 pairs; the centred weights of the deepest sector
+  // must stay within the range that keeps them exact (log2 w_max(n_max) <= 160)
+  if (log2_max_ket_weight(M, n_max) > kMaxLog2KetWeight) {
+    delete sp;
+    return fail(QB_EUNSUPPORTED, "ket weights sqrt(N!/prod n!) of the deepest sector exceed 2^160 (reduce n_max): "
+                                 "the weighted stage vectors would leave the fp32 exponent range");
   }
   sp->nmin = n_min;
   sp->nmax = n_max;
@@ -700,6 +727,14 @@ int qb_space_set_resident_max(qb_space* space, int resident_max_kets) {
   if (!sp) return fail(QB_EINVAL, "space is NULL");
   if (resident_max_kets < 0) return fail(QB_EINVAL, "resident_max_kets must be >= 0");
   sp->resident_max_kets = resident_max_kets;
+  return QB_OK;
+}
+
+int qb_space_set_tile_shape(qb_space* space, int shape) {
+  Space* sp = reinterpret_cast<Space*>(space);
+  if (!sp) return fail(QB_EINVAL, "space is NULL");
+  if (shape < 0 || shape >= QB_TILE_SHAPES) return fail(QB_EINVAL, "shape must be in [0, QB_TILE_SHAPES)");
+  sp->tile_shape = shape;
   return QB_OK;
 }
 

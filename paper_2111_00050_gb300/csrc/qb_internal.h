@@ -52,6 +52,10 @@ struct Tables {
   int o_gd;      // double [n_ann]             diagonal two-body coefficient mult_rs^2 L^sym_{rs;rs}
   int o_sqf;     // float2 [nmax+3]            sqrt(k) as a double-float pair (hi, lo)
   int o_Gf;      // float4 [n_combo]           G as double-float pairs (re.hi, re.lo, im.hi, im.lo)
+  int o_dsw;     // int32  [n_combo][8]        byte shifts of the suffix index, two modes per word: word k
+                 //   holds 4 shift(2k+1) + 65536 * 4 shift(2k+2) (the ranking table's byte offsets of
+                 //   modes 2k+1 and 2k+2 added in one 32-bit add, see the stage kernel)
+  int sw_ok;     // 1: every byte offset into the ranking table fits 16 bits (mod-M momentum only)
   const unsigned char* blob;  // device pointer to the image
   // sectors
   int n_sectors;
@@ -63,6 +67,12 @@ struct Tables {
   // ket weights w(n) = sqrt(N! / prod_m n_m!) = prod_m sqrt(C(rem_m, n_m)), rem_m the
   // particles in modes m..M-1: entry [rem * (nmax + 1) + k] = (sqrt(C(rem, k)), its inverse)
   const double2* wtab;
+  // per particle number N: (2^-e_N, 2^e_N), e_N = round(log2(w_max(N)) / 2) with w_max(N)
+  // the largest ket weight of N particles in M modes; the stages use w(n) 2^-e_N, which
+  // keeps every weight of the sector within [2^-k, 2^k], k = log2(w_max) / 2 + 1/2.  A
+  // constant per sector is a similarity inside each diagonal block of H, so the
+  // weighted operator is unchanged; a power of two changes no rounding.
+  const double2* wscale;
   // packed occupation vector of every ket (written with the diagonal): n_m in bits
   // [m * occ_bits, (m + 1) * occ_bits), occ_bits the bit length of nmax
   int occ_bits;
@@ -100,6 +110,7 @@ struct Space {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int resident_max_kets = 1024;           // sectors up to this size run shared-memory resident
   int order = 4;                          // Taylor order of a time step (4: RK4)
+  int tile_shape = 0;                     // tile shape of the single-state stage kernel (qb_stage.cuh)
   int device = 0;
   int grid_hpsi = 0;  // persistent grid sizes per kernel family
 };
@@ -107,6 +118,33 @@ struct Space {
 // error handling
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
+// reads the space's device status word (clearing it): QB_EINTERNAL if a device-side
+// check failed since the last read
+int check_status(const Space& s, cudaStream_t st);
+
+// Raw moments of one state (doubles): [0] norm, [1] <N> norm, [2] <H> norm, [3] unused,
+// then <a_i> [M], <a_i^dag a_j> [M*M], <a_i a_j> [M*M] as (re, im) pairs.
+__host__ __device__ inline int nmoments(int M) { return 4 + 2 * M + 4 * M * M; }
+// Columns of the per-CTA partials of the observables' first pass: norm, <N>, <n_i> [M].
+__host__ __device__ inline int nprep(int M) { return M + 2; }
+
+// Scratch layout of a space (doubles), sized at set-up for the largest persistent grid
+// G = SMs * 16:  [0, 2) status word | moment partials [G nmom] | moment sums [nmom] |
+// bilinear / <H> partials [(M + 1) G] | their sums [QB_MAX_MODES + 2] | amplitude table
+// [2 M (nmax + 1)] | initial-state norm [2] | first-pass partials [nprep G] | their sums [nprep]
+inline int64_t scratch_doubles_for(int M, int nmax, int64_t G) {
+  return 2 + G * nmoments(M) + nmoments(M) + (int64_t)(M + 1) * G + QB_MAX_MODES + 2 + 2 * (int64_t)M * (nmax + 1) +
+         2 + G * nprep(M) + nprep(M);
+}
+inline int64_t max_grid_of(const Space& s) { return s.scratch_doubles > 0 ? (int64_t)s.grid_hpsi : 0; }
+inline double* partial_area(const Space& s) { return s.d_scratch + 2; }
+inline double* final_area(const Space& s) { return partial_area(s) + max_grid_of(s) * nmoments(s.M); }
+inline double* dot_area(const Space& s) { return final_area(s) + nmoments(s.M); }
+inline double* dot_final(const Space& s) { return dot_area(s) + (int64_t)(s.M + 1) * max_grid_of(s); }
+inline double* table_area(const Space& s) { return dot_final(s) + QB_MAX_MODES + 2; }
+inline double* init_final(const Space& s) { return table_area(s) + 2 * (size_t)s.M * (s.nmax + 1); }
+inline double* prep_area(const Space& s) { return init_final(s) + 2; }
+inline double* prep_final(const Space& s) { return prep_area(s) + max_grid_of(s) * nprep(s.M); }
 
 // launchers (qb_kernels.cu); all return a QB_* status
 int launch_hpsi(const Space& s, const void* d_v, void* d_out, void* stream);
@@ -130,6 +168,12 @@ int launch_to_df(const void* psi, void* psif, int64_t n, void* stream);
 int launch_to_dfw(const Space& s, const void* psi, void* psif, int B, void* stream);
 // observables of Sec. II C-E from the raw moments (host)
 void derive(int M, const double* raw, qb_obs* out);
+// log2 of the largest ket weight sqrt(N! / prod_m n_m!) over all occupations of N
+// particles in M modes (the most even one), and the largest log2 weight a space may
+// reach: the stage vectors hold psi / w as fp32 pairs, so the centred weights
+// w 2^-e_N must stay within 2^+-80 (qb_sector_build refuses deeper spaces)
+double log2_max_ket_weight(int M, int N);
+constexpr double kMaxLog2KetWeight = 160.0;
 int device_setup(Space& s);
 
 }  // namespace qb

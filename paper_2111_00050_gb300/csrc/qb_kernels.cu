@@ -180,21 +180,12 @@ __global__ void to_df_kernel(const double2* psi, float4* out, int64_t n) {
   }
 }
 
-// psi (FP64, [B][total]) -> double-float copy in the weighted basis, f = psi / w(n)
-__global__ void __launch_bounds__(kBlock) to_dfw_kernel(const Tables t, const double2* psi, float4* out, int B) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  load_blob(t, smem);
-  const View v = make_view(t, smem);
-  const RowScratch rs = row_scratch(smem + blob_smem(t));
-  const int tid = threadIdx.x;
-  for (int64_t base = (int64_t)blockIdx.x * kBlock; base < t.total; base += (int64_t)gridDim.x * kBlock) {
-    const int64_t g = base + tid;
-    if (g >= t.total) break;
-    const int sid = find_sector(t, g);
-    const int64_t off = __ldg(t.sec_off + sid);
-    const int64_t D = __ldg(t.sec_off + sid + 1) - off;
-    setup_row(t, v, rs, __ldg(t.sec_N + sid), __ldg(t.sec_K + sid), D, g - off);
-    const double wi = ket_weight<0>(t, rs.occ + tid, kBlock).y;
+// psi (FP64, [B][total]) -> double-float copy in the weighted basis, f = psi / w(n),
+// the ket weights taken from the packed occupation table (coalesced, no unranking)
+template <int MT>
+__global__ void __launch_bounds__(256) to_dfw_kernel(const Tables t, const double2* psi, float4* out, int B) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < t.total; g += (int64_t)gridDim.x * blockDim.x) {
+    const double wi = ket_weight_word<MT>(t, __ldg(t.occ + g)).y;
     for (int b = 0; b < B; ++b) {
       const double2 x = psi[(size_t)b * t.total + g];
       out[(size_t)b * t.total + g] = df_pack(df_of(x.x * wi), df_of(x.y * wi));
@@ -545,555 +536,13 @@ __global__ void __launch_bounds__(kBlock) moments_kernel(const Tables t, const d
 }
 
 
-// Double-float moments: the same sums as moments_kernel from the double-float copy
-// of the state (no FP64 arithmetic per target).
-//
-// The moments are organised as slots, each one operator acting on the row's ket:
-// a_i (M slots), n_i (M), a_i^dag a_j for i < j (the i > j half follows by
-// Hermiticity) and a_i a_j for i <= j (the matrix is symmetric).  A slot changes at
-// most two occupations, (e0, dn0) and (e1, dn1), so one loop over a shared slot
-// table serves them all: target sector, rank, gather and the product c conj(y) x.
-// Every tile of 32 kets (one per lane) emits the same sequence of values: norm,
-// N norm, then Re and Im of each slot.  A lane writes its value into column `lane`
-// of a per-warp 16 x 32 buffer; once 16 values are in, lane r < 16 sums row r over
-// the warp's 32 kets and adds the sum to the warp's double-float accumulator of
-// that value.  The sector offsets and the (N, K) -> sector map are staged in shared
-// memory when they are small, and the per-thread row scratch is sized for M modes.
-
-// x mod Q for x in (-2Q, 3Q), by conditional adds (no integer division)
-__device__ __forceinline__ int mod_small(int x, int M) {
-  if (x < 0) x += M;
-  if (x < 0) x += M;
-  if (x >= M) x -= M;
-  if (x >= M) x -= M;
-  return x;
-}
-
-// rank of the ket reached by changing mode e0 by dn0 and (nch = 2) mode e1 by dn1.
-// The suffix state at mode m holds the changes of the modes >= m, so the shift of
-// its table index is constant on three runs of m: none above hi = max(e0, e1) (the
-// row's own prefix sums), the change at hi alone on (lo, hi], both on [1, lo].
-__device__ __forceinline__ int64_t rank_moved(const Tables& t, const View& v, const RowScratch& rs, int nch, int e0,
-                                              int dn0, int e1, int dn1, int64_t Dt) {
-  const int M = t.M, Q = t.Q, tid = threadIdx.x, twoQ = 2 * Q;
-  if (nch < 2 || dn1 == 0) {
-    e1 = e0;
-    dn1 = 0;
-  }
-  const int hi = max(e0, e1), lo = min(e0, e1);
-  int sum = rs.pe[(M - 1) * kBlock + tid] - rs.pe[hi * kBlock + tid];
-  const int* idx = rs.idx + tid;
-  if (lo < hi) {  // two distinct modes: the one at hi alone on (lo, hi]
-    const int dh = (hi == e0) ? dn0 : dn1;
-    const int sh = dh * twoQ + mod_small(dh * hi, Q);
-    for (int m = hi; m > lo; --m) sum += v.E[idx[m * kBlock] + sh];
-  }
-  const int dc = dn0 + dn1;
-  const int sb = dc * twoQ + mod_small(dn0 * e0 + dn1 * e1, Q);
-  for (int m = lo; m >= 1; --m) sum += v.E[idx[m * kBlock] + sb];
-  return Dt - 1 - (int64_t)sum;
-}
-
-// slots per ket (M a_i, M n_i, M(M-1)/2 a_i^dag a_j with i < j, M(M+1)/2 a_i a_j
-// with i <= j) and values a tile emits (norm, N norm, Re and Im of every slot)
-__host__ __device__ inline int moment_slots(int M) { return 2 * M + M * M; }
-__host__ __device__ inline int moment_values(int M) { return 2 + 2 * moment_slots(M); }
-
-enum { kSlotA = 0, kSlotN = 1, kSlotAdA = 2, kSlotAA = 3 };
-
-// kind | i << 8 | j << 16 of slot s
-__device__ inline uint32_t moment_slot_desc(int s, int M) {
-  if (s < M) return kSlotA | (uint32_t)s << 8 | (uint32_t)s << 16;
-  s -= M;
-  if (s < M) return kSlotN | (uint32_t)s << 8 | (uint32_t)s << 16;
-  s -= M;
-  int i = 0;
-  if (s < M * (M - 1) / 2) {
-    while (s >= M - 1 - i) {
-      s -= M - 1 - i;
-      ++i;
-    }
-    return kSlotAdA | (uint32_t)i << 8 | (uint32_t)(i + 1 + s) << 16;
-  }
-  s -= M * (M - 1) / 2;
-  while (s >= M - i) {
-    s -= M - i;
-    ++i;
-  }
-  return kSlotAA | (uint32_t)i << 8 | (uint32_t)(i + s) << 16;
-}
-
-// moment slot(s) of value e: out[k1] += x and, when k2 >= 0, out[k2] += s2 x
-__device__ inline void moment_fold(int e, uint32_t desc, int M, int& k1, int& k2, double& s2) {
-  const int oA = 4, oM = 4 + 2 * M, oAA = 4 + 2 * M + 2 * M * M;
-  k2 = -1;
-  s2 = 1.0;
-  if (e < 2) {
-    k1 = e;
-    return;
-  }
-  const int part = (e - 2) & 1, kind = desc & 0xff, i = (desc >> 8) & 0xff, j = (desc >> 16) & 0xff;
-  if (kind == kSlotA) {
-    k1 = oA + 2 * i + part;
-  } else if (kind == kSlotN) {
-    k1 = oM + 2 * (i * M + i) + part;  // the imaginary part is zero
-  } else if (kind == kSlotAdA) {
-    k1 = oM + 2 * (i * M + j) + part;
-    k2 = oM + 2 * (j * M + i) + part;  // <a_j^dag a_i> = conj <a_i^dag a_j>
-    s2 = part ? -1.0 : 1.0;
-  } else {
-    k1 = oAA + 2 * (i * M + j) + part;
-  }
-}
-
-constexpr int kTrRows = 16;    // values per flush of the per-warp transpose buffer
-constexpr int kTrStride = 33;  // row stride (float2) of that buffer
-// the block's FP64 moment row reuses the transpose buffers at the end
-static_assert((kBlock / 32) * kTrRows * kTrStride * sizeof(float2) >=
-                  (4 + 2 * kMaxM + 4 * kMaxM * kMaxM) * sizeof(double),
-              "moment row does not fit the transpose buffers");
-// 1: qb_observables runs moments_wc_kernel (lanes over the moment slots); 0: moments_df_kernel
-#ifndef QB_MOMENTS_WC
-#define QB_MOMENTS_WC 1
-#endif
-constexpr size_t kMomSecSmemMax = 16384;  // sector tables larger than this stay in global memory
-
-static size_t mom_sec_bytes(const Tables& t) {
-  return ((sizeof(int64_t) * (size_t)(t.n_sectors + 1) + 15) & ~(size_t)15) +
-         ((sizeof(int32_t) * (size_t)(t.nmax + 1) * t.Q + 15) & ~(size_t)15);
-}
-
-__device__ __forceinline__ int find_sector_in(const int64_t* off, int n, int64_t g) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (off[mid] <= g)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
-
-// first byte of the image the double-float moments kernel stages in shared memory
-__host__ __device__ inline int moments_from(const Tables& t, bool exact) { return exact ? t.o_sqrt : t.o_E; }
-
-// Row scratch of a moments CTA sized for M modes: idx [M][kBlock], pe [M][kBlock],
-// occ [M][kBlock] (setup_row and rank_moved touch modes below M only).
-__host__ __device__ inline size_t row_scratch_m_bytes(int M) { return ((size_t)M * kBlock * 9 + 15) & ~(size_t)15; }
-__device__ __forceinline__ RowScratch row_scratch_m(unsigned char* base, int M) {
-  RowScratch r;
-  r.idx = reinterpret_cast<int32_t*>(base);
-  r.pe = r.idx + M * kBlock;
-  r.occ = reinterpret_cast<uint8_t*>(r.pe + M * kBlock);
-  return r;
-}
-
-template <bool EXACT>
-__global__ void __launch_bounds__(kBlock) moments_df_kernel(const Tables t, const float4* psif, double* partial,
-                                                             int nmom, int sec_smem, int* status) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int from = moments_from(t, EXACT);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, M = t.M, Q = t.Q;
-  const int nslot = moment_slots(M);
-  unsigned char* cur = smem_raw + ((t.blob_bytes - from + 15) & ~15);
-  const RowScratch rs = row_scratch_m(cur, M);
-  cur += row_scratch_m_bytes(M);
-  uint32_t* slot_tab = reinterpret_cast<uint32_t*>(cur);
-  cur += ((size_t)nslot * 4 + 15) & ~(size_t)15;
-  // per slot, ket-independent: kind, the occupation changes (e0, dn0), (e1, dn1), and
-  // the second square-root argument a1 = m1 n_{e1} + c1 (the first is n_{e0})
-  char4* slot_op = reinterpret_cast<char4*>(cur);  // [nslot][2]
-  cur += ((size_t)nslot * 8 + 15) & ~(size_t)15;
-  for (int k = tid; k < nslot; k += kBlock) {
-    const uint32_t d = moment_slot_desc(k, M);
-    slot_tab[k] = d;
-    const int kind = d & 0xff, i = (d >> 8) & 0xff, j = (d >> 16) & 0xff;
-    int e0 = i, dn0 = -1, e1 = i, dn1 = 0, m1 = 0, c1 = 1;  // a_i: sqrt(n_i)
-    if (kind == kSlotAdA) {  // annihilate j, create i: sqrt(n_j) sqrt(n_i + 1)
-      e0 = j;
-      e1 = i;
-      dn1 = 1;
-      m1 = 1;
-    } else if (kind == kSlotAA && i == j) {  // sqrt(n_i) sqrt(n_i - 1)
-      dn0 = -2;
-      m1 = 1;
-      c1 = -1;
-    } else if (kind == kSlotAA) {  // sqrt(n_i) sqrt(n_j)
-      e1 = j;
-      dn1 = -1;
-      m1 = 1;
-      c1 = 0;
-    }
-    slot_op[2 * k] = make_char4((char)kind, (char)e0, (char)dn0, (char)e1);
-    slot_op[2 * k + 1] = make_char4((char)dn1, (char)m1, (char)c1, 0);
-  }
-  const int64_t* soff = t.sec_off;
-  const int32_t* sof = t.sec_of;
-  if (sec_smem) {
-    int64_t* o = reinterpret_cast<int64_t*>(cur);
-    for (int k = tid; k <= t.n_sectors; k += kBlock) o[k] = __ldg(t.sec_off + k);
-    cur += (sizeof(int64_t) * (size_t)(t.n_sectors + 1) + 15) & ~(size_t)15;
-    int32_t* f = reinterpret_cast<int32_t*>(cur);
-    for (int k = tid; k < (t.nmax + 1) * Q; k += kBlock) f[k] = __ldg(t.sec_of + k);
-    cur += (sizeof(int32_t) * (size_t)(t.nmax + 1) * Q + 15) & ~(size_t)15;
-    soff = o;
-    sof = f;
-  }
-  const int nval = moment_values(M), nval_pad = (nval + 31) & ~31;
-  float2* tr = reinterpret_cast<float2*>(cur);               // [warps][kTrRows][kTrStride]
-  float2* wacc = tr + (kBlock / 32) * kTrRows * kTrStride;  // [warps][nval_pad]
-  float2* wb = tr + warp * kTrRows * kTrStride;
-  float2* wa = wacc + warp * nval_pad;
-  for (int k = lane; k < nval_pad; k += 32) wa[k] = make_float2(0.f, 0.f);
-  load_blob_from(t, smem_raw, from);  // ends with a CTA barrier
-  unsigned char* smem = smem_raw - from;
-  View v = view_at(t, smem);
-  v.cnt = reinterpret_cast<const uint32_t*>(t.blob + t.o_cnt);  // fill counts stay in global memory
-  if (EXACT) v.E = reinterpret_cast<const int32_t*>(t.blob + t.o_E);  // and the (large) ranking table
-  const float2* sqf = reinterpret_cast<const float2*>(smem + t.o_sqf);
-  const dfl zero{0.f, 0.f};
-
-  int ecount = 0;  // warp-uniform: values emitted in this tile
-  // lanes r < n add the sum of buffer row r to accumulator e0 + r
-  auto flush = [&](int n, int e0) {
-    __syncwarp();
-    if (lane < n) {
-      const float2* row = wb + lane * kTrStride;
-      float h = row[0].x, l = row[0].y;
-#pragma unroll 8
-      for (int k = 1; k < 32; ++k) {
-        const float2 x = row[k];
-        const float s = __fadd_rn(h, x.x);
-        const float bb = __fsub_rn(s, h);
-        const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(x.x, bb));
-        h = s;
-        l = __fadd_rn(l, __fadd_rn(err, x.y));
-      }
-      const float2 a0 = wa[e0 + lane];
-      const dfl r = df_add(dfl{a0.x, a0.y}, df_renorm(dfl{h, l}));
-      wa[e0 + lane] = make_float2(r.h, r.l);
-    }
-    __syncwarp();
-  };
-  // writes the pair (x0, x1) as the next two values
-  auto emit2 = [&](dfl x0, dfl x1) {
-    wb[(ecount % kTrRows) * kTrStride + lane] = make_float2(x0.h, x0.l);
-    wb[((ecount + 1) % kTrRows) * kTrStride + lane] = make_float2(x1.h, x1.l);
-    ecount += 2;
-    if (ecount % kTrRows == 0) flush(kTrRows, ecount - kTrRows);
-  };
-  static_assert(kTrRows % 2 == 0, "values are emitted in pairs");
-
-  for (int64_t base = (int64_t)blockIdx.x * kBlock; base < t.total; base += (int64_t)gridDim.x * kBlock) {
-    const int64_t g = base + tid;
-    const bool live = g < t.total;
-    int N = 0, K = 0;
-    dfl xr = zero, xi = zero;
-    if (live) {
-      const int sid = find_sector_in(soff, t.n_sectors, g);
-      const int64_t off = soff[sid];
-      const int64_t D = soff[sid + 1] - off;
-      N = __ldg(t.sec_N + sid);
-      K = __ldg(t.sec_K + sid);
-      setup_row(t, v, rs, N, K, D, g - off);
-      const float4 x = psif[g];
-      xr = df_re(x);
-      xi = df_im(x);
-    }
-    const uint8_t* occ = rs.occ + tid;
-    ecount = 0;
-    const dfl p2 = df_add(df_mul(xr, xr), df_mul(xi, xi));
-    emit2(p2, df_mul(p2, dfl{(float)N, 0.f}));
-    for (int sl = 0; sl < nslot; ++sl) {
-      const char4 o0 = slot_op[2 * sl], o1 = slot_op[2 * sl + 1];
-      const int kind = o0.x, e0 = o0.y, dn0 = o0.z, e1 = o0.w, dn1 = o1.x;
-      if (kind == kSlotN) {  // <n_i>: no other ket involved
-        emit2(df_mul(p2, dfl{(float)(live ? occ[e0 * kBlock] : 0), 0.f}), zero);
-        continue;
-      }
-      const int a0 = live ? occ[e0 * kBlock] : 0;
-      const int a1 = o1.y ? occ[e1 * kBlock] + o1.z : o1.z;
-      const int dN = dn0 + dn1, dK = dn0 * e0 + dn1 * e1;
-      bool has = live && a0 >= 1 && a1 >= 1;  // the ket survives the annihilations
-      int64_t tg = 0;
-      if (has) {
-        const int sid = sof[(N + dN) * Q + mod_small(K + dK, Q)];
-        has = sid >= 0;
-        if (has) {
-          const int64_t off = soff[sid], D = soff[sid + 1] - off;
-          tg = off + rank_moved(t, v, rs, 2, e0, dn0, e1, dn1, D);
-          if (tg < 0 || tg >= t.total) {
-            atomicOr(status, 1);
-            has = false;
-          }
-        }
-      }
-      dfl cr = zero, ci = zero;
-      if (has) {
-        const float2 f0 = sqf[a0], f1 = sqf[a1];
-        const dfl c = df_mul(dfl{f0.x, f0.y}, dfl{f1.x, f1.y});
-        const float4 y = psif[tg];
-        const dfl yr = df_re(y), yi = df_im(y);
-        cr = df_mul(c, df_add(df_mul(yr, xr), df_mul(yi, xi)));
-        ci = df_mul(c, df_add(df_mul(yr, xi), df_neg(df_mul(yi, xr))));
-      }
-      emit2(cr, ci);
-    }
-    if (ecount % kTrRows) flush(ecount % kTrRows, ecount - ecount % kTrRows);
-  }
-  __syncthreads();
-  // the warps' accumulators into one FP64 row per block (the transpose buffers are free now)
-  double* acc = reinterpret_cast<double*>(tr);
-  for (int k = tid; k < nmom; k += kBlock) acc[k] = 0.0;
-  __syncthreads();
-  for (int w = 0; w < kBlock / 32; ++w) {
-    if (warp == w)
-      for (int e = lane; e < nval; e += 32) {
-        const float2 a0 = wacc[w * nval_pad + e];
-        const double x = (double)a0.x + (double)a0.y;
-        int k1, k2;
-        double s2;
-        moment_fold(e, e < 2 ? 0u : slot_tab[(e - 2) >> 1], M, k1, k2, s2);
-        acc[k1] += x;
-        if (k2 >= 0) acc[k2] += s2 * x;
-      }
-    __syncthreads();
-  }
-  for (int k = tid; k < nmom; k += kBlock) partial[(size_t)blockIdx.x * nmom + k] = acc[k];
-}
-
-// ------------------------------------------- warp-cooperative double-float moments
-//
-// The same sums as moments_df_kernel, organised the other way round: the lanes of
-// a warp take the entries of a slot list (entry 0 the norm and <N>, entry 1 + k
-// slot k of moment_slot_desc), and the 32 kets of a tile are visited in turn, each
-// one's amplitude, packed occupations, sector and suffix-state indices broadcast
-// by shuffle from the lane that loaded them.  A lane keeps its entries' sums in
-// double-float registers over every tile of its warp, so no value is emitted per
-// ket.  The target rank is the fixed-length sum D - 1 - sum_{m=1}^{M-1}
-// E[idx_m + shift_m]; the shift of an entry is constant on the three runs of
-// rank_moved (0 above hi, the change at hi alone on (lo, hi], both changes on
-// [1, lo]) and is tabulated per entry and mode at the start of the CTA.
-
-constexpr int kMomWarps = 8;
-constexpr int kMomBlock = 32 * kMomWarps;
-constexpr int kSlotP = 4;  // entry 0: the norm (real part) and <N> (imaginary part)
-
-__host__ __device__ inline int mom_entries(int M) { return moment_slots(M) + 1; }
-__host__ __device__ inline int mom_entries_pad(int M) { return (mom_entries(M) + 31) & ~31; }
-
-// shared memory of moments_wc_kernel after the staged table image: entry headers,
-// entry shifts [M-1][entries], the CTA's FP64 moment row
-__host__ __device__ inline size_t mom_wc_bytes(int M, int nmom) {
-  const size_t np = (size_t)mom_entries_pad(M);
-  return np * sizeof(int4) + (size_t)(M > 1 ? M - 1 : 1) * np * sizeof(int32_t) +
-         (((size_t)nmom * sizeof(double) + 15) & ~(size_t)15);
-}
-
-template <int MT, bool EXACT>
-__global__ void __launch_bounds__(kMomBlock) moments_wc_kernel(const Tables t, const float4* psif, double* partial,
-                                                               int nmom, int sec_smem, int* status) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int kMB = (MT > 0) ? MT : kMaxM;
-  constexpr int kSPL = (2 * kMB + kMB * kMB + 1 + 31) / 32;  // entries per lane
-  const int from = moments_from(t, EXACT);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int M = (MT > 0) ? MT : t.M, Q = t.Q, twoQ = 2 * Q;
-  const int nent = mom_entries(M), np = mom_entries_pad(M);
-  unsigned char* cur = smem_raw + ((t.blob_bytes - from + 15) & ~15);
-  int4* hdr = reinterpret_cast<int4*>(cur);  // kind | e0 << 8 | e1 << 16 | m1 << 24, c1, dN, dK mod Q
-  cur += (size_t)np * sizeof(int4);
-  int32_t* shf = reinterpret_cast<int32_t*>(cur);  // [M-1][np] shift of the suffix index at mode m
-  cur += (size_t)(M > 1 ? M - 1 : 1) * np * sizeof(int32_t);
-  double* row = reinterpret_cast<double*>(cur);  // [nmom]
-  cur += ((size_t)nmom * sizeof(double) + 15) & ~(size_t)15;
-  for (int s = tid; s < np; s += kMomBlock) {
-    // a0 = n_{e0}, a1 = m1 n_{e1} + c1: the operator's square-root arguments; the
-    // target changes mode e0 by dn0 and mode e1 by dn1 (kinds as in moments_df_kernel)
-    int kind = 7, e0 = 0, dn0 = 0, e1 = 0, dn1 = 0, m1 = 0, c1 = 0;
-    if (s == 0) {
-      kind = kSlotP;
-    } else if (s < nent) {
-      const uint32_t d = moment_slot_desc(s - 1, M);
-      kind = d & 0xff;
-      const int i = (d >> 8) & 0xff, j = (d >> 16) & 0xff;
-      e0 = i;
-      dn0 = -1;
-      e1 = i;
-      c1 = 1;
-      if (kind == kSlotAdA) {  // annihilate j, create i
-        e0 = j;
-        dn1 = 1;
-        m1 = 1;
-      } else if (kind == kSlotAA && i == j) {
-        dn0 = -2;
-        m1 = 1;
-        c1 = -1;
-      } else if (kind == kSlotAA) {
-        e1 = j;
-        dn1 = -1;
-        m1 = 1;
-        c1 = 0;
-      }
-    }
-    const bool moves = kind == kSlotA || kind == kSlotAdA || kind == kSlotAA;
-    const int f1 = (dn1 == 0) ? e0 : e1;  // a zero second change acts on e0
-    const int hi = max(e0, f1), lo = min(e0, f1);
-    const int dh = (hi == e0) ? dn0 : dn1;
-    const int sh = dh * twoQ + mod_small(dh * hi, Q);
-    const int dc = dn0 + dn1, dk = mod_small(dn0 * e0 + dn1 * f1, Q);
-    const int sb = dc * twoQ + dk;
-    for (int m = 1; m < M; ++m) shf[(m - 1) * np + s] = !moves ? 0 : (m > hi ? 0 : (m > lo ? sh : sb));
-    hdr[s] = make_int4(kind | (e0 << 8) | (e1 << 16) | (m1 << 24), c1, dc, dk);
-  }
-  const int64_t* soff = t.sec_off;
-  const int32_t* sof = t.sec_of;
-  if (sec_smem) {
-    int64_t* o = reinterpret_cast<int64_t*>(cur);
-    for (int k = tid; k <= t.n_sectors; k += kMomBlock) o[k] = __ldg(t.sec_off + k);
-    cur += (sizeof(int64_t) * (size_t)(t.n_sectors + 1) + 15) & ~(size_t)15;
-    int32_t* f = reinterpret_cast<int32_t*>(cur);
-    for (int k = tid; k < (t.nmax + 1) * Q; k += kMomBlock) f[k] = __ldg(t.sec_of + k);
-    soff = o;
-    sof = f;
-  }
-  for (int k = tid; k < nmom; k += kMomBlock) row[k] = 0.0;
-  load_blob_from(t, smem_raw, from);  // ends with a CTA barrier
-  unsigned char* smem = smem_raw - from;
-  View v = view_at(t, smem);
-  if (EXACT) v.E = reinterpret_cast<const int32_t*>(t.blob + t.o_E);  // the (large) ranking table stays global
-  const float2* sqf = reinterpret_cast<const float2*>(smem + t.o_sqf);
-  const int ob = t.occ_bits;
-  const uint32_t omask = (1u << ob) - 1u;
-  const int64_t total = t.total;
-  const int64_t ntiles = (total + 31) / 32;
-
-  dfl acc_r[kSPL], acc_i[kSPL];
-#pragma unroll
-  for (int r = 0; r < kSPL; ++r) acc_r[r] = acc_i[r] = dfl{0.f, 0.f};
-
-  for (int64_t tile = (int64_t)blockIdx.x * kMomWarps + warp; tile < ntiles; tile += (int64_t)gridDim.x * kMomWarps) {
-    // this lane's ket: amplitude, |x|^2, packed occupations, (N, K), suffix-state indices
-    const int64_t g = tile * 32 + lane;
-    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-    dfl p2{0.f, 0.f};
-    uint64_t word = 0;
-    int nk = 0;
-    int idx[kMB];
-#pragma unroll
-    for (int m = 0; m < kMB; ++m) idx[m] = 0;
-    if (g < total) {
-      const int sid = find_sector_in(soff, t.n_sectors, g);
-      nk = __ldg(t.sec_N + sid) | (__ldg(t.sec_K + sid) << 8);
-      word = __ldg(t.occ + g);
-      x = psif[g];
-      p2 = df_add(df_mul(df_re(x), df_re(x)), df_mul(df_im(x), df_im(x)));
-      int srem = 0, skr = 0;
-#pragma unroll
-      for (int m = kMB - 1; m >= 1; --m) {
-        if (m < M) {
-          const int nm = (int)((uint32_t)(word >> (m * ob)) & omask);
-          srem += nm;
-          skr += m * nm;
-          while (skr >= Q) skr -= Q;
-          idx[m] = (m * t.rem_w + srem + 2) * twoQ + skr;
-        }
-      }
-    }
-    const int nt = (int)min((int64_t)32, total - tile * 32);
-    for (int j = 0; j < nt; ++j) {
-      const float4 xj = make_float4(__shfl_sync(~0u, x.x, j), __shfl_sync(~0u, x.y, j), __shfl_sync(~0u, x.z, j),
-                                    __shfl_sync(~0u, x.w, j));
-      const dfl p2j{__shfl_sync(~0u, p2.h, j), __shfl_sync(~0u, p2.l, j)};
-      const uint64_t wj = ((uint64_t)__shfl_sync(~0u, (uint32_t)(word >> 32), j) << 32) |
-                          (uint64_t)__shfl_sync(~0u, (uint32_t)word, j);
-      const int nkj = __shfl_sync(~0u, nk, j);
-      const int N = nkj & 0xff, K = nkj >> 8;
-      int id[kMB];
-#pragma unroll
-      for (int m = 1; m < kMB; ++m)
-        if (m < M) id[m] = __shfl_sync(~0u, idx[m], j);
-      const dfl xr = df_re(xj), xi = df_im(xj);
-#pragma unroll
-      for (int r = 0; r < kSPL; ++r) {
-        const int s = r * 32 + lane;
-        if (s >= nent) continue;
-        const int4 h = hdr[s];
-        const int kind = h.x & 0xff, e0 = (h.x >> 8) & 0xff, e1 = (h.x >> 16) & 0xff, m1 = (h.x >> 24) & 0xff;
-        if (kind == kSlotP) {
-          acc_r[r] = df_add(acc_r[r], p2j);
-          acc_i[r] = df_add(acc_i[r], df_mul(p2j, dfl{(float)N, 0.f}));
-          continue;
-        }
-        const int a0 = (int)((uint32_t)(wj >> (e0 * ob)) & omask);
-        if (kind == kSlotN) {
-          acc_r[r] = df_add(acc_r[r], df_mul(p2j, dfl{(float)a0, 0.f}));
-          continue;
-        }
-        const int a1 = m1 * (int)((uint32_t)(wj >> (e1 * ob)) & omask) + h.y;
-        if (a0 < 1 || a1 < 1) continue;  // the operator annihilates this ket
-        int Kt = K + h.w;
-        if (Kt >= Q) Kt -= Q;
-        const int sid = sof[(N + h.z) * Q + Kt];
-        if (sid < 0) continue;  // target sector outside the space
-        const int64_t off = soff[sid];
-        const int Dt = (int)(soff[sid + 1] - off);
-        int esum = 0;
-#pragma unroll
-        for (int m = 1; m < kMB; ++m)
-          if (m < M) esum += v.E[id[m] + shf[(m - 1) * np + s]];
-        const int rk = Dt - 1 - esum;
-        if ((unsigned)rk >= (unsigned)Dt) {
-          atomicOr(status, 1);
-          continue;
-        }
-        const float4 y = psif[off + rk];
-        const float2 f0 = sqf[a0], f1 = sqf[a1];
-        const dfl c = df_mul(dfl{f0.x, f0.y}, dfl{f1.x, f1.y});
-        const dfl yr = df_re(y), yi = df_im(y);
-        acc_r[r] = df_add(acc_r[r], df_mul(c, df_add(df_mul(yr, xr), df_mul(yi, xi))));
-        acc_i[r] = df_add(acc_i[r], df_mul(c, df_add(df_mul(yr, xi), df_neg(df_mul(yi, xr)))));
-      }
-    }
-  }
-  // the lanes' sums into the CTA's FP64 row, one warp at a time (a fixed order); the
-  // entries of a warp land on distinct moments
-  for (int w = 0; w < kMomWarps; ++w) {
-    if (warp == w) {
-#pragma unroll
-      for (int r = 0; r < kSPL; ++r) {
-        const int s = r * 32 + lane;
-        if (s < nent) {
-          const uint32_t desc = (s == 0) ? 0u : moment_slot_desc(s - 1, M);
-          for (int part = 0; part < 2; ++part) {
-            const dfl a = part ? acc_i[r] : acc_r[r];
-            const int e = (s == 0) ? part : 2 + 2 * (s - 1) + part;
-            int k1, k2;
-            double s2;
-            moment_fold(e, desc, M, k1, k2, s2);
-            const double xv = (double)a.h + (double)a.l;
-            row[k1] += xv;
-            if (k2 >= 0) row[k2] += s2 * xv;
-          }
-        }
-      }
-    }
-    __syncthreads();
-  }
-  for (int k = tid; k < nmom; k += kMomBlock) partial[(size_t)blockIdx.x * nmom + k] = row[k];
-}
-
 // ------------------------------------------------------------------ host side
 
 static size_t row_smem(const Tables& t) { return blob_smem(t) + kRowScratchBytes; }
 
-static int nmoments(int M) { return 4 + 2 * M + 4 * M * M; }
-
 // grid of a persistent row kernel, capped by the scratch sizing
 
-
-static int check_status(const Space& s, cudaStream_t st) {
+int check_status(const Space& s, cudaStream_t st) {
   int h = 0;
   int* d = reinterpret_cast<int*>(s.d_scratch);  // status word lives at the head of the scratch area
   QB_CUDA(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1105,18 +554,6 @@ static int check_status(const Space& s, cudaStream_t st) {
   }
   return QB_OK;
 }
-
-// Scratch layout (doubles), sized at space setup for the largest persistent
-// grid G = sms * 16:  [0, 2) status word | partials [G * nmom] | final [nmom]
-// | dot partials [(M + 1) G] | dot final [QB_MAX_MODES + 2] | amplitude table [2 M (nmax+1)] | init final [2]
-static int nmoments(int M);
-static int64_t max_grid_of(const Space& s) { return s.scratch_doubles > 0 ? (int64_t)s.grid_hpsi : 0; }
-static double* partial_area(const Space& s) { return s.d_scratch + 2; }
-static double* final_area(const Space& s) { return partial_area(s) + max_grid_of(s) * nmoments(s.M); }
-static double* dot_area(const Space& s) { return final_area(s) + nmoments(s.M); }
-static double* dot_final(const Space& s) { return dot_area(s) + (int64_t)(s.M + 1) * max_grid_of(s); }
-static double* table_area(const Space& s) { return dot_final(s) + kMaxM + 2; }
-static double* init_final(const Space& s) { return table_area(s) + 2 * (size_t)s.M * (s.nmax + 1); }
 
 int device_setup(Space& s) {
   QB_CUDA(cudaGetDevice(&s.device));
@@ -1146,8 +583,7 @@ int device_setup(Space& s) {
   QB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s.device));
   const int64_t max_grid = (int64_t)sms * 16;
   s.grid_hpsi = (int)max_grid;
-  s.scratch_doubles = 2 + max_grid * nmoments(s.M) + nmoments(s.M) + (int64_t)(s.M + 1) * max_grid + kMaxM + 2 +
-                      2 * (int64_t)s.M * (s.nmax + 1) + 2;
+  s.scratch_doubles = scratch_doubles_for(s.M, s.nmax, max_grid);
   QB_CUDA(cudaMalloc(&s.d_scratch, sizeof(double) * s.scratch_doubles));
   QB_CUDA(cudaMemset(s.d_scratch, 0, sizeof(double) * s.scratch_doubles));
   QB_CUDA(cudaMalloc(&s.d_diag, sizeof(float4) * (size_t)t.total));
@@ -1157,21 +593,36 @@ int device_setup(Space& s) {
   while ((1 << t.occ_bits) <= s.nmax) ++t.occ_bits;  // M * occ_bits <= 64 (checked by qb_sector_build)
   t.occ = s.d_occ;
   {
-    // sqrt(C(rem, k)) from the exact binomial (C(77, 38) < 2^75 fits 128 bits), then
-    // one rounding to double, one correctly rounded sqrt and one division
+    // sqrt(C(rem, k)): the binomial exactly in 128 bits while it fits (rem <= 125:
+    // C(125, 62) < 2^122), then one rounding to double, one correctly rounded sqrt
+    // and one division; beyond, by the recurrence C(rem, k) = C(rem, k-1) (rem-k+1) / k
+    // in long double (at least 64 significant bits: the accumulated relative error
+    // of at most 2 rem roundings stays far below a double's half-ulp)
     const int V = s.nmax + 1;
     std::vector<double2> wt((size_t)V * V, make_double2(0.0, 0.0));
     for (int rem = 0; rem < V; ++rem) {
       unsigned __int128 c = 1;
+      long double cl = 1.0L;
       for (int k = 0; k <= rem; ++k) {
-        if (k > 0) c = c * (unsigned __int128)(rem - k + 1) / (unsigned __int128)k;
-        const double r = std::sqrt((double)c);
+        if (k > 0) {
+          if (rem <= 125)
+            c = c * (unsigned __int128)(rem - k + 1) / (unsigned __int128)k;
+          else
+            cl = cl * (long double)(rem - k + 1) / (long double)k;
+        }
+        const double r = rem <= 125 ? std::sqrt((double)c) : (double)std::sqrt(cl);
         wt[(size_t)rem * V + k] = make_double2(r, 1.0 / r);
       }
+    }
+    // after the table: the per-N centring powers of two (Tables::wscale)
+    for (int N = 0; N < V; ++N) {
+      const int e = (int)std::floor(0.5 * log2_max_ket_weight(s.M, N) + 0.5);
+      wt.push_back(make_double2(std::ldexp(1.0, -e), std::ldexp(1.0, e)));
     }
     QB_CUDA(cudaMalloc(&s.d_wtab, sizeof(double2) * wt.size()));
     QB_CUDA(cudaMemcpy(s.d_wtab, wt.data(), sizeof(double2) * wt.size(), cudaMemcpyHostToDevice));
     t.wtab = s.d_wtab;
+    t.wscale = s.d_wtab + (size_t)V * V;
   }
   {
     const size_t smem = row_smem(t);
@@ -1249,13 +700,13 @@ static int rk4_issue(Space& s, DfArgs& a, double dt, int64_t steps, float4* w1, 
       if (!plain) {
         a.row0 = row0;
         a.row1 = s.t.total;
-        int rc = stage_launch(s.t, a, d == 1 ? 1 : 0, B, cplx, st, nullptr, false, true);
+        int rc = stage_launch(s.t, a, d == 1 ? 1 : 0, B, cplx, st, nullptr, false, s.tile_shape);
         if (rc) return rc;
       } else {
         for (size_t sec = 0; sec + 1 < s.secOff.size(); ++sec) {
           a.row0 = s.secOff[sec];
           a.row1 = s.secOff[sec + 1];
-          int rc = stage_launch(s.t, a, d == 1 ? 1 : 0, B, cplx, st, nullptr, false, true);
+          int rc = stage_launch(s.t, a, d == 1 ? 1 : 0, B, cplx, st, nullptr, false, s.tile_shape);
           if (rc) return rc;
         }
       }
@@ -1391,11 +842,20 @@ int launch_rk4(Space& s, void* d_psi, int batch, const double* scale, double dt,
 }
 
 int launch_to_dfw(const Space& s, const void* psi, void* psif, int B, void* stream) {
-  const size_t smem = row_smem(s.t);
-  int grid = 0;
-  int rc = persistent_grid(to_dfw_kernel, smem, s.t.total, &grid);
-  if (rc) return rc;
-  to_dfw_kernel<<<grid, kBlock, smem, (cudaStream_t)stream>>>(s.t, (const double2*)psi, (float4*)psif, B);
+  int dev = 0, sms = 0;
+  QB_CUDA(cudaGetDevice(&dev));
+  QB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t want = (s.t.total + 255) / 256;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
+  auto k = to_dfw_kernel<0>;
+  switch (s.M) {
+    case 5: k = to_dfw_kernel<5>; break;
+    case 7: k = to_dfw_kernel<7>; break;
+    case 9: k = to_dfw_kernel<9>; break;
+    case 11: k = to_dfw_kernel<11>; break;
+    default: break;
+  }
+  k<<<grid, 256, 0, (cudaStream_t)stream>>>(s.t, (const double2*)psi, (float4*)psif, B);
   QB_CUDA(cudaGetLastError());
   return QB_OK;
 }
@@ -1520,73 +980,6 @@ int launch_moments_fp64(Space& s, const void* d_psi, double* out_host, void* str
   return check_status(s, st);
 }
 
-int launch_moments(Space& s, const void* d_psi, double* out_host, void* stream) {
-  cudaStream_t st = (cudaStream_t)stream;
-  const int nmom = nmoments(s.M);
-  int rc = launch_to_df(d_psi, s.d_obsf, s.t.total, stream);
-  if (rc) return rc;
-  const int sec_smem = mom_sec_bytes(s.t) <= kMomSecSmemMax ? 1 : 0;
-  const bool ex = s.t.exact != 0;
-  const size_t image = (size_t)(s.t.blob_bytes - moments_from(s.t, ex) + 15) & ~(size_t)15;
-  int grid = 0;
-  double* part = partial_area(s);
-#if QB_MOMENTS_WC
-  {
-    const size_t smem = image + mom_wc_bytes(s.M, nmom) + (sec_smem ? mom_sec_bytes(s.t) : 0);
-    decltype(&moments_wc_kernel<0, false>) kern;
-    switch (s.M) {
-      case 5: kern = ex ? moments_wc_kernel<5, true> : moments_wc_kernel<5, false>; break;
-      case 7: kern = ex ? moments_wc_kernel<7, true> : moments_wc_kernel<7, false>; break;
-      case 9: kern = ex ? moments_wc_kernel<9, true> : moments_wc_kernel<9, false>; break;
-      case 11: kern = ex ? moments_wc_kernel<11, true> : moments_wc_kernel<11, false>; break;
-      default: kern = ex ? moments_wc_kernel<0, true> : moments_wc_kernel<0, false>; break;
-    }
-    rc = persistent_grid(kern, smem, s.t.total, &grid, kMomBlock);
-    if (rc) return rc;
-    kern<<<grid, kMomBlock, smem, st>>>(s.t, s.d_obsf, part, nmom, sec_smem, reinterpret_cast<int*>(s.d_scratch));
-  }
-#else
-  {
-    const size_t tr_bytes = (size_t)(kBlock / 32) * kTrRows * kTrStride * sizeof(float2);
-    const size_t smem = image + row_scratch_m_bytes(s.M) + (((size_t)moment_slots(s.M) * 4 + 15) & ~(size_t)15) +
-                        (((size_t)moment_slots(s.M) * 8 + 15) & ~(size_t)15) +
-                        (sec_smem ? mom_sec_bytes(s.t) : 0) + tr_bytes +
-                        (size_t)(kBlock / 32) * ((moment_values(s.M) + 31) & ~31) * sizeof(float2);
-    auto kern = ex ? moments_df_kernel<true> : moments_df_kernel<false>;
-    rc = persistent_grid(kern, smem, s.t.total, &grid);
-    if (rc) return rc;
-    kern<<<grid, kBlock, smem, st>>>(s.t, s.d_obsf, part, nmom, sec_smem, reinterpret_cast<int*>(s.d_scratch));
-  }
-#endif
-  QB_CUDA(cudaGetLastError());
-  double* fin = final_area(s);
-  reduce_partials_kernel<<<(nmom + 127) / 128, 128, 0, st>>>(part, grid, nmom, fin);
-  QB_CUDA(cudaGetLastError());
-  QB_CUDA(cudaMemcpyAsync(out_host, fin, sizeof(double) * nmom, cudaMemcpyDeviceToHost, st));
-  // <H> = <psi|H psi>: the double-float stage kernel in its reduction-only mode
-  DfArgs a{};
-  a.vin = s.d_obsf;
-  a.diag = s.d_diag;
-  a.scale[0] = make_float2(1.0f, 0.0f);
-  a.row0 = 0;
-  a.row1 = s.t.total;
-  a.status = reinterpret_cast<int*>(s.d_scratch);
-  a.partial = dot_area(s);
-  int g2 = 0;
-  rc = stage_launch(s.t, a, 4, 1, s.t.is_complex != 0, st, &g2, true);
-  if (rc) return rc;
-  double* hfin = dot_final(s);
-  reduce_partials_kernel<<<1, 32, 0, st>>>(a.partial, g2, s.M + 1, hfin);
-  QB_CUDA(cudaGetLastError());
-  double h2[1];
-  QB_CUDA(cudaMemcpyAsync(h2, hfin, sizeof(double), cudaMemcpyDeviceToHost, st));
-  QB_CUDA(cudaStreamSynchronize(st));
-  out_host[2] = h2[0];
-  return check_status(s, st);
-}
-
-
-
 // ----------------------------------------------- allocation-free observables
 //
 // qb_observables_noalloc serves callers that must not allocate device memory
@@ -1625,14 +1018,17 @@ static int noalloc_scratch(double** out) {
   return QB_OK;
 }
 
+// <psi|H psi> partials of at most `grid` CTAs (the size the fixed array was carved
+// for); *launched receives the CTA count, the number of partials to reduce
 template <bool CPLX>
-static int noalloc_dot(const Space& s, const StageArgs& a, int grid, cudaStream_t st) {
+static int noalloc_dot(const Space& s, const StageArgs& a, int grid, cudaStream_t st, int* launched) {
   const size_t smem = row_smem(s.t);
   auto k = hpsi_kernel<MODE_DOT, 1, CPLX>;
   int g0 = 0;
   int rc = persistent_grid(k, smem, s.t.total, &g0);
   if (rc) return rc;
-  k<<<std::min(grid, g0), kBlock, smem, st>>>(s.t, a);
+  *launched = std::min(grid, g0);
+  k<<<*launched, kBlock, smem, st>>>(s.t, a);
   QB_CUDA(cudaGetLastError());
   return QB_OK;
 }
@@ -1682,9 +1078,10 @@ extern "C" int qb_observables_noalloc(qb_space* space, const void* d_psi, qb_obs
   a.scale[0] = 1.0;
   a.status = status;
   a.partial = dpart;
-  rc = sp->t.is_complex ? noalloc_dot<true>(*sp, a, grid, st) : noalloc_dot<false>(*sp, a, grid, st);
+  int gdot = 0;
+  rc = sp->t.is_complex ? noalloc_dot<true>(*sp, a, grid, st, &gdot) : noalloc_dot<false>(*sp, a, grid, st, &gdot);
   if (rc) return rc;
-  reduce_partials_kernel<<<1, 32, 0, st>>>(dpart, grid, 2, dfin);
+  reduce_partials_kernel<<<1, 32, 0, st>>>(dpart, gdot, 2, dfin);
   QB_CUDA(cudaGetLastError());
   std::vector<double> raw(nmom, 0.0);
   double h2[2];

@@ -1,0 +1,580 @@
+// Observables of Sec. II C-E on the GPU: the raw moments norm, <N>, <H>, <a_i>,
+// <a_i^dag a_j>, <a_i a_j> of one state, with FP64 reductions.
+//
+// One call runs three kernels over every ket n of the space (amplitude psi_n):
+//  1. obs_prep_kernel: the weighted double-float copy f = psi / w of the state (the
+//     basis of the RK4 stages, w(n) = sqrt(N! / prod n_m!) 2^-e_N) and, in FP64, the
+//     moments that need no other ket: |psi|^2, N |psi|^2 and n_i |psi|^2.
+//  2. moments_w_kernel: every moment that moves the ket, conj(psi_t) c psi_n with
+//     t = O n for O = a_i, a_i^dag a_j (i < j; the rest by Hermiticity) and a_i a_j
+//     (i <= j), gathered from f.  In the weighted basis
+//        conj(psi_t) c psi_n = conj(f_t) (psi_n w_n) k 2^(e_N - e_N') / sqrt(N! / N'!)
+//     with N' the particle number of t and k a small integer: n_i (a_i), n_j
+//     (a_i^dag a_j), n_i n_j or n_i (n_i - 1) (a_i a_j): the square roots of the
+//     ladder operators cancel against the ratio of ket weights.
+//  3. the double-float stage kernel in its <x|H|x> mode on f, each row's
+//     Re(conj(f_n) (W^-1 H W f)_n) multiplied by w_n^2 in FP64.
+// Every sum over kets is FP64: per-thread FP64 accumulators in kernels 1 and 3; in
+// kernel 2 the double-float products of one 32-ket tile are summed in double-float
+// and the tile sum is added to the lane's FP64 accumulator.  CTA rows and the sum
+// over CTAs are FP64 in a fixed order (deterministic).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+
+#include "qb_device.cuh"
+#include "qb_internal.h"
+#include "qb_stage.cuh"
+
+namespace qb {
+
+constexpr int kObsBlock = 256;  // threads per CTA of the first pass
+constexpr int kMwWarps = 8;     // warps per CTA of the moments kernel
+constexpr int kMwBlock = 32 * kMwWarps;
+constexpr int kMwSplMax = 3;    // moment entries per lane and pass (<= 96 per pass)
+
+// sums partial[0..n)[0..width) over the first index in a fixed order
+__global__ void reduce_rows_kernel(const double* partial, int n, int width, double* out) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < width; c += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += partial[(size_t)k * width + c];
+    out[c] = s;
+  }
+}
+
+// FP64 sum over the CTA in a fixed order: lanes by shuffles, then warps in turn;
+// `red` holds one value per warp.  The result is valid in thread 0.
+__device__ __forceinline__ double cta_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();  // red may still be read by the previous call
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  return s;
+}
+
+// Pass 1: f = df(psi / w) and the FP64 sums of |psi|^2, N |psi|^2, n_i |psi|^2;
+// partial[block][nprep(M)].
+template <int MT>
+__global__ void __launch_bounds__(kObsBlock) obs_prep_kernel(const Tables t, const double2* psi, float4* f,
+                                                             double* partial) {
+  __shared__ double red[kObsBlock / 32];
+  const int M = (MT > 0) ? MT : t.M;
+  constexpr int kMB = (MT > 0) ? MT : kMaxM;
+  const int ob = t.occ_bits;
+  double nrm = 0.0, nN = 0.0, ni[kMB];
+#pragma unroll
+  for (int m = 0; m < kMB; ++m) ni[m] = 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < t.total; g += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t word = __ldg(t.occ + g);
+    const double2 x = psi[g];
+    const double wi = ket_weight_word<MT>(t, word).y;
+    f[g] = df_pack(df_of(x.x * wi), df_of(x.y * wi));
+    const double p2 = x.x * x.x + x.y * x.y;
+    int N = 0;
+#pragma unroll
+    for (int m = 0; m < kMB; ++m)
+      if (m < M) {
+        const int nm = occ_of(word, m, ob);
+        N += nm;
+        ni[m] += p2 * (double)nm;
+      }
+    nrm += p2;
+    nN += p2 * (double)N;
+  }
+  const int w = nprep(M);
+  double s = cta_sum(nrm, red);
+  if (threadIdx.x == 0) partial[(size_t)blockIdx.x * w] = s;
+  s = cta_sum(nN, red);
+  if (threadIdx.x == 0) partial[(size_t)blockIdx.x * w + 1] = s;
+#pragma unroll
+  for (int m = 0; m < kMB; ++m)
+    if (m < M) {
+      s = cta_sum(ni[m], red);
+      if (threadIdx.x == 0) partial[(size_t)blockIdx.x * w + 2 + m] = s;
+    }
+}
+
+// ---------------------------------------------------------------- moment entries
+//
+// Entry s of the moments kernel: [0, M) a_i; then a_i^dag a_j for i < j (the ket
+// loses one particle in j and gains one in i); then a_i a_j for i <= j.  The target
+// ket changes mode e0 by dn0 and mode e1 by dn1; k = n_e0 (times n_e1 + c1 when the
+// entry has a second factor); the class picks the scale of the target's particle
+// number: 0 same N, 1 N - 1, 2 N - 2.
+enum { kEntA = 0, kEntAdA = 1, kEntAA = 2 };
+
+__host__ __device__ inline int mw_entries(int M) { return M + M * (M - 1) / 2 + M * (M + 1) / 2; }
+
+struct MwEntry {
+  int kind, i, j;         // the operator: a_i, a_i^dag a_j or a_i a_j
+  int e0, dn0, e1, dn1;   // occupation changes of the target
+  int has2, c1, cls;      // k = n_e0 (n_e1 + c1 if has2); class of the scale
+};
+
+__host__ __device__ inline MwEntry mw_entry(int s, int M) {
+  MwEntry e{};
+  if (s < M) {
+    e.kind = kEntA;
+    e.i = e.j = s;
+    e.e0 = e.e1 = s;
+    e.dn0 = -1;
+    e.cls = 1;
+    return e;
+  }
+  s -= M;
+  int i = 0;
+  if (s < M * (M - 1) / 2) {
+    while (s >= M - 1 - i) {
+      s -= M - 1 - i;
+      ++i;
+    }
+    e.kind = kEntAdA;
+    e.i = i;
+    e.j = i + 1 + s;
+    e.e0 = e.j;  // annihilate j
+    e.dn0 = -1;
+    e.e1 = e.i;  // create i
+    e.dn1 = 1;
+    e.cls = 0;
+    return e;
+  }
+  s -= M * (M - 1) / 2;
+  while (s >= M - i) {
+    s -= M - i;
+    ++i;
+  }
+  e.kind = kEntAA;
+  e.i = i;
+  e.j = i + s;
+  e.cls = 2;
+  e.has2 = 1;
+  e.e0 = e.i;
+  if (e.i == e.j) {  // n_i (n_i - 1)
+    e.dn0 = -2;
+    e.e1 = e.i;
+    e.c1 = -1;
+  } else {  // n_i n_j
+    e.dn0 = -1;
+    e.e1 = e.j;
+    e.dn1 = -1;
+  }
+  return e;
+}
+
+// shared memory of moments_w_kernel after the staged ranking table (all 16-byte
+// multiples): entry headers [np] int4, shifts [M-1][np] int32, class scales
+// [3][nmax+1] float2, the CTA's FP64 moment row [nmom]
+__host__ __device__ inline size_t mw_smem_after(int M, int np, int nmax, int nmom) {
+  return (size_t)np * 16 + ((((size_t)(M > 1 ? M - 1 : 1) * np * 4) + 15) & ~(size_t)15) +
+         ((3 * (size_t)(nmax + 1) * 8 + 15) & ~(size_t)15) + (((size_t)nmom * 8 + 15) & ~(size_t)15);
+}
+
+constexpr size_t kMwSecSmemMax = 16384;  // sector tables larger than this stay in global memory
+
+static size_t mw_sec_bytes(const Tables& t) {
+  return ((sizeof(int64_t) * (size_t)(t.n_sectors + 1) + 15) & ~(size_t)15) +
+         ((sizeof(int32_t) * (size_t)(t.nmax + 1) * t.Q + 15) & ~(size_t)15);
+}
+
+__device__ __forceinline__ int find_sector_in(const int64_t* off, int n, int64_t g) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= g)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// x mod Q for x in (-2Q, 3Q), by conditional adds
+__device__ __forceinline__ int mod_small(int x, int Q) {
+  if (x < 0) x += Q;
+  if (x < 0) x += Q;
+  if (x >= Q) x -= Q;
+  if (x >= Q) x -= Q;
+  return x;
+}
+
+// Pass 2: the moments that move the ket, entries [e_begin, e_begin + nent) of this
+// pass (nent <= 32 kMwSpl).  The lanes of a warp take the entries (kMwSpl per lane); the
+// tile are visited in turn, each one's data broadcast from the lane that loaded it:
+// x = psi_n w_n (double-float), (N, K), the packed occupations and the suffix-state
+// indices of the ranking table.  A target's rank is D - 1 - sum_{m=1}^{M-1}
+// E[idx_m + shift_m], the shift of the suffix index at mode m depending only on the
+// entry (tabulated per entry and mode).  partial[block][nmom] (FP64).
+template <int MT, bool EXACT, int kMwSpl>
+__global__ void __launch_bounds__(kMwBlock) moments_w_kernel(const Tables t, const double2* psi, const float4* f,
+                                                              double* partial, int nmom, int e_begin, int nent,
+                                                              int sec_smem, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int kMB = (MT > 0) ? MT : kMaxM;
+  const int from = EXACT ? t.o_sqrt : t.o_E;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int M = (MT > 0) ? MT : t.M, Q = t.Q, twoQ = 2 * Q, V = t.nmax + 1;
+  const int np = (nent + 31) & ~31;
+  unsigned char* cur = smem_raw + ((t.blob_bytes - from + 15) & ~15);
+  int4* hdr = reinterpret_cast<int4*>(cur);  // e0 | e1 << 8 | has2 << 16 | cls << 24, c1, dN, dK mod Q
+  cur += (size_t)np * 16;
+  int32_t* shf = reinterpret_cast<int32_t*>(cur);  // [M-1][np]
+  cur += (((size_t)(M > 1 ? M - 1 : 1) * np * 4) + 15) & ~(size_t)15;
+  float2* scl = reinterpret_cast<float2*>(cur);  // [3][V] double-float scale of each class at particle number N
+  cur += (3 * (size_t)V * 8 + 15) & ~(size_t)15;
+  double* row = reinterpret_cast<double*>(cur);  // [nmom]
+  cur += ((size_t)nmom * 8 + 15) & ~(size_t)15;
+  for (int s = tid; s < np; s += kMwBlock) {
+    int4 h = make_int4(0, 0, 0, 0);
+    int sh[kMaxM];
+    for (int m = 0; m < kMaxM; ++m) sh[m] = 0;
+    if (s < nent) {
+      const MwEntry e = mw_entry(e_begin + s, M);
+      const int f1 = (e.dn1 == 0) ? e.e0 : e.e1;  // a zero second change acts on e0
+      const int hi = max(e.e0, f1), lo = min(e.e0, f1);
+      const int dh = (hi == e.e0) ? e.dn0 : e.dn1;
+      const int shh = dh * twoQ + mod_small(dh * hi, Q);
+      const int dc = e.dn0 + e.dn1, dk = mod_small(e.dn0 * e.e0 + e.dn1 * f1, Q);
+      for (int m = 1; m < M; ++m) sh[m] = m > hi ? 0 : (m > lo ? shh : dc * twoQ + dk);
+      h = make_int4(e.e0 | (e.e1 << 8) | (e.has2 << 16) | (e.cls << 24), e.c1, dc, dk);
+    }
+    hdr[s] = h;
+    for (int m = 1; m < M; ++m) shf[(m - 1) * np + s] = sh[m];
+  }
+  // class scales: 1, 2^(e_N - e_{N-1}) / sqrt(N), 2^(e_N - e_{N-2}) / sqrt(N (N - 1))
+  for (int k = tid; k < 3 * V; k += kMwBlock) {
+    const int c = k / V, N = k % V;
+    double v = 1.0;
+    if (c == 1) v = (N >= 1) ? __ldg(t.wscale + N).y * __ldg(t.wscale + N - 1).x / sqrt((double)N) : 0.0;
+    if (c == 2) v = (N >= 2) ? __ldg(t.wscale + N).y * __ldg(t.wscale + N - 2).x / sqrt((double)N * (N - 1)) : 0.0;
+    const dfl d = df_of(v);
+    scl[k] = make_float2(d.h, d.l);
+  }
+  const int64_t* soff = t.sec_off;
+  const int32_t* sof = t.sec_of;
+  if (sec_smem) {
+    int64_t* o = reinterpret_cast<int64_t*>(cur);
+    for (int k = tid; k <= t.n_sectors; k += kMwBlock) o[k] = __ldg(t.sec_off + k);
+    cur += (sizeof(int64_t) * (size_t)(t.n_sectors + 1) + 15) & ~(size_t)15;
+    int32_t* q = reinterpret_cast<int32_t*>(cur);
+    for (int k = tid; k < (t.nmax + 1) * Q; k += kMwBlock) q[k] = __ldg(t.sec_of + k);
+    soff = o;
+    sof = q;
+  }
+  for (int k = tid; k < nmom; k += kMwBlock) row[k] = 0.0;
+  load_blob_from(t, smem_raw, from);  // ends with a CTA barrier
+  const int32_t* E = EXACT ? reinterpret_cast<const int32_t*>(t.blob + t.o_E)
+                           : reinterpret_cast<const int32_t*>(smem_raw + (t.o_E - from));
+  const int ob = t.occ_bits;
+  const int64_t total = t.total;
+  const int64_t ntiles = (total + 31) / 32;
+
+  // this lane's entries: header, and the target sector for the current (N, K)
+  int4 eh[kMwSpl];
+#pragma unroll
+  for (int r = 0; r < kMwSpl; ++r) {
+    const int s = r * 32 + lane;
+    eh[r] = (s < nent) ? hdr[s] : make_int4(-1, 0, 0, 0);
+  }
+  int cur_nk = -1;
+  int64_t toff[kMwSpl];
+  int tD[kMwSpl];
+  dfl csc[kMwSpl];  // class scale at the current N
+  double acc_r[kMwSpl], acc_i[kMwSpl];
+#pragma unroll
+  for (int r = 0; r < kMwSpl; ++r) {
+    toff[r] = 0;
+    tD[r] = -1;
+    csc[r] = dfl{0.f, 0.f};
+    acc_r[r] = acc_i[r] = 0.0;
+  }
+
+  for (int64_t tile = (int64_t)blockIdx.x * kMwWarps + warp; tile < ntiles; tile += (int64_t)gridDim.x * kMwWarps) {
+    // this lane's ket: x = psi w (double-float), packed occupations, (N, K), suffix indices
+    const int64_t g = tile * 32 + lane;
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint64_t word = 0;
+    int nk = 0;
+    int idx[kMB];
+#pragma unroll
+    for (int m = 0; m < kMB; ++m) idx[m] = 0;
+    if (g < total) {
+      const int sid = find_sector_in(soff, t.n_sectors, g);
+      nk = __ldg(t.sec_N + sid) | (__ldg(t.sec_K + sid) << 16);
+      word = __ldg(t.occ + g);
+      const double2 p = psi[g];
+      const double w = ket_weight_word<MT>(t, word).x;
+      x = df_pack(df_of(p.x * w), df_of(p.y * w));
+      int srem = 0, skr = 0;
+#pragma unroll
+      for (int m = kMB - 1; m >= 1; --m) {
+        if (m < M) {
+          const int nm = occ_of(word, m, ob);
+          srem += nm;
+          skr += m * nm;
+          while (skr >= Q) skr -= Q;
+          idx[m] = (m * t.rem_w + srem + 2) * twoQ + skr;
+        }
+      }
+    }
+    // products of this tile, double-float, (re, im) packed
+    dfc tp[kMwSpl];
+#pragma unroll
+    for (int r = 0; r < kMwSpl; ++r) tp[r] = dfc{0ull, 0ull};
+    const int nt = (int)min((int64_t)32, total - tile * 32);
+    for (int j = 0; j < nt; ++j) {
+      const float xrh = __shfl_sync(~0u, x.x, j), xih = __shfl_sync(~0u, x.y, j);
+      const float xrl = __shfl_sync(~0u, x.z, j), xil = __shfl_sync(~0u, x.w, j);
+      const uint64_t wj = ((uint64_t)__shfl_sync(~0u, (uint32_t)(word >> 32), j) << 32) |
+                          (uint64_t)__shfl_sync(~0u, (uint32_t)word, j);
+      const int nkj = __shfl_sync(~0u, nk, j);
+      int id[kMB];
+#pragma unroll
+      for (int m = 1; m < kMB; ++m)
+        if (m < M) id[m] = __shfl_sync(~0u, idx[m], j);
+      if (nkj != cur_nk) {  // warp-uniform: a new (N, K) sector
+        cur_nk = nkj;
+        const int N = nkj & 0xffff, K = nkj >> 16;
+#pragma unroll
+        for (int r = 0; r < kMwSpl; ++r) {
+          tD[r] = -1;
+          if (eh[r].x < 0) continue;
+          const int Nt = N + eh[r].z;
+          if (Nt < 0) continue;
+          int Kt = K + eh[r].w;
+          if (Kt >= Q) Kt -= Q;
+          const int sid = sof[Nt * Q + Kt];
+          if (sid < 0) continue;  // the target sector is not part of the space
+          toff[r] = soff[sid];
+          tD[r] = (int)(soff[sid + 1] - toff[r]);
+          const float2 c = scl[((eh[r].x >> 24) & 3) * V + N];
+          csc[r] = dfl{c.x, c.y};
+        }
+      }
+      // x (own ket) as packed pairs: X_r = (xr, xr), X_i = (xi, xi), and -X_r.h, -X_i.h
+      const f2 XRh = f2_pack(xrh, xrh), XRl = f2_pack(xrl, xrl), XIh = f2_pack(xih, xih), XIl = f2_pack(xil, xil);
+      const f2 nXRh = f2_pack(-xrh, -xrh), nXIh = f2_pack(-xih, -xih);
+#pragma unroll
+      for (int r = 0; r < kMwSpl; ++r) {
+        if (tD[r] < 0) continue;
+        const int hx = eh[r].x;
+        int k = occ_of(wj, hx & 0xff, ob);
+        if (hx & 0x10000) k *= occ_of(wj, (hx >> 8) & 0xff, ob) + eh[r].y;
+        if (k <= 0) continue;  // the operator annihilates this ket
+        const int s = r * 32 + lane;
+        int esum = 0;
+#pragma unroll
+        for (int m = 1; m < kMB; ++m)
+          if (m < M) esum += E[id[m] + shf[(m - 1) * np + s]];
+        const int rk = tD[r] - 1 - esum;
+        if ((unsigned)rk >= (unsigned)tD[r]) {
+          atomicOr(status, 1);
+          continue;
+        }
+        const float4 y = __ldg(f + toff[r] + rk);
+        // conj(y) x = x_r (y_r, -y_i) + x_i (y_i, y_r), lane 0 the real part
+        const f2 one_m = f2_pack(1.f, -1.f);
+        const f2 Ph = f2_mul(f2_pack(y.x, y.y), one_m), Pl = f2_mul(f2_pack(y.z, y.w), one_m);
+        const f2 Sh = f2_pack(y.y, y.x), Sl = f2_pack(y.w, y.z);
+        // exact products with their error terms
+        const f2 n1 = f2_mul(nXRh, Ph);
+        f2 e1 = f2_fma(XRh, Ph, n1);
+        e1 = f2_fma(XRh, Pl, e1);
+        e1 = f2_fma(XRl, Ph, e1);
+        const f2 n2 = f2_mul(nXIh, Sh);
+        f2 e2 = f2_fma(XIh, Sh, n2);
+        e2 = f2_fma(XIh, Sl, e2);
+        e2 = f2_fma(XIl, Sh, e2);
+        // the negated sum -(p1 + p2) = n1 + n2 by TwoSum, ns + nsl with the error terms
+        const f2 ns = f2_add(n1, n2);
+        const f2 bb = f2_sub(ns, n1);
+        const f2 nerr = f2_add(f2_sub(n1, f2_sub(ns, bb)), f2_sub(n2, bb));
+        const f2 nsl = f2_sub(f2_sub(nerr, e1), e2);
+        // times the coefficient c = k * scale: acc += (-c)(ns + nsl) = c conj(y) x
+        const dfl c = df_mul_f(csc[r], (float)k);
+        const f2 Ch = f2_pack(c.h, c.h), nCh = f2_pack(-c.h, -c.h), nCl = f2_pack(-c.l, -c.l);
+        dfc_fma(tp[r], nCh, Ch, nCl, ns, nsl);
+      }
+    }
+    // the tile's sums into the lane's FP64 accumulators
+#pragma unroll
+    for (int r = 0; r < kMwSpl; ++r) {
+      float hr, hi2, lr, li;
+      f2_unpack(tp[r].h, hr, hi2);
+      f2_unpack(tp[r].l, lr, li);
+      acc_r[r] += (double)hr + (double)lr;
+      acc_i[r] += (double)hi2 + (double)li;
+    }
+  }
+  // the lanes' sums into the CTA's FP64 row, one warp at a time (a fixed order); the
+  // entries of a warp land on distinct moments
+  const int oA = 4, oM = 4 + 2 * M, oAA = 4 + 2 * M + 2 * M * M;
+  for (int w = 0; w < kMwWarps; ++w) {
+    if (warp == w) {
+#pragma unroll
+      for (int r = 0; r < kMwSpl; ++r) {
+        const int s = r * 32 + lane;
+        if (s < nent) {
+          const MwEntry e = mw_entry(e_begin + s, M);
+          if (e.kind == kEntA) {
+            row[oA + 2 * e.i] += acc_r[r];
+            row[oA + 2 * e.i + 1] += acc_i[r];
+          } else if (e.kind == kEntAdA) {  // <a_j^dag a_i> = conj <a_i^dag a_j>
+            row[oM + 2 * (e.i * M + e.j)] += acc_r[r];
+            row[oM + 2 * (e.i * M + e.j) + 1] += acc_i[r];
+            row[oM + 2 * (e.j * M + e.i)] += acc_r[r];
+            row[oM + 2 * (e.j * M + e.i) + 1] -= acc_i[r];
+          } else {
+            row[oAA + 2 * (e.i * M + e.j)] += acc_r[r];
+            row[oAA + 2 * (e.i * M + e.j) + 1] += acc_i[r];
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int k = tid; k < nmom; k += kMwBlock) partial[(size_t)blockIdx.x * nmom + k] = row[k];
+}
+
+// ------------------------------------------------------------------ host side
+
+template <int MT>
+static int launch_prep(const Space& s, const double2* psi, float4* f, double* part, int* grid_out, cudaStream_t st) {
+  auto k = obs_prep_kernel<MT>;
+  int grid = 0;
+  int rc = persistent_grid(k, 0, s.t.total, &grid, kObsBlock);
+  if (rc) return rc;
+  grid = (int)std::min<int64_t>(grid, max_grid_of(s));
+  k<<<grid, kObsBlock, 0, st>>>(s.t, psi, f, part);
+  QB_CUDA(cudaGetLastError());
+  *grid_out = grid;
+  return QB_OK;
+}
+
+template <int MT, bool EXACT, int SPL>
+static int launch_mw(const Space& s, const double2* psi, const float4* f, double* part, int nmom, int e_begin,
+                     int nent, int* grid_out, cudaStream_t st) {
+  const Tables& t = s.t;
+  const int from = EXACT ? t.o_sqrt : t.o_E;
+  const int np = (nent + 31) & ~31;
+  const int sec_smem = mw_sec_bytes(t) <= kMwSecSmemMax ? 1 : 0;
+  const size_t smem = ((size_t)(t.blob_bytes - from + 15) & ~(size_t)15) + mw_smem_after(t.M, np, t.nmax, nmom) +
+                      (sec_smem ? mw_sec_bytes(t) : 0);
+  auto k = moments_w_kernel<MT, EXACT, SPL>;
+  int grid = 0;
+  int rc = persistent_grid(k, smem, (t.total + 31) / 32 * kMwBlock / kMwWarps, &grid, kMwBlock);
+  if (rc) return rc;
+  grid = (int)std::min<int64_t>(grid, max_grid_of(s));
+  k<<<grid, kMwBlock, smem, st>>>(t, psi, f, part, nmom, e_begin, nent, sec_smem, reinterpret_cast<int*>(s.d_scratch));
+  QB_CUDA(cudaGetLastError());
+  *grid_out = grid;
+  return QB_OK;
+}
+
+// entries per lane a pass of at most 32 kMwSplMax entries needs, for the mode counts
+// with a specialised kernel (M = 5: 30 entries; 7: 56; 9: 90; 11: 132 in passes of
+// 96 and 36); the generic kernel takes any
+template <int MT, int SPL>
+constexpr bool mw_needed() {
+  return MT == 0 || (MT == 5 && SPL == 1) || (MT == 7 && SPL == 2) || (MT == 9 && SPL == 3) ||
+         (MT == 11 && (SPL == 3 || SPL == 2));
+}
+
+template <int MT, bool EXACT>
+static int launch_mw_m(const Space& s, const double2* psi, const float4* f, double* part, int nmom, int e_begin,
+                       int nent, int* grid, cudaStream_t st) {
+  const int spl = (nent + 31) / 32;
+  if constexpr (mw_needed<MT, 1>())
+    if (spl == 1) return launch_mw<MT, EXACT, 1>(s, psi, f, part, nmom, e_begin, nent, grid, st);
+  if constexpr (mw_needed<MT, 2>())
+    if (spl == 2) return launch_mw<MT, EXACT, 2>(s, psi, f, part, nmom, e_begin, nent, grid, st);
+  if constexpr (mw_needed<MT, 3>())
+    if (spl == 3) return launch_mw<MT, EXACT, 3>(s, psi, f, part, nmom, e_begin, nent, grid, st);
+  return fail(QB_EINTERNAL, "moments pass without a compiled kernel");
+}
+
+template <bool EXACT>
+static int launch_mw_e(const Space& s, const double2* psi, const float4* f, double* part, int nmom, int e_begin,
+                       int nent, int* grid, cudaStream_t st) {
+  switch (s.M) {
+    case 5: return launch_mw_m<5, EXACT>(s, psi, f, part, nmom, e_begin, nent, grid, st);
+    case 7: return launch_mw_m<7, EXACT>(s, psi, f, part, nmom, e_begin, nent, grid, st);
+    case 9: return launch_mw_m<9, EXACT>(s, psi, f, part, nmom, e_begin, nent, grid, st);
+    case 11: return launch_mw_m<11, EXACT>(s, psi, f, part, nmom, e_begin, nent, grid, st);
+    default: return launch_mw_m<0, EXACT>(s, psi, f, part, nmom, e_begin, nent, grid, st);
+  }
+}
+
+int launch_moments(Space& s, const void* d_psi, double* out_host, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const int M = s.M, nmom = nmoments(M), npr = nprep(M);
+  const double2* psi = (const double2*)d_psi;
+  float4* f = s.d_obsf;
+  // pass 1: weighted copy, norm, <N>, <n_i>
+  int gp = 0;
+  int rc;
+  switch (M) {
+    case 5: rc = launch_prep<5>(s, psi, f, prep_area(s), &gp, st); break;
+    case 7: rc = launch_prep<7>(s, psi, f, prep_area(s), &gp, st); break;
+    case 9: rc = launch_prep<9>(s, psi, f, prep_area(s), &gp, st); break;
+    case 11: rc = launch_prep<11>(s, psi, f, prep_area(s), &gp, st); break;
+    default: rc = launch_prep<0>(s, psi, f, prep_area(s), &gp, st); break;
+  }
+  if (rc) return rc;
+  reduce_rows_kernel<<<1, 32, 0, st>>>(prep_area(s), gp, npr, prep_final(s));
+  QB_CUDA(cudaGetLastError());
+  // pass 2: the moments that move the ket, in passes of at most 32 kMwSplMax entries;
+  // each pass's partial rows are summed into its own copy of the moment row
+  const int nent = mw_entries(M), per = 32 * kMwSplMax;
+  const int npass = (nent + per - 1) / per;
+  std::vector<double> mom((size_t)nmom, 0.0), fin((size_t)nmom);
+  for (int p = 0; p < npass; ++p) {
+    const int e0 = p * per, ne = std::min(per, nent - e0);
+    int gm = 0;
+    rc = s.t.exact ? launch_mw_e<true>(s, psi, f, partial_area(s), nmom, e0, ne, &gm, st)
+                   : launch_mw_e<false>(s, psi, f, partial_area(s), nmom, e0, ne, &gm, st);
+    if (rc) return rc;
+    reduce_rows_kernel<<<(nmom + 127) / 128, 128, 0, st>>>(partial_area(s), gm, nmom, final_area(s));
+    QB_CUDA(cudaGetLastError());
+    QB_CUDA(cudaMemcpyAsync(fin.data(), final_area(s), sizeof(double) * nmom, cudaMemcpyDeviceToHost, st));
+    QB_CUDA(cudaStreamSynchronize(st));
+    for (int k = 0; k < nmom; ++k) mom[k] += fin[k];
+  }
+  // pass 3: <psi|H|psi> from the weighted copy, w^2 applied per row in FP64
+  DfArgs a{};
+  a.vin = f;
+  a.diag = s.d_diag;
+  a.scale[0] = make_float2(1.0f, 0.0f);
+  a.row0 = 0;
+  a.row1 = s.t.total;
+  a.status = reinterpret_cast<int*>(s.d_scratch);
+  a.partial = dot_area(s);
+  int g2 = 0;
+  rc = stage_launch(s.t, a, 4, 1, s.t.is_complex != 0, st, &g2, false, 0);
+  if (rc) return rc;
+  reduce_rows_kernel<<<1, 32, 0, st>>>(a.partial, g2, 1, dot_final(s));
+  QB_CUDA(cudaGetLastError());
+  std::vector<double> pre((size_t)npr);
+  double h = 0.0;
+  QB_CUDA(cudaMemcpyAsync(pre.data(), prep_final(s), sizeof(double) * npr, cudaMemcpyDeviceToHost, st));
+  QB_CUDA(cudaMemcpyAsync(&h, dot_final(s), sizeof(double), cudaMemcpyDeviceToHost, st));
+  QB_CUDA(cudaStreamSynchronize(st));
+  for (int k = 0; k < nmom; ++k) out_host[k] = mom[k];
+  out_host[0] = pre[0];
+  out_host[1] = pre[1];
+  out_host[2] = h;
+  out_host[3] = 0.0;
+  const int oM = 4 + 2 * M;
+  for (int i = 0; i < M; ++i) {
+    out_host[oM + 2 * (i * M + i)] = pre[2 + i];
+    out_host[oM + 2 * (i * M + i) + 1] = 0.0;
+  }
+  return check_status(s, st);
+}
+
+}  // namespace qb

@@ -1,70 +1,89 @@
 // The hot kernel: one Horner RK4 stage of every sector (and every member of a
 // batched coupling sweep) in one launch, with the matrix-free sector H psi in
-// double-float arithmetic.
+// double-float arithmetic, in the weighted basis f = psi / w(n).
 //
-//   stage d (d = 4, 3, 2):  out = psi + (-i dt/d) H v     (double-float out)
-//   stage 1:                psi = psi + (-i dt) H v       (FP64 psi, plus its
-//                                                          double-float copy)
+//   stage d (d = 4, 3, 2):  out = f + (-i dt/d) W^-1 H W v    (double-float out)
+//   stage 1:                psi = psi + (-i dt) H v, f = psi / w
+//                                                     (FP64 psi, plus its weighted copy)
 //
-// H is Eq. (Ham) restricted to sectors of fixed N and momentum mod M
-// (Sec. III B).  Per row (ket n) the off-diagonal terms are the disjoint pairs
-// {r, s} -> {p, q} with p + q = r + s (mod M): coefficient
-// G_{pq,rs} sqrt(n_r (n_s - [r=s])) sqrt((n_p + 1)(n_q + 1 + [p=q])), G the
-// multiplicity-summed symmetrised coupling; the diagonal is precomputed per ket.
+// H is Eq. (Ham) restricted to sectors of fixed N and momentum mod M (Sec. III B).
+// Per row (ket n) the off-diagonal terms are the disjoint pairs {r, s} -> {p, q}
+// with p + q = r + s (mod M); in the weighted basis, w(n) = sqrt(N! / prod n_m!) up
+// to a power of two per N, the element of target n' = n - e_r - e_s + e_p + e_q is
+// G_{pq,rs} n_r (n_s - [r = s]): the ratio w(n') / w(n) cancels the creation
+// square roots and squares the annihilation ones.  G is the multiplicity-summed
+// symmetrised coupling; the diagonal is precomputed per ket.
 //
-// Work layout: every warp owns tiles of kWarpRows consecutive kets and runs
-// without CTA-wide barriers.  Phase 1 unranks the tile (kWarpRows/32 kets per
-// lane) into occupations and suffix-state indices; phase 2 counting-sorts the
-// tile by the number of annihilation pairs acting on each ket; phase 3 runs the
-// terms in rounds, the 32 lanes of a round taking 32 kets of nearly equal work.
-// For odd M every annihilation pair has exactly (M-1)/2 creation partners; the
-// specialised kernels unroll them so that their ranks and gathers overlap.
+// Work layout: every warp owns tiles of kRows consecutive kets and runs without
+// CTA-wide barriers.  Phase 1 unpacks the tile's occupations (kRows/32 kets per
+// lane) and their suffix-state indices; phase 2 counting-sorts the tile by the
+// number of annihilation pairs acting on each ket; phase 3 runs the terms in
+// rounds, the 32 lanes of a round taking 32 kets of nearly equal work.  For odd M
+// every annihilation pair has exactly (M-1)/2 creation partners; the specialised
+// kernels unroll them so that their ranks and gathers overlap.
+//
+// Ranking (RK): a target's rank is D - 1 - sum_{m=1}^{M-1} E[idx_m + shift_m], the
+// shift of the suffix index at mode m fixed by the term.
+//   RK_PAIR   the ranking table in shared memory spans < 64 KB: the byte offsets of
+//             modes 2k+1 and 2k+2 share one 32-bit word per ket, and one 32-bit add
+//             of the term's packed shifts advances both (the shifts are stored as the
+//             signed value lo + 65536 hi, so the low half's borrow is part of it);
+//   RK_BYTE   larger tables: element indices and one biased shift byte per mode;
+//   RK_EXACT  exact momentum: 16-bit shifts, the ranking table in global memory.
 #pragma once
 #include "qb_device.cuh"
 
-#ifndef QB_CNT_GLOBAL
-#define QB_CNT_GLOBAL 1
-#endif
 #ifndef QB_UNROLL_PARTNERS
 #define QB_UNROLL_PARTNERS 1
-#endif
-#ifndef QB_CONVERGENT_PAIRS
-#define QB_CONVERGENT_PAIRS 1
-#endif
-#ifndef QB_UNRANK_FROM_E
-#define QB_UNRANK_FROM_E 1
-#endif
-// 1: a ket's occupations are unpacked from the packed table Tables::occ (8 B per ket
-// read, coalesced); 0: unranked through the counting table (a data-dependent walk of
-// about N + M steps per ket)
-#ifndef QB_OCC_TABLE
-#define QB_OCC_TABLE 1
 #endif
 
 namespace qb {
 
-// Warps per CTA of the stage kernel.  The CTA's warps share one copy of the
-// ranking table in shared memory, so larger CTAs leave room for more warps per SM.
-#ifndef QB_STAGE_WARPS
-#define QB_STAGE_WARPS 12
-#endif
-// Resident CTAs per SM that the register budget of the single-state stage kernel
-// is planned for: 3 x 384 threads leave 56 registers per thread (36 warps per SM).
-// The bilinear instantiations (more accumulators per lane) of the specialised mode
-// counts are planned for 2 CTAs (80 registers); the batched ones and the generic
-// bilinear ones (16 accumulators) keep the compiler's choice (one CTA).
-#ifndef QB_STAGE_MIN_BLOCKS
-#define QB_STAGE_MIN_BLOCKS 3
-#endif
-constexpr int kStageWarps = QB_STAGE_WARPS;
-constexpr int kStageBlock = 32 * kStageWarps;
-constexpr int kStageMinBlocks = QB_STAGE_MIN_BLOCKS;
+enum { RK_BYTE = 0, RK_PAIR = 1, RK_EXACT = 2 };
 
-// first byte of the table image the stage kernels stage in shared memory
-// (exact momentum: the ranking table too stays in global memory)
-__host__ __device__ inline int kSmemFrom(const Tables& t, bool exact = false) {
-  return exact ? t.o_sqrt : (QB_CNT_GLOBAL ? t.o_E : 0);
+// What a stage launch computes besides (or instead of) its output vector:
+//   KIND_STAGE  the RK4 / adjoint stage alone (modes 0 to 3);
+//   KIND_BIL    with the adjoint's bilinears fused (modes 2, 3);
+//   KIND_DOT    <x|H|x> only (mode 4): Re(conj(psi_n) (H psi)_n) summed in FP64.
+enum { KIND_STAGE = 0, KIND_BIL = 1, KIND_DOT = 2 };
+
+// Tile shapes of the stage kernel: warps per CTA, kets per warp tile and the
+// resident CTAs per SM its register budget is planned for (65,536 registers per SM
+// shared by warps x 32 x CTAs threads).  The CTA's warps share one copy of the
+// ranking table in shared memory.  Shape 0 is the default; the others are
+// compiled for the single-state stage (qb_space_set_tile_shape selects one).
+struct TileShape {
+  int warps, rows, min_blocks;
+};
+constexpr int kTileShapes = 5;
+__host__ __device__ constexpr TileShape tile_shape(int ts) {
+  return ts == 1   ? TileShape{8, 64, 4}
+         : ts == 2 ? TileShape{16, 64, 2}
+         : ts == 3 ? TileShape{12, 128, 3}
+         : ts == 4 ? TileShape{8, 32, 4}
+                   : TileShape{12, 64, 3};
 }
+constexpr int kStageWarps = 12;  // shape 0 (the bilinear and batched instantiations)
+constexpr int kStageBlock = 32 * kStageWarps;
+
+// Shared scratch of the stage kernel, after the table image, per warp (a tile of
+// `rows` kets):
+//   sidx  int32 [M][rows]   suffix-state index of each ket at mode m (RK_PAIR: two
+//                           modes per word, M/2 words)
+//   socc  uint8 [M][rows]   occupations
+//   sD    int32 [rows]      sector dimension of the ket (-1: no ket)
+//   sOff  int64 [rows]      sector offset of the ket
+//   sperm uint8 [rows]      processing order (kets sorted by work, most first)
+//   hist  int32 [2][n_ann+2] counting-sort buckets and cursors
+__host__ __device__ inline size_t df_warp_scratch_bytes(int M, int n_ann, int rows) {
+  size_t b = (size_t)M * rows * 4 + (((size_t)M * rows + 15) & ~(size_t)15);
+  b += (size_t)rows * 4 + (size_t)rows * 8 + rows + 2 * (size_t)(n_ann + 2) * 4;
+  return (b + 15) & ~(size_t)15;
+}
+
+// first byte of the table image the stage kernels stage in shared memory (the fill
+// counts stay in global memory; exact momentum: the ranking table too)
+__host__ __device__ inline int kSmemFrom(const Tables& t, bool exact = false) { return exact ? t.o_sqrt : t.o_E; }
 
 // Gathered stage-vector entry: read-only global load, or a generic load when the
 // vector is a shared-memory copy (LOCAL; the non-coherent global path does not
@@ -75,37 +94,80 @@ __device__ __forceinline__ float4 gather(const float4* p) {
   return __ldg(p);
 }
 
-// E at suffix index id shifted by `shift` entries.  BYTE: id is a byte offset, so a
-// lookup is one shift-add onto it (measured: 6% faster where the ranking table is
-// in global memory, exact momentum; 2% slower from shared memory).
-template <bool BYTE>
-__device__ __forceinline__ int32_t e_at(const int32_t* E, int id, int shift) {
-  if (BYTE) return *reinterpret_cast<const int32_t*>(reinterpret_cast<const char*>(E) + id + (shift << 2));
-  return E[id + shift];
+// The stage kernels' dynamic shared memory: the table image from the ranking table
+// on (non-exact momentum), so a byte offset into the ranking table is one shared
+// load with an immediate base.
+extern __shared__ __align__(16) unsigned char stage_smem_raw[];
+__device__ __forceinline__ int32_t e_byte(uint32_t off) {
+  return *reinterpret_cast<const int32_t*>(stage_smem_raw + off);
 }
 
-// One warp tile: kets [base, min(base + kWarpRows, row1)) of the launch.  With
-// LOCAL the state vectors of DfArgs are the shared-memory copies of one sector
-// starting at ket local_off (gathers and own-row accesses are sector-local);
-// otherwise they are the global vectors.  The per-ket diagonal is always global.
+// sum_{m=1}^{M-1} E[idx_m + shift_m] of combo j for a ket whose suffix indices are
+// id[] (RK_PAIR: packed words; otherwise per mode)
+template <int MT, int RK>
+__device__ __forceinline__ int rank_esum(const Tables& t, const int32_t* E, const unsigned char* dtab, int j,
+                                         const int* id) {
+  const int M = (MT > 0) ? MT : t.M;
+  int esum = 0;
+  if constexpr (RK == RK_PAIR) {
+    const uint4* dw = reinterpret_cast<const uint4*>(dtab) + 2 * (size_t)j;
+    const uint4 d0 = dw[0];
+    uint4 d1 = make_uint4(0u, 0u, 0u, 0u);
+    if (MT == 0 || MT > 9) d1 = dw[1];
+    constexpr int kW = (MT > 0) ? MT / 2 : 8;
+#pragma unroll
+    for (int k = 0; k < kW; ++k) {
+      if (MT == 0 && 2 * k + 1 >= M) break;
+      const uint32_t dk = (k == 0) ? d0.x : (k == 1) ? d0.y : (k == 2) ? d0.z : (k == 3) ? d0.w
+                        : (k == 4) ? d1.x : (k == 5) ? d1.y : (k == 6) ? d1.z : d1.w;
+      const uint32_t u = (uint32_t)id[k] + dk;
+      esum += e_byte(u & 0xffffu);
+      // the high half of the last word is mode M when M is even: offset 0, where
+      // the table holds zero (mode 0, fewer than one particle)
+      if (MT == 0 || 2 * k + 2 < MT) esum += e_byte(u >> 16);
+    }
+  } else if constexpr (RK == RK_EXACT) {  // int16 shifts, two modes per word
+    const uint4 d0 = reinterpret_cast<const uint4*>(dtab)[2 * (size_t)j];
+    const uint4 d1 = reinterpret_cast<const uint4*>(dtab)[2 * (size_t)j + 1];
+#pragma unroll
+    for (int m = 1; m < 16; ++m) {
+      if (m >= M) break;
+      const uint32_t word = (m < 2) ? d0.x : (m < 4) ? d0.y : (m < 6) ? d0.z : (m < 8) ? d0.w
+                          : (m < 10) ? d1.x : (m < 12) ? d1.y : (m < 14) ? d1.z : d1.w;
+      esum += *reinterpret_cast<const int32_t*>(reinterpret_cast<const char*>(E) + id[m] +
+                                                 ((int)(int16_t)(word >> (16 * (m & 1))) << 2));
+    }
+  } else {  // biased shift bytes, element indices stored minus the bias
+    const uint4 dd = reinterpret_cast<const uint4*>(dtab)[j];
+#pragma unroll
+    for (int m = 1; m < 16; ++m) {
+      if (m >= M) break;
+      const uint32_t word = (m < 4) ? dd.x : (m < 8) ? dd.y : (m < 12) ? dd.z : dd.w;
+      esum += E[id[m] + (int)((word >> (8 * (m & 3))) & 0xffu)];
+    }
+  }
+  return esum;
+}
+
+// One warp tile: kets [base, min(base + kRows, row1)) of the launch.  With LOCAL
+// the state vectors of DfArgs are the shared-memory copies of one sector starting
+// at ket local_off (gathers and own-row accesses are sector-local); otherwise they
+// are the global vectors.  The per-ket diagonal is always global.
 //
-// SIM: the double-float vectors hold f = psi / w in the weighted basis of the ket
-// weights w(n) = sqrt(N! / prod n_m!) (modes 0 to 3).  The similar matrix
-// W^-1 H W has the same diagonal, and for the target n' = n - e_r - e_s + e_p + e_q
-// of a term, w(n') / w(n) = sqrt(n_r (n_s - [r = s]) / ((n_p + 1)(n_q + 1 + [p = q]))),
-// so its element is G n_r (n_s - [r = s]): an integer times the coupling, with no
-// creation-side square roots and no lookup of n_p, n_q.  Modes 1 and 3 map back:
-// psi += w (z W^-1 H W f + sum of basef) in FP64, and write f = psi_new / w; the
-// bilinears multiply each factor by w.
+// The double-float vectors hold f = psi / w; modes 1 and 3 map back to the FP64
+// vector: psi += w (z W^-1 H W f + sum of basef), and write f = psi_new / w; the
+// bilinears and the <x|H|x> reduction multiply by w where true values are formed.
 //
-// EXACT: momentum conserved exactly: momentum arithmetic modulo t.Q > every
-// momentum sum, shifts stored as int16, the ranking table in global memory.
-template <int MT, int B, bool CPLX, bool BIL, bool LOCAL, bool SIM, bool EXACT>
-__device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const float2* sqf, const float4* Gf,
-                                           const uint4* dl4, const DfArgs& a, const int mode, const int64_t base,
-                                           const int64_t row1, const int64_t local_off, int32_t* sidx, uint8_t* socc,
-                                           int32_t* sD, int64_t* sOff, uint8_t* sperm, int32_t* hist,
-                                           int32_t* cursor, dfl& bil_l, dfl* bil_w) {
+// A gather index outside its sector is clamped into it and flagged in the status
+// word once per ket (bit 0), without a branch per term.
+template <int MT, int B, bool CPLX, int KIND, bool LOCAL, int RK, int kRows>
+__device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const float4* Gf, const unsigned char* dtab,
+                                           const DfArgs& a, const int mode, const int64_t base, const int64_t row1,
+                                           const int64_t local_off, int32_t* sidx, uint8_t* socc, int32_t* sD,
+                                           int64_t* sOff, uint8_t* sperm, int32_t* hist, int32_t* cursor, dfl& bil_l,
+                                           dfl* bil_w, double& dot64) {
+  constexpr bool EXACT = (RK == RK_EXACT);
+  constexpr bool BIL = (KIND == KIND_BIL), DOT = (KIND == KIND_DOT);
   const int M = (MT > 0) ? MT : t.M;
   const int Qm = EXACT ? t.Q : M;  // momentum modulus
   const int twoM = 2 * Qm;         // row width of the ranking table
@@ -113,11 +175,12 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
   const int64_t total = t.total;  // stride between sweep members
   const int nb = t.n_ann + 2;
   constexpr int kMB = (MT > 0) ? MT : 16;
-  // ---- phase 1: each lane unpacks (or unranks) kWarpRows/32 kets into occupations and suffix-state indices
+  constexpr int kPW = (MT > 0) ? (MT / 2 > 0 ? MT / 2 : 1) : 8;  // packed index words (RK_PAIR)
+  // ---- phase 1: each lane unpacks kRows/32 kets into occupations and suffix-state indices
   for (int k = lane; k < 2 * nb; k += 32) hist[k] = 0;
-  int key[kWarpRows / 32];
+  int key[kRows / 32];
 #pragma unroll
-  for (int u = 0; u < kWarpRows / 32; ++u) {
+  for (int u = 0; u < kRows / 32; ++u) {
     const int row = u * 32 + lane;
     const int64_t g = base + row;
     key[u] = 0;
@@ -125,56 +188,36 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
       const int sid = find_sector(t, g);
       const int64_t off = __ldg(t.sec_off + sid);
       const int D = (int)(__ldg(t.sec_off + sid + 1) - off);
-#if QB_OCC_TABLE
-      {
-        const uint64_t word = __ldg(t.occ + g);
-        const int ob = t.occ_bits;
-        const uint32_t omask = (1u << ob) - 1u;
-        for (int m = 0; m < M; ++m) socc[m * kWarpRows + row] = (uint8_t)((uint32_t)(word >> (m * ob)) & omask);
-      }
-#else
-      int rem = __ldg(t.sec_N + sid), kr = __ldg(t.sec_K + sid);
-      int left = (int)(g - off);
-      for (int m = 0; m < M - 1; ++m) {
-        int val = 0, kk = kr;
-#if QB_UNRANK_FROM_E
-        // cnt[m+1][n][k] = E_{m+2}(n + 1, k + m + 1), already in shared memory; for
-        // the last step cnt[M-1][n][k] = [n + k = 0 mod M] (one mode left)
-        const int32_t* erow = v.E + (min(m + 2, M - 1) * t.rem_w + 3) * twoM + m + 1;  // used for m + 2 < M
-        while (true) {
-          const int c = (m + 2 < M)  ? erow[(rem - val) * twoM + kk]
-                        : EXACT      ? ((M - 1) * (rem - val) == kk ? 1 : 0)
-                                     : (((rem - val + kk) % M) == 0 ? 1 : 0);
-#else
-        const uint32_t* crow = gcnt + (size_t)(m + 1) * V * M;
-        while (true) {
-          const int c = (int)crow[(rem - val) * M + kk];
-#endif
-          if (left < c || val == rem) break;
-          left -= c;
-          ++val;
-          kk -= m;
-          if (kk < 0) kk += Qm;
-        }
-        socc[m * kWarpRows + row] = (uint8_t)val;
-        rem -= val;
-        kr = kk;
-      }
-      socc[(M - 1) * kWarpRows + row] = (uint8_t)rem;
-#endif
+      const uint64_t word = __ldg(t.occ + g);
+      const int ob = t.occ_bits;
+      for (int m = 0; m < M; ++m) socc[m * kRows + row] = (uint8_t)occ_of(word, m, ob);
       int srem = 0, skr = 0, esum = 0, np = 0, n2 = 0;
+      uint32_t pk[kPW];
+#pragma unroll
+      for (int k = 0; k < kPW; ++k) pk[k] = 0u;
       for (int m = M - 1; m >= 1; --m) {
-        const int nm = socc[m * kWarpRows + row];
+        const int nm = socc[m * kRows + row];
         srem += nm;
         skr += m * nm;
         while (skr >= Qm) skr -= Qm;
         const int ix = (m * t.rem_w + srem + 2) * twoM + skr;
         esum += v.E[ix];
-        sidx[m * kWarpRows + row] = EXACT ? ix * 4 : ix - kDeltaBias;
+        if constexpr (RK == RK_PAIR) {
+#pragma unroll
+          for (int k = 0; k < kPW; ++k)
+            if (k == ((m - 1) >> 1)) pk[k] |= (uint32_t)(ix * 4) << ((m & 1) ? 0 : 16);
+        } else {
+          sidx[m * kRows + row] = EXACT ? ix * 4 : ix - kDeltaBias;
+        }
+      }
+      if constexpr (RK == RK_PAIR) {
+#pragma unroll
+        for (int k = 0; k < kPW; ++k)
+          if (2 * k + 1 < M) sidx[k * kRows + row] = (int32_t)pk[k];
       }
       if (D - 1 - esum != (int)(g - off)) atomicOr(a.status, 2);
       for (int m = 0; m < M; ++m) {
-        const int nm = socc[m * kWarpRows + row];
+        const int nm = socc[m * kRows + row];
         np += nm >= 1;
         n2 += nm >= 2;
       }
@@ -188,7 +231,7 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
   // ---- phase 2: warp-local counting sort of the tile by work, largest first
   __syncwarp();
 #pragma unroll
-  for (int u = 0; u < kWarpRows / 32; ++u) atomicAdd(&hist[key[u]], 1);
+  for (int u = 0; u < kRows / 32; ++u) atomicAdd(&hist[key[u]], 1);
   __syncwarp();
   if (lane == 0) {
     int run = 0;
@@ -199,11 +242,11 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
   }
   __syncwarp();
 #pragma unroll
-  for (int u = 0; u < kWarpRows / 32; ++u) sperm[atomicAdd(&cursor[key[u]], 1)] = (uint8_t)(u * 32 + lane);
+  for (int u = 0; u < kRows / 32; ++u) sperm[atomicAdd(&cursor[key[u]], 1)] = (uint8_t)(u * 32 + lane);
   __syncwarp();
 
   // ---- phase 3: rounds of 32 kets of similar work, one per lane
-  for (int round = 0; round < kWarpRows / 32; ++round) {
+  for (int round = 0; round < kRows / 32; ++round) {
     const int row = sperm[round * 32 + lane];
     const int D = sD[row];
     if (D < 0) continue;
@@ -212,14 +255,20 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
     const int64_t ri = LOCAL ? gr - local_off : gr;  // own-row index into the state vectors
     const uint8_t* occ = socc + row;
     int id[16];
+    if constexpr (RK == RK_PAIR) {
 #pragma unroll
-    for (int m = 1; m < 16; ++m)
-      if (m < M) id[m] = sidx[m * kWarpRows + row];
+      for (int k = 0; k < kPW; ++k)
+        if (2 * k + 1 < M) id[k] = sidx[k * kRows + row];
+    } else {
+#pragma unroll
+      for (int m = 1; m < 16; ++m)
+        if (m < M) id[m] = sidx[m * kRows + row];
+    }
     uint32_t occmask = 0, twomask = 0;
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
       if (m >= M) break;
-      const int nm = occ[m * kWarpRows];
+      const int nm = occ[m * kRows];
       occmask |= (nm >= 1 ? 1u : 0u) << m;
       twomask |= (nm >= 2 ? 1u : 0u) << m;
     }
@@ -227,8 +276,8 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
     dfc acc[B];  // (re, im) of the off-diagonal sum, double-float, packed
 #pragma unroll
     for (int b = 0; b < B; ++b) acc[b] = dfc{0ull, 0ull};
+    bool bad = false;  // a target rank fell outside the sector
 
-#if QB_CONVERGENT_PAIRS
     // One annihilation pair (r <= s, n_r (n_s - [r=s]) > 0) per iteration.  Kets of
     // a round have (nearly) the same pair count, so the iterations line up across
     // the warp; the search for the next r is a short inner loop.
@@ -244,30 +293,10 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
         if (!((twomask >> r) & 1u)) smask &= ~(1u << r);
       }
       if (smask == 0) break;  // not reached: npairs counts exactly the pairs found here
-#else
-    uint32_t rm = occmask, smask = 0;
-    int r = 0;
-    while (true) {
-      if (smask == 0) {
-        if (rm == 0) break;
-        r = __ffs(rm) - 1;
-        rm &= rm - 1;
-        smask = occmask & (~0u << r);
-        if (!((twomask >> r) & 1u)) smask &= ~(1u << r);
-        if (smask == 0) continue;
-      }
-#endif
       const int s = __ffs(smask) - 1;
       smask &= smask - 1;
       const int ai = v.pairidx[r * 16 + s];
-      dfl A{0.f, 0.f};  // sqrt(n_r (n_s - [r = s]))
-      float Af = 0.f;   // n_r (n_s - [r = s]), exact (SIM)
-      if (SIM) {
-        Af = (float)(occ[r * kWarpRows] * (occ[s * kWarpRows] - (r == s ? 1 : 0)));
-      } else {
-        const float2 sa = sqf[occ[r * kWarpRows]], sb = sqf[occ[s * kWarpRows] - (r == s ? 1 : 0)];
-        A = df_mul(dfl{sa.x, sa.y}, dfl{sb.x, sb.y});
-      }
+      const float Af = (float)(occ[r * kRows] * (occ[s * kRows] - (r == s ? 1 : 0)));  // exact
       // (exact momentum: the partner count varies from pair to pair)
       constexpr int kC = (QB_UNROLL_PARTNERS && !CPLX && !EXACT && MT > 0 && (MT % 2) == 1) ? (MT - 1) / 2 : 0;
       if (kC > 0) {
@@ -278,29 +307,11 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
 #pragma unroll
         for (int c = 0; c < kC; ++c) {
           const int j = j0 + c;
-          dfl AB{0.f, 0.f};
-          if (!SIM) {
-            const uint32_t w4 = v.pq[j];
-            const int p = w4 & 0xff, q = (w4 >> 8) & 0xff;
-            const float2 bp = sqf[occ[p * kWarpRows] + 1], bq = sqf[occ[q * kWarpRows] + 1 + (p == q ? 1 : 0)];
-            AB = df_mul(A, df_mul(dfl{bp.x, bp.y}, dfl{bq.x, bq.y}));
-          }
-          const uint4 dd = dl4[j];
-          int esum = 0;
-#pragma unroll
-          for (int m = 1; m < 16; ++m) {
-            if (m >= M) break;
-            const uint32_t word = (m < 4) ? dd.x : (m < 8) ? dd.y : (m < 12) ? dd.z : dd.w;
-            esum += e_at<EXACT>(v.E, id[m], (int)((word >> (8 * (m & 3))) & 0xffu));
-          }
-          int rk = D - 1 - esum;
-          if ((unsigned)rk >= (unsigned)D) {
-            atomicOr(a.status, 1);
-            rk = 0;
-          }
-          rkc[c] = rk;
+          const uint32_t rk = (uint32_t)(D - 1 - rank_esum<MT, RK>(t, v.E, dtab, j, id));
+          bad |= rk >= (uint32_t)D;
+          rkc[c] = (int)min(rk, (uint32_t)(D - 1));
           const float4 gf = Gf[j];
-          crc[c] = SIM ? df_mul_f(dfl{gf.x, gf.y}, Af) : df_mul(dfl{gf.x, gf.y}, AB);
+          crc[c] = df_mul_f(dfl{gf.x, gf.y}, Af);
         }
 #pragma unroll
         for (int b = 0; b < B; ++b) {
@@ -315,48 +326,19 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
       } else {
         const int j1 = v.ann[ai + 1];
         for (int j = v.ann[ai]; j < j1; ++j) {
-          dfl AB{0.f, 0.f};
-          if (!SIM) {
-            const uint32_t w4 = v.pq[j];
-            const int p = w4 & 0xff, q = (w4 >> 8) & 0xff;
-            const float2 bp = sqf[occ[p * kWarpRows] + 1], bq = sqf[occ[q * kWarpRows] + 1 + (p == q ? 1 : 0)];
-            AB = df_mul(A, df_mul(dfl{bp.x, bp.y}, dfl{bq.x, bq.y}));
-          }
-          // rank of the target: D - 1 - sum over every mode of E at the shifted suffix state
-          int esum = 0;
-          if (EXACT) {  // int16 shifts, two modes per word
-            const uint4 d0 = dl4[2 * j], d1 = dl4[2 * j + 1];
-  #pragma unroll
-            for (int m = 1; m < 16; ++m) {
-              if (m >= M) break;
-              const uint32_t word = (m < 2) ? d0.x : (m < 4) ? d0.y : (m < 6) ? d0.z : (m < 8) ? d0.w
-                                  : (m < 10) ? d1.x : (m < 12) ? d1.y : (m < 14) ? d1.z : d1.w;
-              esum += e_at<EXACT>(v.E, id[m], (int)(int16_t)(word >> (16 * (m & 1))));
-            }
-          } else {
-            const uint4 dd = dl4[j];
-  #pragma unroll
-            for (int m = 1; m < 16; ++m) {
-              if (m >= M) break;
-              const uint32_t word = (m < 4) ? dd.x : (m < 8) ? dd.y : (m < 12) ? dd.z : dd.w;
-              esum += e_at<EXACT>(v.E, id[m], (int)((word >> (8 * (m & 3))) & 0xffu));
-            }
-          }
-          int rk = D - 1 - esum;
-          if ((unsigned)rk >= (unsigned)D) {
-            atomicOr(a.status, 1);
-            rk = 0;
-          }
+          const uint32_t rku = (uint32_t)(D - 1 - rank_esum<MT, RK>(t, v.E, dtab, j, id));
+          bad |= rku >= (uint32_t)D;
+          const int rk = (int)min(rku, (uint32_t)(D - 1));
           const float4 gf = Gf[j];
-          const dfl cr = SIM ? df_mul_f(dfl{gf.x, gf.y}, Af) : df_mul(dfl{gf.x, gf.y}, AB);
-  #pragma unroll
+          const dfl cr = df_mul_f(dfl{gf.x, gf.y}, Af);
+#pragma unroll
           for (int b = 0; b < B; ++b) {
             const float4 x = gather<LOCAL>(vsec + (size_t)b * total + rk);
             const f2 xh = f2_pack(x.x, x.y), xl = f2_pack(x.z, x.w);
             dfc_fma(acc[b], f2_pack(cr.h, cr.h), f2_pack(-cr.h, -cr.h), f2_pack(cr.l, cr.l), xh, xl);
             if (CPLX) {
               // + (-c_i x_im, c_i x_re): lanes of x swapped, coefficient (-c_i, c_i)
-              const dfl ci = SIM ? df_mul_f(dfl{gf.z, gf.w}, Af) : df_mul(dfl{gf.z, gf.w}, AB);
+              const dfl ci = df_mul_f(dfl{gf.z, gf.w}, Af);
               dfc_fma(acc[b], f2_pack(-ci.h, ci.h), f2_pack(ci.h, -ci.h), f2_pack(-ci.l, ci.l),
                       f2_pack(x.y, x.x), f2_pack(x.w, x.z));
             }
@@ -367,12 +349,12 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
 #pragma unroll
       for (int b = 0; b < B; ++b) acc[b] = dfc_renorm(acc[b]);
     }
+    if (bad) atomicOr(a.status, 1);
 
     const float4 dg4 = a.diag[gr];
     const dfl zf{a.zf.x, a.zf.y};
-    // the ket weight where true values are formed (weighted basis)
-    const double2 wk = (SIM && (BIL || mode == 1 || mode == 3)) ? ket_weight<MT>(t, occ, kWarpRows)
-                                                                 : make_double2(1.0, 1.0);
+    // the ket weight where true values are formed
+    const double2 wk = (BIL || DOT || mode == 1 || mode == 3) ? ket_weight<MT>(t, occ, kRows) : make_double2(1.0, 1.0);
 #pragma unroll
     for (int b = 0; b < B; ++b) {
       dfl acc_r, acc_i;
@@ -383,25 +365,22 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
       const float4 xo = a.vin[(size_t)b * total + ri];
       const dfl hr = df_add(df_mul(dg, df_re(xo)), df_mul(sc, acc_r));
       const dfl hi = df_add(df_mul(dg, df_im(xo)), df_mul(sc, acc_i));
-      if (BIL && mode == 4) {  // <x|H|x>: Re(conj(x) Hx) of this row, no output
-        bil_l = df_add(bil_l, df_add(df_mul(df_re(xo), hr), df_mul(df_im(xo), hi)));
+      if (DOT) {
+        // <x|H|x>: Re(conj(psi_n) (H psi)_n) = w^2 Re(conj(f_n) (W^-1 H W f)_n), w^2 in
+        // FP64 (w^2 alone may leave the fp32 range); no output
+        const dfl val = df_add(df_mul(df_re(xo), hr), df_mul(df_im(xo), hi));
+        dot64 += df_to(val) * wk.x * wk.x;
         continue;
       }
       if (BIL && b == 0) {
-        // H_L x (two-body part at scale 1) and the pair vector of this row
+        // H_L x (two-body part at scale 1) and the pair vector of this row, as true
+        // values: each factor times w (w^2 alone may leave the fp32 range)
         const float4 pp = a.pair[ri];
-        dfl lr = df_add(df_mul(dfl{dg4.z, dg4.w}, df_re(xo)), acc_r);
-        dfl li = df_add(df_mul(dfl{dg4.z, dg4.w}, df_im(xo)), acc_i);
-        dfl pr = df_re(pp), pi = df_im(pp), xr = df_re(xo), xi = df_im(xo);
-        if (SIM) {  // true values: each factor times w (w^2 alone may leave the fp32 range)
-          const dfl wd = df_of(wk.x);
-          lr = df_mul(wd, lr);
-          li = df_mul(wd, li);
-          pr = df_mul(wd, pr);
-          pi = df_mul(wd, pi);
-          xr = df_mul(wd, xr);
-          xi = df_mul(wd, xi);
-        }
+        const dfl wd = df_of(wk.x);
+        const dfl lr = df_mul(wd, df_add(df_mul(dfl{dg4.z, dg4.w}, df_re(xo)), acc_r));
+        const dfl li = df_mul(wd, df_add(df_mul(dfl{dg4.z, dg4.w}, df_im(xo)), acc_i));
+        const dfl pr = df_mul(wd, df_re(pp)), pi = df_mul(wd, df_im(pp));
+        const dfl xr = df_mul(wd, df_re(xo)), xi = df_mul(wd, df_im(xo));
         // Im(conj(p) h) = p.re h.im - p.im h.re
         bil_l = df_add(bil_l, df_add(df_mul(pr, li), df_neg(df_mul(pi, lr))));
         // Im(conj(x) p) = x.re p.im - x.im p.re, weighted by each occupation
@@ -409,7 +388,7 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
 #pragma unroll
         for (int q = 0; q < kMB; ++q) {
           if (q >= M) break;
-          bil_w[q] = df_add(bil_w[q], df_mul(dfl{(float)occ[q * kWarpRows], 0.f}, tx));
+          bil_w[q] = df_add(bil_w[q], df_mul(dfl{(float)occ[q * kRows], 0.f}, tx));
         }
       }
       if (mode == 0 || mode == 2) {
@@ -420,7 +399,7 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
           oi = df_add(df_im(p0), oi);
         }
         a.out[(size_t)b * total + ri] = df_pack(orr, oi);
-      } else if (SIM) {  // modes 1 and 3: back to the FP64 vector, one weight per ket
+      } else {  // modes 1 and 3: back to the FP64 vector, one weight per ket
         double sr = a.zre * df_to(hi), si = -a.zre * df_to(hr);
         if (mode == 3) {
           for (int k = 0; k < a.nbasef; ++k) {
@@ -433,19 +412,6 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
         const double nr = p0.x + wk.x * sr, ni = p0.y + wk.x * si;
         a.psi[(size_t)b * total + ri] = make_double2(nr, ni);
         a.out[(size_t)b * total + ri] = df_pack(df_of(nr * wk.y), df_of(ni * wk.y));
-      } else {
-        const double2 p0 = a.psi[(size_t)b * total + ri];
-        double nr = p0.x + a.zre * df_to(hi);
-        double ni = p0.y - a.zre * df_to(hr);
-        if (mode == 3) {
-          for (int k = 0; k < a.nbasef; ++k) {
-            const float4 e = a.basef[k][(size_t)b * total + ri];
-            nr += df_to(df_re(e));
-            ni += df_to(df_im(e));
-          }
-        }
-        a.psi[(size_t)b * total + ri] = make_double2(nr, ni);
-        a.out[(size_t)b * total + ri] = df_pack(df_of(nr), df_of(ni));
       }
     }
   }
@@ -456,9 +422,8 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
 // and the per-warp tile scratch; sets up every pointer stage_tile needs.
 struct StageSmem {
   View v;
-  const float2* sqf;
   const float4* Gf;
-  const uint4* dl4;
+  const unsigned char* dtab;  // shifts of the ranking variant
   int32_t* sidx;
   uint8_t* socc;
   int32_t* sD;
@@ -470,40 +435,48 @@ struct StageSmem {
 };
 
 // Stages the table image (a CTA-wide barrier) and lays out the warp scratch.
-template <bool EXACT>
-__device__ __forceinline__ StageSmem stage_smem(const Tables& t, unsigned char* smem_raw, int M, int warps) {
+template <int RK>
+__device__ __forceinline__ StageSmem stage_smem(const Tables& t, int M, int warps, int rows) {
   StageSmem S;
-  const int from = kSmemFrom(t, EXACT);
-  load_blob_from(t, smem_raw, from);
-  unsigned char* smem = smem_raw - from;
+  const int from = kSmemFrom(t, RK == RK_EXACT);
+  load_blob_from(t, stage_smem_raw, from);
+  unsigned char* smem = stage_smem_raw - from;
   S.v = view_at(t, smem);
-  if (EXACT) S.v.E = reinterpret_cast<const int32_t*>(t.blob + t.o_E);
-  S.sqf = reinterpret_cast<const float2*>(smem + t.o_sqf);
+  if (RK == RK_EXACT) S.v.E = reinterpret_cast<const int32_t*>(t.blob + t.o_E);
   S.Gf = reinterpret_cast<const float4*>(smem + t.o_Gf);
-  S.dl4 = reinterpret_cast<const uint4*>(S.v.delta);
+  S.dtab = (RK == RK_PAIR) ? smem + t.o_dsw : reinterpret_cast<const unsigned char*>(S.v.delta);
   const int warp = threadIdx.x >> 5;
-  const size_t wbytes = df_warp_scratch_bytes(M, t.n_ann);
-  unsigned char* base = smem_raw + ((t.blob_bytes - from + 15) & ~15);
+  const size_t wbytes = df_warp_scratch_bytes(M, t.n_ann, rows);
+  unsigned char* base = stage_smem_raw + ((t.blob_bytes - from + 15) & ~15);
   unsigned char* sp = base + (size_t)warp * wbytes;
   S.sidx = reinterpret_cast<int32_t*>(sp);
-  S.socc = reinterpret_cast<uint8_t*>(S.sidx + M * kWarpRows);
-  S.sD = reinterpret_cast<int32_t*>(S.socc + ((M * kWarpRows + 15) & ~15));
-  S.sOff = reinterpret_cast<int64_t*>(S.sD + kWarpRows);
-  S.sperm = reinterpret_cast<uint8_t*>(S.sOff + kWarpRows);
-  S.hist = reinterpret_cast<int32_t*>(S.sperm + kWarpRows);
+  S.socc = reinterpret_cast<uint8_t*>(S.sidx + M * rows);
+  S.sD = reinterpret_cast<int32_t*>(S.socc + ((M * rows + 15) & ~15));
+  S.sOff = reinterpret_cast<int64_t*>(S.sD + rows);
+  S.sperm = reinterpret_cast<uint8_t*>(S.sOff + rows);
+  S.hist = reinterpret_cast<int32_t*>(S.sperm + rows);
   S.cursor = S.hist + (t.n_ann + 2);
   S.after = base + (size_t)warps * wbytes;
   return S;
 }
 
-template <int MT, int B, bool CPLX, bool BIL, bool SIM, bool EXACT>
-__global__ void __launch_bounds__(kStageBlock, (B == 1 && !BIL) ? kStageMinBlocks : ((BIL && MT > 0) ? 2 : 1))
+// Resident CTAs per SM the launch bounds plan for: the single-state stages at their
+// shape's count; the bilinear ones of the specialised mode counts at 2 CTAs per SM
+// (80 registers, more accumulators per lane); the batched ones and the generic
+// bilinear ones (16 accumulators) keep the compiler's choice (one CTA).
+template <int MT, int B, int KIND, int TS>
+__host__ __device__ constexpr int stage_min_blocks() {
+  return (B == 1 && KIND != KIND_BIL) ? tile_shape(TS).min_blocks : ((KIND == KIND_BIL && MT > 0) ? 2 : 1);
+}
+
+template <int MT, int B, bool CPLX, int KIND, int RK, int TS>
+__global__ void __launch_bounds__(32 * tile_shape(TS).warps, (stage_min_blocks<MT, B, KIND, TS>()))
     stage_df_kernel(const Tables t, const DfArgs a, const int mode) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr bool BIL = (KIND == KIND_BIL), DOT = (KIND == KIND_DOT);
+  constexpr int kWarps = tile_shape(TS).warps, kRows = tile_shape(TS).rows;
   const int M = (MT > 0) ? MT : t.M;
   // the only CTA-wide barrier: warps run independently afterwards
-  const StageSmem S = stage_smem<EXACT>(t, smem_raw, M, kStageWarps);
-  constexpr int kWarps = kStageWarps;
+  const StageSmem S = stage_smem<RK>(t, M, kWarps, kRows);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t row1 = a.row1;
   constexpr int kMB = (MT > 0) ? MT : 16;  // bilinear accumulators: one per mode + H_L
@@ -511,22 +484,35 @@ __global__ void __launch_bounds__(kStageBlock, (B == 1 && !BIL) ? kStageMinBlock
   dfl bil_w[BIL ? kMB : 1];
 #pragma unroll
   for (int q = 0; q < (BIL ? kMB : 1); ++q) bil_w[q] = dfl{0.f, 0.f};
+  double dot64 = 0.0;
 
-  for (int64_t base = a.row0 + ((int64_t)blockIdx.x * kWarps + warp) * kWarpRows; base < row1;
-       base += (int64_t)gridDim.x * kWarps * kWarpRows)
-    stage_tile<MT, B, CPLX, BIL, false, SIM, EXACT>(t, S.v, S.sqf, S.Gf, S.dl4, a, mode, base, row1, 0, S.sidx, S.socc,
-                                             S.sD, S.sOff, S.sperm, S.hist, S.cursor, bil_l, bil_w);
-  if (BIL) {
+  for (int64_t base = a.row0 + ((int64_t)blockIdx.x * kWarps + warp) * kRows; base < row1;
+       base += (int64_t)gridDim.x * kWarps * kRows)
+    stage_tile<MT, B, CPLX, KIND, false, RK, kRows>(t, S.v, S.Gf, S.dtab, a, mode, base, row1, 0, S.sidx, S.socc, S.sD,
+                                                    S.sOff, S.sperm, S.hist, S.cursor, bil_l, bil_w, dot64);
+  if constexpr (DOT) {
+    // the CTA's sum in a fixed order: lanes by shuffles, warps in turn; partial[block]
+    __shared__ double red[kWarps];
+    for (int o = 16; o > 0; o >>= 1) dot64 += __shfl_down_sync(0xffffffffu, dot64, o);
+    if (lane == 0) red[warp] = dot64;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int w = 0; w < kWarps; ++w) sum += red[w];
+      a.partial[blockIdx.x] = sum;
+    }
+  }
+  if constexpr (BIL) {
     // per-CTA sums of the bilinears in a fixed order: lanes by shuffles, warps in turn
-    __shared__ double red[kStageWarps][17];
+    __shared__ double red[kWarps][17];
     const int nq = M + 1;
     for (int q = 0; q < nq; ++q) {
-      double v = (q == 0) ? df_to(bil_l) : 0.0;
+      double val = (q == 0) ? df_to(bil_l) : 0.0;
 #pragma unroll
       for (int u = 0; u < kMB; ++u)
-        if (q == u + 1) v = df_to(bil_w[u]);
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) red[warp][q] = v;
+        if (q == u + 1) val = df_to(bil_w[u]);
+      for (int o = 16; o > 0; o >>= 1) val += __shfl_down_sync(0xffffffffu, val, o);
+      if (lane == 0) red[warp][q] = val;
     }
     __syncthreads();
     if (threadIdx.x < nq) {
@@ -556,18 +542,20 @@ struct ResArgs {
   int* status;
 };
 
-template <int MT, bool CPLX, bool EXACT>
+constexpr int kResRows = 64;  // kets per warp tile of the resident kernel
+
+template <int MT, bool CPLX, int RK>
 __global__ void __launch_bounds__(kBlock) resident_kernel(const Tables t, const ResArgs r) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int M = (MT > 0) ? MT : t.M;
-  const StageSmem S = stage_smem<EXACT>(t, smem_raw, M, kBlock / 32);
+  constexpr int kWarps = kBlock / 32;
+  const StageSmem S = stage_smem<RK>(t, M, kWarps, kResRows);
   double2* spsi = reinterpret_cast<double2*>(S.after);
   float4* spsif = reinterpret_cast<float4*>(spsi + r.cap);
   float4* sw1 = spsif + r.cap;
   float4* sw2 = sw1 + r.cap;
-  constexpr int kWarps = kBlock / 32;
   const int warp = threadIdx.x >> 5;
   dfl bil_l{0.f, 0.f}, bil_w[1] = {dfl{0.f, 0.f}};
+  double dot64 = 0.0;
   for (int sid = blockIdx.x; sid < r.n_small; sid += gridDim.x) {
     const int64_t off = __ldg(t.sec_off + sid);
     const int D = (int)(__ldg(t.sec_off + sid + 1) - off);
@@ -595,13 +583,14 @@ __global__ void __launch_bounds__(kBlock) resident_kernel(const Tables t, const 
         a.zre = r.dt / d;
         const float zh = (float)a.zre;
         a.zf = make_float2(zh, (float)(a.zre - (double)zh));
-        // the sector's kets are dealt to the warps in chunks of at most kWarpRows,
+        // the sector's kets are dealt to the warps in chunks of at most kResRows,
         // evenly, so that a small sector still keeps every warp busy
-        const int64_t chunk = min((int64_t)kWarpRows, ((int64_t)D + kWarps - 1) / kWarps);
+        const int64_t chunk = min((int64_t)kResRows, ((int64_t)D + kWarps - 1) / kWarps);
         for (int64_t base = off + (int64_t)warp * chunk; base < off + D; base += (int64_t)kWarps * chunk)
-          stage_tile<MT, 1, CPLX, false, true, true, EXACT>(t, S.v, S.sqf, S.Gf, S.dl4, a, d == 1 ? 1 : 0, base,
-                                               min(base + chunk, off + (int64_t)D), off, S.sidx, S.socc, S.sD,
-                                               S.sOff, S.sperm, S.hist, S.cursor, bil_l, bil_w);
+          stage_tile<MT, 1, CPLX, KIND_STAGE, true, RK, kResRows>(t, S.v, S.Gf, S.dtab, a, d == 1 ? 1 : 0, base,
+                                                             min(base + chunk, off + (int64_t)D), off, S.sidx, S.socc,
+                                                             S.sD, S.sOff, S.sperm, S.hist, S.cursor, bil_l, bil_w,
+                                                             dot64);
         __syncthreads();
       }
     }
@@ -613,23 +602,28 @@ __global__ void __launch_bounds__(kBlock) resident_kernel(const Tables t, const 
   }
 }
 
-// Shared memory of the resident kernel holding `cap` kets per sector.
-inline size_t resident_smem(const Tables& t, int cap) {
-  return ((t.blob_bytes - kSmemFrom(t, t.exact != 0) + 15) & ~15) + df_scratch_bytes(t.M, t.n_ann) +
-         (size_t)cap * 64;
+// ranking variant of a space
+__host__ __device__ inline int rank_variant(const Tables& t) {
+  return t.exact ? RK_EXACT : (t.sw_ok ? RK_PAIR : RK_BYTE);
 }
 
-template <int MT, bool EXACT>
-int resident_launch_e(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t st) {
+// Shared memory of the resident kernel holding `cap` kets per sector.
+inline size_t resident_smem(const Tables& t, int cap) {
+  return ((t.blob_bytes - kSmemFrom(t, t.exact != 0) + 15) & ~15) +
+         (size_t)(kBlock / 32) * df_warp_scratch_bytes(t.M, t.n_ann, kResRows) + (size_t)cap * 64;
+}
+
+template <int MT, int RK>
+int resident_launch_r(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t st) {
   const size_t smem = resident_smem(t, r.cap);
   int grid = 0, rc = QB_OK;
   if (cplx) {
-    auto k = resident_kernel<MT, true, EXACT>;
+    auto k = resident_kernel<MT, true, RK>;
     rc = persistent_grid(k, smem, (int64_t)r.n_small * kBlock, &grid);
     if (rc) return rc;
     k<<<grid, kBlock, smem, st>>>(t, r);
   } else {
-    auto k = resident_kernel<MT, false, EXACT>;
+    auto k = resident_kernel<MT, false, RK>;
     rc = persistent_grid(k, smem, (int64_t)r.n_small * kBlock, &grid);
     if (rc) return rc;
     k<<<grid, kBlock, smem, st>>>(t, r);
@@ -640,59 +634,68 @@ int resident_launch_e(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t
 
 template <int MT>
 int resident_launch_t(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t st) {
-  if (t.exact) return resident_launch_e<MT, true>(t, r, cplx, st);
-  return resident_launch_e<MT, false>(t, r, cplx, st);
+  switch (rank_variant(t)) {
+    case RK_EXACT: return resident_launch_r<MT, RK_EXACT>(t, r, cplx, st);
+    case RK_PAIR: return resident_launch_r<MT, RK_PAIR>(t, r, cplx, st);
+    default: return resident_launch_r<MT, RK_BYTE>(t, r, cplx, st);
+  }
 }
 
-// Launches one stage for mode count MT (0: any M) and the runtime batch size /
-// coupling type / bilinear flag / basis (sim: the weighted basis of the RK4 and
-// adjoint stages, modes 0 to 3; plain: the <H> reduction, mode 4); *grid (if
-// non-NULL) receives the grid size.  Exact momentum: one state at a time.
-template <int MT, bool EXACT>
-int stage_launch_e(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, bool bil, bool sim, cudaStream_t st,
+// Launches one stage for mode count MT (0: any M), ranking variant RK and the
+// runtime batch size / coupling type / bilinear flag; `shape` selects the tile
+// shape of the single-state stage (others run shape 0).  *grid (if non-NULL)
+// receives the grid size.  Exact momentum: one state at a time.
+template <int MT, int RK>
+int stage_launch_r(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, bool bil, int shape, cudaStream_t st,
                    int* grid_out) {
-  const size_t smem = ((t.blob_bytes - kSmemFrom(t, EXACT) + 15) & ~15) +
-                      (size_t)kStageWarps * df_warp_scratch_bytes(t.M, t.n_ann);
   int grid = 0, rc = QB_OK;
-#define QB_STAGE_CASE(BB, CC, LL, SS)                                           \
-  {                                                                             \
-    auto k = stage_df_kernel<MT, BB, CC, LL, SS, EXACT>;                        \
-    rc = persistent_grid(k, smem, a.row1 - a.row0, &grid, kStageBlock);         \
-    if (rc) return rc;                                                          \
-    k<<<grid, kStageBlock, smem, st>>>(t, a, mode);                             \
+#define QB_STAGE_CASE(BB, CC, LL, TT)                                                                   \
+  {                                                                                                     \
+    auto k = stage_df_kernel<MT, BB, CC, LL, RK, TT>;                                                   \
+    constexpr TileShape sh = tile_shape(TT);                                                            \
+    const size_t smem = ((t.blob_bytes - kSmemFrom(t, RK == RK_EXACT) + 15) & ~15) +                    \
+                        (size_t)sh.warps * df_warp_scratch_bytes(t.M, t.n_ann, sh.rows);               \
+    rc = persistent_grid(k, smem, a.row1 - a.row0, &grid, 32 * sh.warps);                               \
+    if (rc) return rc;                                                                                  \
+    k<<<grid, 32 * sh.warps, smem, st>>>(t, a, mode);                                                   \
   }
-  if (sim) {
-    if (mode < 0 || mode > 3) return fail(QB_EINTERNAL, "the weighted basis serves modes 0 to 3");
-    if (bil) {
-      if (B != 1) return fail(QB_EUNSUPPORTED, "bilinear stages run one state at a time");
-      if (cplx)
-        QB_STAGE_CASE(1, true, true, true)
-      else
-        QB_STAGE_CASE(1, false, true, true)
-    } else if (cplx) {
-      if (B != 1) return fail(QB_EUNSUPPORTED, "batched sweeps need a real coupling");
-      QB_STAGE_CASE(1, true, false, true)
+  if (mode < 0 || mode > 4) return fail(QB_EINTERNAL, "bad stage mode");
+  if (mode == 4) {  // <x|H|x>
+    if (B != 1) return fail(QB_EUNSUPPORTED, "the <x|H|x> reduction runs one state at a time");
+    if (cplx)
+      QB_STAGE_CASE(1, true, KIND_DOT, 0)
+    else
+      QB_STAGE_CASE(1, false, KIND_DOT, 0)
+  } else if (bil) {
+    if (B != 1) return fail(QB_EUNSUPPORTED, "bilinear stages run one state at a time");
+    if (cplx)
+      QB_STAGE_CASE(1, true, KIND_BIL, 0)
+    else
+      QB_STAGE_CASE(1, false, KIND_BIL, 0)
+  } else if (cplx) {
+    if (B != 1) return fail(QB_EUNSUPPORTED, "batched sweeps need a real coupling");
+    QB_STAGE_CASE(1, true, KIND_STAGE, 0)
+  } else {
+    if constexpr (RK == RK_EXACT) {
+      if (B != 1) return fail(QB_EUNSUPPORTED, "exact momentum: batched sweeps are not built");
+      QB_STAGE_CASE(1, false, KIND_STAGE, 0)
     } else {
-      if constexpr (EXACT) {
-        if (B != 1) return fail(QB_EUNSUPPORTED, "exact momentum: batched sweeps are not built");
-        QB_STAGE_CASE(1, false, false, true)
-      } else {
-        switch (B) {
-          case 1: QB_STAGE_CASE(1, false, false, true) break;
-          case 2: QB_STAGE_CASE(2, false, false, true) break;
-          case 4: QB_STAGE_CASE(4, false, false, true) break;
-          case 8: QB_STAGE_CASE(8, false, false, true) break;
-          default: return fail(QB_EINVAL, "batch must be 1, 2, 4 or 8");
-        }
+      switch (B) {
+        case 1:
+          switch (shape) {
+            case 1: QB_STAGE_CASE(1, false, KIND_STAGE, 1) break;
+            case 2: QB_STAGE_CASE(1, false, KIND_STAGE, 2) break;
+            case 3: QB_STAGE_CASE(1, false, KIND_STAGE, 3) break;
+            case 4: QB_STAGE_CASE(1, false, KIND_STAGE, 4) break;
+            default: QB_STAGE_CASE(1, false, KIND_STAGE, 0) break;
+          }
+          break;
+        case 2: QB_STAGE_CASE(2, false, KIND_STAGE, 0) break;
+        case 4: QB_STAGE_CASE(4, false, KIND_STAGE, 0) break;
+        case 8: QB_STAGE_CASE(8, false, KIND_STAGE, 0) break;
+        default: return fail(QB_EINVAL, "batch must be 1, 2, 4 or 8");
       }
     }
-  } else {
-    // the plain basis serves the <x|H|x> reduction of the observables
-    if (!bil || mode != 4 || B != 1) return fail(QB_EINTERNAL, "the plain basis serves the <H> reduction only");
-    if (cplx)
-      QB_STAGE_CASE(1, true, true, false)
-    else
-      QB_STAGE_CASE(1, false, true, false)
   }
 #undef QB_STAGE_CASE
   QB_CUDA(cudaGetLastError());
@@ -701,18 +704,21 @@ int stage_launch_e(const Tables& t, const DfArgs& a, int mode, int B, bool cplx,
 }
 
 template <int MT>
-int stage_launch_t(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, bool bil, bool sim, cudaStream_t st,
+int stage_launch_t(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, bool bil, int shape, cudaStream_t st,
                    int* grid_out) {
-  if (t.exact) return stage_launch_e<MT, true>(t, a, mode, B, cplx, bil, sim, st, grid_out);
-  return stage_launch_e<MT, false>(t, a, mode, B, cplx, bil, sim, st, grid_out);
+  switch (rank_variant(t)) {
+    case RK_EXACT: return stage_launch_r<MT, RK_EXACT>(t, a, mode, B, cplx, bil, shape, st, grid_out);
+    case RK_PAIR: return stage_launch_r<MT, RK_PAIR>(t, a, mode, B, cplx, bil, shape, st, grid_out);
+    default: return stage_launch_r<MT, RK_BYTE>(t, a, mode, B, cplx, bil, shape, st, grid_out);
+  }
 }
 
 // one explicit specialisation per translation unit (qb_stage_m*.cu)
-int stage_launch_m5(const Tables&, const DfArgs&, int, int, bool, bool, bool, cudaStream_t, int*);
-int stage_launch_m7(const Tables&, const DfArgs&, int, int, bool, bool, bool, cudaStream_t, int*);
-int stage_launch_m9(const Tables&, const DfArgs&, int, int, bool, bool, bool, cudaStream_t, int*);
-int stage_launch_m11(const Tables&, const DfArgs&, int, int, bool, bool, bool, cudaStream_t, int*);
-int stage_launch_any(const Tables&, const DfArgs&, int, int, bool, bool, bool, cudaStream_t, int*);
+int stage_launch_m5(const Tables&, const DfArgs&, int, int, bool, bool, int, cudaStream_t, int*);
+int stage_launch_m7(const Tables&, const DfArgs&, int, int, bool, bool, int, cudaStream_t, int*);
+int stage_launch_m9(const Tables&, const DfArgs&, int, int, bool, bool, int, cudaStream_t, int*);
+int stage_launch_m11(const Tables&, const DfArgs&, int, int, bool, bool, int, cudaStream_t, int*);
+int stage_launch_any(const Tables&, const DfArgs&, int, int, bool, bool, int, cudaStream_t, int*);
 
 int resident_launch_m5(const Tables&, const ResArgs&, bool, cudaStream_t);
 int resident_launch_m7(const Tables&, const ResArgs&, bool, cudaStream_t);
@@ -730,14 +736,17 @@ inline int resident_launch(const Tables& t, const ResArgs& r, bool cplx, cudaStr
   }
 }
 
+// One stage over rows [a.row0, a.row1) in the weighted basis.  bil: the bilinear
+// instantiations (adjoint modes 2, 3); mode 4 is the <x|H|x> reduction (partial[block]);
+// shape: tile shape of the single-state stage (0: the default).
 inline int stage_launch(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, cudaStream_t st,
-                        int* grid_out = nullptr, bool bil = false, bool sim = false) {
+                        int* grid_out = nullptr, bool bil = false, int shape = 0) {
   switch (t.M) {
-    case 5: return stage_launch_m5(t, a, mode, B, cplx, bil, sim, st, grid_out);
-    case 7: return stage_launch_m7(t, a, mode, B, cplx, bil, sim, st, grid_out);
-    case 9: return stage_launch_m9(t, a, mode, B, cplx, bil, sim, st, grid_out);
-    case 11: return stage_launch_m11(t, a, mode, B, cplx, bil, sim, st, grid_out);
-    default: return stage_launch_any(t, a, mode, B, cplx, bil, sim, st, grid_out);
+    case 5: return stage_launch_m5(t, a, mode, B, cplx, bil, shape, st, grid_out);
+    case 7: return stage_launch_m7(t, a, mode, B, cplx, bil, shape, st, grid_out);
+    case 9: return stage_launch_m9(t, a, mode, B, cplx, bil, shape, st, grid_out);
+    case 11: return stage_launch_m11(t, a, mode, B, cplx, bil, shape, st, grid_out);
+    default: return stage_launch_any(t, a, mode, B, cplx, bil, shape, st, grid_out);
   }
 }
 

@@ -2,9 +2,9 @@
 #include "qb_stage.cuh"
 
 namespace qb {
-int stage_launch_any(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, bool bil, bool sim, cudaStream_t st,
+int stage_launch_any(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, bool bil, int shape, cudaStream_t st,
                    int* grid) {
-  return stage_launch_t<0>(t, a, mode, B, cplx, bil, sim, st, grid);
+  return stage_launch_t<0>(t, a, mode, B, cplx, bil, shape, st, grid);
 }
 int resident_launch_any(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t st) {
   return resident_launch_t<0>(t, r, cplx, st);

@@ -1,5 +1,5 @@
 """The C ABI library loads here (no GPU needed) and exports every function
-include/qb.h declares; host-only entry points work without a device."""
+include/*.h declares; host-only entry points work without a device."""
 import ctypes
 import os
 import re
@@ -11,9 +11,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "qb.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(qb_[a-z_]+)\s*\(", src)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for h in sorted(os.listdir(inc)):
+        if h.endswith(".h"):
+            src = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, h)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(qb_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_library_exports_every_declared_symbol():
@@ -58,7 +62,7 @@ def test_meanfield_matches_oracle():
     np.testing.assert_allclose(a, b, atol=1e-12)
 
 
-@pytest.mark.parametrize("bad", ["nonhermitian", "nonconserving", "too_many_modes", "too_deep"])
+@pytest.mark.parametrize("bad", ["nonhermitian", "nonconserving", "too_many_modes", "too_deep", "too_heavy"])
 def test_model_validation_without_device(bad):
     import paper_2111_00050_gb300 as qb
     import workloads as wl
@@ -76,11 +80,17 @@ def test_model_validation_without_device(bad):
     elif bad == "too_many_modes":
         M = 17
         w, L = np.zeros(M), np.zeros((M,) * 4)
-    else:
+    elif bad == "too_deep":
         n_max = 1 << 13
+    else:
+        # packs into 64 bits (5 x 8), but the largest ket weight sqrt(150!/(30!)^5) is
+        # 2^167: the weighted fp32-pair stage vectors could not hold psi / w
+        n_max = 150
     with pytest.raises(qb.QbError) as e:
         qb.Space(M, w, L, 0, n_max)
     assert e.value.code in (1, 6)
+    if bad == "too_heavy":
+        assert e.value.code == qb.QB_EUNSUPPORTED and "ket weights" in str(e.value)
 
 
 def test_squeezing_analysis_matches_oracle():

@@ -91,6 +91,10 @@ def test_autograd_function_returns_adjoint_gradients():
     assert _rel(s_t.grad.item(), ref[1]) <= 1e-7
     assert _rel(w_t.grad.numpy(), ref[2]) <= 1e-7
     assert _rel(z_t.grad.numpy(), ref[3]) <= 1e-7
+    # without gradients only the forward run and the loss are computed, on the cached space
+    with torch.no_grad():
+        plain = qb.adjoint_loss(s_t, w_t, z_t, M=M, L0=L0, n_min=0, n_max=10, dt=dt, steps=steps, loss="Q")
+    assert abs(plain.item() - ref[0]) <= 1e-10
 
 
 def test_adjoint_full_size_against_central_differences():

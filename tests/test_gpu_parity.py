@@ -273,6 +273,40 @@ def test_errors_are_reported():
         qs.init_number([3, 0, 0, 0, 1], qs.empty_state())  # N=4 not held
 
 
+@pytest.mark.parametrize("call", ["evolve", "hpsi", "observables", "basis"])
+def test_device_status_word_fails_the_next_call(call):
+    """A failed device-side check is reported through the space's status word, not
+    a fault: with a bit pre-set on the host (qb_space_status), the next call that
+    synchronises returns QB_EINTERNAL and clears the word, and the call after it
+    succeeds with unchanged results."""
+    import paper_2111_00050_gb300 as qb
+
+    M = 5
+    w = wl.dispersion_quadratic(M)
+    L = wl.contact_coupling(M, -0.1)
+    qs = qb.Space(M, w, L, 0, 6)
+    psi = qs.empty_state()
+    qs.init_coherent(np.array([0.3, 0.8j, 0.5, 0.0, -0.2]), psi)
+    out = qs.empty_state()
+    run = {"evolve": lambda: qs.evolve(psi, 1e-3, 3), "hpsi": lambda: qs.hpsi(psi, out),
+           "observables": lambda: qs.observables(psi), "basis": lambda: qs.basis(0, 7)}[call]
+    run()
+    ref = to_host(psi).copy()
+    assert qs.status() == 0
+    assert qs.status(2) == 2
+    with pytest.raises(qb.QbError) as e:
+        run()
+    assert e.value.code == qb.QB_EINTERNAL and "status 2" in str(e.value)
+    assert qs.status() == 0
+    if call == "evolve":
+        psi.copy_(to_dev(ref))
+    run()
+    if call == "evolve":
+        again = to_dev(ref)
+        qs.evolve(again, 1e-3, 3)
+        assert bool((psi == again).all())
+
+
 def test_plain_per_sector_path_is_bit_identical_to_batched():
     """One launch per sector per stage and one launch for all sectors compute every
     ket with the same arithmetic: the states must agree bit for bit."""

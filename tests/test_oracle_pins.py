@@ -902,3 +902,19 @@ def test_meanfield_pins_reject_planted_mistakes(mutant):
     drift_e = abs(classical_energy(w, L, x) - E0)
     drift_n = abs(float(np.sum(np.abs(x) ** 2)) - float(np.sum(np.abs(a0) ** 2)))
     assert drift_e > 1e-4 or drift_n > 1e-4
+
+
+def test_row_parallel_rk4_equals_rk4():
+    """The row-by-row RK4 of the timed CPU baseline (OpenMP over rows where the
+    compiler has it) computes the same scheme as rk4: only the summation order of
+    each row differs."""
+    M = 5
+    rng = np.random.default_rng(41)
+    L = random_hermitian_coupling(M, rng, 0.2)
+    w = rng.standard_normal(M)
+    space = orc.Space(M, orc.all_sectors(M, 0, 7))
+    psi = rng.standard_normal(space.total) + 1j * rng.standard_normal(space.total)
+    a = orc.rk4(space, w, L, psi, 0.01, 5)
+    b = orc.rk4_rows(space, w, L, psi, 0.01, 5)
+    assert np.linalg.norm(a - b) <= 1e-13 * np.linalg.norm(a)
+    assert orc.threads() >= 1
