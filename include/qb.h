@@ -195,8 +195,8 @@ int qb_space_set_resident_max(qb_space* space, int resident_max_kets);
  * Sec. III B, mapped onto thread blocks): the tile shape of the stage kernel, one of
  * QB_TILE_SHAPES compiled shapes given as (warps per thread block, kets per warp
  * tile, thread blocks per SM the register budget is planned for):
- *   0 (12, 64, 3) the default;  1 (8, 64, 4);  2 (16, 64, 2);  3 (12, 128, 3);
- *   4 (8, 32, 4).
+ *   0 (32, 64, 1) the default;  1 (16, 64, 2);  2 (24, 64, 1);  3 (12, 64, 3);
+ *   4 (32, 128, 1).
  * Every ket sums its terms in the same order under every shape, so results are
  * bit-identical; only the time differs (the Python binding's Space.autotune times
  * them on the caller's workload).  QB_EINVAL outside [0, QB_TILE_SHAPES). */

@@ -204,8 +204,11 @@ static int build_tables(Space& sp) {
   t.o_dsw = (int)off;
   off = align16(off + sizeof(int32_t) * 8 * (size_t)std::max(1, t.n_combo));
   t.blob_bytes = (int)off;
-  // two ranking-table byte offsets share one 32-bit word when the table spans < 64 KB
+  // mod M: the stage kernels hold two ranking-table byte offsets per 32-bit word, so
+  // the table must span at most 64 KB (every space within the other limits does but
+  // M = 9 with 97 <= n_max <= 108, whose sectors exceed 2^31 kets anyway)
   t.sw_ok = (!sp.exact && (int64_t)M * t.rem_w * twoQ * 4 <= 65536) ? 1 : 0;
+  if (!sp.exact && !t.sw_ok) return fail(QB_EUNSUPPORTED, "the ranking table exceeds 64 KB (reduce n_max)");
   // exact momentum: the fill counts and the ranking table grow with (M-1) n_max
   // and stay in global memory for every kernel
   t.sm_from = sp.exact ? t.o_sqrt : 0;
@@ -542,6 +545,7 @@ void qb_space_free(qb_space* space) {
   cudaFree(sp->d_obsf);
   cudaFree(sp->d_wtab);
   cudaFree(sp->d_occ);
+  cudaFree(sp->d_wi);
   if (sp->capture_stream) cudaStreamDestroy(sp->capture_stream);
   if (sp->side_stream) cudaStreamDestroy(sp->side_stream);
   if (sp->ev_fork) cudaEventDestroy(sp->ev_fork);

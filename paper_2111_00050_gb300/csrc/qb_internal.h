@@ -55,7 +55,7 @@ struct Tables {
   int o_dsw;     // int32  [n_combo][8]        byte shifts of the suffix index, two modes per word: word k
                  //   holds 4 shift(2k+1) + 65536 * 4 shift(2k+2) (the ranking table's byte offsets of
                  //   modes 2k+1 and 2k+2 added in one 32-bit add, see the stage kernel)
-  int sw_ok;     // 1: every byte offset into the ranking table fits 16 bits (mod-M momentum only)
+  int sw_ok;     // 1: every byte offset into the ranking table fits 16 bits (required for mod-M momentum)
   const unsigned char* blob;  // device pointer to the image
   // sectors
   int n_sectors;
@@ -77,6 +77,7 @@ struct Tables {
   // [m * occ_bits, (m + 1) * occ_bits), occ_bits the bit length of nmax
   int occ_bits;
   const uint64_t* occ;  // [total]
+  const double* wi;     // [total] 1 / w(n) of every ket (the centred ket weight; ket_weight)
 };
 
 struct Space {
@@ -103,6 +104,7 @@ struct Space {
   float4* d_obsf = nullptr;     // double-float copy of the state being observed (qb_observables)
   double2* d_wtab = nullptr;    // ket-weight factors (Tables::wtab)
   uint64_t* d_occ = nullptr;    // packed occupation vectors (Tables::occ)
+  double* d_wi = nullptr;       // inverse ket weights (Tables::wi)
   int64_t scratch_doubles = 0;
   Tables t{};
   cudaStream_t capture_stream = nullptr;  // private stream on which RK4 chunks are captured into graphs

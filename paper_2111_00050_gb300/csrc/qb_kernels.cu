@@ -181,11 +181,11 @@ __global__ void to_df_kernel(const double2* psi, float4* out, int64_t n) {
 }
 
 // psi (FP64, [B][total]) -> double-float copy in the weighted basis, f = psi / w(n),
-// the ket weights taken from the packed occupation table (coalesced, no unranking)
+// with the inverse weights of the per-ket table (coalesced, no unranking)
 template <int MT>
 __global__ void __launch_bounds__(256) to_dfw_kernel(const Tables t, const double2* psi, float4* out, int B) {
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < t.total; g += (int64_t)gridDim.x * blockDim.x) {
-    const double wi = ket_weight_word<MT>(t, __ldg(t.occ + g)).y;
+    const double wi = __ldg(t.wi + g);
     for (int b = 0; b < B; ++b) {
       const double2 x = psi[(size_t)b * t.total + g];
       out[(size_t)b * t.total + g] = df_pack(df_of(x.x * wi), df_of(x.y * wi));
@@ -193,8 +193,9 @@ __global__ void __launch_bounds__(256) to_dfw_kernel(const Tables t, const doubl
   }
 }
 
-// per-ket diagonal of H, one-body and two-body parts, as double-float pairs
-__global__ void __launch_bounds__(kBlock) diag_kernel(const Tables t, float4* diag, uint64_t* occ) {
+// per-ket diagonal of H, one-body and two-body parts, as double-float pairs; the
+// packed occupations and the inverse ket weight of every ket
+__global__ void __launch_bounds__(kBlock) diag_kernel(const Tables t, float4* diag, uint64_t* occ, double* wi) {
   extern __shared__ __align__(16) unsigned char smem[];
   load_blob(t, smem);
   const View v = make_view(t, smem);
@@ -221,6 +222,7 @@ __global__ void __launch_bounds__(kBlock) diag_kernel(const Tables t, float4* di
     const dfl a = df_of(dw), b = df_of(dl);
     diag[g] = make_float4(a.h, a.l, b.h, b.l);
     occ[g] = word;
+    wi[g] = ket_weight<0>(t, rs.occ + tid, kBlock).y;
   }
 }
 
@@ -589,6 +591,8 @@ int device_setup(Space& s) {
   QB_CUDA(cudaMalloc(&s.d_diag, sizeof(float4) * (size_t)t.total));
   QB_CUDA(cudaMalloc(&s.d_obsf, sizeof(float4) * (size_t)t.total));
   QB_CUDA(cudaMalloc(&s.d_occ, sizeof(uint64_t) * (size_t)t.total));
+  QB_CUDA(cudaMalloc(&s.d_wi, sizeof(double) * (size_t)t.total));
+  t.wi = s.d_wi;
   t.occ_bits = 1;
   while ((1 << t.occ_bits) <= s.nmax) ++t.occ_bits;  // M * occ_bits <= 64 (checked by qb_sector_build)
   t.occ = s.d_occ;
@@ -629,7 +633,7 @@ int device_setup(Space& s) {
     int grid = 0;
     int rc = persistent_grid(diag_kernel, smem, t.total, &grid);
     if (rc) return rc;
-    diag_kernel<<<grid, kBlock, smem>>>(t, s.d_diag, s.d_occ);
+    diag_kernel<<<grid, kBlock, smem>>>(t, s.d_diag, s.d_occ, s.d_wi);
     QB_CUDA(cudaGetLastError());
     QB_CUDA(cudaDeviceSynchronize());
   }

@@ -3,8 +3,9 @@
 //
 // One call runs three kernels over every ket n of the space (amplitude psi_n):
 //  1. obs_prep_kernel: the weighted double-float copy f = psi / w of the state (the
-//     basis of the RK4 stages, w(n) = sqrt(N! / prod n_m!) 2^-e_N) and, in FP64, the
-//     moments that need no other ket: |psi|^2, N |psi|^2 and n_i |psi|^2.
+//     basis of the RK4 stages, w(n) = sqrt(N! / prod n_m!) 2^-e_N) and the moments
+//     that need no other ket: |psi|^2 and N |psi|^2 summed in FP64, n_i |psi|^2 in
+//     double-float over 32 kets at a time, added in FP64.
 //  2. moments_w_kernel: every moment that moves the ket, conj(psi_t) c psi_n with
 //     t = O n for O = a_i, a_i^dag a_j (i < j; the rest by Hermiticity) and a_i a_j
 //     (i <= j), gathered from f.  In the weighted basis
@@ -14,10 +15,11 @@
 //     ladder operators cancel against the ratio of ket weights.
 //  3. the double-float stage kernel in its <x|H|x> mode on f, each row's
 //     Re(conj(f_n) (W^-1 H W f)_n) multiplied by w_n^2 in FP64.
-// Every sum over kets is FP64: per-thread FP64 accumulators in kernels 1 and 3; in
-// kernel 2 the double-float products of one 32-ket tile are summed in double-float
-// and the tile sum is added to the lane's FP64 accumulator.  CTA rows and the sum
-// over CTAs are FP64 in a fixed order (deterministic).
+// Every sum over kets is FP64: per-thread FP64 accumulators in kernels 1 and 3, and
+// where a term is a double-float product (n_i |psi|^2 in kernel 1, the gathered
+// moments in kernel 2) the products of 32 kets are summed in double-float and each
+// such partial is added to an FP64 accumulator.  CTA rows and the sum over CTAs are
+// FP64 in a fixed order (deterministic).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -67,26 +69,46 @@ __global__ void __launch_bounds__(kObsBlock) obs_prep_kernel(const Tables t, con
   const int M = (MT > 0) ? MT : t.M;
   constexpr int kMB = (MT > 0) ? MT : kMaxM;
   const int ob = t.occ_bits;
+  // norm and <N> in FP64 per ket; <n_i> as double-float sums of |psi|^2 n_i over 32
+  // kets at a time, each added to an FP64 sum (the FP64 pipe is the limit here)
   double nrm = 0.0, nN = 0.0, ni[kMB];
+  dfl nt[kMB];
 #pragma unroll
-  for (int m = 0; m < kMB; ++m) ni[m] = 0.0;
+  for (int m = 0; m < kMB; ++m) {
+    ni[m] = 0.0;
+    nt[m] = dfl{0.f, 0.f};
+  }
+  int cnt = 0;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < t.total; g += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t word = __ldg(t.occ + g);
     const double2 x = psi[g];
-    const double wi = ket_weight_word<MT>(t, word).y;
+    const double wi = __ldg(t.wi + g);
     f[g] = df_pack(df_of(x.x * wi), df_of(x.y * wi));
     const double p2 = x.x * x.x + x.y * x.y;
+    const dfl p2f = df_of(p2);
     int N = 0;
 #pragma unroll
     for (int m = 0; m < kMB; ++m)
       if (m < M) {
         const int nm = occ_of(word, m, ob);
         N += nm;
-        ni[m] += p2 * (double)nm;
+        nt[m] = df_add(nt[m], df_mul_f(p2f, (float)nm));
       }
     nrm += p2;
     nN += p2 * (double)N;
+    if (++cnt == 32) {
+      cnt = 0;
+#pragma unroll
+      for (int m = 0; m < kMB; ++m)
+        if (m < M) {
+          ni[m] += df_to(nt[m]);
+          nt[m] = dfl{0.f, 0.f};
+        }
+    }
   }
+#pragma unroll
+  for (int m = 0; m < kMB; ++m)
+    if (m < M) ni[m] += df_to(nt[m]);
   const int w = nprep(M);
   double s = cta_sum(nrm, red);
   if (threadIdx.x == 0) partial[(size_t)blockIdx.x * w] = s;
@@ -168,11 +190,13 @@ __host__ __device__ inline MwEntry mw_entry(int s, int M) {
 }
 
 // shared memory of moments_w_kernel after the staged ranking table (all 16-byte
-// multiples): entry headers [np] int4, shifts [M-1][np] int32, class scales
-// [3][nmax+1] float2, the CTA's FP64 moment row [nmom]
-__host__ __device__ inline size_t mw_smem_after(int M, int np, int nmax, int nmom) {
-  return (size_t)np * 16 + ((((size_t)(M > 1 ? M - 1 : 1) * np * 4) + 15) & ~(size_t)15) +
-         ((3 * (size_t)(nmax + 1) * 8 + 15) & ~(size_t)15) + (((size_t)nmom * 8 + 15) & ~(size_t)15);
+// multiples): entry headers [np] int4, byte shifts [iwords][np] int32, class scales
+// [3][nmax+1] float2, the CTA's FP64 moment row [nmom], and per warp the staged
+// tile of 32 kets (x float4, occupations uint64, (N, K) int32, offsets [iwords] int32)
+__host__ __device__ inline size_t mw_smem_after(int np, int nmax, int nmom, int iwords) {
+  return (size_t)np * 16 + (((size_t)iwords * np * 4 + 15) & ~(size_t)15) +
+         ((3 * (size_t)(nmax + 1) * 8 + 15) & ~(size_t)15) + (((size_t)nmom * 8 + 15) & ~(size_t)15) +
+         (size_t)kMwWarps * 32 * (16 + 8 + 4 + 4 * (size_t)iwords);
 }
 
 constexpr size_t kMwSecSmemMax = 16384;  // sector tables larger than this stay in global memory
@@ -204,31 +228,49 @@ __device__ __forceinline__ int mod_small(int x, int Q) {
 }
 
 // Pass 2: the moments that move the ket, entries [e_begin, e_begin + nent) of this
-// pass (nent <= 32 kMwSpl).  The lanes of a warp take the entries (kMwSpl per lane); the
-// tile are visited in turn, each one's data broadcast from the lane that loaded it:
-// x = psi_n w_n (double-float), (N, K), the packed occupations and the suffix-state
-// indices of the ranking table.  A target's rank is D - 1 - sum_{m=1}^{M-1}
-// E[idx_m + shift_m], the shift of the suffix index at mode m depending only on the
-// entry (tabulated per entry and mode).  partial[block][nmom] (FP64).
+// pass (nent <= 32 kMwSpl).  The lanes of a warp take the entries (kMwSpl per lane);
+// the 32 kets of a tile are staged in the warp's shared memory -- x = psi_n w_n
+// (double-float), the packed occupations, (N, K) and the suffix-state offsets of the
+// ranking table -- and visited in turn, every lane reading ket j's data by broadcast.
+// A target's rank is D - 1 - sum_{m=1}^{M-1} E[idx_m + shift_m], the shift of the
+// suffix index at mode m depending only on the entry; for momentum mod M the byte
+// offsets of two modes share a 32-bit word (as in the stage kernel), for exact
+// momentum each mode has its own.  partial[block][nmom] (FP64).
+template <int MT, bool EXACT>
+struct MwWords {  // 32-bit words of suffix-state offsets per ket
+  static constexpr int n = EXACT ? ((MT > 0) ? MT : kMaxM) : ((MT > 0) ? (MT / 2 > 0 ? MT / 2 : 1) : kMaxM / 2);
+};
+
 template <int MT, bool EXACT, int kMwSpl>
-__global__ void __launch_bounds__(kMwBlock) moments_w_kernel(const Tables t, const double2* psi, const float4* f,
-                                                              double* partial, int nmom, int e_begin, int nent,
-                                                              int sec_smem, int* status) {
+__global__ void __launch_bounds__(kMwBlock, 3) moments_w_kernel(const Tables t, const double2* psi, const float4* f,
+                                                                 double* partial, int nmom, int e_begin, int nent,
+                                                                 int sec_smem, int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int kMB = (MT > 0) ? MT : kMaxM;
+  constexpr int kIW = MwWords<MT, EXACT>::n;
   const int from = EXACT ? t.o_sqrt : t.o_E;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int M = (MT > 0) ? MT : t.M, Q = t.Q, twoQ = 2 * Q, V = t.nmax + 1;
   const int np = (nent + 31) & ~31;
+  const int iw = EXACT ? M : M / 2;  // offset words in use (mode m: word m, or word (m-1)/2 packed)
   unsigned char* cur = smem_raw + ((t.blob_bytes - from + 15) & ~15);
   int4* hdr = reinterpret_cast<int4*>(cur);  // e0 | e1 << 8 | has2 << 16 | cls << 24, c1, dN, dK mod Q
   cur += (size_t)np * 16;
-  int32_t* shf = reinterpret_cast<int32_t*>(cur);  // [M-1][np]
-  cur += (((size_t)(M > 1 ? M - 1 : 1) * np * 4) + 15) & ~(size_t)15;
+  int32_t* shf = reinterpret_cast<int32_t*>(cur);  // [kIW][np] byte shifts (packed in pairs for mod M)
+  cur += ((size_t)kIW * np * 4 + 15) & ~(size_t)15;
   float2* scl = reinterpret_cast<float2*>(cur);  // [3][V] double-float scale of each class at particle number N
   cur += (3 * (size_t)V * 8 + 15) & ~(size_t)15;
   double* row = reinterpret_cast<double*>(cur);  // [nmom]
   cur += ((size_t)nmom * 8 + 15) & ~(size_t)15;
+  // per warp: the tile's kets (x, occupations, (N, K), offset words)
+  float4* kx = reinterpret_cast<float4*>(cur) + (size_t)warp * 32;
+  cur += (size_t)kMwWarps * 32 * 16;
+  uint64_t* kw = reinterpret_cast<uint64_t*>(cur) + (size_t)warp * 32;
+  cur += (size_t)kMwWarps * 32 * 8;
+  int32_t* knk = reinterpret_cast<int32_t*>(cur) + (size_t)warp * 32;
+  cur += (size_t)kMwWarps * 32 * 4;
+  int32_t* kid = reinterpret_cast<int32_t*>(cur) + (size_t)warp * 32 * kIW;  // [kIW][32]
+  cur += (size_t)kMwWarps * 32 * kIW * 4;
   for (int s = tid; s < np; s += kMwBlock) {
     int4 h = make_int4(0, 0, 0, 0);
     int sh[kMaxM];
@@ -244,7 +286,15 @@ __global__ void __launch_bounds__(kMwBlock) moments_w_kernel(const Tables t, con
       h = make_int4(e.e0 | (e.e1 << 8) | (e.has2 << 16) | (e.cls << 24), e.c1, dc, dk);
     }
     hdr[s] = h;
-    for (int m = 1; m < M; ++m) shf[(m - 1) * np + s] = sh[m];
+    for (int k = 0; k < kIW; ++k) {
+      int v = 0;
+      if (EXACT) {
+        if (k >= 1 && k < M) v = 4 * sh[k];
+      } else if (2 * k + 1 < M) {  // signed lo + 65536 hi, so that the low half's borrow is part of it
+        v = 4 * sh[2 * k + 1] + 65536 * 4 * ((2 * k + 2 < M) ? sh[2 * k + 2] : 0);
+      }
+      shf[k * np + s] = v;
+    }
   }
   // class scales: 1, 2^(e_N - e_{N-1}) / sqrt(N), 2^(e_N - e_{N-2}) / sqrt(N (N - 1))
   for (int k = tid; k < 3 * V; k += kMwBlock) {
@@ -268,19 +318,11 @@ __global__ void __launch_bounds__(kMwBlock) moments_w_kernel(const Tables t, con
   }
   for (int k = tid; k < nmom; k += kMwBlock) row[k] = 0.0;
   load_blob_from(t, smem_raw, from);  // ends with a CTA barrier
-  const int32_t* E = EXACT ? reinterpret_cast<const int32_t*>(t.blob + t.o_E)
-                           : reinterpret_cast<const int32_t*>(smem_raw + (t.o_E - from));
+  const char* Eg = reinterpret_cast<const char*>(t.blob + t.o_E);  // exact momentum: the table stays global
   const int ob = t.occ_bits;
   const int64_t total = t.total;
   const int64_t ntiles = (total + 31) / 32;
 
-  // this lane's entries: header, and the target sector for the current (N, K)
-  int4 eh[kMwSpl];
-#pragma unroll
-  for (int r = 0; r < kMwSpl; ++r) {
-    const int s = r * 32 + lane;
-    eh[r] = (s < nent) ? hdr[s] : make_int4(-1, 0, 0, 0);
-  }
   int cur_nk = -1;
   int64_t toff[kMwSpl];
   int tD[kMwSpl];
@@ -295,32 +337,48 @@ __global__ void __launch_bounds__(kMwBlock) moments_w_kernel(const Tables t, con
   }
 
   for (int64_t tile = (int64_t)blockIdx.x * kMwWarps + warp; tile < ntiles; tile += (int64_t)gridDim.x * kMwWarps) {
-    // this lane's ket: x = psi w (double-float), packed occupations, (N, K), suffix indices
-    const int64_t g = tile * 32 + lane;
-    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-    uint64_t word = 0;
-    int nk = 0;
-    int idx[kMB];
+    {  // stage this lane's ket: x = psi w (double-float), packed occupations, (N, K), offsets
+      const int64_t g = tile * 32 + lane;
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      uint64_t word = 0;
+      int nk = 0;
+      uint32_t pk[kIW];
 #pragma unroll
-    for (int m = 0; m < kMB; ++m) idx[m] = 0;
-    if (g < total) {
-      const int sid = find_sector_in(soff, t.n_sectors, g);
-      nk = __ldg(t.sec_N + sid) | (__ldg(t.sec_K + sid) << 16);
-      word = __ldg(t.occ + g);
-      const double2 p = psi[g];
-      const double w = ket_weight_word<MT>(t, word).x;
-      x = df_pack(df_of(p.x * w), df_of(p.y * w));
-      int srem = 0, skr = 0;
+      for (int k = 0; k < kIW; ++k) pk[k] = 0u;
+      if (g < total) {
+        const int sid = find_sector_in(soff, t.n_sectors, g);
+        nk = __ldg(t.sec_N + sid) | (__ldg(t.sec_K + sid) << 16);
+        word = __ldg(t.occ + g);
+        const double2 p = psi[g];
+        const double w = ket_weight_word<MT>(t, word).x;
+        x = df_pack(df_of(p.x * w), df_of(p.y * w));
+        int srem = 0, skr = 0;
 #pragma unroll
-      for (int m = kMB - 1; m >= 1; --m) {
-        if (m < M) {
-          const int nm = occ_of(word, m, ob);
-          srem += nm;
-          skr += m * nm;
-          while (skr >= Q) skr -= Q;
-          idx[m] = (m * t.rem_w + srem + 2) * twoQ + skr;
+        for (int m = kMB - 1; m >= 1; --m) {
+          if (m < M) {
+            const int nm = occ_of(word, m, ob);
+            srem += nm;
+            skr += m * nm;
+            while (skr >= Q) skr -= Q;
+            const uint32_t ix4 = 4u * (uint32_t)((m * t.rem_w + srem + 2) * twoQ + skr);
+#pragma unroll
+            for (int k = 0; k < kIW; ++k) {
+              if (EXACT) {
+                if (k == m) pk[k] = ix4;
+              } else if (k == ((m - 1) >> 1)) {
+                pk[k] |= ix4 << ((m & 1) ? 0 : 16);
+              }
+            }
+          }
         }
       }
+      __syncwarp();  // the previous tile's reads are done
+      kx[lane] = x;
+      kw[lane] = word;
+      knk[lane] = nk;
+#pragma unroll
+      for (int k = 0; k < kIW; ++k) kid[k * 32 + lane] = (int32_t)pk[k];
+      __syncwarp();
     }
     // products of this tile, double-float, (re, im) packed
     dfc tp[kMwSpl];
@@ -328,49 +386,51 @@ __global__ void __launch_bounds__(kMwBlock) moments_w_kernel(const Tables t, con
     for (int r = 0; r < kMwSpl; ++r) tp[r] = dfc{0ull, 0ull};
     const int nt = (int)min((int64_t)32, total - tile * 32);
     for (int j = 0; j < nt; ++j) {
-      const float xrh = __shfl_sync(~0u, x.x, j), xih = __shfl_sync(~0u, x.y, j);
-      const float xrl = __shfl_sync(~0u, x.z, j), xil = __shfl_sync(~0u, x.w, j);
-      const uint64_t wj = ((uint64_t)__shfl_sync(~0u, (uint32_t)(word >> 32), j) << 32) |
-                          (uint64_t)__shfl_sync(~0u, (uint32_t)word, j);
-      const int nkj = __shfl_sync(~0u, nk, j);
-      int id[kMB];
-#pragma unroll
-      for (int m = 1; m < kMB; ++m)
-        if (m < M) id[m] = __shfl_sync(~0u, idx[m], j);
+      const int nkj = knk[j];
       if (nkj != cur_nk) {  // warp-uniform: a new (N, K) sector
         cur_nk = nkj;
         const int N = nkj & 0xffff, K = nkj >> 16;
 #pragma unroll
         for (int r = 0; r < kMwSpl; ++r) {
           tD[r] = -1;
-          if (eh[r].x < 0) continue;
-          const int Nt = N + eh[r].z;
+          const int s = r * 32 + lane;
+          if (s >= nent) continue;
+          const int4 h = hdr[s];
+          const int Nt = N + h.z;
           if (Nt < 0) continue;
-          int Kt = K + eh[r].w;
+          int Kt = K + h.w;
           if (Kt >= Q) Kt -= Q;
           const int sid = sof[Nt * Q + Kt];
           if (sid < 0) continue;  // the target sector is not part of the space
           toff[r] = soff[sid];
           tD[r] = (int)(soff[sid + 1] - toff[r]);
-          const float2 c = scl[((eh[r].x >> 24) & 3) * V + N];
+          const float2 c = scl[((h.x >> 24) & 3) * V + N];
           csc[r] = dfl{c.x, c.y};
         }
       }
-      // x (own ket) as packed pairs: X_r = (xr, xr), X_i = (xi, xi), and -X_r.h, -X_i.h
-      const f2 XRh = f2_pack(xrh, xrh), XRl = f2_pack(xrl, xrl), XIh = f2_pack(xih, xih), XIl = f2_pack(xil, xil);
-      const f2 nXRh = f2_pack(-xrh, -xrh), nXIh = f2_pack(-xih, -xih);
+      const float4 xj = kx[j];
+      const uint64_t wj = kw[j];
 #pragma unroll
       for (int r = 0; r < kMwSpl; ++r) {
         if (tD[r] < 0) continue;
-        const int hx = eh[r].x;
-        int k = occ_of(wj, hx & 0xff, ob);
-        if (hx & 0x10000) k *= occ_of(wj, (hx >> 8) & 0xff, ob) + eh[r].y;
-        if (k <= 0) continue;  // the operator annihilates this ket
         const int s = r * 32 + lane;
+        const int4 h = hdr[s];
+        int k = occ_of(wj, h.x & 0xff, ob);
+        if (h.x & 0x10000) k *= occ_of(wj, (h.x >> 8) & 0xff, ob) + h.y;
+        if (k <= 0) continue;  // the operator annihilates this ket
         int esum = 0;
 #pragma unroll
-        for (int m = 1; m < kMB; ++m)
-          if (m < M) esum += E[id[m] + shf[(m - 1) * np + s]];
+        for (int q = 0; q < kIW; ++q) {
+          if (q >= iw + (EXACT ? 0 : 0)) break;
+          const uint32_t u = (uint32_t)kid[q * 32 + j] + (uint32_t)shf[q * np + s];
+          if (EXACT) {
+            if (q >= 1) esum += *reinterpret_cast<const int32_t*>(Eg + u);
+          } else {
+            esum += e_byte(u & 0xffffu);
+            // the high half of the last word is mode M when M is even: offset 0 holds zero
+            if (MT == 0 || 2 * q + 2 < MT) esum += e_byte(u >> 16);
+          }
+        }
         const int rk = tD[r] - 1 - esum;
         if ((unsigned)rk >= (unsigned)tD[r]) {
           atomicOr(status, 1);
@@ -382,14 +442,14 @@ __global__ void __launch_bounds__(kMwBlock) moments_w_kernel(const Tables t, con
         const f2 Ph = f2_mul(f2_pack(y.x, y.y), one_m), Pl = f2_mul(f2_pack(y.z, y.w), one_m);
         const f2 Sh = f2_pack(y.y, y.x), Sl = f2_pack(y.w, y.z);
         // exact products with their error terms
-        const f2 n1 = f2_mul(nXRh, Ph);
-        f2 e1 = f2_fma(XRh, Ph, n1);
-        e1 = f2_fma(XRh, Pl, e1);
-        e1 = f2_fma(XRl, Ph, e1);
-        const f2 n2 = f2_mul(nXIh, Sh);
-        f2 e2 = f2_fma(XIh, Sh, n2);
-        e2 = f2_fma(XIh, Sl, e2);
-        e2 = f2_fma(XIl, Sh, e2);
+        const f2 n1 = f2_mul(f2_pack(-xj.x, -xj.x), Ph);
+        f2 e1 = f2_fma(f2_pack(xj.x, xj.x), Ph, n1);
+        e1 = f2_fma(f2_pack(xj.x, xj.x), Pl, e1);
+        e1 = f2_fma(f2_pack(xj.z, xj.z), Ph, e1);
+        const f2 n2 = f2_mul(f2_pack(-xj.y, -xj.y), Sh);
+        f2 e2 = f2_fma(f2_pack(xj.y, xj.y), Sh, n2);
+        e2 = f2_fma(f2_pack(xj.y, xj.y), Sl, e2);
+        e2 = f2_fma(f2_pack(xj.w, xj.w), Sh, e2);
         // the negated sum -(p1 + p2) = n1 + n2 by TwoSum, ns + nsl with the error terms
         const f2 ns = f2_add(n1, n2);
         const f2 bb = f2_sub(ns, n1);
@@ -463,7 +523,8 @@ static int launch_mw(const Space& s, const double2* psi, const float4* f, double
   const int from = EXACT ? t.o_sqrt : t.o_E;
   const int np = (nent + 31) & ~31;
   const int sec_smem = mw_sec_bytes(t) <= kMwSecSmemMax ? 1 : 0;
-  const size_t smem = ((size_t)(t.blob_bytes - from + 15) & ~(size_t)15) + mw_smem_after(t.M, np, t.nmax, nmom) +
+  const size_t smem = ((size_t)(t.blob_bytes - from + 15) & ~(size_t)15) +
+                      mw_smem_after(np, t.nmax, nmom, MwWords<MT, EXACT>::n) +
                       (sec_smem ? mw_sec_bytes(t) : 0);
   auto k = moments_w_kernel<MT, EXACT, SPL>;
   int grid = 0;
@@ -528,6 +589,20 @@ int launch_moments(Space& s, const void* d_psi, double* out_host, void* stream) 
   if (rc) return rc;
   reduce_rows_kernel<<<1, 32, 0, st>>>(prep_area(s), gp, npr, prep_final(s));
   QB_CUDA(cudaGetLastError());
+  // pass 3: <psi|H|psi> from the weighted copy, w^2 applied per row in FP64
+  DfArgs a{};
+  a.vin = f;
+  a.diag = s.d_diag;
+  a.scale[0] = make_float2(1.0f, 0.0f);
+  a.row0 = 0;
+  a.row1 = s.t.total;
+  a.status = reinterpret_cast<int*>(s.d_scratch);
+  a.partial = dot_area(s);
+  int g2 = 0;
+  rc = stage_launch(s.t, a, 4, 1, s.t.is_complex != 0, st, &g2, false, 0);
+  if (rc) return rc;
+  reduce_rows_kernel<<<1, 32, 0, st>>>(a.partial, g2, 1, dot_final(s));
+  QB_CUDA(cudaGetLastError());
   // pass 2: the moments that move the ket, in passes of at most 32 kMwSplMax entries;
   // each pass's partial rows are summed into its own copy of the moment row
   const int nent = mw_entries(M), per = 32 * kMwSplMax;
@@ -545,20 +620,6 @@ int launch_moments(Space& s, const void* d_psi, double* out_host, void* stream) 
     QB_CUDA(cudaStreamSynchronize(st));
     for (int k = 0; k < nmom; ++k) mom[k] += fin[k];
   }
-  // pass 3: <psi|H|psi> from the weighted copy, w^2 applied per row in FP64
-  DfArgs a{};
-  a.vin = f;
-  a.diag = s.d_diag;
-  a.scale[0] = make_float2(1.0f, 0.0f);
-  a.row0 = 0;
-  a.row1 = s.t.total;
-  a.status = reinterpret_cast<int*>(s.d_scratch);
-  a.partial = dot_area(s);
-  int g2 = 0;
-  rc = stage_launch(s.t, a, 4, 1, s.t.is_complex != 0, st, &g2, false, 0);
-  if (rc) return rc;
-  reduce_rows_kernel<<<1, 32, 0, st>>>(a.partial, g2, 1, dot_final(s));
-  QB_CUDA(cudaGetLastError());
   std::vector<double> pre((size_t)npr);
   double h = 0.0;
   QB_CUDA(cudaMemcpyAsync(pre.data(), prep_final(s), sizeof(double) * npr, cudaMemcpyDeviceToHost, st));

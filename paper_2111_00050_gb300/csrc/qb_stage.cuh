@@ -24,11 +24,11 @@
 //
 // Ranking (RK): a target's rank is D - 1 - sum_{m=1}^{M-1} E[idx_m + shift_m], the
 // shift of the suffix index at mode m fixed by the term.
-//   RK_PAIR   the ranking table in shared memory spans < 64 KB: the byte offsets of
+//   RK_PAIR   momentum mod M: the ranking table sits in shared memory and spans
+//             < 64 KB (qb_sector_build refuses larger ones), so the byte offsets of
 //             modes 2k+1 and 2k+2 share one 32-bit word per ket, and one 32-bit add
 //             of the term's packed shifts advances both (the shifts are stored as the
 //             signed value lo + 65536 hi, so the low half's borrow is part of it);
-//   RK_BYTE   larger tables: element indices and one biased shift byte per mode;
 //   RK_EXACT  exact momentum: 16-bit shifts, the ranking table in global memory.
 #pragma once
 #include "qb_device.cuh"
@@ -36,10 +36,20 @@
 #ifndef QB_UNROLL_PARTNERS
 #define QB_UNROLL_PARTNERS 1
 #endif
+// 1: a ket's sector from its occupations (N, K) and the (N, K) -> sector table;
+// 0: binary search of the sector offsets
+#ifndef QB_SEC_FROM_WORD
+#define QB_SEC_FROM_WORD 1
+#endif
+// 1: the per-term coupling and shift tables are read through the read-only L1 path
+// from global memory; 0: from the CTA's shared-memory copy
+#ifndef QB_TERM_TABLES_L1
+#define QB_TERM_TABLES_L1 0
+#endif
 
 namespace qb {
 
-enum { RK_BYTE = 0, RK_PAIR = 1, RK_EXACT = 2 };
+enum { RK_PAIR = 1, RK_EXACT = 2 };
 
 // What a stage launch computes besides (or instead of) its output vector:
 //   KIND_STAGE  the RK4 / adjoint stage alone (modes 0 to 3);
@@ -57,26 +67,28 @@ struct TileShape {
 };
 constexpr int kTileShapes = 5;
 __host__ __device__ constexpr TileShape tile_shape(int ts) {
-  return ts == 1   ? TileShape{8, 64, 4}
-         : ts == 2 ? TileShape{16, 64, 2}
-         : ts == 3 ? TileShape{12, 128, 3}
-         : ts == 4 ? TileShape{8, 32, 4}
-                   : TileShape{12, 64, 3};
+  return ts == 1   ? TileShape{16, 64, 2}
+         : ts == 2 ? TileShape{24, 64, 1}
+         : ts == 3 ? TileShape{12, 64, 3}
+         : ts == 4 ? TileShape{32, 128, 1}
+                   : TileShape{32, 64, 1};
 }
-constexpr int kStageWarps = 12;  // shape 0 (the bilinear and batched instantiations)
-constexpr int kStageBlock = 32 * kStageWarps;
+// the shape of the batched sweeps and the bilinear stages (12 warps: room for the
+// registers of their extra accumulators)
+constexpr int kWideShape = 3;
 
 // Shared scratch of the stage kernel, after the table image, per warp (a tile of
 // `rows` kets):
-//   sidx  int32 [M][rows]   suffix-state index of each ket at mode m (RK_PAIR: two
-//                           modes per word, M/2 words)
+//   sidx  int32 [iw][rows]  suffix-state offsets of each ket: RK_PAIR two modes per
+//                           word (iw = M/2 words), RK_EXACT one per mode (iw = M)
 //   socc  uint8 [M][rows]   occupations
 //   sD    int32 [rows]      sector dimension of the ket (-1: no ket)
 //   sOff  int64 [rows]      sector offset of the ket
 //   sperm uint8 [rows]      processing order (kets sorted by work, most first)
 //   hist  int32 [2][n_ann+2] counting-sort buckets and cursors
-__host__ __device__ inline size_t df_warp_scratch_bytes(int M, int n_ann, int rows) {
-  size_t b = (size_t)M * rows * 4 + (((size_t)M * rows + 15) & ~(size_t)15);
+__host__ __device__ inline int sidx_words(int M, bool exact) { return exact ? M : (M / 2 > 0 ? M / 2 : 1); }
+__host__ __device__ inline size_t df_warp_scratch_bytes(int iw, int M, int n_ann, int rows) {
+  size_t b = (size_t)iw * rows * 4 + (((size_t)M * rows + 15) & ~(size_t)15);
   b += (size_t)rows * 4 + (size_t)rows * 8 + rows + 2 * (size_t)(n_ann + 2) * 4;
   return (b + 15) & ~(size_t)15;
 }
@@ -103,7 +115,8 @@ __device__ __forceinline__ int32_t e_byte(uint32_t off) {
 }
 
 // sum_{m=1}^{M-1} E[idx_m + shift_m] of combo j for a ket whose suffix indices are
-// id[] (RK_PAIR: packed words; otherwise per mode)
+// id[] (RK_PAIR: packed byte offsets, two modes per word; RK_EXACT: byte offsets
+// per mode)
 template <int MT, int RK>
 __device__ __forceinline__ int rank_esum(const Tables& t, const int32_t* E, const unsigned char* dtab, int j,
                                          const int* id) {
@@ -111,9 +124,9 @@ __device__ __forceinline__ int rank_esum(const Tables& t, const int32_t* E, cons
   int esum = 0;
   if constexpr (RK == RK_PAIR) {
     const uint4* dw = reinterpret_cast<const uint4*>(dtab) + 2 * (size_t)j;
-    const uint4 d0 = dw[0];
+    const uint4 d0 = QB_TERM_TABLES_L1 ? __ldg(dw) : dw[0];
     uint4 d1 = make_uint4(0u, 0u, 0u, 0u);
-    if (MT == 0 || MT > 9) d1 = dw[1];
+    if (MT == 0 || MT > 9) d1 = QB_TERM_TABLES_L1 ? __ldg(dw + 1) : dw[1];
     constexpr int kW = (MT > 0) ? MT / 2 : 8;
 #pragma unroll
     for (int k = 0; k < kW; ++k) {
@@ -126,7 +139,7 @@ __device__ __forceinline__ int rank_esum(const Tables& t, const int32_t* E, cons
       // the table holds zero (mode 0, fewer than one particle)
       if (MT == 0 || 2 * k + 2 < MT) esum += e_byte(u >> 16);
     }
-  } else if constexpr (RK == RK_EXACT) {  // int16 shifts, two modes per word
+  } else {  // RK_EXACT: int16 shifts, two modes per word
     const uint4 d0 = reinterpret_cast<const uint4*>(dtab)[2 * (size_t)j];
     const uint4 d1 = reinterpret_cast<const uint4*>(dtab)[2 * (size_t)j + 1];
 #pragma unroll
@@ -136,14 +149,6 @@ __device__ __forceinline__ int rank_esum(const Tables& t, const int32_t* E, cons
                           : (m < 10) ? d1.x : (m < 12) ? d1.y : (m < 14) ? d1.z : d1.w;
       esum += *reinterpret_cast<const int32_t*>(reinterpret_cast<const char*>(E) + id[m] +
                                                  ((int)(int16_t)(word >> (16 * (m & 1))) << 2));
-    }
-  } else {  // biased shift bytes, element indices stored minus the bias
-    const uint4 dd = reinterpret_cast<const uint4*>(dtab)[j];
-#pragma unroll
-    for (int m = 1; m < 16; ++m) {
-      if (m >= M) break;
-      const uint32_t word = (m < 4) ? dd.x : (m < 8) ? dd.y : (m < 12) ? dd.z : dd.w;
-      esum += E[id[m] + (int)((word >> (8 * (m & 3))) & 0xffu)];
     }
   }
   return esum;
@@ -185,12 +190,22 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
     const int64_t g = base + row;
     key[u] = 0;
     if (g < row1) {
-      const int sid = find_sector(t, g);
-      const int64_t off = __ldg(t.sec_off + sid);
-      const int D = (int)(__ldg(t.sec_off + sid + 1) - off);
       const uint64_t word = __ldg(t.occ + g);
       const int ob = t.occ_bits;
-      for (int m = 0; m < M; ++m) socc[m * kRows + row] = (uint8_t)occ_of(word, m, ob);
+      int nN = 0, nK = 0;
+      for (int m = 0; m < M; ++m) {
+        const int nm = occ_of(word, m, ob);
+        socc[m * kRows + row] = (uint8_t)nm;
+        nN += nm;
+        nK += m * nm;
+      }
+#if QB_SEC_FROM_WORD
+      const int sid = __ldg(t.sec_of + nN * Qm + nK % Qm);
+#else
+      const int sid = find_sector(t, g);
+#endif
+      const int64_t off = __ldg(t.sec_off + sid);
+      const int D = (int)(__ldg(t.sec_off + sid + 1) - off);
       int srem = 0, skr = 0, esum = 0, np = 0, n2 = 0;
       uint32_t pk[kPW];
 #pragma unroll
@@ -207,7 +222,7 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
           for (int k = 0; k < kPW; ++k)
             if (k == ((m - 1) >> 1)) pk[k] |= (uint32_t)(ix * 4) << ((m & 1) ? 0 : 16);
         } else {
-          sidx[m * kRows + row] = EXACT ? ix * 4 : ix - kDeltaBias;
+          sidx[m * kRows + row] = ix * 4;
         }
       }
       if constexpr (RK == RK_PAIR) {
@@ -310,7 +325,7 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
           const uint32_t rk = (uint32_t)(D - 1 - rank_esum<MT, RK>(t, v.E, dtab, j, id));
           bad |= rk >= (uint32_t)D;
           rkc[c] = (int)min(rk, (uint32_t)(D - 1));
-          const float4 gf = Gf[j];
+          const float4 gf = QB_TERM_TABLES_L1 ? __ldg(Gf + j) : Gf[j];
           crc[c] = df_mul_f(dfl{gf.x, gf.y}, Af);
         }
 #pragma unroll
@@ -329,7 +344,7 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
           const uint32_t rku = (uint32_t)(D - 1 - rank_esum<MT, RK>(t, v.E, dtab, j, id));
           bad |= rku >= (uint32_t)D;
           const int rk = (int)min(rku, (uint32_t)(D - 1));
-          const float4 gf = Gf[j];
+          const float4 gf = QB_TERM_TABLES_L1 ? __ldg(Gf + j) : Gf[j];
           const dfl cr = df_mul_f(dfl{gf.x, gf.y}, Af);
 #pragma unroll
           for (int b = 0; b < B; ++b) {
@@ -443,14 +458,16 @@ __device__ __forceinline__ StageSmem stage_smem(const Tables& t, int M, int warp
   unsigned char* smem = stage_smem_raw - from;
   S.v = view_at(t, smem);
   if (RK == RK_EXACT) S.v.E = reinterpret_cast<const int32_t*>(t.blob + t.o_E);
-  S.Gf = reinterpret_cast<const float4*>(smem + t.o_Gf);
-  S.dtab = (RK == RK_PAIR) ? smem + t.o_dsw : reinterpret_cast<const unsigned char*>(S.v.delta);
+  S.Gf = reinterpret_cast<const float4*>((QB_TERM_TABLES_L1 ? t.blob : smem) + t.o_Gf);
+  S.dtab = (RK == RK_PAIR) ? (QB_TERM_TABLES_L1 ? t.blob : smem) + t.o_dsw
+                           : reinterpret_cast<const unsigned char*>(S.v.delta);
   const int warp = threadIdx.x >> 5;
-  const size_t wbytes = df_warp_scratch_bytes(M, t.n_ann, rows);
+  const int iw = sidx_words(M, RK == RK_EXACT);
+  const size_t wbytes = df_warp_scratch_bytes(iw, M, t.n_ann, rows);
   unsigned char* base = stage_smem_raw + ((t.blob_bytes - from + 15) & ~15);
   unsigned char* sp = base + (size_t)warp * wbytes;
   S.sidx = reinterpret_cast<int32_t*>(sp);
-  S.socc = reinterpret_cast<uint8_t*>(S.sidx + M * rows);
+  S.socc = reinterpret_cast<uint8_t*>(S.sidx + iw * rows);
   S.sD = reinterpret_cast<int32_t*>(S.socc + ((M * rows + 15) & ~15));
   S.sOff = reinterpret_cast<int64_t*>(S.sD + rows);
   S.sperm = reinterpret_cast<uint8_t*>(S.sOff + rows);
@@ -603,14 +620,13 @@ __global__ void __launch_bounds__(kBlock) resident_kernel(const Tables t, const 
 }
 
 // ranking variant of a space
-__host__ __device__ inline int rank_variant(const Tables& t) {
-  return t.exact ? RK_EXACT : (t.sw_ok ? RK_PAIR : RK_BYTE);
-}
+__host__ __device__ inline int rank_variant(const Tables& t) { return t.exact ? RK_EXACT : RK_PAIR; }
 
 // Shared memory of the resident kernel holding `cap` kets per sector.
 inline size_t resident_smem(const Tables& t, int cap) {
   return ((t.blob_bytes - kSmemFrom(t, t.exact != 0) + 15) & ~15) +
-         (size_t)(kBlock / 32) * df_warp_scratch_bytes(t.M, t.n_ann, kResRows) + (size_t)cap * 64;
+         (size_t)(kBlock / 32) * df_warp_scratch_bytes(sidx_words(t.M, t.exact != 0), t.M, t.n_ann, kResRows) +
+         (size_t)cap * 64;
 }
 
 template <int MT, int RK>
@@ -634,11 +650,8 @@ int resident_launch_r(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t
 
 template <int MT>
 int resident_launch_t(const Tables& t, const ResArgs& r, bool cplx, cudaStream_t st) {
-  switch (rank_variant(t)) {
-    case RK_EXACT: return resident_launch_r<MT, RK_EXACT>(t, r, cplx, st);
-    case RK_PAIR: return resident_launch_r<MT, RK_PAIR>(t, r, cplx, st);
-    default: return resident_launch_r<MT, RK_BYTE>(t, r, cplx, st);
-  }
+  if (rank_variant(t) == RK_EXACT) return resident_launch_r<MT, RK_EXACT>(t, r, cplx, st);
+  return resident_launch_r<MT, RK_PAIR>(t, r, cplx, st);
 }
 
 // Launches one stage for mode count MT (0: any M), ranking variant RK and the
@@ -654,7 +667,8 @@ int stage_launch_r(const Tables& t, const DfArgs& a, int mode, int B, bool cplx,
     auto k = stage_df_kernel<MT, BB, CC, LL, RK, TT>;                                                   \
     constexpr TileShape sh = tile_shape(TT);                                                            \
     const size_t smem = ((t.blob_bytes - kSmemFrom(t, RK == RK_EXACT) + 15) & ~15) +                    \
-                        (size_t)sh.warps * df_warp_scratch_bytes(t.M, t.n_ann, sh.rows);               \
+                        (size_t)sh.warps *                                                              \
+                            df_warp_scratch_bytes(sidx_words(t.M, RK == RK_EXACT), t.M, t.n_ann, sh.rows); \
     rc = persistent_grid(k, smem, a.row1 - a.row0, &grid, 32 * sh.warps);                               \
     if (rc) return rc;                                                                                  \
     k<<<grid, 32 * sh.warps, smem, st>>>(t, a, mode);                                                   \
@@ -669,9 +683,9 @@ int stage_launch_r(const Tables& t, const DfArgs& a, int mode, int B, bool cplx,
   } else if (bil) {
     if (B != 1) return fail(QB_EUNSUPPORTED, "bilinear stages run one state at a time");
     if (cplx)
-      QB_STAGE_CASE(1, true, KIND_BIL, 0)
+      QB_STAGE_CASE(1, true, KIND_BIL, kWideShape)
     else
-      QB_STAGE_CASE(1, false, KIND_BIL, 0)
+      QB_STAGE_CASE(1, false, KIND_BIL, kWideShape)
   } else if (cplx) {
     if (B != 1) return fail(QB_EUNSUPPORTED, "batched sweeps need a real coupling");
     QB_STAGE_CASE(1, true, KIND_STAGE, 0)
@@ -690,9 +704,9 @@ int stage_launch_r(const Tables& t, const DfArgs& a, int mode, int B, bool cplx,
             default: QB_STAGE_CASE(1, false, KIND_STAGE, 0) break;
           }
           break;
-        case 2: QB_STAGE_CASE(2, false, KIND_STAGE, 0) break;
-        case 4: QB_STAGE_CASE(4, false, KIND_STAGE, 0) break;
-        case 8: QB_STAGE_CASE(8, false, KIND_STAGE, 0) break;
+        case 2: QB_STAGE_CASE(2, false, KIND_STAGE, kWideShape) break;
+        case 4: QB_STAGE_CASE(4, false, KIND_STAGE, kWideShape) break;
+        case 8: QB_STAGE_CASE(8, false, KIND_STAGE, kWideShape) break;
         default: return fail(QB_EINVAL, "batch must be 1, 2, 4 or 8");
       }
     }
@@ -706,11 +720,8 @@ int stage_launch_r(const Tables& t, const DfArgs& a, int mode, int B, bool cplx,
 template <int MT>
 int stage_launch_t(const Tables& t, const DfArgs& a, int mode, int B, bool cplx, bool bil, int shape, cudaStream_t st,
                    int* grid_out) {
-  switch (rank_variant(t)) {
-    case RK_EXACT: return stage_launch_r<MT, RK_EXACT>(t, a, mode, B, cplx, bil, shape, st, grid_out);
-    case RK_PAIR: return stage_launch_r<MT, RK_PAIR>(t, a, mode, B, cplx, bil, shape, st, grid_out);
-    default: return stage_launch_r<MT, RK_BYTE>(t, a, mode, B, cplx, bil, shape, st, grid_out);
-  }
+  if (rank_variant(t) == RK_EXACT) return stage_launch_r<MT, RK_EXACT>(t, a, mode, B, cplx, bil, shape, st, grid_out);
+  return stage_launch_r<MT, RK_PAIR>(t, a, mode, B, cplx, bil, shape, st, grid_out);
 }
 
 // one explicit specialisation per translation unit (qb_stage_m*.cu)

@@ -401,6 +401,36 @@ def test_resident_small_sectors_bit_identical_to_stage_launches(steps):
         assert rel_err(to_host(a), ref) <= STATE_TOL
 
 
+@pytest.mark.parametrize("M", [5, 7, 9, 4])
+def test_every_tile_shape_is_bit_identical(M):
+    """The compiled tile shapes of the stage kernel (qb_space_set_tile_shape) only
+    change how kets map to warps, not the order of any ket's sums: 40 steps (graph
+    replay included) under every shape equal shape 0 bit for bit; the autotuner keeps
+    one of them and reports its timings."""
+    import paper_2111_00050_gb300 as qb
+
+    nmax = {5: 12, 7: 11, 9: 9, 4: 14}[M]
+    z, w, L = _coherent_case(M, 3.0, nmax, -0.05, 7)
+    qs = qb.Space(M, w, L, 0, nmax)
+    qs.set_resident_max(0)
+    x = qs.empty_state()
+    qs.init_coherent(z, x)
+    ref = None
+    for shape in range(qb._lib.QB_TILE_SHAPES):
+        qs.set_tile_shape(shape)
+        y = x.clone()
+        qs.evolve(y, 2e-3, 40)
+        if ref is None:
+            ref = y
+        else:
+            assert bool((y == ref).all()), shape
+    with pytest.raises(qb.QbError):
+        qs.set_tile_shape(qb._lib.QB_TILE_SHAPES)
+    chosen = qs.autotune(2e-3, x, steps=2)
+    assert qs.tuning["tile_shape"] in range(qb._lib.QB_TILE_SHAPES) and chosen == qs.tuning["resident_max_kets"]
+    assert len(qs.tuning["tile_shape_ms"]) == qb._lib.QB_TILE_SHAPES
+
+
 @pytest.mark.parametrize("order", [2, 3])
 def test_taylor_order_matches_oracle(order):
     """Selectable step order (Sec. III B's second-order Taylor step, and third order) on
