@@ -246,7 +246,9 @@ int qb_evolve_observe(qb_space* space, void* d_psi, double dt, int64_t steps, in
  * status word is cleared at the start of each call.  Calls that overlap on the
  * GPU (several streams or host threads at once) race on it: serialise them.
  * The first call on a device looks up the array's address on that device, so
- * make it before any stream capture, with that device current.  The grid of the
+ * make it before any stream capture, with that device current; the address is
+ * kept for the process, which assumes one CUDA context per device for its life
+ * (after cudaDeviceReset the library must be reloaded).  The grid of the
  * reduction is capped so that (4 + 2M + 4M^2 + 2) * grid + ~10 doubles fit;
  * QB_EUNSUPPORTED if even 32 CTAs would not (not reachable for M <= 16).
  * Same arguments, errors and synchronisation as qb_observables. */

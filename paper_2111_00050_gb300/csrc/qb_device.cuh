@@ -400,11 +400,6 @@ struct DfArgs {
   int* status;
 };
 
-// 1: each kernel's shared-memory carveout is set to what its resident CTAs need
-#ifndef QB_SMEM_CARVEOUT
-#define QB_SMEM_CARVEOUT 0
-#endif
-
 // Resident CTAs per SM of `kernel` with `smem` dynamic shared memory, cached
 // per (kernel, smem) so that launch loops do not repeat the occupancy query.
 template <typename K>
@@ -438,17 +433,6 @@ static int occupancy_cached(K kernel, size_t smem, int* per_sm, int* sms, int bl
                                optin - (int)fa.sharedSizeBytes));
   QB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, block, smem));
   if (per < 1) return fail(QB_EUNSUPPORTED, "kernel does not fit on an SM with this table size");
-#if QB_SMEM_CARVEOUT
-  {
-    // shared memory only as large as `per` resident CTAs need, the rest of the
-    // unified L1 / shared array left to the L1 cache (the gathers' working set)
-    int smsm = 0;
-    QB_CUDA(cudaDeviceGetAttribute(&smsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-    const size_t need = (size_t)per * (smem + fa.sharedSizeBytes + 1024);
-    const int pct = (int)std::min<size_t>(100, (100 * need + smsm - 1) / (size_t)smsm);
-    QB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
-  }
-#endif
   Entry e{fn, smem, dev, per, s};
   cache[used < 64 ? used++ : 63] = e;
   *per_sm = per;

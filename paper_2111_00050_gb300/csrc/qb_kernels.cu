@@ -999,7 +999,9 @@ int launch_moments_fp64(Space& s, const void* d_psi, double* out_host, void* str
 // Calls that overlap on the GPU (several streams or threads at once) race on it.
 // The first call on each device looks up the array's device address
 // (cudaGetSymbolAddress) with that device current; make that first call before
-// any stream capture.
+// any stream capture.  The address is cached per device for the process: one CUDA
+// context per device for the life of the process is assumed (a cudaDeviceReset
+// would reload the module and leave the cached address stale).
 
 constexpr int64_t kNoAllocDoubles = 131072;  // 1 MiB
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];

@@ -622,9 +622,14 @@ __global__ void __launch_bounds__(kBlock) resident_kernel(const Tables t, const 
 // ranking variant of a space
 __host__ __device__ inline int rank_variant(const Tables& t) { return t.exact ? RK_EXACT : RK_PAIR; }
 
+// shared-memory bytes of the staged table image
+inline size_t stage_image_smem(const Tables& t, bool exact) {
+  return (size_t)(t.blob_bytes - kSmemFrom(t, exact) + 15) & ~(size_t)15;
+}
+
 // Shared memory of the resident kernel holding `cap` kets per sector.
 inline size_t resident_smem(const Tables& t, int cap) {
-  return ((t.blob_bytes - kSmemFrom(t, t.exact != 0) + 15) & ~15) +
+  return stage_image_smem(t, t.exact != 0) +
          (size_t)(kBlock / 32) * df_warp_scratch_bytes(sidx_words(t.M, t.exact != 0), t.M, t.n_ann, kResRows) +
          (size_t)cap * 64;
 }
@@ -666,7 +671,7 @@ int stage_launch_r(const Tables& t, const DfArgs& a, int mode, int B, bool cplx,
   {                                                                                                     \
     auto k = stage_df_kernel<MT, BB, CC, LL, RK, TT>;                                                   \
     constexpr TileShape sh = tile_shape(TT);                                                            \
-    const size_t smem = ((t.blob_bytes - kSmemFrom(t, RK == RK_EXACT) + 15) & ~15) +                    \
+    const size_t smem = stage_image_smem(t, RK == RK_EXACT) +                                           \
                         (size_t)sh.warps *                                                              \
                             df_warp_scratch_bytes(sidx_words(t.M, RK == RK_EXACT), t.M, t.n_ann, sh.rows); \
     rc = persistent_grid(k, smem, a.row1 - a.row0, &grid, 32 * sh.warps);                               \
