@@ -197,6 +197,8 @@ int qb_space_set_resident_max(qb_space* space, int resident_max_kets);
  * tile, thread blocks per SM the register budget is planned for):
  *   0 (32, 64, 1) the default;  1 (16, 64, 2);  2 (24, 64, 1);  3 (12, 64, 3);
  *   4 (32, 128, 1).
+ * A shape whose shared memory (the coupling tables plus the warps' tiles) does not
+ * fit a thread block on the device runs as shape 3 (large tables, e.g. M = 16).
  * Every ket sums its terms in the same order under every shape, so results are
  * bit-identical; only the time differs (the Python binding's Space.autotune times
  * them on the caller's workload).  QB_EINVAL outside [0, QB_TILE_SHAPES). */

@@ -627,6 +627,24 @@ inline size_t stage_image_smem(const Tables& t, bool exact) {
   return (size_t)(t.blob_bytes - kSmemFrom(t, exact) + 15) & ~(size_t)15;
 }
 
+// dynamic shared memory of a stage launch at tile shape ts
+inline size_t stage_shape_smem(const Tables& t, bool exact, int ts) {
+  const TileShape sh = tile_shape(ts);
+  return stage_image_smem(t, exact) +
+         (size_t)sh.warps * df_warp_scratch_bytes(sidx_words(t.M, exact), t.M, t.n_ann, sh.rows);
+}
+
+// The tile shape a stage launch runs at: the requested one where its shared memory
+// fits a CTA on the current device (with room for the kernels' static arrays),
+// otherwise the 12-warp shape (large tables, e.g. M = 16).
+inline int fitting_shape(const Tables& t, bool exact, int ts) {
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return kWideShape;
+  return stage_shape_smem(t, exact, ts) + 4096 <= (size_t)optin ? ts : kWideShape;
+}
+
 // Shared memory of the resident kernel holding `cap` kets per sector.
 inline size_t resident_smem(const Tables& t, int cap) {
   return stage_image_smem(t, t.exact != 0) +
@@ -671,20 +689,28 @@ int stage_launch_r(const Tables& t, const DfArgs& a, int mode, int B, bool cplx,
   {                                                                                                     \
     auto k = stage_df_kernel<MT, BB, CC, LL, RK, TT>;                                                   \
     constexpr TileShape sh = tile_shape(TT);                                                            \
-    const size_t smem = stage_image_smem(t, RK == RK_EXACT) +                                           \
-                        (size_t)sh.warps *                                                              \
-                            df_warp_scratch_bytes(sidx_words(t.M, RK == RK_EXACT), t.M, t.n_ann, sh.rows); \
+    const size_t smem = stage_shape_smem(t, RK == RK_EXACT, TT);                                        \
     rc = persistent_grid(k, smem, a.row1 - a.row0, &grid, 32 * sh.warps);                               \
     if (rc) return rc;                                                                                  \
     k<<<grid, 32 * sh.warps, smem, st>>>(t, a, mode);                                                   \
   }
   if (mode < 0 || mode > 4) return fail(QB_EINTERNAL, "bad stage mode");
+  // the launches of a fixed shape 0 drop to the 12-warp shape when shape 0 does not fit
+  const bool wide0 = fitting_shape(t, RK == RK_EXACT, 0) != 0;
+  shape = fitting_shape(t, RK == RK_EXACT, shape);
   if (mode == 4) {  // <x|H|x>
     if (B != 1) return fail(QB_EUNSUPPORTED, "the <x|H|x> reduction runs one state at a time");
-    if (cplx)
-      QB_STAGE_CASE(1, true, KIND_DOT, 0)
-    else
-      QB_STAGE_CASE(1, false, KIND_DOT, 0)
+    if (cplx) {
+      if (wide0)
+        QB_STAGE_CASE(1, true, KIND_DOT, kWideShape)
+      else
+        QB_STAGE_CASE(1, true, KIND_DOT, 0)
+    } else {
+      if (wide0)
+        QB_STAGE_CASE(1, false, KIND_DOT, kWideShape)
+      else
+        QB_STAGE_CASE(1, false, KIND_DOT, 0)
+    }
   } else if (bil) {
     if (B != 1) return fail(QB_EUNSUPPORTED, "bilinear stages run one state at a time");
     if (cplx)
@@ -693,11 +719,17 @@ int stage_launch_r(const Tables& t, const DfArgs& a, int mode, int B, bool cplx,
       QB_STAGE_CASE(1, false, KIND_BIL, kWideShape)
   } else if (cplx) {
     if (B != 1) return fail(QB_EUNSUPPORTED, "batched sweeps need a real coupling");
-    QB_STAGE_CASE(1, true, KIND_STAGE, 0)
+    if (wide0)
+      QB_STAGE_CASE(1, true, KIND_STAGE, kWideShape)
+    else
+      QB_STAGE_CASE(1, true, KIND_STAGE, 0)
   } else {
     if constexpr (RK == RK_EXACT) {
       if (B != 1) return fail(QB_EUNSUPPORTED, "exact momentum: batched sweeps are not built");
-      QB_STAGE_CASE(1, false, KIND_STAGE, 0)
+      if (wide0)
+        QB_STAGE_CASE(1, false, KIND_STAGE, kWideShape)
+      else
+        QB_STAGE_CASE(1, false, KIND_STAGE, 0)
     } else {
       switch (B) {
         case 1:
