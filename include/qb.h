@@ -226,7 +226,8 @@ int qb_evolve_plain(qb_space* space, void* d_psi, double dt, int64_t steps, void
  * <a_i a_j>) as double-float products (about 48 significant bits) of the state and
  * its weighted double-float copy, summed in double-float over 32 kets at a time and
  * added in FP64; <H> from the weighted double-float H psi, each row's contribution
- * formed and summed in FP64.  The space's weighted-copy buffer (16 B per ket) is
+ * formed and summed in FP64, with every off-diagonal term of H taken once together
+ * with its Hermitian reverse (half the terms of an H psi).  The space's weighted-copy buffer (16 B per ket) is
  * overwritten.  Relative errors are of order 1e-14. */
 int qb_observables(qb_space* space, const void* d_psi, qb_obs* out, void* stream);
 

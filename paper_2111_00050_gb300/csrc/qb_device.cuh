@@ -31,6 +31,7 @@ struct View {
   const double* G;
   const int8_t* delta;
   const int32_t* ann;
+  const int32_t* hs;
   const uint8_t* pairidx;
   const double* w;
   const double* gd;
@@ -46,6 +47,7 @@ __device__ __forceinline__ View view_at(const Tables& t, const unsigned char* s)
   v.G = (const double*)(s + t.o_G);
   v.delta = (const int8_t*)(s + t.o_delta);
   v.ann = (const int32_t*)(s + t.o_ann);
+  v.hs = (const int32_t*)(s + t.o_hs);
   v.pairidx = (const uint8_t*)(s + t.o_pairidx);
   v.w = (const double*)(s + t.o_w);
   v.gd = (const double*)(s + t.o_gd);

@@ -175,34 +175,39 @@ static int build_tables(Space& sp) {
   t.n_combo = (int)pq.size();
   t.is_complex = cplx ? 1 : 0;
 
-  // shared-memory image
+  // shared-memory image: the stage kernels' tables first after the ranking table
+  // (ann .. dsw), so that they stage [E, delta) (mod M) or [ann, sqrt) (exact)
   size_t off = 0;
+  t.ncp = (std::max(1, t.n_combo) + 3) & ~3;
+  const int nsw = std::max(1, M / 2);  // shift words of a term (modes 1 .. M-1, two per word)
   t.o_cnt = (int)off;
   off = align16(off + sizeof(uint32_t) * (size_t)(M + 1) * (nmax + 1) * Q);
   t.o_E = (int)off;
   off = align16(off + sizeof(int32_t) * (size_t)M * t.rem_w * twoQ);
+  t.o_ann = (int)off;
+  off = align16(off + sizeof(int32_t) * (size_t)(t.n_ann + 1));
+  t.o_hs = (int)off;
+  off = align16(off + sizeof(int32_t) * (size_t)t.n_ann);
+  t.o_pairidx = (int)off;
+  off = align16(off + 256);
+  t.o_Gf = (int)off;
+  off = align16(off + sizeof(float) * 4 * (size_t)t.ncp);
+  t.o_dsw = (int)off;
+  off = align16(off + sizeof(uint32_t) * (size_t)std::max(2, nsw) * t.ncp);
+  t.o_delta = (int)off;
+  off = align16(off + (size_t)(sp.exact ? 32 : 16) * std::max(1, t.n_combo));
   t.o_sqrt = (int)off;
   off = align16(off + sizeof(double) * (size_t)(nmax + 3));
   t.o_pq = (int)off;
   off = align16(off + sizeof(uint32_t) * (size_t)std::max(1, t.n_combo));
   t.o_G = (int)off;
   off = align16(off + sizeof(double) * 2 * (size_t)std::max(1, t.n_combo));
-  t.o_delta = (int)off;
-  off = align16(off + (size_t)(sp.exact ? 32 : 16) * std::max(1, t.n_combo));
-  t.o_ann = (int)off;
-  off = align16(off + sizeof(int32_t) * (size_t)(t.n_ann + 1));
-  t.o_pairidx = (int)off;
-  off = align16(off + 256);
   t.o_w = (int)off;
   off = align16(off + sizeof(double) * (size_t)M);
   t.o_gd = (int)off;
   off = align16(off + sizeof(double) * (size_t)t.n_ann);
   t.o_sqf = (int)off;
   off = align16(off + sizeof(float) * 2 * (size_t)(nmax + 3));
-  t.o_Gf = (int)off;
-  off = align16(off + sizeof(float) * 4 * (size_t)std::max(1, t.n_combo));
-  t.o_dsw = (int)off;
-  off = align16(off + sizeof(int32_t) * 8 * (size_t)std::max(1, t.n_combo));
   t.blob_bytes = (int)off;
   // mod M: the stage kernels hold two ranking-table byte offsets per 32-bit word, so
   // the table must span at most 64 KB (every space within the other limits does but
@@ -211,7 +216,7 @@ static int build_tables(Space& sp) {
   if (!sp.exact && !t.sw_ok) return fail(QB_EUNSUPPORTED, "the ranking table exceeds 64 KB (reduce n_max)");
   // exact momentum: the fill counts and the ranking table grow with (M-1) n_max
   // and stay in global memory for every kernel
-  t.sm_from = sp.exact ? t.o_sqrt : 0;
+  t.sm_from = sp.exact ? t.o_ann : 0;
   sp.blob.assign(off, 0);
   unsigned char* b = sp.blob.data();
   uint32_t* cnt32 = (uint32_t*)(b + t.o_cnt);
@@ -242,12 +247,24 @@ static int build_tables(Space& sp) {
   {  // packed byte shifts: a signed sum, so that the low half's borrow is part of the value
     int32_t* dw = (int32_t*)(b + t.o_dsw);
     for (int j = 0; j < t.n_combo; ++j)
-      for (int k = 0; k < 8; ++k) {
+      for (int k = 0; k < std::max(2, nsw); ++k) {
         const int lo = delta[j][2 * k + 1], hi = (2 * k + 2 < 16) ? delta[j][2 * k + 2] : 0;
-        dw[(size_t)j * 8 + k] = (int32_t)(4 * lo + 65536 * 4 * hi);
+        const int32_t v = (int32_t)(4 * lo + 65536 * 4 * hi);
+        if (k < 2)
+          dw[2 * (size_t)j + k] = v;  // words 0, 1 side by side
+        else
+          dw[(size_t)k * t.ncp + j] = v;  // word k >= 2: column k - 2 after the ncp pairs
       }
   }
   memcpy(b + t.o_ann, annStart.data(), sizeof(int32_t) * annStart.size());
+  {  // first combo of each pair whose creation pair comes after it (partners ascend)
+    int32_t* hs = (int32_t*)(b + t.o_hs);
+    for (int a = 0; a < t.n_ann; ++a) {
+      int j = annStart[a];
+      while (j < annStart[a + 1] && (int)pairidx[pq[j] & 0xff][(pq[j] >> 8) & 0xff] < a) ++j;
+      hs[a] = j;
+    }
+  }
   memcpy(b + t.o_pairidx, pairidx, 256);
   memcpy(b + t.o_w, sp.w.data(), sizeof(double) * M);
   memcpy(b + t.o_gd, gd.data(), sizeof(double) * gd.size());
@@ -261,8 +278,8 @@ static int build_tables(Space& sp) {
   for (int k = 0; k < nmax + 3; ++k) split(std::sqrt((double)k), sqf + 2 * k);
   float* Gf = (float*)(b + t.o_Gf);
   for (int j = 0; j < t.n_combo; ++j) {
-    split(G[2 * j], Gf + 4 * j);
-    split(G[2 * j + 1], Gf + 4 * j + 2);
+    split(G[2 * j], Gf + 2 * j);
+    split(G[2 * j + 1], Gf + 2 * ((size_t)t.ncp + j));
   }
   return QB_OK;
 }

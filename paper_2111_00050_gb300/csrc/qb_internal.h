@@ -47,14 +47,22 @@ struct Tables {
   int o_delta;   // uint8  [n_combo][16]       kDeltaBias + flat-index shift of the suffix state at mode m
                  //   (exact: int16 [n_combo][16], the shift itself)
   int o_ann;     // int32  [n_ann + 1]         first combo of annihilation pair a
+  int o_hs;      // int32  [n_ann]             first combo of pair a whose creation pair (p, q) has a
+                 //   larger pair index: <x|H|x> takes each term once with its reverse
   int o_pairidx; // uint8  [16][16]            pair index of (r <= s)
   int o_w;       // double [M]                 one-body w_p
   int o_gd;      // double [n_ann]             diagonal two-body coefficient mult_rs^2 L^sym_{rs;rs}
   int o_sqf;     // float2 [nmax+3]            sqrt(k) as a double-float pair (hi, lo)
-  int o_Gf;      // float4 [n_combo]           G as double-float pairs (re.hi, re.lo, im.hi, im.lo)
-  int o_dsw;     // int32  [n_combo][8]        byte shifts of the suffix index, two modes per word: word k
-                 //   holds 4 shift(2k+1) + 65536 * 4 shift(2k+2) (the ranking table's byte offsets of
-                 //   modes 2k+1 and 2k+2 added in one 32-bit add, see the stage kernel)
+  // The stage kernel's per-term tables are column arrays of ncp entries (n_combo
+  // rounded up to a multiple of 4), so that the 32 lanes of a warp, each on its own
+  // term, load 8 or 4 bytes apiece from densely packed rows:
+  int ncp;
+  int o_Gf;      // float2 [2][ncp]            G as double-float pairs: [0][j] (re.hi, re.lo), [1][j] (im.hi, im.lo)
+  int o_dsw;     // uint2 [ncp], then uint32 [nsw - 2][ncp]: byte shifts of the suffix index, two modes
+                 //   per word (nsw = max(1, M / 2) words): word k holds 4 shift(2k+1) + 65536 * 4
+                 //   shift(2k+2) (the ranking table's byte offsets of modes 2k+1 and 2k+2 added in one
+                 //   32-bit add, see the stage kernel); words 0 and 1 side by side, the rest one array
+                 //   per word
   int sw_ok;     // 1: every byte offset into the ranking table fits 16 bits (required for mod-M momentum)
   const unsigned char* blob;  // device pointer to the image
   // sectors

@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kMwBlock, 3) moments_w_kernel(const Tables t, 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int kMB = (MT > 0) ? MT : kMaxM;
   constexpr int kIW = MwWords<MT, EXACT>::n;
-  const int from = EXACT ? t.o_sqrt : t.o_E;
+  const int from = EXACT ? t.o_ann : t.o_E;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int M = (MT > 0) ? MT : t.M, Q = t.Q, twoQ = 2 * Q, V = t.nmax + 1;
   const int np = (nent + 31) & ~31;
@@ -520,7 +520,7 @@ template <int MT, bool EXACT, int SPL>
 static int launch_mw(const Space& s, const double2* psi, const float4* f, double* part, int nmom, int e_begin,
                      int nent, int* grid_out, cudaStream_t st) {
   const Tables& t = s.t;
-  const int from = EXACT ? t.o_sqrt : t.o_E;
+  const int from = EXACT ? t.o_ann : t.o_E;
   const int np = (nent + 31) & ~31;
   const int sec_smem = mw_sec_bytes(t) <= kMwSecSmemMax ? 1 : 0;
   const size_t smem = ((size_t)(t.blob_bytes - from + 15) & ~(size_t)15) +

@@ -41,11 +41,6 @@
 #ifndef QB_SEC_FROM_WORD
 #define QB_SEC_FROM_WORD 1
 #endif
-// 1: the per-term coupling and shift tables are read through the read-only L1 path
-// from global memory; 0: from the CTA's shared-memory copy
-#ifndef QB_TERM_TABLES_L1
-#define QB_TERM_TABLES_L1 0
-#endif
 
 namespace qb {
 
@@ -54,7 +49,9 @@ enum { RK_PAIR = 1, RK_EXACT = 2 };
 // What a stage launch computes besides (or instead of) its output vector:
 //   KIND_STAGE  the RK4 / adjoint stage alone (modes 0 to 3);
 //   KIND_BIL    with the adjoint's bilinears fused (modes 2, 3);
-//   KIND_DOT    <x|H|x> only (mode 4): Re(conj(psi_n) (H psi)_n) summed in FP64.
+//   KIND_DOT    <x|H|x> only (mode 4): Re(conj(psi_n) (H psi)_n) summed in FP64,
+//               with each off-diagonal term and its Hermitian reverse taken once
+//               (the partners of a pair that come after it, counted twice).
 enum { KIND_STAGE = 0, KIND_BIL = 1, KIND_DOT = 2 };
 
 // Tile shapes of the stage kernel: warps per CTA, kets per warp tile and the
@@ -93,9 +90,12 @@ __host__ __device__ inline size_t df_warp_scratch_bytes(int iw, int M, int n_ann
   return (b + 15) & ~(size_t)15;
 }
 
-// first byte of the table image the stage kernels stage in shared memory (the fill
-// counts stay in global memory; exact momentum: the ranking table too)
-__host__ __device__ inline int kSmemFrom(const Tables& t, bool exact = false) { return exact ? t.o_sqrt : t.o_E; }
+// The bytes [kSmemFrom, kSmemEnd) of the table image the stage kernels stage in
+// shared memory: the ranking table (mod M; exact momentum keeps it in global
+// memory), the pair offsets and indices, the couplings and the term shifts (exact
+// momentum: the int16 shift table)
+__host__ __device__ inline int kSmemFrom(const Tables& t, bool exact = false) { return exact ? t.o_ann : t.o_E; }
+__host__ __device__ inline int kSmemEnd(const Tables& t, bool exact = false) { return exact ? t.o_sqrt : t.o_delta; }
 
 // Gathered stage-vector entry: read-only global load, or a generic load when the
 // vector is a shared-memory copy (LOCAL; the non-coherent global path does not
@@ -123,16 +123,14 @@ __device__ __forceinline__ int rank_esum(const Tables& t, const int32_t* E, cons
   const int M = (MT > 0) ? MT : t.M;
   int esum = 0;
   if constexpr (RK == RK_PAIR) {
-    const uint4* dw = reinterpret_cast<const uint4*>(dtab) + 2 * (size_t)j;
-    const uint4 d0 = QB_TERM_TABLES_L1 ? __ldg(dw) : dw[0];
-    uint4 d1 = make_uint4(0u, 0u, 0u, 0u);
-    if (MT == 0 || MT > 9) d1 = QB_TERM_TABLES_L1 ? __ldg(dw + 1) : dw[1];
+    // words 0 and 1 side by side, word k >= 2 in column k of the ncp-row table
+    const uint2 w01 = reinterpret_cast<const uint2*>(dtab)[j];
+    const uint32_t* wk = reinterpret_cast<const uint32_t*>(dtab) + j;
     constexpr int kW = (MT > 0) ? MT / 2 : 8;
 #pragma unroll
     for (int k = 0; k < kW; ++k) {
       if (MT == 0 && 2 * k + 1 >= M) break;
-      const uint32_t dk = (k == 0) ? d0.x : (k == 1) ? d0.y : (k == 2) ? d0.z : (k == 3) ? d0.w
-                        : (k == 4) ? d1.x : (k == 5) ? d1.y : (k == 6) ? d1.z : d1.w;
+      const uint32_t dk = (k == 0) ? w01.x : (k == 1) ? w01.y : wk[(size_t)k * t.ncp];
       const uint32_t u = (uint32_t)id[k] + dk;
       esum += e_byte(u & 0xffffu);
       // the high half of the last word is mode M when M is even: offset 0, where
@@ -166,7 +164,7 @@ __device__ __forceinline__ int rank_esum(const Tables& t, const int32_t* E, cons
 // A gather index outside its sector is clamped into it and flagged in the status
 // word once per ket (bit 0), without a branch per term.
 template <int MT, int B, bool CPLX, int KIND, bool LOCAL, int RK, int kRows>
-__device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const float4* Gf, const unsigned char* dtab,
+__device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const float2* Gf, const unsigned char* dtab,
                                            const DfArgs& a, const int mode, const int64_t base, const int64_t row1,
                                            const int64_t local_off, int32_t* sidx, uint8_t* socc, int32_t* sD,
                                            int64_t* sOff, uint8_t* sperm, int32_t* hist, int32_t* cursor, dfl& bil_l,
@@ -312,8 +310,10 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
       smask &= smask - 1;
       const int ai = v.pairidx[r * 16 + s];
       const float Af = (float)(occ[r * kRows] * (occ[s * kRows] - (r == s ? 1 : 0)));  // exact
-      // (exact momentum: the partner count varies from pair to pair)
-      constexpr int kC = (QB_UNROLL_PARTNERS && !CPLX && !EXACT && MT > 0 && (MT % 2) == 1) ? (MT - 1) / 2 : 0;
+      // (exact momentum: the partner count varies from pair to pair; <x|H|x> takes
+      // only the partners after the pair)
+      constexpr int kC =
+          (QB_UNROLL_PARTNERS && !CPLX && !EXACT && !DOT && MT > 0 && (MT % 2) == 1) ? (MT - 1) / 2 : 0;
       if (kC > 0) {
         // fixed partner count: all ranks first, then all gathers, then the sums
         const int j0 = v.ann[ai];
@@ -325,8 +325,8 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
           const uint32_t rk = (uint32_t)(D - 1 - rank_esum<MT, RK>(t, v.E, dtab, j, id));
           bad |= rk >= (uint32_t)D;
           rkc[c] = (int)min(rk, (uint32_t)(D - 1));
-          const float4 gf = QB_TERM_TABLES_L1 ? __ldg(Gf + j) : Gf[j];
-          crc[c] = df_mul_f(dfl{gf.x, gf.y}, Af);
+          const float2 gr = Gf[j];  // real coupling (hi, lo)
+          crc[c] = df_mul_f(dfl{gr.x, gr.y}, Af);
         }
 #pragma unroll
         for (int b = 0; b < B; ++b) {
@@ -340,12 +340,13 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
         }
       } else {
         const int j1 = v.ann[ai + 1];
-        for (int j = v.ann[ai]; j < j1; ++j) {
+        for (int j = DOT ? v.hs[ai] : v.ann[ai]; j < j1; ++j) {
           const uint32_t rku = (uint32_t)(D - 1 - rank_esum<MT, RK>(t, v.E, dtab, j, id));
           bad |= rku >= (uint32_t)D;
           const int rk = (int)min(rku, (uint32_t)(D - 1));
-          const float4 gf = QB_TERM_TABLES_L1 ? __ldg(Gf + j) : Gf[j];
-          const dfl cr = df_mul_f(dfl{gf.x, gf.y}, Af);
+          const float2 gr = Gf[j];  // coupling (re.hi, re.lo), (im.hi, im.lo)
+          const float2 gi = CPLX ? Gf[t.ncp + j] : make_float2(0.f, 0.f);
+          const dfl cr = df_mul_f(dfl{gr.x, gr.y}, Af);
 #pragma unroll
           for (int b = 0; b < B; ++b) {
             const float4 x = gather<LOCAL>(vsec + (size_t)b * total + rk);
@@ -353,7 +354,7 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
             dfc_fma(acc[b], f2_pack(cr.h, cr.h), f2_pack(-cr.h, -cr.h), f2_pack(cr.l, cr.l), xh, xl);
             if (CPLX) {
               // + (-c_i x_im, c_i x_re): lanes of x swapped, coefficient (-c_i, c_i)
-              const dfl ci = df_mul_f(dfl{gf.z, gf.w}, Af);
+              const dfl ci = df_mul_f(dfl{gi.x, gi.y}, Af);
               dfc_fma(acc[b], f2_pack(-ci.h, ci.h), f2_pack(ci.h, -ci.h), f2_pack(-ci.l, ci.l),
                       f2_pack(x.y, x.x), f2_pack(x.w, x.z));
             }
@@ -375,6 +376,10 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
       dfl acc_r, acc_i;
       f2_unpack(acc[b].h, acc_r.h, acc_i.h);
       f2_unpack(acc[b].l, acc_r.l, acc_i.l);
+      if (DOT) {  // each term stands for itself and its reverse (H Hermitian): twice the real part
+        acc_r = dfl{2.f * acc_r.h, 2.f * acc_r.l};
+        acc_i = dfl{2.f * acc_i.h, 2.f * acc_i.l};
+      }
       const dfl sc{a.scale[b].x, a.scale[b].y};
       const dfl dg = df_add(dfl{dg4.x, dg4.y}, df_mul(sc, dfl{dg4.z, dg4.w}));
       const float4 xo = a.vin[(size_t)b * total + ri];
@@ -437,7 +442,7 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
 // and the per-warp tile scratch; sets up every pointer stage_tile needs.
 struct StageSmem {
   View v;
-  const float4* Gf;
+  const float2* Gf;           // coupling columns (real, imaginary) of ncp double-float pairs
   const unsigned char* dtab;  // shifts of the ranking variant
   int32_t* sidx;
   uint8_t* socc;
@@ -453,18 +458,22 @@ struct StageSmem {
 template <int RK>
 __device__ __forceinline__ StageSmem stage_smem(const Tables& t, int M, int warps, int rows) {
   StageSmem S;
-  const int from = kSmemFrom(t, RK == RK_EXACT);
-  load_blob_from(t, stage_smem_raw, from);
+  const int from = kSmemFrom(t, RK == RK_EXACT), end = kSmemEnd(t, RK == RK_EXACT);
+  {
+    const int4* src = reinterpret_cast<const int4*>(t.blob + from);
+    int4* dst = reinterpret_cast<int4*>(stage_smem_raw);
+    for (int i = threadIdx.x; i < (end - from) / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
+  }
   unsigned char* smem = stage_smem_raw - from;
   S.v = view_at(t, smem);
   if (RK == RK_EXACT) S.v.E = reinterpret_cast<const int32_t*>(t.blob + t.o_E);
-  S.Gf = reinterpret_cast<const float4*>((QB_TERM_TABLES_L1 ? t.blob : smem) + t.o_Gf);
-  S.dtab = (RK == RK_PAIR) ? (QB_TERM_TABLES_L1 ? t.blob : smem) + t.o_dsw
-                           : reinterpret_cast<const unsigned char*>(S.v.delta);
+  S.Gf = reinterpret_cast<const float2*>(smem + t.o_Gf);
+  S.dtab = (RK == RK_PAIR) ? smem + t.o_dsw : reinterpret_cast<const unsigned char*>(S.v.delta);
   const int warp = threadIdx.x >> 5;
   const int iw = sidx_words(M, RK == RK_EXACT);
   const size_t wbytes = df_warp_scratch_bytes(iw, M, t.n_ann, rows);
-  unsigned char* base = stage_smem_raw + ((t.blob_bytes - from + 15) & ~15);
+  unsigned char* base = stage_smem_raw + ((end - from + 15) & ~15);
   unsigned char* sp = base + (size_t)warp * wbytes;
   S.sidx = reinterpret_cast<int32_t*>(sp);
   S.socc = reinterpret_cast<uint8_t*>(S.sidx + iw * rows);
@@ -624,7 +633,7 @@ __host__ __device__ inline int rank_variant(const Tables& t) { return t.exact ? 
 
 // shared-memory bytes of the staged table image
 inline size_t stage_image_smem(const Tables& t, bool exact) {
-  return (size_t)(t.blob_bytes - kSmemFrom(t, exact) + 15) & ~(size_t)15;
+  return (size_t)(kSmemEnd(t, exact) - kSmemFrom(t, exact) + 15) & ~(size_t)15;
 }
 
 // dynamic shared memory of a stage launch at tile shape ts
