@@ -192,11 +192,26 @@ __host__ __device__ inline MwEntry mw_entry(int s, int M) {
 // shared memory of moments_w_kernel after the staged ranking table (all 16-byte
 // multiples): entry headers [np] int4, byte shifts [iwords][np] int32, class scales
 // [3][nmax+1] float2, the CTA's FP64 moment row [nmom], and per warp the staged
-// tile of 32 kets (x float4, occupations uint64, (N, K) int32, offsets [iwords] int32)
-__host__ __device__ inline size_t mw_smem_after(int np, int nmax, int nmom, int iwords) {
+// tile of 32 kets (x float4, occupations as bytes [obwords] uint32, (N, K) int32,
+// offsets [iwords] int32)
+__host__ __device__ inline size_t mw_smem_after(int np, int nmax, int nmom, int iwords, int obwords) {
   return (size_t)np * 16 + (((size_t)iwords * np * 4 + 15) & ~(size_t)15) +
          ((3 * (size_t)(nmax + 1) * 8 + 15) & ~(size_t)15) + (((size_t)nmom * 8 + 15) & ~(size_t)15) +
-         (size_t)kMwWarps * 32 * (16 + 8 + 4 + 4 * (size_t)iwords);
+         (size_t)kMwWarps * 32 * (16 + 4 * (size_t)obwords + 4 + 4 * (size_t)iwords);
+}
+
+// n_m from occupations packed as bytes, four modes a word (M <= 16): one byte
+// permute of the two words that hold mode m
+template <int NW>
+__device__ __forceinline__ int mw_occ(const uint32_t (&w)[NW], int m) {
+  if constexpr (NW <= 2) {
+    return (int)(__byte_perm(w[0], NW > 1 ? w[NW - 1] : 0u, (uint32_t)m) & 0xffu);
+  } else {
+    const bool hi = m >= 8;
+    const uint32_t x = hi ? w[2] : w[0];
+    const uint32_t y = hi ? (NW > 3 ? w[NW - 1] : 0u) : w[1];
+    return (int)(__byte_perm(x, y, (uint32_t)(m & 7)) & 0xffu);
+  }
 }
 
 constexpr size_t kMwSecSmemMax = 16384;  // sector tables larger than this stay in global memory
@@ -240,6 +255,10 @@ template <int MT, bool EXACT>
 struct MwWords {  // 32-bit words of suffix-state offsets per ket
   static constexpr int n = EXACT ? ((MT > 0) ? MT : kMaxM) : ((MT > 0) ? (MT / 2 > 0 ? MT / 2 : 1) : kMaxM / 2);
 };
+template <int MT>
+struct MwOccWords {  // 32-bit words of byte occupations per ket
+  static constexpr int n = (MT > 0) ? (MT + 3) / 4 : kMaxM / 4;
+};
 
 template <int MT, bool EXACT, int kMwSpl>
 __global__ void __launch_bounds__(kMwBlock, 3) moments_w_kernel(const Tables t, const double2* psi, const float4* f,
@@ -248,6 +267,7 @@ __global__ void __launch_bounds__(kMwBlock, 3) moments_w_kernel(const Tables t, 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int kMB = (MT > 0) ? MT : kMaxM;
   constexpr int kIW = MwWords<MT, EXACT>::n;
+  constexpr int kOBW = MwOccWords<MT>::n;
   const int from = EXACT ? t.o_ann : t.o_E;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int M = (MT > 0) ? MT : t.M, Q = t.Q, twoQ = 2 * Q, V = t.nmax + 1;
@@ -265,8 +285,8 @@ __global__ void __launch_bounds__(kMwBlock, 3) moments_w_kernel(const Tables t, 
   // per warp: the tile's kets (x, occupations, (N, K), offset words)
   float4* kx = reinterpret_cast<float4*>(cur) + (size_t)warp * 32;
   cur += (size_t)kMwWarps * 32 * 16;
-  uint64_t* kw = reinterpret_cast<uint64_t*>(cur) + (size_t)warp * 32;
-  cur += (size_t)kMwWarps * 32 * 8;
+  uint32_t* kob = reinterpret_cast<uint32_t*>(cur) + (size_t)warp * 32 * kOBW;  // [kOBW][32]
+  cur += (size_t)kMwWarps * 32 * kOBW * 4;
   int32_t* knk = reinterpret_cast<int32_t*>(cur) + (size_t)warp * 32;
   cur += (size_t)kMwWarps * 32 * 4;
   int32_t* kid = reinterpret_cast<int32_t*>(cur) + (size_t)warp * 32 * kIW;  // [kIW][32]
@@ -322,6 +342,22 @@ __global__ void __launch_bounds__(kMwBlock, 3) moments_w_kernel(const Tables t, 
   const int ob = t.occ_bits;
   const int64_t total = t.total;
   const int64_t ntiles = (total + 31) / 32;
+  const int rem_w = t.rem_w;
+
+  // this lane's entries in registers for the whole sweep: the modes whose
+  // occupations form k (e0 | e1 << 8 | has2 << 16 | (c1 = -1) << 17), and, where
+  // the registers allow, the byte shifts of the target's suffix indices
+  constexpr bool kHoist = kMwSpl * (1 + kIW) <= 10;
+  uint32_t mop[kMwSpl];
+  uint32_t msh[kMwSpl][kHoist ? kIW : 1];
+#pragma unroll
+  for (int r = 0; r < kMwSpl; ++r) {
+    const int s = min(r * 32 + lane, np - 1);
+    const int4 h = hdr[s];
+    mop[r] = (uint32_t)(h.x & 0x1ffff) | (h.y != 0 ? 1u << 17 : 0u);
+#pragma unroll
+    for (int q = 0; q < (kHoist ? kIW : 1); ++q) msh[r][q] = kHoist ? (uint32_t)shf[q * np + s] : 0u;
+  }
 
   int cur_nk = -1;
   int64_t toff[kMwSpl];
@@ -337,10 +373,12 @@ __global__ void __launch_bounds__(kMwBlock, 3) moments_w_kernel(const Tables t, 
   }
 
   for (int64_t tile = (int64_t)blockIdx.x * kMwWarps + warp; tile < ntiles; tile += (int64_t)gridDim.x * kMwWarps) {
-    {  // stage this lane's ket: x = psi w (double-float), packed occupations, (N, K), offsets
+    {  // stage this lane's ket: x = psi w (double-float), occupations as bytes, (N, K), offsets
       const int64_t g = tile * 32 + lane;
       float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-      uint64_t word = 0;
+      uint32_t obw[kOBW];
+#pragma unroll
+      for (int k = 0; k < kOBW; ++k) obw[k] = 0u;
       int nk = 0;
       uint32_t pk[kIW];
 #pragma unroll
@@ -348,19 +386,21 @@ __global__ void __launch_bounds__(kMwBlock, 3) moments_w_kernel(const Tables t, 
       if (g < total) {
         const int sid = find_sector_in(soff, t.n_sectors, g);
         nk = __ldg(t.sec_N + sid) | (__ldg(t.sec_K + sid) << 16);
-        word = __ldg(t.occ + g);
+        const uint64_t word = __ldg(t.occ + g);
         const double2 p = psi[g];
         const double w = ket_weight_word<MT>(t, word).x;
         x = df_pack(df_of(p.x * w), df_of(p.y * w));
         int srem = 0, skr = 0;
 #pragma unroll
-        for (int m = kMB - 1; m >= 1; --m) {
+        for (int m = kMB - 1; m >= 0; --m) {
           if (m < M) {
             const int nm = occ_of(word, m, ob);
+            obw[m >> 2] |= (uint32_t)nm << (8 * (m & 3));
+            if (m == 0) continue;
             srem += nm;
             skr += m * nm;
             while (skr >= Q) skr -= Q;
-            const uint32_t ix4 = 4u * (uint32_t)((m * t.rem_w + srem + 2) * twoQ + skr);
+            const uint32_t ix4 = 4u * (uint32_t)((m * rem_w + srem + 2) * twoQ + skr);
 #pragma unroll
             for (int k = 0; k < kIW; ++k) {
               if (EXACT) {
@@ -374,7 +414,8 @@ __global__ void __launch_bounds__(kMwBlock, 3) moments_w_kernel(const Tables t, 
       }
       __syncwarp();  // the previous tile's reads are done
       kx[lane] = x;
-      kw[lane] = word;
+#pragma unroll
+      for (int k = 0; k < kOBW; ++k) kob[k * 32 + lane] = obw[k];
       knk[lane] = nk;
 #pragma unroll
       for (int k = 0; k < kIW; ++k) kid[k * 32 + lane] = (int32_t)pk[k];
@@ -409,54 +450,70 @@ __global__ void __launch_bounds__(kMwBlock, 3) moments_w_kernel(const Tables t, 
         }
       }
       const float4 xj = kx[j];
-      const uint64_t wj = kw[j];
+      uint32_t obj[kOBW];
+#pragma unroll
+      for (int k = 0; k < kOBW; ++k) obj[k] = kob[k * 32 + j];
+      // the ket's suffix offsets, read once per ket where the registers allow
+      constexpr bool kHoistKet = kMwSpl <= 2;
+      int idj[kHoistKet ? kIW : 1];
+#pragma unroll
+      for (int q = 0; q < (kHoistKet ? kIW : 1); ++q) idj[q] = kHoistKet ? kid[q * 32 + j] : 0;
 #pragma unroll
       for (int r = 0; r < kMwSpl; ++r) {
-        if (tD[r] < 0) continue;
-        const int s = r * 32 + lane;
-        const int4 h = hdr[s];
-        int k = occ_of(wj, h.x & 0xff, ob);
-        if (h.x & 0x10000) k *= occ_of(wj, (h.x >> 8) & 0xff, ob) + h.y;
-        if (k <= 0) continue;  // the operator annihilates this ket
-        int esum = 0;
+        const uint32_t op = mop[r];
+        int k = mw_occ<kOBW>(obj, (int)(op & 0xffu));
+        if (op & 0x10000u) k *= mw_occ<kOBW>(obj, (int)((op >> 8) & 0xffu)) - (int)((op >> 17) & 1u);
+        // k = 0: the operator annihilates this ket; tD < 0: no target sector
+        bool act = k > 0 && tD[r] >= 0;
+        float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (act) {
+          int esum = 0;
 #pragma unroll
-        for (int q = 0; q < kIW; ++q) {
-          if (q >= iw + (EXACT ? 0 : 0)) break;
-          const uint32_t u = (uint32_t)kid[q * 32 + j] + (uint32_t)shf[q * np + s];
-          if (EXACT) {
-            if (q >= 1) esum += *reinterpret_cast<const int32_t*>(Eg + u);
+          for (int q = 0; q < kIW; ++q) {
+            if (q >= iw) break;
+            const uint32_t u = (uint32_t)(kHoistKet ? idj[kHoistKet ? q : 0] : kid[q * 32 + j]) +
+                               (kHoist ? msh[r][kHoist ? q : 0] : (uint32_t)shf[q * np + r * 32 + lane]);
+            if (EXACT) {
+              if (q >= 1) esum += *reinterpret_cast<const int32_t*>(Eg + u);
+            } else {
+              esum += e_byte(u & 0xffffu);
+              // the high half of the last word is mode M when M is even: offset 0 holds zero
+              if (MT == 0 || 2 * q + 2 < MT) esum += e_byte(u >> 16);
+            }
+          }
+          const int rk = tD[r] - 1 - esum;
+          if ((unsigned)rk >= (unsigned)tD[r]) {
+            atomicOr(status, 1);
+            act = false;
           } else {
-            esum += e_byte(u & 0xffffu);
-            // the high half of the last word is mode M when M is even: offset 0 holds zero
-            if (MT == 0 || 2 * q + 2 < MT) esum += e_byte(u >> 16);
+            y = __ldg(f + toff[r] + rk);
           }
         }
-        const int rk = tD[r] - 1 - esum;
-        if ((unsigned)rk >= (unsigned)tD[r]) {
-          atomicOr(status, 1);
-          continue;
-        }
-        const float4 y = __ldg(f + toff[r] + rk);
+        // (three entries a lane: skip instead of adding zeros, which keeps the
+        // registers of the unrolled entries apart)
+        if (kMwSpl >= 3 && !act) continue;
         // conj(y) x = x_r (y_r, -y_i) + x_i (y_i, y_r), lane 0 the real part
+        const f2 xr = f2_pack(xj.x, xj.x), nxr = f2_pack(-xj.x, -xj.x), xrl = f2_pack(xj.z, xj.z);
+        const f2 xi = f2_pack(xj.y, xj.y), nxi = f2_pack(-xj.y, -xj.y), xil = f2_pack(xj.w, xj.w);
         const f2 one_m = f2_pack(1.f, -1.f);
         const f2 Ph = f2_mul(f2_pack(y.x, y.y), one_m), Pl = f2_mul(f2_pack(y.z, y.w), one_m);
         const f2 Sh = f2_pack(y.y, y.x), Sl = f2_pack(y.w, y.z);
         // exact products with their error terms
-        const f2 n1 = f2_mul(f2_pack(-xj.x, -xj.x), Ph);
-        f2 e1 = f2_fma(f2_pack(xj.x, xj.x), Ph, n1);
-        e1 = f2_fma(f2_pack(xj.x, xj.x), Pl, e1);
-        e1 = f2_fma(f2_pack(xj.z, xj.z), Ph, e1);
-        const f2 n2 = f2_mul(f2_pack(-xj.y, -xj.y), Sh);
-        f2 e2 = f2_fma(f2_pack(xj.y, xj.y), Sh, n2);
-        e2 = f2_fma(f2_pack(xj.y, xj.y), Sl, e2);
-        e2 = f2_fma(f2_pack(xj.w, xj.w), Sh, e2);
+        const f2 n1 = f2_mul(nxr, Ph);
+        f2 e1 = f2_fma(xr, Ph, n1);
+        e1 = f2_fma(xr, Pl, e1);
+        e1 = f2_fma(xrl, Ph, e1);
+        const f2 n2 = f2_mul(nxi, Sh);
+        f2 e2 = f2_fma(xi, Sh, n2);
+        e2 = f2_fma(xi, Sl, e2);
+        e2 = f2_fma(xil, Sh, e2);
         // the negated sum -(p1 + p2) = n1 + n2 by TwoSum, ns + nsl with the error terms
         const f2 ns = f2_add(n1, n2);
         const f2 bb = f2_sub(ns, n1);
         const f2 nerr = f2_add(f2_sub(n1, f2_sub(ns, bb)), f2_sub(n2, bb));
         const f2 nsl = f2_sub(f2_sub(nerr, e1), e2);
         // times the coefficient c = k * scale: acc += (-c)(ns + nsl) = c conj(y) x
-        const dfl c = df_mul_f(csc[r], (float)k);
+        const dfl c = df_mul_f(csc[r], act ? (float)k : 0.f);
         const f2 Ch = f2_pack(c.h, c.h), nCh = f2_pack(-c.h, -c.h), nCl = f2_pack(-c.l, -c.l);
         dfc_fma(tp[r], nCh, Ch, nCl, ns, nsl);
       }
@@ -524,7 +581,7 @@ static int launch_mw(const Space& s, const double2* psi, const float4* f, double
   const int np = (nent + 31) & ~31;
   const int sec_smem = mw_sec_bytes(t) <= kMwSecSmemMax ? 1 : 0;
   const size_t smem = ((size_t)(t.blob_bytes - from + 15) & ~(size_t)15) +
-                      mw_smem_after(np, t.nmax, nmom, MwWords<MT, EXACT>::n) +
+                      mw_smem_after(np, t.nmax, nmom, MwWords<MT, EXACT>::n, MwOccWords<MT>::n) +
                       (sec_smem ? mw_sec_bytes(t) : 0);
   auto k = moments_w_kernel<MT, EXACT, SPL>;
   int grid = 0;
