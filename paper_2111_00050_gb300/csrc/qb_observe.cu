@@ -36,6 +36,10 @@ constexpr int kObsBlock = 256;  // threads per CTA of the first pass
 constexpr int kMwWarps = 8;     // warps per CTA of the moments kernel
 constexpr int kMwBlock = 32 * kMwWarps;
 constexpr int kMwSplMax = 3;    // moment entries per lane and pass (<= 96 per pass)
+// resident CTAs per SM the moments kernel's registers are planned for
+#ifndef QB_MW_MIN_BLOCKS
+#define QB_MW_MIN_BLOCKS 3
+#endif
 
 // sums partial[0..n)[0..width) over the first index in a fixed order
 __global__ void reduce_rows_kernel(const double* partial, int n, int width, double* out) {
@@ -261,7 +265,7 @@ struct MwOccWords {  // 32-bit words of byte occupations per ket
 };
 
 template <int MT, bool EXACT, int kMwSpl>
-__global__ void __launch_bounds__(kMwBlock, 3) moments_w_kernel(const Tables t, const double2* psi, const float4* f,
+__global__ void __launch_bounds__(kMwBlock, QB_MW_MIN_BLOCKS) moments_w_kernel(const Tables t, const double2* psi, const float4* f,
                                                                  double* partial, int nmom, int e_begin, int nent,
                                                                  int sec_smem, int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

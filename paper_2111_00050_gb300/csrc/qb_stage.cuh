@@ -338,6 +338,32 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
             dfc_fma(acc[b], f2_pack(crc[c].h, crc[c].h), f2_pack(-crc[c].h, -crc[c].h),
                     f2_pack(crc[c].l, crc[c].l), f2_pack(x[c].x, x[c].y), f2_pack(x[c].z, x[c].w));
         }
+      } else if (DOT && !CPLX && B == 1) {
+        // <x|H|x>: the partners after the pair, two terms in flight
+        const int j1 = v.ann[ai + 1];
+        int j = v.hs[ai];
+        for (; j + 1 < j1; j += 2) {
+          const uint32_t ra = (uint32_t)(D - 1 - rank_esum<MT, RK>(t, v.E, dtab, j, id));
+          const uint32_t rb = (uint32_t)(D - 1 - rank_esum<MT, RK>(t, v.E, dtab, j + 1, id));
+          bad |= (ra >= (uint32_t)D) | (rb >= (uint32_t)D);
+          const float4 xa = gather<LOCAL>(vsec + min(ra, (uint32_t)(D - 1)));
+          const float4 xb = gather<LOCAL>(vsec + min(rb, (uint32_t)(D - 1)));
+          const float2 ga = Gf[j], gb = Gf[j + 1];
+          const dfl ca = df_mul_f(dfl{ga.x, ga.y}, Af), cb = df_mul_f(dfl{gb.x, gb.y}, Af);
+          dfc_fma(acc[0], f2_pack(ca.h, ca.h), f2_pack(-ca.h, -ca.h), f2_pack(ca.l, ca.l), f2_pack(xa.x, xa.y),
+                  f2_pack(xa.z, xa.w));
+          dfc_fma(acc[0], f2_pack(cb.h, cb.h), f2_pack(-cb.h, -cb.h), f2_pack(cb.l, cb.l), f2_pack(xb.x, xb.y),
+                  f2_pack(xb.z, xb.w));
+        }
+        if (j < j1) {
+          const uint32_t ra = (uint32_t)(D - 1 - rank_esum<MT, RK>(t, v.E, dtab, j, id));
+          bad |= ra >= (uint32_t)D;
+          const float4 xa = gather<LOCAL>(vsec + min(ra, (uint32_t)(D - 1)));
+          const float2 ga = Gf[j];
+          const dfl ca = df_mul_f(dfl{ga.x, ga.y}, Af);
+          dfc_fma(acc[0], f2_pack(ca.h, ca.h), f2_pack(-ca.h, -ca.h), f2_pack(ca.l, ca.l), f2_pack(xa.x, xa.y),
+                  f2_pack(xa.z, xa.w));
+        }
       } else {
         const int j1 = v.ann[ai + 1];
         for (int j = DOT ? v.hs[ai] : v.ann[ai]; j < j1; ++j) {
