@@ -36,9 +36,13 @@ import workloads as wl  # noqa: E402
 # roofline uses the DFMA rate measured on the GPU by the run itself (qb_measure_fp64_fma)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per ket of one stage launch (the first stage of a step), from an ncu capture
-# of the current stage kernel (batched coherent at n_tot=12: 757.5 MB read + 232.1 MB
+# of the current stage kernel (batched coherent at n_tot=12: 616.1 MB read + 226.8 MB
 # written over 15,380,937 kets); scaled by kets
-STAGE_DRAM_BYTES_PER_KET = (757.470208e6 + 232.080128e6) / 15380937
+STAGE_DRAM_BYTES_PER_KET = (616.088064e6 + 226.754816e6) / 15380937
+# the same capture's issue-slot and L1 data-pipe utilisation (the kernel's real limits:
+# the FP64 pipe is idle)
+STAGE_NCU_ISSUE_ACTIVE = 0.627
+STAGE_NCU_L1_WAVEFRONTS = 0.922
 
 
 def _peaks():
@@ -549,6 +553,10 @@ def main():
         "hbm_GBps": hbm_bytes / stage_time / 1e9, "hbm_peak_GBps": peaks.get("hbm_gbs"),
         "hbm_frac": (hbm_bytes / stage_time / 1e9) / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
         "fp64_hpsi_ms": fp64_ms,
+        "ncu_issue_active": STAGE_NCU_ISSUE_ACTIVE if args.config == "batched_coherent" else None,
+        "ncu_l1_data_pipe": STAGE_NCU_L1_WAVEFRONTS if args.config == "batched_coherent" else None,
+        "ncu_note": "issue-slot and L1/shared data-pipe wavefront utilisation of the stage kernel from the "
+                    "ncu capture at n_tot=12 (profiles/stage_df_kernel_batched_coherent_ntot12.md)",
     }
 
     # ---- plain path: one launch per sector per stage, same workload and arithmetic
