@@ -219,18 +219,32 @@ def adjoint_extra(qb, torch, steps: int = 20, ckpt_every: int = 10):
     torch.cuda.synchronize()
     fwd = (time.perf_counter() - t0) / steps
     del psi, work
-    nbytes = int(qb.lib().qb_adjoint_workspace_bytes(qs._h, steps, ckpt_every))
-    aw = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-    qs.adjoint(W.z, -0.1, W.dt, 2, ckpt_every=2, loss="Q", work=aw)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    r = qs.adjoint(W.z, -0.1, W.dt, steps, ckpt_every=ckpt_every, loss="Q", work=aw)
-    torch.cuda.synchronize()
-    adj = (time.perf_counter() - t0) / steps
+
+    def timed(ck):
+        nbytes = int(qb.lib().qb_adjoint_workspace_bytes(qs._h, steps, ck))
+        aw = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        qs.adjoint(W.z, -0.1, W.dt, 2, ckpt_every=ck if ck == 0 else 2, loss="Q", work=aw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = qs.adjoint(W.z, -0.1, W.dt, steps, ckpt_every=ck, loss="Q", work=aw)
+        torch.cuda.synchronize()
+        del aw
+        torch.cuda.empty_cache()
+        return (time.perf_counter() - t0) / steps, r, nbytes
+
+    adj, r, nb = timed(ckpt_every)
     out = {"workload": W.name, "kets": qs.total, "sectors": qs.n_sectors, "steps": steps, "ckpt_every": ckpt_every,
            "forward_ms_per_step": fwd * 1e3, "adjoint_ms_per_step": adj * 1e3, "adjoint_over_forward": adj / fwd,
-           "loss_Q": r["loss"], "grad_scale": r["grad_scale"]}
-    del aw, qs
+           "loss_Q": r["loss"], "grad_scale": r["grad_scale"], "workspace_GB": nb / 1e9}
+    # the tape mode (every step's stage vectors kept) where its workspace fits
+    tape_bytes = int(qb.lib().qb_adjoint_workspace_bytes(qs._h, steps, 0))
+    free, _ = torch.cuda.mem_get_info()
+    if tape_bytes < 0.8 * free:
+        adj0, r0, nb0 = timed(0)
+        out["tape"] = {"ckpt_every": 0, "adjoint_ms_per_step": adj0 * 1e3, "adjoint_over_forward": adj0 / fwd,
+                       "workspace_GB": nb0 / 1e9, "grad_scale": r0["grad_scale"],
+                       "grad_scale_rel_diff": abs(r0["grad_scale"] - r["grad_scale"]) / abs(r["grad_scale"])}
+    del qs
     torch.cuda.empty_cache()
     return out
 

@@ -260,8 +260,10 @@ int qb_observables_noalloc(qb_space* space, const void* d_psi, qb_obs* out, void
 /* ---- adjoint gradients ---------------------------------------------------- */
 
 /* Bytes of device workspace qb_adjoint needs (256-byte aligned buffer): the
- * checkpoints, steps / ckpt_every + 1 state vectors, plus 12 state-sized
- * buffers and small reduction areas. */
+ * checkpoints, steps / ckpt_every + 1 state vectors (ckpt_every = 0: one state
+ * vector plus the tape, 4 * steps state-sized double-float vectors), plus 12
+ * state-sized buffers and small reduction areas.  -1 for a NULL space, steps < 1
+ * or ckpt_every < 0. */
 int64_t qb_adjoint_workspace_bytes(const qb_space* space, int64_t steps, int ckpt_every);
 
 /* Loss and gradients of a run from a coherent state.  The run: psi_0 = the
@@ -274,7 +276,11 @@ int64_t qb_adjoint_workspace_bytes(const qb_space* space, int64_t steps, int ckp
  * exact discrete adjoint of the RK4 map, run backwards with the costate;
  * forward states are rebuilt by time reversal, psi_n ~ RK4 step of size -dt from
  * psi_{n+1}, restarted from a stored checkpoint every ckpt_every steps
- * (ckpt_every = 1 stores every state and reverses nothing).  d_work:
+ * (ckpt_every = 1 stores every state and reverses nothing).  ckpt_every = 0 is the
+ * tape mode: the forward pass keeps each step's weighted state and its three
+ * Horner stage vectors (64 bytes per ket and step), so that the backward pass runs
+ * only the four costate stages per step (no reversal, no recomputed stage vectors);
+ * its results equal those of ckpt_every = 1.  d_work:
  * qb_adjoint_workspace_bytes(space, steps, ckpt_every) bytes, 256-byte aligned. */
 int qb_adjoint(qb_space* space, const double* z, double scale, double dt, int64_t steps, int ckpt_every,
                int loss_kind, double* loss, double* grad_scale, double* grad_w, double* grad_z, void* d_work,

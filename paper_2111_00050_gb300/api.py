@@ -237,7 +237,10 @@ class Space:
     def adjoint(self, z, scale: float, dt: float, steps: int, ckpt_every: int = 1, loss: str = "Q",
                 work: Optional[torch.Tensor] = None) -> dict:
         """qb_adjoint: loss (Q or PO = lam_p) at t_f and its gradients with respect to
-        the two-body scale, w_p and the coherent amplitudes z (d/dRe z + i d/dIm z)."""
+        the two-body scale, w_p and the coherent amplitudes z (d/dRe z + i d/dIm z).
+        ckpt_every >= 1 stores every ckpt_every-th state and rebuilds the others by time
+        reversal; 0 keeps every step's stage vectors on the device (64 B per ket and
+        step) and runs only the costate stages backwards."""
         kind = {"Q": _lib.QB_LOSS_Q, "PO": _lib.QB_LOSS_PO}[loss]
         nbytes = int(lib().qb_adjoint_workspace_bytes(self._h, int(steps), int(ckpt_every)))
         if work is None:

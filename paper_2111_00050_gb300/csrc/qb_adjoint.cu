@@ -203,6 +203,7 @@ struct AdjointLayout {
   int64_t n;  // kets
   int64_t nck;
   double2* ckpt;  // [nck][n]
+  float4* tape;   // tape mode: [steps][4][n] weighted state and stage vectors v4, v3, v2 of each step
   double2* psi;
   double2* lam;
   float4 *w1, *w2, *psif;  // contiguous: the RK4 workspace layout of launch_rk4
@@ -215,10 +216,11 @@ struct AdjointLayout {
 
 int64_t round256(int64_t x) { return (x + 255) & ~int64_t(255); }
 
+// ckpt_every = 0: the tape mode (psi_0 plus four double-float vectors per step)
 AdjointLayout adjoint_layout(const Space& s, int64_t steps, int ckpt_every, unsigned char* base) {
   AdjointLayout L{};
   L.n = s.t.total;
-  L.nck = steps / ckpt_every + 1;
+  L.nck = ckpt_every > 0 ? steps / ckpt_every + 1 : 1;
   const int64_t V = round256(L.n * 16);
   int64_t off = 0;
   auto take = [&](int64_t bytes) {
@@ -227,6 +229,7 @@ AdjointLayout adjoint_layout(const Space& s, int64_t steps, int ckpt_every, unsi
     return p;
   };
   L.ckpt = reinterpret_cast<double2*>(take(V * L.nck));
+  L.tape = ckpt_every > 0 ? nullptr : reinterpret_cast<float4*>(take(4 * V * steps));
   L.psi = reinterpret_cast<double2*>(take(V));
   L.lam = reinterpret_cast<double2*>(take(V));
   L.w1 = reinterpret_cast<float4*>(take(3 * L.n * 16));  // w1, w2, psif back to back
@@ -255,7 +258,7 @@ using namespace qb;
 
 extern "C" int64_t qb_adjoint_workspace_bytes(const qb_space* space, int64_t steps, int ckpt_every) {
   const Space* sp = reinterpret_cast<const Space*>(space);
-  if (!sp || steps < 1 || ckpt_every < 1) return -1;
+  if (!sp || steps < 1 || ckpt_every < 0) return -1;
   return adjoint_layout(*sp, steps, ckpt_every, nullptr).bytes;
 }
 
@@ -264,7 +267,7 @@ extern "C" int qb_adjoint(qb_space* space, const double* z, double scale, double
                           void* d_work, void* stream) {
   Space* sp = reinterpret_cast<Space*>(space);
   if (!sp || !z || !loss || !grad_scale || !grad_w || !grad_z) return fail(QB_EINVAL, "NULL argument");
-  if (steps < 1 || ckpt_every < 1) return fail(QB_EINVAL, "need steps >= 1 and ckpt_every >= 1");
+  if (steps < 1 || ckpt_every < 0) return fail(QB_EINVAL, "need steps >= 1 and ckpt_every >= 0");
   if (loss_kind != QB_LOSS_Q && loss_kind != QB_LOSS_PO) return fail(QB_EINVAL, "unknown loss kind");
   if (!std::isfinite(dt) || !std::isfinite(scale)) return fail(QB_EINVAL, "dt and scale must be finite");
   if (!d_work || (reinterpret_cast<uintptr_t>(d_work) & 255)) return fail(QB_EINVAL, "d_work must be 256-byte aligned");
@@ -281,7 +284,38 @@ extern "C" int qb_adjoint(qb_space* space, const double* z, double scale, double
   int rc = qb_init_coherent(space, z, L.psi, nullptr, stream);
   if (rc) return rc;
   QB_CUDA(cudaMemcpyAsync(L.ckpt, L.psi, n * 16, cudaMemcpyDeviceToDevice, st));
-  for (int64_t done = 0; done < steps;) {
+  const float hs = (float)scale;
+  // tape mode: vector k of step j (0: the weighted state psif_j, 1-3: v4, v3, v2)
+  const int64_t vstride = round256(n * 16) / 16;
+  auto slot = [&](int64_t j, int k) { return L.tape + (j * 4 + k) * vstride; };
+  if (ckpt_every == 0) {
+    // each step's Horner stages launched one by one, their vectors kept: v4, v3, v2
+    // from psif_j, then the last stage updates psi and writes psif_{j+1} (the next
+    // step's slot 0; the final one into the RK4 workspace)
+    rc = launch_to_dfw(*sp, L.psi, slot(0, 0), 1, stream);
+    if (rc) return rc;
+    DfArgs f{};
+    f.diag = sp->d_diag;
+    f.scale[0] = make_float2(hs, (float)(scale - (double)hs));
+    f.row0 = 0;
+    f.row1 = n;
+    f.status = status;
+    f.psi = L.psi;
+    for (int64_t j = 0; j < steps; ++j) {
+      f.psif = slot(j, 0);
+      for (int d = 4; d >= 1; --d) {
+        f.vin = (d == 4) ? slot(j, 0) : slot(j, 4 - d);
+        f.out = (d > 1) ? slot(j, 5 - d) : (j + 1 < steps ? slot(j + 1, 0) : L.psif);
+        f.zre = dt / d;
+        const float h = (float)f.zre;
+        f.zf = make_float2(h, (float)(f.zre - (double)h));
+        int grid = 0;
+        rc = stage_launch(sp->t, f, d == 1 ? 1 : 0, 1, cplx, st, &grid, false, sp->tile_shape);
+        if (rc) return rc;
+      }
+    }
+  }
+  for (int64_t done = 0; ckpt_every > 0 && done < steps;) {
     const int64_t seg = std::min<int64_t>(ckpt_every, steps - done);
     rc = launch_rk4(*sp, L.psi, 1, sc, dt, seg, L.w1, stream);
     if (rc) return rc;
@@ -291,11 +325,12 @@ extern "C" int qb_adjoint(qb_space* space, const double* z, double scale, double
   }
 
   // ---- loss and seed lam_N = d loss / d psi^*
-  // the loss in FP64 arithmetic throughout (qb_observables works in double-float)
+  // the loss from the moments of qb_observables (FP64 reductions of double-float
+  // products, about 1e-14 relative)
   qb_obs ob;
   {
     std::vector<double> raw(4 + 2 * M + 4 * (size_t)M * M, 0.0);
-    rc = launch_moments_fp64(*sp, L.psi, raw.data(), stream);
+    rc = launch_moments(*sp, L.psi, raw.data(), stream);
     if (rc) return rc;
     if (!(raw[0] > 0.0)) return fail(QB_EINVAL, "the final state has zero norm");
     derive(M, raw.data(), &ob);
@@ -336,7 +371,6 @@ extern "C" int qb_adjoint(qb_space* space, const double* z, double scale, double
   // ---- backward pass
   DfArgs a{};
   a.diag = sp->d_diag;
-  const float hs = (float)scale;
   a.scale[0] = make_float2(hs, (float)(scale - (double)hs));
   a.row0 = 0;
   a.row1 = n;
@@ -359,7 +393,15 @@ extern "C" int qb_adjoint(qb_space* space, const double* z, double scale, double
   a.partial = L.partial;
   for (int64_t step = steps - 1; step >= 0; --step) {
     // psi_step: a checkpoint, or one RK4 step backwards in time from psi_{step+1}
-    if (step % ckpt_every == 0) {
+    // (tape mode: the stored weighted state and stage vectors of the step)
+    float4* psif = L.psif;
+    float4 *v4 = L.v4, *v3 = L.v3, *v2 = L.v2;
+    if (ckpt_every == 0) {
+      psif = slot(step, 0);
+      v4 = slot(step, 1);
+      v3 = slot(step, 2);
+      v2 = slot(step, 3);
+    } else if (step % ckpt_every == 0) {
       QB_CUDA(cudaMemcpyAsync(L.psi, L.ckpt + (step / ckpt_every) * n, n * 16, cudaMemcpyDeviceToDevice, st));
       rc = launch_to_dfw(*sp, L.psi, L.psif, 1, stream);
       if (rc) return rc;
@@ -367,39 +409,41 @@ extern "C" int qb_adjoint(qb_space* space, const double* z, double scale, double
       rc = launch_rk4(*sp, L.psi, 1, sc, -dt, 1, L.w1, stream);  // leaves the weighted copy in psif
       if (rc) return rc;
     }
-    // forward stage vectors of this step
+    // forward stage vectors of this step (tape mode: stored)
     a.nbasef = 0;
-    a.psif = L.psif;
-    a.vin = L.psif;
-    a.out = L.v4;
-    set_z(dt / 4);
-    if ((rc = run(0, false, 0.0))) return rc;
-    a.vin = L.v4;
-    a.out = L.v3;
-    set_z(dt / 3);
-    if ((rc = run(0, false, 0.0))) return rc;
-    a.vin = L.v3;
-    a.out = L.v2;
-    set_z(dt / 2);
-    if ((rc = run(0, false, 0.0))) return rc;
+    if (ckpt_every > 0) {
+      a.psif = L.psif;
+      a.vin = L.psif;
+      a.out = L.v4;
+      set_z(dt / 4);
+      if ((rc = run(0, false, 0.0))) return rc;
+      a.vin = L.v4;
+      a.out = L.v3;
+      set_z(dt / 3);
+      if ((rc = run(0, false, 0.0))) return rc;
+      a.vin = L.v3;
+      a.out = L.v2;
+      set_z(dt / 2);
+      if ((rc = run(0, false, 0.0))) return rc;
+    }
     // costates: g2 = A^dag lam', g3 = A^dag g2 / 2, g4 = A^dag g3 / 3, lam = lam' + g2 + g3 + g4 + A^dag g4 / 4
     a.vin = L.lamf;
-    a.pair = L.v2;
+    a.pair = v2;
     a.out = L.g2;
     set_z(-dt);
     if ((rc = run(2, true, 1.0))) return rc;
     a.vin = L.g2;
-    a.pair = L.v3;
+    a.pair = v3;
     a.out = L.g3;
     set_z(-dt / 2);
     if ((rc = run(2, true, 0.5))) return rc;
     a.vin = L.g3;
-    a.pair = L.v4;
+    a.pair = v4;
     a.out = L.g4;
     set_z(-dt / 3);
     if ((rc = run(2, true, 1.0 / 3.0))) return rc;
     a.vin = L.g4;
-    a.pair = L.psif;
+    a.pair = psif;
     a.psi = L.lam;
     a.basef[0] = L.g2;
     a.basef[1] = L.g3;
@@ -410,6 +454,8 @@ extern "C" int qb_adjoint(qb_space* space, const double* z, double scale, double
     if ((rc = run(3, true, 0.25))) return rc;
   }
 
+  // tape mode: psi still holds the final state; psi_0 is checkpoint 0
+  if (ckpt_every == 0) QB_CUDA(cudaMemcpyAsync(L.psi, L.ckpt, n * 16, cudaMemcpyDeviceToDevice, st));
   // ---- initial-state gradient: d psi_0 / d z_k through a_k^dag and the renormalisation
   double hacc[kMaxM + 1];
   QB_CUDA(cudaMemcpyAsync(hacc, L.acc, 8 * (M + 1), cudaMemcpyDeviceToHost, st));

@@ -2,8 +2,8 @@
 (every state stored) and against central differences of the GPU loss.
 
 Tolerances: relative 1e-8 against the oracle with every state stored
-(ckpt_every = 1) and 1e-7 with time reversal between checkpoints; 1e-6 against
-central differences with h = 1e-6.
+(ckpt_every = 1) or every stage vector kept (ckpt_every = 0, the tape mode) and 1e-7
+with time reversal between checkpoints; 1e-6 against central differences with h = 1e-6.
 """
 import math
 
@@ -33,7 +33,7 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("kind", ["Q", "PO"])
-@pytest.mark.parametrize("ckpt", [1, 20])
+@pytest.mark.parametrize("ckpt", [0, 1, 20])
 def test_adjoint_matches_oracle_discrete_adjoint(kind, ckpt):
     import paper_2111_00050_gb300 as qb
 
@@ -42,11 +42,33 @@ def test_adjoint_matches_oracle_discrete_adjoint(kind, ckpt):
     got = qs.adjoint(z, scale, dt, steps, ckpt_every=ckpt, loss=kind)
     os_ = orc.Space(M, qs.sectors)
     loss, gs, gw, gz = orc.adjoint_gradient(os_, w, L0, scale, z, dt, steps, kind)
-    tol = 1e-8 if ckpt == 1 else 1e-7
+    tol = 1e-8 if ckpt <= 1 else 1e-7
     assert abs(got["loss"] - loss) <= 1e-10 * max(1, abs(loss))
     assert _rel(got["grad_scale"], gs) <= tol
     assert _rel(got["grad_w"], gw) <= tol
     assert _rel(got["grad_z"], gz) <= tol
+
+
+def test_tape_mode_equals_stored_states():
+    """ckpt_every = 0 keeps the stage vectors of the forward pass instead of
+    recomputing them from stored states: the same arithmetic on the same vectors,
+    so the loss and gradients agree with ckpt_every = 1 to rounding (they are the
+    same double-float stage vectors); the workspace holds 4 vectors per step more."""
+    import paper_2111_00050_gb300 as qb
+
+    M, w, L0, z, scale, dt, steps = _case()
+    qs = qb.Space(M, w, L0, 0, 10)
+    lib = qb.lib()
+    b1 = lib.qb_adjoint_workspace_bytes(qs._h, steps, 1)
+    b0 = lib.qb_adjoint_workspace_bytes(qs._h, steps, 0)
+    assert b0 - b1 >= 4 * steps * 16 * qs.total - steps * 16 * qs.total - 4096
+    assert lib.qb_adjoint_workspace_bytes(qs._h, steps, -1) == -1
+    for kind in ("Q", "PO"):
+        a = qs.adjoint(z, scale, dt, steps, ckpt_every=0, loss=kind)
+        b = qs.adjoint(z, scale, dt, steps, ckpt_every=1, loss=kind)
+        assert abs(a["loss"] - b["loss"]) <= 1e-14 * abs(b["loss"])
+        for k in ("grad_scale", "grad_w", "grad_z"):
+            assert _rel(a[k], b[k]) <= 1e-13
 
 
 def test_adjoint_matches_gpu_central_differences():
