@@ -169,8 +169,6 @@ int launch_scale(const Space& s, void* d_psi, double factor, void* stream);
 int launch_number(const Space& s, int64_t index, void* d_psi, void* stream);
 // raw moments: out[0]=norm, out[1]=<N>, out[2]=<H>, then a[M], Mij[M*M], aa[M*M] complex
 int launch_moments(Space& s, const void* d_psi, double* out_host, void* stream);
-// the same in FP64 arithmetic throughout (slower; for loss values)
-int launch_moments_fp64(Space& s, const void* d_psi, double* out_host, void* stream);
 int64_t workspace_bytes(const Space& s, int batch);
 // psi (FP64 complex) -> double-float copy (float4 per ket)
 int launch_to_df(const void* psi, void* psif, int64_t n, void* stream);

@@ -946,44 +946,6 @@ int launch_number(const Space& s, int64_t index, void* d_psi, void* stream) {
   return QB_OK;
 }
 
-// FP64 moments and <H> (moments_kernel and the FP64 H psi in its dot mode): the
-// exact-arithmetic path, used where a loss value must carry full FP64 accuracy.
-int launch_moments_fp64(Space& s, const void* d_psi, double* out_host, void* stream) {
-  cudaStream_t st = (cudaStream_t)stream;
-  const int nmom = nmoments(s.M);
-  const size_t smem = row_smem(s.t) + ((kRowScratchBytes + 15) & ~15) - kRowScratchBytes +
-                      (size_t)(kBlock / 32) * nmom * sizeof(double) + 16;
-  int grid = 0;
-  int rc = persistent_grid(moments_kernel, smem, s.t.total, &grid);
-  if (rc) return rc;
-  double* part = partial_area(s);
-  moments_kernel<<<grid, kBlock, smem, st>>>(s.t, (const double2*)d_psi, part, nmom,
-                                             reinterpret_cast<int*>(s.d_scratch));
-  QB_CUDA(cudaGetLastError());
-  double* fin = final_area(s);
-  reduce_partials_kernel<<<(nmom + 127) / 128, 128, 0, st>>>(part, grid, nmom, fin);
-  QB_CUDA(cudaGetLastError());
-  QB_CUDA(cudaMemcpyAsync(out_host, fin, sizeof(double) * nmom, cudaMemcpyDeviceToHost, st));
-  // <H> = <psi|H psi>
-  StageArgs a{};
-  a.vin = (const double2*)d_psi;
-  a.scale[0] = 1.0;
-  a.status = reinterpret_cast<int*>(s.d_scratch);
-  double* dpart = dot_area(s);
-  a.partial = dpart;
-  int g2 = 0;
-  rc = launch_stage_c<MODE_DOT, 1>(s, a, st, &g2);
-  if (rc) return rc;
-  double* hfin = dot_final(s);
-  reduce_partials_kernel<<<1, 32, 0, st>>>(dpart, g2, 2, hfin);
-  QB_CUDA(cudaGetLastError());
-  double h2[2];
-  QB_CUDA(cudaMemcpyAsync(h2, hfin, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  QB_CUDA(cudaStreamSynchronize(st));
-  out_host[2] = h2[0];
-  return check_status(s, st);
-}
-
 // ----------------------------------------------- allocation-free observables
 //
 // qb_observables_noalloc serves callers that must not allocate device memory
