@@ -220,13 +220,13 @@ def adjoint_extra(qb, torch, steps: int = 20, ckpt_every: int = 10):
     fwd = (time.perf_counter() - t0) / steps
     del psi, work
 
-    def timed(ck):
+    def timed(ck, cg=False):
         nbytes = int(qb.lib().qb_adjoint_workspace_bytes(qs._h, steps, ck))
         aw = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-        qs.adjoint(W.z, -0.1, W.dt, 2, ckpt_every=ck if ck == 0 else 2, loss="Q", work=aw)
+        qs.adjoint(W.z, -0.1, W.dt, 2, ckpt_every=ck if ck == 0 else 2, loss="Q", work=aw, coupling_grad=cg)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r = qs.adjoint(W.z, -0.1, W.dt, steps, ckpt_every=ck, loss="Q", work=aw)
+        r = qs.adjoint(W.z, -0.1, W.dt, steps, ckpt_every=ck, loss="Q", work=aw, coupling_grad=cg)
         torch.cuda.synchronize()
         del aw
         torch.cuda.empty_cache()
@@ -244,6 +244,12 @@ def adjoint_extra(qb, torch, steps: int = 20, ckpt_every: int = 10):
         out["tape"] = {"ckpt_every": 0, "adjoint_ms_per_step": adj0 * 1e3, "adjoint_over_forward": adj0 / fwd,
                        "workspace_GB": nb0 / 1e9, "grad_scale": r0["grad_scale"],
                        "grad_scale_rel_diff": abs(r0["grad_scale"] - r["grad_scale"]) / abs(r["grad_scale"])}
+        # with the gradient of every coupling entry (qb_adjoint_couplings)
+        adjc, rc, _ = timed(0, True)
+        L0u = wl.contact_coupling(W.M, 1.0)
+        along = float(np.sum((np.conj(rc["grad_L"]) * L0u).real))
+        out["tape_couplings"] = {"adjoint_ms_per_step": adjc * 1e3, "adjoint_over_forward": adjc / fwd,
+                                 "along_L0_minus_grad_scale_rel": abs(along - rc["grad_scale"]) / abs(rc["grad_scale"])}
     del qs
     torch.cuda.empty_cache()
     return out

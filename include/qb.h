@@ -286,6 +286,21 @@ int qb_adjoint(qb_space* space, const double* z, double scale, double dt, int64_
                int loss_kind, double* loss, double* grad_scale, double* grad_w, double* grad_z, void* d_work,
                void* stream);
 
+/* qb_adjoint plus the gradient with respect to every coupling entry (Eq. Ham):
+ * grad_L[2 M^4] (host), for each ordered (p, q, r, s) the pair
+ * (d loss / d Re L_{pq;rs}, d loss / d Im L_{pq;rs}) of the couplings of H, i.e.
+ * scale times the space's L, each entry varied on its own in
+ * H = sum_{pqrs} L_{pq;rs} a_p^dag a_q^dag a_r a_s (orderings of the two pairs are the
+ * same operator and get the same value; zero off momentum conservation).  The
+ * derivative along a coupling direction D is sum Re(conj(g) D) with g = grad_L[2k] +
+ * i grad_L[2k + 1]; along the space's own L it equals grad_scale.  The costate
+ * stages add one sweep each that forms <forward stage vector, O costate> for every
+ * momentum-conserving two-body operator O.  Other arguments, results and errors as
+ * qb_adjoint; QB_EINVAL if grad_L is NULL. */
+int qb_adjoint_couplings(qb_space* space, const double* z, double scale, double dt, int64_t steps, int ckpt_every,
+                 int loss_kind, double* loss, double* grad_scale, double* grad_w, double* grad_z, double* grad_L,
+                 void* d_work, void* stream);
+
 /* ---- breaktime and mean field (Sec. III A, IV C-D) ----------------------- */
 
 /* First sample k with values[k] >= thr; t_br interpolates linearly between

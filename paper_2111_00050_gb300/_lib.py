@@ -83,6 +83,9 @@ SIGNATURES = {
     "qb_adjoint": (ctypes.c_int, [ctypes.c_void_p, _c_double_p, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                   ctypes.c_int, ctypes.c_int, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
                                   ctypes.c_void_p, ctypes.c_void_p]),
+    "qb_adjoint_couplings": (ctypes.c_int, [ctypes.c_void_p, _c_double_p, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                    ctypes.c_int, ctypes.c_int, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
+                                    _c_double_p, ctypes.c_void_p, ctypes.c_void_p]),
     "qb_breaktime": (ctypes.c_int, [_c_double_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, _c_double_p,
                                     _c_int_p]),
     "qb_squeezing": (ctypes.c_int, [_c_double_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, _c_double_p,

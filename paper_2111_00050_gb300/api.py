@@ -235,12 +235,14 @@ class Space:
 
     # ---- adjoint
     def adjoint(self, z, scale: float, dt: float, steps: int, ckpt_every: int = 1, loss: str = "Q",
-                work: Optional[torch.Tensor] = None) -> dict:
+                work: Optional[torch.Tensor] = None, coupling_grad: bool = False) -> dict:
         """qb_adjoint: loss (Q or PO = lam_p) at t_f and its gradients with respect to
         the two-body scale, w_p and the coherent amplitudes z (d/dRe z + i d/dIm z).
         ckpt_every >= 1 stores every ckpt_every-th state and rebuilds the others by time
         reversal; 0 keeps every step's stage vectors on the device (64 B per ket and
-        step) and runs only the costate stages backwards."""
+        step) and runs only the costate stages backwards.  coupling_grad: also
+        grad_L[p, q, r, s] = d loss / d Re L_{pq;rs} + i d loss / d Im L_{pq;rs} for the
+        couplings of H (scale times the space's L), qb_adjoint_couplings."""
         kind = {"Q": _lib.QB_LOSS_Q, "PO": _lib.QB_LOSS_PO}[loss]
         nbytes = int(lib().qb_adjoint_workspace_bytes(self._h, int(steps), int(ckpt_every)))
         if work is None:
@@ -252,10 +254,18 @@ class Space:
         gw = np.zeros(self.M)
         gz = np.zeros(2 * self.M)
         dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        check(lib().qb_adjoint(self._h, dp(zf), float(scale), float(dt), int(steps), int(ckpt_every), kind,
-                               ctypes.byref(out_loss), ctypes.byref(gs), dp(gw), dp(gz), _dptr(work), _stream()))
-        return {"loss": out_loss.value, "grad_scale": gs.value, "grad_w": gw,
-                "grad_z": gz[0::2] + 1j * gz[1::2]}
+        if coupling_grad:
+            gl = np.zeros(2 * self.M ** 4)
+            check(lib().qb_adjoint_couplings(self._h, dp(zf), float(scale), float(dt), int(steps), int(ckpt_every), kind,
+                                     ctypes.byref(out_loss), ctypes.byref(gs), dp(gw), dp(gz), dp(gl), _dptr(work),
+                                     _stream()))
+        else:
+            check(lib().qb_adjoint(self._h, dp(zf), float(scale), float(dt), int(steps), int(ckpt_every), kind,
+                                   ctypes.byref(out_loss), ctypes.byref(gs), dp(gw), dp(gz), _dptr(work), _stream()))
+        out = {"loss": out_loss.value, "grad_scale": gs.value, "grad_w": gw, "grad_z": gz[0::2] + 1j * gz[1::2]}
+        if coupling_grad:
+            out["grad_L"] = (gl[0::2] + 1j * gl[1::2]).reshape(self.M, self.M, self.M, self.M)
+        return out
 
     # ---- observables
     def observables(self, psi: torch.Tensor) -> dict:
@@ -354,38 +364,48 @@ def _cached_space(M: int, w, L0, n_min: int, n_max: int, p_list) -> Space:
 class AdjointLoss(torch.autograd.Function):
     """Loss (Q or lam_p at t_f) of an RK4 run from a coherent state, with gradients
     by qb_adjoint.  Inputs: the two-body scale (0-d float64 tensor), the dispersion
-    w (float64 [M]) and the coherent amplitudes z (complex128 [M]); the space holds
-    the unit coupling L0 and is reused across calls with the same model and range.
-    When no input requires a gradient (or autograd is off) only the forward run and
-    the loss are computed; otherwise qb_adjoint runs once, in forward, and backward
-    returns its gradients.  z.grad follows torch's convention for real losses,
-    d loss / d Re z + i d loss / d Im z."""
+    w (float64 [M]), the coherent amplitudes z (complex128 [M]) and optionally the unit
+    coupling L0 (complex128 [M, M, M, M]; else spec["L0"], constant), H = H_w + scale
+    H_{L0}; the space is reused across calls with the same model and range.  When no
+    input requires a gradient (or autograd is off) only the forward run and the loss
+    are computed; otherwise the adjoint runs once, in forward (qb_adjoint_couplings
+    when L0 requires a gradient), and backward returns its gradients.  Complex inputs
+    follow torch's convention for real losses: d loss / d Re + i d loss / d Im."""
 
     @staticmethod
-    def forward(ctx, scale, w, z, spec):
-        space = _cached_space(spec["M"], w.detach().cpu().numpy(), spec["L0"], spec["n_min"], spec["n_max"],
+    def forward(ctx, scale, w, z, L0, spec):
+        L0n = L0.detach().cpu().numpy() if L0 is not None else spec["L0"]
+        space = _cached_space(spec["M"], w.detach().cpu().numpy(), L0n, spec["n_min"], spec["n_max"],
                               spec.get("p_list"))
         zz = z.detach().cpu().numpy()
         kind = spec.get("loss", "Q")
-        if not any(ctx.needs_input_grad[:3]):
+        want_L = L0 is not None and ctx.needs_input_grad[3]
+        if not any(ctx.needs_input_grad[:4]):
             psi = space.empty_state()
             space.init_coherent(zz, psi)
             space.evolve_batch(psi, [float(scale)], spec["dt"], spec["steps"])
             ob = space.observables(psi)
             ctx.grads = None
             return torch.tensor(ob["Q"] if kind == "Q" else ob["lam_p"], dtype=torch.float64)
-        r = space.adjoint(zz, float(scale), spec["dt"], spec["steps"], spec.get("ckpt_every", 1), kind)
+        r = space.adjoint(zz, float(scale), spec["dt"], spec["steps"], spec.get("ckpt_every", 1), kind,
+                          coupling_grad=want_L)
+        # d loss / d L0 = scale times the gradient with respect to H's couplings
+        gL = torch.from_numpy(float(scale) * r["grad_L"]) if want_L else None
         ctx.grads = (torch.tensor(r["grad_scale"], dtype=torch.float64),
                      torch.from_numpy(np.asarray(r["grad_w"], dtype=np.float64)),
-                     torch.from_numpy(np.asarray(r["grad_z"], dtype=np.complex128)))
+                     torch.from_numpy(np.asarray(r["grad_z"], dtype=np.complex128)), gL)
         return torch.tensor(r["loss"], dtype=torch.float64)
 
     @staticmethod
     def backward(ctx, g):
-        gs, gw, gz = ctx.grads
-        return g * gs, g * gw, g * gz, None
+        gs, gw, gz, gL = ctx.grads
+        return g * gs, g * gw, g * gz, (g * gL if gL is not None else None), None
 
 
-def adjoint_loss(scale, w, z, **spec):
-    """Differentiable loss of a coherent-state run: see AdjointLoss."""
-    return AdjointLoss.apply(scale, w, z, spec)
+def adjoint_loss(scale, w, z, L0=None, **spec):
+    """Differentiable loss of a coherent-state run: see AdjointLoss.  L0 may be a
+    complex128 tensor (an input with a gradient) or an array (a constant)."""
+    if L0 is not None and not torch.is_tensor(L0):
+        spec["L0"] = L0
+        L0 = None
+    return AdjointLoss.apply(scale, w, z, L0, spec)

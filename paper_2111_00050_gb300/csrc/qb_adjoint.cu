@@ -211,8 +211,23 @@ struct AdjointLayout {
   double* partial;  // [max_grid][M + 1] or [max_grid][2 (M + 1)]
   double* acc;      // [M + 1]
   double* fin;      // [2 (M + 1)]
+  int n_tb;         // two-body operators of the coupling gradient
+  int* tb;          // [n_tb] a1 | a2 << 8 | c1 << 16 | c2 << 24
+  double* tbacc;    // [2 n_tb] weighted sums of <forward stage vector, O costate>
   int64_t bytes;
 };
+
+// The two-body operators a_a1^dag a_a2^dag a_c1 a_c2 (a1 <= a2, c1 <= c2) that conserve
+// momentum (mod Q, the tables' modulus), diagonal ones (a = c) included.
+std::vector<int> two_body_ops(int M, int Q) {
+  std::vector<int> ops;
+  for (int a1 = 0; a1 < M; ++a1)
+    for (int a2 = a1; a2 < M; ++a2)
+      for (int c1 = 0; c1 < M; ++c1)
+        for (int c2 = c1; c2 < M; ++c2)
+          if ((a1 + a2) % Q == (c1 + c2) % Q) ops.push_back(a1 | (a2 << 8) | (c1 << 16) | (c2 << 24));
+  return ops;
+}
 
 int64_t round256(int64_t x) { return (x + 255) & ~int64_t(255); }
 
@@ -246,6 +261,9 @@ AdjointLayout adjoint_layout(const Space& s, int64_t steps, int ckpt_every, unsi
   L.partial = reinterpret_cast<double*>(take(8 * max_grid * 2 * (kMaxM + 1)));
   L.acc = reinterpret_cast<double*>(take(8 * (kMaxM + 1)));
   L.fin = reinterpret_cast<double*>(take(8 * 2 * (kMaxM + 1)));
+  L.n_tb = (int)two_body_ops(s.M, s.t.Q).size();
+  L.tb = reinterpret_cast<int*>(take(4 * (int64_t)L.n_tb));
+  L.tbacc = reinterpret_cast<double*>(take(16 * (int64_t)L.n_tb));
   L.bytes = off;
   return L;
 }
@@ -262,9 +280,9 @@ extern "C" int64_t qb_adjoint_workspace_bytes(const qb_space* space, int64_t ste
   return adjoint_layout(*sp, steps, ckpt_every, nullptr).bytes;
 }
 
-extern "C" int qb_adjoint(qb_space* space, const double* z, double scale, double dt, int64_t steps, int ckpt_every,
-                          int loss_kind, double* loss, double* grad_scale, double* grad_w, double* grad_z,
-                          void* d_work, void* stream) {
+static int adjoint_impl(qb_space* space, const double* z, double scale, double dt, int64_t steps, int ckpt_every,
+                        int loss_kind, double* loss, double* grad_scale, double* grad_w, double* grad_z,
+                        double* grad_L, void* d_work, void* stream) {
   Space* sp = reinterpret_cast<Space*>(space);
   if (!sp || !z || !loss || !grad_scale || !grad_w || !grad_z) return fail(QB_EINVAL, "NULL argument");
   if (steps < 1 || ckpt_every < 0) return fail(QB_EINVAL, "need steps >= 1 and ckpt_every >= 0");
@@ -367,6 +385,11 @@ extern "C" int qb_adjoint(qb_space* space, const double* z, double scale, double
     QB_CUDA(cudaGetLastError());
   }
   QB_CUDA(cudaMemsetAsync(L.acc, 0, 8 * (kMaxM + 1), st));
+  const std::vector<int> ops = two_body_ops(M, sp->t.Q);
+  if (grad_L) {
+    QB_CUDA(cudaMemcpy(L.tb, ops.data(), 4 * ops.size(), cudaMemcpyHostToDevice));
+    QB_CUDA(cudaMemsetAsync(L.tbacc, 0, 16 * ops.size(), st));
+  }
 
   // ---- backward pass
   DfArgs a{};
@@ -387,6 +410,11 @@ extern "C" int qb_adjoint(qb_space* space, const double* z, double scale, double
     if (bil) {
       accumulate_kernel<<<1, 32, 0, st>>>(L.partial, grid, M + 1, weight, L.acc);
       QB_CUDA(cudaGetLastError());
+      // coupling gradient: <forward stage vector, O costate> for every two-body O
+      if (grad_L) {
+        r = launch_tb_bilinear(*sp, a.pair, a.vin, L.tb, L.n_tb, weight, L.tbacc, stream);
+        if (r) return r;
+      }
     }
     return QB_OK;
   };
@@ -487,6 +515,33 @@ extern "C" int qb_adjoint(qb_space* space, const double* z, double scale, double
   }
   // each bilinear stage adds 2 dt c Im <ybar, dH x>: Im <x, H_L p> = -(stored H_L sum)
   *grad_scale = -2.0 * dt * hacc[0];
+  if (grad_L) {
+    // d loss / d L_{pq;rs} for H = sum L_{pq;rs} a_p^dag a_q^dag a_r a_s: the operator of
+    // the entry, O_{A;C}, against the stored sums of its reverse O_{C;A} (the sweep
+    // pairs the forward vector as bra with the costate as ket):
+    // d/dRe L = -2 dt Im B_{C;A}, d/dIm L = 2 dt Re B_{C;A}; every ordering of the
+    // two pairs is the same operator, so it gets the same value
+    std::vector<double> B(2 * ops.size());
+    QB_CUDA(cudaMemcpyAsync(B.data(), L.tbacc, 16 * ops.size(), cudaMemcpyDeviceToHost, st));
+    QB_CUDA(cudaStreamSynchronize(st));
+    const size_t M4 = (size_t)M * M * M * M;
+    std::fill(grad_L, grad_L + 2 * M4, 0.0);
+    auto at = [&](int p, int q, int r2, int s2) { return (((size_t)p * M + q) * M + r2) * M + s2; };
+    for (size_t e = 0; e < ops.size(); ++e) {
+      const int a1 = ops[e] & 0xff, a2 = (ops[e] >> 8) & 0xff, c1 = (ops[e] >> 16) & 0xff, c2 = (ops[e] >> 24) & 0xff;
+      const int rev = c1 | (c2 << 8) | (a1 << 16) | (a2 << 24);
+      const size_t er = (size_t)(std::find(ops.begin(), ops.end(), rev) - ops.begin());
+      if (er >= ops.size()) return fail(QB_EINTERNAL, "two-body operator without its reverse");
+      const double gre = -2.0 * dt * B[2 * er + 1], gim = 2.0 * dt * B[2 * er];
+      const int P[2][2] = {{a1, a2}, {a2, a1}}, R[2][2] = {{c1, c2}, {c2, c1}};
+      for (int u = 0; u < 2; ++u)
+        for (int v = 0; v < 2; ++v) {
+          const size_t ix = at(P[u][0], P[u][1], R[v][0], R[v][1]);
+          grad_L[2 * ix] = gre;
+          grad_L[2 * ix + 1] = gim;
+        }
+    }
+  }
   for (int q = 0; q < M; ++q) grad_w[q] = 2.0 * dt * hacc[q + 1];
   const double cre = lamps[0];  // Re <lam_0, psi_0>
   for (int k = 0; k < M; ++k) {
@@ -496,4 +551,19 @@ extern "C" int qb_adjoint(qb_space* space, const double* z, double scale, double
     grad_z[2 * k + 1] = -2.0 * Gi + 2.0 * cre * Hi;
   }
   return QB_OK;
+}
+
+extern "C" int qb_adjoint(qb_space* space, const double* z, double scale, double dt, int64_t steps, int ckpt_every,
+                          int loss_kind, double* loss, double* grad_scale, double* grad_w, double* grad_z,
+                          void* d_work, void* stream) {
+  return adjoint_impl(space, z, scale, dt, steps, ckpt_every, loss_kind, loss, grad_scale, grad_w, grad_z, nullptr,
+                      d_work, stream);
+}
+
+extern "C" int qb_adjoint_couplings(qb_space* space, const double* z, double scale, double dt, int64_t steps, int ckpt_every,
+                            int loss_kind, double* loss, double* grad_scale, double* grad_w, double* grad_z,
+                            double* grad_L, void* d_work, void* stream) {
+  if (!grad_L) return fail(QB_EINVAL, "grad_L must be non-NULL");
+  return adjoint_impl(space, z, scale, dt, steps, ckpt_every, loss_kind, loss, grad_scale, grad_w, grad_z, grad_L,
+                      d_work, stream);
 }

@@ -169,6 +169,11 @@ int launch_scale(const Space& s, void* d_psi, double factor, void* stream);
 int launch_number(const Space& s, int64_t index, void* d_psi, void* stream);
 // raw moments: out[0]=norm, out[1]=<N>, out[2]=<H>, then a[M], Mij[M*M], aa[M*M] complex
 int launch_moments(Space& s, const void* d_psi, double* out_host, void* stream);
+// d_acc[2e], d_acc[2e + 1] += weight * <bra, O_e ket> (re, im) for the two-body operators
+// O_e = a_a1^dag a_a2^dag a_c1 a_c2 listed in d_tb[e] = a1 | a2 << 8 | c1 << 16 | c2 << 24;
+// bra and ket are weighted double-float vectors of the space (as the stage kernels hold them)
+int launch_tb_bilinear(Space& s, const float4* bra, const float4* ket, const int* d_tb, int n_tb, double weight,
+                       double* d_acc, void* stream);
 int64_t workspace_bytes(const Space& s, int batch);
 // psi (FP64 complex) -> double-float copy (float4 per ket)
 int launch_to_df(const void* psi, void* psif, int64_t n, void* stream);

@@ -267,7 +267,8 @@ struct MwOccWords {  // 32-bit words of byte occupations per ket
 template <int MT, bool EXACT, int kMwSpl>
 __global__ void __launch_bounds__(kMwBlock, QB_MW_MIN_BLOCKS) moments_w_kernel(const Tables t, const double2* psi, const float4* f,
                                                                  double* partial, int nmom, int e_begin, int nent,
-                                                                 int sec_smem, int* status) {
+                                                                 int sec_smem, int* status, const float4* ketf,
+                                                                 const int* tb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int kMB = (MT > 0) ? MT : kMaxM;
   constexpr int kIW = MwWords<MT, EXACT>::n;
@@ -299,7 +300,21 @@ __global__ void __launch_bounds__(kMwBlock, QB_MW_MIN_BLOCKS) moments_w_kernel(c
     int4 h = make_int4(0, 0, 0, 0);
     int sh[kMaxM];
     for (int m = 0; m < kMaxM; ++m) sh[m] = 0;
-    if (s < nent) {
+    if (s < nent && tb) {
+      // two-body operator a_a1^dag a_a2^dag a_c1 a_c2 (tb[] = a1 | a2 << 8 | c1 << 16 | c2 << 24):
+      // k = n_c1 (n_c2 - [c1 = c2]), the target in the same sector; the suffix shift
+      // of mode m sums the changes of the modes >= m
+      const int w = tb[e_begin + s];
+      const int a1 = w & 0xff, a2 = (w >> 8) & 0xff, c1 = (w >> 16) & 0xff, c2 = (w >> 24) & 0xff;
+      int dc = 0, dk = 0;
+      for (int m = M - 1; m >= 1; --m) {
+        const int dm = (m == a1) + (m == a2) - (m == c1) - (m == c2);
+        dc += dm;
+        dk += dm * m;
+        sh[m] = dc * twoQ + (((dk % Q) + Q) % Q);
+      }
+      h = make_int4(c1 | (c2 << 8) | (1 << 16), c1 == c2 ? -1 : 0, 0, 0);
+    } else if (s < nent) {
       const MwEntry e = mw_entry(e_begin + s, M);
       const int f1 = (e.dn1 == 0) ? e.e0 : e.e1;  // a zero second change acts on e0
       const int hi = max(e.e0, f1), lo = min(e.e0, f1);
@@ -391,9 +406,15 @@ __global__ void __launch_bounds__(kMwBlock, QB_MW_MIN_BLOCKS) moments_w_kernel(c
         const int sid = find_sector_in(soff, t.n_sectors, g);
         nk = __ldg(t.sec_N + sid) | (__ldg(t.sec_K + sid) << 16);
         const uint64_t word = __ldg(t.occ + g);
-        const double2 p = psi[g];
         const double w = ket_weight_word<MT>(t, word).x;
-        x = df_pack(df_of(p.x * w), df_of(p.y * w));
+        if (tb) {  // a weighted double-float ket k: true value w k, times w
+          const float4 kv = ketf[g];
+          const double w2 = w * w;
+          x = df_pack(df_of(df_to(df_re(kv)) * w2), df_of(df_to(df_im(kv)) * w2));
+        } else {
+          const double2 p = psi[g];
+          x = df_pack(df_of(p.x * w), df_of(p.y * w));
+        }
         int srem = 0, skr = 0;
 #pragma unroll
         for (int m = kMB - 1; m >= 0; --m) {
@@ -540,7 +561,10 @@ __global__ void __launch_bounds__(kMwBlock, QB_MW_MIN_BLOCKS) moments_w_kernel(c
 #pragma unroll
       for (int r = 0; r < kMwSpl; ++r) {
         const int s = r * 32 + lane;
-        if (s < nent) {
+        if (s < nent && tb) {  // one complex slot per operator
+          row[2 * s] += acc_r[r];
+          row[2 * s + 1] += acc_i[r];
+        } else if (s < nent) {
           const MwEntry e = mw_entry(e_begin + s, M);
           if (e.kind == kEntA) {
             row[oA + 2 * e.i] += acc_r[r];
@@ -579,7 +603,7 @@ static int launch_prep(const Space& s, const double2* psi, float4* f, double* pa
 
 template <int MT, bool EXACT, int SPL>
 static int launch_mw(const Space& s, const double2* psi, const float4* f, double* part, int nmom, int e_begin,
-                     int nent, int* grid_out, cudaStream_t st) {
+                     int nent, int* grid_out, cudaStream_t st, const float4* ketf, const int* tb) {
   const Tables& t = s.t;
   const int from = EXACT ? t.o_ann : t.o_E;
   const int np = (nent + 31) & ~31;
@@ -592,7 +616,8 @@ static int launch_mw(const Space& s, const double2* psi, const float4* f, double
   int rc = persistent_grid(k, smem, (t.total + 31) / 32 * kMwBlock / kMwWarps, &grid, kMwBlock);
   if (rc) return rc;
   grid = (int)std::min<int64_t>(grid, max_grid_of(s));
-  k<<<grid, kMwBlock, smem, st>>>(t, psi, f, part, nmom, e_begin, nent, sec_smem, reinterpret_cast<int*>(s.d_scratch));
+  k<<<grid, kMwBlock, smem, st>>>(t, psi, f, part, nmom, e_begin, nent, sec_smem, reinterpret_cast<int*>(s.d_scratch),
+                                  ketf, tb);
   QB_CUDA(cudaGetLastError());
   *grid_out = grid;
   return QB_OK;
@@ -609,27 +634,67 @@ constexpr bool mw_needed() {
 
 template <int MT, bool EXACT>
 static int launch_mw_m(const Space& s, const double2* psi, const float4* f, double* part, int nmom, int e_begin,
-                       int nent, int* grid, cudaStream_t st) {
+                       int nent, int* grid, cudaStream_t st, const float4* ketf, const int* tb) {
+  // the compiled variant with the fewest entries per lane that holds the pass
   const int spl = (nent + 31) / 32;
   if constexpr (mw_needed<MT, 1>())
-    if (spl == 1) return launch_mw<MT, EXACT, 1>(s, psi, f, part, nmom, e_begin, nent, grid, st);
+    if (spl <= 1) return launch_mw<MT, EXACT, 1>(s, psi, f, part, nmom, e_begin, nent, grid, st, ketf, tb);
   if constexpr (mw_needed<MT, 2>())
-    if (spl == 2) return launch_mw<MT, EXACT, 2>(s, psi, f, part, nmom, e_begin, nent, grid, st);
+    if (spl <= 2) return launch_mw<MT, EXACT, 2>(s, psi, f, part, nmom, e_begin, nent, grid, st, ketf, tb);
   if constexpr (mw_needed<MT, 3>())
-    if (spl == 3) return launch_mw<MT, EXACT, 3>(s, psi, f, part, nmom, e_begin, nent, grid, st);
+    if (spl <= 3) return launch_mw<MT, EXACT, 3>(s, psi, f, part, nmom, e_begin, nent, grid, st, ketf, tb);
   return fail(QB_EINTERNAL, "moments pass without a compiled kernel");
+}
+
+// entries per pass of the two-body sweep for M: a multiple of 32 the compiled
+// variants take in full passes
+static int tb_pass_entries(int M) {
+  switch (M) {
+    case 5: return 32;
+    case 7: return 64;
+    case 9: return 96;
+    case 11: return 96;
+    default: return 32 * kMwSplMax;
+  }
 }
 
 template <bool EXACT>
 static int launch_mw_e(const Space& s, const double2* psi, const float4* f, double* part, int nmom, int e_begin,
-                       int nent, int* grid, cudaStream_t st) {
+                       int nent, int* grid, cudaStream_t st, const float4* ketf = nullptr,
+                       const int* tb = nullptr) {
   switch (s.M) {
-    case 5: return launch_mw_m<5, EXACT>(s, psi, f, part, nmom, e_begin, nent, grid, st);
-    case 7: return launch_mw_m<7, EXACT>(s, psi, f, part, nmom, e_begin, nent, grid, st);
-    case 9: return launch_mw_m<9, EXACT>(s, psi, f, part, nmom, e_begin, nent, grid, st);
-    case 11: return launch_mw_m<11, EXACT>(s, psi, f, part, nmom, e_begin, nent, grid, st);
-    default: return launch_mw_m<0, EXACT>(s, psi, f, part, nmom, e_begin, nent, grid, st);
+    case 5: return launch_mw_m<5, EXACT>(s, psi, f, part, nmom, e_begin, nent, grid, st, ketf, tb);
+    case 7: return launch_mw_m<7, EXACT>(s, psi, f, part, nmom, e_begin, nent, grid, st, ketf, tb);
+    case 9: return launch_mw_m<9, EXACT>(s, psi, f, part, nmom, e_begin, nent, grid, st, ketf, tb);
+    case 11: return launch_mw_m<11, EXACT>(s, psi, f, part, nmom, e_begin, nent, grid, st, ketf, tb);
+    default: return launch_mw_m<0, EXACT>(s, psi, f, part, nmom, e_begin, nent, grid, st, ketf, tb);
   }
+}
+
+// acc[c] += weight * sum_k partial[k][c], in a fixed order
+__global__ void accumulate_rows_kernel(const double* partial, int n, int width, double weight, double* acc) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < width; c += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += partial[(size_t)k * width + c];
+    acc[c] += weight * s;
+  }
+}
+
+int launch_tb_bilinear(Space& s, const float4* bra, const float4* ket, const int* d_tb, int n_tb, double weight,
+                       double* d_acc, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  // (a pass's partial rows, 2 doubles an entry, live in the moments' partial area)
+  const int per = std::min(tb_pass_entries(s.M), std::max(1, nmoments(s.M) / 2));
+  for (int e0 = 0; e0 < n_tb; e0 += per) {
+    const int ne = std::min(per, n_tb - e0);
+    int gm = 0;
+    int rc = s.t.exact ? launch_mw_e<true>(s, nullptr, bra, partial_area(s), 2 * ne, e0, ne, &gm, st, ket, d_tb)
+                       : launch_mw_e<false>(s, nullptr, bra, partial_area(s), 2 * ne, e0, ne, &gm, st, ket, d_tb);
+    if (rc) return rc;
+    accumulate_rows_kernel<<<(2 * ne + 127) / 128, 128, 0, st>>>(partial_area(s), gm, 2 * ne, weight, d_acc + 2 * e0);
+    QB_CUDA(cudaGetLastError());
+  }
+  return QB_OK;
 }
 
 int launch_moments(Space& s, const void* d_psi, double* out_host, void* stream) {

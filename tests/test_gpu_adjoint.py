@@ -117,6 +117,15 @@ def test_autograd_function_returns_adjoint_gradients():
     with torch.no_grad():
         plain = qb.adjoint_loss(s_t, w_t, z_t, M=M, L0=L0, n_min=0, n_max=10, dt=dt, steps=steps, loss="Q")
     assert abs(plain.item() - ref[0]) <= 1e-10
+    # the coupling as an input: L0.grad = scale * d loss / d L (qb_adjoint_couplings)
+    L_t = torch.tensor(L0, dtype=torch.complex128, requires_grad=True)
+    loss2 = qb.adjoint_loss(s_t, w_t, z_t, L_t, M=M, n_min=0, n_max=10, dt=dt, steps=steps, ckpt_every=1,
+                            loss="Q")
+    loss2.backward()
+    r = qb.Space(M, w, L0, 0, 10).adjoint(z, scale, dt, steps, ckpt_every=1, loss="Q", coupling_grad=True)
+    assert np.allclose(L_t.grad.numpy(), scale * r["grad_L"], rtol=0, atol=1e-14 * np.abs(r["grad_L"]).max())
+    assert abs(float(np.sum((np.conj(L_t.grad.numpy()) * L0).real)) - scale * r["grad_scale"]) <= \
+        1e-10 * abs(scale * r["grad_scale"])
 
 
 def test_adjoint_full_size_against_central_differences():
@@ -152,3 +161,70 @@ def test_adjoint_full_size_against_central_differences():
     ez[1] = 1j * h
     fd = (loss(zz=W.z + ez) - loss(zz=W.z - ez)) / (2 * h)
     assert abs(got["grad_z"][1].imag - fd) <= 1e-4 * abs(fd)
+
+
+def _hermitian_direction(M, seed):
+    """A random coupling direction D with D_{pq;rs} = conj(D_{rs;pq}), zero off momentum
+    conservation mod M."""
+    rng = np.random.default_rng(seed)
+    D = rng.standard_normal((M,) * 4) + 1j * rng.standard_normal((M,) * 4)
+    idx = np.indices((M,) * 4)
+    D[(idx[0] + idx[1] - idx[2] - idx[3]) % M != 0] = 0.0
+    return 0.5 * (D + np.conj(D.transpose(2, 3, 0, 1)))
+
+
+@pytest.mark.parametrize("kind", ["Q", "PO"])
+def test_coupling_gradient_against_scale_and_central_differences(kind):
+    """qb_adjoint_couplings: the derivative along the space's own coupling equals
+    grad_scale (an identity of the two sums, 1e-10), and along two random Hermitian
+    momentum-conserving directions it matches central differences of the loss (1e-6).
+    The other outputs equal those of qb_adjoint."""
+    import paper_2111_00050_gb300 as qb
+
+    M, w, L0, z, scale, dt, steps = _case()
+    qs = qb.Space(M, w, L0, 0, 10)
+    got = qs.adjoint(z, scale, dt, steps, ckpt_every=1, loss=kind, coupling_grad=True)
+    ref = qs.adjoint(z, scale, dt, steps, ckpt_every=1, loss=kind)
+    assert got["loss"] == ref["loss"] and got["grad_scale"] == ref["grad_scale"]
+    g = got["grad_L"]
+    along_L0 = float(np.sum((np.conj(g) * L0).real))
+    assert abs(along_L0 - got["grad_scale"]) <= 1e-10 * abs(got["grad_scale"])
+    h = 1e-5
+    for seed in (1, 2):
+        D = _hermitian_direction(M, seed)
+
+        def loss(eps):
+            Lp = scale * L0 + eps * D
+            sp = qb.Space(M, w, Lp, 0, 10)
+            return sp.adjoint(z, 1.0, dt, steps, ckpt_every=1, loss=kind)["loss"]
+
+        fd = (loss(h) - loss(-h)) / (2 * h)
+        an = float(np.sum((np.conj(g) * D).real))
+        assert abs(an - fd) <= 1e-6 * max(abs(fd), 1e-3 * abs(got["grad_scale"]))
+
+
+def test_coupling_gradient_complex_generic_tape():
+    """The generic kernels (M = 4, a random complex Hermitian coupling) in tape mode:
+    the derivative along the coupling equals grad_scale and along a random direction
+    matches central differences."""
+    import paper_2111_00050_gb300 as qb
+
+    M = 4
+    rng = np.random.default_rng(5)
+    w = rng.standard_normal(M)
+    L0 = 0.05 * _hermitian_direction(M, 9)
+    z = (rng.standard_normal(M) + 1j * rng.standard_normal(M)) * 0.6
+    dt, steps = 2e-3, 40
+    qs = qb.Space(M, w, L0, 0, 8)
+    got = qs.adjoint(z, 1.0, dt, steps, ckpt_every=0, loss="Q", coupling_grad=True)
+    g = got["grad_L"]
+    assert abs(float(np.sum((np.conj(g) * L0).real)) - got["grad_scale"]) <= 1e-10 * abs(got["grad_scale"])
+    D = _hermitian_direction(M, 11)
+    h = 1e-5
+
+    def loss(eps):
+        return qb.Space(M, w, L0 + eps * D, 0, 8).adjoint(z, 1.0, dt, steps, ckpt_every=1, loss="Q")["loss"]
+
+    fd = (loss(h) - loss(-h)) / (2 * h)
+    an = float(np.sum((np.conj(g) * D).real))
+    assert abs(an - fd) <= 1e-6 * max(abs(fd), 1e-3 * abs(got["grad_scale"]))
