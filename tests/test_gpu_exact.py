@@ -153,6 +153,21 @@ def test_exact_adjoint_matches_oracle():
     assert rel(got["grad_scale"], gs) <= 1e-8
     assert rel(got["grad_w"], gw) <= 1e-8
     assert rel(got["grad_z"], gz) <= 1e-8
+    # every coupling entry (tape mode): along L0 it is grad_scale; along an exactly
+    # conserving Hermitian direction it matches central differences
+    gc = qs.adjoint(z, -0.2, 2e-3, 40, ckpt_every=0, loss="Q", coupling_grad=True)
+    g = gc["grad_L"]
+    assert abs(float(np.sum((np.conj(g) * L0).real)) - gc["grad_scale"]) <= 1e-10 * abs(gc["grad_scale"])
+    _, D = _random_exact_hermitian(M, 3)
+    h = 1e-5
+
+    def fl(eps):
+        return qb.Space(M, w, -0.2 * L0 + eps * D, 0, 10, exact=True).adjoint(z, 1.0, 2e-3, 40, ckpt_every=1,
+                                                                              loss="Q")["loss"]
+
+    fd = (fl(h) - fl(-h)) / (2 * h)
+    an = float(np.sum((np.conj(g) * D).real))
+    assert abs(an - fd) <= 1e-6 * max(abs(fd), 1e-3 * abs(gc["grad_scale"]))
 
 
 def test_exact_rejects_umklapp_coupling_and_batches():
