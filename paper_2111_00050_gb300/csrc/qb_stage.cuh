@@ -137,16 +137,18 @@ __device__ __forceinline__ int rank_esum(const Tables& t, const int32_t* E, cons
       // the table holds zero (mode 0, fewer than one particle)
       if (MT == 0 || 2 * k + 2 < MT) esum += e_byte(u >> 16);
     }
-  } else {  // RK_EXACT: int16 shifts, two modes per word
+  } else {  // RK_EXACT: int16 shifts, two modes per word (modes 8-15 in the second row)
     const uint4 d0 = reinterpret_cast<const uint4*>(dtab)[2 * (size_t)j];
-    const uint4 d1 = reinterpret_cast<const uint4*>(dtab)[2 * (size_t)j + 1];
+    uint4 d1 = make_uint4(0u, 0u, 0u, 0u);
+    if (MT == 0 || MT > 8) d1 = reinterpret_cast<const uint4*>(dtab)[2 * (size_t)j + 1];
 #pragma unroll
     for (int m = 1; m < 16; ++m) {
       if (m >= M) break;
       const uint32_t word = (m < 2) ? d0.x : (m < 4) ? d0.y : (m < 6) ? d0.z : (m < 8) ? d0.w
                           : (m < 10) ? d1.x : (m < 12) ? d1.y : (m < 14) ? d1.z : d1.w;
-      esum += *reinterpret_cast<const int32_t*>(reinterpret_cast<const char*>(E) + id[m] +
-                                                 ((int)(int16_t)(word >> (16 * (m & 1))) << 2));
+      // the ranking table is read-only for the kernel's life: the non-coherent path
+      esum += __ldg(reinterpret_cast<const int32_t*>(reinterpret_cast<const char*>(E) + id[m] +
+                                                      ((int)(int16_t)(word >> (16 * (m & 1))) << 2)));
     }
   }
   return esum;
