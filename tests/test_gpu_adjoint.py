@@ -228,3 +228,21 @@ def test_coupling_gradient_complex_generic_tape():
     fd = (loss(h) - loss(-h)) / (2 * h)
     an = float(np.sum((np.conj(g) * D).real))
     assert abs(an - fd) <= 1e-6 * max(abs(fd), 1e-3 * abs(got["grad_scale"]))
+
+
+@pytest.mark.parametrize("M", [1, 3, 6])
+def test_coupling_gradient_small_and_even_mode_counts(M):
+    """The generic kernels with one operator (M = 1: L_{00;00} only), a few (M = 3) and
+    an even mode count (M = 6): the derivative along the space's own coupling equals
+    grad_scale, and the entries are the same for every ordering of the two pairs."""
+    import paper_2111_00050_gb300 as qb
+
+    rng = np.random.default_rng(M)
+    w = wl.dispersion_quadratic(M)
+    L0 = wl.contact_coupling(M, 1.0) if M != 3 else 0.2 * _hermitian_direction(M, 4)
+    z = (rng.standard_normal(M) + 1j * rng.standard_normal(M)) * 0.8
+    qs = qb.Space(M, w, L0, 0, 9 if M < 6 else 6)
+    got = qs.adjoint(z, -0.3, 2e-3, 30, ckpt_every=0, loss="Q", coupling_grad=True)
+    g = got["grad_L"]
+    assert abs(float(np.sum((np.conj(g) * L0).real)) - got["grad_scale"]) <= 1e-10 * abs(got["grad_scale"]) + 1e-16
+    assert np.array_equal(g, g.transpose(1, 0, 2, 3)) and np.array_equal(g, g.transpose(0, 1, 3, 2))
