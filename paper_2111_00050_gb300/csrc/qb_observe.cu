@@ -33,12 +33,16 @@
 namespace qb {
 
 constexpr int kObsBlock = 256;  // threads per CTA of the first pass
-constexpr int kMwWarps = 8;     // warps per CTA of the moments kernel
+// warps per CTA of the moments kernel (its CTAs share nothing but the staged table)
+#ifndef QB_MW_WARPS
+#define QB_MW_WARPS 24
+#endif
+constexpr int kMwWarps = QB_MW_WARPS;
 constexpr int kMwBlock = 32 * kMwWarps;
 constexpr int kMwSplMax = 3;    // moment entries per lane and pass (<= 96 per pass)
 // resident CTAs per SM the moments kernel's registers are planned for
 #ifndef QB_MW_MIN_BLOCKS
-#define QB_MW_MIN_BLOCKS 3
+#define QB_MW_MIN_BLOCKS 1
 #endif
 
 // sums partial[0..n)[0..width) over the first index in a fixed order
