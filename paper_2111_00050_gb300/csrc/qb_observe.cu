@@ -222,6 +222,9 @@ __device__ __forceinline__ int mw_occ(const uint32_t (&w)[NW], int m) {
   }
 }
 
+// bytes of the ranking table (16-byte multiple: the next table starts aligned)
+__host__ __device__ inline int mw_table_bytes(const Tables& t) { return t.o_ann - t.o_E; }
+
 constexpr size_t kMwSecSmemMax = 16384;  // sector tables larger than this stay in global memory
 
 static size_t mw_sec_bytes(const Tables& t) {
@@ -277,12 +280,14 @@ __global__ void __launch_bounds__(kMwBlock, QB_MW_MIN_BLOCKS) moments_w_kernel(c
   constexpr int kMB = (MT > 0) ? MT : kMaxM;
   constexpr int kIW = MwWords<MT, EXACT>::n;
   constexpr int kOBW = MwOccWords<MT>::n;
-  const int from = EXACT ? t.o_ann : t.o_E;
+  // shared memory starts with the ranking table (mod M; exact momentum keeps it in
+  // global memory and stages nothing)
+  const int e_bytes = EXACT ? 0 : mw_table_bytes(t);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int M = (MT > 0) ? MT : t.M, Q = t.Q, twoQ = 2 * Q, V = t.nmax + 1;
   const int np = (nent + 31) & ~31;
   const int iw = EXACT ? M : M / 2;  // offset words in use (mode m: word m, or word (m-1)/2 packed)
-  unsigned char* cur = smem_raw + ((t.blob_bytes - from + 15) & ~15);
+  unsigned char* cur = smem_raw + e_bytes;
   int4* hdr = reinterpret_cast<int4*>(cur);  // e0 | e1 << 8 | has2 << 16 | cls << 24, c1, dN, dK mod Q
   cur += (size_t)np * 16;
   int32_t* shf = reinterpret_cast<int32_t*>(cur);  // [kIW][np] byte shifts (packed in pairs for mod M)
@@ -360,7 +365,12 @@ __global__ void __launch_bounds__(kMwBlock, QB_MW_MIN_BLOCKS) moments_w_kernel(c
     sof = q;
   }
   for (int k = tid; k < nmom; k += kMwBlock) row[k] = 0.0;
-  load_blob_from(t, smem_raw, from);  // ends with a CTA barrier
+  {
+    const int4* src = reinterpret_cast<const int4*>(t.blob + t.o_E);
+    int4* dst = reinterpret_cast<int4*>(smem_raw);
+    for (int i = tid; i < e_bytes / 16; i += kMwBlock) dst[i] = __ldg(src + i);
+    __syncthreads();
+  }
   const char* Eg = reinterpret_cast<const char*>(t.blob + t.o_E);  // exact momentum: the table stays global
   const int ob = t.occ_bits;
   const int64_t total = t.total;
@@ -609,10 +619,9 @@ template <int MT, bool EXACT, int SPL>
 static int launch_mw(const Space& s, const double2* psi, const float4* f, double* part, int nmom, int e_begin,
                      int nent, int* grid_out, cudaStream_t st, const float4* ketf, const int* tb) {
   const Tables& t = s.t;
-  const int from = EXACT ? t.o_ann : t.o_E;
   const int np = (nent + 31) & ~31;
   const int sec_smem = mw_sec_bytes(t) <= kMwSecSmemMax ? 1 : 0;
-  const size_t smem = ((size_t)(t.blob_bytes - from + 15) & ~(size_t)15) +
+  const size_t smem = (size_t)(EXACT ? 0 : mw_table_bytes(t)) +
                       mw_smem_after(np, t.nmax, nmom, MwWords<MT, EXACT>::n, MwOccWords<MT>::n) +
                       (sec_smem ? mw_sec_bytes(t) : 0);
   auto k = moments_w_kernel<MT, EXACT, SPL>;
