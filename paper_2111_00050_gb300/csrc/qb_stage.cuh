@@ -36,6 +36,14 @@
 #ifndef QB_UNROLL_PARTNERS
 #define QB_UNROLL_PARTNERS 1
 #endif
+// 1: the specialised kernels for odd M <= QB_REG_OCC_MAX_M take a pair's occupations
+// from registers
+#ifndef QB_REG_OCC
+#define QB_REG_OCC 1
+#endif
+#ifndef QB_REG_OCC_MAX_M
+#define QB_REG_OCC_MAX_M 11
+#endif
 // 1: a ket's sector from its occupations (N, K) and the (N, K) -> sector table;
 // 0: binary search of the sector offsets
 #ifndef QB_SEC_FROM_WORD
@@ -45,6 +53,13 @@
 namespace qb {
 
 enum { RK_PAIR = 1, RK_EXACT = 2 };
+
+// n_m of occupations held as bytes in three words (modes 0-3, 4-7, 8-11)
+template <int MT>
+__device__ __forceinline__ int reg_occ(uint32_t ob0, uint32_t ob1, uint32_t ob2, int m) {
+  if constexpr (MT <= 8) return (int)(__byte_perm(ob0, ob1, (uint32_t)m) & 0xffu);
+  return m < 8 ? (int)(__byte_perm(ob0, ob1, (uint32_t)m) & 0xffu) : (int)((ob2 >> (8 * (m - 8))) & 0xffu);
+}
 
 // What a stage launch computes besides (or instead of) its output vector:
 //   KIND_STAGE  the RK4 / adjoint stage alone (modes 0 to 3);
@@ -280,12 +295,24 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
         if (m < M) id[m] = sidx[m * kRows + row];
     }
     uint32_t occmask = 0, twomask = 0;
+    // the specialised odd-M kernels with M <= 7 also keep the occupations as bytes in
+    // registers, so that a pair's n_r and n_s are byte permutes instead of shared loads
+    constexpr bool kRegOcc = QB_REG_OCC && MT > 0 && MT <= QB_REG_OCC_MAX_M && (MT % 2) == 1 && !CPLX && !EXACT;
+    uint32_t ob0 = 0u, ob1 = 0u, ob2 = 0u;
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
       if (m >= M) break;
       const int nm = occ[m * kRows];
       occmask |= (nm >= 1 ? 1u : 0u) << m;
       twomask |= (nm >= 2 ? 1u : 0u) << m;
+      if (kRegOcc) {
+        if (m < 4)
+          ob0 |= (uint32_t)nm << (8 * m);
+        else if (m < 8)
+          ob1 |= (uint32_t)nm << (8 * (m - 4));
+        else
+          ob2 |= (uint32_t)nm << (8 * (m - 8));
+      }
     }
     const float4* vsec = a.vin + (LOCAL ? 0 : off);  // gathers
     dfc acc[B];  // (re, im) of the off-diagonal sum, double-float, packed
@@ -310,15 +337,19 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
       if (smask == 0) break;  // not reached: npairs counts exactly the pairs found here
       const int s = __ffs(smask) - 1;
       smask &= smask - 1;
-      const int ai = v.pairidx[r * 16 + s];
-      const float Af = (float)(occ[r * kRows] * (occ[s * kRows] - (r == s ? 1 : 0)));  // exact
+      // pair index of (r <= s) in the order r = 0.., s = r..: r (2M - r + 1) / 2 + s - r
+      const int ai = kRegOcc ? (r * (2 * MT - r + 1)) / 2 + s - r : v.pairidx[r * 16 + s];
+      const int nr = kRegOcc ? reg_occ<MT>(ob0, ob1, ob2, r) : occ[r * kRows];
+      const int ns = kRegOcc ? reg_occ<MT>(ob0, ob1, ob2, s) : occ[s * kRows];
+      const float Af = (float)(nr * (ns - (r == s ? 1 : 0)));  // exact
       // (exact momentum: the partner count varies from pair to pair; <x|H|x> takes
       // only the partners after the pair)
       constexpr int kC =
           (QB_UNROLL_PARTNERS && !CPLX && !EXACT && !DOT && MT > 0 && (MT % 2) == 1) ? (MT - 1) / 2 : 0;
       if (kC > 0) {
         // fixed partner count: all ranks first, then all gathers, then the sums
-        const int j0 = v.ann[ai];
+        // every pair has kC partners, laid out pair by pair
+        const int j0 = kRegOcc ? ai * kC : v.ann[ai];
         int rkc[kC > 0 ? kC : 1];
         dfl crc[kC > 0 ? kC : 1];
 #pragma unroll
