@@ -36,13 +36,13 @@ import workloads as wl  # noqa: E402
 # roofline uses the DFMA rate measured on the GPU by the run itself (qb_measure_fp64_fma)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per ket of one stage launch (the first stage of a step), from an ncu capture
-# of the current stage kernel (batched coherent at n_tot=12: 616.1 MB read + 226.8 MB
+# of the current stage kernel (batched coherent at n_tot=12: 617.2 MB read + 226.8 MB
 # written over 15,380,937 kets); scaled by kets
-STAGE_DRAM_BYTES_PER_KET = (616.088064e6 + 226.754816e6) / 15380937
+STAGE_DRAM_BYTES_PER_KET = (617.219072e6 + 226.820352e6) / 15380937
 # the same capture's issue-slot and L1 data-pipe utilisation (the kernel's real limits:
 # the FP64 pipe is idle)
-STAGE_NCU_ISSUE_ACTIVE = 0.627
-STAGE_NCU_L1_WAVEFRONTS = 0.922
+STAGE_NCU_ISSUE_ACTIVE = 0.670
+STAGE_NCU_L1_WAVEFRONTS = 0.920
 
 
 def _peaks():

@@ -297,7 +297,8 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
     uint32_t occmask = 0, twomask = 0;
     // the specialised odd-M kernels with M <= 7 also keep the occupations as bytes in
     // registers, so that a pair's n_r and n_s are byte permutes instead of shared loads
-    constexpr bool kRegOcc = QB_REG_OCC && MT > 0 && MT <= QB_REG_OCC_MAX_M && (MT % 2) == 1 && !CPLX && !EXACT;
+    constexpr bool kRegOcc =
+        QB_REG_OCC && MT > 0 && MT <= QB_REG_OCC_MAX_M && (MT % 2) == 1 && !CPLX && !EXACT && !DOT;
     uint32_t ob0 = 0u, ob1 = 0u, ob2 = 0u;
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
