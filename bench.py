@@ -306,6 +306,33 @@ def exact_extra(qb, torch, steps: int = 3):
     return out
 
 
+def long_range_extra(qb, torch, steps: int = 3):
+    """The long-range field-number workload (M=9, L = -(0.1/n_tot) / (M (p-r)^2), n_p from
+    Poisson(3) with seed-0 phases: one particle number, every P sector): RK4 steps through
+    the specialised M=9 stage kernel, shape and resident threshold autotuned."""
+    W = wl.long_range_field_number()
+    qs = qb.Space(W.M, W.w, W.L, W.n_min, W.n_max)
+    terms, _ = qs.terms()
+    psi = qs.empty_state()
+    qs.init_field_number(W.z, W.n_tot, psi)
+    work = qs.workspace(1)
+    resident_max = qs.autotune(W.dt, psi, steps=1, work=work)
+    qs.evolve(psi, W.dt, 1, work)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    qs.evolve(psi, W.dt, steps, work)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    out = {"workload": W.name, "kets": qs.total, "sectors": qs.n_sectors, "terms_per_hpsi": terms,
+           "ms_per_step": ms, "terms_per_s": 4 * terms / (ms * 1e-3), "rk4_steps_per_s": 1e3 / ms,
+           "tile_shape": qs.tuning.get("tile_shape"), "resident_max_kets": resident_max}
+    del psi, work, qs
+    torch.cuda.empty_cache()
+    return out
+
+
 def squeezing_extra(qb, torch, n_list=(4, 8, 12)):
     """Sec. IV E's squeezing analysis (the paper's n_tot sweep, scaled down): for each
     n_tot the M=7 long-range system from a Gaussian coherent profile, its strength set
@@ -698,6 +725,7 @@ def main():
         line["sweep"] = sweep_extra(qb, torch)
         line["small_sector"] = small_extra(qb, torch)
         line["exact_momentum"] = exact_extra(qb, torch)
+        line["long_range"] = long_range_extra(qb, torch)
         line["squeezing"] = squeezing_extra(qb, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W)
