@@ -128,6 +128,10 @@ static int build_tables(Space& sp) {
   std::vector<uint32_t> pq;
   std::vector<double> G;
   std::vector<std::vector<int>> delta;  // [combo][16]
+  std::vector<std::vector<int>> dex;    // [combo][16] shifts of the compact exact index
+  // exact momentum: width of mode m's window of suffix momenta, (M-1-m) nmax + 1
+  int exw[16] = {0};
+  for (int m = 1; m < M; ++m) exw[m] = (M - 1 - m) * nmax + 1;
   std::vector<double> gd;
   unsigned char pairidx[16][16];
   memset(pairidx, 0xff, sizeof(pairidx));
@@ -160,6 +164,7 @@ static int build_tables(Space& sp) {
           dn[s] -= 1;
           dn[p] += 1;
           dn[q] += 1;
+          std::vector<int> dx(16, 0);
           for (int m = lo + 1; m <= hi; ++m) {
             int dc = 0, dk = 0;
             for (int e = m; e < M; ++e) {
@@ -167,8 +172,11 @@ static int build_tables(Space& sp) {
               dk += dn[e] * e;
             }
             d[m] = dc * twoQ + modp(dk, Q);
+            // compact exact index: row (rem) by dc, column (skr - m rem) by dk - m dc
+            dx[m] = dc * exw[m] + dk - m * dc;
           }
           delta.push_back(d);
+          dex.push_back(dx);
         }
     }
   annStart.push_back((int)pq.size());
@@ -184,6 +192,29 @@ static int build_tables(Space& sp) {
   off = align16(off + sizeof(uint32_t) * (size_t)(M + 1) * (nmax + 1) * Q);
   t.o_E = (int)off;
   off = align16(off + sizeof(int32_t) * (size_t)M * t.rem_w * twoQ);
+  // exact momentum: the compact ranking table, where it and the stage kernels' other
+  // tables and 12 warps' tiles fit a CTA's shared memory and its shifts fit 16 bits
+  t.o_Ex = (int)off;
+  t.ex_smem = 0;
+  if (sp.exact) {
+    size_t exb = 0;
+    int dmax = 0;
+    for (int m = 1; m < M; ++m) {
+      t.ex_w[m] = exw[m];
+      t.ex_base[m] = (int)exb;
+      exb += sizeof(int32_t) * (size_t)t.rem_w * exw[m];
+      dmax = std::max(dmax, 2 * exw[m] + 2 * (M - 1) + 2 * m);
+    }
+    const size_t rows = 64, iw = (size_t)M;
+    size_t wb = iw * rows * 4 + (((size_t)M * rows + 15) & ~(size_t)15) + rows * 4 + rows * 8 + rows +
+                2 * (size_t)(t.n_ann + 2) * 4;
+    wb = (wb + 15) & ~(size_t)15;
+    const size_t rest = 4096 + 32 * (size_t)std::max(1, t.n_combo) * 3 + 16 * (size_t)t.ncp + 1024;
+    if (exb + 12 * wb + rest <= 200 * 1024 && dmax <= 32767) {
+      t.ex_smem = 1;
+      off = align16(off + exb);
+    }
+  }
   t.o_ann = (int)off;
   off = align16(off + sizeof(int32_t) * (size_t)(t.n_ann + 1));
   t.o_hs = (int)off;
@@ -194,6 +225,8 @@ static int build_tables(Space& sp) {
   off = align16(off + sizeof(float) * 4 * (size_t)t.ncp);
   t.o_dsw = (int)off;
   off = align16(off + sizeof(uint32_t) * (size_t)std::max(2, nsw) * t.ncp);
+  t.o_dex = (int)off;
+  off = align16(off + (t.ex_smem ? (size_t)32 * std::max(1, t.n_combo) : 0));
   t.o_delta = (int)off;
   off = align16(off + (size_t)(sp.exact ? 32 : 16) * std::max(1, t.n_combo));
   t.o_sqrt = (int)off;
@@ -230,6 +263,20 @@ static int build_tables(Space& sp) {
         if (m >= 1 && rem >= 1 && rem - 1 <= nmax) v = (int32_t)sp.cnt[CI(m - 1, rem - 1, modp(kk - (m - 1), Q))];
         E[((size_t)m * t.rem_w + rr) * twoQ + kk] = v;
       }
+  if (t.ex_smem) {
+    int32_t* Ex = (int32_t*)(b + t.o_Ex);
+    for (int m = 1; m < M; ++m)
+      for (int rr = 0; rr < t.rem_w; ++rr)
+        for (int c = 0; c < t.ex_w[m]; ++c) {
+          const int rem = rr - 2, skr = c + m * rem;
+          int32_t v = 0;
+          if (rem >= 1 && rem - 1 <= nmax) v = (int32_t)sp.cnt[CI(m - 1, rem - 1, modp(skr - (m - 1), Q))];
+          Ex[t.ex_base[m] / 4 + (size_t)rr * t.ex_w[m] + c] = v;
+        }
+    int16_t* dx = (int16_t*)(b + t.o_dex);
+    for (int j = 0; j < t.n_combo; ++j)
+      for (int m = 0; m < 16; ++m) dx[(size_t)j * 16 + m] = (int16_t)dex[j][m];
+  }
   double* sq = (double*)(b + t.o_sqrt);
   for (int k = 0; k < nmax + 3; ++k) sq[k] = std::sqrt((double)k);
   memcpy(b + t.o_pq, pq.data(), sizeof(uint32_t) * pq.size());

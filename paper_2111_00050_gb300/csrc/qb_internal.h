@@ -46,6 +46,13 @@ struct Tables {
   int o_G;       // double [n_combo][2]        conj(mult * L^sym_{pq;rs}) (re, im)
   int o_delta;   // uint8  [n_combo][16]       kDeltaBias + flat-index shift of the suffix state at mode m
                  //   (exact: int16 [n_combo][16], the shift itself)
+  int o_Ex;      // exact momentum, when it fits a CTA: the compact ranking table, mode m (1 .. M-1)
+                 //   at byte ex_base[m], int32 [rem_w][ex_w[m]], column skr - m rem (the suffix
+                 //   momentum of mode m lies in [m rem, (M-1) rem]); empty otherwise (o_Ex = o_ann)
+  int ex_smem;   // 1: the stage kernels rank exact-momentum targets in the compact table
+  int ex_w[16];
+  int ex_base[16];
+  int o_dex;     // int16  [n_combo][16]       shifts of the flat compact index per mode (exact, compact)
   int o_ann;     // int32  [n_ann + 1]         first combo of annihilation pair a
   int o_hs;      // int32  [n_ann]             first combo of pair a whose creation pair (p, q) has a
                  //   larger pair index: <x|H|x> takes each term once with its reverse

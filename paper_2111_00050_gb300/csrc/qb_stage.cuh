@@ -109,7 +109,7 @@ __host__ __device__ inline size_t df_warp_scratch_bytes(int iw, int M, int n_ann
 // shared memory: the ranking table (mod M; exact momentum keeps it in global
 // memory), the pair offsets and indices, the couplings and the term shifts (exact
 // momentum: the int16 shift table)
-__host__ __device__ inline int kSmemFrom(const Tables& t, bool exact = false) { return exact ? t.o_ann : t.o_E; }
+__host__ __device__ inline int kSmemFrom(const Tables& t, bool exact = false) { return exact ? t.o_Ex : t.o_E; }
 __host__ __device__ inline int kSmemEnd(const Tables& t, bool exact = false) { return exact ? t.o_sqrt : t.o_delta; }
 
 // Gathered stage-vector entry: read-only global load, or a generic load when the
@@ -161,9 +161,11 @@ __device__ __forceinline__ int rank_esum(const Tables& t, const int32_t* E, cons
       if (m >= M) break;
       const uint32_t word = (m < 2) ? d0.x : (m < 4) ? d0.y : (m < 6) ? d0.z : (m < 8) ? d0.w
                           : (m < 10) ? d1.x : (m < 12) ? d1.y : (m < 14) ? d1.z : d1.w;
-      // the ranking table is read-only for the kernel's life: the non-coherent path
-      esum += __ldg(reinterpret_cast<const int32_t*>(reinterpret_cast<const char*>(E) + id[m] +
-                                                      ((int)(int16_t)(word >> (16 * (m & 1))) << 2)));
+      const int sh = (int)(int16_t)(word >> (16 * (m & 1))) << 2;
+      if (t.ex_smem)  // the compact table staged in shared memory
+        esum += e_byte((uint32_t)(id[m] + sh));
+      else  // the ranking table is read-only for the kernel's life: the non-coherent path
+        esum += __ldg(reinterpret_cast<const int32_t*>(reinterpret_cast<const char*>(E) + id[m] + sh));
     }
   }
   return esum;
@@ -231,6 +233,12 @@ __device__ __forceinline__ void stage_tile(const Tables& t, const View& v, const
         skr += m * nm;
         while (skr >= Qm) skr -= Qm;
         const int ix = (m * t.rem_w + srem + 2) * twoM + skr;
+        if (EXACT && t.ex_smem) {  // byte offset into the compact table (column skr - m srem)
+          const int ixb = t.ex_base[m] + ((srem + 2) * t.ex_w[m] + skr - m * srem) * 4;
+          esum += e_byte((uint32_t)ixb);
+          sidx[m * kRows + row] = ixb;
+          continue;
+        }
         esum += v.E[ix];
         if constexpr (RK == RK_PAIR) {
 #pragma unroll
@@ -529,7 +537,8 @@ __device__ __forceinline__ StageSmem stage_smem(const Tables& t, int M, int warp
   S.v = view_at(t, smem);
   if (RK == RK_EXACT) S.v.E = reinterpret_cast<const int32_t*>(t.blob + t.o_E);
   S.Gf = reinterpret_cast<const float2*>(smem + t.o_Gf);
-  S.dtab = (RK == RK_PAIR) ? smem + t.o_dsw : reinterpret_cast<const unsigned char*>(S.v.delta);
+  S.dtab = (RK == RK_PAIR) ? smem + t.o_dsw
+                           : (t.ex_smem ? smem + t.o_dex : reinterpret_cast<const unsigned char*>(S.v.delta));
   const int warp = threadIdx.x >> 5;
   const int iw = sidx_words(M, RK == RK_EXACT);
   const size_t wbytes = df_warp_scratch_bytes(iw, M, t.n_ann, rows);
@@ -795,10 +804,13 @@ int stage_launch_r(const Tables& t, const DfArgs& a, int mode, int B, bool cplx,
   } else {
     if constexpr (RK == RK_EXACT) {
       if (B != 1) return fail(QB_EUNSUPPORTED, "exact momentum: batched sweeps are not built");
-      if (wide0)
-        QB_STAGE_CASE(1, false, KIND_STAGE, kWideShape)
-      else
+      // the widest of 32, 24 and 12 warps that fits beside the compact ranking table
+      if (!wide0)
         QB_STAGE_CASE(1, false, KIND_STAGE, 0)
+      else if (fitting_shape(t, true, 2) == 2)
+        QB_STAGE_CASE(1, false, KIND_STAGE, 2)
+      else
+        QB_STAGE_CASE(1, false, KIND_STAGE, kWideShape)
     } else {
       switch (B) {
         case 1:
