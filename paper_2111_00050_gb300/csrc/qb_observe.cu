@@ -33,17 +33,25 @@
 namespace qb {
 
 constexpr int kObsBlock = 256;  // threads per CTA of the first pass
-// warps per CTA of the moments kernel (its CTAs share nothing but the staged table)
+// warps per CTA of the moments kernel (its CTAs share nothing but the staged table);
+// the kernels with two entries a lane keep two kets in flight, which takes more
+// registers a thread, and run fewer warps
 #ifndef QB_MW_WARPS
 #define QB_MW_WARPS 24
 #endif
-constexpr int kMwWarps = QB_MW_WARPS;
-constexpr int kMwBlock = 32 * kMwWarps;
+#ifndef QB_MW_WARPS_SPL2
+#define QB_MW_WARPS_SPL2 20
+#endif
 constexpr int kMwSplMax = 3;    // moment entries per lane and pass (<= 96 per pass)
 // resident CTAs per SM the moments kernel's registers are planned for
 #ifndef QB_MW_MIN_BLOCKS
 #define QB_MW_MIN_BLOCKS 1
 #endif
+// moments kernels with at most two entries a lane keep two kets' gathers in flight
+#ifndef QB_MW_PIPE
+#define QB_MW_PIPE 1
+#endif
+__host__ __device__ constexpr int mw_warps(int spl) { return (QB_MW_PIPE && spl == 2) ? QB_MW_WARPS_SPL2 : QB_MW_WARPS; }
 
 // sums partial[0..n)[0..width) over the first index in a fixed order
 __global__ void reduce_rows_kernel(const double* partial, int n, int width, double* out) {
@@ -202,10 +210,10 @@ __host__ __device__ inline MwEntry mw_entry(int s, int M) {
 // [3][nmax+1] float2, the CTA's FP64 moment row [nmom], and per warp the staged
 // tile of 32 kets (x float4, occupations as bytes [obwords] uint32, (N, K) int32,
 // offsets [iwords] int32)
-__host__ __device__ inline size_t mw_smem_after(int np, int nmax, int nmom, int iwords, int obwords) {
+__host__ __device__ inline size_t mw_smem_after(int np, int nmax, int nmom, int iwords, int obwords, int warps) {
   return (size_t)np * 16 + (((size_t)iwords * np * 4 + 15) & ~(size_t)15) +
          ((3 * (size_t)(nmax + 1) * 8 + 15) & ~(size_t)15) + (((size_t)nmom * 8 + 15) & ~(size_t)15) +
-         (size_t)kMwWarps * 32 * (16 + 4 * (size_t)obwords + 4 + 4 * (size_t)iwords);
+         (size_t)warps * 32 * (16 + 4 * (size_t)obwords + 4 + 4 * (size_t)iwords);
 }
 
 // n_m from occupations packed as bytes, four modes a word (M <= 16): one byte
@@ -272,11 +280,12 @@ struct MwOccWords {  // 32-bit words of byte occupations per ket
 };
 
 template <int MT, bool EXACT, int kMwSpl>
-__global__ void __launch_bounds__(kMwBlock, QB_MW_MIN_BLOCKS) moments_w_kernel(const Tables t, const double2* psi, const float4* f,
+__global__ void __launch_bounds__(32 * mw_warps(kMwSpl), QB_MW_MIN_BLOCKS) moments_w_kernel(const Tables t, const double2* psi, const float4* f,
                                                                  double* partial, int nmom, int e_begin, int nent,
                                                                  int sec_smem, int* status, const float4* ketf,
                                                                  const int* tb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int kMwWarps = mw_warps(kMwSpl), kMwBlock = 32 * kMwWarps;
   constexpr int kMB = (MT > 0) ? MT : kMaxM;
   constexpr int kIW = MwWords<MT, EXACT>::n;
   constexpr int kOBW = MwOccWords<MT>::n;
@@ -465,6 +474,115 @@ __global__ void __launch_bounds__(kMwBlock, QB_MW_MIN_BLOCKS) moments_w_kernel(c
 #pragma unroll
     for (int r = 0; r < kMwSpl; ++r) tp[r] = dfc{0ull, 0ull};
     const int nt = (int)min((int64_t)32, total - tile * 32);
+#if QB_MW_PIPE
+    if constexpr (kMwSpl <= 2) {
+      // two kets in flight: the targets of ket j + 1 are ranked and gathered before
+      // the products of ket j, which keeps twice the gathers outstanding per warp.
+      // issue(j): the coefficient c = k scale(N) (0 where the operator annihilates
+      // the ket or has no target sector) and the gathered target y of each entry
+      auto issue = [&](int j, float4 (&y)[kMwSpl], dfl (&cc)[kMwSpl]) {
+        const int nkj = knk[j];
+        if (nkj != cur_nk) {  // warp-uniform: a new (N, K) sector
+          cur_nk = nkj;
+          const int N = nkj & 0xffff, K = nkj >> 16;
+#pragma unroll
+          for (int r = 0; r < kMwSpl; ++r) {
+            tD[r] = -1;
+            const int s = r * 32 + lane;
+            if (s >= nent) continue;
+            const int4 h = hdr[s];
+            const int Nt = N + h.z;
+            if (Nt < 0) continue;
+            int Kt = K + h.w;
+            if (Kt >= Q) Kt -= Q;
+            const int sid = sof[Nt * Q + Kt];
+            if (sid < 0) continue;
+            toff[r] = soff[sid];
+            tD[r] = (int)(soff[sid + 1] - toff[r]);
+            const float2 c = scl[((h.x >> 24) & 3) * V + N];
+            csc[r] = dfl{c.x, c.y};
+          }
+        }
+        uint32_t obj[kOBW];
+#pragma unroll
+        for (int k = 0; k < kOBW; ++k) obj[k] = kob[k * 32 + j];
+        int idj[kIW];
+#pragma unroll
+        for (int q = 0; q < kIW; ++q) idj[q] = kid[q * 32 + j];
+#pragma unroll
+        for (int r = 0; r < kMwSpl; ++r) {
+          const uint32_t op = mop[r];
+          int k = mw_occ<kOBW>(obj, (int)(op & 0xffu));
+          if (op & 0x10000u) k *= mw_occ<kOBW>(obj, (int)((op >> 8) & 0xffu)) - (int)((op >> 17) & 1u);
+          bool act = k > 0 && tD[r] >= 0;
+          y[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (act) {
+            int esum = 0;
+#pragma unroll
+            for (int q = 0; q < kIW; ++q) {
+              if (q >= iw) break;
+              const uint32_t u =
+                  (uint32_t)idj[q] + (kHoist ? msh[r][kHoist ? q : 0] : (uint32_t)shf[q * np + r * 32 + lane]);
+              if (EXACT) {
+                if (q >= 1) esum += *reinterpret_cast<const int32_t*>(Eg + u);
+              } else {
+                esum += e_byte(u & 0xffffu);
+                if (MT == 0 || 2 * q + 2 < MT) esum += e_byte(u >> 16);
+              }
+            }
+            const int rk = tD[r] - 1 - esum;
+            if ((unsigned)rk >= (unsigned)tD[r]) {
+              atomicOr(status, 1);
+              act = false;
+            } else {
+              y[r] = __ldg(f + toff[r] + rk);
+            }
+          }
+          cc[r] = df_mul_f(csc[r], act ? (float)k : 0.f);
+        }
+      };
+      // consume(j): tp += c conj(y) x_j, the same arithmetic as the one-ket loop
+      auto consume = [&](int j, const float4 (&y4)[kMwSpl], const dfl (&cc)[kMwSpl]) {
+        const float4 xj = kx[j];
+#pragma unroll
+        for (int r = 0; r < kMwSpl; ++r) {
+          const float4 y = y4[r];
+          const f2 xr = f2_pack(xj.x, xj.x), nxr = f2_pack(-xj.x, -xj.x), xrl = f2_pack(xj.z, xj.z);
+          const f2 xi = f2_pack(xj.y, xj.y), nxi = f2_pack(-xj.y, -xj.y), xil = f2_pack(xj.w, xj.w);
+          const f2 one_m = f2_pack(1.f, -1.f);
+          const f2 Ph = f2_mul(f2_pack(y.x, y.y), one_m), Pl = f2_mul(f2_pack(y.z, y.w), one_m);
+          const f2 Sh = f2_pack(y.y, y.x), Sl = f2_pack(y.w, y.z);
+          const f2 n1 = f2_mul(nxr, Ph);
+          f2 e1 = f2_fma(xr, Ph, n1);
+          e1 = f2_fma(xr, Pl, e1);
+          e1 = f2_fma(xrl, Ph, e1);
+          const f2 n2 = f2_mul(nxi, Sh);
+          f2 e2 = f2_fma(xi, Sh, n2);
+          e2 = f2_fma(xi, Sl, e2);
+          e2 = f2_fma(xil, Sh, e2);
+          const f2 ns = f2_add(n1, n2);
+          const f2 bb = f2_sub(ns, n1);
+          const f2 nerr = f2_add(f2_sub(n1, f2_sub(ns, bb)), f2_sub(n2, bb));
+          const f2 nsl = f2_sub(f2_sub(nerr, e1), e2);
+          const dfl c = cc[r];
+          const f2 Ch = f2_pack(c.h, c.h), nCh = f2_pack(-c.h, -c.h), nCl = f2_pack(-c.l, -c.l);
+          dfc_fma(tp[r], nCh, Ch, nCl, ns, nsl);
+        }
+      };
+      float4 ya[kMwSpl], yb[kMwSpl];
+      dfl ca[kMwSpl], cb[kMwSpl];
+      issue(0, ya, ca);
+      for (int j = 0; j < nt; j += 2) {
+        const bool two = j + 1 < nt;
+        if (two) issue(j + 1, yb, cb);
+        consume(j, ya, ca);
+        if (two) {
+          if (j + 2 < nt) issue(j + 2, ya, ca);
+          consume(j + 1, yb, cb);
+        }
+      }
+    } else {
+#endif
     for (int j = 0; j < nt; ++j) {
       const int nkj = knk[j];
       if (nkj != cur_nk) {  // warp-uniform: a new (N, K) sector
@@ -557,6 +675,9 @@ __global__ void __launch_bounds__(kMwBlock, QB_MW_MIN_BLOCKS) moments_w_kernel(c
         dfc_fma(tp[r], nCh, Ch, nCl, ns, nsl);
       }
     }
+#if QB_MW_PIPE
+    }
+#endif
     // the tile's sums into the lane's FP64 accumulators
 #pragma unroll
     for (int r = 0; r < kMwSpl; ++r) {
@@ -621,8 +742,9 @@ static int launch_mw(const Space& s, const double2* psi, const float4* f, double
   const Tables& t = s.t;
   const int np = (nent + 31) & ~31;
   const int sec_smem = mw_sec_bytes(t) <= kMwSecSmemMax ? 1 : 0;
+  constexpr int kMwWarps = mw_warps(SPL), kMwBlock = 32 * kMwWarps;
   const size_t smem = (size_t)(EXACT ? 0 : mw_table_bytes(t)) +
-                      mw_smem_after(np, t.nmax, nmom, MwWords<MT, EXACT>::n, MwOccWords<MT>::n) +
+                      mw_smem_after(np, t.nmax, nmom, MwWords<MT, EXACT>::n, MwOccWords<MT>::n, kMwWarps) +
                       (sec_smem ? mw_sec_bytes(t) : 0);
   auto k = moments_w_kernel<MT, EXACT, SPL>;
   int grid = 0;
