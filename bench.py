@@ -592,7 +592,7 @@ def main():
         "frac": achieved / dfma_tflops, "peak_kind": "measured DFMA rate of this GPU (qb_measure_fp64_fma)",
         "peak_unit_count": FP64_PEAK_TFLOPS, "frac_of_unit_count": achieved / FP64_PEAK_TFLOPS,
         "traffic": STAGE_DRAM_BYTES_PER_KET * qs.total if args.config == "batched_coherent" else None,
-        "kernel": f"stage_df_kernel<{W.M},1,0,0,1,0> (one RK4 stage = one H psi over all sectors, weighted basis)",
+        "kernel": f"stage_df_kernel<{W.M},1,0,0,1,{qs.tile_shape}> (one RK4 stage = one H psi over all sectors, weighted basis)",
         "stage_ms": stage_time * 1e3,
         "peak_note": "FP64-equivalent flops (2 FMA/term) vs the FP64 FMA rate measured on this GPU; the "
                      "kernel itself runs double-float on the FP32/ALU pipes (FP64 pipe idle), so frac > 1 "
