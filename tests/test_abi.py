@@ -117,3 +117,52 @@ def test_squeezing_analysis_matches_oracle():
     y = 0.9 * x ** -0.2 * np.exp(0.01 * rng.standard_normal(x.size))
     for kind in ("power", "log"):
         np.testing.assert_allclose(api.fit(x, y, kind), orc.fit(x, y, kind), rtol=1e-12)
+
+
+def test_null_space_is_refused_without_device():
+    """Every entry point that takes a space refuses NULL with QB_EINVAL (the size
+    queries with -1) before any device call, and names the fault in qb_last_error."""
+    import paper_2111_00050_gb300._lib as L
+
+    lib = L.lib()
+    d = ctypes.c_double()
+    i64 = ctypes.c_int64()
+    i32 = ctypes.c_int()
+    z = (ctypes.c_double * 32)()
+    g = (ctypes.c_double * 32)()
+    gl = (ctypes.c_double * (2 * 16 ** 4))()
+    occ = (ctypes.c_int * 16)()
+    obs = L.QbObs()
+    series = (L.QbObs * 2)()
+    scale = (ctypes.c_double * 1)(1.0)
+    calls = {
+        "qb_space_info": (None, ctypes.byref(i64), ctypes.byref(i32), ctypes.byref(i64)),
+        "qb_space_sectors": (None, None, None, None, None),
+        "qb_space_basis": (None, 0, 1, None, None),
+        "qb_space_rank": (None, None, 1, None, None),
+        "qb_space_terms": (None, ctypes.byref(i64), None, None),
+        "qb_init_number": (None, occ, None, None),
+        "qb_init_coherent": (None, z, None, ctypes.byref(d), None),
+        "qb_init_field_number": (None, z, 4, None, None),
+        "qb_hpsi": (None, None, None, None),
+        "qb_evolve": (None, None, 1e-3, 1, None, None),
+        "qb_evolve_batch": (None, None, 1, scale, 1e-3, 1, None, None),
+        "qb_evolve_plain": (None, None, 1e-3, 1, None, None),
+        "qb_space_set_resident_max": (None, 0),
+        "qb_space_set_tile_shape": (None, 0),
+        "qb_space_set_order": (None, 4),
+        "qb_observables": (None, None, ctypes.byref(obs), None),
+        "qb_observables_noalloc": (None, None, ctypes.byref(obs), None),
+        "qb_evolve_observe": (None, None, 1e-3, 1, 1, series, None, None),
+        "qb_adjoint": (None, z, 1.0, 1e-3, 1, 1, 0, ctypes.byref(d), ctypes.byref(d), g, z, None, None),
+        "qb_adjoint_couplings": (None, z, 1.0, 1e-3, 1, 1, 0, ctypes.byref(d), ctypes.byref(d), g, z, gl, None,
+                                 None),
+        "qb_space_status": (None, 0, ctypes.byref(i32), None),
+    }
+    for name, args in calls.items():
+        rc = getattr(lib, name)(*args)
+        assert rc == 1, (name, rc)  # QB_EINVAL
+        assert lib.qb_last_error(), name
+    assert lib.qb_workspace_bytes(None, 1) == -1
+    assert lib.qb_adjoint_workspace_bytes(None, 1, 1) == -1
+    lib.qb_space_free(None)  # a no-op
