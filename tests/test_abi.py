@@ -166,3 +166,32 @@ def test_null_space_is_refused_without_device():
     assert lib.qb_workspace_bytes(None, 1) == -1
     assert lib.qb_adjoint_workspace_bytes(None, 1, 1) == -1
     lib.qb_space_free(None)  # a no-op
+
+
+def test_host_only_entry_points_refuse_bad_arguments():
+    """The host-only analysis calls return QB_EINVAL on the arguments their header
+    comments exclude (NULL pointers, too few samples, a non-positive spacing, an
+    unknown fit kind, data a power-law fit cannot take the log of)."""
+    import paper_2111_00050_gb300._lib as L
+
+    lib = L.lib()
+    d, d2, d3 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    flag = ctypes.c_int()
+    v = (ctypes.c_double * 4)(0.9, 0.85, 0.7, 0.75)
+    x = (ctypes.c_double * 3)(1.0, 2.0, 4.0)
+    y = (ctypes.c_double * 3)(1.0, -2.0, 4.0)
+    assert lib.qb_breaktime(None, 4, 0.1, 0.5, ctypes.byref(d), ctypes.byref(flag)) == 1
+    assert lib.qb_breaktime(v, -1, 0.1, 0.5, ctypes.byref(d), ctypes.byref(flag)) == 1
+    assert lib.qb_breaktime(v, 4, 0.1, 0.5, None, ctypes.byref(flag)) == 1
+    sq = (ctypes.byref(d), ctypes.byref(flag), ctypes.byref(d2), ctypes.byref(d3))
+    assert lib.qb_squeezing(v, 0, 0.1, 0.8, *sq) == 1
+    assert lib.qb_squeezing(v, 4, 0.0, 0.8, *sq) == 1
+    assert lib.qb_squeezing(v, 4, 0.1, 0.8, *sq) == 0 and flag.value == L.QB_CROSSED
+    assert lib.qb_fit(x, x, 1, 0, ctypes.byref(d), ctypes.byref(d2)) == 1  # n < 2
+    assert lib.qb_fit(x, x, 3, 2, ctypes.byref(d), ctypes.byref(d2)) == 1  # unknown kind
+    assert lib.qb_fit(x, y, 3, 0, ctypes.byref(d), ctypes.byref(d2)) == 1  # log of a negative y
+    assert lib.qb_fit(x, y, 3, 1, ctypes.byref(d), ctypes.byref(d2)) == 0  # y = c0 + c1 log x takes any y
+    z = (ctypes.c_double * 4)()
+    traj = (ctypes.c_double * 8)()
+    assert lib.qb_meanfield(None, z, 1e-3, 1, 1, traj) == 1
+    assert lib.qb_interaction_per_occupation(None, z, ctypes.byref(d)) == 1
