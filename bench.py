@@ -204,7 +204,7 @@ def cpu_baseline(W, seconds_cap: float = 15.0):
 
 def adjoint_extra(qb, torch, steps: int = 20, ckpt_every: int = 10):
     """Adjoint workload (M=5, contact C=-0.1, complex-Gaussian alpha scaled to n_tot=40,
-    N <= 77: 390 sectors, 27.3M kets): forward RK4 time per step against the time per
+    N <= 77: 386 sectors, 27.3M kets): forward RK4 time per step against the time per
     step of qb_adjoint (forward pass with checkpoints + loss + backward costate pass)."""
     W = wl.adjoint_coherent()
     L0 = wl.contact_coupling(W.M, 1.0)

@@ -130,7 +130,7 @@ def test_autograd_function_returns_adjoint_gradients():
 
 def test_adjoint_full_size_against_central_differences():
     """The adjoint benchmark workload at full size (M=5, contact, complex-Gaussian
-    amplitudes with n_tot = 40, N <= 77: 390 sectors, 27,285,336 kets), 4 steps with
+    amplitudes with n_tot = 40, N <= 77: 386 sectors, 27,285,336 kets), 4 steps with
     checkpoints every 2: d Q / d scale, d Q / d w_2 and d Q / d Im z_1 against central
     differences of the loss.  After 4 steps Q and its w-derivatives are small (~5e-9),
     so the steps are sized for the loss's rounding: h = 1e-4 for the scale, 1e-2 for
