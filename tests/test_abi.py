@@ -39,6 +39,21 @@ def test_obs_struct_layout_matches_header():
     assert ctypes.sizeof(L.QbObs) == 8 * (10 + 2 * M + 4 * M * M + 2 * M + M + M)
 
 
+def test_header_constants_match_binding():
+    """Every QB_* value constant of include/*.h equals the binding's constant of the
+    same name."""
+    import paper_2111_00050_gb300._lib as L
+
+    found = 0
+    inc = os.path.join(ROOT, "include")
+    for h in sorted(os.listdir(inc)):
+        if h.endswith(".h"):
+            for name, value in re.findall(r"^#define (QB_[A-Z0-9_]+) (\d+)", open(os.path.join(inc, h)).read(), re.M):
+                assert getattr(L, name) == int(value), name
+                found += 1
+    assert found >= 14
+
+
 def test_host_only_entry_points():
     import paper_2111_00050_gb300 as qb
 
